@@ -1,0 +1,82 @@
+"""Seeded synthetic workloads: parameters and input generators only.
+
+This module holds none of the method's arithmetic.  It names the problem instances (lattice
+parameters, temperatures, external frequencies, seeds, sample counts) and generates the
+random inputs that are passed to both the CUDA path and the CPU oracle.  Momentum samples are
+not generated here: each side draws them from Philox4x32-10 (Salmon et al., SC'11) with the
+counter layout (sample_lo, sample_hi, internal_variable, 0) and key (seed_lo, seed_hi).
+
+The paper's benchmark diagrams (its Fig. diagrams) are not available, so the instances below
+use Hubbard self-energy diagrams from this project's own enumerator at the paper's orders.
+"""
+import math
+
+import numpy as np
+
+PI = math.pi
+SEED = 20231128
+
+
+def matsubara(beta, n_freq, first=0):
+    """Fermionic Matsubara frequencies i(2n+1)pi/beta, n = first .. first+n_freq-1
+    (the paper's example frequencies, Sec. 5.1)."""
+    n = np.arange(first, first + n_freq, dtype=np.float64)
+    return 1j * (2.0 * n + 1.0) * PI / beta
+
+
+def real_axis(omega_lo, omega_hi, n, gamma):
+    """omega + i Gamma on a uniform grid (analytic continuation i nu -> omega + i0+)."""
+    return np.linspace(omega_lo, omega_hi, n) + 1j * gamma
+
+
+# Order-2 Hubbard self-energy in the basis (q, k', k_ext): lines q+k_ext, k', q+k'; q is a
+# bosonic transfer, k' fermionic.  t=1, mu=0, beta=5, U=1, one frequency i pi/beta, 1e5 samples.
+ORDER2 = dict(
+    name="order2_hubbard_sigma",
+    alpha=np.array([[1, 0, 1], [0, 1, 0], [1, 1, 0]], dtype=np.int32),
+    var_is_boson=np.array([1, 0, 0], dtype=np.int32),
+    t=1.0, tp=0.0, mu=0.0, beta=5.0, U=1.0, kext=(PI / 2, PI / 2),
+    n_freq=1, n_samples=100_000, seed=SEED,
+)
+
+# Order-4 Hubbard self-energy: the diagram with the largest flat term count among the order-4
+# diagrams of the project's enumerator (canonical code below; 7 lines, 4 loop momenta).
+# t=1, t'=-0.3, mu=-0.5, beta=8, 16 fermionic Matsubara frequencies n=0..15, 2^24 samples.
+ORDER4 = dict(
+    name="order4_hubbard_sigma",
+    order=4,
+    code=(0, 1, 1, 4, 2, 3, 3, 2, 0),
+    t=1.0, tp=-0.3, mu=-0.5, beta=8.0, U=1.0, kext=(PI / 2, PI / 2),
+    n_freq=16, n_samples=1 << 24, seed=SEED,
+)
+
+# Order-3 self-energy continued to the real axis: omega + i 0.05 on 256 points in [-4, 4].
+ORDER3_REAL = dict(
+    name="order3_sigma_real_axis",
+    order=3, diagram_index=0,
+    t=1.0, tp=0.0, mu=0.0, beta=10.0, U=1.0, kext=(PI / 2, PI / 2),
+    omega=(-4.0, 4.0, 256), gamma=0.05, n_samples=1 << 22, seed=SEED,
+)
+
+# Every order-2..5 diagram in one launch: diagram d gets 2^(20 + d mod 4) samples, 32 freqs.
+ALL_ORDERS = dict(
+    name="sigma_orders_2_to_5",
+    orders=(2, 3, 4, 5), t=1.0, tp=0.0, mu=0.0, beta=5.0, U=1.0, kext=(PI / 2, PI / 2),
+    n_freq=32, seed=SEED,
+)
+
+
+def all_orders_samples(d):
+    return 1 << (20 + d % 4)
+
+
+def lattice(cfg):
+    """(t, t', mu, kx_ext, ky_ext) as passed to both sides."""
+    return (cfg["t"], cfg["tp"], cfg["mu"], cfg["kext"][0], cfg["kext"][1])
+
+
+def random_energies(n_e, n_lines, a=8.0, seed=SEED):
+    """Energy-input workload of the paper's evaluation example (Sec. 5.1): base energies
+    uniform on (-a, a), one row per configuration."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-a, a, size=(n_e, n_lines))
