@@ -1,0 +1,154 @@
+/*
+ * tami.h -- C ABI of libtami, a GB300 (sm_103a) implementation of the batched evaluation of
+ * algorithmic Matsubara integration (AMI) solutions.
+ *
+ * Method: M. D. Burke and J. P. F. LeBlanc, "TorchAmi: Generalized CPU/GPU Implementation of
+ * Algorithmic Matsubara Integration", arXiv:2311.17189.  Section, equation and figure names
+ * below are the paper's.
+ *
+ * Conventions (all calls):
+ *   - Status: every int-returning call returns TAMI_OK (0) or one of the TAMI_E* codes below;
+ *     tami_last_error() then gives a message (per host thread).  Nothing throws across the ABI.
+ *   - Complex numbers are two adjacent doubles (re, im).  Arrays are C-contiguous.
+ *   - "device" pointers are CUDA global-memory pointers on the device the diagram was uploaded
+ *     to; they are owned by the caller and must stay valid until the stream has run the work.
+ *     "host" pointers are ordinary CPU memory read before the call returns.
+ *   - stream: a cudaStream_t (NULL = legacy default stream).  Device work is asynchronous on it;
+ *     outputs are valid once the stream is synchronised.
+ *   - A diagram is library-owned: created by tami_construct, freed by tami_destroy.  Its device
+ *     term table is created by tami_upload and freed by tami_destroy.
+ *   - Variables: n_vars = m + 1 frequency/momentum labels, the m internal (summed) ones first and
+ *     the external one last (Sec. 2.3, "external frequency(s) are the last elements").
+ *   - Lines: n_lines = N Green's functions G_j = 1/(X_j + E_j) (Eq. Green_Function) with
+ *     X_j = sum_l i alpha_jl nu_l and E_j = sum_k eps_jk E_k (base energies E_k).
+ */
+#ifndef TAMI_H
+#define TAMI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* tami_stream_t; /* identical to cudaStream_t */
+
+enum {
+  TAMI_OK = 0,
+  TAMI_EINVAL = 1,       /* bad argument (sizes, NULL, malformed labels)                  */
+  TAMI_ENOMEM = 2,       /* host or device allocation failed                               */
+  TAMI_ECUDA = 3,        /* a CUDA runtime call failed                                     */
+  TAMI_ETIMEOUT = 4,     /* a bounded device wait gave up                                  */
+  TAMI_EUNSUPPORTED = 5  /* valid input outside what this build handles (see message)     */
+};
+
+enum { TAMI_MAX_LINES = 16, TAMI_MAX_VARS = 8 };
+
+typedef struct tami_diagram tami_diagram;
+
+/* Square-lattice Hubbard dispersion eps(k) = -2t(cos kx + cos ky) - 4t' cos kx cos ky and the
+ * external momentum; the line energy is E = mu - eps(k) (Sec. 5.2: per-line dispersion of the
+ * composed momenta K = k A^T; Eq. Green_Function: epsilon^j is minus the dispersion). */
+typedef struct {
+  double t, tp, mu;
+  double kx_ext, ky_ext;
+} tami_lattice;
+
+/* Sizes of a constructed solution and of its device table. */
+typedef struct {
+  int n_lines, n_vars;
+  int64_t n_terms;          /* flat terms A * FT * R (FACTORIZE=false form, Sec. 2.2)        */
+  int64_t n_fermi_factors;  /* Fermi/Bose factors over all terms                              */
+  int64_t n_g_factors;      /* Green's functions over all terms, powers counted               */
+  int max_der;              /* highest derivative order of a Fermi/Bose factor (Eq. Res_mul)  */
+  int max_g;                /* most Green's functions in one term                             */
+  int64_t unique_poles;     /* distinct (energy combination up to sign, sigma) of FT factors  */
+  int64_t unique_dens;      /* distinct (energy combination, external coefficient) of R       */
+  /* device table */
+  int n_combos;             /* distinct energy combinations c.E evaluated per sample          */
+  int n_fermi_values;       /* distinct Fermi/Bose values per sample                          */
+  int n_real_dens;          /* frequency-independent denominators                            */
+  int n_cplx_dens;          /* denominators carrying the external frequency                   */
+  int n_groups_fixed;       /* groups of terms with one denominator signature                 */
+  int n_groups_freq;        /* groups sharing one frequency-dependent signature               */
+  int table_bytes;
+  /* FP64 flops of the kernels' explicit arithmetic (fma = 2): per sample (frequency
+   * independent part, library math calls counted as one flop each) and per (sample, frequency) */
+  double flops_per_sample;
+  double flops_per_sample_freq;
+} tami_info;
+
+const char* tami_last_error(void);
+
+/* Build the AMI solution (Sec. 2.2) of beta^-m sum_{nu_1..nu_m} prod_j G_j (Eq. goal) by summing
+ * nu_1..nu_m with the residue theorem (Eq. Res_Th), multipole residues (Eq. Res_mul) for
+ * coinciding poles.
+ *   alpha        host int8 [n_lines][n_vars], entries in {-1,0,1}, external column last.
+ *   eps          host int8 [n_lines][n_lines] energy coefficients, or NULL for the identity
+ *                (Sec. 5.1: the starting point; rows of lines with equal alpha may be equal).
+ *   var_is_boson host uint8 [n_vars] or NULL (all fermionic, as in the paper).  A bosonic
+ *                internal variable is summed with weight -n_B.
+ *   order        host int32 [n_vars-1] summation order or NULL for 0,1,..,m-1 (Sec. 5.1).
+ *   prefactor    constant multiplying the whole integrand (e.g. (-U)^m (-1)^F).
+ * Errors: TAMI_EINVAL for bad sizes/labels, TAMI_EUNSUPPORTED if a summed variable appears with
+ * |coefficient| > 1, a term decays slower than 1/z^2, or a Bose factor sits at zero energy. */
+int tami_construct(int n_lines, int n_vars, const int8_t* alpha, const int8_t* eps,
+                   const uint8_t* var_is_boson, const int32_t* order, double prefactor,
+                   tami_diagram** out);
+
+int tami_diagram_info(const tami_diagram* d, tami_info* info);
+
+/* Copy the flattened term table to `device` (cudaMalloc + cudaMemcpyAsync on `stream`).
+ * Must precede every evaluation call.  Re-uploading to another device moves the table. */
+int tami_upload(tami_diagram* d, int device, tami_stream_t stream);
+
+/* Per-sample momenta and line energies exactly as tami_forward forms them (Sec. 5.2): internal
+ * momenta from Philox4x32-10, counter (s_lo, s_hi, l, 0), key (seed_lo, seed_hi), sample
+ * s = offset + i; line momenta K_j = sum_l alpha_jl k_l + alpha_j,ext k_ext; E_j = mu - eps(K_j).
+ *   E  device double [n][n_lines] (row i = sample offset+i). */
+int tami_sample_energies(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
+                         int64_t n, double* E, tami_stream_t stream);
+
+/* Energy-input evaluation (Sec. 2.3, energy_t / frequency_t): for each configuration i and
+ * external frequency f, the sum over terms of A * FT(E_i) * R(E_i, X_f).
+ *   E    device double [n_e][n_lines] base energies.
+ *   X    device double [n_f][2] external frequencies (i nu_n, or omega + i Gamma after analytic
+ *        continuation).
+ *   out  device double [n_f][n_e][2] (rows are frequencies, Sec. 2.3). */
+int tami_eval_energies(const tami_diagram* d, const double* E, int64_t n_e, const double* X, int n_f,
+                       double beta, double* out, tami_stream_t stream);
+
+/* Scratch needed by tami_forward for n samples and n_f frequencies (per-block partial sums). */
+int tami_forward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, size_t* bytes);
+
+/* Monte Carlo evaluation over momenta (Sec. 5.2; samples and their energies as in
+ * tami_sample_energies), reduced over samples (Sec. 2.3, "summing the rows"):
+ *   X           device double [n_f][2]
+ *   mean        device double [n_f][2]  sample mean of the integrand
+ *   var         device double [n_f][2]  unbiased sample variances of Re and Im (may be NULL)
+ *   per_sample  device double [n_f][n][2] every sample's value, or NULL
+ *   workspace   device, at least tami_forward_workspace() bytes, 256-byte aligned.
+ * The reduction is deterministic for fixed (n, n_f, device). */
+int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
+                 int64_t n_samples, const double* X, int n_f, double beta, double* mean, double* var,
+                 double* per_sample, void* workspace, size_t workspace_bytes, tami_stream_t stream);
+
+/* Hubbard (U n_up n_down) self-energy diagrams of the given order (2..6), one-particle
+ * irreducible, without tadpoles, in canonical order, labelled with momentum-conserving alpha
+ * (Sec. 2.5: graph representation and labelling).  With capacity 0 only *n_out is set.
+ *   alpha  host int8  [capacity][2m-1][m+1]
+ *   eps    host int8  [capacity][2m-1][2m-1]  (lines with equal labels share a base energy)
+ *   code   host int32 [capacity][1+2m]        canonical contraction code
+ *   loops  host int32 [capacity]              closed fermion loops F (sign (-1)^F)
+ * Any output pointer may be NULL. */
+int tami_enumerate_sigma(int order, int capacity, int8_t* alpha, int8_t* eps, int32_t* code,
+                         int32_t* loops, int* n_out);
+
+void tami_destroy(tami_diagram* d);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TAMI_H */

@@ -350,14 +350,15 @@ int construct(int N, int nv, const int* alpha, const int* eps, const int* boson,
 // Fermi/Bose factors and their derivatives.
 // g = g_sigma(x) and h = 1 - g obey dg/dx = -beta g h and dh/dx = +beta g h for both
 // sigma, so d^k g/dx^k is a homogeneous polynomial of degree k+1 in (g, h).  g and h are
-// formed from y = exp(-beta |x|) through expm1, which keeps both accurate for any x.
+// formed from y = exp(-beta |x|) (exact in relative terms for the tails, where g or h is
+// tiny) and, for sigma = -1, 1 - y = -expm1(-beta |x|) (exact in relative terms near x = 0).
 // ---------------------------------------------------------------------------------------
 struct GH { double g, h; };
 
 GH fermi_gh(int sigma, double beta, double x) {
-  double em = std::expm1(-beta * std::fabs(x));   // y - 1
-  double y = em + 1.0;
-  double D = sigma == 1 ? 2.0 + em : -em;          // 1 + sigma y
+  double nt = -beta * std::fabs(x);
+  double y = std::exp(nt);
+  double D = sigma == 1 ? 1.0 + y : -std::expm1(nt);   // 1 + sigma y
   double sy = sigma * y;
   if (x <= 0) return {1.0 / D, sy / D};
   return {sy / D, 1.0 / D};

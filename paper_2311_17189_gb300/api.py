@@ -1,0 +1,141 @@
+"""Python surface of libtami: a Diagram handle over the C ABI (include/tami.h).
+
+Arrays on the device are torch tensors (complex128 / float64, CUDA); the calls run on
+torch's current CUDA stream.  Host-only calls (construction, info, enumeration) take and
+return numpy arrays.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _as_c_pairs(X, device):
+    """complex [n_f] -> contiguous float64 [n_f, 2] on `device`."""
+    torch = _torch()
+    X = torch.as_tensor(X)
+    if not torch.is_complex(X):
+        X = X.to(torch.complex128)
+    X = X.to(device=device, dtype=torch.complex128).reshape(-1)
+    return torch.view_as_real(X).contiguous()
+
+
+class Diagram:
+    """An AMI solution (flat terms A * FT * R, Sec. 2.2) and its device term table."""
+
+    def __init__(self, alpha, eps=None, var_is_boson=None, order=None, prefactor=1.0):
+        a = np.ascontiguousarray(np.asarray(alpha, dtype=np.int8))
+        self.alpha = a
+        self.n_lines, self.n_vars = a.shape
+        e = None if eps is None else np.ascontiguousarray(np.asarray(eps, dtype=np.int8))
+        b = None if var_is_boson is None else np.ascontiguousarray(np.asarray(var_is_boson, dtype=np.uint8))
+        o = None if order is None else np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+        h = ctypes.c_void_p()
+        L.check(L.lib().tami_construct(self.n_lines, self.n_vars, L._np_ptr(a), L._np_ptr(e), L._np_ptr(b),
+                                       L._np_ptr(o), float(prefactor), ctypes.byref(h)))
+        self._h = h
+        self.device = None
+        self._ws = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                L.lib().tami_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def info(self):
+        i = L.Info()
+        L.check(L.lib().tami_diagram_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in L.Info._fields_}
+
+    def upload(self, device=None):
+        torch = _torch()
+        dev = torch.cuda.current_device() if device is None else int(device)
+        with torch.cuda.device(dev):
+            L.check(L.lib().tami_upload(self._h, dev, _stream_ptr()))
+        self.device = dev
+        return self
+
+    # ---------------------------------------------------------------- evaluation
+    def sample_energies(self, lattice, seed, offset, n):
+        torch = _torch()
+        E = torch.empty((n, self.n_lines), dtype=torch.float64, device=f"cuda:{self.device}")
+        lat = L.Lattice(*[float(v) for v in lattice])
+        L.check(L.lib().tami_sample_energies(self._h, ctypes.byref(lat), int(seed), int(offset), int(n),
+                                             ctypes.c_void_p(E.data_ptr()), _stream_ptr()))
+        return E
+
+    def eval_energies(self, E, X, beta):
+        """E: float64 [n_e, n_lines] CUDA tensor; X: complex [n_f].  Returns complex128 [n_f, n_e]."""
+        torch = _torch()
+        E = E.to(dtype=torch.float64).contiguous()
+        Xp = _as_c_pairs(X, E.device)
+        n_e, n_f = E.shape[0], Xp.shape[0]
+        out = torch.empty((n_f, n_e, 2), dtype=torch.float64, device=E.device)
+        L.check(L.lib().tami_eval_energies(self._h, ctypes.c_void_p(E.data_ptr()), n_e,
+                                           ctypes.c_void_p(Xp.data_ptr()), n_f, float(beta),
+                                           ctypes.c_void_p(out.data_ptr()), _stream_ptr()))
+        return torch.view_as_complex(out)
+
+    def workspace(self, n, n_f):
+        torch = _torch()
+        nbytes = ctypes.c_size_t()
+        L.check(L.lib().tami_forward_workspace(self._h, int(n), int(n_f), ctypes.byref(nbytes)))
+        need = (nbytes.value + 255) // 256 * 256
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
+        return self._ws
+
+    def forward(self, lattice, seed, offset, n, X, beta, per_sample=False, out=None):
+        """Monte Carlo mean over n momentum samples (Sec. 5.2).  Returns (mean complex [n_f],
+        var float64 [n_f, 2], per-sample complex [n_f, n] or None)."""
+        torch = _torch()
+        dev = f"cuda:{self.device}"
+        Xp = _as_c_pairs(X, dev)
+        n_f = Xp.shape[0]
+        if out is None:
+            mean = torch.empty((n_f, 2), dtype=torch.float64, device=dev)
+            var = torch.empty((n_f, 2), dtype=torch.float64, device=dev)
+        else:
+            mean, var = out
+        ps = torch.empty((n_f, n, 2), dtype=torch.float64, device=dev) if per_sample else None
+        ws = self.workspace(n, n_f)
+        lat = L.Lattice(*[float(v) for v in lattice])
+        L.check(L.lib().tami_forward(self._h, ctypes.byref(lat), int(seed), int(offset), int(n),
+                                     ctypes.c_void_p(Xp.data_ptr()), n_f, float(beta),
+                                     ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(var.data_ptr()),
+                                     ctypes.c_void_p(ps.data_ptr()) if ps is not None else None,
+                                     ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr()))
+        return (torch.view_as_complex(mean), var, torch.view_as_complex(ps) if ps is not None else None)
+
+
+def enumerate_sigma(order):
+    """Hubbard self-energy diagrams of `order` (libtami's enumerator and labeller, Sec. 2.5):
+    list of dicts with alpha [N, m+1], eps [N, N], code, loops, in canonical order."""
+    m = int(order)
+    N, nv = 2 * m - 1, m + 1
+    n = ctypes.c_int()
+    L.check(L.lib().tami_enumerate_sigma(m, 0, None, None, None, None, ctypes.byref(n)))
+    cnt = n.value
+    a = np.zeros((cnt, N, nv), dtype=np.int8)
+    e = np.zeros((cnt, N, N), dtype=np.int8)
+    c = np.zeros((cnt, 2 * m + 1), dtype=np.int32)
+    lo = np.zeros(cnt, dtype=np.int32)
+    L.check(L.lib().tami_enumerate_sigma(m, cnt, L._np_ptr(a), L._np_ptr(e), L._np_ptr(c), L._np_ptr(lo),
+                                         ctypes.byref(n)))
+    return [{"alpha": a[i], "eps": e[i], "code": tuple(int(v) for v in c[i]), "loops": int(lo[i])}
+            for i in range(cnt)]

@@ -1,0 +1,628 @@
+// Device side of libtami: evaluation of a flattened AMI term table over Monte Carlo momentum
+// samples (Sec. 5.2) or given energies (Sec. 2.3) on sm_103a, FP64/complex128 throughout.
+//
+// Work split.  One thread block owns a tile of S samples at a time:
+//   phase 1 (one thread per sample, frequency independent, Sec. 2.2 "FT is not a function of
+//     the external frequencies"): Philox momenta -> line momenta -> energies -> energy
+//     combinations -> Fermi/Bose values and their derivatives -> per group of terms sharing
+//     one denominator signature, sum_t A_t prod FT factors, times the frequency-independent
+//     denominators -> W[group][sample] in shared memory;
+//   phase 2 (threads over (frequency, sample) pairs): the frequency-dependent reciprocals
+//     1/(a X_f + b) once per denominator, the per-group products, and the sum over groups.
+// Sums over samples stay in registers per thread, are reduced per block in a fixed order,
+// and a second kernel reduces the per-block partials in a fixed order (deterministic).
+//
+// The term table of the diagram is moved into shared memory once per block with a bulk
+// (TMA) copy, cp.async.bulk, completed on an mbarrier whose wait is bounded.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "tami_internal.h"
+
+namespace tami {
+namespace {
+
+constexpr int kBlock = 128;            // threads per block = samples per tile
+constexpr int kMaxFreqPerThread = 16;  // n_f <= kMaxFreqPerThread * kBlock
+constexpr long long kSpinLimit = 1ll << 24;
+
+// ------------------------------------------------------------------------------- helpers
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+}
+
+// [0,1) from 53 bits of two words, then k = 2 pi u - pi with one rounding
+__device__ __forceinline__ double to_momentum(uint32_t hi, uint32_t lo) {
+  unsigned long long m = ((unsigned long long)hi << 21) | (unsigned long long)(lo >> 11);
+  double u = __dmul_rn(__ull2double_rn(m), 0x1.0p-53);
+  const double pi = 0x1.921fb54442d18p+1;
+  return fma(u, 2.0 * pi, -pi);
+}
+
+// cos and sin: Cody-Waite reduction by pi/2 (three-part constant) and Taylor series on
+// [-pi/4, pi/4] (W. J. Cody and W. Waite, 1980).  Every operation is an explicit fma or a
+// rounded mul/add intrinsic, so the result is the same on any IEEE machine that follows
+// the same recipe.
+__device__ __forceinline__ void cw_sincos(double k, double& s_out, double& c_out) {
+  const double two_over_pi = 0x1.45f306dc9c883p-1;
+  const double P1 = 0x1.921fb54442d18p+0, P2 = 0x1.1a62633145c07p-54, P3 = -0x1.f1976b7ed8fbcp-110;
+  double n = rint(__dmul_rn(k, two_over_pi));
+  double r = fma(-n, P1, k);
+  r = fma(-n, P2, r);
+  r = fma(-n, P3, r);
+  double z = __dmul_rn(r, r);
+  double ps = -0x1.2f49b46814157p-57;
+  ps = fma(ps, z, 0x1.952c77030ad4ap-49);
+  ps = fma(ps, z, -0x1.ae7f3e733b81fp-41);
+  ps = fma(ps, z, 0x1.6124613a86d09p-33);
+  ps = fma(ps, z, -0x1.ae64567f544e4p-26);
+  ps = fma(ps, z, 0x1.71de3a556c734p-19);
+  ps = fma(ps, z, -0x1.a01a01a01a01ap-13);
+  ps = fma(ps, z, 0x1.1111111111111p-7);
+  ps = fma(ps, z, -0x1.5555555555555p-3);
+  double sr = fma(__dmul_rn(r, z), ps, r);
+  double pc = 0x1.e542ba4020225p-62;
+  pc = fma(pc, z, -0x1.6827863b97d97p-53);
+  pc = fma(pc, z, 0x1.ae7f3e733b81fp-45);
+  pc = fma(pc, z, -0x1.93974a8c07c9dp-37);
+  pc = fma(pc, z, 0x1.1eed8eff8d898p-29);
+  pc = fma(pc, z, -0x1.27e4fb7789f5cp-22);
+  pc = fma(pc, z, 0x1.a01a01a01a01ap-16);
+  pc = fma(pc, z, -0x1.6c16c16c16c17p-10);
+  pc = fma(pc, z, 0x1.5555555555555p-5);
+  pc = fma(pc, z, -0x1.0000000000000p-1);
+  double cr = fma(z, pc, 1.0);
+  int q = (int)((long long)n & 3);
+  double s = (q == 0) ? sr : (q == 1) ? cr : (q == 2) ? -sr : -cr;
+  double c = (q == 0) ? cr : (q == 1) ? -sr : (q == 2) ? -cr : sr;
+  s_out = s;
+  c_out = c;
+}
+
+// E = mu - eps(k),  eps(k) = -2t(cos kx + cos ky) - 4t' cos kx cos ky
+__device__ __forceinline__ double line_energy(double kx, double ky, double t, double tp, double mu) {
+  double sx, cx, sy, cy;
+  cw_sincos(kx, sx, cx);
+  cw_sincos(ky, sy, cy);
+  double sum = __dadd_rn(cx, cy);
+  double prod = __dmul_rn(cx, cy);
+  return fma(4.0 * tp, prod, fma(2.0 * t, sum, mu));
+}
+
+// 1/d: hardware estimate refined by one third-order Newton-Raphson step,
+// r <- r (1 + e + e^2), e = 1 - d r  (error e^3).
+__device__ __forceinline__ double rcp(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+
+// d^k/dx^k g at (g, h = 1 - g): (-beta)^k sum_i (-1)^i A(k,i) g^(i+1) h^(k-i), A = Eulerian
+__device__ __forceinline__ double fermi_poly(int k, double g, double h, double beta) {
+  if (k == 0) return g;
+  double gh = g * h;
+  if (k == 1) return -beta * gh;
+  double d = h - g;
+  if (k == 2) return beta * beta * gh * d;
+  if (k == 3) return -beta * beta * beta * gh * fma(d, d, -2.0 * gh);
+  double b4 = beta * beta * beta * beta;
+  double h2 = h * h, g2 = g * g;
+  if (k == 4) return b4 * gh * (h2 * h - 11.0 * g * h2 + 11.0 * g2 * h - g2 * g);
+  return -b4 * beta * gh * (h2 * h2 - 26.0 * g * h2 * h + 66.0 * g2 * h2 - 26.0 * g2 * g * h + g2 * g2);
+}
+
+struct FwdParams {
+  TableHeader h;
+  const unsigned char* table;   // device blob, 16-byte aligned, h.bytes long
+  double t, tp, mu, kx, ky;
+  unsigned long long seed, offset;
+  long long n;
+  const double* E_in;           // energy input [n][N] or null
+  const double* X;              // [n_f][2]
+  int n_f;
+  double beta;
+  double* per_sample;           // [n_f][n][2] or null
+  double* partial;              // [gridDim][n_f][4] or null
+  int* status;                  // device status word or null
+};
+
+__host__ __device__ __forceinline__ int align16(int b) { return (b + 15) & ~15; }
+
+// Shared memory: table | X [n_f][2] | CB [n_cden][S] | W [n_g2][S] | red [4][S]
+__host__ __device__ __forceinline__ size_t fwd_smem_bytes(const TableHeader& h, int n_f) {
+  return (size_t)align16(h.bytes) + sizeof(double) * (2 * (size_t)n_f + (size_t)(h.n_cden + h.n_g2 + 4) * kBlock);
+}
+
+__device__ __forceinline__ bool stage_table(unsigned char* dst, const unsigned char* src, int bytes, int* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(d), "l"(src), "r"(bytes), "r"(b) : "memory");
+  }
+  uint32_t done = 0;
+  long long it = 0;
+  for (; it < kSpinLimit && !done; ++it) {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(b) : "memory");
+    if (!done && it > 64) __nanosleep(64);
+  }
+  if (!done) {
+    if (status) atomicExch(status, TAMI_ETIMEOUT);
+    // the copy is still owned by this block: wait for it once more (bounded) before leaving
+    for (long long j = 0; j < kSpinLimit && !done; ++j) {
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                   : "=r"(done) : "r"(b) : "memory");
+      __nanosleep(256);
+    }
+  }
+  return done != 0;
+}
+
+template <bool ENERGY_IN>
+__global__ void __launch_bounds__(kBlock) fwd_kernel(const FwdParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TableHeader& H = P.h;
+  const int tid = threadIdx.x;
+  if (!stage_table(smem, P.table, H.bytes, P.status)) return;
+  double* Xs = reinterpret_cast<double*>(smem + align16(H.bytes));
+  double* CB = Xs + 2 * P.n_f;
+  double* W = CB + H.n_cden * kBlock;
+  double* red = W + H.n_g2 * kBlock;
+  for (int i = tid; i < 2 * P.n_f; i += kBlock) Xs[i] = P.X[i];
+
+  const double* alpha = reinterpret_cast<const double*>(smem + H.off_alpha);
+  const int* repl = reinterpret_cast<const int*>(smem + H.off_repl);
+  const int* combo_ptr = reinterpret_cast<const int*>(smem + H.off_combo_ptr);
+  const int* combo_j = reinterpret_cast<const int*>(smem + H.off_combo_j);
+  const double* combo_c = reinterpret_cast<const double*>(smem + H.off_combo_c);
+  const int* fbase = reinterpret_cast<const int*>(smem + H.off_fbase);
+  const int* fvr = reinterpret_cast<const int*>(smem + H.off_fv);
+  const int* rden = reinterpret_cast<const int*>(smem + H.off_rden);
+  const int* cden = reinterpret_cast<const int*>(smem + H.off_cden);
+  const double* cden_a = reinterpret_cast<const double*>(smem + H.off_cden_a);
+  const int* g1 = reinterpret_cast<const int*>(smem + H.off_g1);
+  const int* g1_tgt = reinterpret_cast<const int*>(smem + H.off_g1_tgt);
+  const int* term = reinterpret_cast<const int*>(smem + H.off_term);
+  const double* term_A = reinterpret_cast<const double*>(smem + H.off_term_A);
+  const int* tfac = reinterpret_cast<const int*>(smem + H.off_tfac);
+  const int* g1rd = reinterpret_cast<const int*>(smem + H.off_g1rd);
+  const int* g2 = reinterpret_cast<const int*>(smem + H.off_g2);
+  const int* g2cd = reinterpret_cast<const int*>(smem + H.off_g2cd);
+
+  // phase-2 assignment: TPF threads per frequency, or several frequencies per thread
+  const int n_f = P.n_f;
+  int tpf, my_f0, my_fstep, my_nf, my_s0, my_sstep;
+  if (n_f <= kBlock) {
+    tpf = kBlock / n_f;
+    my_f0 = tid / tpf;
+    my_fstep = 1;
+    my_nf = my_f0 < n_f ? 1 : 0;
+    my_s0 = tid % tpf;
+    my_sstep = tpf;
+  } else {
+    tpf = 1;
+    my_f0 = tid;
+    my_fstep = kBlock;
+    my_nf = (n_f - tid + kBlock - 1) / kBlock;
+    my_s0 = 0;
+    my_sstep = 1;
+  }
+  double acc[kMaxFreqPerThread][4];
+  for (int i = 0; i < kMaxFreqPerThread; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0;
+  __syncthreads();
+
+  const double beta = P.beta;
+  const long long n_tiles = (P.n + kBlock - 1) / kBlock;
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const long long s0 = tile * kBlock;
+    // ---------------------------------------------------------------- phase 1
+    {
+      const long long s = s0 + tid;
+      if (s < P.n) {
+        double E[kMaxLines];
+        if (ENERGY_IN) {
+          for (int r = 0; r < H.n_rep; ++r) E[repl[r]] = P.E_in[s * H.N + repl[r]];
+        } else {
+          double kx[kMaxVars], ky[kMaxVars];
+          const unsigned long long sg = P.offset + (unsigned long long)s;
+          for (int l = 0; l < H.m; ++l) {
+            uint32_t c[4] = {(uint32_t)sg, (uint32_t)(sg >> 32), (uint32_t)l, 0u};
+            philox4x32_10(c, (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+            kx[l] = to_momentum(c[0], c[1]);
+            ky[l] = to_momentum(c[2], c[3]);
+          }
+          kx[H.m] = P.kx;
+          ky[H.m] = P.ky;
+          for (int r = 0; r < H.n_rep; ++r) {
+            const int j = repl[r];
+            double ax = 0.0, ay = 0.0;
+            for (int l = 0; l < H.nv; ++l) {
+              const double cf = alpha[j * H.nv + l];
+              if (cf != 0.0) { ax = fma(cf, kx[l], ax); ay = fma(cf, ky[l], ay); }
+            }
+            E[j] = line_energy(ax, ay, P.t, P.tp, P.mu);
+          }
+        }
+        double x[kMaxCombos];
+        for (int u = 0; u < H.n_combo; ++u) {
+          double v = 0.0;
+          for (int q = combo_ptr[u]; q < combo_ptr[u + 1]; ++q) v = fma(combo_c[q], E[combo_j[q]], v);
+          x[u] = v;
+        }
+        double fv[kMaxFermiValues];
+        for (int b = 0; b < H.n_fbase; ++b) {
+          // y = e^{-beta|x|} keeps the tails exact; 1 - y = -expm1 only where a Bose form needs it
+          const double xv = x[fbase[4 * b]];
+          const double nt = -beta * fabs(xv);
+          const double y = exp(nt);
+          const double em = fbase[4 * b + 3] ? expm1(nt) : 0.0;
+          int cur_sigma = 0;
+          double g = 0.0, hh = 0.0;
+          for (int v = fbase[4 * b + 1]; v < fbase[4 * b + 2]; ++v) {
+            const int sigma = fvr[4 * v], sign = fvr[4 * v + 1], k = fvr[4 * v + 2];
+            if (sigma != cur_sigma) {
+              cur_sigma = sigma;
+              const double rD = rcp(sigma > 0 ? 1.0 + y : -em);
+              const double t2 = (sigma > 0 ? y : -y) * rD;
+              if (xv <= 0.0) { g = rD; hh = t2; } else { g = t2; hh = rD; }
+            }
+            fv[v] = sign > 0 ? fermi_poly(k, g, hh, beta) : fermi_poly(k, hh, g, beta);
+          }
+        }
+        double rr[kMaxRealDens];
+        for (int i = 0; i < H.n_rden; ++i) rr[i] = rcp(x[rden[2 * i]]);
+        int cur = g1_tgt[0];
+        double wacc = 0.0;
+        for (int gi = 0; gi < H.n_g1; ++gi) {
+          const int tg = g1_tgt[gi];
+          if (tg != cur) { W[cur * kBlock + tid] = wacc; wacc = 0.0; cur = tg; }
+          double ft = 0.0;
+          for (int t = g1[4 * gi]; t < g1[4 * gi + 1]; ++t) {
+            double p = term_A[t];
+            const int f0 = term[t], f1 = term[t + 1];
+            for (int q = f0; q < f1 - 1; ++q) p *= fv[tfac[q]];
+            ft = fma(p, fv[tfac[f1 - 1]], ft);
+          }
+          for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
+            const double r = rr[g1rd[2 * q]];
+            for (int pw = g1rd[2 * q + 1]; pw > 0; --pw) ft *= r;
+          }
+          wacc += ft;
+        }
+        W[cur * kBlock + tid] = wacc;
+        for (int c = 0; c < H.n_cden; ++c) {
+          const double xv = x[cden[2 * c]];
+          CB[c * kBlock + tid] = cden[2 * c + 1] > 0 ? xv : -xv;
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------------------------------------------------------- phase 2
+    for (int fi = 0; fi < my_nf; ++fi) {
+      const int f = my_f0 + fi * my_fstep;
+      const double Xr = Xs[2 * f], Xi = Xs[2 * f + 1];
+      for (int sl = my_s0; sl < kBlock; sl += my_sstep) {
+        const long long s = s0 + sl;
+        if (s >= P.n) break;
+        double rc_re[kMaxCplxDens], rc_im[kMaxCplxDens];
+        for (int c = 0; c < H.n_cden; ++c) {
+          const double a = cden_a[c];
+          const double Dr = fma(a, Xr, CB[c * kBlock + sl]);
+          const double Di = a * Xi;
+          const double r = rcp(fma(Dr, Dr, Di * Di));
+          rc_re[c] = Dr * r;
+          rc_im[c] = -Di * r;
+        }
+        double vr = 0.0, vi = 0.0;
+        for (int hg = 0; hg < H.n_g2; ++hg) {
+          const double w = W[hg * kBlock + sl];
+          const int q0 = g2[hg], q1 = g2[hg + 1];
+          if (q0 == q1) { vr += w; continue; }
+          double Rr = 1.0, Ri = 0.0;
+          bool first = true;
+          for (int q = q0; q < q1; ++q) {
+            const int c = g2cd[2 * q];
+            const double ar = rc_re[c], ai = rc_im[c];
+            for (int pw = g2cd[2 * q + 1]; pw > 0; --pw) {
+              if (first) { Rr = ar; Ri = ai; first = false; }
+              else {
+                const double nr = fma(Rr, ar, -Ri * ai);
+                Ri = fma(Rr, ai, Ri * ar);
+                Rr = nr;
+              }
+            }
+          }
+          vr = fma(w, Rr, vr);
+          vi = fma(w, Ri, vi);
+        }
+        if (P.per_sample) {
+          double2* o = reinterpret_cast<double2*>(P.per_sample) + (size_t)f * P.n + s;
+          *o = make_double2(vr, vi);
+        }
+        acc[fi][0] += vr;
+        acc[fi][1] += vi;
+        acc[fi][2] = fma(vr, vr, acc[fi][2]);
+        acc[fi][3] = fma(vi, vi, acc[fi][3]);
+      }
+    }
+    __syncthreads();
+  }
+  // ------------------------------------------------------------------ block reduction
+  if (!P.partial) return;
+  if (n_f <= kBlock) {
+    for (int k = 0; k < 4; ++k) {
+      red[k * kBlock + tid] = acc[0][k];
+    }
+    __syncthreads();
+    if (tid < n_f) {
+      double* out = P.partial + ((size_t)blockIdx.x * n_f + tid) * 4;
+      for (int k = 0; k < 4; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < tpf; ++j) s += red[k * kBlock + tid * tpf + j];
+        out[k] = s;
+      }
+    }
+  } else {
+    for (int fi = 0; fi < my_nf; ++fi) {
+      const int f = my_f0 + fi * my_fstep;
+      double* out = P.partial + ((size_t)blockIdx.x * n_f + f) * 4;
+      for (int k = 0; k < 4; ++k) out[k] = acc[fi][k];
+    }
+  }
+}
+
+// mean and unbiased variances from per-block partials, summed in block order
+__global__ void finalize_kernel(const double* partial, int n_blocks, int n_f, long long n, const int* status,
+                                double* mean, double* var) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_f) return;
+  double s1r = 0.0, s1i = 0.0, s2r = 0.0, s2i = 0.0;
+  for (int b = 0; b < n_blocks; ++b) {
+    const double* p = partial + ((size_t)b * n_f + f) * 4;
+    s1r += p[0]; s1i += p[1]; s2r += p[2]; s2i += p[3];
+  }
+  const double nn = (double)n;
+  double mr = s1r / nn, mi = s1i / nn;
+  double vr = n > 1 ? (s2r - s1r * mr) / (nn - 1.0) : 0.0;
+  double vi = n > 1 ? (s2i - s1i * mi) / (nn - 1.0) : 0.0;
+  if (status && *status != 0) mr = mi = vr = vi = __longlong_as_double(0x7ff8000000000000ll);
+  mean[2 * f] = mr;
+  mean[2 * f + 1] = mi;
+  if (var) { var[2 * f] = vr; var[2 * f + 1] = vi; }
+}
+
+__global__ void sample_energies_kernel(const FwdParams P, double* E) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= P.n) return;
+  const TableHeader& H = P.h;
+  const double* alpha = reinterpret_cast<const double*>(P.table + H.off_alpha);
+  double kx[kMaxVars], ky[kMaxVars];
+  const unsigned long long sg = P.offset + (unsigned long long)s;
+  for (int l = 0; l < H.m; ++l) {
+    uint32_t c[4] = {(uint32_t)sg, (uint32_t)(sg >> 32), (uint32_t)l, 0u};
+    philox4x32_10(c, (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    kx[l] = to_momentum(c[0], c[1]);
+    ky[l] = to_momentum(c[2], c[3]);
+  }
+  kx[H.m] = P.kx;
+  ky[H.m] = P.ky;
+  for (int j = 0; j < H.N; ++j) {
+    double ax = 0.0, ay = 0.0;
+    for (int l = 0; l < H.nv; ++l) {
+      const double cf = alpha[j * H.nv + l];
+      if (cf != 0.0) { ax = fma(cf, kx[l], ax); ay = fma(cf, ky[l], ay); }
+    }
+    E[s * H.N + j] = line_energy(ax, ay, P.t, P.tp, P.mu);
+  }
+}
+
+// ------------------------------------------------------------------------------- host glue
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return TAMI_ECUDA;
+}
+
+struct DeviceProps { int sms = 0; size_t smem_optin = 0; };
+DeviceProps device_props(int dev) {
+  static std::mutex mu;
+  static DeviceProps cache[64];
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 0 || dev >= 64) return DeviceProps{};
+  if (!cache[dev].sms) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) {
+      cache[dev].sms = p.multiProcessorCount;
+      cache[dev].smem_optin = p.sharedMemPerBlockOptin;
+    }
+  }
+  return cache[dev];
+}
+
+template <bool E_IN>
+int launch_fwd(const tami_diagram* d, FwdParams& P, cudaStream_t stream, int max_blocks) {
+  const size_t smem = fwd_smem_bytes(d->hdr, P.n_f);
+  DeviceProps dp = device_props(d->device);
+  if (smem > dp.smem_optin) { set_error("term table and tiles exceed shared memory"); return TAMI_EUNSUPPORTED; }
+  cudaError_t e = cudaFuncSetAttribute(fwd_kernel<E_IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<E_IN>, kBlock, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+  if (per_sm < 1) per_sm = 1;
+  long long tiles = (P.n + kBlock - 1) / kBlock;
+  long long grid = (long long)dp.sms * per_sm;
+  if (grid > tiles) grid = tiles;
+  if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
+  if (grid < 1) grid = 1;
+  fwd_kernel<E_IN><<<(unsigned)grid, kBlock, smem, stream>>>(P);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "fwd_kernel launch");
+  return TAMI_OK;
+}
+
+int grid_for(const tami_diagram* d, int n_f, long long n) {
+  DeviceProps dp = device_props(d->device);
+  const size_t smem = fwd_smem_bytes(d->hdr, n_f);
+  int per_sm = 0;
+  cudaFuncSetAttribute(fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<false>, kBlock, smem) != cudaSuccess) per_sm = 1;
+  if (per_sm < 1) per_sm = 1;
+  long long tiles = (n + kBlock - 1) / kBlock;
+  long long grid = (long long)dp.sms * per_sm;
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  return (int)grid;
+}
+
+int check_common(const tami_diagram* d, int n_f) {
+  if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
+  if (!d->d_blob) { set_error("diagram not uploaded (call tami_upload)"); return TAMI_EINVAL; }
+  if (n_f < 1 || n_f > kMaxFreqPerThread * kBlock) { set_error("n_f must be in [1, 2048]"); return TAMI_EINVAL; }
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != d->device) { set_error("current device differs from the upload device"); return TAMI_EINVAL; }
+  return TAMI_OK;
+}
+
+FwdParams make_params(const tami_diagram* d, int n_f, double beta) {
+  FwdParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.h = d->hdr;
+  P.table = static_cast<const unsigned char*>(d->d_blob);
+  P.n_f = n_f;
+  P.beta = beta;
+  return P;
+}
+
+constexpr size_t kStatusBytes = 256;
+
+}  // namespace
+}  // namespace tami
+
+using namespace tami;
+
+extern "C" {
+
+int tami_upload(tami_diagram* d, int device, tami_stream_t stream) {
+  if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  if (d->d_blob) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(d->device);
+    cudaFree(d->d_blob);
+    cudaSetDevice(device);
+    d->d_blob = nullptr;
+  }
+  void* p = nullptr;
+  e = cudaMalloc(&p, d->blob.size());
+  if (e != cudaSuccess) { set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e)); return TAMI_ENOMEM; }
+  e = cudaMemcpyAsync(p, d->blob.data(), d->blob.size(), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  if (e != cudaSuccess) { cudaFree(p); return cuda_fail(e, "cudaMemcpyAsync"); }
+  e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) { cudaFree(p); return cuda_fail(e, "cudaStreamSynchronize"); }
+  d->d_blob = p;
+  d->device = device;
+  return TAMI_OK;
+}
+
+int tami_sample_energies(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
+                         int64_t n, double* E, tami_stream_t stream) {
+  int rc = check_common(d, 1);
+  if (rc) return rc;
+  if (!lat || !E || n < 0) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (n == 0) return TAMI_OK;
+  FwdParams P = make_params(d, 1, 1.0);
+  P.t = lat->t; P.tp = lat->tp; P.mu = lat->mu; P.kx = lat->kx_ext; P.ky = lat->ky_ext;
+  P.seed = seed; P.offset = offset; P.n = n;
+  unsigned grid = (unsigned)((n + 255) / 256);
+  sample_energies_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(P, E);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "sample_energies launch");
+}
+
+int tami_eval_energies(const tami_diagram* d, const double* E, int64_t n_e, const double* X, int n_f,
+                       double beta, double* out, tami_stream_t stream) {
+  int rc = check_common(d, n_f);
+  if (rc) return rc;
+  if (!E || !X || !out || n_e < 0) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (n_e == 0) return TAMI_OK;
+  FwdParams P = make_params(d, n_f, beta);
+  P.n = n_e;
+  P.E_in = E;
+  P.X = X;
+  P.per_sample = out;
+  return launch_fwd<true>(d, P, (cudaStream_t)stream, 0);
+}
+
+int tami_forward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, size_t* bytes) {
+  int rc = check_common(d, n_f);
+  if (rc) return rc;
+  if (!bytes || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
+  int grid = grid_for(d, n_f, n_samples);
+  *bytes = kStatusBytes + sizeof(double) * 4 * (size_t)n_f * (size_t)grid;
+  return TAMI_OK;
+}
+
+int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
+                 int64_t n_samples, const double* X, int n_f, double beta, double* mean, double* var,
+                 double* per_sample, void* workspace, size_t workspace_bytes, tami_stream_t stream) {
+  int rc = check_common(d, n_f);
+  if (rc) return rc;
+  if (!lat || !X || !mean || !workspace || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (((uintptr_t)workspace & 255) != 0) { set_error("workspace must be 256-byte aligned"); return TAMI_EINVAL; }
+  const int grid = grid_for(d, n_f, n_samples);
+  const size_t need = kStatusBytes + sizeof(double) * 4 * (size_t)n_f * (size_t)grid;
+  if (workspace_bytes < need) { set_error("workspace too small"); return TAMI_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  int* status = static_cast<int*>(workspace);
+  double* partial = reinterpret_cast<double*>(static_cast<char*>(workspace) + kStatusBytes);
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  FwdParams P = make_params(d, n_f, beta);
+  P.t = lat->t; P.tp = lat->tp; P.mu = lat->mu; P.kx = lat->kx_ext; P.ky = lat->ky_ext;
+  P.seed = seed; P.offset = offset; P.n = n_samples;
+  P.X = X;
+  P.per_sample = per_sample;
+  P.partial = partial;
+  P.status = status;
+  rc = launch_fwd<false>(d, P, st, grid);
+  if (rc) return rc;
+  finalize_kernel<<<(n_f + 127) / 128, 128, 0, st>>>(partial, grid, n_f, n_samples, status, mean, var);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "finalize launch");
+}
+
+void tami_destroy(tami_diagram* d) {
+  if (!d) return;
+  if (d->d_blob) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(d->device);
+    cudaFree(d->d_blob);
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  delete d;
+}
+
+}  // extern "C"

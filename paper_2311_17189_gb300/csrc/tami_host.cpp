@@ -1,0 +1,720 @@
+// Host side of libtami: AMI construction (Sec. 2.2), flattening of the solution into the
+// device term table, and the Hubbard self-energy enumerator with its momentum labeller
+// (Sec. 2.5).  This code is cold: it runs once per diagram.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "tami_internal.h"
+
+namespace tami {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+using Factors = std::vector<std::pair<Form, int>>;
+
+void add_factor(Factors& G, const Form& f, int q) {
+  auto it = std::lower_bound(G.begin(), G.end(), f,
+                             [](const std::pair<Form, int>& p, const Form& x) { return p.first < x; });
+  if (it != G.end() && it->first == f) it->second += q;
+  else G.insert(it, {f, q});
+}
+
+bool is_zero(const Form& f) {
+  for (int8_t v : f.e) if (v) return false;
+  for (int8_t v : f.a) if (v) return false;
+  return true;
+}
+
+// n! and the binomial coefficient as doubles (exact for the small arguments used here)
+double fact(int n) { double r = 1.0; while (n > 1) r *= n--; return r; }
+double choose(int n, int k) {
+  double r = 1.0;
+  for (int i = 0; i < k; ++i) r = r * (n - i) / (i + 1);
+  return r;
+}
+
+struct Movable {       // a Green's function left after the pole is taken out
+  Form f;              // its form with z replaced by the pole position
+  int q;               // power
+  int arp;             // its coefficient of the summed variable (0: constant in z)
+};
+
+// Sum over nu_p of every term: residues at the poles of the z-dependent Green's functions
+// (Eq. Res_Th), multipole ones through the Leibniz rule (Eq. Res_mul).
+int sum_over(const std::vector<SymTerm>& in, int p, int nv, const std::vector<uint8_t>& boson,
+             std::vector<SymTerm>& out) {
+  out.clear();
+  for (const SymTerm& T : in) {
+    std::map<Form, std::vector<int>> poles;   // pole position (a linear form) -> factors
+    int degree = 0;
+    for (int i = 0; i < (int)T.G.size(); ++i) {
+      const Form& g = T.G[i].first;
+      int ap = g.a[p];
+      if (ap == 0) continue;
+      if (ap != 1 && ap != -1) {
+        set_error("summed variable appears with a coefficient of magnitude > 1");
+        return TAMI_EUNSUPPORTED;
+      }
+      degree += T.G[i].second;
+      // root of ap z + rest: z0 = -ap * rest
+      Form z0;
+      for (int j = 0; j < kMaxLines; ++j) z0.e[j] = (int8_t)(-ap * g.e[j]);
+      for (int l = 0; l < nv; ++l) z0.a[l] = l == p ? 0 : (int8_t)(-ap * g.a[l]);
+      poles[z0].push_back(i);
+    }
+    if (degree < 2) {
+      set_error("a term decays slower than 1/z^2 in a summed variable");
+      return TAMI_EUNSUPPORTED;
+    }
+    for (const auto& pole : poles) {
+      const Form& z0 = pole.first;
+      const std::vector<int>& mem = pole.second;
+      int M = 0;
+      double sgn = 1.0;
+      for (int i : mem) {
+        M += T.G[i].second;
+        if (T.G[i].first.a[p] < 0 && (T.G[i].second & 1)) sgn = -sgn;
+      }
+      // weight f (fermionic nu_p) or -n_B (bosonic), reduced by the Matsubara shift's parity
+      FermiFactor ff;
+      ff.c = z0.e;
+      int parity = 0;
+      for (int l = 0; l < nv; ++l)
+        if (l != p && !boson[l]) parity += std::abs((int)z0.a[l]);
+      int sigma = boson[p] ? -1 : 1;
+      if (parity & 1) sigma = -sigma;
+      ff.sigma = (int8_t)sigma;
+      bool czero = std::all_of(ff.c.begin(), ff.c.end(), [](int8_t v) { return v == 0; });
+      if (czero && sigma < 0) {
+        set_error("Bose factor at zero energy");
+        return TAMI_EUNSUPPORTED;
+      }
+      std::vector<Movable> rest;
+      std::vector<int> zdep;
+      for (int i = 0; i < (int)T.G.size(); ++i) {
+        if (std::find(mem.begin(), mem.end(), i) != mem.end()) continue;
+        const Form& g = T.G[i].first;
+        int arp = g.a[p];
+        Movable mv{g, T.G[i].second, arp};
+        for (int j = 0; j < kMaxLines; ++j) {
+          int v = g.e[j] + arp * z0.e[j];
+          if (v > 100 || v < -100) { set_error("energy coefficient overflow"); return TAMI_EUNSUPPORTED; }
+          mv.f.e[j] = (int8_t)v;
+        }
+        for (int l = 0; l < nv; ++l) mv.f.a[l] = (int8_t)(g.a[l] + arp * z0.a[l]);
+        mv.f.a[p] = 0;
+        if (is_zero(mv.f)) { set_error("vanishing denominator after substitution"); return TAMI_EUNSUPPORTED; }
+        if (arp) zdep.push_back((int)rest.size());
+        rest.push_back(mv);
+      }
+      // distribute M-1 derivatives over the weight and the z-dependent factors
+      const int n = M - 1;
+      // all (k_1..k_R) with sum <= n; the weight takes k_0 = n - sum (odometer)
+      std::vector<int> kz(zdep.size(), 0);
+      while (true) {
+        int used = 0;
+        for (int v : kz) used += v;
+        if (used <= n) {
+          int k0 = n - used;
+          SymTerm nt;
+          double A = T.A * sgn / fact(k0);
+          for (size_t r = 0; r < zdep.size(); ++r) {
+            const Movable& mv = rest[zdep[r]];
+            int kr = kz[r];
+            double c = choose(mv.q + kr - 1, kr);
+            if ((kr & 1) && mv.arp > 0) c = -c;   // (-1)^k a^k with a = +1
+            A *= c;                                // a = -1: (-1)^k (-1)^k = 1
+          }
+          nt.A = A;
+          nt.F = T.F;
+          FermiFactor f = ff;
+          f.k = (int8_t)k0;
+          nt.F.push_back(f);
+          for (size_t i = 0; i < rest.size(); ++i) {
+            int extra = 0;
+            auto it = std::find(zdep.begin(), zdep.end(), (int)i);
+            if (it != zdep.end()) extra = kz[it - zdep.begin()];
+            add_factor(nt.G, rest[i].f, rest[i].q + extra);
+          }
+          out.push_back(std::move(nt));
+        }
+        // advance odometer
+        size_t pos = 0;
+        while (pos < kz.size()) {
+          if (++kz[pos] <= n) break;
+          kz[pos] = 0;
+          ++pos;
+        }
+        if (pos == kz.size()) break;
+      }
+    }
+  }
+  return TAMI_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ flatten
+namespace {
+
+using Vec = std::array<int8_t, kMaxLines>;
+
+int first_sign(const Vec& v) {
+  for (int8_t x : v) if (x) return x > 0 ? 1 : -1;
+  return 1;
+}
+Vec scaled(const Vec& v, int s) {
+  Vec r;
+  for (int i = 0; i < kMaxLines; ++i) r[i] = (int8_t)(s * v[i]);
+  return r;
+}
+
+struct Blob {
+  std::vector<unsigned char> b;
+  int reserve(size_t bytes) {
+    size_t off = (b.size() + 15) & ~size_t(15);
+    b.resize(off + ((bytes + 15) & ~size_t(15)), 0);
+    return (int)off;
+  }
+  template <class T> T* at(int off) { return reinterpret_cast<T*>(b.data() + off); }
+};
+
+}  // namespace
+
+int flatten(tami_diagram* d) {
+  const int N = d->N, nv = d->nv;
+  // ---- energy combinations (sign-canonical), Fermi values, denominators
+  std::map<Vec, int> combo_id;
+  std::vector<Vec> combos;
+  auto combo = [&](const Vec& v, int* sign) {
+    int s = first_sign(v);
+    Vec c = scaled(v, s);
+    *sign = s;
+    auto it = combo_id.find(c);
+    if (it != combo_id.end()) return it->second;
+    int id = (int)combos.size();
+    combo_id[c] = id;
+    combos.push_back(c);
+    return id;
+  };
+  struct FvKey { int u, sigma, sign, k; bool operator<(const FvKey& o) const {
+      return std::tie(u, sigma, sign, k) < std::tie(o.u, o.sigma, o.sign, o.k); } };
+  std::map<FvKey, int> fv_tmp;   // provisional ids, renumbered by base below
+  struct CdKey { int u, sign, a; bool operator<(const CdKey& o) const {
+      return std::tie(u, sign, a) < std::tie(o.u, o.sign, o.a); } };
+  std::map<int, int> rden_id;
+  std::vector<int> rdens;
+  std::map<CdKey, int> cden_id;
+  std::vector<CdKey> cdens;
+  struct FlatTerm {
+    double A;
+    std::vector<FvKey> fv;
+    std::vector<std::pair<int, int>> rd, cd;   // (id, power), sorted
+  };
+  std::vector<FlatTerm> ft;
+  ft.reserve(d->terms.size());
+  int64_t nF = 0, nG = 0;
+  int max_der = 0, max_g = 0;
+  std::set<std::pair<Vec, int>> upoles;
+  std::set<std::pair<Vec, int>> udens;
+  for (const SymTerm& T : d->terms) {
+    FlatTerm t;
+    t.A = T.A * d->prefactor;
+    for (const FermiFactor& f : T.F) {
+      int s;
+      int u = combo(f.c, &s);
+      FvKey key{u, f.sigma, s, f.k};
+      fv_tmp.emplace(key, 0);
+      t.fv.push_back(key);
+      max_der = std::max(max_der, (int)f.k);
+      upoles.insert({combos[u], f.sigma});
+      ++nF;
+    }
+    int gcount = 0;
+    for (const auto& gq : T.G) {
+      const Form& g = gq.first;
+      int q = gq.second;
+      gcount += q;
+      nG += q;
+      int a = g.a[nv - 1];
+      Vec e = g.e;
+      udens.insert({e, a});
+      int dsign = a ? (a > 0 ? 1 : -1) : first_sign(e);
+      if (dsign < 0 && (q & 1)) t.A = -t.A;     // 1/(-D)^q = (-1)^q / D^q
+      e = scaled(e, dsign);
+      a *= dsign;
+      int s;
+      int u = combo(e, &s);
+      if (a == 0) {
+        auto it = rden_id.find(u);
+        int id;
+        if (it == rden_id.end()) { id = (int)rdens.size(); rden_id[u] = id; rdens.push_back(u); }
+        else id = it->second;
+        t.rd.push_back({id, q});
+      } else {
+        CdKey key{u, s, a};
+        auto it = cden_id.find(key);
+        int id;
+        if (it == cden_id.end()) { id = (int)cdens.size(); cden_id[key] = id; cdens.push_back(key); }
+        else id = it->second;
+        t.cd.push_back({id, q});
+      }
+    }
+    max_g = std::max(max_g, gcount);
+    std::sort(t.rd.begin(), t.rd.end());
+    std::sort(t.cd.begin(), t.cd.end());
+    ft.push_back(std::move(t));
+  }
+  if (max_der > kMaxDer) { set_error("derivative order above the kernels' limit"); return TAMI_EUNSUPPORTED; }
+  // Fermi bases and values, ordered by combination
+  std::map<int, std::vector<FvKey>> by_base;
+  for (auto& kv : fv_tmp) by_base[kv.first.u].push_back(kv.first);
+  std::vector<int> fbase_combo, fbase_begin, fbase_end;
+  std::vector<FvKey> fvs;
+  for (auto& kv : by_base) {
+    fbase_combo.push_back(kv.first);
+    fbase_begin.push_back((int)fvs.size());
+    for (auto& k : kv.second) { fv_tmp[k] = (int)fvs.size(); fvs.push_back(k); }
+    fbase_end.push_back((int)fvs.size());
+  }
+  // ---- groups: by (complex signature) and within it by (real signature)
+  std::map<std::vector<std::pair<int, int>>, int> g2_id;
+  std::vector<std::vector<std::pair<int, int>>> g2s;
+  std::map<std::pair<std::vector<std::pair<int, int>>, std::vector<std::pair<int, int>>>, std::vector<int>> g1map;
+  for (size_t i = 0; i < ft.size(); ++i) {
+    if (!g2_id.count(ft[i].cd)) { g2_id[ft[i].cd] = (int)g2s.size(); g2s.push_back(ft[i].cd); }
+    g1map[{ft[i].cd, ft[i].rd}].push_back((int)i);
+  }
+  struct G1 { int g2; std::vector<std::pair<int, int>> rd; std::vector<int> terms; };
+  std::vector<G1> g1s;
+  for (auto& kv : g1map) g1s.push_back({g2_id[kv.first.first], kv.first.second, kv.second});
+  std::stable_sort(g1s.begin(), g1s.end(), [](const G1& x, const G1& y) { return x.g2 < y.g2; });
+
+  if ((int)combos.size() > kMaxCombos || (int)fvs.size() > kMaxFermiValues ||
+      (int)rdens.size() > kMaxRealDens || (int)cdens.size() > kMaxCplxDens) {
+    set_error("term table exceeds the kernels' per-sample capacities");
+    return TAMI_EUNSUPPORTED;
+  }
+  // ---- momentum labels: representative lines
+  std::vector<int> repl;
+  for (int j = 0; j < N; ++j) {
+    bool dup = false;
+    for (int k = 0; k < j; ++k)
+      if (std::equal(d->alpha.begin() + j * nv, d->alpha.begin() + (j + 1) * nv, d->alpha.begin() + k * nv)) dup = true;
+    if (!dup) repl.push_back(j);
+  }
+  // every base energy that the table reads must be computed
+  std::vector<char> needed(N, 0);
+  for (const Vec& c : combos) for (int j = 0; j < N; ++j) if (c[j]) needed[j] = 1;
+  for (int j = 0; j < N; ++j)
+    if (needed[j] && std::find(repl.begin(), repl.end(), j) == repl.end()) repl.push_back(j);
+  std::sort(repl.begin(), repl.end());
+
+  // ---- blob
+  TableHeader& h = d->hdr;
+  h = TableHeader{};
+  h.N = N; h.nv = nv; h.m = nv - 1;
+  h.n_rep = (int)repl.size();
+  h.n_combo = (int)combos.size();
+  int nnz = 0;
+  for (const Vec& c : combos) for (int j = 0; j < N; ++j) if (c[j]) ++nnz;
+  h.combo_nnz = nnz;
+  h.n_fbase = (int)fbase_combo.size();
+  h.n_fv = (int)fvs.size();
+  h.n_rden = (int)rdens.size();
+  h.n_cden = (int)cdens.size();
+  h.n_g1 = (int)g1s.size();
+  h.n_terms = (int)ft.size();
+  int ntfac = 0, ng1rd = 0, ng2cd = 0;
+  for (auto& t : ft) ntfac += (int)t.fv.size();
+  for (auto& g : g1s) ng1rd += (int)g.rd.size();
+  for (auto& g : g2s) ng2cd += (int)g.size();
+  h.n_tfac = ntfac; h.n_g1rd = ng1rd;
+  h.n_g2 = (int)g2s.size(); h.n_g2cd = ng2cd;
+  h.max_der = max_der;
+  Blob B;
+  h.off_alpha = B.reserve(sizeof(double) * N * nv);
+  h.off_repl = B.reserve(sizeof(int) * h.n_rep);
+  h.off_combo_ptr = B.reserve(sizeof(int) * (h.n_combo + 1));
+  h.off_combo_j = B.reserve(sizeof(int) * nnz);
+  h.off_combo_c = B.reserve(sizeof(double) * nnz);
+  h.off_fbase = B.reserve(sizeof(int) * 4 * h.n_fbase);
+  h.off_fv = B.reserve(sizeof(int) * 4 * h.n_fv);
+  h.off_rden = B.reserve(sizeof(int) * 2 * h.n_rden);
+  h.off_cden = B.reserve(sizeof(int) * 2 * h.n_cden);
+  h.off_cden_a = B.reserve(sizeof(double) * h.n_cden);
+  h.off_g1 = B.reserve(sizeof(int) * 4 * h.n_g1);
+  h.off_g1_tgt = B.reserve(sizeof(int) * h.n_g1);
+  h.off_term = B.reserve(sizeof(int) * (h.n_terms + 1));
+  h.off_term_A = B.reserve(sizeof(double) * h.n_terms);
+  h.off_tfac = B.reserve(sizeof(int) * ntfac);
+  h.off_g1rd = B.reserve(sizeof(int) * 2 * ng1rd);
+  h.off_g2 = B.reserve(sizeof(int) * (h.n_g2 + 1));
+  h.off_g2cd = B.reserve(sizeof(int) * 2 * ng2cd);
+  B.reserve(16);
+  h.bytes = (int)B.b.size();
+
+  for (int j = 0; j < N * nv; ++j) B.at<double>(h.off_alpha)[j] = (double)d->alpha[j];
+  for (int i = 0; i < h.n_rep; ++i) B.at<int>(h.off_repl)[i] = repl[i];
+  {
+    int k = 0;
+    for (int u = 0; u < h.n_combo; ++u) {
+      B.at<int>(h.off_combo_ptr)[u] = k;
+      for (int j = 0; j < N; ++j)
+        if (combos[u][j]) {
+          B.at<int>(h.off_combo_j)[k] = j;
+          B.at<double>(h.off_combo_c)[k] = (double)combos[u][j];
+          ++k;
+        }
+    }
+    B.at<int>(h.off_combo_ptr)[h.n_combo] = k;
+  }
+  for (int b = 0; b < h.n_fbase; ++b) {
+    int* r = B.at<int>(h.off_fbase) + 4 * b;
+    r[0] = fbase_combo[b]; r[1] = fbase_begin[b]; r[2] = fbase_end[b]; r[3] = 0;
+    for (int v = fbase_begin[b]; v < fbase_end[b]; ++v) if (fvs[v].sigma < 0) r[3] = 1;
+  }
+  for (int v = 0; v < h.n_fv; ++v) {
+    int* r = B.at<int>(h.off_fv) + 4 * v;
+    r[0] = fvs[v].sigma; r[1] = fvs[v].sign; r[2] = fvs[v].k; r[3] = 0;
+  }
+  for (int i = 0; i < h.n_rden; ++i) {
+    int* r = B.at<int>(h.off_rden) + 2 * i;
+    r[0] = rdens[i]; r[1] = 1;
+  }
+  for (int i = 0; i < h.n_cden; ++i) {
+    int* r = B.at<int>(h.off_cden) + 2 * i;
+    r[0] = cdens[i].u; r[1] = cdens[i].sign;
+    B.at<double>(h.off_cden_a)[i] = (double)cdens[i].a;
+  }
+  {
+    int tpos = 0, fpos = 0, rdpos = 0;
+    for (int g = 0; g < h.n_g1; ++g) {
+      int* r = B.at<int>(h.off_g1) + 4 * g;
+      r[0] = tpos;
+      for (int ti : g1s[g].terms) {
+        B.at<int>(h.off_term)[tpos] = fpos;
+        B.at<double>(h.off_term_A)[tpos] = ft[ti].A;
+        for (const FvKey& k : ft[ti].fv) B.at<int>(h.off_tfac)[fpos++] = fv_tmp[k];
+        ++tpos;
+      }
+      r[1] = tpos;
+      r[2] = rdpos;
+      for (auto& pr : g1s[g].rd) {
+        B.at<int>(h.off_g1rd)[2 * rdpos] = pr.first;
+        B.at<int>(h.off_g1rd)[2 * rdpos + 1] = pr.second;
+        ++rdpos;
+      }
+      r[3] = rdpos;
+      B.at<int>(h.off_g1_tgt)[g] = g1s[g].g2;
+    }
+    B.at<int>(h.off_term)[tpos] = fpos;
+  }
+  {
+    int pos = 0;
+    for (int g = 0; g < h.n_g2; ++g) {
+      B.at<int>(h.off_g2)[g] = pos;
+      for (auto& pr : g2s[g]) {
+        B.at<int>(h.off_g2cd)[2 * pos] = pr.first;
+        B.at<int>(h.off_g2cd)[2 * pos + 1] = pr.second;
+        ++pos;
+      }
+    }
+    B.at<int>(h.off_g2)[h.n_g2] = pos;
+  }
+  d->blob.swap(B.b);
+
+  // ---- info and the flop model of the kernels' explicit arithmetic
+  tami_info& I = d->info;
+  I.n_lines = N; I.n_vars = nv;
+  I.n_terms = (int64_t)d->terms.size();
+  I.n_fermi_factors = nF; I.n_g_factors = nG;
+  I.max_der = max_der; I.max_g = max_g;
+  I.unique_poles = (int64_t)upoles.size();
+  I.unique_dens = (int64_t)udens.size();
+  I.n_combos = h.n_combo; I.n_fermi_values = h.n_fv;
+  I.n_real_dens = h.n_rden; I.n_cplx_dens = h.n_cden;
+  I.n_groups_fixed = h.n_g1; I.n_groups_freq = h.n_g2;
+  I.table_bytes = h.bytes;
+  const int m = nv - 1;
+  // Counts follow the kernel: fma = 2 flops, mul/add = 1, expm1 = 1, the reciprocal
+  // (estimate + one third-order Newton step) = 3 fma.
+  double fl = 0.0;
+  fl += 3.0 * 2 * m;                                    // u -> k: mul + fma per component
+  for (int j : repl) {
+    int nz = 0;
+    for (int l = 0; l < nv; ++l) if (d->alpha[j * nv + l]) ++nz;
+    fl += 2.0 * 2.0 * nz;                               // line momenta, fma per term and dimension
+    fl += 2.0 * 47.0 + 6.0;                             // cos/sin of both components, energy
+  }
+  fl += 2.0 * nnz;                                      // energy combinations
+  for (int b = 0; b < h.n_fbase; ++b) {
+    std::set<int> sig;
+    for (int v = fbase_begin[b]; v < fbase_end[b]; ++v) sig.insert(fvs[v].sigma);
+    fl += 2.0 + (sig.count(-1) ? 1.0 : 0.0);            // -beta|x|, exp, expm1 (Bose forms)
+    fl += 8.0 * sig.size();                             // D, reciprocal, +-y / D
+    for (int v = fbase_begin[b]; v < fbase_end[b]; ++v) {
+      const int k = fvs[v].k;
+      fl += k == 0 ? 0.0 : k == 1 ? 2.0 : k == 2 ? 5.0 : k == 3 ? 9.0 : 16.0 + 4.0 * k;
+    }
+  }
+  fl += 6.0 * h.n_rden;                                 // real reciprocals
+  fl += (double)ntfac + h.n_terms;                      // term products, fused accumulate
+  for (auto& g : g1s) {
+    for (auto& pr : g.rd) fl += pr.second;              // frequency-independent denominators
+    fl += 1.0;
+  }
+  I.flops_per_sample = fl;
+  double ff = 14.0 * h.n_cden;                          // complex reciprocal per denominator
+  for (auto& g : g2s) {
+    int pw = 0;
+    for (auto& pr : g) pw += pr.second;
+    ff += pw ? 6.0 * (pw - 1) + 4.0 : 1.0;              // complex products, fused accumulate
+  }
+  ff += 6.0;                                            // mean and variance sums
+  I.flops_per_sample_freq = ff;
+  return TAMI_OK;
+}
+
+// ------------------------------------------------------------------------------ enumerator
+namespace {
+
+// Canonical relabelling of a contraction.  up[v] (v < m) is where the up line leaving
+// interaction v goes, up[m] is where the incoming external leg enters (m = external slot);
+// dn[v] likewise for down lines.  Interaction lines are numbered on first visit: first along
+// the external up chain, then, for each numbered line in turn, around the closed up cycle
+// through it and the down cycle through it.
+bool canonical_code(int m, const int* up, const int* dn, std::vector<int>& code) {
+  std::vector<int> newlab(m, -1), visit;
+  std::vector<char> upv(m, 0), dnv(m, 0);
+  auto mark = [&](int v) { if (newlab[v] < 0) { newlab[v] = (int)visit.size(); visit.push_back(v); } };
+  for (int v = up[m]; v != m; v = up[v]) { mark(v); upv[v] = 1; }
+  for (size_t q = 0; q < visit.size(); ++q) {
+    int i = visit[q];
+    if (!upv[i]) for (int v = i;;) { mark(v); upv[v] = 1; v = up[v]; if (v == i) break; }
+    if (!dnv[i]) for (int v = i;;) { mark(v); dnv[v] = 1; v = dn[v]; if (v == i) break; }
+  }
+  if ((int)visit.size() < m) return false;
+  code.resize(2 * m + 1);
+  code[0] = newlab[up[m]];
+  for (int c = 0; c < m; ++c) {
+    int old = visit[c];
+    code[1 + 2 * c] = up[old] == m ? m : newlab[up[old]];
+    code[2 + 2 * c] = newlab[dn[old]];
+  }
+  return true;
+}
+
+struct Labelled {
+  std::vector<int8_t> alpha, eps;
+  int loops;
+};
+
+// Momentum labels of a canonical diagram; false if one-particle reducible or a tadpole.
+bool label_code(int m, const std::vector<int>& code, Labelled& L) {
+  const int N = 2 * m - 1, nv = m + 1;
+  std::vector<int> up(m + 1), dn(m);
+  up[m] = code[0];
+  for (int c = 0; c < m; ++c) { up[c] = code[1 + 2 * c]; dn[c] = code[2 + 2 * c]; }
+  std::vector<int> src, dst;
+  int exit_node = -1;
+  for (int c = 0; c < m; ++c) {
+    if (up[c] == m) exit_node = c;
+    else { src.push_back(c); dst.push_back(up[c]); }
+  }
+  const int n_up = (int)src.size();
+  for (int c = 0; c < m; ++c) { src.push_back(c); dst.push_back(dn[c]); }
+  if ((int)src.size() != N || exit_node < 0) return false;
+  const int root = up[m];
+  // BFS tree: dequeue a node, take every line to an unseen node, lines in index order
+  std::vector<int> par_line(m, -1), depth(m, -1), order{root};
+  depth[root] = 0;
+  std::vector<char> is_tree(N, 0);
+  for (size_t q = 0; q < order.size(); ++q) {
+    int u = order[q];
+    for (int j = 0; j < N; ++j) {
+      int other;
+      if (src[j] == u) other = dst[j];
+      else if (dst[j] == u) other = src[j];
+      else continue;
+      if (depth[other] >= 0) continue;
+      depth[other] = depth[u] + 1;
+      par_line[other] = j;
+      is_tree[j] = 1;
+      order.push_back(other);
+    }
+  }
+  std::vector<int> a(N * nv, 0);
+  auto parent = [&](int x) { int j = par_line[x]; return src[j] == x ? dst[j] : src[j]; };
+  // add `coef` units of flow running from node `from` to node `to` along the tree
+  auto route = [&](int from, int to, int var, int coef) {
+    int x = from, y = to;
+    while (x != y) {
+      if (depth[x] >= depth[y]) {           // step x toward the root: flow x -> parent
+        int j = par_line[x];
+        a[j * nv + var] += (src[j] == x) ? coef : -coef;
+        x = parent(x);
+      } else {                              // step y toward the root: flow parent -> y
+        int j = par_line[y];
+        a[j * nv + var] += (dst[j] == y) ? coef : -coef;
+        y = parent(y);
+      }
+    }
+  };
+  int var = 0;
+  for (int j = 0; j < N; ++j) {
+    if (is_tree[j]) continue;
+    if (var >= m) return false;
+    a[j * nv + var] = 1;
+    route(dst[j], src[j], var, 1);           // the loop closes from the chord's head back to its tail
+    ++var;
+  }
+  if (var != m) return false;
+  route(root, exit_node, m, 1);
+  for (int j = 0; j < N; ++j) {
+    bool loop = false;
+    for (int l = 0; l < m; ++l) loop |= a[j * nv + l] != 0;
+    if (!loop) return false;               // a bridge: one-particle reducible
+  }
+  for (int c = 0; c < m; ++c) {            // momentum transfer through interaction c (up side)
+    int jo = -1, ji = -1;
+    for (int j = 0; j < n_up; ++j) { if (src[j] == c) jo = j; if (dst[j] == c) ji = j; }
+    bool zero = true;
+    for (int l = 0; l < nv; ++l) {
+      int o = jo >= 0 ? a[jo * nv + l] : (l == m);
+      int i = ji >= 0 ? a[ji * nv + l] : (l == m);
+      if (o != i) zero = false;
+    }
+    if (zero) return false;                 // tadpole
+  }
+  L.alpha.assign(N * nv, 0);
+  for (int i = 0; i < N * nv; ++i) L.alpha[i] = (int8_t)a[i];
+  L.eps.assign(N * N, 0);
+  for (int j = 0; j < N; ++j) {
+    int r = j;
+    for (int k = 0; k < j && r == j; ++k)
+      if (std::equal(a.begin() + j * nv, a.begin() + (j + 1) * nv, a.begin() + k * nv)) r = k;
+    L.eps[j * N + r] = 1;
+  }
+  // closed loops: up cycles avoiding the external slot, and all down cycles
+  int loops = 0;
+  std::vector<char> seen(m + 1, 0);
+  for (int v = up[m]; v != m; v = up[v]) seen[v] = 1;
+  for (int c = 0; c < m; ++c) {
+    if (seen[c]) continue;
+    ++loops;
+    for (int v = c; !seen[v]; v = up[v]) seen[v] = 1;
+  }
+  std::fill(seen.begin(), seen.end(), 0);
+  for (int c = 0; c < m; ++c) {
+    if (seen[c]) continue;
+    ++loops;
+    for (int v = c; !seen[v]; v = dn[v]) seen[v] = 1;
+  }
+  L.loops = loops;
+  return true;
+}
+
+}  // namespace
+}  // namespace tami
+
+using namespace tami;
+
+extern "C" {
+
+const char* tami_last_error(void) { return g_last_error.c_str(); }
+
+int tami_construct(int n_lines, int n_vars, const int8_t* alpha, const int8_t* eps,
+                   const uint8_t* var_is_boson, const int32_t* order, double prefactor,
+                   tami_diagram** out) {
+  if (!out || !alpha) { set_error("NULL argument"); return TAMI_EINVAL; }
+  *out = nullptr;
+  if (n_lines < 1 || n_lines > kMaxLines || n_vars < 2 || n_vars > kMaxVars) {
+    set_error("n_lines must be in [1,16] and n_vars in [2,8]");
+    return TAMI_EINVAL;
+  }
+  for (int i = 0; i < n_lines * n_vars; ++i)
+    if (alpha[i] < -1 || alpha[i] > 1) { set_error("alpha entries must be -1, 0 or 1"); return TAMI_EINVAL; }
+  tami_diagram* d = new (std::nothrow) tami_diagram;
+  if (!d) { set_error("out of host memory"); return TAMI_ENOMEM; }
+  d->N = n_lines;
+  d->nv = n_vars;
+  d->prefactor = prefactor;
+  d->alpha.assign(alpha, alpha + n_lines * n_vars);
+  d->boson.assign(n_vars, 0);
+  if (var_is_boson) for (int l = 0; l < n_vars; ++l) d->boson[l] = var_is_boson[l] ? 1 : 0;
+  SymTerm t0;
+  for (int j = 0; j < n_lines; ++j) {
+    Form g;
+    for (int l = 0; l < n_vars; ++l) g.a[l] = alpha[j * n_vars + l];
+    for (int k = 0; k < n_lines; ++k) g.e[k] = eps ? eps[j * n_lines + k] : (int8_t)(j == k);
+    if (is_zero(g)) { delete d; set_error("a line with zero energy and frequency"); return TAMI_EINVAL; }
+    add_factor(t0.G, g, 1);
+  }
+  std::vector<SymTerm> cur{t0}, nxt;
+  std::vector<char> done(n_vars - 1, 0);
+  for (int s = 0; s < n_vars - 1; ++s) {
+    int p = order ? order[s] : s;
+    if (p < 0 || p >= n_vars - 1 || done[p]) { delete d; set_error("order must be a permutation of 0..m-1"); return TAMI_EINVAL; }
+    done[p] = 1;
+    int rc = sum_over(cur, p, n_vars, d->boson, nxt);
+    if (rc != TAMI_OK) { delete d; return rc; }
+    cur.swap(nxt);
+  }
+  d->terms.swap(cur);
+  int rc = flatten(d);
+  if (rc != TAMI_OK) { delete d; return rc; }
+  *out = d;
+  return TAMI_OK;
+}
+
+int tami_diagram_info(const tami_diagram* d, tami_info* info) {
+  if (!d || !info) { set_error("NULL argument"); return TAMI_EINVAL; }
+  *info = d->info;
+  return TAMI_OK;
+}
+
+int tami_enumerate_sigma(int order, int capacity, int8_t* alpha, int8_t* eps, int32_t* code,
+                         int32_t* loops, int* n_out) {
+  if (order < 2 || order > 6 || capacity < 0) { set_error("order must be in [2,6]"); return TAMI_EINVAL; }
+  const int m = order, N = 2 * m - 1, nv = m + 1;
+  std::set<std::vector<int>> codes;
+  std::vector<int> up(m + 1), dn(m), c;
+  for (int i = 0; i <= m; ++i) up[i] = i;
+  do {
+    if (up[m] == m) continue;
+    bool fixed = false;
+    for (int v = 0; v < m; ++v) fixed |= up[v] == v;
+    if (fixed) continue;
+    for (int i = 0; i < m; ++i) dn[i] = i;
+    do {
+      bool f2 = false;
+      for (int v = 0; v < m; ++v) f2 |= dn[v] == v;
+      if (!f2 && canonical_code(m, up.data(), dn.data(), c)) codes.insert(c);
+    } while (std::next_permutation(dn.begin(), dn.end()));
+  } while (std::next_permutation(up.begin(), up.end()));
+  int n = 0;
+  for (const auto& cc : codes) {
+    Labelled L;
+    if (!label_code(m, cc, L)) continue;
+    if (n < capacity) {
+      if (alpha) std::copy(L.alpha.begin(), L.alpha.end(), alpha + (size_t)n * N * nv);
+      if (eps) std::copy(L.eps.begin(), L.eps.end(), eps + (size_t)n * N * N);
+      if (code) std::copy(cc.begin(), cc.end(), code + (size_t)n * (2 * m + 1));
+      if (loops) loops[n] = L.loops;
+    }
+    ++n;
+  }
+  if (n_out) *n_out = n;
+  return TAMI_OK;
+}
+
+}  // extern "C"

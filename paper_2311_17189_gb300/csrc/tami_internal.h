@@ -1,0 +1,97 @@
+// Internal layout of libtami: the symbolic solution kept on the host and the flattened
+// device term table the kernels read.  Not part of the public ABI.
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tami.h"
+
+namespace tami {
+
+constexpr int kMaxLines = TAMI_MAX_LINES;
+constexpr int kMaxVars = TAMI_MAX_VARS;
+
+// Per-thread capacities of the evaluation kernels (checked at flatten time).
+constexpr int kMaxCombos = 128;
+constexpr int kMaxFermiValues = 256;
+constexpr int kMaxRealDens = 128;
+constexpr int kMaxCplxDens = 64;
+constexpr int kMaxDer = 5;
+
+void set_error(const std::string& msg);
+
+// Linear form  sum_l i a[l] nu_l + sum_j e[j] E_j.
+struct Form {
+  std::array<int8_t, kMaxLines> e{};
+  std::array<int8_t, kMaxVars> a{};
+  bool operator==(const Form& o) const { return e == o.e && a == o.a; }
+  bool operator<(const Form& o) const { return e != o.e ? e < o.e : a < o.a; }
+};
+
+// d^k/dx^k g_sigma(x) at x = c.E, with g_sigma(x) = 1/(sigma e^{beta x} + 1).
+struct FermiFactor {
+  std::array<int8_t, kMaxLines> c{};
+  int8_t sigma = 1;
+  int8_t k = 0;
+};
+
+struct SymTerm {
+  double A = 1.0;
+  std::vector<FermiFactor> F;
+  std::vector<std::pair<Form, int>> G;  // distinct Green's functions and their powers
+};
+
+// Flattened table.  All offsets are byte offsets into one blob, 16-byte aligned, so the blob
+// can be moved into shared memory with one bulk copy.  Integer records are int32.
+struct TableHeader {
+  int N, nv, m;
+  int n_rep;        // lines whose energy is computed (first line of each momentum label)
+  int n_combo, combo_nnz;
+  int n_fbase, n_fv;
+  int n_rden, n_cden;
+  int n_g1, n_terms, n_tfac, n_g1rd;
+  int n_g2, n_g2cd;
+  int max_der;
+  int bytes;
+  // offsets
+  int off_alpha;      // double [N][nv]
+  int off_repl;       // int32 [n_rep]            rep lines
+  int off_combo_ptr;  // int32 [n_combo+1]
+  int off_combo_j;    // int32 [combo_nnz]        base-energy index, ascending per combo
+  int off_combo_c;    // double [combo_nnz]       coefficient
+  int off_fbase;      // int32 [n_fbase][4]      combo, fv_begin, fv_end, needs 1 - y
+  int off_fv;         // int32 [n_fv][4]         sigma, sign, k, unused
+  int off_rden;       // int32 [n_rden][2]       combo, sign
+  int off_cden;       // int32 [n_cden][2]       combo, sign
+  int off_cden_a;     // double [n_cden]          external-frequency coefficient
+  int off_g1;         // int32 [n_g1][4]         term_begin, term_end, rd_begin, rd_end
+  int off_g1_tgt;     // int32 [n_g1]             frequency group it feeds (ascending)
+  int off_term;       // int32 [n_terms+1]       factor offsets
+  int off_term_A;     // double [n_terms]
+  int off_tfac;       // int32 [n_tfac]          Fermi-value index
+  int off_g1rd;       // int32 [n_g1rd][2]       real-den index, power
+  int off_g2;         // int32 [n_g2+1]          complex-den offsets
+  int off_g2cd;       // int32 [n_g2cd][2]       complex-den index, power
+};
+
+}  // namespace tami
+
+struct tami_diagram {
+  int N = 0, nv = 0;
+  std::vector<int8_t> alpha;          // [N][nv]
+  std::vector<uint8_t> boson;         // [nv]
+  double prefactor = 1.0;
+  std::vector<tami::SymTerm> terms;
+  tami_info info{};
+  tami::TableHeader hdr{};
+  std::vector<unsigned char> blob;    // host copy of the table
+  void* d_blob = nullptr;             // device copy
+  int device = -1;
+};
+
+namespace tami {
+int flatten(tami_diagram* d);  // terms -> hdr + blob + info
+}

@@ -1,0 +1,194 @@
+"""GPU parity of the forward path (CUDA kernels through the C ABI) against the CPU oracle.
+
+Tolerances.  Both sides build identical energies (same Philox stream, same Cody-Waite/Taylor
+cos, same fma order), identical energy combinations and identical denominators up to sign;
+they differ only in the rounding of exp/expm1, the reciprocals and the order of products and
+sums.  Each of those is a relative error of a few ulp on a factor, so the per-sample error is
+bounded by a small multiple of 2^-53 times the rounding envelope
+sum_t |A_t| prod env(FT factors) prod |G| that the oracle returns; the tests allow 1e-11 of it
+(the relative 1e-11 of the target, scaled to the terms that cancel).  Monte Carlo means are
+compared to a relative 1e-11 of mean |value| (strong sample-to-sample cancellation makes |mean|
+itself the wrong scale).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+import paper_2311_17189_gb300 as T
+from paper_2311_17189_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def lib_and_oracle(alpha, eps=None, boson=None, prefactor=1.0, order=None):
+    D = T.Diagram(alpha, eps=eps, var_is_boson=boson, prefactor=prefactor, order=order).upload(0)
+    S = O.Solution(alpha, eps=eps, var_is_boson=boson, prefactor=prefactor, order=order)
+    return D, S
+
+
+def diagram(order, index=None, code=None):
+    ds = O.enumerate_sigma(order)
+    if code is not None:
+        return next(d for d in ds if d["code"] == tuple(code))
+    return ds[index]
+
+
+def check_per_sample(gpu, ref, env, what):
+    gpu = np.asarray(gpu)
+    err = np.abs(gpu - ref)
+    bound = RTOL * env
+    bad = err > bound
+    assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} samples off; worst err/env " \
+                          f"{np.max(err / np.maximum(env, 1e-300)):.3e}"
+    return float(np.mean(err <= RTOL * np.abs(ref)))
+
+
+# ---------------------------------------------------------------------------- sampling
+@pytest.mark.parametrize("order,offset", [(2, 0), (4, 0), (4, (1 << 33) + 12345), (5, 77)])
+def test_sampled_energies_bitwise(order, offset):
+    """Philox momenta, line momenta and dispersion: bit-for-bit the oracle's energies."""
+    d = diagram(order, 0)
+    D = T.Diagram(d["alpha"], eps=d["eps"]).upload(0)
+    lat = (1.0, -0.3, -0.5, np.pi / 2, np.pi / 2)
+    n = 5000
+    Eg = D.sample_energies(lat, W.SEED, offset, n).cpu().numpy()
+    Eo, _ = O.sample_energies(d["alpha"], lat, W.SEED, offset, n)
+    assert np.array_equal(Eg.view(np.uint64), Eo.view(np.uint64))
+
+
+# ---------------------------------------------------------------------------- energy input
+ENERGY_CASES = [
+    ("paper_order2", [[1, 0, 0], [0, 1, 0], [-1, 1, 1]], None, None, 1.0),
+    ("bosonic_q_order2", [[1, 0, 1], [0, 1, 0], [1, 1, 0]], None, [1, 0, 0], 5.0),
+    ("quadruple_pole", [[1, 0], [1, 0], [1, 0], [1, 0], [1, 1]], [[1, 0, 0, 0, 0]] * 4 + [[0, 0, 0, 0, 1]],
+     [0, 1], 1.2),
+]
+
+
+@pytest.mark.parametrize("case", ENERGY_CASES, ids=[c[0] for c in ENERGY_CASES])
+def test_eval_energies_small_cases(case):
+    """Energy-input evaluation (Sec. 2.3) on the paper's example workload: energies U(-8, 8),
+    fermionic/bosonic frequencies, several tiles and a ragged tail (n_e = 3*128 + 37)."""
+    name, alpha, eps, boson, beta = case
+    D, S = lib_and_oracle(alpha, eps, boson)
+    N = len(alpha)
+    E = W.random_energies(3 * 128 + 37, N, a=8.0, seed=11)
+    X = W.matsubara(beta, 5) if boson is None or not boson[-1] else 2j * np.pi / beta * np.arange(1, 6)
+    ref, _, env = S.eval_energies(E, X, beta)
+    gpu = D.eval_energies(torch.tensor(E, device="cuda"), X, beta).cpu().numpy()
+    check_per_sample(gpu, ref, env, name)
+
+
+@pytest.mark.parametrize("order", [3, 4, 5])
+def test_eval_energies_enumerated_diagrams(order):
+    """Every enumerated diagram of orders 3-5 on random energies (equal-label lines share
+    energies), Matsubara and real-axis frequencies."""
+    ds = O.enumerate_sigma(order)
+    step = max(1, len(ds) // 8)
+    for d in ds[::step]:
+        D, S = lib_and_oracle(d["alpha"], d["eps"])
+        N = d["alpha"].shape[0]
+        E = W.random_energies(300, N, a=4.0, seed=order)
+        rep = d["eps"].argmax(1)
+        E = E[:, rep]
+        for X, beta in ((W.matsubara(3.0, 4), 3.0), (W.real_axis(-2.0, 2.0, 3, 0.05), 10.0)):
+            ref, _, env = S.eval_energies(E, X, beta)
+            gpu = D.eval_energies(torch.tensor(E, device="cuda"), X, beta).cpu().numpy()
+            check_per_sample(gpu, ref, env, f"order {order} code {d['code']}")
+
+
+# ---------------------------------------------------------------------------- momentum mode
+def run_both(D, S, lat, seed, offset, n, X, beta, threads=8):
+    mean, var, ps = D.forward(lat, seed, offset, n, X, beta, per_sample=True)
+    torch.cuda.synchronize()
+    ref = S.eval_momenta(lat, seed, offset, n, X, beta, per_sample=True, threads=threads)
+    return mean.cpu().numpy(), var.cpu().numpy(), ps.cpu().numpy(), ref
+
+
+def check_mean(mean, var, ps_ref, ref):
+    scale = np.mean(np.abs(ps_ref), axis=1)
+    assert np.all(np.abs(mean - ref["mean"]) <= RTOL * scale)
+    assert np.allclose(var, ref["var"], rtol=1e-9, atol=0)
+
+
+def test_order2_hubbard_full_workload():
+    """Order-2 Hubbard self-energy, full workload: 1e5 samples, beta=5, one frequency; every
+    sample and the mean."""
+    c = W.ORDER2
+    D, S = lib_and_oracle(c["alpha"], boson=c["var_is_boson"])
+    X = W.matsubara(c["beta"], c["n_freq"])
+    mean, var, ps, ref = run_both(D, S, W.lattice(c), c["seed"], 0, c["n_samples"], X, c["beta"])
+    frac = check_per_sample(ps, ref["values"], ref["envelope"], "order 2")
+    assert frac > 0.999
+    check_mean(mean, var, ref["values"], ref)
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 3 * 128 + 37, 4096 + 5])
+def test_order4_small_sample_counts(n):
+    """Order-4 workload (t'=-0.3, mu=-0.5, beta=8, 16 frequencies) at sample counts around the
+    tile size, including a single sample and ragged tails."""
+    c = W.ORDER4
+    d = diagram(4, code=c["code"])
+    D, S = lib_and_oracle(d["alpha"], d["eps"])
+    X = W.matsubara(c["beta"], c["n_freq"])
+    mean, var, ps, ref = run_both(D, S, W.lattice(c), c["seed"], 3, n, X, c["beta"])
+    check_per_sample(ps, ref["values"], ref["envelope"], f"order 4 n={n}")
+    check_mean(mean, var, ref["values"], ref)
+
+
+@pytest.mark.parametrize("n_f", [1, 3, 129, 300])
+def test_frequency_counts(n_f):
+    """Frequency counts below, at and above the block size (the per-thread frequency split)."""
+    d = diagram(3, 1)
+    D, S = lib_and_oracle(d["alpha"], d["eps"])
+    X = W.real_axis(-4, 4, n_f, 0.05) if n_f > 3 else W.matsubara(10.0, n_f)
+    mean, var, ps, ref = run_both(D, S, (1.0, 0.0, 0.0, np.pi / 2, np.pi / 2), 5, 0, 700, X, 10.0)
+    check_per_sample(ps, ref["values"], ref["envelope"], f"n_f={n_f}")
+    check_mean(mean, var, ref["values"], ref)
+
+
+@pytest.mark.parametrize("order", [3, 5])
+def test_all_diagrams_momentum_mode(order):
+    """Every enumerated diagram of orders 3 and 5 (a sample of them at order 5) with the
+    -U^m (-1)^F prefactor, momentum sampling, 2 frequencies."""
+    ds = O.enumerate_sigma(order)
+    for d in ds[:: max(1, len(ds) // 10)]:
+        pref = (-1.0) ** order * (-1.0) ** d["loops"]
+        D, S = lib_and_oracle(d["alpha"], d["eps"], prefactor=pref)
+        X = W.matsubara(5.0, 2)
+        mean, var, ps, ref = run_both(D, S, (1.0, -0.2, 0.1, np.pi / 2, np.pi / 3), 9, 1000, 400, X, 5.0)
+        check_per_sample(ps, ref["values"], ref["envelope"], f"order {order} {d['code']}")
+        check_mean(mean, var, ref["values"], ref)
+
+
+def test_order4_full_size_sampled():
+    """Order-4 workload at its full size (2^24 samples, 16 frequencies), the launch the
+    benchmark times: per-sample values at 2000 random indices against the oracle computed one
+    by one, and the mean against the mean of all per-sample outputs."""
+    c = W.ORDER4
+    d = diagram(4, code=c["code"])
+    D, S = lib_and_oracle(d["alpha"], d["eps"])
+    X = W.matsubara(c["beta"], c["n_freq"])
+    n = c["n_samples"]
+    mean, var, ps = D.forward(W.lattice(c), c["seed"], 0, n, X, c["beta"], per_sample=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(n, 2000, replace=False))
+    got = ps[:, torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    for k, i in enumerate(idx):
+        r = S.eval_momenta(W.lattice(c), c["seed"], int(i), 1, X, c["beta"], per_sample=True)
+        check_per_sample(got[:, k:k + 1], r["values"], r["envelope"], f"sample {i}")
+    ps_mean = ps.mean(dim=1).cpu().numpy()
+    scale = ps.abs().mean(dim=1).cpu().numpy()
+    assert np.all(np.abs(mean.cpu().numpy() - ps_mean) <= 1e-12 * scale)

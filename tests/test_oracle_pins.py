@@ -89,6 +89,23 @@ def test_fermi_higher_derivatives_against_finite_differences(sigma, k):
         assert O.fermi_deriv(sigma, k, beta, x) == pytest.approx(fd, rel=2e-8, abs=1e-10)
 
 
+def test_fermi_relative_accuracy_in_tails_and_near_zero():
+    """g_sigma and its first derivatives keep full relative accuracy where they are tiny
+    (beta x up to 600) and where the Bose form 1/(1 - e^{beta x}) cancels (beta x ~ 1e-9),
+    compared with the definition evaluated in 60-digit arithmetic."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    for sigma in (1, -1):
+        for bx in (-600.0, -75.0, -40.0, -12.0, -1e-3, -1e-9, 1e-9, 1e-3, 12.0, 40.0, 75.0, 600.0):
+            beta = 2.0
+            x = bx / beta
+            e = mp.exp(mp.mpf(beta) * mp.mpf(x))
+            g = 1 / (sigma * e + 1)
+            d1 = -sigma * beta * e / (sigma * e + 1) ** 2
+            assert O.fermi_deriv(sigma, 0, beta, x) == pytest.approx(float(g), rel=4e-15)
+            assert O.fermi_deriv(sigma, 1, beta, x) == pytest.approx(float(d1), rel=1e-14)
+
+
 def test_fermi_extreme_arguments_and_reflection():
     """No overflow at beta x = +-1000, and g_sigma(-x) = 1 - g_sigma(x) for both sigma."""
     for sigma in (1, -1):
@@ -143,6 +160,25 @@ def test_bosonic_transfer_labelling_closed_form():
         for fi, x in enumerate(X):
             cf = -(f_fermi(beta, -E1) - f_fermi(beta, -E3)) * (f_fermi(beta, -E2) + n_bose(beta, E1 - E3)) / (x + E1 + E2 - E3)
             assert abs(v[fi, i] - cf) <= 1e-13 * abs(cf) + 1e-15
+
+
+def test_closed_form_exact_arithmetic_wide_energies():
+    """Against the same closed form evaluated in 50-digit arithmetic, over energies U(-8, 8) at
+    beta=5 (Fermi tails down to e^-80, strong cancellation between terms): the error stays
+    within 1e-13 of the rounding envelope sum_t |A| prod |FT factors| prod |G| on every sample."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    beta = 5.0
+    S = O.Solution([[1, 0, 1], [0, 1, 0], [1, 1, 0]], var_is_boson=[1, 0, 0])
+    E = np.random.default_rng(11).uniform(-8, 8, (300, 3))
+    x = 1j * np.pi / beta
+    v, _, env = S.eval_energies(E, [x], beta)
+    f = lambda z: 1 / (mp.exp(beta * z) + 1)
+    nb = lambda z: 1 / (mp.exp(beta * z) - 1)
+    for i in range(E.shape[0]):
+        E1, E2, E3 = (mp.mpf(float(e)) for e in E[i])
+        ex = -(f(-E1) - f(-E3)) * (f(-E2) + nb(E1 - E3)) / (mp.mpc(0, x.imag) + E1 + E2 - E3)
+        assert abs(v[0, i] - complex(ex)) <= 1e-13 * env[0, i]
 
 
 def test_lindhard_bubble_closed_form():
