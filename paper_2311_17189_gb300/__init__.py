@@ -8,7 +8,7 @@
 Only marshalling lives in Python; the construction is libtami's C++ and every evaluation
 step is a libtami CUDA kernel.  `workloads` holds the seeded synthetic inputs.
 """
-from . import _lib
+from . import _lib, mc
 from .api import Diagram, enumerate_sigma
 
-__all__ = ["Diagram", "enumerate_sigma", "_lib"]
+__all__ = ["Diagram", "enumerate_sigma", "_lib", "mc"]
