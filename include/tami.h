@@ -135,6 +135,29 @@ int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, 
                  int64_t n_samples, const double* X, int n_f, double beta, double* mean, double* var,
                  double* per_sample, void* workspace, size_t workspace_bytes, tami_stream_t stream);
 
+/* tami_forward without a workspace argument: the same Monte Carlo evaluation and outputs, with
+ * its scratch (a status word and the per-block partial sums) taken from a fixed 4 MiB array
+ * inside libtami instead of memory the caller allocates.  The paper has no counterpart; this
+ * entry exists for callers that cannot allocate device memory, e.g. code whose device memory
+ * is all owned by a pool fixed at start-up, or loops that must not let cudaMalloc/cudaFree
+ * synchronise the device.
+ *   - It allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *   - The array is part of the loaded library, so every GPU that loads libtami holds its 4 MiB
+ *     until the process exits.
+ *   - Limit: 256 + 32 * n_f * grid bytes must fit in 4 MiB, grid being the launch's block count
+ *     (SM count x resident blocks per SM, at most the number of 128-sample tiles); with 1216
+ *     blocks that is n_f <= 107.  Larger requests return TAMI_EINVAL with the sizes in the
+ *     message; use tami_forward with a workspace for them.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call shares the one array and it keeps the last call's contents; the call clears the
+ *     status word itself.  Calls whose work overlaps on the GPU (other streams, other host
+ *     threads) race on the array: serialise them.
+ * Arguments, layouts and errors are otherwise those of tami_forward. */
+int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
+                         int64_t n_samples, const double* X, int n_f, double beta, double* mean,
+                         double* var, double* per_sample, tami_stream_t stream);
+
 /* Hubbard (U n_up n_down) self-energy diagrams of the given order (2..6), one-particle
  * irreducible, without tadpoles, in canonical order, labelled with momentum-conserving alpha
  * (Sec. 2.5: graph representation and labelling).  With capacity 0 only *n_out is set.

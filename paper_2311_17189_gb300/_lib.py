@@ -14,10 +14,11 @@ LIB_PATH = os.path.join(_PKG, "libtami.so")
 
 TAMI_OK, TAMI_EINVAL, TAMI_ENOMEM, TAMI_ECUDA, TAMI_ETIMEOUT, TAMI_EUNSUPPORTED = range(6)
 
-# functions declared in include/tami.h (checked by tests/test_capi_symbols.py)
+# functions declared in include/tami.h (checked by tests/test_lib_host.py)
 EXPORTS = [
     "tami_last_error", "tami_construct", "tami_diagram_info", "tami_upload", "tami_sample_energies",
-    "tami_eval_energies", "tami_forward_workspace", "tami_forward", "tami_enumerate_sigma",
+    "tami_eval_energies", "tami_forward_workspace", "tami_forward", "tami_forward_noalloc",
+    "tami_enumerate_sigma",
     "tami_destroy",
 ]
 
@@ -66,6 +67,8 @@ def lib():
     L.tami_forward_workspace.argtypes = [vp, i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.tami_forward.argtypes = [vp, ctypes.POINTER(Lattice), u64, u64, i64, dp, ctypes.c_int, ctypes.c_double,
                                dp, dp, dp, dp, ctypes.c_size_t, vp]
+    L.tami_forward_noalloc.argtypes = [vp, ctypes.POINTER(Lattice), u64, u64, i64, dp, ctypes.c_int,
+                                       ctypes.c_double, dp, dp, dp, vp]
     L.tami_enumerate_sigma.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     L.tami_destroy.argtypes = [vp]
     L.tami_destroy.restype = None

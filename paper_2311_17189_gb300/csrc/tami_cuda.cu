@@ -19,6 +19,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "tami_internal.h"
 
@@ -515,6 +516,31 @@ FwdParams make_params(const tami_diagram* d, int n_f, double beta) {
 
 constexpr size_t kStatusBytes = 256;
 
+// Scratch of tami_forward_noalloc: a status word (first 256 bytes) followed by the per-block
+// partial sums [grid][n_f][4].  It lives in the library image, so every GPU that loads the
+// library holds these bytes until the process exits; no call allocates them.
+constexpr size_t kNoAllocScratchBytes = 4u << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch, resolved once per device with that device current
+// (in host code the symbol itself is only a host-side handle, not a device address).
+unsigned char* noalloc_scratch(int dev) {
+  static std::mutex mu;
+  static unsigned char* addr[64] = {};
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      return nullptr;
+    }
+    addr[dev] = static_cast<unsigned char*>(p);
+  }
+  return addr[dev];
+}
+
 }  // namespace
 }  // namespace tami
 
@@ -597,6 +623,45 @@ int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, 
   cudaStream_t st = (cudaStream_t)stream;
   int* status = static_cast<int*>(workspace);
   double* partial = reinterpret_cast<double*>(static_cast<char*>(workspace) + kStatusBytes);
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  FwdParams P = make_params(d, n_f, beta);
+  P.t = lat->t; P.tp = lat->tp; P.mu = lat->mu; P.kx = lat->kx_ext; P.ky = lat->ky_ext;
+  P.seed = seed; P.offset = offset; P.n = n_samples;
+  P.X = X;
+  P.per_sample = per_sample;
+  P.partial = partial;
+  P.status = status;
+  rc = launch_fwd<false>(d, P, st, grid);
+  if (rc) return rc;
+  finalize_kernel<<<(n_f + 127) / 128, 128, 0, st>>>(partial, grid, n_f, n_samples, status, mean, var);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "finalize launch");
+}
+
+// Same evaluation as tami_forward, with its scratch taken from a fixed array inside the
+// library instead of a caller-supplied workspace, for callers that cannot allocate device
+// memory.  See include/tami.h for the contract (size limit, first-call set-up, shared state).
+int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
+                         int64_t n_samples, const double* X, int n_f, double beta, double* mean, double* var,
+                         double* per_sample, tami_stream_t stream) {
+  int rc = check_common(d, n_f);
+  if (rc) return rc;
+  if (!lat || !X || !mean || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
+  const int grid = grid_for(d, n_f, n_samples);
+  const size_t need = kStatusBytes + sizeof(double) * 4 * (size_t)n_f * (size_t)grid;
+  if (need > kNoAllocScratchBytes) {
+    set_error("tami_forward_noalloc: needs " + std::to_string(need) + " bytes of scratch for n_f=" +
+              std::to_string(n_f) + " over " + std::to_string(grid) + " blocks, above the fixed " +
+              std::to_string(kNoAllocScratchBytes) + "-byte array; use tami_forward with a workspace");
+    return TAMI_EINVAL;
+  }
+  unsigned char* base = noalloc_scratch(d->device);
+  if (!base) return TAMI_ECUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* status = reinterpret_cast<int*>(base);
+  double* partial = reinterpret_cast<double*>(base + kStatusBytes);
+  // the status word must start at zero; the partials are fully rewritten by every launch
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   FwdParams P = make_params(d, n_f, beta);
