@@ -30,7 +30,7 @@ from paper_2311_17189_gb300 import workloads as W  # noqa: E402
 
 CFG = W.ORDER4
 FP64_PEAK_TFLOPS = 1.2586   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
-METRIC = "order-4 Sigma evals/s (samples x terms x frequencies, FP64)"
+METRIC = "order-4 Sigma evals/s (samples x terms x frequencies, FP64), forward + adjoint"
 
 
 def dist_env():
@@ -82,15 +82,23 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def oracle_step(S, offset, n, X, cores):
+    """One forward + adjoint step of the oracle: the mean, then dual-number derivatives along
+    omega, mu, kx_ext and ky_ext."""
+    S.eval_momenta(W.lattice(CFG), CFG["seed"], offset, n, X, CFG["beta"], per_sample=False, threads=cores)
+    for which in ("omega", "mu", "kx", "ky"):
+        S.eval_momenta_deriv(W.lattice(CFG), CFG["seed"], offset, n, X, CFG["beta"], which, threads=cores)
+
+
 def cpu_baseline(diagram, X, target_s=10.0):
     """The oracle as it stands on all host cores, on the first samples of the same stream."""
     import oracle as O
     S = O.Solution(diagram["alpha"], eps=diagram["eps"])
     cores = os.cpu_count() or 1
-    n = 1024
+    n = 256
     while True:
         t0 = time.perf_counter()
-        S.eval_momenta(W.lattice(CFG), CFG["seed"], 0, n, X, CFG["beta"], per_sample=False, threads=cores)
+        oracle_step(S, 0, n, X, cores)
         dt = time.perf_counter() - t0
         if dt * 4 > target_s or n >= (1 << 22):
             break
@@ -98,7 +106,7 @@ def cpu_baseline(diagram, X, target_s=10.0):
     info = S.info()
     return {"value": n * info["terms"] * len(X) / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
             "sample": f"first {n} of the {CFG['n_samples']} samples (same seed), {len(X)} frequencies, "
-                      f"{dt:.2f} s wall"}
+                      f"forward + 4 dual-number derivative passes, {dt:.2f} s wall"}
 
 
 def order4_diagram(lib):
@@ -117,10 +125,10 @@ def run_reference(args):
     n = args.ref_samples
     T = S.info()["terms"]
     for i in range(args.warmup):
-        S.eval_momenta(W.lattice(CFG), CFG["seed"], i * n, n, X, CFG["beta"], per_sample=False, threads=cores)
+        oracle_step(S, i * n, n, X, cores)
     t0 = time.perf_counter()
     for i in range(args.steps):
-        S.eval_momenta(W.lattice(CFG), CFG["seed"], i * n, n, X, CFG["beta"], per_sample=False, threads=cores)
+        oracle_step(S, (args.warmup + i) * n, n, X, cores)
     dt = (time.perf_counter() - t0) / args.steps
     value = n * T * len(X) / dt
     line = {
@@ -130,7 +138,8 @@ def run_reference(args):
         "config": {"workload": CFG["name"], "samples_per_step": n, "frequencies": len(X), "terms": T,
                    "beta": CFG["beta"], "t": CFG["t"], "tp": CFG["tp"], "mu": CFG["mu"]},
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{n} samples per step of the {CFG['n_samples']}-sample workload"},
+                         "sample": f"{n} samples per step of the {CFG['n_samples']}-sample workload, "
+                                   "forward + 4 dual-number derivative passes"},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -162,58 +171,84 @@ def run_tami(args):
     var = torch.empty((n_f, 2), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def step(i):
+    g_host = W.matsubara(CFG["beta"], CFG["n_freq"]).real * 0 + (1.0 + 0.5j)   # fixed upstream gradient
+    G = torch.view_as_real(torch.as_tensor(g_host, dtype=torch.complex128, device=dev)).contiguous()
+    Gc = torch.view_as_complex(G)
+
+    def fwd(i):
         return D.forward(lat, CFG["seed"], offset + i * n * world, n, Xc, CFG["beta"], out=(mean, var))
 
+    def bwd(i):
+        return D.backward(lat, CFG["seed"], offset + i * n * world, n, Xc, CFG["beta"], Gc)
+
     for i in range(args.warmup):
-        step(i)
+        fwd(i)
+        bwd(i)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    mk = lambda: torch.cuda.Event(enable_timing=True)
+    ev = [(mk(), mk(), mk()) for _ in range(args.steps)]
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(i & 0xFF)                       # evict L2 (256 MiB > 129 MB) outside the timed span
         ev[i][0].record(stream)
-        step(args.warmup + i)
+        fwd(args.warmup + i)
         ev[i][1].record(stream)
+        bwd(args.warmup + i)
+        ev[i][2].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    # end-to-end through the public API: pinned host frequencies in, host mean/var out
+    fwd_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    bwd_ms = [b.elapsed_time(c) for _, b, c in ev]
+    # end-to-end through the public API: pinned host inputs in, host results out, every step
     Xh = torch.view_as_real(torch.as_tensor(X, dtype=torch.complex128)).contiguous().pin_memory()
+    Gh = torch.view_as_real(torch.as_tensor(g_host, dtype=torch.complex128)).contiguous().pin_memory()
     mh = torch.empty((n_f, 2), dtype=torch.float64).pin_memory()
     vh = torch.empty((n_f, 2), dtype=torch.float64).pin_memory()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gh = torch.empty((n_f + 3,), dtype=torch.float64).pin_memory()
+    e0, e1 = mk(), mk()
     e2e_ms = []
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         e0.record(stream)
         Xd.copy_(Xh, non_blocking=True)
-        D.forward(lat, CFG["seed"], offset + i * n * world, n, Xc, CFG["beta"], out=(mean, var))
+        G.copy_(Gh, non_blocking=True)
+        fwd(args.warmup + i)
+        out = bwd(args.warmup + i)
         mh.copy_(mean, non_blocking=True)
         vh.copy_(var, non_blocking=True)
+        gh[:n_f].copy_(out["grad_X_re"], non_blocking=True)
+        gh[n_f:].copy_(out["grad_params"], non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     clk = clocks.stop()
-    ms = float(np.mean(step_ms))
+    tf, tb = float(np.mean(fwd_ms)), float(np.mean(bwd_ms))
+    ms = tf + tb
     e2e = float(np.mean(e2e_ms))
     if world > 1:
-        t = torch.tensor([ms, e2e], dtype=torch.float64, device=dev)
+        t = torch.tensor([ms, e2e, tf], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e = float(t[0]), float(t[1])
+        ms, e2e, tf = float(t[0]), float(t[1]), float(t[2])
     evals = float(n) * info["n_terms"] * n_f * world
     value = evals / (ms * 1e-3)
-    flops = n * (info["flops_per_sample"] + n_f * info["flops_per_sample_freq"])
-    achieved = flops / (float(np.mean(step_ms)) * 1e-3) / 1e12
+    fl_f = n * (info["flops_per_sample"] + n_f * info["flops_per_sample_freq"])
+    fl_b = n * (info["bwd_flops_per_sample"] + n_f * info["bwd_flops_per_sample_freq"])
+    dom = ("bwd_kernel", fl_b, tb) if tb >= tf else ("fwd_kernel", fl_f, tf)
+    achieved = dom[1] / (dom[2] * 1e-3) / 1e12
+    h2d = 2 * n_f * 16
+    d2h = n_f * 32 + (n_f + 3) * 8
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "step": "forward + adjoint (tami_forward then tami_backward on the same samples)",
+            "plain_fwd": {"value": evals / (tf * 1e-3), "unit": "evals/s", "ms": tf},
+            "adjoint_ms": tb,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (Philox momenta, in-kernel)",
             "config": {"workload": CFG["name"], "samples_per_gpu": n, "frequencies": n_f,
@@ -222,11 +257,13 @@ def run_tami(args):
                        "parallelism": f"samples sharded over {world} GPU(s)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "fwd_kernel", "flops_per_launch": flops,
+                         "kernel": dom[0], "flops_per_launch": dom[1],
+                         "fwd_kernel_tflops": fl_f / (tf * 1e-3) / 1e12,
+                         "bwd_kernel_tflops": fl_b / (tb * 1e-3) / 1e12,
                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (nominal 1.25 TFLOP/s)"},
-            "e2e": {"value": evals / (e2e * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": n_f * 16,
-                    "d2h_bytes_per_step": n_f * 32},
-            "gpu_launches": 2 * args.steps,
+            "e2e": {"value": evals / (e2e * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "wall_s_timed": wall,
         }
@@ -244,7 +281,7 @@ def main():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="tami", choices=["tami", "reference"])
-    p.add_argument("--ref-samples", type=int, default=1 << 14)
+    p.add_argument("--ref-samples", type=int, default=1 << 12)
     p.add_argument("--samples", type=int, default=CFG["n_samples"], help="samples per GPU (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args()

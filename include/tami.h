@@ -78,6 +78,9 @@ typedef struct {
    * independent part, library math calls counted as one flop each) and per (sample, frequency) */
   double flops_per_sample;
   double flops_per_sample_freq;
+  /* the same for tami_backward (recomputation + adjoint sweep) */
+  double bwd_flops_per_sample;
+  double bwd_flops_per_sample_freq;
 } tami_info;
 
 const char* tami_last_error(void);
@@ -134,6 +137,29 @@ int tami_forward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, si
 int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
                  int64_t n_samples, const double* X, int n_f, double beta, double* mean, double* var,
                  double* per_sample, void* workspace, size_t workspace_bytes, tami_stream_t stream);
+
+/* Scratch needed by tami_backward for n samples and n_f frequencies. */
+int tami_backward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, size_t* bytes);
+
+/* Adjoint of tami_forward's mean (the paper defines only the forward evaluation, Sec. 2.3 and
+ * Sec. 5.2).  For an upstream gradient g_f = dL/dSigma_f (PyTorch's convention for a real loss
+ * L of complex outputs: g = dL/dRe + i dL/dIm) over the same samples:
+ *   dsigma_dX   device double [n_f][2] or NULL: dSigma_f/dX_f, the derivative of the mean along
+ *               its external frequency (X = omega + i Gamma: dSigma/domega; its real part gives
+ *               the quasiparticle weight Z = 1/(1 - dRe Sigma/domega)).
+ *   grad_X_re   device double [n_f] or NULL: dL/domega_f = Re(conj(g_f) dSigma_f/dX_f).
+ *   grad_params device double [3] or NULL: dL/dmu, dL/dkx_ext, dL/dky_ext
+ *               = Re sum_f conj(g_f) dSigma_f/dtheta, through E = mu - eps(K), K = ... + alpha_ext k_ext.
+ *   per_sample_dX    device double [n_f][n][2] or NULL: each sample's dv/dX.
+ *   per_sample_grads device double [n][3] or NULL: each sample's
+ *               Re sum_f conj(g_f) dv/dtheta (theta = mu, kx, ky; not divided by n).
+ *   gout        device double [n_f][2]; workspace as tami_backward_workspace, 256-byte aligned.
+ * Term products are recomputed, not stored.  Limits: n_f <= 256, derivative order <= 4.
+ * Deterministic for fixed (n, n_f, device). */
+int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
+                  int64_t n_samples, const double* X, int n_f, double beta, const double* gout,
+                  double* dsigma_dX, double* grad_X_re, double* grad_params, double* per_sample_dX,
+                  double* per_sample_grads, void* workspace, size_t workspace_bytes, tami_stream_t stream);
 
 /* tami_forward without a workspace argument: the same Monte Carlo evaluation and outputs, with
  * its scratch (a status word and the per-block partial sums) taken from a fixed 4 MiB array

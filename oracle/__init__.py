@@ -48,7 +48,7 @@ def lib():
                                        dp, dp, ctypes.c_int]
         L.orc_eval_momenta_deriv.argtypes = [ctypes.c_void_p, i32p, dp, ctypes.c_uint64, ctypes.c_uint64,
                                              ctypes.c_int64, dp, dp, ctypes.c_int, ctypes.c_double,
-                                             ctypes.c_int, dp, dp, dp, dp, ctypes.c_int]
+                                             ctypes.c_int, dp, dp, dp, dp, dp, ctypes.c_int]
         L.orc_eval_energies_deriv.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_int64, dp, dp,
                                               ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                               ctypes.c_double, dp, dp]
@@ -180,9 +180,11 @@ class Solution:
             out["envelope"] = en
         return out
 
-    def eval_momenta_deriv(self, lattice, seed, offset, n, X, beta, which, threads=1, alpha=None):
+    def eval_momenta_deriv(self, lattice, seed, offset, n, X, beta, which, threads=1, alpha=None,
+                           envelope=False):
         """Per-sample dual-number derivative [n_f, n] along which in
-        {'omega', 'mu', 'kx', 'ky'}; returns (values, derivatives)."""
+        {'omega', 'mu', 'kx', 'ky'}; returns (values, derivatives) or, with envelope=True,
+        (values, derivatives, derivative rounding envelope)."""
         w = {"omega": 0, "mu": 1, "kx": 2, "ky": 3}[which]
         a = self.alpha if alpha is None else _i32(alpha)
         lat = _f64(lattice)
@@ -191,9 +193,12 @@ class Solution:
         nf = X.size
         d = ctypes.c_double
         vr = np.empty((nf, n)); vi = np.empty((nf, n)); dr = np.empty((nf, n)); di = np.empty((nf, n))
+        de = np.empty((nf, n))
         lib().orc_eval_momenta_deriv(self._h, _ptr(a, ctypes.c_int), _ptr(lat, d), int(seed), int(offset),
                                      int(n), _ptr(xr, d), _ptr(xi, d), nf, float(beta), w, _ptr(vr, d),
-                                     _ptr(vi, d), _ptr(dr, d), _ptr(di, d), int(threads))
+                                     _ptr(vi, d), _ptr(dr, d), _ptr(di, d), _ptr(de, d), int(threads))
+        if envelope:
+            return vr + 1j * vi, dr + 1j * di, de
         return vr + 1j * vi, dr + 1j * di
 
     def eval_energies_deriv(self, E, dE, X, dX, beta):

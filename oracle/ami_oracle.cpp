@@ -455,31 +455,43 @@ struct Dual {
 Dual dmul(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
 
 void eval_one_dual(const Solution& S, const double* E, const double* dE, cplx X, cplx dX,
-                   double beta, cplx* val, cplx* der) {
+                   double beta, cplx* val, cplx* der, double* der_env) {
   Neumaier vr, vi, dr, di;
+  double env = 0.0;
   for (const Term& T : S.terms) {
     Dual t{cplx(S.prefactor * T.A), 0.0};
+    // rounding envelope of the derivative: the same product rule on magnitudes
+    double ev = std::fabs(S.prefactor * T.A), ed = 0.0;
     for (const FFac& f : T.F) {
       double x = combo(f.c, E);
-      double dx = 0.0;
-      for (size_t j = 0; j < f.c.size(); ++j) dx += f.c[j] * dE[j];
-      double p = fermi_deriv(f.sigma, f.k, beta, x, nullptr);
-      double dp = fermi_deriv(f.sigma, f.k + 1, beta, x, nullptr) * dx;
+      double dx = 0.0, adx = 0.0;
+      for (size_t j = 0; j < f.c.size(); ++j) { dx += f.c[j] * dE[j]; adx += std::fabs(f.c[j] * dE[j]); }
+      double e0, e1;
+      double p = fermi_deriv(f.sigma, f.k, beta, x, &e0);
+      double dp = fermi_deriv(f.sigma, f.k + 1, beta, x, &e1) * dx;
       t = dmul(t, Dual{cplx(p), cplx(dp)});
+      ed = ed * e0 + ev * e1 * adx;
+      ev = ev * e0;
     }
     for (const GFac& g : T.G) {
       cplx D = den_value(g, E, X, S.nv);
-      double dEe = 0.0;
-      for (size_t j = 0; j < g.e.size(); ++j) dEe += g.e[j] * dE[j];
-      cplx dD = dEe + (double)g.a[S.nv - 1] * dX;
+      double dEe = 0.0, adEe = 0.0;
+      for (size_t j = 0; j < g.e.size(); ++j) { dEe += g.e[j] * dE[j]; adEe += std::fabs(g.e[j] * dE[j]); }
+      double a = (double)g.a[S.nv - 1];
+      cplx dD = dEe + a * dX;
       cplx r = 1.0 / D;
       t = dmul(t, Dual{r, -dD * r * r});
+      double ar = std::abs(r);
+      ed = ed * ar + ev * (adEe + std::fabs(a) * std::abs(dX)) * ar * ar;
+      ev = ev * ar;
     }
     vr.add(t.v.real()); vi.add(t.v.imag());
     dr.add(t.d.real()); di.add(t.d.imag());
+    env += ed;
   }
   *val = cplx(vr.value(), vi.value());
   *der = cplx(dr.value(), di.value());
+  if (der_env) *der_env = env;
 }
 
 // Lattice parameters (t, t', mu, k_ext) and the per-line momenta of one sample.
@@ -906,14 +918,15 @@ int orc_eval_momenta(const void* sp, const int* alpha, const double* lat, uint64
   return 0;
 }
 
-// Dual-number derivative of the per-sample value along one direction:
+// Dual-number derivative of the per-sample value along one direction (der_env, optional: the
+// rounding envelope of the derivative, the product rule applied to magnitudes):
 // which = 0: d/d omega (X -> X + h, the same shift for every frequency; the derivative of
 // Sigma_f is with respect to its own omega_f), 1: d/d mu, 2: d/d kx_ext, 3: d/d ky_ext.
 // der [n_f][n] complex (re, im arrays).
 int orc_eval_momenta_deriv(const void* sp, const int* alpha, const double* lat, uint64_t seed,
                            uint64_t offset, int64_t n, const double* X_re, const double* X_im, int n_f,
                            double beta, int which, double* val_re, double* val_im, double* der_re,
-                           double* der_im, int n_threads) {
+                           double* der_im, double* der_env, int n_threads) {
   const Solution& S = *(const Solution*)sp;
   Lattice L{lat[0], lat[1], lat[2], lat[3], lat[4]};
   int nv = S.nv;
@@ -931,10 +944,12 @@ int orc_eval_momenta_deriv(const void* sp, const int* alpha, const double* lat, 
       cplx dX = which == 0 ? cplx(1.0, 0.0) : cplx(0.0, 0.0);
       for (int f = 0; f < n_f; ++f) {
         cplx v, d;
-        eval_one_dual(S, E.data(), dE.data(), cplx(X_re[f], X_im[f]), dX, beta, &v, &d);
+        double de;
+        eval_one_dual(S, E.data(), dE.data(), cplx(X_re[f], X_im[f]), dX, beta, &v, &d, &de);
         size_t o = (size_t)f * n + i;
         if (val_re) { val_re[o] = v.real(); val_im[o] = v.imag(); }
         der_re[o] = d.real(); der_im[o] = d.imag();
+        if (der_env) der_env[o] = de;
       }
     }
   };
@@ -956,7 +971,8 @@ int orc_eval_energies_deriv(const void* sp, const double* E, const double* dE, i
   for (int64_t i = 0; i < n_e; ++i)
     for (int f = 0; f < n_f; ++f) {
       cplx v, d;
-      eval_one_dual(S, E + i * S.N, dE + i * S.N, cplx(X_re[f], X_im[f]), cplx(dX_re, dX_im), beta, &v, &d);
+      eval_one_dual(S, E + i * S.N, dE + i * S.N, cplx(X_re[f], X_im[f]), cplx(dX_re, dX_im), beta, &v, &d,
+                    nullptr);
       der_re[(size_t)f * n_e + i] = d.real();
       der_im[(size_t)f * n_e + i] = d.imag();
     }

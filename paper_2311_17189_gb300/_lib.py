@@ -18,6 +18,7 @@ TAMI_OK, TAMI_EINVAL, TAMI_ENOMEM, TAMI_ECUDA, TAMI_ETIMEOUT, TAMI_EUNSUPPORTED 
 EXPORTS = [
     "tami_last_error", "tami_construct", "tami_diagram_info", "tami_upload", "tami_sample_energies",
     "tami_eval_energies", "tami_forward_workspace", "tami_forward", "tami_forward_noalloc",
+    "tami_backward_workspace", "tami_backward",
     "tami_enumerate_sigma",
     "tami_destroy",
 ]
@@ -44,6 +45,7 @@ class Info(ctypes.Structure):
         ("n_cplx_dens", ctypes.c_int), ("n_groups_fixed", ctypes.c_int), ("n_groups_freq", ctypes.c_int),
         ("table_bytes", ctypes.c_int),
         ("flops_per_sample", ctypes.c_double), ("flops_per_sample_freq", ctypes.c_double),
+        ("bwd_flops_per_sample", ctypes.c_double), ("bwd_flops_per_sample_freq", ctypes.c_double),
     ]
 
 
@@ -69,6 +71,9 @@ def lib():
                                dp, dp, dp, dp, ctypes.c_size_t, vp]
     L.tami_forward_noalloc.argtypes = [vp, ctypes.POINTER(Lattice), u64, u64, i64, dp, ctypes.c_int,
                                        ctypes.c_double, dp, dp, dp, vp]
+    L.tami_backward_workspace.argtypes = [vp, i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.tami_backward.argtypes = [vp, ctypes.POINTER(Lattice), u64, u64, i64, dp, ctypes.c_int, ctypes.c_double,
+                                dp, dp, dp, dp, dp, dp, dp, ctypes.c_size_t, vp]
     L.tami_enumerate_sigma.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     L.tami_destroy.argtypes = [vp]
     L.tami_destroy.restype = None

@@ -122,6 +122,38 @@ class Diagram:
                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr()))
         return (torch.view_as_complex(mean), var, torch.view_as_complex(ps) if ps is not None else None)
 
+    def backward(self, lattice, seed, offset, n, X, beta, gout, per_sample=False):
+        """Adjoint of forward()'s mean for the upstream gradient gout (complex [n_f]).
+        Returns dict: dSigma_dX (complex [n_f]), grad_X_re (float64 [n_f]), grad_params
+        (float64 [3]: mu, kx_ext, ky_ext) and, with per_sample, dX (complex [n_f, n]) and
+        grads (float64 [n, 3])."""
+        torch = _torch()
+        dev = f"cuda:{self.device}"
+        Xp = _as_c_pairs(X, dev)
+        Gp = _as_c_pairs(gout, dev)
+        n_f = Xp.shape[0]
+        dX = torch.empty((n_f, 2), dtype=torch.float64, device=dev)
+        gX = torch.empty((n_f,), dtype=torch.float64, device=dev)
+        gp = torch.empty((3,), dtype=torch.float64, device=dev)
+        ps_dX = torch.empty((n_f, n, 2), dtype=torch.float64, device=dev) if per_sample else None
+        ps_g = torch.empty((n, 3), dtype=torch.float64, device=dev) if per_sample else None
+        nbytes = ctypes.c_size_t()
+        L.check(L.lib().tami_backward_workspace(self._h, int(n), n_f, ctypes.byref(nbytes)))
+        need = (nbytes.value + 255) // 256 * 256
+        if getattr(self, "_bws", None) is None or self._bws.numel() < need:
+            self._bws = torch.empty(need, dtype=torch.uint8, device=dev)
+        ws = self._bws
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        lat = L.Lattice(*[float(v) for v in lattice])
+        L.check(L.lib().tami_backward(self._h, ctypes.byref(lat), int(seed), int(offset), int(n), ptr(Xp), n_f,
+                                      float(beta), ptr(Gp), ptr(dX), ptr(gX), ptr(gp), ptr(ps_dX), ptr(ps_g),
+                                      ptr(ws), ws.numel(), _stream_ptr()))
+        out = {"dSigma_dX": torch.view_as_complex(dX), "grad_X_re": gX, "grad_params": gp}
+        if per_sample:
+            out["dX"] = torch.view_as_complex(ps_dX)
+            out["grads"] = ps_g
+        return out
+
 
 def enumerate_sigma(order):
     """Hubbard self-energy diagrams of `order` (libtami's enumerator and labeller, Sec. 2.5):

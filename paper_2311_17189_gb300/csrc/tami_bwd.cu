@@ -1,0 +1,422 @@
+// Adjoint of the Monte Carlo evaluation (sm_103a, FP64).  For an upstream gradient g_f of the
+// sample means Sigma_f (one complex number per external frequency) it returns
+//   dSigma_f/dX_f                          (the derivative along the external frequency; with
+//                                           X = omega + i Gamma this is dSigma/domega, whose real
+//                                           part gives the quasiparticle weight),
+//   d/domega_f  Re conj(g_f) Sigma_f,
+//   d/dtheta    Re sum_f conj(g_f) Sigma_f  for theta = mu, kx_ext, ky_ext.
+// The paper defines the forward evaluation (Sec. 2.3, Sec. 5.2); it has no adjoint.
+//
+// One thread per sample, every phase sample-major: the forward quantities of phase 1 are
+// recomputed (energies, combinations, Fermi values and their next derivative, group weights),
+// phase 2 runs over all frequencies and collects dv/dX, the adjoints of the group weights and
+// of the frequency-dependent denominator energies, and a reverse sweep pushes those back
+// through the term products (recomputed with prefix/suffix products, never stored), the
+// Fermi/Bose derivatives (d/dx P_k = P_{k+1}), the energy combinations and the dispersion
+// (dE/dmu = 1, dE/dk_ext = -alpha_ext * grad eps).  Reductions are in a fixed order.
+#include <algorithm>
+#include <cstring>
+
+#include "tami_device.cuh"
+#include "tami_internal.h"
+
+namespace tami {
+namespace {
+
+using namespace dev;
+
+// per-thread capacities of the adjoint (checked before launch)
+constexpr int kBwCombos = 64, kBwFv = 128, kBwRden = 32, kBwCden = 32, kBwG1 = 128, kBwG2 = 64;
+constexpr int kBwFreq = 256, kBwFac = 8;
+
+struct BwdParams {
+  TableHeader h;
+  const unsigned char* table;
+  double t, tp, mu, kx, ky;
+  unsigned long long seed, offset;
+  long long n;
+  const double* X;       // [n_f][2]
+  const double* G;       // [n_f][2] upstream gradient
+  int n_f;
+  double beta;
+  double* ps_dX;         // [n_f][n][2] or null
+  double* ps_grad;       // [n][3] or null
+  double* partial;       // [grid][2 n_f + 3]
+  int* status;
+};
+
+__host__ __device__ __forceinline__ size_t bwd_smem_bytes(const TableHeader& h, int n_f) {
+  return (size_t)align16(h.bytes) + sizeof(double) * (4 * (size_t)n_f + 4 * (2 * (size_t)n_f + 3));
+}
+
+__global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TableHeader& H = P.h;
+  const int tid = threadIdx.x;
+  if (!stage_table(smem, P.table, H.bytes, P.status)) return;
+  const int n_f = P.n_f;
+  double* Xs = reinterpret_cast<double*>(smem + align16(H.bytes));
+  double* Gs = Xs + 2 * n_f;
+  double* red = Gs + 2 * n_f;                 // [4 warps][2 n_f + 3]
+  for (int i = tid; i < 2 * n_f; i += kBlock) { Xs[i] = P.X[i]; Gs[i] = P.G[i]; }
+
+  const double* alpha = reinterpret_cast<const double*>(smem + H.off_alpha);
+  const int* repl = reinterpret_cast<const int*>(smem + H.off_repl);
+  const int* combo_ptr = reinterpret_cast<const int*>(smem + H.off_combo_ptr);
+  const int* combo_j = reinterpret_cast<const int*>(smem + H.off_combo_j);
+  const double* combo_c = reinterpret_cast<const double*>(smem + H.off_combo_c);
+  const int* fbase = reinterpret_cast<const int*>(smem + H.off_fbase);
+  const int* fvr = reinterpret_cast<const int*>(smem + H.off_fv);
+  const int* rden = reinterpret_cast<const int*>(smem + H.off_rden);
+  const int* cden = reinterpret_cast<const int*>(smem + H.off_cden);
+  const double* cden_a = reinterpret_cast<const double*>(smem + H.off_cden_a);
+  const int* g1 = reinterpret_cast<const int*>(smem + H.off_g1);
+  const int* g1_tgt = reinterpret_cast<const int*>(smem + H.off_g1_tgt);
+  const int* term = reinterpret_cast<const int*>(smem + H.off_term);
+  const double* term_A = reinterpret_cast<const double*>(smem + H.off_term_A);
+  const int* tfac = reinterpret_cast<const int*>(smem + H.off_tfac);
+  const int* g1rd = reinterpret_cast<const int*>(smem + H.off_g1rd);
+  const int* g2 = reinterpret_cast<const int*>(smem + H.off_g2);
+  const int* g2cd = reinterpret_cast<const int*>(smem + H.off_g2cd);
+
+  double accX[2 * kBwFreq];
+  for (int i = 0; i < 2 * n_f; ++i) accX[i] = 0.0;
+  double gmu = 0.0, gkx = 0.0, gky = 0.0;
+  __syncthreads();
+
+  const double beta = P.beta;
+  const long long n_tiles = (P.n + kBlock - 1) / kBlock;
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const long long s = tile * kBlock + tid;
+    if (s >= P.n) continue;
+    // ------------------------------------------------------------ forward recomputation
+    double kx[kMaxVars], ky[kMaxVars];
+    const unsigned long long sg = P.offset + (unsigned long long)s;
+    for (int l = 0; l < H.m; ++l) {
+      uint32_t c[4] = {(uint32_t)sg, (uint32_t)(sg >> 32), (uint32_t)l, 0u};
+      philox4x32_10(c, (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+      kx[l] = to_momentum(c[0], c[1]);
+      ky[l] = to_momentum(c[2], c[3]);
+    }
+    kx[H.m] = P.kx;
+    ky[H.m] = P.ky;
+    double E[kMaxLines], Sx[kMaxLines], Cx[kMaxLines], Sy[kMaxLines], Cy[kMaxLines];
+    for (int r = 0; r < H.n_rep; ++r) {
+      const int j = repl[r];
+      double ax = 0.0, ay = 0.0;
+      for (int l = 0; l < H.nv; ++l) {
+        const double cf = alpha[j * H.nv + l];
+        if (cf != 0.0) { ax = fma(cf, kx[l], ax); ay = fma(cf, ky[l], ay); }
+      }
+      double sx, cx, sy, cy;
+      cw_sincos(ax, sx, cx);
+      cw_sincos(ay, sy, cy);
+      E[j] = fma(4.0 * P.tp, __dmul_rn(cx, cy), fma(2.0 * P.t, __dadd_rn(cx, cy), P.mu));
+      Sx[j] = sx; Cx[j] = cx; Sy[j] = sy; Cy[j] = cy;
+    }
+    double x[kBwCombos];
+    for (int u = 0; u < H.n_combo; ++u) {
+      double v = 0.0;
+      for (int q = combo_ptr[u]; q < combo_ptr[u + 1]; ++q) v = fma(combo_c[q], E[combo_j[q]], v);
+      x[u] = v;
+    }
+    double fv[kBwFv], fvd[kBwFv];
+    for (int b = 0; b < H.n_fbase; ++b) {
+      const double xv = x[fbase[4 * b]];
+      const double nt = -beta * fabs(xv);
+      const double y = exp(nt);
+      const double em = fbase[4 * b + 3] ? expm1(nt) : 0.0;
+      int cur_sigma = 0;
+      double g = 0.0, hh = 0.0;
+      for (int v = fbase[4 * b + 1]; v < fbase[4 * b + 2]; ++v) {
+        const int sigma = fvr[4 * v], sign = fvr[4 * v + 1], k = fvr[4 * v + 2];
+        if (sigma != cur_sigma) {
+          cur_sigma = sigma;
+          const double rD = rcp(sigma > 0 ? 1.0 + y : -em);
+          const double t2 = (sigma > 0 ? y : -y) * rD;
+          if (xv <= 0.0) { g = rD; hh = t2; } else { g = t2; hh = rD; }
+        }
+        const double gg = sign > 0 ? g : hh, hg = sign > 0 ? hh : g;
+        fv[v] = fermi_poly(k, gg, hg, beta);
+        fvd[v] = fermi_poly(k + 1, gg, hg, beta);
+      }
+    }
+    double rr[kBwRden];
+    for (int i = 0; i < H.n_rden; ++i) rr[i] = rcp(x[rden[2 * i]]);
+    double W1[kBwG1], W2[kBwG2];
+    for (int h = 0; h < H.n_g2; ++h) W2[h] = 0.0;
+    for (int gi = 0; gi < H.n_g1; ++gi) {
+      double ft = 0.0;
+      for (int t = g1[4 * gi]; t < g1[4 * gi + 1]; ++t) {
+        double p = term_A[t];
+        const int f0 = term[t], f1 = term[t + 1];
+        for (int q = f0; q < f1 - 1; ++q) p *= fv[tfac[q]];
+        ft = fma(p, fv[tfac[f1 - 1]], ft);
+      }
+      for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
+        const double r = rr[g1rd[2 * q]];
+        for (int pw = g1rd[2 * q + 1]; pw > 0; --pw) ft *= r;
+      }
+      W1[gi] = ft;
+      W2[g1_tgt[gi]] += ft;
+    }
+    double b[kBwCden];
+    for (int c = 0; c < H.n_cden; ++c) {
+      const double xv = x[cden[2 * c]];
+      b[c] = cden[2 * c + 1] > 0 ? xv : -xv;
+    }
+    // ------------------------------------------------------------ phase 2 over frequencies
+    double Wb2[kBwG2], bb[kBwCden];
+    for (int h = 0; h < H.n_g2; ++h) Wb2[h] = 0.0;
+    for (int c = 0; c < H.n_cden; ++c) bb[c] = 0.0;
+    for (int f = 0; f < n_f; ++f) {
+      const double Xr = Xs[2 * f], Xi = Xs[2 * f + 1], gr = Gs[2 * f], gim = Gs[2 * f + 1];
+      double rc_re[kBwCden], rc_im[kBwCden], U_re[kBwCden], U_im[kBwCden];
+      for (int c = 0; c < H.n_cden; ++c) {
+        const double a = cden_a[c];
+        const double Dr = fma(a, Xr, b[c]);
+        const double Di = a * Xi;
+        const double r = rcp(fma(Dr, Dr, Di * Di));
+        rc_re[c] = Dr * r;
+        rc_im[c] = -Di * r;
+        U_re[c] = 0.0;
+        U_im[c] = 0.0;
+      }
+      for (int h = 0; h < H.n_g2; ++h) {
+        const int q0 = g2[h], q1 = g2[h + 1];
+        if (q0 == q1) { Wb2[h] += gr; continue; }   // R = 1
+        double Rr = 1.0, Ri = 0.0;
+        bool first = true;
+        for (int q = q0; q < q1; ++q) {
+          const int c = g2cd[2 * q];
+          for (int pw = g2cd[2 * q + 1]; pw > 0; --pw) {
+            if (first) { Rr = rc_re[c]; Ri = rc_im[c]; first = false; }
+            else {
+              const double nr = fma(Rr, rc_re[c], -Ri * rc_im[c]);
+              Ri = fma(Rr, rc_im[c], Ri * rc_re[c]);
+              Rr = nr;
+            }
+          }
+        }
+        Wb2[h] = fma(gr, Rr, fma(gim, Ri, Wb2[h]));
+        const double Tr = W2[h] * Rr, Ti = W2[h] * Ri;
+        for (int q = q0; q < q1; ++q) {
+          const int c = g2cd[2 * q];
+          const double p = (double)g2cd[2 * q + 1];
+          U_re[c] = fma(p, Tr, U_re[c]);
+          U_im[c] = fma(p, Ti, U_im[c]);
+        }
+      }
+      double dvr = 0.0, dvi = 0.0;
+      for (int c = 0; c < H.n_cden; ++c) {
+        const double Zr = fma(rc_re[c], U_re[c], -rc_im[c] * U_im[c]);
+        const double Zi = fma(rc_re[c], U_im[c], rc_im[c] * U_re[c]);
+        dvr = fma(-cden_a[c], Zr, dvr);
+        dvi = fma(-cden_a[c], Zi, dvi);
+        bb[c] -= fma(gr, Zr, gim * Zi);
+      }
+      accX[2 * f] += dvr;
+      accX[2 * f + 1] += dvi;
+      if (P.ps_dX) {
+        double2* o = reinterpret_cast<double2*>(P.ps_dX) + (size_t)f * P.n + s;
+        *o = make_double2(dvr, dvi);
+      }
+    }
+    // ------------------------------------------------------------ reverse sweep
+    double xbar[kBwCombos], fvbar[kBwFv];
+    for (int u = 0; u < H.n_combo; ++u) xbar[u] = 0.0;
+    for (int v = 0; v < H.n_fv; ++v) fvbar[v] = 0.0;
+    for (int c = 0; c < H.n_cden; ++c) {
+      const int u = cden[2 * c];
+      xbar[u] += cden[2 * c + 1] > 0 ? bb[c] : -bb[c];
+    }
+    for (int gi = 0; gi < H.n_g1; ++gi) {
+      const double wb = Wb2[g1_tgt[gi]];
+      double RR = 1.0;
+      for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
+        const int i = g1rd[2 * q];
+        const int pw = g1rd[2 * q + 1];
+        for (int k = 0; k < pw; ++k) RR *= rr[i];
+        // W1 = FT prod rr^p and rr = 1/x:  dW1/dx = -p rr W1
+        xbar[rden[2 * i]] -= wb * W1[gi] * (double)pw * rr[i];
+      }
+      const double ftbar = wb * RR;
+      for (int t = g1[4 * gi]; t < g1[4 * gi + 1]; ++t) {
+        const int f0 = term[t], nfac = term[t + 1] - f0;
+        double pre[kBwFac];
+        pre[0] = term_A[t];
+        for (int i = 1; i < nfac; ++i) pre[i] = pre[i - 1] * fv[tfac[f0 + i - 1]];
+        double suf = ftbar;
+        for (int i = nfac - 1; i >= 0; --i) {
+          const int v = tfac[f0 + i];
+          fvbar[v] = fma(pre[i], suf, fvbar[v]);
+          suf *= fv[v];
+        }
+      }
+    }
+    for (int bse = 0; bse < H.n_fbase; ++bse) {
+      const int u = fbase[4 * bse];
+      double acc = 0.0;
+      for (int v = fbase[4 * bse + 1]; v < fbase[4 * bse + 2]; ++v) {
+        const double d = fvbar[v] * fvd[v];
+        acc += fvr[4 * v + 1] > 0 ? d : -d;
+      }
+      xbar[u] += acc;
+    }
+    double Ebar[kMaxLines];
+    for (int r = 0; r < H.n_rep; ++r) Ebar[repl[r]] = 0.0;
+    for (int u = 0; u < H.n_combo; ++u)
+      for (int q = combo_ptr[u]; q < combo_ptr[u + 1]; ++q) Ebar[combo_j[q]] = fma(xbar[u], combo_c[q], Ebar[combo_j[q]]);
+    double mub = 0.0, kxb = 0.0, kyb = 0.0;
+    for (int r = 0; r < H.n_rep; ++r) {
+      const int j = repl[r];
+      const double eb = Ebar[j];
+      mub += eb;
+      const double ae = alpha[j * H.nv + H.m];
+      if (ae != 0.0) {
+        // dE/dKx = -(2t + 4t' cos Ky) sin Kx,  dK/dk_ext = alpha_ext
+        kxb = fma(-eb * ae, fma(4.0 * P.tp, Cy[j], 2.0 * P.t) * Sx[j], kxb);
+        kyb = fma(-eb * ae, fma(4.0 * P.tp, Cx[j], 2.0 * P.t) * Sy[j], kyb);
+      }
+    }
+    gmu += mub;
+    gkx += kxb;
+    gky += kyb;
+    if (P.ps_grad) {
+      P.ps_grad[3 * s] = mub;
+      P.ps_grad[3 * s + 1] = kxb;
+      P.ps_grad[3 * s + 2] = kyb;
+    }
+  }
+  // -------------------------------------------------------------- block reduction
+  const int nval = 2 * n_f + 3;
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int i = 0; i < nval; ++i) {
+    double v = i < 2 * n_f ? accX[i] : (i == 2 * n_f ? gmu : (i == 2 * n_f + 1 ? gkx : gky));
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp * nval + i] = v;
+  }
+  __syncthreads();
+  for (int i = tid; i < nval; i += kBlock) {
+    double v = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) v += red[w * nval + i];
+    P.partial[(size_t)blockIdx.x * nval + i] = v;
+  }
+}
+
+__global__ void bwd_finalize_kernel(const double* partial, int n_blocks, int n_f, long long n, const double* G,
+                                    const int* status, double* dX, double* grad_omega, double* grad_params) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nval = 2 * n_f + 3;
+  const bool bad = status && *status != 0;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  if (i < n_f) {
+    double re = 0.0, im = 0.0;
+    for (int b = 0; b < n_blocks; ++b) {
+      re += partial[(size_t)b * nval + 2 * i];
+      im += partial[(size_t)b * nval + 2 * i + 1];
+    }
+    re /= (double)n;
+    im /= (double)n;
+    if (bad) re = im = nan;
+    if (dX) { dX[2 * i] = re; dX[2 * i + 1] = im; }
+    if (grad_omega) grad_omega[i] = bad ? nan : fma(G[2 * i], re, G[2 * i + 1] * im);
+  } else if (i < n_f + 3) {
+    const int k = i - n_f;
+    double v = 0.0;
+    for (int b = 0; b < n_blocks; ++b) v += partial[(size_t)b * nval + 2 * n_f + k];
+    if (grad_params) grad_params[k] = bad ? nan : v / (double)n;
+  }
+}
+
+int bwd_grid(const tami_diagram* d, int n_f, long long n, size_t* smem_out) {
+  DeviceProps dp = device_props(d->device);
+  const size_t smem = bwd_smem_bytes(d->hdr, n_f);
+  if (smem_out) *smem_out = smem;
+  if (smem > dp.smem_optin) return -1;
+  cudaFuncSetAttribute(bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel, kBlock, smem) != cudaSuccess) per_sm = 1;
+  if (per_sm < 1) per_sm = 1;
+  long long tiles = (n + kBlock - 1) / kBlock;
+  long long grid = (long long)dp.sms * per_sm;
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  return (int)grid;
+}
+
+int bwd_check(const tami_diagram* d, int n_f) {
+  if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
+  if (!d->d_blob) { set_error("diagram not uploaded (call tami_upload)"); return TAMI_EINVAL; }
+  if (n_f < 1 || n_f > kBwFreq) { set_error("n_f must be in [1, 256] for the adjoint"); return TAMI_EINVAL; }
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != d->device) { set_error("current device differs from the upload device"); return TAMI_EINVAL; }
+  const TableHeader& h = d->hdr;
+  int max_fac = 0;
+  for (const SymTerm& t : d->terms) max_fac = std::max(max_fac, (int)t.F.size());
+  if (h.max_der > 4) { set_error("the adjoint needs derivative orders up to 4"); return TAMI_EUNSUPPORTED; }
+  if (h.n_combo > kBwCombos || h.n_fv > kBwFv || h.n_rden > kBwRden || h.n_cden > kBwCden ||
+      h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || max_fac > kBwFac) {
+    set_error("term table exceeds the adjoint kernel's per-sample capacities");
+    return TAMI_EUNSUPPORTED;
+  }
+  return TAMI_OK;
+}
+
+constexpr size_t kBwStatusBytes = 256;
+
+}  // namespace
+}  // namespace tami
+
+using namespace tami;
+
+extern "C" {
+
+int tami_backward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, size_t* bytes) {
+  int rc = bwd_check(d, n_f);
+  if (rc) return rc;
+  if (!bytes || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
+  const int grid = bwd_grid(d, n_f, n_samples, nullptr);
+  if (grid < 0) { set_error("term table and frequencies exceed shared memory"); return TAMI_EUNSUPPORTED; }
+  *bytes = kBwStatusBytes + sizeof(double) * (size_t)(2 * n_f + 3) * (size_t)grid;
+  return TAMI_OK;
+}
+
+int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
+                  int64_t n_samples, const double* X, int n_f, double beta, const double* gout,
+                  double* dsigma_dX, double* grad_X_re, double* grad_params, double* per_sample_dX,
+                  double* per_sample_grads, void* workspace, size_t workspace_bytes, tami_stream_t stream) {
+  int rc = bwd_check(d, n_f);
+  if (rc) return rc;
+  if (!lat || !X || !gout || !workspace || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (((uintptr_t)workspace & 255) != 0) { set_error("workspace must be 256-byte aligned"); return TAMI_EINVAL; }
+  size_t smem = 0;
+  const int grid = bwd_grid(d, n_f, n_samples, &smem);
+  if (grid < 0) { set_error("term table and frequencies exceed shared memory"); return TAMI_EUNSUPPORTED; }
+  const size_t need = kBwStatusBytes + sizeof(double) * (size_t)(2 * n_f + 3) * (size_t)grid;
+  if (workspace_bytes < need) { set_error("workspace too small"); return TAMI_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  int* status = static_cast<int*>(workspace);
+  double* partial = reinterpret_cast<double*>(static_cast<char*>(workspace) + kBwStatusBytes);
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  BwdParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.h = d->hdr;
+  P.table = static_cast<const unsigned char*>(d->d_blob);
+  P.t = lat->t; P.tp = lat->tp; P.mu = lat->mu; P.kx = lat->kx_ext; P.ky = lat->ky_ext;
+  P.seed = seed; P.offset = offset; P.n = n_samples;
+  P.X = X; P.G = gout; P.n_f = n_f; P.beta = beta;
+  P.ps_dX = per_sample_dX; P.ps_grad = per_sample_grads;
+  P.partial = partial; P.status = status;
+  bwd_kernel<<<grid, kBlock, smem, st>>>(P);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "bwd_kernel launch");
+  bwd_finalize_kernel<<<(n_f + 3 + 127) / 128, 128, 0, st>>>(partial, grid, n_f, n_samples, gout, status,
+                                                              dsigma_dX, grad_X_re, grad_params);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "bwd finalize launch");
+}
+
+}  // extern "C"

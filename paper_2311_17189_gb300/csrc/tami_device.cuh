@@ -1,0 +1,169 @@
+// Device helpers shared by the libtami kernels (forward and adjoint translation units), and
+// the host-side launch helpers they share.  Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+
+#include "tami_internal.h"
+
+namespace tami {
+namespace dev {
+
+constexpr int kBlock = 128;                 // threads per block = samples per tile
+constexpr long long kSpinLimit = 1ll << 24;  // bound on every device-side wait
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+}
+
+// [0,1) from 53 bits of two words, then k = 2 pi u - pi with one rounding
+__device__ __forceinline__ double to_momentum(uint32_t hi, uint32_t lo) {
+  unsigned long long m = ((unsigned long long)hi << 21) | (unsigned long long)(lo >> 11);
+  double u = __dmul_rn(__ull2double_rn(m), 0x1.0p-53);
+  const double pi = 0x1.921fb54442d18p+1;
+  return fma(u, 2.0 * pi, -pi);
+}
+
+// cos and sin: Cody-Waite reduction by pi/2 (three-part constant) and Taylor series on
+// [-pi/4, pi/4] (W. J. Cody and W. Waite, 1980).  Every operation is an explicit fma or a
+// rounded mul/add intrinsic, so the result is the same on any IEEE machine that follows
+// the same recipe.
+__device__ __forceinline__ void cw_sincos(double k, double& s_out, double& c_out) {
+  const double two_over_pi = 0x1.45f306dc9c883p-1;
+  const double P1 = 0x1.921fb54442d18p+0, P2 = 0x1.1a62633145c07p-54, P3 = -0x1.f1976b7ed8fbcp-110;
+  double n = rint(__dmul_rn(k, two_over_pi));
+  double r = fma(-n, P1, k);
+  r = fma(-n, P2, r);
+  r = fma(-n, P3, r);
+  double z = __dmul_rn(r, r);
+  double ps = -0x1.2f49b46814157p-57;
+  ps = fma(ps, z, 0x1.952c77030ad4ap-49);
+  ps = fma(ps, z, -0x1.ae7f3e733b81fp-41);
+  ps = fma(ps, z, 0x1.6124613a86d09p-33);
+  ps = fma(ps, z, -0x1.ae64567f544e4p-26);
+  ps = fma(ps, z, 0x1.71de3a556c734p-19);
+  ps = fma(ps, z, -0x1.a01a01a01a01ap-13);
+  ps = fma(ps, z, 0x1.1111111111111p-7);
+  ps = fma(ps, z, -0x1.5555555555555p-3);
+  double sr = fma(__dmul_rn(r, z), ps, r);
+  double pc = 0x1.e542ba4020225p-62;
+  pc = fma(pc, z, -0x1.6827863b97d97p-53);
+  pc = fma(pc, z, 0x1.ae7f3e733b81fp-45);
+  pc = fma(pc, z, -0x1.93974a8c07c9dp-37);
+  pc = fma(pc, z, 0x1.1eed8eff8d898p-29);
+  pc = fma(pc, z, -0x1.27e4fb7789f5cp-22);
+  pc = fma(pc, z, 0x1.a01a01a01a01ap-16);
+  pc = fma(pc, z, -0x1.6c16c16c16c17p-10);
+  pc = fma(pc, z, 0x1.5555555555555p-5);
+  pc = fma(pc, z, -0x1.0000000000000p-1);
+  double cr = fma(z, pc, 1.0);
+  int q = (int)((long long)n & 3);
+  double s = (q == 0) ? sr : (q == 1) ? cr : (q == 2) ? -sr : -cr;
+  double c = (q == 0) ? cr : (q == 1) ? -sr : (q == 2) ? -cr : sr;
+  s_out = s;
+  c_out = c;
+}
+
+// E = mu - eps(k),  eps(k) = -2t(cos kx + cos ky) - 4t' cos kx cos ky
+__device__ __forceinline__ double line_energy(double kx, double ky, double t, double tp, double mu) {
+  double sx, cx, sy, cy;
+  cw_sincos(kx, sx, cx);
+  cw_sincos(ky, sy, cy);
+  double sum = __dadd_rn(cx, cy);
+  double prod = __dmul_rn(cx, cy);
+  return fma(4.0 * tp, prod, fma(2.0 * t, sum, mu));
+}
+
+// 1/d: hardware estimate refined by one third-order Newton-Raphson step,
+// r <- r (1 + e + e^2), e = 1 - d r  (error e^3).
+__device__ __forceinline__ double rcp(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+
+// d^k/dx^k g at (g, h = 1 - g): (-beta)^k sum_i (-1)^i A(k,i) g^(i+1) h^(k-i), A = Eulerian
+__device__ __forceinline__ double fermi_poly(int k, double g, double h, double beta) {
+  if (k == 0) return g;
+  double gh = g * h;
+  if (k == 1) return -beta * gh;
+  double d = h - g;
+  if (k == 2) return beta * beta * gh * d;
+  if (k == 3) return -beta * beta * beta * gh * fma(d, d, -2.0 * gh);
+  double b4 = beta * beta * beta * beta;
+  double h2 = h * h, g2 = g * g;
+  if (k == 4) return b4 * gh * (h2 * h - 11.0 * g * h2 + 11.0 * g2 * h - g2 * g);
+  return -b4 * beta * gh * (h2 * h2 - 26.0 * g * h2 * h + 66.0 * g2 * h2 - 26.0 * g2 * g * h + g2 * g2);
+}
+
+__host__ __device__ __forceinline__ int align16(int b) { return (b + 15) & ~15; }
+
+__device__ __forceinline__ bool stage_table(unsigned char* dst, const unsigned char* src, int bytes, int* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(d), "l"(src), "r"(bytes), "r"(b) : "memory");
+  }
+  uint32_t done = 0;
+  long long it = 0;
+  for (; it < kSpinLimit && !done; ++it) {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(b) : "memory");
+    if (!done && it > 64) __nanosleep(64);
+  }
+  if (!done) {
+    if (status) atomicExch(status, TAMI_ETIMEOUT);
+    // the copy is still owned by this block: wait for it once more (bounded) before leaving
+    for (long long j = 0; j < kSpinLimit && !done; ++j) {
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                   : "=r"(done) : "r"(b) : "memory");
+      __nanosleep(256);
+    }
+  }
+  return done != 0;
+}
+
+// ------------------------------------------------------------------------------- host helpers
+inline int cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return TAMI_ECUDA;
+}
+
+struct DeviceProps { int sms = 0; size_t smem_optin = 0; };
+inline DeviceProps device_props(int dev) {
+  static std::mutex mu;
+  static DeviceProps cache[64];
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 0 || dev >= 64) return DeviceProps{};
+  if (!cache[dev].sms) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) {
+      cache[dev].sms = p.multiProcessorCount;
+      cache[dev].smem_optin = p.sharedMemPerBlockOptin;
+    }
+  }
+  return cache[dev];
+}
+
+}  // namespace dev
+}  // namespace tami

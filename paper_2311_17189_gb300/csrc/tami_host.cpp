@@ -481,6 +481,25 @@ int flatten(tami_diagram* d) {
   }
   ff += 6.0;                                            // mean and variance sums
   I.flops_per_sample_freq = ff;
+  // adjoint: the forward's phase 1 again plus the next derivative of every Fermi value, then per
+  // frequency the phase-2 products with the adjoint contractions, then the reverse sweep
+  double bl = fl;
+  for (const FvKey& k : fvs) bl += k.k + 1 == 1 ? 2.0 : k.k + 1 == 2 ? 5.0 : 9.0 + 3.0 * k.k;
+  bl += 2.0 * h.n_cden;                                 // cden adjoints into combinations
+  for (auto& g : g1s) {
+    for (auto& pr : g.rd) bl += pr.second + 4.0;        // RR and the real-denominator adjoint
+    bl += 1.0;
+    for (int ti : g.terms) bl += 4.0 * ft[ti].fv.size();  // prefix/suffix products, fvbar fma
+  }
+  bl += 3.0 * h.n_fv + 2.0 * nnz + 10.0 * h.n_rep;     // fvbar -> x -> E -> (mu, k_ext)
+  I.bwd_flops_per_sample = bl;
+  double bf = 14.0 * h.n_cden + 12.0 * h.n_cden + 2.0;  // reciprocals, Z, dv/dX and b-adjoints, accX
+  for (auto& g : g2s) {
+    int pw = 0;
+    for (auto& pr : g) pw += pr.second;
+    bf += pw ? 6.0 * (pw - 1) + 4.0 + 2.0 + 4.0 * g.size() : 1.0;   // R, Wbar, T, U
+  }
+  I.bwd_flops_per_sample_freq = bf;
   return TAMI_OK;
 }
 
