@@ -184,6 +184,31 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
                          int64_t n_samples, const double* X, int n_f, double beta, double* mean,
                          double* var, double* per_sample, tami_stream_t stream);
 
+/* Many diagrams in one persistent launch (the paper evaluates one diagram per call; this batches
+ * them).  Each diagram d gets samples[d] Philox samples with key seeds[d] (counter offset 0), the
+ * lattice and the n_f external frequencies are shared.
+ * tami_batch_plan packs the diagrams' tables into one device buffer, cuts every sample stream into
+ * work items of chunk_tiles x 128 samples, orders the items by estimated cost (largest first) and
+ * captures [queue reset, persistent kernel, reduction] into a CUDA graph on the current device.
+ * chunk_tiles = 0 lets an autotuner pick the chunk size by timing graph replays with typical
+ * inputs; the choice is cached per (GPU, batch signature) in memory and in a text file
+ * ($TAMI_TUNE_CACHE, default $HOME/.cache/libtami_autotune.txt).  The diagrams must outlive the plan
+ * only until tami_batch_plan returns (their tables are copied).  Allocates device memory. */
+typedef struct tami_batch tami_batch;
+int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* samples, const uint64_t* seeds, int n_f,
+                    int chunk_tiles, tami_batch** out);
+
+/* Work items, grid size and chunk size (tiles of 128 samples per item) of a plan. */
+int tami_batch_info(const tami_batch* b, int* n_items, int* grid, int* chunk_tiles);
+
+/* Replay the plan: X device double [n_f][2]; mean and var device double [n_d][n_f][2] (var may be
+ * NULL), as tami_forward's mean and variances for each diagram.  Launches asynchronously on
+ * `stream`; the per-item reduction is in tile order, so results are deterministic for a plan. */
+int tami_batch_launch(tami_batch* b, const tami_lattice* lat, const double* X, double beta, double* mean,
+                      double* var, tami_stream_t stream);
+
+void tami_batch_destroy(tami_batch* b);
+
 /* Hubbard (U n_up n_down) self-energy diagrams of the given order (2..6), one-particle
  * irreducible, without tadpoles, in canonical order, labelled with momentum-conserving alpha
  * (Sec. 2.5: graph representation and labelling).  With capacity 0 only *n_out is set.

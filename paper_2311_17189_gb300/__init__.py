@@ -9,6 +9,6 @@ Only marshalling lives in Python; the construction is libtami's C++ and every ev
 step is a libtami CUDA kernel.  `workloads` holds the seeded synthetic inputs.
 """
 from . import _lib, mc
-from .api import Diagram, enumerate_sigma
+from .api import Batch, Diagram, enumerate_sigma
 
-__all__ = ["Diagram", "enumerate_sigma", "_lib", "mc"]
+__all__ = ["Batch", "Diagram", "enumerate_sigma", "_lib", "mc"]

@@ -18,7 +18,8 @@ TAMI_OK, TAMI_EINVAL, TAMI_ENOMEM, TAMI_ECUDA, TAMI_ETIMEOUT, TAMI_EUNSUPPORTED 
 EXPORTS = [
     "tami_last_error", "tami_construct", "tami_diagram_info", "tami_upload", "tami_sample_energies",
     "tami_eval_energies", "tami_forward_workspace", "tami_forward", "tami_forward_noalloc",
-    "tami_backward_workspace", "tami_backward",
+    "tami_backward_workspace", "tami_backward", "tami_batch_plan", "tami_batch_info", "tami_batch_launch",
+    "tami_batch_destroy",
     "tami_enumerate_sigma",
     "tami_destroy",
 ]
@@ -74,6 +75,12 @@ def lib():
     L.tami_backward_workspace.argtypes = [vp, i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.tami_backward.argtypes = [vp, ctypes.POINTER(Lattice), u64, u64, i64, dp, ctypes.c_int, ctypes.c_double,
                                 dp, dp, dp, dp, dp, dp, dp, ctypes.c_size_t, vp]
+    L.tami_batch_plan.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+    L.tami_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int)]
+    L.tami_batch_launch.argtypes = [vp, ctypes.POINTER(Lattice), dp, ctypes.c_double, dp, dp, vp]
+    L.tami_batch_destroy.argtypes = [vp]
+    L.tami_batch_destroy.restype = None
     L.tami_enumerate_sigma.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     L.tami_destroy.argtypes = [vp]
     L.tami_destroy.restype = None

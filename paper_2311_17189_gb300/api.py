@@ -155,6 +155,55 @@ class Diagram:
         return out
 
 
+class Batch:
+    """Many diagrams in one persistent, graph-captured launch (tami_batch_*).  Each diagram d gets
+    samples[d] Philox samples with key seeds[d]; the lattice and frequencies are shared."""
+
+    def __init__(self, diagrams, samples, seeds, n_f, chunk_tiles=0):
+        torch = _torch()
+        self.diagrams = list(diagrams)
+        n_d = len(self.diagrams)
+        hs = (ctypes.c_void_p * n_d)(*[d._h.value for d in self.diagrams])
+        smp = np.ascontiguousarray(np.asarray(samples, dtype=np.int64))
+        sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+        h = ctypes.c_void_p()
+        L.check(L.lib().tami_batch_plan(ctypes.cast(hs, ctypes.c_void_p), n_d, L._np_ptr(smp), L._np_ptr(sd),
+                                        int(n_f), int(chunk_tiles), ctypes.byref(h)))
+        self._h = h
+        self.n_d, self.n_f = n_d, int(n_f)
+        self.device = torch.cuda.current_device()
+
+    def info(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        L.check(L.lib().tami_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"items": a.value, "grid": b.value, "chunk_tiles": c.value}
+
+    def launch(self, lattice, X, beta, out=None):
+        """Returns (mean complex [n_d, n_f], var float64 [n_d, n_f, 2])."""
+        torch = _torch()
+        dev = f"cuda:{self.device}"
+        Xp = _as_c_pairs(X, dev)
+        if out is None:
+            mean = torch.empty((self.n_d, self.n_f, 2), dtype=torch.float64, device=dev)
+            var = torch.empty((self.n_d, self.n_f, 2), dtype=torch.float64, device=dev)
+        else:
+            mean, var = out
+        lat = L.Lattice(*[float(v) for v in lattice])
+        L.check(L.lib().tami_batch_launch(self._h, ctypes.byref(lat), ctypes.c_void_p(Xp.data_ptr()), float(beta),
+                                          ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(var.data_ptr()),
+                                          _stream_ptr()))
+        return torch.view_as_complex(mean), var
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                L.lib().tami_batch_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+
 def enumerate_sigma(order):
     """Hubbard self-energy diagrams of `order` (libtami's enumerator and labeller, Sec. 2.5):
     list of dicts with alpha [N, m+1], eps [N, N], code, loops, in canonical order."""

@@ -16,8 +16,8 @@ OUT = os.path.join(PKG, "libtami.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["tami_host.cpp", "tami_cuda.cu", "tami_bwd.cu"]
-HEADERS = ["tami_internal.h", "tami_device.cuh"]
+SOURCES = ["tami_host.cpp", "tami_cuda.cu", "tami_bwd.cu", "tami_batch.cu"]
+HEADERS = ["tami_internal.h", "tami_device.cuh", "tami_fwd_tile.cuh"]
 
 
 def _stale(out, deps):

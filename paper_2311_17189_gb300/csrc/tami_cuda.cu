@@ -22,14 +22,13 @@
 #include <string>
 
 #include "tami_device.cuh"
+#include "tami_fwd_tile.cuh"
 #include "tami_internal.h"
 
 namespace tami {
 namespace {
 
 using namespace dev;
-
-constexpr int kMaxFreqPerThread = 16;  // n_f <= kMaxFreqPerThread * kBlock
 
 struct FwdParams {
   TableHeader h;
@@ -63,206 +62,20 @@ __global__ void __launch_bounds__(kBlock) fwd_kernel(const FwdParams P) {
   double* W = CB + H.n_cden * kBlock;
   double* red = W + H.n_g2 * kBlock;
   for (int i = tid; i < 2 * P.n_f; i += kBlock) Xs[i] = P.X[i];
-
-  const double* alpha = reinterpret_cast<const double*>(smem + H.off_alpha);
-  const int* repl = reinterpret_cast<const int*>(smem + H.off_repl);
-  const int* combo_ptr = reinterpret_cast<const int*>(smem + H.off_combo_ptr);
-  const int* combo_j = reinterpret_cast<const int*>(smem + H.off_combo_j);
-  const double* combo_c = reinterpret_cast<const double*>(smem + H.off_combo_c);
-  const int* fbase = reinterpret_cast<const int*>(smem + H.off_fbase);
-  const int* fvr = reinterpret_cast<const int*>(smem + H.off_fv);
-  const int* rden = reinterpret_cast<const int*>(smem + H.off_rden);
-  const int* cden = reinterpret_cast<const int*>(smem + H.off_cden);
-  const double* cden_a = reinterpret_cast<const double*>(smem + H.off_cden_a);
-  const int* g1 = reinterpret_cast<const int*>(smem + H.off_g1);
-  const int* g1_tgt = reinterpret_cast<const int*>(smem + H.off_g1_tgt);
-  const int* term = reinterpret_cast<const int*>(smem + H.off_term);
-  const double* term_A = reinterpret_cast<const double*>(smem + H.off_term_A);
-  const int* tfac = reinterpret_cast<const int*>(smem + H.off_tfac);
-  const int* g1rd = reinterpret_cast<const int*>(smem + H.off_g1rd);
-  const int* g2 = reinterpret_cast<const int*>(smem + H.off_g2);
-  const int* g2cd = reinterpret_cast<const int*>(smem + H.off_g2cd);
-
-  // phase-2 assignment: TPF threads per frequency, or several frequencies per thread
-  const int n_f = P.n_f;
-  int tpf, my_f0, my_fstep, my_nf, my_s0, my_sstep;
-  if (n_f <= kBlock) {
-    tpf = kBlock / n_f;
-    my_f0 = tid / tpf;
-    my_fstep = 1;
-    my_nf = my_f0 < n_f ? 1 : 0;
-    my_s0 = tid % tpf;
-    my_sstep = tpf;
-  } else {
-    tpf = 1;
-    my_f0 = tid;
-    my_fstep = kBlock;
-    my_nf = (n_f - tid + kBlock - 1) / kBlock;
-    my_s0 = 0;
-    my_sstep = 1;
-  }
+  const TableView T = table_view(smem, H);
+  const FreqMap M = freq_map(P.n_f, tid);
   double acc[kMaxFreqPerThread][4];
   for (int i = 0; i < kMaxFreqPerThread; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0;
   __syncthreads();
-
-  const double beta = P.beta;
+  TileArgs A;
+  A.t = P.t; A.tp = P.tp; A.mu = P.mu; A.kx = P.kx; A.ky = P.ky; A.beta = P.beta;
+  A.seed = P.seed; A.offset = P.offset; A.n = P.n; A.E_in = P.E_in; A.per_sample = P.per_sample;
+  A.n_f = P.n_f;
   const long long n_tiles = (P.n + kBlock - 1) / kBlock;
-  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const long long s0 = tile * kBlock;
-    // ---------------------------------------------------------------- phase 1
-    {
-      const long long s = s0 + tid;
-      if (s < P.n) {
-        double E[kMaxLines];
-        if (ENERGY_IN) {
-          for (int r = 0; r < H.n_rep; ++r) E[repl[r]] = P.E_in[s * H.N + repl[r]];
-        } else {
-          double kx[kMaxVars], ky[kMaxVars];
-          const unsigned long long sg = P.offset + (unsigned long long)s;
-          for (int l = 0; l < H.m; ++l) {
-            uint32_t c[4] = {(uint32_t)sg, (uint32_t)(sg >> 32), (uint32_t)l, 0u};
-            philox4x32_10(c, (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-            kx[l] = to_momentum(c[0], c[1]);
-            ky[l] = to_momentum(c[2], c[3]);
-          }
-          kx[H.m] = P.kx;
-          ky[H.m] = P.ky;
-          for (int r = 0; r < H.n_rep; ++r) {
-            const int j = repl[r];
-            double ax = 0.0, ay = 0.0;
-            for (int l = 0; l < H.nv; ++l) {
-              const double cf = alpha[j * H.nv + l];
-              if (cf != 0.0) { ax = fma(cf, kx[l], ax); ay = fma(cf, ky[l], ay); }
-            }
-            E[j] = line_energy(ax, ay, P.t, P.tp, P.mu);
-          }
-        }
-        double x[kMaxCombos];
-        for (int u = 0; u < H.n_combo; ++u) {
-          double v = 0.0;
-          for (int q = combo_ptr[u]; q < combo_ptr[u + 1]; ++q) v = fma(combo_c[q], E[combo_j[q]], v);
-          x[u] = v;
-        }
-        double fv[kMaxFermiValues];
-        for (int b = 0; b < H.n_fbase; ++b) {
-          // y = e^{-beta|x|} keeps the tails exact; 1 - y = -expm1 only where a Bose form needs it
-          const double xv = x[fbase[4 * b]];
-          const double nt = -beta * fabs(xv);
-          const double y = exp(nt);
-          const double em = fbase[4 * b + 3] ? expm1(nt) : 0.0;
-          int cur_sigma = 0;
-          double g = 0.0, hh = 0.0;
-          for (int v = fbase[4 * b + 1]; v < fbase[4 * b + 2]; ++v) {
-            const int sigma = fvr[4 * v], sign = fvr[4 * v + 1], k = fvr[4 * v + 2];
-            if (sigma != cur_sigma) {
-              cur_sigma = sigma;
-              const double rD = rcp(sigma > 0 ? 1.0 + y : -em);
-              const double t2 = (sigma > 0 ? y : -y) * rD;
-              if (xv <= 0.0) { g = rD; hh = t2; } else { g = t2; hh = rD; }
-            }
-            fv[v] = sign > 0 ? fermi_poly(k, g, hh, beta) : fermi_poly(k, hh, g, beta);
-          }
-        }
-        double rr[kMaxRealDens];
-        for (int i = 0; i < H.n_rden; ++i) rr[i] = rcp(x[rden[2 * i]]);
-        int cur = g1_tgt[0];
-        double wacc = 0.0;
-        for (int gi = 0; gi < H.n_g1; ++gi) {
-          const int tg = g1_tgt[gi];
-          if (tg != cur) { W[cur * kBlock + tid] = wacc; wacc = 0.0; cur = tg; }
-          double ft = 0.0;
-          for (int t = g1[4 * gi]; t < g1[4 * gi + 1]; ++t) {
-            double p = term_A[t];
-            const int f0 = term[t], f1 = term[t + 1];
-            for (int q = f0; q < f1 - 1; ++q) p *= fv[tfac[q]];
-            ft = fma(p, fv[tfac[f1 - 1]], ft);
-          }
-          for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
-            const double r = rr[g1rd[2 * q]];
-            for (int pw = g1rd[2 * q + 1]; pw > 0; --pw) ft *= r;
-          }
-          wacc += ft;
-        }
-        W[cur * kBlock + tid] = wacc;
-        for (int c = 0; c < H.n_cden; ++c) {
-          const double xv = x[cden[2 * c]];
-          CB[c * kBlock + tid] = cden[2 * c + 1] > 0 ? xv : -xv;
-        }
-      }
-    }
-    __syncthreads();
-    // ---------------------------------------------------------------- phase 2
-    for (int fi = 0; fi < my_nf; ++fi) {
-      const int f = my_f0 + fi * my_fstep;
-      const double Xr = Xs[2 * f], Xi = Xs[2 * f + 1];
-      for (int sl = my_s0; sl < kBlock; sl += my_sstep) {
-        const long long s = s0 + sl;
-        if (s >= P.n) break;
-        double rc_re[kMaxCplxDens], rc_im[kMaxCplxDens];
-        for (int c = 0; c < H.n_cden; ++c) {
-          const double a = cden_a[c];
-          const double Dr = fma(a, Xr, CB[c * kBlock + sl]);
-          const double Di = a * Xi;
-          const double r = rcp(fma(Dr, Dr, Di * Di));
-          rc_re[c] = Dr * r;
-          rc_im[c] = -Di * r;
-        }
-        double vr = 0.0, vi = 0.0;
-        for (int hg = 0; hg < H.n_g2; ++hg) {
-          const double w = W[hg * kBlock + sl];
-          const int q0 = g2[hg], q1 = g2[hg + 1];
-          if (q0 == q1) { vr += w; continue; }
-          double Rr = 1.0, Ri = 0.0;
-          bool first = true;
-          for (int q = q0; q < q1; ++q) {
-            const int c = g2cd[2 * q];
-            const double ar = rc_re[c], ai = rc_im[c];
-            for (int pw = g2cd[2 * q + 1]; pw > 0; --pw) {
-              if (first) { Rr = ar; Ri = ai; first = false; }
-              else {
-                const double nr = fma(Rr, ar, -Ri * ai);
-                Ri = fma(Rr, ai, Ri * ar);
-                Rr = nr;
-              }
-            }
-          }
-          vr = fma(w, Rr, vr);
-          vi = fma(w, Ri, vi);
-        }
-        if (P.per_sample) {
-          double2* o = reinterpret_cast<double2*>(P.per_sample) + (size_t)f * P.n + s;
-          *o = make_double2(vr, vi);
-        }
-        acc[fi][0] += vr;
-        acc[fi][1] += vi;
-        acc[fi][2] = fma(vr, vr, acc[fi][2]);
-        acc[fi][3] = fma(vi, vi, acc[fi][3]);
-      }
-    }
-    __syncthreads();
-  }
-  // ------------------------------------------------------------------ block reduction
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x)
+    fwd_tile<ENERGY_IN>(H, T, A, tile, Xs, CB, W, M, acc);
   if (!P.partial) return;
-  if (n_f <= kBlock) {
-    for (int k = 0; k < 4; ++k) {
-      red[k * kBlock + tid] = acc[0][k];
-    }
-    __syncthreads();
-    if (tid < n_f) {
-      double* out = P.partial + ((size_t)blockIdx.x * n_f + tid) * 4;
-      for (int k = 0; k < 4; ++k) {
-        double s = 0.0;
-        for (int j = 0; j < tpf; ++j) s += red[k * kBlock + tid * tpf + j];
-        out[k] = s;
-      }
-    }
-  } else {
-    for (int fi = 0; fi < my_nf; ++fi) {
-      const int f = my_f0 + fi * my_fstep;
-      double* out = P.partial + ((size_t)blockIdx.x * n_f + f) * 4;
-      for (int k = 0; k < 4; ++k) out[k] = acc[fi][k];
-    }
-  }
+  block_reduce_store(M, P.n_f, acc, red, P.partial + (size_t)blockIdx.x * P.n_f * 4);
 }
 
 // mean and unbiased variances from per-block partials, summed in block order

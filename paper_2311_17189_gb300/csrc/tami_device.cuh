@@ -110,37 +110,56 @@ __device__ __forceinline__ double fermi_poly(int k, double g, double h, double b
 
 __host__ __device__ __forceinline__ int align16(int b) { return (b + 15) & ~15; }
 
-__device__ __forceinline__ bool stage_table(unsigned char* dst, const unsigned char* src, int bytes, int* status) {
-  __shared__ __align__(8) unsigned long long bar;
-  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+
+// Bulk copy (TMA, cp.async.bulk) of `bytes` (multiple of 16, both addresses 16-byte aligned)
+// into shared memory, completed on the mbarrier `bar` (initialised once with count 1 by
+// mbar_init).  `parity` is the phase being completed: 0 for the first use, then alternating.
+// The caller must __syncthreads() before a re-fill so that no thread still reads the old data.
+// Every wait is bounded; on timeout the status word is set and the copy is waited for again.
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
   if (threadIdx.x == 0) {
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncthreads();
+}
+
+__device__ __forceinline__ bool bulk_stage(unsigned char* dst, const unsigned char* src, int bytes,
+                                           unsigned long long* bar, uint32_t parity, int* status) {
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
   if (threadIdx.x == 0) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    // order this block's earlier generic-proxy reads of dst before the async-proxy writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
     asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(d), "l"(src), "r"(bytes), "r"(b) : "memory");
   }
   uint32_t done = 0;
-  long long it = 0;
-  for (; it < kSpinLimit && !done; ++it) {
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(done) : "r"(b) : "memory");
+  for (long long it = 0; it < kSpinLimit && !done; ++it) {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(b), "r"(parity) : "memory");
     if (!done && it > 64) __nanosleep(64);
   }
   if (!done) {
     if (status) atomicExch(status, TAMI_ETIMEOUT);
-    // the copy is still owned by this block: wait for it once more (bounded) before leaving
     for (long long j = 0; j < kSpinLimit && !done; ++j) {
-      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-                   : "=r"(done) : "r"(b) : "memory");
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                   : "=r"(done) : "r"(b), "r"(parity) : "memory");
       __nanosleep(256);
     }
   }
   return done != 0;
+}
+
+__device__ __forceinline__ bool stage_table(unsigned char* dst, const unsigned char* src, int bytes, int* status) {
+  // one-shot staging: init the barrier, copy, wait on phase 0
+  __shared__ __align__(8) unsigned long long bar;
+  mbar_init(&bar);
+  __syncthreads();
+  const bool ok = bulk_stage(dst, src, bytes, &bar, 0u, status);
+  // the decision to go on must be the same in every thread of the block
+  return !__syncthreads_or(!ok);
 }
 
 // ------------------------------------------------------------------------------- host helpers

@@ -1,0 +1,259 @@
+// One tile of the forward evaluation (phase 1 + phase 2) and the fixed-order block reduction,
+// shared by the single-diagram kernel (tami_cuda.cu) and the persistent multi-diagram kernel
+// (tami_batch.cu).  Internal to the library.
+#pragma once
+
+#include "tami_device.cuh"
+
+namespace tami {
+namespace dev {
+
+constexpr int kMaxFreqPerThread = 16;  // n_f <= kMaxFreqPerThread * kBlock
+
+// typed views of a staged term table
+struct TableView {
+  const double* alpha;
+  const int* repl;
+  const int* combo_ptr;
+  const int* combo_j;
+  const double* combo_c;
+  const int* fbase;
+  const int* fvr;
+  const int* rden;
+  const int* cden;
+  const double* cden_a;
+  const int* g1;
+  const int* g1_tgt;
+  const int* term;
+  const double* term_A;
+  const int* tfac;
+  const int* g1rd;
+  const int* g2;
+  const int* g2cd;
+};
+
+__device__ __forceinline__ TableView table_view(const unsigned char* t, const TableHeader& H) {
+  TableView v;
+  v.alpha = reinterpret_cast<const double*>(t + H.off_alpha);
+  v.repl = reinterpret_cast<const int*>(t + H.off_repl);
+  v.combo_ptr = reinterpret_cast<const int*>(t + H.off_combo_ptr);
+  v.combo_j = reinterpret_cast<const int*>(t + H.off_combo_j);
+  v.combo_c = reinterpret_cast<const double*>(t + H.off_combo_c);
+  v.fbase = reinterpret_cast<const int*>(t + H.off_fbase);
+  v.fvr = reinterpret_cast<const int*>(t + H.off_fv);
+  v.rden = reinterpret_cast<const int*>(t + H.off_rden);
+  v.cden = reinterpret_cast<const int*>(t + H.off_cden);
+  v.cden_a = reinterpret_cast<const double*>(t + H.off_cden_a);
+  v.g1 = reinterpret_cast<const int*>(t + H.off_g1);
+  v.g1_tgt = reinterpret_cast<const int*>(t + H.off_g1_tgt);
+  v.term = reinterpret_cast<const int*>(t + H.off_term);
+  v.term_A = reinterpret_cast<const double*>(t + H.off_term_A);
+  v.tfac = reinterpret_cast<const int*>(t + H.off_tfac);
+  v.g1rd = reinterpret_cast<const int*>(t + H.off_g1rd);
+  v.g2 = reinterpret_cast<const int*>(t + H.off_g2);
+  v.g2cd = reinterpret_cast<const int*>(t + H.off_g2cd);
+  return v;
+}
+
+// Phase-2 assignment of (frequency, sample) pairs: tpf threads per frequency when n_f <= block,
+// else several frequencies per thread over all samples of the tile.
+struct FreqMap {
+  int tpf, f0, fstep, nf, s0, sstep;
+};
+
+__device__ __forceinline__ FreqMap freq_map(int n_f, int tid) {
+  FreqMap m;
+  if (n_f <= kBlock) {
+    m.tpf = kBlock / n_f;
+    m.f0 = tid / m.tpf;
+    m.fstep = 1;
+    m.nf = m.f0 < n_f ? 1 : 0;
+    m.s0 = tid % m.tpf;
+    m.sstep = m.tpf;
+  } else {
+    m.tpf = 1;
+    m.f0 = tid;
+    m.fstep = kBlock;
+    m.nf = (n_f - tid + kBlock - 1) / kBlock;
+    m.s0 = 0;
+    m.sstep = 1;
+  }
+  return m;
+}
+
+struct TileArgs {
+  double t, tp, mu, kx, ky, beta;
+  unsigned long long seed, offset;  // sample s of the tile stream is Philox counter offset + s
+  long long n;                      // samples in the stream
+  const double* E_in;               // energy input [n][N] or null
+  double* per_sample;               // [n_f][n][2] or null
+  int n_f;
+};
+
+// Shared memory per tile: X [n_f][2] (filled by the caller), CB [n_cden][kBlock], W [n_g2][kBlock].
+template <bool ENERGY_IN>
+__device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& T, const TileArgs& A,
+                                         long long tile, const double* Xs, double* CB, double* W,
+                                         const FreqMap& M, double (*acc)[4]) {
+  const int tid = threadIdx.x;
+  const long long s0 = tile * kBlock;
+  const double beta = A.beta;
+  // ---------------------------------------------------------------- phase 1 (thread = sample)
+  {
+    const long long s = s0 + tid;
+    if (s < A.n) {
+      double E[kMaxLines];
+      if (ENERGY_IN) {
+        for (int r = 0; r < H.n_rep; ++r) E[T.repl[r]] = A.E_in[s * H.N + T.repl[r]];
+      } else {
+        double kx[kMaxVars], ky[kMaxVars];
+        const unsigned long long sg = A.offset + (unsigned long long)s;
+        for (int l = 0; l < H.m; ++l) {
+          uint32_t c[4] = {(uint32_t)sg, (uint32_t)(sg >> 32), (uint32_t)l, 0u};
+          philox4x32_10(c, (uint32_t)A.seed, (uint32_t)(A.seed >> 32));
+          kx[l] = to_momentum(c[0], c[1]);
+          ky[l] = to_momentum(c[2], c[3]);
+        }
+        kx[H.m] = A.kx;
+        ky[H.m] = A.ky;
+        for (int r = 0; r < H.n_rep; ++r) {
+          const int j = T.repl[r];
+          double ax = 0.0, ay = 0.0;
+          for (int l = 0; l < H.nv; ++l) {
+            const double cf = T.alpha[j * H.nv + l];
+            if (cf != 0.0) { ax = fma(cf, kx[l], ax); ay = fma(cf, ky[l], ay); }
+          }
+          E[j] = line_energy(ax, ay, A.t, A.tp, A.mu);
+        }
+      }
+      double x[kMaxCombos];
+      for (int u = 0; u < H.n_combo; ++u) {
+        double v = 0.0;
+        for (int q = T.combo_ptr[u]; q < T.combo_ptr[u + 1]; ++q) v = fma(T.combo_c[q], E[T.combo_j[q]], v);
+        x[u] = v;
+      }
+      double fv[kMaxFermiValues];
+      for (int b = 0; b < H.n_fbase; ++b) {
+        // y = e^{-beta|x|} keeps the tails exact; 1 - y = -expm1 only where a Bose form needs it
+        const double xv = x[T.fbase[4 * b]];
+        const double nt = -beta * fabs(xv);
+        const double y = exp(nt);
+        const double em = T.fbase[4 * b + 3] ? expm1(nt) : 0.0;
+        int cur_sigma = 0;
+        double g = 0.0, hh = 0.0;
+        for (int v = T.fbase[4 * b + 1]; v < T.fbase[4 * b + 2]; ++v) {
+          const int sigma = T.fvr[4 * v], sign = T.fvr[4 * v + 1], k = T.fvr[4 * v + 2];
+          if (sigma != cur_sigma) {
+            cur_sigma = sigma;
+            const double rD = rcp(sigma > 0 ? 1.0 + y : -em);
+            const double t2 = (sigma > 0 ? y : -y) * rD;
+            if (xv <= 0.0) { g = rD; hh = t2; } else { g = t2; hh = rD; }
+          }
+          fv[v] = sign > 0 ? fermi_poly(k, g, hh, beta) : fermi_poly(k, hh, g, beta);
+        }
+      }
+      double rr[kMaxRealDens];
+      for (int i = 0; i < H.n_rden; ++i) rr[i] = rcp(x[T.rden[2 * i]]);
+      int cur = T.g1_tgt[0];
+      double wacc = 0.0;
+      for (int gi = 0; gi < H.n_g1; ++gi) {
+        const int tg = T.g1_tgt[gi];
+        if (tg != cur) { W[cur * kBlock + tid] = wacc; wacc = 0.0; cur = tg; }
+        double ft = 0.0;
+        for (int t = T.g1[4 * gi]; t < T.g1[4 * gi + 1]; ++t) {
+          double p = T.term_A[t];
+          const int f0 = T.term[t], f1 = T.term[t + 1];
+          for (int q = f0; q < f1 - 1; ++q) p *= fv[T.tfac[q]];
+          ft = fma(p, fv[T.tfac[f1 - 1]], ft);
+        }
+        for (int q = T.g1[4 * gi + 2]; q < T.g1[4 * gi + 3]; ++q) {
+          const double r = rr[T.g1rd[2 * q]];
+          for (int pw = T.g1rd[2 * q + 1]; pw > 0; --pw) ft *= r;
+        }
+        wacc += ft;
+      }
+      W[cur * kBlock + tid] = wacc;
+      for (int c = 0; c < H.n_cden; ++c) {
+        const double xv = x[T.cden[2 * c]];
+        CB[c * kBlock + tid] = T.cden[2 * c + 1] > 0 ? xv : -xv;
+      }
+    }
+  }
+  __syncthreads();
+  // ---------------------------------------------------------------- phase 2 ((f, s) pairs)
+  for (int fi = 0; fi < M.nf; ++fi) {
+    const int f = M.f0 + fi * M.fstep;
+    const double Xr = Xs[2 * f], Xi = Xs[2 * f + 1];
+    for (int sl = M.s0; sl < kBlock; sl += M.sstep) {
+      const long long s = s0 + sl;
+      if (s >= A.n) break;
+      double rc_re[kMaxCplxDens], rc_im[kMaxCplxDens];
+      for (int c = 0; c < H.n_cden; ++c) {
+        const double a = T.cden_a[c];
+        const double Dr = fma(a, Xr, CB[c * kBlock + sl]);
+        const double Di = a * Xi;
+        const double r = rcp(fma(Dr, Dr, Di * Di));
+        rc_re[c] = Dr * r;
+        rc_im[c] = -Di * r;
+      }
+      double vr = 0.0, vi = 0.0;
+      for (int hg = 0; hg < H.n_g2; ++hg) {
+        const double w = W[hg * kBlock + sl];
+        const int q0 = T.g2[hg], q1 = T.g2[hg + 1];
+        if (q0 == q1) { vr += w; continue; }
+        double Rr = 1.0, Ri = 0.0;
+        bool first = true;
+        for (int q = q0; q < q1; ++q) {
+          const int c = T.g2cd[2 * q];
+          const double ar = rc_re[c], ai = rc_im[c];
+          for (int pw = T.g2cd[2 * q + 1]; pw > 0; --pw) {
+            if (first) { Rr = ar; Ri = ai; first = false; }
+            else {
+              const double nr = fma(Rr, ar, -Ri * ai);
+              Ri = fma(Rr, ai, Ri * ar);
+              Rr = nr;
+            }
+          }
+        }
+        vr = fma(w, Rr, vr);
+        vi = fma(w, Ri, vi);
+      }
+      if (A.per_sample) {
+        double2* o = reinterpret_cast<double2*>(A.per_sample) + (size_t)f * A.n + s;
+        *o = make_double2(vr, vi);
+      }
+      acc[fi][0] += vr;
+      acc[fi][1] += vi;
+      acc[fi][2] = fma(vr, vr, acc[fi][2]);
+      acc[fi][3] = fma(vi, vi, acc[fi][3]);
+    }
+  }
+  __syncthreads();
+}
+
+// Sum the per-thread accumulators of the block in a fixed order into out[n_f][4].
+// red: 4 * kBlock doubles of shared memory.  Ends with a barrier.
+__device__ __forceinline__ void block_reduce_store(const FreqMap& M, int n_f, double (*acc)[4], double* red,
+                                                   double* out) {
+  const int tid = threadIdx.x;
+  if (n_f <= kBlock) {
+    for (int k = 0; k < 4; ++k) red[k * kBlock + tid] = acc[0][k];
+    __syncthreads();
+    if (tid < n_f) {
+      for (int k = 0; k < 4; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < M.tpf; ++j) s += red[k * kBlock + tid * M.tpf + j];
+        out[tid * 4 + k] = s;
+      }
+    }
+  } else {
+    for (int fi = 0; fi < M.nf; ++fi) {
+      const int f = M.f0 + fi * M.fstep;
+      for (int k = 0; k < 4; ++k) out[f * 4 + k] = acc[fi][k];
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace dev
+}  // namespace tami

@@ -1,0 +1,132 @@
+"""GPU tests of the persistent multi-diagram launch (tami_batch_*): every diagram's mean and
+variance against the CPU oracle, against separate tami_forward launches on the same samples,
+determinism of a plan, the autotuner and its cache, and the full all-orders workload."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+import paper_2311_17189_gb300 as T
+from paper_2311_17189_gb300 import _lib as L
+from paper_2311_17189_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def mixed_batch():
+    """Diagrams of orders 2..5 with uneven sample counts (a single sample, ragged tails)."""
+    picks = [(2, 0), (3, 1), (4, 2), (4, 7), (5, 3), (5, 40)]
+    counts = [1, 3 * 128 + 37, 5000, 129, 2000, 700]
+    ds = [O.enumerate_sigma(m)[i] for m, i in picks]
+    lib = [T.Diagram(d["alpha"], eps=d["eps"], prefactor=(-1.0) ** m * (-1.0) ** d["loops"])
+           for d, (m, _) in zip(ds, picks)]
+    orc = [O.Solution(d["alpha"], eps=d["eps"], prefactor=(-1.0) ** m * (-1.0) ** d["loops"])
+           for d, (m, _) in zip(ds, picks)]
+    seeds = [W.SEED + k for k in range(len(ds))]
+    return lib, orc, counts, seeds
+
+
+LAT = (1.0, -0.2, 0.1, np.pi / 2, np.pi / 3)
+BETA = 5.0
+
+
+@pytest.mark.parametrize("chunk", [1, 3])
+def test_batch_against_oracle(chunk):
+    lib, orc, counts, seeds = mixed_batch()
+    X = W.matsubara(BETA, 5)
+    B = T.Batch(lib, counts, seeds, len(X), chunk_tiles=chunk)
+    assert B.info()["chunk_tiles"] == chunk
+    mean, var = B.launch(LAT, X, BETA)
+    torch.cuda.synchronize()
+    mean, var = mean.cpu().numpy(), var.cpu().numpy()
+    for d, (S, n, sd) in enumerate(zip(orc, counts, seeds)):
+        ref = S.eval_momenta(LAT, sd, 0, n, X, BETA, per_sample=True, threads=8)
+        scale = np.mean(ref["envelope"], axis=1) + np.mean(np.abs(ref["values"]), axis=1)
+        assert np.all(np.abs(mean[d] - ref["mean"]) <= RTOL * scale), d
+        dev = ref["values"] - ref["mean"][:, None]
+        for part, k in ((np.real, 0), (np.imag, 1)):
+            tol = 2.0 / max(n - 1, 1) * np.sum(np.abs(part(dev)) * RTOL * ref["envelope"], axis=1) \
+                + 1e-10 * ref["var"][:, k]
+            assert np.all(np.abs(var[d][:, k] - ref["var"][:, k]) <= tol), d
+
+
+def test_batch_matches_single_launches_and_is_deterministic():
+    lib, orc, counts, seeds = mixed_batch()
+    X = W.real_axis(-2.0, 2.0, 40, 0.1)
+    for D in lib:
+        D.upload(0)
+    B = T.Batch(lib, counts, seeds, len(X), chunk_tiles=2)
+    m1, v1 = B.launch(LAT, X, BETA)
+    m2, v2 = B.launch(LAT, X, BETA)
+    torch.cuda.synchronize()
+    assert torch.equal(m1, m2) and torch.equal(v1, v2)
+    for d, D in enumerate(lib):
+        m, v, ps = D.forward(LAT, seeds[d], 0, counts[d], X, BETA, per_sample=True)
+        scale = ps.abs().mean(dim=1)
+        assert torch.all((m1[d] - m).abs() <= 1e-13 * scale)
+
+
+def test_autotune_and_cache(tmp_path, monkeypatch):
+    monkeypatch.setenv("TAMI_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    lib, orc, counts, seeds = mixed_batch()
+    counts = [c * 40 for c in counts]
+    X = W.matsubara(BETA, 8)
+    B1 = T.Batch(lib, counts, seeds, len(X), chunk_tiles=0)
+    i1 = B1.info()
+    assert i1["chunk_tiles"] >= 1 and i1["items"] >= 1 and i1["grid"] >= 1
+    text = (tmp_path / "tune.txt").read_text()
+    assert len(text.strip().splitlines()) == 1
+    B2 = T.Batch(lib, counts, seeds, len(X), chunk_tiles=0)          # cache hit: no new line
+    assert B2.info()["chunk_tiles"] == i1["chunk_tiles"]
+    assert (tmp_path / "tune.txt").read_text() == text
+    m1, _ = B1.launch(LAT, X, BETA)
+    m2, _ = B2.launch(LAT, X, BETA)
+    assert torch.equal(m1, m2)
+
+
+def test_batch_rejects_bad_arguments():
+    lib, orc, counts, seeds = mixed_batch()
+    with pytest.raises(L.TamiError):
+        T.Batch(lib, counts, seeds, 0)
+    with pytest.raises(L.TamiError):
+        T.Batch(lib, [0] + counts[1:], seeds, 4)
+
+
+def test_all_orders_workload_full_size():
+    """Every Hubbard self-energy diagram of orders 2..5 (85 diagrams), diagram d with
+    2^(20 + d mod 4) samples and seed 20231128 + d, 32 Matsubara frequencies, beta = 5, in one
+    persistent launch; each diagram's mean against a separate tami_forward launch over the same
+    samples (the two differ only in how partial sums are grouped)."""
+    c = W.ALL_ORDERS
+    diags, lib = [], []
+    for m in c["orders"]:
+        for d in T.enumerate_sigma(m):
+            lib.append(T.Diagram(d["alpha"], eps=d["eps"], prefactor=(-1.0) ** m * (-1.0) ** d["loops"]))
+    n_d = len(lib)
+    assert n_d == 85
+    counts = [W.all_orders_samples(d) for d in range(n_d)]
+    seeds = [c["seed"] + d for d in range(n_d)]
+    X = W.matsubara(c["beta"], c["n_freq"])
+    lat = W.lattice(c)
+    B = T.Batch(lib, counts, seeds, len(X), chunk_tiles=16)
+    mean, var = B.launch(lat, X, c["beta"])
+    torch.cuda.synchronize()
+    assert torch.isfinite(torch.view_as_real(mean)).all()
+    for d, D in enumerate(lib):
+        D.upload(0)
+        m, v, _ = D.forward(lat, seeds[d], 0, counts[d], X, c["beta"])
+        rms = torch.sqrt(v.sum(dim=1) + m.abs() ** 2)
+        assert torch.all((mean[d] - m).abs() <= 1e-12 * rms), d
+        assert torch.allclose(var[d], v, rtol=1e-9, atol=0)
