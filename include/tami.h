@@ -101,6 +101,26 @@ int tami_construct(int n_lines, int n_vars, const int8_t* alpha, const int8_t* e
                    const uint8_t* var_is_boson, const int32_t* order, double prefactor,
                    tami_diagram** out);
 
+/* Momentum labels of a self-energy graph (Sec. 2.5: label_graph and graph_to_R0 on the 4-column
+ * "source target B/F spin" format).
+ *   edges  host int32 [n_edges][4]: source vertex, target vertex, 1 = fermionic / 0 = bosonic,
+ *          spin (carried, unused).  Fermionic lines are directed along the particle flow; bosonic
+ *          lines are instantaneous interactions (no propagator).  One vertex (the external one)
+ *          has one outgoing and one incoming fermionic line -- the amputated external legs -- and
+ *          no bosonic line; every other vertex has one fermionic line in, one out and one bosonic.
+ *   Outputs: the internal fermionic lines, in file order, are the n_lines rows: alpha int8
+ *   [n_lines][n_vars] (loop variables on the non-tree lines of a breadth-first spanning tree from
+ *   the node the incoming leg enters, external last), eps int8 [n_lines][n_lines] (equal labels
+ *   share an energy), row_line int32 [n_lines] (input line of each row), loops = closed fermion
+ *   loops F.  With capacity_lines < n_lines only the sizes are written.
+ * Errors: TAMI_EINVAL for a malformed or disconnected graph, TAMI_EUNSUPPORTED beyond 16 lines,
+ * 7 loops or labels outside {-1,0,1}. */
+int tami_label_graph(const int32_t* edges, int n_edges, int capacity_lines, int8_t* alpha, int8_t* eps,
+                     int32_t* row_line, int* n_lines, int* n_vars, int* loops);
+
+/* tami_label_graph followed by tami_construct (all variables fermionic, summed in label order). */
+int tami_construct_from_graph(const int32_t* edges, int n_edges, double prefactor, tami_diagram** out);
+
 int tami_diagram_info(const tami_diagram* d, tami_info* info);
 
 /* Copy the flattened term table to `device` (cudaMalloc + cudaMemcpyAsync on `stream`).

@@ -10,5 +10,6 @@ step is a libtami CUDA kernel.  `workloads` holds the seeded synthetic inputs.
 """
 from . import _lib, mc
 from .api import Batch, Diagram, enumerate_sigma
+from . import graph
 
-__all__ = ["Batch", "Diagram", "enumerate_sigma", "_lib", "mc"]
+__all__ = ["Batch", "Diagram", "enumerate_sigma", "graph", "_lib", "mc"]

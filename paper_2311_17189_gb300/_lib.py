@@ -16,7 +16,7 @@ TAMI_OK, TAMI_EINVAL, TAMI_ENOMEM, TAMI_ECUDA, TAMI_ETIMEOUT, TAMI_EUNSUPPORTED 
 
 # functions declared in include/tami.h (checked by tests/test_lib_host.py)
 EXPORTS = [
-    "tami_last_error", "tami_construct", "tami_diagram_info", "tami_upload", "tami_sample_energies",
+    "tami_last_error", "tami_construct", "tami_label_graph", "tami_construct_from_graph", "tami_diagram_info", "tami_upload", "tami_sample_energies",
     "tami_eval_energies", "tami_forward_workspace", "tami_forward", "tami_forward_noalloc",
     "tami_backward_workspace", "tami_backward", "tami_batch_plan", "tami_batch_info", "tami_batch_launch",
     "tami_batch_destroy",
@@ -63,6 +63,9 @@ def lib():
     vp, i64, u64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
     L.tami_last_error.restype = ctypes.c_char_p
     L.tami_construct.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, ctypes.c_double, ctypes.POINTER(vp)]
+    L.tami_label_graph.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.tami_construct_from_graph.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(vp)]
     L.tami_diagram_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.tami_upload.argtypes = [vp, ctypes.c_int, vp]
     L.tami_sample_energies.argtypes = [vp, ctypes.POINTER(Lattice), u64, u64, i64, dp, vp]
