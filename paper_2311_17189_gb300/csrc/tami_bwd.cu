@@ -27,7 +27,7 @@ using namespace dev;
 
 // per-thread capacities of the adjoint (checked before launch)
 constexpr int kBwCombos = 64, kBwFv = 128, kBwRden = 32, kBwCden = 32, kBwG1 = 128, kBwG2 = 64;
-constexpr int kBwFreq = 256, kBwFac = 8;
+constexpr int kBwFreq = 256, kBwCloses = 512;
 
 struct BwdParams {
   TableHeader h;
@@ -72,9 +72,8 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
   const double* cden_a = reinterpret_cast<const double*>(smem + H.off_cden_a);
   const int* g1 = reinterpret_cast<const int*>(smem + H.off_g1);
   const int* g1_tgt = reinterpret_cast<const int*>(smem + H.off_g1_tgt);
-  const int* term = reinterpret_cast<const int*>(smem + H.off_term);
-  const double* term_A = reinterpret_cast<const double*>(smem + H.off_term_A);
-  const int* tfac = reinterpret_cast<const int*>(smem + H.off_tfac);
+  const int2* ops = reinterpret_cast<const int2*>(smem + H.off_ops);
+  const double* leafA = reinterpret_cast<const double*>(smem + H.off_leafA);
   const int* g1rd = reinterpret_cast<const int*>(smem + H.off_g1rd);
   const int* g2 = reinterpret_cast<const int*>(smem + H.off_g2);
   const int* g2cd = reinterpret_cast<const int*>(smem + H.off_g2cd);
@@ -146,12 +145,18 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
     double W1[kBwG1], W2[kBwG2];
     for (int h = 0; h < H.n_g2; ++h) W2[h] = 0.0;
     for (int gi = 0; gi < H.n_g1; ++gi) {
-      double ft = 0.0;
-      for (int t = g1[4 * gi]; t < g1[4 * gi + 1]; ++t) {
-        double p = term_A[t];
-        const int f0 = term[t], f1 = term[t + 1];
-        for (int q = f0; q < f1 - 1; ++q) p *= fv[tfac[q]];
-        ft = fma(p, fv[tfac[f1 - 1]], ft);
+      double ft;
+      {
+        double acc[kMaxDepth + 1];
+        acc[0] = 0.0;
+        for (int o = g1[4 * gi]; o < g1[4 * gi + 1]; ++o) {
+          const int2 op = ops[o];
+          const int kind = op.x & 3, dd = (op.x >> 2) & 63;
+          if (kind == kOpOpen) acc[dd] = 0.0;
+          else if (kind == kOpClose) acc[dd - 1] = fma(fv[op.y], acc[dd], acc[dd - 1]);
+          else acc[dd - 1] = fma(fv[op.y], leafA[op.x >> 8], acc[dd - 1]);
+        }
+        ft = acc[0];
       }
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
         const double r = rr[g1rd[2 * q]];
@@ -241,16 +246,34 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
         xbar[rden[2 * i]] -= wb * W1[gi] * (double)pw * rr[i];
       }
       const double ftbar = wb * RR;
-      for (int t = g1[4 * gi]; t < g1[4 * gi + 1]; ++t) {
-        const int f0 = term[t], nfac = term[t + 1] - f0;
-        double pre[kBwFac];
-        pre[0] = term_A[t];
-        for (int i = 1; i < nfac; ++i) pre[i] = pre[i - 1] * fv[tfac[f0 + i - 1]];
-        double suf = ftbar;
-        for (int i = nfac - 1; i >= 0; --i) {
-          const int v = tfac[f0 + i];
-          fvbar[v] = fma(pre[i], suf, fvbar[v]);
-          suf *= fv[v];
+      // pole tree, reverse: recompute each inner node's subtree value (cv), then walk the program
+      // backwards: CLOSE(d,F): Fbar += acc[d] accbar[d-1], accbar[d] = F accbar[d-1];
+      // LEAFCLOSE(d,F,A): Fbar += A accbar[d-1]
+      const int o0 = g1[4 * gi], o1 = g1[4 * gi + 1];
+      double cv[kBwCloses];
+      {
+        double acc[kMaxDepth + 1];
+        acc[0] = 0.0;
+        int nc = 0;
+        for (int o = o0; o < o1; ++o) {
+          const int2 op = ops[o];
+          const int kind = op.x & 3, dd = (op.x >> 2) & 63;
+          if (kind == kOpOpen) acc[dd] = 0.0;
+          else if (kind == kOpClose) { cv[nc++] = acc[dd]; acc[dd - 1] = fma(fv[op.y], acc[dd], acc[dd - 1]); }
+          else acc[dd - 1] = fma(fv[op.y], leafA[op.x >> 8], acc[dd - 1]);
+        }
+        double bar[kMaxDepth + 1];
+        bar[0] = ftbar;
+        for (int o = o1 - 1; o >= o0; --o) {
+          const int2 op = ops[o];
+          const int kind = op.x & 3, dd = (op.x >> 2) & 63;
+          if (kind == kOpClose) {
+            const double pb = bar[dd - 1];
+            fvbar[op.y] = fma(cv[--nc], pb, fvbar[op.y]);
+            bar[dd] = fv[op.y] * pb;
+          } else if (kind == kOpLeafClose) {
+            fvbar[op.y] = fma(leafA[op.x >> 8], bar[dd - 1], fvbar[op.y]);
+          }
         }
       }
     }
@@ -353,11 +376,9 @@ int bwd_check(const tami_diagram* d, int n_f) {
   cudaGetDevice(&cur);
   if (cur != d->device) { set_error("current device differs from the upload device"); return TAMI_EINVAL; }
   const TableHeader& h = d->hdr;
-  int max_fac = 0;
-  for (const SymTerm& t : d->terms) max_fac = std::max(max_fac, (int)t.F.size());
   if (h.max_der > 4) { set_error("the adjoint needs derivative orders up to 4"); return TAMI_EUNSUPPORTED; }
   if (h.n_combo > kBwCombos || h.n_fv > kBwFv || h.n_rden > kBwRden || h.n_cden > kBwCden ||
-      h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || max_fac > kBwFac) {
+      h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || h.max_closes > kBwCloses) {
     set_error("term table exceeds the adjoint kernel's per-sample capacities");
     return TAMI_EUNSUPPORTED;
   }

@@ -24,9 +24,8 @@ struct TableView {
   const double* cden_a;
   const int* g1;
   const int* g1_tgt;
-  const int* term;
-  const double* term_A;
-  const int* tfac;
+  const int2* ops;
+  const double* leafA;
   const int* g1rd;
   const int* g2;
   const int* g2cd;
@@ -46,13 +45,26 @@ __device__ __forceinline__ TableView table_view(const unsigned char* t, const Ta
   v.cden_a = reinterpret_cast<const double*>(t + H.off_cden_a);
   v.g1 = reinterpret_cast<const int*>(t + H.off_g1);
   v.g1_tgt = reinterpret_cast<const int*>(t + H.off_g1_tgt);
-  v.term = reinterpret_cast<const int*>(t + H.off_term);
-  v.term_A = reinterpret_cast<const double*>(t + H.off_term_A);
-  v.tfac = reinterpret_cast<const int*>(t + H.off_tfac);
+  v.ops = reinterpret_cast<const int2*>(t + H.off_ops);
+  v.leafA = reinterpret_cast<const double*>(t + H.off_leafA);
   v.g1rd = reinterpret_cast<const int*>(t + H.off_g1rd);
   v.g2 = reinterpret_cast<const int*>(t + H.off_g2);
   v.g2cd = reinterpret_cast<const int*>(t + H.off_g2cd);
   return v;
+}
+
+// Sum over a group's terms of A_t prod FT factors, by the group's pole-tree program.
+__device__ __forceinline__ double pole_tree(const TableView& T, int op0, int op1, const double* fv) {
+  double acc[kMaxDepth + 1];
+  acc[0] = 0.0;
+  for (int o = op0; o < op1; ++o) {
+    const int2 op = T.ops[o];
+    const int kind = op.x & 3, d = (op.x >> 2) & 63;
+    if (kind == kOpOpen) acc[d] = 0.0;
+    else if (kind == kOpClose) acc[d - 1] = fma(fv[op.y], acc[d], acc[d - 1]);
+    else acc[d - 1] = fma(fv[op.y], T.leafA[op.x >> 8], acc[d - 1]);
+  }
+  return acc[0];
 }
 
 // Phase-2 assignment of (frequency, sample) pairs: tpf threads per frequency when n_f <= block,
@@ -159,13 +171,7 @@ __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& 
       for (int gi = 0; gi < H.n_g1; ++gi) {
         const int tg = T.g1_tgt[gi];
         if (tg != cur) { W[cur * kBlock + tid] = wacc; wacc = 0.0; cur = tg; }
-        double ft = 0.0;
-        for (int t = T.g1[4 * gi]; t < T.g1[4 * gi + 1]; ++t) {
-          double p = T.term_A[t];
-          const int f0 = T.term[t], f1 = T.term[t + 1];
-          for (int q = f0; q < f1 - 1; ++q) p *= fv[T.tfac[q]];
-          ft = fma(p, fv[T.tfac[f1 - 1]], ft);
-        }
+        double ft = pole_tree(T, T.g1[4 * gi], T.g1[4 * gi + 1], fv);
         for (int q = T.g1[4 * gi + 2]; q < T.g1[4 * gi + 3]; ++q) {
           const double r = rr[T.g1rd[2 * q]];
           for (int pw = T.g1rd[2 * q + 1]; pw > 0; --pw) ft *= r;

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <set>
 #include <string>
@@ -332,12 +333,55 @@ int flatten(tami_diagram* d) {
   h.n_rden = (int)rdens.size();
   h.n_cden = (int)cdens.size();
   h.n_g1 = (int)g1s.size();
-  h.n_terms = (int)ft.size();
-  int ntfac = 0, ng1rd = 0, ng2cd = 0;
-  for (auto& t : ft) ntfac += (int)t.fv.size();
+  // Pole tree (Sec. 2.1, the factorised FT): per group, a trie over each term's Fermi values
+  // taken in reverse residue order (last summed variable first); leaves with equal paths merge
+  // their coefficients.  Emitted depth first as a program over a stack of accumulators:
+  //   OPEN(d): acc[d] = 0;  CLOSE(d, F): acc[d-1] += F acc[d];  LEAFCLOSE(d, F, A): acc[d-1] += F A.
+  std::vector<std::pair<int, int>> ops;   // (kind | depth << 2 | leaf << 8, fv)
+  std::vector<double> leafA;
+  std::vector<std::pair<int, int>> g1_ops(g1s.size());
+  int max_closes = 0;
+  const int m_depth = nv - 1;
+  for (size_t g = 0; g < g1s.size(); ++g) {
+    struct Node { int fv; std::vector<int> kids; double A; };
+    std::vector<Node> nodes(1, Node{-1, {}, 0.0});
+    for (int ti : g1s[g].terms) {
+      if ((int)ft[ti].fv.size() != m_depth) { set_error("term with an unexpected number of Fermi factors"); return TAMI_EUNSUPPORTED; }
+      int cur = 0;
+      for (int L = m_depth - 1; L >= 0; --L) {
+        const int f = fv_tmp[ft[ti].fv[L]];
+        int nxt = -1;
+        for (int c : nodes[cur].kids) if (nodes[c].fv == f) { nxt = c; break; }
+        if (nxt < 0) { nxt = (int)nodes.size(); nodes.push_back(Node{f, {}, 0.0}); nodes[cur].kids.push_back(nxt); }
+        cur = nxt;
+      }
+      nodes[cur].A += ft[ti].A;
+    }
+    const int begin = (int)ops.size();
+    int closes = 0;
+    std::function<void(int, int)> emit = [&](int u, int d) {
+      if (d == m_depth) {
+        ops.push_back({kOpLeafClose | (d << 2) | ((int)leafA.size() << 8), nodes[u].fv});
+        leafA.push_back(nodes[u].A);
+        return;
+      }
+      if (d > 0) ops.push_back({kOpOpen | (d << 2), 0});
+      for (int c : nodes[u].kids) emit(c, d + 1);
+      if (d > 0) { ops.push_back({kOpClose | (d << 2), nodes[u].fv}); ++closes; }
+    };
+    emit(0, 0);
+    g1_ops[g] = {begin, (int)ops.size()};
+    max_closes = std::max(max_closes, closes);
+  }
+  h.n_ops = (int)ops.size();
+  h.n_leaves = (int)leafA.size();
+  h.max_depth = m_depth;
+  h.max_closes = max_closes;
+  int ng1rd = 0, ng2cd = 0, n_mul_ops = 0;
+  for (auto& o : ops) if ((o.first & 3) != kOpOpen) ++n_mul_ops;
   for (auto& g : g1s) ng1rd += (int)g.rd.size();
   for (auto& g : g2s) ng2cd += (int)g.size();
-  h.n_tfac = ntfac; h.n_g1rd = ng1rd;
+  h.n_g1rd = ng1rd;
   h.n_g2 = (int)g2s.size(); h.n_g2cd = ng2cd;
   h.max_der = max_der;
   Blob B;
@@ -353,9 +397,8 @@ int flatten(tami_diagram* d) {
   h.off_cden_a = B.reserve(sizeof(double) * h.n_cden);
   h.off_g1 = B.reserve(sizeof(int) * 4 * h.n_g1);
   h.off_g1_tgt = B.reserve(sizeof(int) * h.n_g1);
-  h.off_term = B.reserve(sizeof(int) * (h.n_terms + 1));
-  h.off_term_A = B.reserve(sizeof(double) * h.n_terms);
-  h.off_tfac = B.reserve(sizeof(int) * ntfac);
+  h.off_ops = B.reserve(sizeof(int) * 2 * h.n_ops);
+  h.off_leafA = B.reserve(sizeof(double) * h.n_leaves);
   h.off_g1rd = B.reserve(sizeof(int) * 2 * ng1rd);
   h.off_g2 = B.reserve(sizeof(int) * (h.n_g2 + 1));
   h.off_g2cd = B.reserve(sizeof(int) * 2 * ng2cd);
@@ -395,18 +438,17 @@ int flatten(tami_diagram* d) {
     r[0] = cdens[i].u; r[1] = cdens[i].sign;
     B.at<double>(h.off_cden_a)[i] = (double)cdens[i].a;
   }
+  for (int o = 0; o < h.n_ops; ++o) {
+    B.at<int>(h.off_ops)[2 * o] = ops[o].first;
+    B.at<int>(h.off_ops)[2 * o + 1] = ops[o].second;
+  }
+  for (int i = 0; i < h.n_leaves; ++i) B.at<double>(h.off_leafA)[i] = leafA[i];
   {
-    int tpos = 0, fpos = 0, rdpos = 0;
+    int rdpos = 0;
     for (int g = 0; g < h.n_g1; ++g) {
       int* r = B.at<int>(h.off_g1) + 4 * g;
-      r[0] = tpos;
-      for (int ti : g1s[g].terms) {
-        B.at<int>(h.off_term)[tpos] = fpos;
-        B.at<double>(h.off_term_A)[tpos] = ft[ti].A;
-        for (const FvKey& k : ft[ti].fv) B.at<int>(h.off_tfac)[fpos++] = fv_tmp[k];
-        ++tpos;
-      }
-      r[1] = tpos;
+      r[0] = g1_ops[g].first;
+      r[1] = g1_ops[g].second;
       r[2] = rdpos;
       for (auto& pr : g1s[g].rd) {
         B.at<int>(h.off_g1rd)[2 * rdpos] = pr.first;
@@ -416,7 +458,6 @@ int flatten(tami_diagram* d) {
       r[3] = rdpos;
       B.at<int>(h.off_g1_tgt)[g] = g1s[g].g2;
     }
-    B.at<int>(h.off_term)[tpos] = fpos;
   }
   {
     int pos = 0;
@@ -467,7 +508,7 @@ int flatten(tami_diagram* d) {
     }
   }
   fl += 6.0 * h.n_rden;                                 // real reciprocals
-  fl += (double)ntfac + h.n_terms;                      // term products, fused accumulate
+  fl += 2.0 * n_mul_ops;                                // pole-tree program: one fma per edge
   for (auto& g : g1s) {
     for (auto& pr : g.rd) fl += pr.second;              // frequency-independent denominators
     fl += 1.0;
@@ -489,7 +530,12 @@ int flatten(tami_diagram* d) {
   for (auto& g : g1s) {
     for (auto& pr : g.rd) bl += pr.second + 4.0;        // RR and the real-denominator adjoint
     bl += 1.0;
-    for (int ti : g.terms) bl += 4.0 * ft[ti].fv.size();  // prefix/suffix products, fvbar fma
+  }
+  // pole tree in the adjoint: recompute (fma per edge), then per edge an fma into the Fermi-value
+  // adjoint and, for inner edges, a mul for the child's adjoint
+  for (auto& o : ops) {
+    const int kind = o.first & 3;
+    bl += kind == kOpClose ? 2.0 + 3.0 : kind == kOpLeafClose ? 2.0 + 2.0 : 0.0;
   }
   bl += 3.0 * h.n_fv + 2.0 * nnz + 10.0 * h.n_rep;     // fvbar -> x -> E -> (mu, k_ext)
   I.bwd_flops_per_sample = bl;

@@ -20,6 +20,10 @@ constexpr int kMaxFermiValues = 256;
 constexpr int kMaxRealDens = 128;
 constexpr int kMaxCplxDens = 64;
 constexpr int kMaxDer = 5;
+constexpr int kMaxDepth = kMaxVars;   // pole-tree depth = number of summed variables
+
+// pole-tree program ops (see flatten): acc[d] = 0 / acc[d-1] += F * acc[d] / acc[d-1] += F * A_leaf
+enum { kOpOpen = 0, kOpClose = 1, kOpLeafClose = 2 };
 
 void set_error(const std::string& msg);
 
@@ -52,7 +56,8 @@ struct TableHeader {
   int n_combo, combo_nnz;
   int n_fbase, n_fv;
   int n_rden, n_cden;
-  int n_g1, n_terms, n_tfac, n_g1rd;
+  int n_g1, n_ops, n_leaves, n_g1rd;
+  int max_depth, max_closes;   // pole-tree depth (= m) and most CLOSE ops in one group
   int n_g2, n_g2cd;
   int max_der;
   int bytes;
@@ -67,11 +72,10 @@ struct TableHeader {
   int off_rden;       // int32 [n_rden][2]       combo, sign
   int off_cden;       // int32 [n_cden][2]       combo, sign
   int off_cden_a;     // double [n_cden]          external-frequency coefficient
-  int off_g1;         // int32 [n_g1][4]         term_begin, term_end, rd_begin, rd_end
+  int off_g1;         // int32 [n_g1][4]         op_begin, op_end, rd_begin, rd_end
   int off_g1_tgt;     // int32 [n_g1]             frequency group it feeds (ascending)
-  int off_term;       // int32 [n_terms+1]       factor offsets
-  int off_term_A;     // double [n_terms]
-  int off_tfac;       // int32 [n_tfac]          Fermi-value index
+  int off_ops;        // int2 [n_ops]            pole-tree program: x = kind | depth<<2 | leaf<<8, y = Fermi value
+  int off_leafA;      // double [n_leaves]        merged coefficients of the leaves
   int off_g1rd;       // int32 [n_g1rd][2]       real-den index, power
   int off_g2;         // int32 [n_g2+1]          complex-den offsets
   int off_g2cd;       // int32 [n_g2cd][2]       complex-den index, power
