@@ -55,14 +55,15 @@ struct BatchParams {
   const double* params;   // t, t', mu, kx, ky, beta
   const double* X;
   int n_f;
-  int table_cap, max_cden, max_g2;
+  int table_cap, max_cden, max_g2;   // largest table (bytes), denominators and groups
   int* counter;
   int* status;
   double* partial;        // [n_items][n_f][4]
 };
 
 size_t batch_smem_bytes(int table_cap, int n_f, int max_cden, int max_g2) {
-  return (size_t)table_cap + sizeof(double) * (2 * (size_t)n_f + (size_t)(max_cden + max_g2 + 4) * kBlock);
+  return (size_t)table_cap +
+         sizeof(double) * ((2 + 2 * (size_t)max_cden) * n_f + (size_t)(max_cden + max_g2 + 4) * kBlock);
 }
 
 __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchParams P) {
@@ -74,7 +75,9 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchParams P) {
   const int n_f = P.n_f;
   unsigned char* tab = smem;
   double* Xs = reinterpret_cast<double*>(smem + P.table_cap);
-  double* CB = Xs + 2 * n_f;
+  double* AXI = Xs + 2 * n_f;
+  double* AXI2 = AXI + P.max_cden * n_f;
+  double* CB = AXI2 + P.max_cden * n_f;
   double* W = CB + P.max_cden * kBlock;
   double* red = W + P.max_g2 * kBlock;
   for (int i = tid; i < 2 * n_f; i += kBlock) Xs[i] = P.X[i];
@@ -89,6 +92,7 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchParams P) {
   A.n_f = n_f;
   int cur_d = -1;
   uint32_t phase = 0;
+  bool xr_zero = true;
   double acc[kMaxFreqPerThread][4];
   __syncthreads();
   while (true) {
@@ -110,12 +114,13 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchParams P) {
       if (__syncthreads_or(!ok)) return;
       phase ^= 1u;
       cur_d = d;
+      xr_zero = freq_constants(Hs, table_view(tab, Hs), Xs, n_f, AXI, AXI2);
     }
     const TableView T = table_view(tab, Hs);
     A.seed = P.diags[d].seed;
     A.n = P.diags[d].n;
     for (int i = 0; i < kMaxFreqPerThread; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0;
-    for (long long tile = item.tile0; tile < item.tile1; ++tile) fwd_tile<false>(Hs, T, A, tile, Xs, CB, W, M, acc);
+    for (long long tile = item.tile0; tile < item.tile1; ++tile) fwd_tile<false>(Hs, T, A, tile, Xs, AXI, AXI2, xr_zero, CB, W, M, acc);
     block_reduce_store(M, n_f, acc, red, P.partial + (size_t)it * n_f * 4);
   }
 }

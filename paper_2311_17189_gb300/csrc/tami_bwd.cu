@@ -45,8 +45,10 @@ struct BwdParams {
   int* status;
 };
 
+// Shared memory: table | X, G [n_f][2] | AXI, AXI2 [n_cden][n_f] | red [4 warps][2 n_f + 3]
 __host__ __device__ __forceinline__ size_t bwd_smem_bytes(const TableHeader& h, int n_f) {
-  return (size_t)align16(h.bytes) + sizeof(double) * (4 * (size_t)n_f + 4 * (2 * (size_t)n_f + 3));
+  return (size_t)align16(h.bytes) +
+         sizeof(double) * ((4 + 2 * (size_t)h.n_cden) * n_f + 4 * (2 * (size_t)n_f + 3));
 }
 
 __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
@@ -57,7 +59,9 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
   const int n_f = P.n_f;
   double* Xs = reinterpret_cast<double*>(smem + align16(H.bytes));
   double* Gs = Xs + 2 * n_f;
-  double* red = Gs + 2 * n_f;                 // [4 warps][2 n_f + 3]
+  double* AXI = Gs + 2 * n_f;
+  double* AXI2 = AXI + H.n_cden * n_f;
+  double* red = AXI2 + H.n_cden * n_f;       // [4 warps][2 n_f + 3]
   for (int i = tid; i < 2 * n_f; i += kBlock) { Xs[i] = P.X[i]; Gs[i] = P.G[i]; }
 
   const double* alpha = reinterpret_cast<const double*>(smem + H.off_alpha);
@@ -82,6 +86,17 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
   for (int i = 0; i < 2 * n_f; ++i) accX[i] = 0.0;
   double gmu = 0.0, gkx = 0.0, gky = 0.0;
   __syncthreads();
+  bool xr_zero;
+  {
+    int nonzero = 0;
+    for (int i = tid; i < H.n_cden * n_f; i += kBlock) {
+      const double a = cden_a[i / n_f] * Xs[2 * (i % n_f) + 1];
+      AXI[i] = a;
+      AXI2[i] = a * a;
+    }
+    for (int f = tid; f < n_f; f += kBlock) nonzero |= Xs[2 * f] != 0.0;
+    xr_zero = !__syncthreads_or(nonzero);
+  }
 
   const double beta = P.beta;
   const long long n_tiles = (P.n + kBlock - 1) / kBlock;
@@ -175,15 +190,13 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
     for (int h = 0; h < H.n_g2; ++h) Wb2[h] = 0.0;
     for (int c = 0; c < H.n_cden; ++c) bb[c] = 0.0;
     for (int f = 0; f < n_f; ++f) {
-      const double Xr = Xs[2 * f], Xi = Xs[2 * f + 1], gr = Gs[2 * f], gim = Gs[2 * f + 1];
+      const double Xr = Xs[2 * f], gr = Gs[2 * f], gim = Gs[2 * f + 1];
       double rc_re[kBwCden], rc_im[kBwCden], U_re[kBwCden], U_im[kBwCden];
       for (int c = 0; c < H.n_cden; ++c) {
-        const double a = cden_a[c];
-        const double Dr = fma(a, Xr, b[c]);
-        const double Di = a * Xi;
-        const double r = rcp(fma(Dr, Dr, Di * Di));
+        const double Dr = xr_zero ? b[c] : fma(cden_a[c], Xr, b[c]);
+        const double r = rcp(fma(Dr, Dr, AXI2[c * n_f + f]));
         rc_re[c] = Dr * r;
-        rc_im[c] = -Di * r;
+        rc_im[c] = -AXI[c * n_f + f] * r;
         U_re[c] = 0.0;
         U_im[c] = 0.0;
       }

@@ -46,9 +46,10 @@ struct FwdParams {
 };
 
 
-// Shared memory: table | X [n_f][2] | CB [n_cden][S] | W [n_g2][S] | red [4][S]
+// Shared memory: table | X [n_f][2] | AXI, AXI2 [n_cden][n_f] | CB [n_cden][S] | W [n_g2][S] | red [4][S]
 __host__ __device__ __forceinline__ size_t fwd_smem_bytes(const TableHeader& h, int n_f) {
-  return (size_t)align16(h.bytes) + sizeof(double) * (2 * (size_t)n_f + (size_t)(h.n_cden + h.n_g2 + 4) * kBlock);
+  return (size_t)align16(h.bytes) +
+         sizeof(double) * ((2 + 2 * (size_t)h.n_cden) * n_f + (size_t)(h.n_cden + h.n_g2 + 4) * kBlock);
 }
 
 template <bool ENERGY_IN>
@@ -58,7 +59,9 @@ __global__ void __launch_bounds__(kBlock) fwd_kernel(const FwdParams P) {
   const int tid = threadIdx.x;
   if (!stage_table(smem, P.table, H.bytes, P.status)) return;
   double* Xs = reinterpret_cast<double*>(smem + align16(H.bytes));
-  double* CB = Xs + 2 * P.n_f;
+  double* AXI = Xs + 2 * P.n_f;
+  double* AXI2 = AXI + H.n_cden * P.n_f;
+  double* CB = AXI2 + H.n_cden * P.n_f;
   double* W = CB + H.n_cden * kBlock;
   double* red = W + H.n_g2 * kBlock;
   for (int i = tid; i < 2 * P.n_f; i += kBlock) Xs[i] = P.X[i];
@@ -67,13 +70,14 @@ __global__ void __launch_bounds__(kBlock) fwd_kernel(const FwdParams P) {
   double acc[kMaxFreqPerThread][4];
   for (int i = 0; i < kMaxFreqPerThread; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0;
   __syncthreads();
+  const bool xr_zero = freq_constants(H, T, Xs, P.n_f, AXI, AXI2);
   TileArgs A;
   A.t = P.t; A.tp = P.tp; A.mu = P.mu; A.kx = P.kx; A.ky = P.ky; A.beta = P.beta;
   A.seed = P.seed; A.offset = P.offset; A.n = P.n; A.E_in = P.E_in; A.per_sample = P.per_sample;
   A.n_f = P.n_f;
   const long long n_tiles = (P.n + kBlock - 1) / kBlock;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x)
-    fwd_tile<ENERGY_IN>(H, T, A, tile, Xs, CB, W, M, acc);
+    fwd_tile<ENERGY_IN>(H, T, A, tile, Xs, AXI, AXI2, xr_zero, CB, W, M, acc);
   if (!P.partial) return;
   block_reduce_store(M, P.n_f, acc, red, P.partial + (size_t)blockIdx.x * P.n_f * 4);
 }

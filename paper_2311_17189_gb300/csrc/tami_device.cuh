@@ -35,29 +35,25 @@ __device__ __forceinline__ double to_momentum(uint32_t hi, uint32_t lo) {
   return fma(u, 2.0 * pi, -pi);
 }
 
-// cos and sin: Cody-Waite reduction by pi/2 (three-part constant) and Taylor series on
-// [-pi/4, pi/4] (W. J. Cody and W. Waite, 1980).  Every operation is an explicit fma or a
-// rounded mul/add intrinsic, so the result is the same on any IEEE machine that follows
-// the same recipe.
-__device__ __forceinline__ void cw_sincos(double k, double& s_out, double& c_out) {
-  const double two_over_pi = 0x1.45f306dc9c883p-1;
-  const double P1 = 0x1.921fb54442d18p+0, P2 = 0x1.1a62633145c07p-54, P3 = -0x1.f1976b7ed8fbcp-110;
-  double n = rint(__dmul_rn(k, two_over_pi));
+// cos and sin: Cody-Waite reduction by pi (three-part constant), k = n pi + r, |r| <= pi/2, then
+// Taylor series in r (to r^24 for cos, r^25 for sin) and the sign (-1)^n (W. J. Cody and
+// W. Waite, 1980).  Every operation is an explicit fma or a rounded mul intrinsic, so the result
+// is the same on any IEEE machine that follows the same recipe.
+__device__ __forceinline__ double cw_reduce(double k, double& odd_sign) {
+  const double inv_pi = 0x1.45f306dc9c883p-2;
+  const double P1 = 0x1.921fb54442d18p+1, P2 = 0x1.1a62633145c07p-53, P3 = -0x1.f1976b7ed8fbcp-109;
+  const double n = rint(__dmul_rn(k, inv_pi));
   double r = fma(-n, P1, k);
   r = fma(-n, P2, r);
   r = fma(-n, P3, r);
-  double z = __dmul_rn(r, r);
-  double ps = -0x1.2f49b46814157p-57;
-  ps = fma(ps, z, 0x1.952c77030ad4ap-49);
-  ps = fma(ps, z, -0x1.ae7f3e733b81fp-41);
-  ps = fma(ps, z, 0x1.6124613a86d09p-33);
-  ps = fma(ps, z, -0x1.ae64567f544e4p-26);
-  ps = fma(ps, z, 0x1.71de3a556c734p-19);
-  ps = fma(ps, z, -0x1.a01a01a01a01ap-13);
-  ps = fma(ps, z, 0x1.1111111111111p-7);
-  ps = fma(ps, z, -0x1.5555555555555p-3);
-  double sr = fma(__dmul_rn(r, z), ps, r);
-  double pc = 0x1.e542ba4020225p-62;
+  odd_sign = ((long long)n & 1) ? -1.0 : 1.0;
+  return r;
+}
+
+__device__ __forceinline__ double cw_cos_poly(double z) {
+  double pc = 0x1.f2cf01972f578p-80;
+  pc = fma(pc, z, -0x1.0ce396db7f853p-70);
+  pc = fma(pc, z, 0x1.e542ba4020225p-62);
   pc = fma(pc, z, -0x1.6827863b97d97p-53);
   pc = fma(pc, z, 0x1.ae7f3e733b81fp-45);
   pc = fma(pc, z, -0x1.93974a8c07c9dp-37);
@@ -67,21 +63,43 @@ __device__ __forceinline__ void cw_sincos(double k, double& s_out, double& c_out
   pc = fma(pc, z, -0x1.6c16c16c16c17p-10);
   pc = fma(pc, z, 0x1.5555555555555p-5);
   pc = fma(pc, z, -0x1.0000000000000p-1);
-  double cr = fma(z, pc, 1.0);
-  int q = (int)((long long)n & 3);
-  double s = (q == 0) ? sr : (q == 1) ? cr : (q == 2) ? -sr : -cr;
-  double c = (q == 0) ? cr : (q == 1) ? -sr : (q == 2) ? -cr : sr;
-  s_out = s;
-  c_out = c;
+  return fma(z, pc, 1.0);
+}
+
+__device__ __forceinline__ double cw_cos(double k) {
+  double sg;
+  const double r = cw_reduce(k, sg);
+  const double c = cw_cos_poly(__dmul_rn(r, r));
+  return sg < 0.0 ? -c : c;
+}
+
+__device__ __forceinline__ void cw_sincos(double k, double& s_out, double& c_out) {
+  double sg;
+  const double r = cw_reduce(k, sg);
+  const double z = __dmul_rn(r, r);
+  const double cr = cw_cos_poly(z);
+  double ps = 0x1.3f3ccdd165fa9p-84;
+  ps = fma(ps, z, -0x1.761b41316381ap-75);
+  ps = fma(ps, z, 0x1.71b8ef6dcf572p-66);
+  ps = fma(ps, z, -0x1.2f49b46814157p-57);
+  ps = fma(ps, z, 0x1.952c77030ad4ap-49);
+  ps = fma(ps, z, -0x1.ae7f3e733b81fp-41);
+  ps = fma(ps, z, 0x1.6124613a86d09p-33);
+  ps = fma(ps, z, -0x1.ae64567f544e4p-26);
+  ps = fma(ps, z, 0x1.71de3a556c734p-19);
+  ps = fma(ps, z, -0x1.a01a01a01a01ap-13);
+  ps = fma(ps, z, 0x1.1111111111111p-7);
+  ps = fma(ps, z, -0x1.5555555555555p-3);
+  const double sr = fma(__dmul_rn(r, z), ps, r);
+  s_out = sg < 0.0 ? -sr : sr;
+  c_out = sg < 0.0 ? -cr : cr;
 }
 
 // E = mu - eps(k),  eps(k) = -2t(cos kx + cos ky) - 4t' cos kx cos ky
 __device__ __forceinline__ double line_energy(double kx, double ky, double t, double tp, double mu) {
-  double sx, cx, sy, cy;
-  cw_sincos(kx, sx, cx);
-  cw_sincos(ky, sy, cy);
-  double sum = __dadd_rn(cx, cy);
-  double prod = __dmul_rn(cx, cy);
+  const double cx = cw_cos(kx), cy = cw_cos(ky);
+  const double sum = __dadd_rn(cx, cy);
+  const double prod = __dmul_rn(cx, cy);
   return fma(4.0 * tp, prod, fma(2.0 * t, sum, mu));
 }
 

@@ -102,11 +102,28 @@ struct TileArgs {
   int n_f;
 };
 
-// Shared memory per tile: X [n_f][2] (filled by the caller), CB [n_cden][kBlock], W [n_g2][kBlock].
+// Per-(denominator, frequency) constants of phase 2: AXI = a_c Im X_f and AXI2 = AXI^2, in shared
+// memory [n_cden][n_f] each.  Returns whether every Re X_f is zero (then Re D = b exactly).
+// Ends with a barrier.
+__device__ __forceinline__ bool freq_constants(const TableHeader& H, const TableView& T, const double* Xs, int n_f,
+                                               double* AXI, double* AXI2) {
+  int nonzero = 0;
+  for (int i = threadIdx.x; i < H.n_cden * n_f; i += kBlock) {
+    const int c = i / n_f, f = i % n_f;
+    const double a = T.cden_a[c] * Xs[2 * f + 1];
+    AXI[i] = a;
+    AXI2[i] = a * a;
+  }
+  for (int f = threadIdx.x; f < n_f; f += kBlock) nonzero |= Xs[2 * f] != 0.0;
+  return !__syncthreads_or(nonzero);
+}
+
+// Shared memory per tile: X [n_f][2] (filled by the caller), AXI and AXI2 [n_cden][n_f] (from
+// freq_constants), CB [n_cden][kBlock], W [n_g2][kBlock].
 template <bool ENERGY_IN>
 __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& T, const TileArgs& A,
-                                         long long tile, const double* Xs, double* CB, double* W,
-                                         const FreqMap& M, double (*acc)[4]) {
+                                         long long tile, const double* Xs, const double* AXI, const double* AXI2,
+                                         bool xr_zero, double* CB, double* W, const FreqMap& M, double (*acc)[4]) {
   const int tid = threadIdx.x;
   const long long s0 = tile * kBlock;
   const double beta = A.beta;
@@ -189,18 +206,17 @@ __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& 
   // ---------------------------------------------------------------- phase 2 ((f, s) pairs)
   for (int fi = 0; fi < M.nf; ++fi) {
     const int f = M.f0 + fi * M.fstep;
-    const double Xr = Xs[2 * f], Xi = Xs[2 * f + 1];
+    const double Xr = Xs[2 * f];
     for (int sl = M.s0; sl < kBlock; sl += M.sstep) {
       const long long s = s0 + sl;
       if (s >= A.n) break;
       double rc_re[kMaxCplxDens], rc_im[kMaxCplxDens];
       for (int c = 0; c < H.n_cden; ++c) {
-        const double a = T.cden_a[c];
-        const double Dr = fma(a, Xr, CB[c * kBlock + sl]);
-        const double Di = a * Xi;
-        const double r = rcp(fma(Dr, Dr, Di * Di));
+        const double b = CB[c * kBlock + sl];
+        const double Dr = xr_zero ? b : fma(T.cden_a[c], Xr, b);    // D = a X + b
+        const double r = rcp(fma(Dr, Dr, AXI2[c * A.n_f + f]));
         rc_re[c] = Dr * r;
-        rc_im[c] = -Di * r;
+        rc_im[c] = -AXI[c * A.n_f + f] * r;
       }
       double vr = 0.0, vi = 0.0;
       for (int hg = 0; hg < H.n_g2; ++hg) {

@@ -494,7 +494,7 @@ int flatten(tami_diagram* d) {
     int nz = 0;
     for (int l = 0; l < nv; ++l) if (d->alpha[j * nv + l]) ++nz;
     fl += 2.0 * 2.0 * nz;                               // line momenta, fma per term and dimension
-    fl += 2.0 * 47.0 + 6.0;                             // cos/sin of both components, energy
+    fl += 2.0 * 33.0 + 6.0;                             // cos of both components, energy
   }
   fl += 2.0 * nnz;                                      // energy combinations
   for (int b = 0; b < h.n_fbase; ++b) {
@@ -514,7 +514,7 @@ int flatten(tami_diagram* d) {
     fl += 1.0;
   }
   I.flops_per_sample = fl;
-  double ff = 14.0 * h.n_cden;                          // complex reciprocal per denominator
+  double ff = 12.0 * h.n_cden;                          // |D|^2, reciprocal, 1/D (+ Re D off the imaginary axis)
   for (auto& g : g2s) {
     int pw = 0;
     for (auto& pr : g) pw += pr.second;
@@ -539,7 +539,7 @@ int flatten(tami_diagram* d) {
   }
   bl += 3.0 * h.n_fv + 2.0 * nnz + 10.0 * h.n_rep;     // fvbar -> x -> E -> (mu, k_ext)
   I.bwd_flops_per_sample = bl;
-  double bf = 14.0 * h.n_cden + 12.0 * h.n_cden + 2.0;  // reciprocals, Z, dv/dX and b-adjoints, accX
+  double bf = 12.0 * h.n_cden + 12.0 * h.n_cden + 2.0;  // reciprocals, Z, dv/dX and b-adjoints, accX
   for (auto& g : g2s) {
     int pw = 0;
     for (auto& pr : g) pw += pr.second;
