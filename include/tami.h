@@ -240,6 +240,11 @@ void tami_batch_destroy(tami_batch* b);
 int tami_enumerate_sigma(int order, int capacity, int8_t* alpha, int8_t* eps, int32_t* code,
                          int32_t* loops, int* n_out);
 
+/* Diagnostic: the kernels' exponential for t <= 0 (table-driven after Tang, ACM TOMS 1989), applied
+ * elementwise: y = e^t, em = e^t - 1.  t, y, em: device double [n].  Used by the tests to check it
+ * against CUDA's exp/expm1. */
+int tami_selftest_exp(const double* t, int64_t n, double* y, double* em, tami_stream_t stream);
+
 void tami_destroy(tami_diagram* d);
 
 #ifdef __cplusplus

@@ -51,6 +51,71 @@ __host__ __device__ __forceinline__ size_t bwd_smem_bytes(const TableHeader& h, 
          sizeof(double) * ((4 + 2 * (size_t)h.n_cden) * n_f + 4 * (2 * (size_t)n_f + 3));
 }
 
+// Phase 2 of the adjoint for one sample over all frequencies: the reciprocals, group products R_h,
+// T_h = W_h R_h, the weight adjoints Wb_h += Re(conj g R_h), U_d = sum_h p T_h, Z_d = r_d U_d,
+// dv/dX = -sum_d a_d Z_d and the denominator-energy adjoints bb_d -= Re(conj g Z_d).  As in the
+// forward, no data-dependent selects around FP64 work (predicated-off FP64 instructions still
+// cost FP64-pipe time): the first factor of each product is peeled, the R = 1 group is group 0,
+// the imaginary-axis case is a template parameter.
+template <bool XR_ZERO>
+__device__ __forceinline__ void bwd_phase2(const TableHeader& H, int n_f, long long s, const BwdParams& P,
+                                           const double* Xs, const double* Gs, const double* AXI, const double* AXI2,
+                                           const double* cden_a, const int* g2, const int* g2cd, const double* g2cd_p,
+                                           const double* b, const double* W2, double* Wb2, double* bb, double* accX) {
+  for (int f = 0; f < n_f; ++f) {
+    const double Xr = Xs[2 * f], gr = Gs[2 * f], gim = Gs[2 * f + 1];
+    double rc_re[kBwCden], rc_im[kBwCden], U_re[kBwCden], U_im[kBwCden];
+    for (int c = 0; c < H.n_cden; ++c) {
+      const double Dr = XR_ZERO ? b[c] : fma(cden_a[c], Xr, b[c]);
+      const double r = rcp(fma(Dr, Dr, AXI2[c * n_f + f]));
+      rc_re[c] = Dr * r;
+      rc_im[c] = -AXI[c * n_f + f] * r;
+      U_re[c] = 0.0;
+      U_im[c] = 0.0;
+    }
+    if (H.g2_const) Wb2[0] += gr;                 // R = 1
+    for (int h = H.g2_const; h < H.n_g2; ++h) {
+      const int q0 = g2[h], q1 = g2[h + 1];
+      int c = g2cd[2 * q0];
+      double Rr = rc_re[c], Ri = rc_im[c];
+      for (int pw = g2cd[2 * q0 + 1]; pw > 1; --pw) {
+        const double nr = fma(Rr, rc_re[c], -Ri * rc_im[c]);
+        Ri = fma(Rr, rc_im[c], Ri * rc_re[c]);
+        Rr = nr;
+      }
+      for (int q = q0 + 1; q < q1; ++q) {
+        c = g2cd[2 * q];
+        for (int pw = g2cd[2 * q + 1]; pw > 0; --pw) {
+          const double nr = fma(Rr, rc_re[c], -Ri * rc_im[c]);
+          Ri = fma(Rr, rc_im[c], Ri * rc_re[c]);
+          Rr = nr;
+        }
+      }
+      Wb2[h] = fma(gr, Rr, fma(gim, Ri, Wb2[h]));
+      const double Tr = W2[h] * Rr, Ti = W2[h] * Ri;
+      for (int q = q0; q < q1; ++q) {
+        const int cc = g2cd[2 * q];
+        U_re[cc] = fma(g2cd_p[q], Tr, U_re[cc]);
+        U_im[cc] = fma(g2cd_p[q], Ti, U_im[cc]);
+      }
+    }
+    double dvr = 0.0, dvi = 0.0;
+    for (int c = 0; c < H.n_cden; ++c) {
+      const double Zr = fma(rc_re[c], U_re[c], -rc_im[c] * U_im[c]);
+      const double Zi = fma(rc_re[c], U_im[c], rc_im[c] * U_re[c]);
+      dvr = fma(-cden_a[c], Zr, dvr);
+      dvi = fma(-cden_a[c], Zi, dvi);
+      bb[c] -= fma(gr, Zr, gim * Zi);
+    }
+    accX[2 * f] += dvr;
+    accX[2 * f + 1] += dvi;
+    if (P.ps_dX) {
+      double2* o = reinterpret_cast<double2*>(P.ps_dX) + (size_t)f * P.n + s;
+      *o = make_double2(dvr, dvi);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const TableHeader& H = P.h;
@@ -81,6 +146,7 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
   const int* g1rd = reinterpret_cast<const int*>(smem + H.off_g1rd);
   const int* g2 = reinterpret_cast<const int*>(smem + H.off_g2);
   const int* g2cd = reinterpret_cast<const int*>(smem + H.off_g2cd);
+  const double* g2cd_p = reinterpret_cast<const double*>(smem + H.off_g2cd_p);
 
   double accX[2 * kBwFreq];
   for (int i = 0; i < 2 * n_f; ++i) accX[i] = 0.0;
@@ -138,8 +204,8 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
     for (int b = 0; b < H.n_fbase; ++b) {
       const double xv = x[fbase[4 * b]];
       const double nt = -beta * fabs(xv);
-      const double y = exp(nt);
-      const double em = fbase[4 * b + 3] ? expm1(nt) : 0.0;
+      double em = 0.0;
+      const double y = fbase[4 * b + 3] ? exp_neg<true>(nt, em) : exp_neg<false>(nt, em);
       int cur_sigma = 0;
       double g = 0.0, hh = 0.0;
       for (int v = fbase[4 * b + 1]; v < fbase[4 * b + 2]; ++v) {
@@ -189,57 +255,10 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
     double Wb2[kBwG2], bb[kBwCden];
     for (int h = 0; h < H.n_g2; ++h) Wb2[h] = 0.0;
     for (int c = 0; c < H.n_cden; ++c) bb[c] = 0.0;
-    for (int f = 0; f < n_f; ++f) {
-      const double Xr = Xs[2 * f], gr = Gs[2 * f], gim = Gs[2 * f + 1];
-      double rc_re[kBwCden], rc_im[kBwCden], U_re[kBwCden], U_im[kBwCden];
-      for (int c = 0; c < H.n_cden; ++c) {
-        const double Dr = xr_zero ? b[c] : fma(cden_a[c], Xr, b[c]);
-        const double r = rcp(fma(Dr, Dr, AXI2[c * n_f + f]));
-        rc_re[c] = Dr * r;
-        rc_im[c] = -AXI[c * n_f + f] * r;
-        U_re[c] = 0.0;
-        U_im[c] = 0.0;
-      }
-      for (int h = 0; h < H.n_g2; ++h) {
-        const int q0 = g2[h], q1 = g2[h + 1];
-        if (q0 == q1) { Wb2[h] += gr; continue; }   // R = 1
-        double Rr = 1.0, Ri = 0.0;
-        bool first = true;
-        for (int q = q0; q < q1; ++q) {
-          const int c = g2cd[2 * q];
-          for (int pw = g2cd[2 * q + 1]; pw > 0; --pw) {
-            if (first) { Rr = rc_re[c]; Ri = rc_im[c]; first = false; }
-            else {
-              const double nr = fma(Rr, rc_re[c], -Ri * rc_im[c]);
-              Ri = fma(Rr, rc_im[c], Ri * rc_re[c]);
-              Rr = nr;
-            }
-          }
-        }
-        Wb2[h] = fma(gr, Rr, fma(gim, Ri, Wb2[h]));
-        const double Tr = W2[h] * Rr, Ti = W2[h] * Ri;
-        for (int q = q0; q < q1; ++q) {
-          const int c = g2cd[2 * q];
-          const double p = (double)g2cd[2 * q + 1];
-          U_re[c] = fma(p, Tr, U_re[c]);
-          U_im[c] = fma(p, Ti, U_im[c]);
-        }
-      }
-      double dvr = 0.0, dvi = 0.0;
-      for (int c = 0; c < H.n_cden; ++c) {
-        const double Zr = fma(rc_re[c], U_re[c], -rc_im[c] * U_im[c]);
-        const double Zi = fma(rc_re[c], U_im[c], rc_im[c] * U_re[c]);
-        dvr = fma(-cden_a[c], Zr, dvr);
-        dvi = fma(-cden_a[c], Zi, dvi);
-        bb[c] -= fma(gr, Zr, gim * Zi);
-      }
-      accX[2 * f] += dvr;
-      accX[2 * f + 1] += dvi;
-      if (P.ps_dX) {
-        double2* o = reinterpret_cast<double2*>(P.ps_dX) + (size_t)f * P.n + s;
-        *o = make_double2(dvr, dvi);
-      }
-    }
+    if (xr_zero)
+      bwd_phase2<true>(H, n_f, s, P, Xs, Gs, AXI, AXI2, cden_a, g2, g2cd, g2cd_p, b, W2, Wb2, bb, accX);
+    else
+      bwd_phase2<false>(H, n_f, s, P, Xs, Gs, AXI, AXI2, cden_a, g2, g2cd, g2cd_p, b, W2, Wb2, bb, accX);
     // ------------------------------------------------------------ reverse sweep
     double xbar[kBwCombos], fvbar[kBwFv];
     for (int u = 0; u < H.n_combo; ++u) xbar[u] = 0.0;

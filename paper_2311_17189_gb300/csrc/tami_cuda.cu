@@ -102,6 +102,14 @@ __global__ void finalize_kernel(const double* partial, int n_blocks, int n_f, lo
   if (var) { var[2 * f] = vr; var[2 * f + 1] = vi; }
 }
 
+__global__ void exp_selftest_kernel(const double* t, long long n, double* y, double* em) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double e = 0.0;
+  y[i] = exp_neg<true>(t[i], e);
+  em[i] = e;
+}
+
 __global__ void sample_energies_kernel(const FwdParams P, double* E) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.n) return;
@@ -346,6 +354,14 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
   finalize_kernel<<<(n_f + 127) / 128, 128, 0, st>>>(partial, grid, n_f, n_samples, status, mean, var);
   e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "finalize launch");
+}
+
+int tami_selftest_exp(const double* t, int64_t n, double* y, double* em, tami_stream_t stream) {
+  if (!t || !y || !em || n < 0) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (n == 0) return TAMI_OK;
+  exp_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(t, n, y, em);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "exp_selftest launch");
 }
 
 void tami_destroy(tami_diagram* d) {

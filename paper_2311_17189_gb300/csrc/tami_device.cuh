@@ -103,6 +103,74 @@ __device__ __forceinline__ double line_energy(double kx, double ky, double t, do
   return fma(4.0 * tp, prod, fma(2.0 * t, sum, mu));
 }
 
+// e^t and e^t - 1 for t <= 0, after P. T. P. Tang, "Table-driven implementation of the exponential
+// function in IEEE floating-point arithmetic", ACM TOMS 15 (1989) 144-157:
+// t = k ln2/32 + r with k = 32 m + j (0 <= j < 32), |r| <= ln2/64, and
+// e^t = 2^m 2^(j/32) e^r, 2^(j/32) = T_hi + T_lo from a two-part table, e^r - 1 = p(r) its Taylor
+// polynomial to r^7 (truncation < 4e-19 relative).  k is read from the low word of
+// t * 32/ln2 + 1.5 * 2^52 (round to nearest), and r is formed with a two-part ln2/32 whose high
+// part has few enough bits that the first reduction step is exact.  Then
+//   e^t     = T_hi' + (T_hi' p + T_lo'),        e^t - 1 = (T_hi' - 1) + (T_hi' p + T_lo'),
+// T' = 2^m T; T_hi' - 1 is exact where it matters (T_hi' in [1/2, 1]).
+__device__ const double kExp2TabHi[32] = {
+  0x1.0000000000000p+0, 0x1.059b0d3158574p+0, 0x1.0b5586cf9890fp+0, 0x1.11301d0125b51p+0,
+  0x1.172b83c7d517bp+0, 0x1.1d4873168b9aap+0, 0x1.2387a6e756238p+0, 0x1.29e9df51fdee1p+0,
+  0x1.306fe0a31b715p+0, 0x1.371a7373aa9cbp+0, 0x1.3dea64c123422p+0, 0x1.44e086061892dp+0,
+  0x1.4bfdad5362a27p+0, 0x1.5342b569d4f82p+0, 0x1.5ab07dd485429p+0, 0x1.6247eb03a5585p+0,
+  0x1.6a09e667f3bcdp+0, 0x1.71f75e8ec5f74p+0, 0x1.7a11473eb0187p+0, 0x1.82589994cce13p+0,
+  0x1.8ace5422aa0dbp+0, 0x1.93737b0cdc5e5p+0, 0x1.9c49182a3f090p+0, 0x1.a5503b23e255dp+0,
+  0x1.ae89f995ad3adp+0, 0x1.b7f76f2fb5e47p+0, 0x1.c199bdd85529cp+0, 0x1.cb720dcef9069p+0,
+  0x1.d5818dcfba487p+0, 0x1.dfc97337b9b5fp+0, 0x1.ea4afa2a490dap+0, 0x1.f50765b6e4540p+0};
+__device__ const double kExp2TabLo[32] = {
+  0x0.0p+0, 0x1.d73e2a475b465p-55, 0x1.8a62e4adc610bp-54, -0x1.6c51039449b3ap-54,
+  -0x1.19041b9d78a76p-55, 0x1.e016e00a2643cp-54, 0x1.9b07eb6c70573p-54, 0x1.612e8afad1255p-55,
+  0x1.6f46ad23182e4p-55, -0x1.63aeabf42eae2p-54, 0x1.ada0911f09ebcp-55, 0x1.89b7a04ef80d0p-59,
+  0x1.d4397afec42e2p-56, -0x1.07abe1db13cadp-55, 0x1.6324c054647adp-54, -0x1.383c17e40b497p-54,
+  -0x1.bdd3413b26456p-54, -0x1.16e4786887a99p-55, -0x1.41577ee04992fp-55, -0x1.d4c1dd41532d8p-54,
+  0x1.6e9f156864b27p-54, -0x1.75fc781b57ebcp-57, 0x1.c7c46b071f2bep-56, -0x1.d2f6edb8d41e1p-54,
+  0x1.7a1cd345dcc81p-54, -0x1.5584f7e54ac3bp-56, 0x1.11065895048ddp-55, 0x1.503cbd1e949dbp-56,
+  0x1.2ed02d75b3707p-55, -0x1.1a5cd4f184b5cp-54, -0x1.e9c23179c2893p-54, 0x1.9d3e12dd8a18bp-54};
+
+// 2^m T_hi (1 + p) for m < -960 (T_lo dropped), with 2^m applied in two steps; 0 below 2^-2000.
+// Out of line so that the common path carries no predicated FP64 work.
+static __device__ __noinline__ double exp_neg_deep_tail(double th, double p, int m) {
+  if (m < -2000) return 0.0;
+  th = __longlong_as_double(__double_as_longlong(th) + ((long long)(m + 1000) << 52));
+  return fma(th, p, th) * 0x1.0p-1000;
+}
+
+template <bool NEED_EM>
+__device__ __forceinline__ double exp_neg(double t, double& em) {
+  const double kd = fma(t, 0x1.71547652b82fep+5, 0x1.8p52);
+  const int k = __double2loint(kd);
+  const double kf = kd - 0x1.8p52;
+  double r = fma(-kf, 0x1.62e42fefa4000p-6, t);
+  r = fma(-kf, -0x1.8432a1b0e2634p-48, r);
+  const double r2 = r * r;
+  double q = 0x1.a01a01a01a01ap-13;
+  q = fma(q, r, 0x1.6c16c16c16c17p-10);
+  q = fma(q, r, 0x1.1111111111111p-7);
+  q = fma(q, r, 0x1.5555555555555p-5);
+  q = fma(q, r, 0x1.5555555555555p-3);
+  q = fma(q, r, 0x1.0000000000000p-1);
+  const double p = fma(r2, q, r);                 // e^r - 1
+  const int j = k & 31, m = k >> 5;
+  double th = __ldg(&kExp2TabHi[j]), tl = __ldg(&kExp2TabLo[j]);
+  double y;
+  if (m >= -960) {                                 // 2^m T_hi and 2^m T_lo stay normal numbers
+    const long long sh = (long long)m << 52;
+    th = __longlong_as_double(__double_as_longlong(th) + sh);
+    tl = tl == 0.0 ? 0.0 : __longlong_as_double(__double_as_longlong(tl) + sh);
+    const double c = fma(th, p, tl);
+    y = th + c;
+    if (NEED_EM) em = (th - 1.0) + c;
+  } else {
+    y = exp_neg_deep_tail(th, p, m);               // e^t < 1e-289: a real branch, rarely taken
+    if (NEED_EM) em = y - 1.0;
+  }
+  return y;
+}
+
 // 1/d: hardware estimate refined by one third-order Newton-Raphson step,
 // r <- r (1 + e + e^2), e = 1 - d r  (error e^3).
 __device__ __forceinline__ double rcp(double d) {

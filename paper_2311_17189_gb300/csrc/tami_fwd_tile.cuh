@@ -118,6 +118,67 @@ __device__ __forceinline__ bool freq_constants(const TableHeader& H, const Table
   return !__syncthreads_or(nonzero);
 }
 
+// Phase 2 for one (sample slot sl, frequency f): the complex reciprocals of the frequency-dependent
+// denominators, the group products R_h and the sum over groups of W_h R_h.  Written without
+// data-dependent selects: on this GPU an FP64 instruction issued with its predicate off still
+// occupies the FP64 pipe, so the first factor of each product is peeled and the imaginary-axis
+// case is a template parameter.  A group without frequency-dependent factors sits first (g2_const).
+template <bool XR_ZERO>
+__device__ __forceinline__ void phase2_sample(const TableHeader& H, const TableView& T, const TileArgs& A, int sl,
+                                              int f, double Xr, const double* AXI, const double* AXI2,
+                                              const double* CB, const double* W, double& vr_out, double& vi_out) {
+  double rc_re[kMaxCplxDens], rc_im[kMaxCplxDens];
+  for (int c = 0; c < H.n_cden; ++c) {
+    const double b = CB[c * kBlock + sl];
+    const double Dr = XR_ZERO ? b : fma(T.cden_a[c], Xr, b);    // D = a X + b
+    const double r = rcp(fma(Dr, Dr, AXI2[c * A.n_f + f]));
+    rc_re[c] = Dr * r;
+    rc_im[c] = -AXI[c * A.n_f + f] * r;
+  }
+  double vr = H.g2_const ? W[sl] : 0.0, vi = 0.0;
+  for (int hg = H.g2_const; hg < H.n_g2; ++hg) {
+    const double w = W[hg * kBlock + sl];
+    const int q0 = T.g2[hg], q1 = T.g2[hg + 1];
+    int c = T.g2cd[2 * q0];
+    double Rr = rc_re[c], Ri = rc_im[c];
+    for (int pw = T.g2cd[2 * q0 + 1]; pw > 1; --pw) {
+      const double nr = fma(Rr, rc_re[c], -Ri * rc_im[c]);
+      Ri = fma(Rr, rc_im[c], Ri * rc_re[c]);
+      Rr = nr;
+    }
+    for (int q = q0 + 1; q < q1; ++q) {
+      c = T.g2cd[2 * q];
+      const double ar = rc_re[c], ai = rc_im[c];
+      for (int pw = T.g2cd[2 * q + 1]; pw > 0; --pw) {
+        const double nr = fma(Rr, ar, -Ri * ai);
+        Ri = fma(Rr, ai, Ri * ar);
+        Rr = nr;
+      }
+    }
+    vr = fma(w, Rr, vr);
+    vi = fma(w, Ri, vi);
+  }
+  vr_out = vr;
+  vi_out = vi;
+}
+
+template <bool XR_ZERO>
+__device__ __forceinline__ void phase2_loop(const TableHeader& H, const TableView& T, const TileArgs& A, long long s0,
+                                            const double* Xs, const double* AXI, const double* AXI2, const double* CB,
+                                            const double* W, const FreqMap& M, double (*acc)[4]);
+
+__device__ __forceinline__ void phase2_store(const TileArgs& A, int f, long long s, double vr, double vi,
+                                             double* acc) {
+  if (A.per_sample) {
+    double2* o = reinterpret_cast<double2*>(A.per_sample) + (size_t)f * A.n + s;
+    *o = make_double2(vr, vi);
+  }
+  acc[0] += vr;
+  acc[1] += vi;
+  acc[2] = fma(vr, vr, acc[2]);
+  acc[3] = fma(vi, vi, acc[3]);
+}
+
 // Shared memory per tile: X [n_f][2] (filled by the caller), AXI and AXI2 [n_cden][n_f] (from
 // freq_constants), CB [n_cden][kBlock], W [n_g2][kBlock].
 template <bool ENERGY_IN>
@@ -163,11 +224,11 @@ __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& 
       }
       double fv[kMaxFermiValues];
       for (int b = 0; b < H.n_fbase; ++b) {
-        // y = e^{-beta|x|} keeps the tails exact; 1 - y = -expm1 only where a Bose form needs it
+        // y = e^{-beta|x|} keeps the tails exact; 1 - y = -(e^t - 1) only where a Bose form needs it
         const double xv = x[T.fbase[4 * b]];
         const double nt = -beta * fabs(xv);
-        const double y = exp(nt);
-        const double em = T.fbase[4 * b + 3] ? expm1(nt) : 0.0;
+        double em = 0.0;
+        const double y = T.fbase[4 * b + 3] ? exp_neg<true>(nt, em) : exp_neg<false>(nt, em);
         int cur_sigma = 0;
         double g = 0.0, hh = 0.0;
         for (int v = T.fbase[4 * b + 1]; v < T.fbase[4 * b + 2]; ++v) {
@@ -178,7 +239,8 @@ __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& 
             const double t2 = (sigma > 0 ? y : -y) * rD;
             if (xv <= 0.0) { g = rD; hh = t2; } else { g = t2; hh = rD; }
           }
-          fv[v] = sign > 0 ? fermi_poly(k, g, hh, beta) : fermi_poly(k, hh, g, beta);
+          const double gg = sign > 0 ? g : hh, hg = sign > 0 ? hh : g;   // g(-x) = h(x)
+          fv[v] = fermi_poly(k, gg, hg, beta);
         }
       }
       double rr[kMaxRealDens];
@@ -204,53 +266,34 @@ __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& 
   }
   __syncthreads();
   // ---------------------------------------------------------------- phase 2 ((f, s) pairs)
+  if (xr_zero) phase2_loop<true>(H, T, A, s0, Xs, AXI, AXI2, CB, W, M, acc);
+  else phase2_loop<false>(H, T, A, s0, Xs, AXI, AXI2, CB, W, M, acc);
+  __syncthreads();
+}
+
+// Two samples per iteration give the FP64 pipe two independent dependency chains; the sums are
+// still taken sample by sample, in the same order.
+template <bool XR_ZERO>
+__device__ __forceinline__ void phase2_loop(const TableHeader& H, const TableView& T, const TileArgs& A, long long s0,
+                                            const double* Xs, const double* AXI, const double* AXI2, const double* CB,
+                                            const double* W, const FreqMap& M, double (*acc)[4]) {
   for (int fi = 0; fi < M.nf; ++fi) {
     const int f = M.f0 + fi * M.fstep;
     const double Xr = Xs[2 * f];
-    for (int sl = M.s0; sl < kBlock; sl += M.sstep) {
-      const long long s = s0 + sl;
-      if (s >= A.n) break;
-      double rc_re[kMaxCplxDens], rc_im[kMaxCplxDens];
-      for (int c = 0; c < H.n_cden; ++c) {
-        const double b = CB[c * kBlock + sl];
-        const double Dr = xr_zero ? b : fma(T.cden_a[c], Xr, b);    // D = a X + b
-        const double r = rcp(fma(Dr, Dr, AXI2[c * A.n_f + f]));
-        rc_re[c] = Dr * r;
-        rc_im[c] = -AXI[c * A.n_f + f] * r;
-      }
-      double vr = 0.0, vi = 0.0;
-      for (int hg = 0; hg < H.n_g2; ++hg) {
-        const double w = W[hg * kBlock + sl];
-        const int q0 = T.g2[hg], q1 = T.g2[hg + 1];
-        if (q0 == q1) { vr += w; continue; }
-        double Rr = 1.0, Ri = 0.0;
-        bool first = true;
-        for (int q = q0; q < q1; ++q) {
-          const int c = T.g2cd[2 * q];
-          const double ar = rc_re[c], ai = rc_im[c];
-          for (int pw = T.g2cd[2 * q + 1]; pw > 0; --pw) {
-            if (first) { Rr = ar; Ri = ai; first = false; }
-            else {
-              const double nr = fma(Rr, ar, -Ri * ai);
-              Ri = fma(Rr, ai, Ri * ar);
-              Rr = nr;
-            }
-          }
-        }
-        vr = fma(w, Rr, vr);
-        vi = fma(w, Ri, vi);
-      }
-      if (A.per_sample) {
-        double2* o = reinterpret_cast<double2*>(A.per_sample) + (size_t)f * A.n + s;
-        *o = make_double2(vr, vi);
-      }
-      acc[fi][0] += vr;
-      acc[fi][1] += vi;
-      acc[fi][2] = fma(vr, vr, acc[fi][2]);
-      acc[fi][3] = fma(vi, vi, acc[fi][3]);
+    int sl = M.s0;
+    for (; sl + M.sstep < kBlock && s0 + sl + M.sstep < A.n; sl += 2 * M.sstep) {
+      double ar, ai, br, bi;
+      phase2_sample<XR_ZERO>(H, T, A, sl, f, Xr, AXI, AXI2, CB, W, ar, ai);
+      phase2_sample<XR_ZERO>(H, T, A, sl + M.sstep, f, Xr, AXI, AXI2, CB, W, br, bi);
+      phase2_store(A, f, s0 + sl, ar, ai, acc[fi]);
+      phase2_store(A, f, s0 + sl + M.sstep, br, bi, acc[fi]);
+    }
+    for (; sl < kBlock && s0 + sl < A.n; sl += M.sstep) {
+      double ar, ai;
+      phase2_sample<XR_ZERO>(H, T, A, sl, f, Xr, AXI, AXI2, CB, W, ar, ai);
+      phase2_store(A, f, s0 + sl, ar, ai, acc[fi]);
     }
   }
-  __syncthreads();
 }
 
 // Sum the per-thread accumulators of the block in a fixed order into out[n_f][4].

@@ -294,6 +294,21 @@ int flatten(tami_diagram* d) {
     if (!g2_id.count(ft[i].cd)) { g2_id[ft[i].cd] = (int)g2s.size(); g2s.push_back(ft[i].cd); }
     g1map[{ft[i].cd, ft[i].rd}].push_back((int)i);
   }
+  // the group without frequency-dependent factors (if any) goes first: the kernels add its weight
+  // without a product
+  int g2_const = 0;
+  for (size_t g = 0; g < g2s.size(); ++g)
+    if (g2s[g].empty()) {
+      if (g != 0) {
+        std::swap(g2s[0], g2s[g]);
+        for (auto& kv : g2_id) {
+          if (kv.second == 0) kv.second = (int)g;
+          else if (kv.second == (int)g) kv.second = 0;
+        }
+      }
+      g2_const = 1;
+      break;
+    }
   struct G1 { int g2; std::vector<std::pair<int, int>> rd; std::vector<int> terms; };
   std::vector<G1> g1s;
   for (auto& kv : g1map) g1s.push_back({g2_id[kv.first.first], kv.first.second, kv.second});
@@ -383,6 +398,7 @@ int flatten(tami_diagram* d) {
   for (auto& g : g2s) ng2cd += (int)g.size();
   h.n_g1rd = ng1rd;
   h.n_g2 = (int)g2s.size(); h.n_g2cd = ng2cd;
+  h.g2_const = g2_const;
   h.max_der = max_der;
   Blob B;
   h.off_alpha = B.reserve(sizeof(double) * N * nv);
@@ -402,6 +418,7 @@ int flatten(tami_diagram* d) {
   h.off_g1rd = B.reserve(sizeof(int) * 2 * ng1rd);
   h.off_g2 = B.reserve(sizeof(int) * (h.n_g2 + 1));
   h.off_g2cd = B.reserve(sizeof(int) * 2 * ng2cd);
+  h.off_g2cd_p = B.reserve(sizeof(double) * ng2cd);
   B.reserve(16);
   h.bytes = (int)B.b.size();
 
@@ -466,6 +483,7 @@ int flatten(tami_diagram* d) {
       for (auto& pr : g2s[g]) {
         B.at<int>(h.off_g2cd)[2 * pos] = pr.first;
         B.at<int>(h.off_g2cd)[2 * pos + 1] = pr.second;
+        B.at<double>(h.off_g2cd_p)[pos] = (double)pr.second;
         ++pos;
       }
     }
@@ -486,8 +504,8 @@ int flatten(tami_diagram* d) {
   I.n_groups_fixed = h.n_g1; I.n_groups_freq = h.n_g2;
   I.table_bytes = h.bytes;
   const int m = nv - 1;
-  // Counts follow the kernel: fma = 2 flops, mul/add = 1, expm1 = 1, the reciprocal
-  // (estimate + one third-order Newton step) = 3 fma.
+  // Counts follow the kernel: fma = 2 flops, mul/add = 1, the reciprocal (estimate + one
+  // third-order Newton step) = 3 fma, the table-driven exponential 10 fma + 3 add/mul.
   double fl = 0.0;
   fl += 3.0 * 2 * m;                                    // u -> k: mul + fma per component
   for (int j : repl) {
@@ -500,7 +518,7 @@ int flatten(tami_diagram* d) {
   for (int b = 0; b < h.n_fbase; ++b) {
     std::set<int> sig;
     for (int v = fbase_begin[b]; v < fbase_end[b]; ++v) sig.insert(fvs[v].sigma);
-    fl += 2.0 + (sig.count(-1) ? 1.0 : 0.0);            // -beta|x|, exp, expm1 (Bose forms)
+    fl += 1.0 + 23.0 + (sig.count(-1) ? 2.0 : 0.0);     // -beta|x|; e^t (10 fma, 3 add/mul); e^t - 1
     fl += 8.0 * sig.size();                             // D, reciprocal, +-y / D
     for (int v = fbase_begin[b]; v < fbase_end[b]; ++v) {
       const int k = fvs[v].k;

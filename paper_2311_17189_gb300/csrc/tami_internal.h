@@ -59,6 +59,7 @@ struct TableHeader {
   int n_g1, n_ops, n_leaves, n_g1rd;
   int max_depth, max_closes;   // pole-tree depth (= m) and most CLOSE ops in one group
   int n_g2, n_g2cd;
+  int g2_const;     // 1 if group 0 of phase 2 has no frequency-dependent factor (R = 1)
   int max_der;
   int bytes;
   // offsets
@@ -79,6 +80,7 @@ struct TableHeader {
   int off_g1rd;       // int32 [n_g1rd][2]       real-den index, power
   int off_g2;         // int32 [n_g2+1]          complex-den offsets
   int off_g2cd;       // int32 [n_g2cd][2]       complex-den index, power
+  int off_g2cd_p;     // double [n_g2cd]          the same powers as doubles
 };
 
 }  // namespace tami
