@@ -105,13 +105,14 @@ void sample_momentum(uint64_t seed, uint64_t s, int l, double* kx, double* ky) {
 }
 
 // cos and sin by Cody-Waite reduction by pi (three-part constant), k = n pi + r with
-// |r| <= pi/2, then Taylor series in r (terms to r^24 for cos and r^25 for sin: truncation
-// < 3e-22) and the sign (-1)^n.
+// |r| <= pi/2 (n the nearest integer to k/pi), then Taylor series in r (terms to r^24 for cos
+// and r^25 for sin: truncation < 3e-22) and the sign (-1)^n.
 void cw_sincos(double k, double* s_out, double* c_out) {
   const double inv_pi = 0x1.45f306dc9c883p-2;
   const double P1 = 0x1.921fb54442d18p+1, P2 = 0x1.1a62633145c07p-53,
                P3 = -0x1.f1976b7ed8fbcp-109;
-  double n = std::nearbyint(k * inv_pi);
+  // n = nearest integer to k/pi: k/pi + 1.5*2^52 rounded once leaves it in the low bits
+  double n = std::fma(k, inv_pi, 0x1.8p52) - 0x1.8p52;
   double r = std::fma(-n, P1, k);
   r = std::fma(-n, P2, r);
   r = std::fma(-n, P3, r);

@@ -129,12 +129,15 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
   double* red = AXI2 + H.n_cden * n_f;       // [4 warps][2 n_f + 3]
   for (int i = tid; i < 2 * n_f; i += kBlock) { Xs[i] = P.X[i]; Gs[i] = P.G[i]; }
 
-  const double* alpha = reinterpret_cast<const double*>(smem + H.off_alpha);
   const int* repl = reinterpret_cast<const int*>(smem + H.off_repl);
+  const int* lm_ptr = reinterpret_cast<const int*>(smem + H.off_lm_ptr);
+  const int* lm_l = reinterpret_cast<const int*>(smem + H.off_lm_l);
+  const double* lm_c = reinterpret_cast<const double*>(smem + H.off_lm_c);
+  const double* rep_aext = reinterpret_cast<const double*>(smem + H.off_rep_aext);
   const int* combo_ptr = reinterpret_cast<const int*>(smem + H.off_combo_ptr);
   const int* combo_j = reinterpret_cast<const int*>(smem + H.off_combo_j);
   const double* combo_c = reinterpret_cast<const double*>(smem + H.off_combo_c);
-  const int* fbase = reinterpret_cast<const int*>(smem + H.off_fbase);
+  const int* fseg = reinterpret_cast<const int*>(smem + H.off_fseg);
   const int* fvr = reinterpret_cast<const int*>(smem + H.off_fv);
   const int* rden = reinterpret_cast<const int*>(smem + H.off_rden);
   const int* cden = reinterpret_cast<const int*>(smem + H.off_cden);
@@ -184,9 +187,11 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
     for (int r = 0; r < H.n_rep; ++r) {
       const int j = repl[r];
       double ax = 0.0, ay = 0.0;
-      for (int l = 0; l < H.nv; ++l) {
-        const double cf = alpha[j * H.nv + l];
-        if (cf != 0.0) { ax = fma(cf, kx[l], ax); ay = fma(cf, ky[l], ay); }
+      for (int q = lm_ptr[r]; q < lm_ptr[r + 1]; ++q) {
+        const double cf = lm_c[q];
+        const int l = lm_l[q];
+        ax = fma(cf, kx[l], ax);
+        ay = fma(cf, ky[l], ay);
       }
       double sx, cx, sy, cy;
       cw_sincos(ax, sx, cx);
@@ -201,26 +206,8 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
       x[u] = v;
     }
     double fv[kBwFv], fvd[kBwFv];
-    for (int b = 0; b < H.n_fbase; ++b) {
-      const double xv = x[fbase[4 * b]];
-      const double nt = -beta * fabs(xv);
-      double em = 0.0;
-      const double y = fbase[4 * b + 3] ? exp_neg<true>(nt, em) : exp_neg<false>(nt, em);
-      int cur_sigma = 0;
-      double g = 0.0, hh = 0.0;
-      for (int v = fbase[4 * b + 1]; v < fbase[4 * b + 2]; ++v) {
-        const int sigma = fvr[4 * v], sign = fvr[4 * v + 1], k = fvr[4 * v + 2];
-        if (sigma != cur_sigma) {
-          cur_sigma = sigma;
-          const double rD = rcp(sigma > 0 ? 1.0 + y : -em);
-          const double t2 = (sigma > 0 ? y : -y) * rD;
-          if (xv <= 0.0) { g = rD; hh = t2; } else { g = t2; hh = rD; }
-        }
-        const double gg = sign > 0 ? g : hh, hg = sign > 0 ? hh : g;
-        fv[v] = fermi_poly(k, gg, hg, beta);
-        fvd[v] = fermi_poly(k + 1, gg, hg, beta);
-      }
-    }
+    for (int b = 0; b < H.n_fseg_bose; ++b) fermi_segment<true, true>(fseg + 8 * b, fvr, x, beta, fv, fvd);
+    for (int b = H.n_fseg_bose; b < H.n_fseg; ++b) fermi_segment<false, true>(fseg + 8 * b, fvr, x, beta, fv, fvd);
     double rr[kBwRden];
     for (int i = 0; i < H.n_rden; ++i) rr[i] = rcp(x[rden[2 * i]]);
     double W1[kBwG1], W2[kBwG2];
@@ -229,13 +216,12 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
       double ft;
       {
         double acc[kMaxDepth + 1];
-        acc[0] = 0.0;
         for (int o = g1[4 * gi]; o < g1[4 * gi + 1]; ++o) {
           const int2 op = ops[o];
-          const int kind = op.x & 3, dd = (op.x >> 2) & 63;
-          if (kind == kOpOpen) acc[dd] = 0.0;
-          else if (kind == kOpClose) acc[dd - 1] = fma(fv[op.y], acc[dd], acc[dd - 1]);
-          else acc[dd - 1] = fma(fv[op.y], leafA[op.x >> 8], acc[dd - 1]);
+          const int dd = op.x & 63;
+          const double operand = (op.x & kOpLeaf) ? leafA[op.x >> 8] : acc[dd];
+          const double addend = (op.x & kOpFirst) ? 0.0 : acc[dd - 1];
+          acc[dd - 1] = fma(fv[op.y], operand, addend);
         }
         ft = acc[0];
       }
@@ -279,44 +265,44 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
       }
       const double ftbar = wb * RR;
       // pole tree, reverse: recompute each inner node's subtree value (cv), then walk the program
-      // backwards: CLOSE(d,F): Fbar += acc[d] accbar[d-1], accbar[d] = F accbar[d-1];
-      // LEAFCLOSE(d,F,A): Fbar += A accbar[d-1]
+      // backwards; for the edge acc[d-1] = F * operand + addend:
+      //   Fbar += operand * accbar[d-1],  accbar[d] = F * accbar[d-1]  (read only below inner edges)
       const int o0 = g1[4 * gi], o1 = g1[4 * gi + 1];
       double cv[kBwCloses];
       {
         double acc[kMaxDepth + 1];
-        acc[0] = 0.0;
         int nc = 0;
         for (int o = o0; o < o1; ++o) {
           const int2 op = ops[o];
-          const int kind = op.x & 3, dd = (op.x >> 2) & 63;
-          if (kind == kOpOpen) acc[dd] = 0.0;
-          else if (kind == kOpClose) { cv[nc++] = acc[dd]; acc[dd - 1] = fma(fv[op.y], acc[dd], acc[dd - 1]); }
-          else acc[dd - 1] = fma(fv[op.y], leafA[op.x >> 8], acc[dd - 1]);
+          const int dd = op.x & 63;
+          const bool leaf = op.x & kOpLeaf;
+          if (!leaf) cv[nc++] = acc[dd];
+          const double operand = leaf ? leafA[op.x >> 8] : acc[dd];
+          const double addend = (op.x & kOpFirst) ? 0.0 : acc[dd - 1];
+          acc[dd - 1] = fma(fv[op.y], operand, addend);
         }
         double bar[kMaxDepth + 1];
         bar[0] = ftbar;
         for (int o = o1 - 1; o >= o0; --o) {
           const int2 op = ops[o];
-          const int kind = op.x & 3, dd = (op.x >> 2) & 63;
-          if (kind == kOpClose) {
-            const double pb = bar[dd - 1];
-            fvbar[op.y] = fma(cv[--nc], pb, fvbar[op.y]);
-            bar[dd] = fv[op.y] * pb;
-          } else if (kind == kOpLeafClose) {
-            fvbar[op.y] = fma(leafA[op.x >> 8], bar[dd - 1], fvbar[op.y]);
-          }
+          const int dd = op.x & 63;
+          const bool leaf = op.x & kOpLeaf;
+          if (!leaf) --nc;
+          const double operand = leaf ? leafA[op.x >> 8] : cv[nc];
+          const double pb = bar[dd - 1];
+          fvbar[op.y] = fma(operand, pb, fvbar[op.y]);
+          bar[dd] = fv[op.y] * pb;
         }
       }
     }
-    for (int bse = 0; bse < H.n_fbase; ++bse) {
-      const int u = fbase[4 * bse];
+    for (int bse = 0; bse < H.n_fseg; ++bse) {
+      const int* sgm = fseg + 8 * bse;
       double acc = 0.0;
-      for (int v = fbase[4 * bse + 1]; v < fbase[4 * bse + 2]; ++v) {
+      for (int v = sgm[2]; v < sgm[4]; ++v) {
         const double d = fvbar[v] * fvd[v];
-        acc += fvr[4 * v + 1] > 0 ? d : -d;
+        acc += fvr[2 * v] > 0 ? d : -d;
       }
-      xbar[u] += acc;
+      xbar[sgm[0]] += acc;
     }
     double Ebar[kMaxLines];
     for (int r = 0; r < H.n_rep; ++r) Ebar[repl[r]] = 0.0;
@@ -327,12 +313,10 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
       const int j = repl[r];
       const double eb = Ebar[j];
       mub += eb;
-      const double ae = alpha[j * H.nv + H.m];
-      if (ae != 0.0) {
-        // dE/dKx = -(2t + 4t' cos Ky) sin Kx,  dK/dk_ext = alpha_ext
-        kxb = fma(-eb * ae, fma(4.0 * P.tp, Cy[j], 2.0 * P.t) * Sx[j], kxb);
-        kyb = fma(-eb * ae, fma(4.0 * P.tp, Cx[j], 2.0 * P.t) * Sy[j], kyb);
-      }
+      const double ae = rep_aext[r];
+      // dE/dKx = -(2t + 4t' cos Ky) sin Kx,  dK/dk_ext = alpha_ext
+      kxb = fma(-eb * ae, fma(4.0 * P.tp, Cy[j], 2.0 * P.t) * Sx[j], kxb);
+      kyb = fma(-eb * ae, fma(4.0 * P.tp, Cx[j], 2.0 * P.t) * Sy[j], kyb);
     }
     gmu += mub;
     gkx += kxb;

@@ -35,19 +35,27 @@ __device__ __forceinline__ double to_momentum(uint32_t hi, uint32_t lo) {
   return fma(u, 2.0 * pi, -pi);
 }
 
-// cos and sin: Cody-Waite reduction by pi (three-part constant), k = n pi + r, |r| <= pi/2, then
+// cos and sin: Cody-Waite reduction by pi (three-part constant), k = n pi + r, |r| <= pi/2 (n the
+// integer nearest to k/pi, from one fma against 1.5 * 2^52), then
 // Taylor series in r (to r^24 for cos, r^25 for sin) and the sign (-1)^n (W. J. Cody and
 // W. Waite, 1980).  Every operation is an explicit fma or a rounded mul intrinsic, so the result
 // is the same on any IEEE machine that follows the same recipe.
-__device__ __forceinline__ double cw_reduce(double k, double& odd_sign) {
+// n = nearest integer to k/pi, read from the low word of k/pi + 1.5 * 2^52 (one rounding);
+// r = k - n pi with a three-part pi; odd = n & 1.
+__device__ __forceinline__ double cw_reduce(double k, int& odd) {
   const double inv_pi = 0x1.45f306dc9c883p-2;
   const double P1 = 0x1.921fb54442d18p+1, P2 = 0x1.1a62633145c07p-53, P3 = -0x1.f1976b7ed8fbcp-109;
-  const double n = rint(__dmul_rn(k, inv_pi));
+  const double nd = fma(k, inv_pi, 0x1.8p52);
+  odd = __double2loint(nd) & 1;
+  const double n = nd - 0x1.8p52;
   double r = fma(-n, P1, k);
   r = fma(-n, P2, r);
   r = fma(-n, P3, r);
-  odd_sign = ((long long)n & 1) ? -1.0 : 1.0;
   return r;
+}
+
+__device__ __forceinline__ double flip_if(double v, int odd) {   // (-1)^odd v, on the sign bit
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)odd << 63));
 }
 
 __device__ __forceinline__ double cw_cos_poly(double z) {
@@ -67,15 +75,14 @@ __device__ __forceinline__ double cw_cos_poly(double z) {
 }
 
 __device__ __forceinline__ double cw_cos(double k) {
-  double sg;
-  const double r = cw_reduce(k, sg);
-  const double c = cw_cos_poly(__dmul_rn(r, r));
-  return sg < 0.0 ? -c : c;
+  int odd;
+  const double r = cw_reduce(k, odd);
+  return flip_if(cw_cos_poly(__dmul_rn(r, r)), odd);
 }
 
 __device__ __forceinline__ void cw_sincos(double k, double& s_out, double& c_out) {
-  double sg;
-  const double r = cw_reduce(k, sg);
+  int odd;
+  const double r = cw_reduce(k, odd);
   const double z = __dmul_rn(r, r);
   const double cr = cw_cos_poly(z);
   double ps = 0x1.3f3ccdd165fa9p-84;
@@ -91,8 +98,8 @@ __device__ __forceinline__ void cw_sincos(double k, double& s_out, double& c_out
   ps = fma(ps, z, 0x1.1111111111111p-7);
   ps = fma(ps, z, -0x1.5555555555555p-3);
   const double sr = fma(__dmul_rn(r, z), ps, r);
-  s_out = sg < 0.0 ? -sr : sr;
-  c_out = sg < 0.0 ? -cr : cr;
+  s_out = flip_if(sr, odd);
+  c_out = flip_if(cr, odd);
 }
 
 // E = mu - eps(k),  eps(k) = -2t(cos kx + cos ky) - 4t' cos kx cos ky
@@ -192,6 +199,36 @@ __device__ __forceinline__ double fermi_poly(int k, double g, double h, double b
   double h2 = h * h, g2 = g * g;
   if (k == 4) return b4 * gh * (h2 * h - 11.0 * g * h2 + 11.0 * g2 * h - g2 * g);
   return -b4 * beta * gh * (h2 * h2 - 26.0 * g * h2 * h + 66.0 * g2 * h2 - 26.0 * g2 * g * h + g2 * g2);
+}
+
+// Fermi values of one segment of the term table: one energy combination x and one sigma, every
+// value g_sigma^(k)(+-x) that the terms use (k = 0 first).  y = e^{-beta|x|} keeps the tails exact;
+// the Bose-type segments (sigma = -1) take 1 - y = -(e^t - 1) from the same exponential.  With
+// DUAL, fvd holds each value's derivative with respect to its own argument (order k + 1).
+// seg = {combo, sigma, v_begin, first v with k >= 1, v_end}; fvr[v] = {sign, k}.
+template <bool BOSE, bool DUAL>
+__device__ __forceinline__ void fermi_segment(const int* seg, const int* fvr, const double* x, double beta,
+                                              double* fv, double* fvd) {
+  const double xv = x[seg[0]];
+  double em = 0.0;
+  const double y = exp_neg<BOSE>(-beta * fabs(xv), em);
+  const double rD = rcp(BOSE ? -em : 1.0 + y);
+  const double t2 = (BOSE ? -y : y) * rD;
+  const bool neg = xv <= 0.0;
+  const double g = neg ? rD : t2, h = neg ? t2 : rD;   // g_sigma(x) and g_sigma(-x)
+  double d1 = 0.0;
+  if (DUAL) d1 = -beta * (g * h);
+  for (int v = seg[2]; v < seg[3]; ++v) {
+    fv[v] = fvr[2 * v] > 0 ? g : h;
+    if (DUAL) fvd[v] = d1;
+  }
+  for (int v = seg[3]; v < seg[4]; ++v) {
+    const bool pos = fvr[2 * v] > 0;
+    const int k = fvr[2 * v + 1];
+    const double gg = pos ? g : h, hg = pos ? h : g;
+    fv[v] = fermi_poly(k, gg, hg, beta);
+    if (DUAL) fvd[v] = fermi_poly(k + 1, gg, hg, beta);
+  }
 }
 
 __host__ __device__ __forceinline__ int align16(int b) { return (b + 15) & ~15; }

@@ -12,12 +12,14 @@ constexpr int kMaxFreqPerThread = 16;  // n_f <= kMaxFreqPerThread * kBlock
 
 // typed views of a staged term table
 struct TableView {
-  const double* alpha;
   const int* repl;
+  const int* lm_ptr;
+  const int* lm_l;
+  const double* lm_c;
   const int* combo_ptr;
   const int* combo_j;
   const double* combo_c;
-  const int* fbase;
+  const int* fseg;
   const int* fvr;
   const int* rden;
   const int* cden;
@@ -33,12 +35,14 @@ struct TableView {
 
 __device__ __forceinline__ TableView table_view(const unsigned char* t, const TableHeader& H) {
   TableView v;
-  v.alpha = reinterpret_cast<const double*>(t + H.off_alpha);
   v.repl = reinterpret_cast<const int*>(t + H.off_repl);
+  v.lm_ptr = reinterpret_cast<const int*>(t + H.off_lm_ptr);
+  v.lm_l = reinterpret_cast<const int*>(t + H.off_lm_l);
+  v.lm_c = reinterpret_cast<const double*>(t + H.off_lm_c);
   v.combo_ptr = reinterpret_cast<const int*>(t + H.off_combo_ptr);
   v.combo_j = reinterpret_cast<const int*>(t + H.off_combo_j);
   v.combo_c = reinterpret_cast<const double*>(t + H.off_combo_c);
-  v.fbase = reinterpret_cast<const int*>(t + H.off_fbase);
+  v.fseg = reinterpret_cast<const int*>(t + H.off_fseg);
   v.fvr = reinterpret_cast<const int*>(t + H.off_fv);
   v.rden = reinterpret_cast<const int*>(t + H.off_rden);
   v.cden = reinterpret_cast<const int*>(t + H.off_cden);
@@ -53,16 +57,17 @@ __device__ __forceinline__ TableView table_view(const unsigned char* t, const Ta
   return v;
 }
 
-// Sum over a group's terms of A_t prod FT factors, by the group's pole-tree program.
+// Sum over a group's terms of A_t prod FT factors, by the group's pole-tree program: one fma per
+// tree edge, acc[d-1] = F * (leaf ? A_leaf : acc[d]) + (first child ? 0 : acc[d-1]); the root's
+// sum ends in acc[0].  Every group has at least one edge.
 __device__ __forceinline__ double pole_tree(const TableView& T, int op0, int op1, const double* fv) {
   double acc[kMaxDepth + 1];
-  acc[0] = 0.0;
   for (int o = op0; o < op1; ++o) {
     const int2 op = T.ops[o];
-    const int kind = op.x & 3, d = (op.x >> 2) & 63;
-    if (kind == kOpOpen) acc[d] = 0.0;
-    else if (kind == kOpClose) acc[d - 1] = fma(fv[op.y], acc[d], acc[d - 1]);
-    else acc[d - 1] = fma(fv[op.y], T.leafA[op.x >> 8], acc[d - 1]);
+    const int d = op.x & 63;
+    const double operand = (op.x & kOpLeaf) ? T.leafA[op.x >> 8] : acc[d];
+    const double addend = (op.x & kOpFirst) ? 0.0 : acc[d - 1];
+    acc[d - 1] = fma(fv[op.y], operand, addend);
   }
   return acc[0];
 }
@@ -207,13 +212,14 @@ __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& 
         kx[H.m] = A.kx;
         ky[H.m] = A.ky;
         for (int r = 0; r < H.n_rep; ++r) {
-          const int j = T.repl[r];
           double ax = 0.0, ay = 0.0;
-          for (int l = 0; l < H.nv; ++l) {
-            const double cf = T.alpha[j * H.nv + l];
-            if (cf != 0.0) { ax = fma(cf, kx[l], ax); ay = fma(cf, ky[l], ay); }
+          for (int q = T.lm_ptr[r]; q < T.lm_ptr[r + 1]; ++q) {
+            const double cf = T.lm_c[q];
+            const int l = T.lm_l[q];
+            ax = fma(cf, kx[l], ax);
+            ay = fma(cf, ky[l], ay);
           }
-          E[j] = line_energy(ax, ay, A.t, A.tp, A.mu);
+          E[T.repl[r]] = line_energy(ax, ay, A.t, A.tp, A.mu);
         }
       }
       double x[kMaxCombos];
@@ -223,26 +229,9 @@ __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& 
         x[u] = v;
       }
       double fv[kMaxFermiValues];
-      for (int b = 0; b < H.n_fbase; ++b) {
-        // y = e^{-beta|x|} keeps the tails exact; 1 - y = -(e^t - 1) only where a Bose form needs it
-        const double xv = x[T.fbase[4 * b]];
-        const double nt = -beta * fabs(xv);
-        double em = 0.0;
-        const double y = T.fbase[4 * b + 3] ? exp_neg<true>(nt, em) : exp_neg<false>(nt, em);
-        int cur_sigma = 0;
-        double g = 0.0, hh = 0.0;
-        for (int v = T.fbase[4 * b + 1]; v < T.fbase[4 * b + 2]; ++v) {
-          const int sigma = T.fvr[4 * v], sign = T.fvr[4 * v + 1], k = T.fvr[4 * v + 2];
-          if (sigma != cur_sigma) {
-            cur_sigma = sigma;
-            const double rD = rcp(sigma > 0 ? 1.0 + y : -em);
-            const double t2 = (sigma > 0 ? y : -y) * rD;
-            if (xv <= 0.0) { g = rD; hh = t2; } else { g = t2; hh = rD; }
-          }
-          const double gg = sign > 0 ? g : hh, hg = sign > 0 ? hh : g;   // g(-x) = h(x)
-          fv[v] = fermi_poly(k, gg, hg, beta);
-        }
-      }
+      for (int b = 0; b < H.n_fseg_bose; ++b) fermi_segment<true, false>(T.fseg + 8 * b, T.fvr, x, beta, fv, nullptr);
+      for (int b = H.n_fseg_bose; b < H.n_fseg; ++b)
+        fermi_segment<false, false>(T.fseg + 8 * b, T.fvr, x, beta, fv, nullptr);
       double rr[kMaxRealDens];
       for (int i = 0; i < H.n_rden; ++i) rr[i] = rcp(x[T.rden[2 * i]]);
       int cur = T.g1_tgt[0];

@@ -275,16 +275,30 @@ int flatten(tami_diagram* d) {
     ft.push_back(std::move(t));
   }
   if (max_der > kMaxDer) { set_error("derivative order above the kernels' limit"); return TAMI_EUNSUPPORTED; }
-  // Fermi bases and values, ordered by combination
-  std::map<int, std::vector<FvKey>> by_base;
-  for (auto& kv : fv_tmp) by_base[kv.first.u].push_back(kv.first);
-  std::vector<int> fbase_combo, fbase_begin, fbase_end;
+  // Fermi segments: one per (combination, sigma), the Bose-type ones (sigma = -1, which need
+  // 1 - e^{-beta|x|}) first; inside a segment the values by derivative order (k = 0 first), then
+  // sign.  The kernels then run plain loops over segments and values, with no data-dependent
+  // branches around FP64 work.
+  struct Seg { int combo, sigma, v0, vk1, v1; };
+  std::map<std::pair<int, int>, std::vector<FvKey>> by_seg;
+  for (auto& kv : fv_tmp) by_seg[{kv.first.sigma < 0 ? 0 : 1, kv.first.u}].push_back(kv.first);
+  std::vector<Seg> segs;
   std::vector<FvKey> fvs;
-  for (auto& kv : by_base) {
-    fbase_combo.push_back(kv.first);
-    fbase_begin.push_back((int)fvs.size());
-    for (auto& k : kv.second) { fv_tmp[k] = (int)fvs.size(); fvs.push_back(k); }
-    fbase_end.push_back((int)fvs.size());
+  int n_bose_seg = 0;
+  for (auto& kv : by_seg) {
+    std::vector<FvKey> list = kv.second;
+    std::sort(list.begin(), list.end(), [](const FvKey& a, const FvKey& b) {
+      return a.k != b.k ? a.k < b.k : a.sign < b.sign; });
+    Seg g{kv.first.second, list[0].sigma, (int)fvs.size(), -1, 0};
+    for (auto& k : list) {
+      if (k.k >= 1 && g.vk1 < 0) g.vk1 = (int)fvs.size();
+      fv_tmp[k] = (int)fvs.size();
+      fvs.push_back(k);
+    }
+    g.v1 = (int)fvs.size();
+    if (g.vk1 < 0) g.vk1 = g.v1;
+    if (g.sigma < 0) ++n_bose_seg;
+    segs.push_back(g);
   }
   // ---- groups: by (complex signature) and within it by (real signature)
   std::map<std::vector<std::pair<int, int>>, int> g2_id;
@@ -343,16 +357,18 @@ int flatten(tami_diagram* d) {
   int nnz = 0;
   for (const Vec& c : combos) for (int j = 0; j < N; ++j) if (c[j]) ++nnz;
   h.combo_nnz = nnz;
-  h.n_fbase = (int)fbase_combo.size();
+  h.n_fseg = (int)segs.size();
+  h.n_fseg_bose = n_bose_seg;
   h.n_fv = (int)fvs.size();
   h.n_rden = (int)rdens.size();
   h.n_cden = (int)cdens.size();
   h.n_g1 = (int)g1s.size();
   // Pole tree (Sec. 2.1, the factorised FT): per group, a trie over each term's Fermi values
   // taken in reverse residue order (last summed variable first); leaves with equal paths merge
-  // their coefficients.  Emitted depth first as a program over a stack of accumulators:
-  //   OPEN(d): acc[d] = 0;  CLOSE(d, F): acc[d-1] += F acc[d];  LEAFCLOSE(d, F, A): acc[d-1] += F A.
-  std::vector<std::pair<int, int>> ops;   // (kind | depth << 2 | leaf << 8, fv)
+  // their coefficients.  Emitted in post order as a program over a stack of accumulators, one
+  // fma per tree edge: for the edge to child c at depth d,
+  //   acc[d-1] = F_c * (c is a leaf ? A_c : acc[d]) + (c is its parent's first child ? 0 : acc[d-1]).
+  std::vector<std::pair<int, int>> ops;   // (d | first << 6 | leaf << 7 | leaf index << 8, fv)
   std::vector<double> leafA;
   std::vector<std::pair<int, int>> g1_ops(g1s.size());
   int max_closes = 0;
@@ -374,15 +390,19 @@ int flatten(tami_diagram* d) {
     }
     const int begin = (int)ops.size();
     int closes = 0;
-    std::function<void(int, int)> emit = [&](int u, int d) {
-      if (d == m_depth) {
-        ops.push_back({kOpLeafClose | (d << 2) | ((int)leafA.size() << 8), nodes[u].fv});
-        leafA.push_back(nodes[u].A);
-        return;
+    std::function<void(int, int)> emit = [&](int u, int d) {   // children of u sit at depth d + 1
+      for (size_t i = 0; i < nodes[u].kids.size(); ++i) {
+        const int c = nodes[u].kids[i];
+        const int first = i == 0 ? 1 : 0;
+        if (d + 1 == m_depth) {
+          ops.push_back({(d + 1) | (first << 6) | (1 << 7) | ((int)leafA.size() << 8), nodes[c].fv});
+          leafA.push_back(nodes[c].A);
+        } else {
+          emit(c, d + 1);
+          ops.push_back({(d + 1) | (first << 6), nodes[c].fv});
+          ++closes;
+        }
       }
-      if (d > 0) ops.push_back({kOpOpen | (d << 2), 0});
-      for (int c : nodes[u].kids) emit(c, d + 1);
-      if (d > 0) { ops.push_back({kOpClose | (d << 2), nodes[u].fv}); ++closes; }
     };
     emit(0, 0);
     g1_ops[g] = {begin, (int)ops.size()};
@@ -392,8 +412,8 @@ int flatten(tami_diagram* d) {
   h.n_leaves = (int)leafA.size();
   h.max_depth = m_depth;
   h.max_closes = max_closes;
-  int ng1rd = 0, ng2cd = 0, n_mul_ops = 0;
-  for (auto& o : ops) if ((o.first & 3) != kOpOpen) ++n_mul_ops;
+  int ng1rd = 0, ng2cd = 0;
+  const int n_mul_ops = (int)ops.size();
   for (auto& g : g1s) ng1rd += (int)g.rd.size();
   for (auto& g : g2s) ng2cd += (int)g.size();
   h.n_g1rd = ng1rd;
@@ -401,13 +421,20 @@ int flatten(tami_diagram* d) {
   h.g2_const = g2_const;
   h.max_der = max_der;
   Blob B;
+  int n_lm = 0;
+  for (int j : repl) for (int l = 0; l < nv; ++l) if (d->alpha[j * nv + l]) ++n_lm;
+  h.n_lm = n_lm;
   h.off_alpha = B.reserve(sizeof(double) * N * nv);
   h.off_repl = B.reserve(sizeof(int) * h.n_rep);
+  h.off_lm_ptr = B.reserve(sizeof(int) * (h.n_rep + 1));
+  h.off_lm_l = B.reserve(sizeof(int) * n_lm);
+  h.off_lm_c = B.reserve(sizeof(double) * n_lm);
+  h.off_rep_aext = B.reserve(sizeof(double) * h.n_rep);
   h.off_combo_ptr = B.reserve(sizeof(int) * (h.n_combo + 1));
   h.off_combo_j = B.reserve(sizeof(int) * nnz);
   h.off_combo_c = B.reserve(sizeof(double) * nnz);
-  h.off_fbase = B.reserve(sizeof(int) * 4 * h.n_fbase);
-  h.off_fv = B.reserve(sizeof(int) * 4 * h.n_fv);
+  h.off_fseg = B.reserve(sizeof(int) * 8 * h.n_fseg);
+  h.off_fv = B.reserve(sizeof(int) * 2 * h.n_fv);
   h.off_rden = B.reserve(sizeof(int) * 2 * h.n_rden);
   h.off_cden = B.reserve(sizeof(int) * 2 * h.n_cden);
   h.off_cden_a = B.reserve(sizeof(double) * h.n_cden);
@@ -425,6 +452,21 @@ int flatten(tami_diagram* d) {
   for (int j = 0; j < N * nv; ++j) B.at<double>(h.off_alpha)[j] = (double)d->alpha[j];
   for (int i = 0; i < h.n_rep; ++i) B.at<int>(h.off_repl)[i] = repl[i];
   {
+    int q = 0;
+    for (int r = 0; r < h.n_rep; ++r) {
+      const int j = repl[r];
+      B.at<int>(h.off_lm_ptr)[r] = q;
+      for (int l = 0; l < nv; ++l)
+        if (d->alpha[j * nv + l]) {
+          B.at<int>(h.off_lm_l)[q] = l;
+          B.at<double>(h.off_lm_c)[q] = (double)d->alpha[j * nv + l];
+          ++q;
+        }
+      B.at<double>(h.off_rep_aext)[r] = (double)d->alpha[j * nv + nv - 1];
+    }
+    B.at<int>(h.off_lm_ptr)[h.n_rep] = q;
+  }
+  {
     int k = 0;
     for (int u = 0; u < h.n_combo; ++u) {
       B.at<int>(h.off_combo_ptr)[u] = k;
@@ -437,14 +479,13 @@ int flatten(tami_diagram* d) {
     }
     B.at<int>(h.off_combo_ptr)[h.n_combo] = k;
   }
-  for (int b = 0; b < h.n_fbase; ++b) {
-    int* r = B.at<int>(h.off_fbase) + 4 * b;
-    r[0] = fbase_combo[b]; r[1] = fbase_begin[b]; r[2] = fbase_end[b]; r[3] = 0;
-    for (int v = fbase_begin[b]; v < fbase_end[b]; ++v) if (fvs[v].sigma < 0) r[3] = 1;
+  for (int g = 0; g < h.n_fseg; ++g) {
+    int* r = B.at<int>(h.off_fseg) + 8 * g;
+    r[0] = segs[g].combo; r[1] = segs[g].sigma; r[2] = segs[g].v0; r[3] = segs[g].vk1; r[4] = segs[g].v1;
   }
   for (int v = 0; v < h.n_fv; ++v) {
-    int* r = B.at<int>(h.off_fv) + 4 * v;
-    r[0] = fvs[v].sigma; r[1] = fvs[v].sign; r[2] = fvs[v].k; r[3] = 0;
+    int* r = B.at<int>(h.off_fv) + 2 * v;
+    r[0] = fvs[v].sign; r[1] = fvs[v].k;
   }
   for (int i = 0; i < h.n_rden; ++i) {
     int* r = B.at<int>(h.off_rden) + 2 * i;
@@ -508,19 +549,13 @@ int flatten(tami_diagram* d) {
   // third-order Newton step) = 3 fma, the table-driven exponential 10 fma + 3 add/mul.
   double fl = 0.0;
   fl += 3.0 * 2 * m;                                    // u -> k: mul + fma per component
-  for (int j : repl) {
-    int nz = 0;
-    for (int l = 0; l < nv; ++l) if (d->alpha[j * nv + l]) ++nz;
-    fl += 2.0 * 2.0 * nz;                               // line momenta, fma per term and dimension
-    fl += 2.0 * 33.0 + 6.0;                             // cos of both components, energy
-  }
+  fl += 2.0 * 2.0 * n_lm;                               // line momenta, fma per nonzero label and dimension
+  fl += h.n_rep * (2.0 * 34.0 + 6.0);                   // cos of both components, energy
   fl += 2.0 * nnz;                                      // energy combinations
-  for (int b = 0; b < h.n_fbase; ++b) {
-    std::set<int> sig;
-    for (int v = fbase_begin[b]; v < fbase_end[b]; ++v) sig.insert(fvs[v].sigma);
-    fl += 1.0 + 23.0 + (sig.count(-1) ? 2.0 : 0.0);     // -beta|x|; e^t (10 fma, 3 add/mul); e^t - 1
-    fl += 8.0 * sig.size();                             // D, reciprocal, +-y / D
-    for (int v = fbase_begin[b]; v < fbase_end[b]; ++v) {
+  for (const Seg& g : segs) {
+    fl += 1.0 + 23.0 + (g.sigma < 0 ? 2.0 : 0.0);       // -beta|x|; e^t (10 fma, 3 add/mul); e^t - 1
+    fl += 8.0;                                          // D, reciprocal, +-y / D
+    for (int v = g.v0; v < g.v1; ++v) {
       const int k = fvs[v].k;
       fl += k == 0 ? 0.0 : k == 1 ? 2.0 : k == 2 ? 5.0 : k == 3 ? 9.0 : 16.0 + 4.0 * k;
     }
@@ -551,10 +586,7 @@ int flatten(tami_diagram* d) {
   }
   // pole tree in the adjoint: recompute (fma per edge), then per edge an fma into the Fermi-value
   // adjoint and, for inner edges, a mul for the child's adjoint
-  for (auto& o : ops) {
-    const int kind = o.first & 3;
-    bl += kind == kOpClose ? 2.0 + 3.0 : kind == kOpLeafClose ? 2.0 + 2.0 : 0.0;
-  }
+  bl += 2.0 * ops.size() + 3.0 * ops.size();            // recompute, then fma + mul per edge
   bl += 3.0 * h.n_fv + 2.0 * nnz + 10.0 * h.n_rep;     // fvbar -> x -> E -> (mu, k_ext)
   I.bwd_flops_per_sample = bl;
   double bf = 12.0 * h.n_cden + 12.0 * h.n_cden + 2.0;  // reciprocals, Z, dv/dX and b-adjoints, accX

@@ -22,8 +22,8 @@ constexpr int kMaxCplxDens = 64;
 constexpr int kMaxDer = 5;
 constexpr int kMaxDepth = kMaxVars;   // pole-tree depth = number of summed variables
 
-// pole-tree program ops (see flatten): acc[d] = 0 / acc[d-1] += F * acc[d] / acc[d-1] += F * A_leaf
-enum { kOpOpen = 0, kOpClose = 1, kOpLeafClose = 2 };
+// pole-tree program op (see flatten): acc[d-1] = F * (leaf ? A_leaf : acc[d]) + (first ? 0 : acc[d-1])
+enum { kOpFirst = 1 << 6, kOpLeaf = 1 << 7 };
 
 void set_error(const std::string& msg);
 
@@ -54,7 +54,8 @@ struct TableHeader {
   int N, nv, m;
   int n_rep;        // lines whose energy is computed (first line of each momentum label)
   int n_combo, combo_nnz;
-  int n_fbase, n_fv;
+  int n_fseg, n_fseg_bose, n_fv;   // Fermi segments (Bose-type first) and values
+  int n_lm;                         // nonzero momentum labels of the representative lines
   int n_rden, n_cden;
   int n_g1, n_ops, n_leaves, n_g1rd;
   int max_depth, max_closes;   // pole-tree depth (= m) and most CLOSE ops in one group
@@ -65,17 +66,22 @@ struct TableHeader {
   // offsets
   int off_alpha;      // double [N][nv]
   int off_repl;       // int32 [n_rep]            rep lines
+  int off_lm_ptr;     // int32 [n_rep+1]         nonzero labels per rep line (CSR)
+  int off_lm_l;       // int32 [n_lm]             variable index, ascending
+  int off_lm_c;       // double [n_lm]            label
+  int off_rep_aext;   // double [n_rep]           external label of each rep line
   int off_combo_ptr;  // int32 [n_combo+1]
   int off_combo_j;    // int32 [combo_nnz]        base-energy index, ascending per combo
   int off_combo_c;    // double [combo_nnz]       coefficient
-  int off_fbase;      // int32 [n_fbase][4]      combo, fv_begin, fv_end, needs 1 - y
-  int off_fv;         // int32 [n_fv][4]         sigma, sign, k, unused
+  int off_fseg;       // int32 [n_fseg][8]       combo, sigma, v_begin, first v with k >= 1, v_end
+  int off_fv;         // int32 [n_fv][2]         sign, k
   int off_rden;       // int32 [n_rden][2]       combo, sign
   int off_cden;       // int32 [n_cden][2]       combo, sign
   int off_cden_a;     // double [n_cden]          external-frequency coefficient
   int off_g1;         // int32 [n_g1][4]         op_begin, op_end, rd_begin, rd_end
   int off_g1_tgt;     // int32 [n_g1]             frequency group it feeds (ascending)
-  int off_ops;        // int2 [n_ops]            pole-tree program: x = kind | depth<<2 | leaf<<8, y = Fermi value
+  int off_ops;        // int2 [n_ops]            pole-tree program: x = d | first<<6 | leaf<<7 | leaf index<<8,
+                      //                         y = Fermi value
   int off_leafA;      // double [n_leaves]        merged coefficients of the leaves
   int off_g1rd;       // int32 [n_g1rd][2]       real-den index, power
   int off_g2;         // int32 [n_g2+1]          complex-den offsets
