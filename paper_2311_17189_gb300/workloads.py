@@ -58,6 +58,27 @@ ORDER3_REAL = dict(
     omega=(-4.0, 4.0, 256), gamma=0.05, n_samples=1 << 22, seed=SEED,
 )
 
+# Large order: the order-5 diagram with the largest flat term table among the project's
+# enumerated order-5 diagrams (744 terms; lowest enumeration index among equals; the multipole
+# residues there need Fermi derivatives up to first order).  t=1, t'=0, mu=0, one frequency
+# i pi/beta, 2^26 samples at each beta in (2, 5, 10, 20); forward and adjoint.
+ORDER5 = dict(
+    name="order5_hubbard_sigma",
+    order=5,
+    code=(0, 1, 1, 5, 2, 3, 3, 4, 4, 2, 0),
+    t=1.0, tp=0.0, mu=0.0, betas=(2.0, 5.0, 10.0, 20.0), U=1.0, kext=(PI / 2, PI / 2),
+    n_freq=1, n_samples=1 << 26, seed=SEED,
+)
+
+# The paper's evaluation example at its own size (Sec. 5.1): the order-2 integrand of Sec. 5
+# (frequency labels (1,0,0), (0,1,0), (-1,1,1), identity energies) on 10^6 rows of energies
+# uniform on (-8, 8) and 100 fermionic Matsubara frequencies, beta = 1.
+ENERGY_X1 = dict(
+    name="energy_input_order2_x1",
+    alpha=np.array([[1, 0, 0], [0, 1, 0], [-1, 1, 1]], dtype=np.int32),
+    a=8.0, beta=1.0, n_freq=100, n_e=1_000_000, seed=SEED,
+)
+
 # Every order-2..5 diagram in one launch: diagram d gets 2^(20 + d mod 4) samples, 32 freqs.
 ALL_ORDERS = dict(
     name="sigma_orders_2_to_5",

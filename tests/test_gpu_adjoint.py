@@ -42,11 +42,20 @@ CASES = [
     ("order3_real_axis", 3, 0, (1.0, 0.0, 0.0, np.pi / 2, np.pi / 2), 10.0, W.real_axis(-4.0, 4.0, 7, 0.05)),
     ("order4_matsubara", 4, 2, (1.0, -0.3, -0.5, np.pi / 2, np.pi / 2), 8.0, W.matsubara(8.0, 5)),
     ("order5_real_axis", 5, 7, (1.0, -0.2, 0.1, np.pi / 2, np.pi / 3), 5.0, W.real_axis(-2.0, 2.0, 3, 0.1)),
+    # four lines with one momentum label: a fourth-order pole, so the forward needs f^(3) and the
+    # adjoint f^(4); the external variable bosonic
+    ("quadruple_pole", dict(alpha=[[1, 0], [1, 0], [1, 0], [1, 0], [1, 1]],
+                            eps=[[1, 0, 0, 0, 0]] * 4 + [[0, 0, 0, 0, 1]], boson=[0, 1]), None,
+     (1.0, -0.3, 0.2, np.pi / 3, np.pi / 5), 2.0, W.real_axis(-3.0, 3.0, 5, 0.1)),
 ]
 
 
 def setup_case(case):
     name, order, idx, lat, beta, X = case
+    if isinstance(order, dict):
+        D, S = both(np.array(order["alpha"]), np.array(order["eps"]), boson=order["boson"])
+        assert S.info()["max_der"] == 3
+        return D, S, lat, beta, X
     d = O.enumerate_sigma(order)[idx]
     D, S = both(d["alpha"], d["eps"], prefactor=(-1.0) ** order * (-1.0) ** d["loops"])
     return D, S, lat, beta, X
@@ -151,3 +160,48 @@ def test_order3_real_axis_full_size_sampled():
     full = D.backward(lat, c["seed"], 0, n, X, c["beta"], g, per_sample=False)
     assert torch.equal(full["grad_params"], out["grad_params"])          # deterministic
     assert torch.equal(full["dSigma_dX"], out["dSigma_dX"])
+
+
+@pytest.mark.parametrize("beta", W.ORDER5["betas"])
+def test_order5_large_full_size_sampled(beta):
+    """The large-order workload at its full size: the order-5 diagram with the largest flat table
+    (744 terms), 2^26 samples, one frequency i pi/beta.  Forward: per-sample values at 200 random
+    samples against the oracle computed one by one, and the mean against the mean of all
+    per-sample outputs.  Adjoint (term products recomputed, nothing stored per sample): the
+    per-sample dSigma/dX and contracted gradients at 40 random samples against the oracle's dual
+    numbers, and a second full launch equal bit for bit."""
+    c = W.ORDER5
+    d = next(x for x in O.enumerate_sigma(c["order"]) if x["code"] == c["code"])
+    D, S = both(d["alpha"], d["eps"])
+    assert S.info()["terms"] == D.info()["n_terms"] == 744
+    X = W.matsubara(beta, c["n_freq"])
+    n = c["n_samples"]
+    lat = W.lattice(c)
+    mean, var, ps = D.forward(lat, c["seed"], 0, n, X, beta, per_sample=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(int(beta))
+    idx = np.sort(rng.choice(n, 200, replace=False))
+    got = ps[:, torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    for k, i in enumerate(idx):
+        r = S.eval_momenta(lat, c["seed"], int(i), 1, X, beta, per_sample=True)
+        err = np.abs(got[:, k] - r["values"][:, 0])
+        assert np.all(err <= RTOL * r["envelope"][:, 0]), (i, err, r["envelope"][:, 0])
+    ps_mean = ps.mean(dim=1).cpu().numpy()
+    scale = ps.abs().mean(dim=1).cpu().numpy()
+    assert np.all(np.abs(mean.cpu().numpy() - ps_mean) <= 1e-12 * scale)
+    del ps
+    g = np.array([1.0 + 0.5j])
+    out = D.backward(lat, c["seed"], 0, n, X, beta, g, per_sample=False)
+    again = D.backward(lat, c["seed"], 0, n, X, beta, g, per_sample=False)
+    assert torch.equal(out["grad_params"], again["grad_params"])
+    assert torch.equal(out["dSigma_dX"], again["dSigma_dX"])
+    assert np.all(np.isfinite(out["grad_params"].cpu().numpy()))
+    for i in idx[:40]:
+        o1 = D.backward(lat, c["seed"], int(i), 1, X, beta, g, per_sample=True)
+        gs = o1["grads"].cpu().numpy()[0]
+        _, dref, denv = S.eval_momenta_deriv(lat, c["seed"], int(i), 1, X, beta, "omega", envelope=True)
+        assert np.all(np.abs(o1["dX"].cpu().numpy()[:, 0] - dref[:, 0]) <= RTOL * denv[:, 0])
+        for k, which in enumerate(("mu", "kx", "ky")):
+            _, der, denv = S.eval_momenta_deriv(lat, c["seed"], int(i), 1, X, beta, which, envelope=True)
+            ref = np.real(np.conj(g) * der[:, 0]).sum()
+            assert abs(gs[k] - ref) <= RTOL * (np.abs(g) * denv[:, 0]).sum(), (i, which, gs[k], ref)

@@ -109,6 +109,29 @@ def test_eval_energies_enumerated_diagrams(order):
             check_per_sample(gpu, ref, env, f"order {order} code {d['code']}")
 
 
+def test_energy_input_paper_example_full_size():
+    """The paper's evaluation example at its own size (Sec. 5.1): 10^6 energy rows U(-8, 8), 100
+    fermionic frequencies, beta = 1, the full [n_f][n_e] output.  Rows at 2000 random indices
+    against the oracle; a launch over a slice of the rows equals that slice of the full output
+    bit for bit (each row is evaluated by itself)."""
+    c = W.ENERGY_X1
+    D, S = lib_and_oracle(c["alpha"])
+    E = W.random_energies(c["n_e"], c["alpha"].shape[0], a=c["a"], seed=c["seed"])
+    X = W.matsubara(c["beta"], c["n_freq"])
+    Ed = torch.tensor(E, device="cuda")
+    out = D.eval_energies(Ed, X, c["beta"])
+    torch.cuda.synchronize()
+    assert tuple(out.shape) == (c["n_freq"], c["n_e"])
+    rng = np.random.default_rng(2)
+    idx = np.sort(rng.choice(c["n_e"], 2000, replace=False))
+    got = out[:, torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    ref, _, env = S.eval_energies(E[idx], X, c["beta"])
+    check_per_sample(got, ref, env, "energy-input example")
+    lo, hi = 123_457, 123_457 + 5 * 128 + 3
+    part = D.eval_energies(Ed[lo:hi].contiguous(), X, c["beta"])
+    assert torch.equal(part, out[:, lo:hi])
+
+
 # ---------------------------------------------------------------------------- momentum mode
 def run_both(D, S, lat, seed, offset, n, X, beta, threads=8):
     mean, var, ps = D.forward(lat, seed, offset, n, X, beta, per_sample=True)
