@@ -27,7 +27,7 @@ using namespace dev;
 
 // per-thread capacities of the adjoint (checked before launch)
 constexpr int kBwCombos = 64, kBwFv = 128, kBwRden = 32, kBwCden = 32, kBwG1 = 128, kBwG2 = 64;
-constexpr int kBwFreq = 256, kBwCloses = 512;
+constexpr int kBwFreq = 256, kBwInner = 768;
 
 struct BwdParams {
   TableHeader h;
@@ -116,7 +116,13 @@ __device__ __forceinline__ void bwd_phase2(const TableHeader& H, int n_f, long l
   }
 }
 
-__global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
+// Resident blocks per SM that the register allocation must allow (the kernel's arrays live in
+// local memory; 8 blocks fit in 64 registers without spills).
+#ifndef TAMI_BWD_MIN_BLOCKS
+#define TAMI_BWD_MIN_BLOCKS 8
+#endif
+
+__global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const BwdParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const TableHeader& H = P.h;
   const int tid = threadIdx.x;
@@ -210,7 +216,9 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
     for (int b = H.n_fseg_bose; b < H.n_fseg; ++b) fermi_segment<false, true>(fseg + 8 * b, fvr, x, beta, fv, fvd);
     double rr[kBwRden];
     for (int i = 0; i < H.n_rden; ++i) rr[i] = rcp(x[rden[2 * i]]);
-    double W1[kBwG1], W2[kBwG2];
+    // pole trees, keeping each inner node's value (cv) for the reverse sweep
+    double W1[kBwG1], W2[kBwG2], cv[kBwInner];
+    int nc = 0;
     for (int h = 0; h < H.n_g2; ++h) W2[h] = 0.0;
     for (int gi = 0; gi < H.n_g1; ++gi) {
       double ft;
@@ -219,7 +227,9 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
         for (int o = g1[4 * gi]; o < g1[4 * gi + 1]; ++o) {
           const int2 op = ops[o];
           const int dd = op.x & 63;
-          const double operand = (op.x & kOpLeaf) ? leafA[op.x >> 8] : acc[dd];
+          const bool leaf = op.x & kOpLeaf;
+          if (!leaf) cv[nc++] = acc[dd];
+          const double operand = leaf ? leafA[op.x >> kOpLeafShift] : acc[dd];
           const double addend = (op.x & kOpFirst) ? 0.0 : acc[dd - 1];
           acc[dd - 1] = fma(fv[op.y], operand, addend);
         }
@@ -253,7 +263,8 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
       const int u = cden[2 * c];
       xbar[u] += cden[2 * c + 1] > 0 ? bb[c] : -bb[c];
     }
-    for (int gi = 0; gi < H.n_g1; ++gi) {
+    // groups in reverse, so that the inner-node values come off cv in reverse order
+    for (int gi = H.n_g1 - 1; gi >= 0; --gi) {
       const double wb = Wb2[g1_tgt[gi]];
       double RR = 1.0;
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
@@ -263,35 +274,27 @@ __global__ void __launch_bounds__(kBlock) bwd_kernel(const BwdParams P) {
         // W1 = FT prod rr^p and rr = 1/x:  dW1/dx = -p rr W1
         xbar[rden[2 * i]] -= wb * W1[gi] * (double)pw * rr[i];
       }
-      const double ftbar = wb * RR;
-      // pole tree, reverse: recompute each inner node's subtree value (cv), then walk the program
-      // backwards; for the edge acc[d-1] = F * operand + addend:
-      //   Fbar += operand * accbar[d-1],  accbar[d] = F * accbar[d-1]  (read only below inner edges)
-      const int o0 = g1[4 * gi], o1 = g1[4 * gi + 1];
-      double cv[kBwCloses];
-      {
-        double acc[kMaxDepth + 1];
-        int nc = 0;
-        for (int o = o0; o < o1; ++o) {
-          const int2 op = ops[o];
-          const int dd = op.x & 63;
-          const bool leaf = op.x & kOpLeaf;
-          if (!leaf) cv[nc++] = acc[dd];
-          const double operand = leaf ? leafA[op.x >> 8] : acc[dd];
-          const double addend = (op.x & kOpFirst) ? 0.0 : acc[dd - 1];
-          acc[dd - 1] = fma(fv[op.y], operand, addend);
-        }
-        double bar[kMaxDepth + 1];
-        bar[0] = ftbar;
-        for (int o = o1 - 1; o >= o0; --o) {
-          const int2 op = ops[o];
-          const int dd = op.x & 63;
-          const bool leaf = op.x & kOpLeaf;
-          if (!leaf) --nc;
-          const double operand = leaf ? leafA[op.x >> 8] : cv[nc];
-          const double pb = bar[dd - 1];
-          fvbar[op.y] = fma(operand, pb, fvbar[op.y]);
+      // pole tree, reverse: for the edge acc[d-1] += F * operand,
+      //   Fbar += operand * accbar[d-1]  and, below inner edges only,  accbar[d] = F * accbar[d-1];
+      // a parent's run of leaves shares accbar[d-1] and needs no child adjoint
+      const int o0 = g1[4 * gi];
+      double bar[kMaxDepth + 1];
+      bar[0] = wb * RR;
+      for (int o = g1[4 * gi + 1] - 1; o >= o0;) {
+        const int2 op = ops[o];
+        const int dd = op.x & 63;
+        const double pb = bar[dd - 1];
+        if (op.x & kOpLeaf) {
+          const int run = max((op.x >> kOpRunShift) & 255, 1);   // >= 1: the walk always advances
+          for (int i = 0; i < run; ++i) {
+            const int2 q = ops[o - i];
+            fvbar[q.y] = fma(leafA[q.x >> kOpLeafShift], pb, fvbar[q.y]);
+          }
+          o -= run;
+        } else {
+          fvbar[op.y] = fma(cv[--nc], pb, fvbar[op.y]);
           bar[dd] = fv[op.y] * pb;
+          --o;
         }
       }
     }
@@ -394,7 +397,7 @@ int bwd_check(const tami_diagram* d, int n_f) {
   const TableHeader& h = d->hdr;
   if (h.max_der > 4) { set_error("the adjoint needs derivative orders up to 4"); return TAMI_EUNSUPPORTED; }
   if (h.n_combo > kBwCombos || h.n_fv > kBwFv || h.n_rden > kBwRden || h.n_cden > kBwCden ||
-      h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || h.max_closes > kBwCloses) {
+      h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || h.n_inner > kBwInner) {
     set_error("term table exceeds the adjoint kernel's per-sample capacities");
     return TAMI_EUNSUPPORTED;
   }

@@ -65,7 +65,7 @@ __device__ __forceinline__ double pole_tree(const TableView& T, int op0, int op1
   for (int o = op0; o < op1; ++o) {
     const int2 op = T.ops[o];
     const int d = op.x & 63;
-    const double operand = (op.x & kOpLeaf) ? T.leafA[op.x >> 8] : acc[d];
+    const double operand = (op.x & kOpLeaf) ? T.leafA[op.x >> kOpLeafShift] : acc[d];
     const double addend = (op.x & kOpFirst) ? 0.0 : acc[d - 1];
     acc[d - 1] = fma(fv[op.y], operand, addend);
   }

@@ -363,55 +363,88 @@ int flatten(tami_diagram* d) {
   h.n_rden = (int)rdens.size();
   h.n_cden = (int)cdens.size();
   h.n_g1 = (int)g1s.size();
-  // Pole tree (Sec. 2.1, the factorised FT): per group, a trie over each term's Fermi values
-  // taken in reverse residue order (last summed variable first); leaves with equal paths merge
-  // their coefficients.  Emitted in post order as a program over a stack of accumulators, one
-  // fma per tree edge: for the edge to child c at depth d,
+  // Pole tree (Sec. 2.1, the factorised FT): per group, a tree over each term's Fermi values,
+  // one level per residue step; terms with equal paths merge their coefficients at a leaf.  The
+  // level a node branches on is chosen per node: the one with the fewest distinct Fermi values
+  // among the node's terms (the usual greedy ordering for small decision trees; ties go to the
+  // later residue step), unless the fixed reverse residue order gives fewer edges for the group.
+  // Emitted in post order as a program over a stack of accumulators, one fma per tree edge: for
+  // the edge to child c at depth d,
   //   acc[d-1] = F_c * (c is a leaf ? A_c : acc[d]) + (c is its parent's first child ? 0 : acc[d-1]).
-  std::vector<std::pair<int, int>> ops;   // (d | first << 6 | leaf << 7 | leaf index << 8, fv)
+  std::vector<std::pair<int, int>> ops;   // (d | first << 6 | leaf << 7 | run << 8 | leaf index << 16, fv)
   std::vector<double> leafA;
   std::vector<std::pair<int, int>> g1_ops(g1s.size());
-  int max_closes = 0;
+  int n_inner = 0;
   const int m_depth = nv - 1;
-  for (size_t g = 0; g < g1s.size(); ++g) {
-    struct Node { int fv; std::vector<int> kids; double A; };
+  struct Node { int fv; std::vector<int> kids; double A; };
+  auto build_tree = [&](const std::vector<int>& terms, bool greedy) {
     std::vector<Node> nodes(1, Node{-1, {}, 0.0});
-    for (int ti : g1s[g].terms) {
-      if ((int)ft[ti].fv.size() != m_depth) { set_error("term with an unexpected number of Fermi factors"); return TAMI_EUNSUPPORTED; }
-      int cur = 0;
-      for (int L = m_depth - 1; L >= 0; --L) {
-        const int f = fv_tmp[ft[ti].fv[L]];
-        int nxt = -1;
-        for (int c : nodes[cur].kids) if (nodes[c].fv == f) { nxt = c; break; }
-        if (nxt < 0) { nxt = (int)nodes.size(); nodes.push_back(Node{f, {}, 0.0}); nodes[cur].kids.push_back(nxt); }
-        cur = nxt;
+    std::function<void(int, const std::vector<int>&, unsigned)> grow = [&](int u, const std::vector<int>& ts,
+                                                                           unsigned left) {
+      if (!left) {
+        for (int ti : ts) nodes[u].A += ft[ti].A;
+        return;
       }
-      nodes[cur].A += ft[ti].A;
-    }
+      int best = -1;
+      size_t best_n = 0;
+      for (int L = m_depth - 1; L >= 0; --L) {
+        if (!(left >> L & 1u)) continue;
+        if (!greedy) { best = L; break; }
+        std::set<int> vals;
+        for (int ti : ts) vals.insert(fv_tmp[ft[ti].fv[L]]);
+        if (best < 0 || vals.size() < best_n) { best = L; best_n = vals.size(); }
+      }
+      std::vector<int> first_seen;
+      std::map<int, std::vector<int>> parts;
+      for (int ti : ts) {
+        const int f = fv_tmp[ft[ti].fv[best]];
+        if (!parts.count(f)) first_seen.push_back(f);
+        parts[f].push_back(ti);
+      }
+      for (int f : first_seen) {
+        const int c = (int)nodes.size();
+        nodes.push_back(Node{f, {}, 0.0});
+        nodes[u].kids.push_back(c);
+        grow(c, parts[f], left & ~(1u << best));
+      }
+    };
+    grow(0, terms, (1u << m_depth) - 1u);
+    return nodes;
+  };
+  for (size_t g = 0; g < g1s.size(); ++g) {
+    for (int ti : g1s[g].terms)
+      if ((int)ft[ti].fv.size() != m_depth) { set_error("term with an unexpected number of Fermi factors"); return TAMI_EUNSUPPORTED; }
+    std::vector<Node> nodes = build_tree(g1s[g].terms, true);
+    std::vector<Node> fixed = build_tree(g1s[g].terms, false);
+    if (fixed.size() <= nodes.size()) nodes.swap(fixed);
     const int begin = (int)ops.size();
-    int closes = 0;
     std::function<void(int, int)> emit = [&](int u, int d) {   // children of u sit at depth d + 1
-      for (size_t i = 0; i < nodes[u].kids.size(); ++i) {
+      const int nk = (int)nodes[u].kids.size();
+      for (int i = 0; i < nk; ++i) {
         const int c = nodes[u].kids[i];
         const int first = i == 0 ? 1 : 0;
-        if (d + 1 == m_depth) {
-          ops.push_back({(d + 1) | (first << 6) | (1 << 7) | ((int)leafA.size() << 8), nodes[c].fv});
+        if (d + 1 == m_depth) {       // every child of u is a leaf: the last one carries the run length
+          const int run = i == nk - 1 ? nk : 0;
+          ops.push_back({(d + 1) | (first << 6) | kOpLeaf | (run << kOpRunShift) |
+                         ((int)leafA.size() << kOpLeafShift), nodes[c].fv});
           leafA.push_back(nodes[c].A);
         } else {
           emit(c, d + 1);
           ops.push_back({(d + 1) | (first << 6), nodes[c].fv});
-          ++closes;
+          ++n_inner;
         }
       }
     };
+    for (const Node& nd : nodes)
+      if (nd.kids.size() > 255) { set_error("pole tree node with more than 255 children"); return TAMI_EUNSUPPORTED; }
     emit(0, 0);
+    if (leafA.size() >= (1u << 15)) { set_error("pole tree with too many leaves"); return TAMI_EUNSUPPORTED; }
     g1_ops[g] = {begin, (int)ops.size()};
-    max_closes = std::max(max_closes, closes);
   }
   h.n_ops = (int)ops.size();
   h.n_leaves = (int)leafA.size();
   h.max_depth = m_depth;
-  h.max_closes = max_closes;
+  h.n_inner = n_inner;
   int ng1rd = 0, ng2cd = 0;
   const int n_mul_ops = (int)ops.size();
   for (auto& g : g1s) ng1rd += (int)g.rd.size();
@@ -584,9 +617,9 @@ int flatten(tami_diagram* d) {
     for (auto& pr : g.rd) bl += pr.second + 4.0;        // RR and the real-denominator adjoint
     bl += 1.0;
   }
-  // pole tree in the adjoint: recompute (fma per edge), then per edge an fma into the Fermi-value
-  // adjoint and, for inner edges, a mul for the child's adjoint
-  bl += 2.0 * ops.size() + 3.0 * ops.size();            // recompute, then fma + mul per edge
+  // pole tree in the adjoint (the forward pass is counted in fl): per edge an fma into the
+  // Fermi-value adjoint and, for inner edges, a mul for the child's adjoint
+  bl += 2.0 * ops.size() + 1.0 * n_inner;
   bl += 3.0 * h.n_fv + 2.0 * nnz + 10.0 * h.n_rep;     // fvbar -> x -> E -> (mu, k_ext)
   I.bwd_flops_per_sample = bl;
   double bf = 12.0 * h.n_cden + 12.0 * h.n_cden + 2.0;  // reciprocals, Z, dv/dX and b-adjoints, accX

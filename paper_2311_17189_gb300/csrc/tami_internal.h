@@ -22,8 +22,11 @@ constexpr int kMaxCplxDens = 64;
 constexpr int kMaxDer = 5;
 constexpr int kMaxDepth = kMaxVars;   // pole-tree depth = number of summed variables
 
-// pole-tree program op (see flatten): acc[d-1] = F * (leaf ? A_leaf : acc[d]) + (first ? 0 : acc[d-1])
+// pole-tree program op (see flatten): acc[d-1] = F * (leaf ? A_leaf : acc[d]) + (first ? 0 : acc[d-1]);
+// x = d | first << 6 | leaf << 7 | run << 8 | leaf index << 16, y = Fermi value.  run (8 bits) is
+// set on the last leaf of each parent's run of leaves: the number of leaves in that run.
 enum { kOpFirst = 1 << 6, kOpLeaf = 1 << 7 };
+constexpr int kOpRunShift = 8, kOpLeafShift = 16;
 
 void set_error(const std::string& msg);
 
@@ -58,7 +61,7 @@ struct TableHeader {
   int n_lm;                         // nonzero momentum labels of the representative lines
   int n_rden, n_cden;
   int n_g1, n_ops, n_leaves, n_g1rd;
-  int max_depth, max_closes;   // pole-tree depth (= m) and most CLOSE ops in one group
+  int max_depth, n_inner;      // pole-tree depth (= m) and inner (non-leaf) edges over all groups
   int n_g2, n_g2cd;
   int g2_const;     // 1 if group 0 of phase 2 has no frequency-dependent factor (R = 1)
   int max_der;
@@ -80,8 +83,8 @@ struct TableHeader {
   int off_cden_a;     // double [n_cden]          external-frequency coefficient
   int off_g1;         // int32 [n_g1][4]         op_begin, op_end, rd_begin, rd_end
   int off_g1_tgt;     // int32 [n_g1]             frequency group it feeds (ascending)
-  int off_ops;        // int2 [n_ops]            pole-tree program: x = d | first<<6 | leaf<<7 | leaf index<<8,
-                      //                         y = Fermi value
+  int off_ops;        // int2 [n_ops]            pole-tree program: x = d | first<<6 | leaf<<7 | run<<8 |
+                      //                         leaf index<<16, y = Fermi value
   int off_leafA;      // double [n_leaves]        merged coefficients of the leaves
   int off_g1rd;       // int32 [n_g1rd][2]       real-den index, power
   int off_g2;         // int32 [n_g2+1]          complex-den offsets
