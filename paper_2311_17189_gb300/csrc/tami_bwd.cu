@@ -190,20 +190,29 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
     kx[H.m] = P.kx;
     ky[H.m] = P.ky;
     double E[kMaxLines], Sx[kMaxLines], Cx[kMaxLines], Sy[kMaxLines], Cy[kMaxLines];
-    for (int r = 0; r < H.n_rep; ++r) {
-      const int j = repl[r];
-      double ax = 0.0, ay = 0.0;
+    auto line_momentum = [&](int r, double& ax, double& ay) {
+      ax = 0.0;
+      ay = 0.0;
       for (int q = lm_ptr[r]; q < lm_ptr[r + 1]; ++q) {
         const double cf = lm_c[q];
         const int l = lm_l[q];
         ax = fma(cf, kx[l], ax);
         ay = fma(cf, ky[l], ay);
       }
-      double sx, cx, sy, cy;
+    };
+    for (int r = 0; r < H.n_rep_ext; ++r) {     // lines carrying k_ext: sin too, for dE/dk_ext
+      const int j = repl[r];
+      double ax, ay, sx, cx, sy, cy;
+      line_momentum(r, ax, ay);
       cw_sincos(ax, sx, cx);
       cw_sincos(ay, sy, cy);
       E[j] = fma(4.0 * P.tp, __dmul_rn(cx, cy), fma(2.0 * P.t, __dadd_rn(cx, cy), P.mu));
       Sx[j] = sx; Cx[j] = cx; Sy[j] = sy; Cy[j] = cy;
+    }
+    for (int r = H.n_rep_ext; r < H.n_rep; ++r) {
+      double ax, ay;
+      line_momentum(r, ax, ay);
+      E[repl[r]] = line_energy(ax, ay, P.t, P.tp, P.mu);
     }
     double x[kBwCombos];
     for (int u = 0; u < H.n_combo; ++u) {
@@ -312,10 +321,10 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
     for (int u = 0; u < H.n_combo; ++u)
       for (int q = combo_ptr[u]; q < combo_ptr[u + 1]; ++q) Ebar[combo_j[q]] = fma(xbar[u], combo_c[q], Ebar[combo_j[q]]);
     double mub = 0.0, kxb = 0.0, kyb = 0.0;
-    for (int r = 0; r < H.n_rep; ++r) {
+    for (int r = 0; r < H.n_rep; ++r) mub += Ebar[repl[r]];
+    for (int r = 0; r < H.n_rep_ext; ++r) {
       const int j = repl[r];
       const double eb = Ebar[j];
-      mub += eb;
       const double ae = rep_aext[r];
       // dE/dKx = -(2t + 4t' cos Ky) sin Kx,  dK/dk_ext = alpha_ext
       kxb = fma(-eb * ae, fma(4.0 * P.tp, Cy[j], 2.0 * P.t) * Sx[j], kxb);
@@ -346,28 +355,31 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
   }
 }
 
-__global__ void bwd_finalize_kernel(const double* partial, int n_blocks, int n_f, long long n, const double* G,
+__global__ void __launch_bounds__(kFinBlock) bwd_finalize_kernel(const double* partial, int n_blocks, int n_f, long long n, const double* G,
                                     const int* status, double* dX, double* grad_omega, double* grad_params) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // block i < n_f: dSigma/dX_i (two columns); block n_f: the three parameter gradients
+  __shared__ double sh[3][kFinBlock];
+  const int i = blockIdx.x;
   const int nval = 2 * n_f + 3;
+  const int c0 = i < n_f ? 2 * i : 2 * n_f;
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < n_blocks; b += kFinBlock) {
+    const double* p = partial + (size_t)b * nval + c0;
+    s[0] += p[0];
+    s[1] += p[1];
+    if (i == n_f) s[2] += p[2];
+  }
+  fixed_tree_sum<3>(s, sh);
+  if (threadIdx.x != 0) return;
   const bool bad = status && *status != 0;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   if (i < n_f) {
-    double re = 0.0, im = 0.0;
-    for (int b = 0; b < n_blocks; ++b) {
-      re += partial[(size_t)b * nval + 2 * i];
-      im += partial[(size_t)b * nval + 2 * i + 1];
-    }
-    re /= (double)n;
-    im /= (double)n;
+    double re = s[0] / (double)n, im = s[1] / (double)n;
     if (bad) re = im = nan;
     if (dX) { dX[2 * i] = re; dX[2 * i + 1] = im; }
     if (grad_omega) grad_omega[i] = bad ? nan : fma(G[2 * i], re, G[2 * i + 1] * im);
-  } else if (i < n_f + 3) {
-    const int k = i - n_f;
-    double v = 0.0;
-    for (int b = 0; b < n_blocks; ++b) v += partial[(size_t)b * nval + 2 * n_f + k];
-    if (grad_params) grad_params[k] = bad ? nan : v / (double)n;
+  } else if (grad_params) {
+    for (int k = 0; k < 3; ++k) grad_params[k] = bad ? nan : s[k] / (double)n;
   }
 }
 
@@ -453,7 +465,7 @@ int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed,
   bwd_kernel<<<grid, kBlock, smem, st>>>(P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "bwd_kernel launch");
-  bwd_finalize_kernel<<<(n_f + 3 + 127) / 128, 128, 0, st>>>(partial, grid, n_f, n_samples, gout, status,
+  bwd_finalize_kernel<<<n_f + 1, kFinBlock, 0, st>>>(partial, grid, n_f, n_samples, gout, status,
                                                               dsigma_dX, grad_X_re, grad_params);
   e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "bwd finalize launch");

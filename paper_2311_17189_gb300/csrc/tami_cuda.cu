@@ -83,15 +83,19 @@ __global__ void __launch_bounds__(kBlock) fwd_kernel(const FwdParams P) {
 }
 
 // mean and unbiased variances from per-block partials, summed in block order
-__global__ void finalize_kernel(const double* partial, int n_blocks, int n_f, long long n, const int* status,
-                                double* mean, double* var) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= n_f) return;
-  double s1r = 0.0, s1i = 0.0, s2r = 0.0, s2i = 0.0;
-  for (int b = 0; b < n_blocks; ++b) {
+// One block of kFinBlock threads per frequency: the sums over the per-block partials.
+__global__ void __launch_bounds__(kFinBlock) finalize_kernel(const double* partial, int n_blocks, int n_f, long long n,
+                                                            const int* status, double* mean, double* var) {
+  __shared__ double sh[4][kFinBlock];
+  const int f = blockIdx.x;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < n_blocks; b += kFinBlock) {
     const double* p = partial + ((size_t)b * n_f + f) * 4;
-    s1r += p[0]; s1i += p[1]; s2r += p[2]; s2i += p[3];
+    for (int k = 0; k < 4; ++k) s[k] += p[k];
   }
+  fixed_tree_sum<4>(s, sh);
+  if (threadIdx.x != 0) return;
+  const double s1r = s[0], s1i = s[1], s2r = s[2], s2i = s[3];
   const double nn = (double)n;
   double mr = s1r / nn, mi = s1i / nn;
   double vr = n > 1 ? (s2r - s1r * mr) / (nn - 1.0) : 0.0;
@@ -312,7 +316,7 @@ int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, 
   P.status = status;
   rc = launch_fwd<false>(d, P, st, grid);
   if (rc) return rc;
-  finalize_kernel<<<(n_f + 127) / 128, 128, 0, st>>>(partial, grid, n_f, n_samples, status, mean, var);
+  finalize_kernel<<<n_f, kFinBlock, 0, st>>>(partial, grid, n_f, n_samples, status, mean, var);
   e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "finalize launch");
 }
@@ -351,7 +355,7 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
   P.status = status;
   rc = launch_fwd<false>(d, P, st, grid);
   if (rc) return rc;
-  finalize_kernel<<<(n_f + 127) / 128, 128, 0, st>>>(partial, grid, n_f, n_samples, status, mean, var);
+  finalize_kernel<<<n_f, kFinBlock, 0, st>>>(partial, grid, n_f, n_samples, status, mean, var);
   e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "finalize launch");
 }

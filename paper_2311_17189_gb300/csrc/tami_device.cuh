@@ -231,6 +231,24 @@ __device__ __forceinline__ void fermi_segment(const int* seg, const int* fvr, co
   }
 }
 
+// Final reduction of per-block partial sums, in a fixed order for a given number of rows: thread
+// t of a kFinBlock-thread block adds rows t, t + kFinBlock, ... in turn, then the block adds the
+// threads' sums pairwise in a fixed tree.  The result is in s[] of thread 0.
+constexpr int kFinBlock = 256;
+
+template <int NC>
+__device__ __forceinline__ void fixed_tree_sum(double (&s)[NC], double (*sh)[kFinBlock]) {
+  const int t = threadIdx.x;
+  for (int k = 0; k < NC; ++k) sh[k][t] = s[k];
+  __syncthreads();
+  for (int w = kFinBlock / 2; w > 0; w >>= 1) {
+    if (t < w)
+      for (int k = 0; k < NC; ++k) sh[k][t] += sh[k][t + w];
+    __syncthreads();
+  }
+  for (int k = 0; k < NC; ++k) s[k] = sh[k][0];
+}
+
 __host__ __device__ __forceinline__ int align16(int b) { return (b + 15) & ~15; }
 
 

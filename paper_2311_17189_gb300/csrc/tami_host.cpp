@@ -347,12 +347,16 @@ int flatten(tami_diagram* d) {
   for (int j = 0; j < N; ++j)
     if (needed[j] && std::find(repl.begin(), repl.end(), j) == repl.end()) repl.push_back(j);
   std::sort(repl.begin(), repl.end());
+  // lines carrying k_ext first: only their energies depend on k_ext (the adjoint needs sin there)
+  const int n_rep_ext = (int)(std::stable_partition(repl.begin(), repl.end(), [&](int j) {
+                                return d->alpha[j * nv + nv - 1] != 0; }) - repl.begin());
 
   // ---- blob
   TableHeader& h = d->hdr;
   h = TableHeader{};
   h.N = N; h.nv = nv; h.m = nv - 1;
   h.n_rep = (int)repl.size();
+  h.n_rep_ext = n_rep_ext;
   h.n_combo = (int)combos.size();
   int nnz = 0;
   for (const Vec& c : combos) for (int j = 0; j < N; ++j) if (c[j]) ++nnz;
@@ -620,7 +624,8 @@ int flatten(tami_diagram* d) {
   // pole tree in the adjoint (the forward pass is counted in fl): per edge an fma into the
   // Fermi-value adjoint and, for inner edges, a mul for the child's adjoint
   bl += 2.0 * ops.size() + 1.0 * n_inner;
-  bl += 3.0 * h.n_fv + 2.0 * nnz + 10.0 * h.n_rep;     // fvbar -> x -> E -> (mu, k_ext)
+  bl += h.n_rep_ext * 2.0 * 27.0;                       // sin of both components where k_ext enters
+  bl += 3.0 * h.n_fv + 2.0 * nnz + h.n_rep + 10.0 * h.n_rep_ext;   // fvbar -> x -> E -> (mu, k_ext)
   I.bwd_flops_per_sample = bl;
   double bf = 12.0 * h.n_cden + 12.0 * h.n_cden + 2.0;  // reciprocals, Z, dv/dX and b-adjoints, accX
   for (auto& g : g2s) {

@@ -56,6 +56,7 @@ struct SymTerm {
 struct TableHeader {
   int N, nv, m;
   int n_rep;        // lines whose energy is computed (first line of each momentum label)
+  int n_rep_ext;    // the first n_rep_ext of them carry the external momentum
   int n_combo, combo_nnz;
   int n_fseg, n_fseg_bose, n_fv;   // Fermi segments (Bose-type first) and values
   int n_lm;                         // nonzero momentum labels of the representative lines
