@@ -27,7 +27,7 @@ using namespace dev;
 
 // per-thread capacities of the adjoint (checked before launch)
 constexpr int kBwCombos = 64, kBwFv = 128, kBwRden = 32, kBwCden = 32, kBwG1 = 128, kBwG2 = 64;
-constexpr int kBwFreq = 256, kBwInner = 768;
+constexpr int kBwFreq = 256, kBwInner = 768, kBwG2cd = 256;
 
 struct BwdParams {
   TableHeader h;
@@ -51,58 +51,50 @@ __host__ __device__ __forceinline__ size_t bwd_smem_bytes(const TableHeader& h, 
          sizeof(double) * ((4 + 2 * (size_t)h.n_cden) * n_f + 4 * (2 * (size_t)n_f + 3));
 }
 
-// Phase 2 of the adjoint for one sample over all frequencies: the reciprocals, group products R_h,
-// T_h = W_h R_h, the weight adjoints Wb_h += Re(conj g R_h), U_d = sum_h p T_h, Z_d = r_d U_d,
-// dv/dX = -sum_d a_d Z_d and the denominator-energy adjoints bb_d -= Re(conj g Z_d).  As in the
-// forward, no data-dependent selects around FP64 work (predicated-off FP64 instructions still
-// cost FP64-pipe time): the first factor of each product is peeled, the R = 1 group is group 0,
-// the imaginary-axis case is a template parameter.
+// Phase 2 of the adjoint for one sample over all frequencies: the reciprocals, the group products
+// R_h (the flattener's product trie), the weight adjoints Wb_h += Re(conj g R_h), U_d = sum_h p W_h R_h
+// (pW = p W_h per group factor, formed once per sample), Z_d = r_d U_d, dv/dX = -sum_d a_d Z_d and
+// the denominator-energy adjoints bb_d -= Re(conj g Z_d).  As in the forward, no data-dependent
+// selects around FP64 work (predicated-off FP64 instructions still cost FP64-pipe time): the R = 1
+// group is group 0 and the imaginary-axis case is a template parameter.
 template <bool XR_ZERO>
 __device__ __forceinline__ void bwd_phase2(const TableHeader& H, int n_f, long long s, const BwdParams& P,
                                            const double* Xs, const double* Gs, const double* AXI, const double* AXI2,
-                                           const double* cden_a, const int* g2, const int* g2cd, const double* g2cd_p,
-                                           const double* b, const double* W2, double* Wb2, double* bb, double* accX) {
+                                           const double* cden_a, const int* g2, const int* g2cd, const int* pnode,
+                                           const int* g2node, const double* pW, const double* b, double* Wb2,
+                                           double* bb, double* accX) {
   for (int f = 0; f < n_f; ++f) {
     const double Xr = Xs[2 * f], gr = Gs[2 * f], gim = Gs[2 * f + 1];
-    double rc_re[kBwCden], rc_im[kBwCden], U_re[kBwCden], U_im[kBwCden];
+    double vre[kBwCden + kMaxProdNodes], vim[kBwCden + kMaxProdNodes], U_re[kBwCden], U_im[kBwCden];
     for (int c = 0; c < H.n_cden; ++c) {
       const double Dr = XR_ZERO ? b[c] : fma(cden_a[c], Xr, b[c]);
       const double r = rcp(fma(Dr, Dr, AXI2[c * n_f + f]));
-      rc_re[c] = Dr * r;
-      rc_im[c] = -AXI[c * n_f + f] * r;
+      vre[c] = Dr * r;
+      vim[c] = -AXI[c * n_f + f] * r;
       U_re[c] = 0.0;
       U_im[c] = 0.0;
     }
+    for (int k = 0; k < H.n_pnode; ++k) {
+      const int src = pnode[2 * k], c = pnode[2 * k + 1];
+      const double ar = vre[src], ai = vim[src], br = vre[c], bi = vim[c];
+      vre[H.n_cden + k] = fma(ar, br, -ai * bi);
+      vim[H.n_cden + k] = fma(ar, bi, ai * br);
+    }
     if (H.g2_const) Wb2[0] += gr;                 // R = 1
     for (int h = H.g2_const; h < H.n_g2; ++h) {
-      const int q0 = g2[h], q1 = g2[h + 1];
-      int c = g2cd[2 * q0];
-      double Rr = rc_re[c], Ri = rc_im[c];
-      for (int pw = g2cd[2 * q0 + 1]; pw > 1; --pw) {
-        const double nr = fma(Rr, rc_re[c], -Ri * rc_im[c]);
-        Ri = fma(Rr, rc_im[c], Ri * rc_re[c]);
-        Rr = nr;
-      }
-      for (int q = q0 + 1; q < q1; ++q) {
-        c = g2cd[2 * q];
-        for (int pw = g2cd[2 * q + 1]; pw > 0; --pw) {
-          const double nr = fma(Rr, rc_re[c], -Ri * rc_im[c]);
-          Ri = fma(Rr, rc_im[c], Ri * rc_re[c]);
-          Rr = nr;
-        }
-      }
+      const int v = g2node[h];
+      const double Rr = vre[v], Ri = vim[v];
       Wb2[h] = fma(gr, Rr, fma(gim, Ri, Wb2[h]));
-      const double Tr = W2[h] * Rr, Ti = W2[h] * Ri;
-      for (int q = q0; q < q1; ++q) {
+      for (int q = g2[h]; q < g2[h + 1]; ++q) {
         const int cc = g2cd[2 * q];
-        U_re[cc] = fma(g2cd_p[q], Tr, U_re[cc]);
-        U_im[cc] = fma(g2cd_p[q], Ti, U_im[cc]);
+        U_re[cc] = fma(pW[q], Rr, U_re[cc]);
+        U_im[cc] = fma(pW[q], Ri, U_im[cc]);
       }
     }
     double dvr = 0.0, dvi = 0.0;
     for (int c = 0; c < H.n_cden; ++c) {
-      const double Zr = fma(rc_re[c], U_re[c], -rc_im[c] * U_im[c]);
-      const double Zi = fma(rc_re[c], U_im[c], rc_im[c] * U_re[c]);
+      const double Zr = fma(vre[c], U_re[c], -vim[c] * U_im[c]);
+      const double Zi = fma(vre[c], U_im[c], vim[c] * U_re[c]);
       dvr = fma(-cden_a[c], Zr, dvr);
       dvi = fma(-cden_a[c], Zi, dvi);
       bb[c] -= fma(gr, Zr, gim * Zi);
@@ -156,6 +148,8 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
   const int* g2 = reinterpret_cast<const int*>(smem + H.off_g2);
   const int* g2cd = reinterpret_cast<const int*>(smem + H.off_g2cd);
   const double* g2cd_p = reinterpret_cast<const double*>(smem + H.off_g2cd_p);
+  const int* pnode = reinterpret_cast<const int*>(smem + H.off_pnode);
+  const int* g2node = reinterpret_cast<const int*>(smem + H.off_g2node);
 
   double accX[2 * kBwFreq];
   for (int i = 0; i < 2 * n_f; ++i) accX[i] = 0.0;
@@ -257,13 +251,16 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
       b[c] = cden[2 * c + 1] > 0 ? xv : -xv;
     }
     // ------------------------------------------------------------ phase 2 over frequencies
-    double Wb2[kBwG2], bb[kBwCden];
-    for (int h = 0; h < H.n_g2; ++h) Wb2[h] = 0.0;
+    double Wb2[kBwG2], bb[kBwCden], pW[kBwG2cd];
+    for (int h = 0; h < H.n_g2; ++h) {
+      Wb2[h] = 0.0;
+      for (int q = g2[h]; q < g2[h + 1]; ++q) pW[q] = g2cd_p[q] * W2[h];
+    }
     for (int c = 0; c < H.n_cden; ++c) bb[c] = 0.0;
     if (xr_zero)
-      bwd_phase2<true>(H, n_f, s, P, Xs, Gs, AXI, AXI2, cden_a, g2, g2cd, g2cd_p, b, W2, Wb2, bb, accX);
+      bwd_phase2<true>(H, n_f, s, P, Xs, Gs, AXI, AXI2, cden_a, g2, g2cd, pnode, g2node, pW, b, Wb2, bb, accX);
     else
-      bwd_phase2<false>(H, n_f, s, P, Xs, Gs, AXI, AXI2, cden_a, g2, g2cd, g2cd_p, b, W2, Wb2, bb, accX);
+      bwd_phase2<false>(H, n_f, s, P, Xs, Gs, AXI, AXI2, cden_a, g2, g2cd, pnode, g2node, pW, b, Wb2, bb, accX);
     // ------------------------------------------------------------ reverse sweep
     double xbar[kBwCombos], fvbar[kBwFv];
     for (int u = 0; u < H.n_combo; ++u) xbar[u] = 0.0;
@@ -409,7 +406,7 @@ int bwd_check(const tami_diagram* d, int n_f) {
   const TableHeader& h = d->hdr;
   if (h.max_der > 4) { set_error("the adjoint needs derivative orders up to 4"); return TAMI_EUNSUPPORTED; }
   if (h.n_combo > kBwCombos || h.n_fv > kBwFv || h.n_rden > kBwRden || h.n_cden > kBwCden ||
-      h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || h.n_inner > kBwInner) {
+      h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || h.n_inner > kBwInner || h.n_g2cd > kBwG2cd) {
     set_error("term table exceeds the adjoint kernel's per-sample capacities");
     return TAMI_EUNSUPPORTED;
   }

@@ -37,7 +37,7 @@ __device__ __forceinline__ double to_momentum(uint32_t hi, uint32_t lo) {
 
 // cos and sin: Cody-Waite reduction by pi (three-part constant), k = n pi + r, |r| <= pi/2 (n the
 // integer nearest to k/pi, from one fma against 1.5 * 2^52), then
-// Taylor series in r (to r^24 for cos, r^25 for sin) and the sign (-1)^n (W. J. Cody and
+// Taylor series in r (to r^20 for cos, r^21 for sin) and the sign (-1)^n (W. J. Cody and
 // W. Waite, 1980).  Every operation is an explicit fma or a rounded mul intrinsic, so the result
 // is the same on any IEEE machine that follows the same recipe.
 // n = nearest integer to k/pi, read from the low word of k/pi + 1.5 * 2^52 (one rounding);
@@ -59,9 +59,7 @@ __device__ __forceinline__ double flip_if(double v, int odd) {   // (-1)^odd v, 
 }
 
 __device__ __forceinline__ double cw_cos_poly(double z) {
-  double pc = 0x1.f2cf01972f578p-80;
-  pc = fma(pc, z, -0x1.0ce396db7f853p-70);
-  pc = fma(pc, z, 0x1.e542ba4020225p-62);
+  double pc = 0x1.e542ba4020225p-62;
   pc = fma(pc, z, -0x1.6827863b97d97p-53);
   pc = fma(pc, z, 0x1.ae7f3e733b81fp-45);
   pc = fma(pc, z, -0x1.93974a8c07c9dp-37);
@@ -85,9 +83,7 @@ __device__ __forceinline__ void cw_sincos(double k, double& s_out, double& c_out
   const double r = cw_reduce(k, odd);
   const double z = __dmul_rn(r, r);
   const double cr = cw_cos_poly(z);
-  double ps = 0x1.3f3ccdd165fa9p-84;
-  ps = fma(ps, z, -0x1.761b41316381ap-75);
-  ps = fma(ps, z, 0x1.71b8ef6dcf572p-66);
+  double ps = 0x1.71b8ef6dcf572p-66;
   ps = fma(ps, z, -0x1.2f49b46814157p-57);
   ps = fma(ps, z, 0x1.952c77030ad4ap-49);
   ps = fma(ps, z, -0x1.ae7f3e733b81fp-41);

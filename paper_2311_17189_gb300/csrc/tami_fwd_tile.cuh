@@ -31,6 +31,8 @@ struct TableView {
   const int* g1rd;
   const int* g2;
   const int* g2cd;
+  const int* pnode;
+  const int* g2node;
 };
 
 __device__ __forceinline__ TableView table_view(const unsigned char* t, const TableHeader& H) {
@@ -54,6 +56,8 @@ __device__ __forceinline__ TableView table_view(const unsigned char* t, const Ta
   v.g1rd = reinterpret_cast<const int*>(t + H.off_g1rd);
   v.g2 = reinterpret_cast<const int*>(t + H.off_g2);
   v.g2cd = reinterpret_cast<const int*>(t + H.off_g2cd);
+  v.pnode = reinterpret_cast<const int*>(t + H.off_pnode);
+  v.g2node = reinterpret_cast<const int*>(t + H.off_g2node);
   return v;
 }
 
@@ -124,44 +128,36 @@ __device__ __forceinline__ bool freq_constants(const TableHeader& H, const Table
 }
 
 // Phase 2 for one (sample slot sl, frequency f): the complex reciprocals of the frequency-dependent
-// denominators, the group products R_h and the sum over groups of W_h R_h.  Written without
-// data-dependent selects: on this GPU an FP64 instruction issued with its predicate off still
-// occupies the FP64 pipe, so the first factor of each product is peeled and the imaginary-axis
-// case is a template parameter.  A group without frequency-dependent factors sits first (g2_const).
+// denominators, the group products R_h (one complex product per node of the flattener's product
+// trie) and the sum over groups of W_h R_h.  Written without data-dependent selects: on this GPU
+// an FP64 instruction issued with its predicate off still occupies the FP64 pipe, so the
+// imaginary-axis case is a template parameter.  A group without frequency-dependent factors sits
+// first (g2_const).
 template <bool XR_ZERO>
 __device__ __forceinline__ void phase2_sample(const TableHeader& H, const TableView& T, const TileArgs& A, int sl,
                                               int f, double Xr, const double* AXI, const double* AXI2,
                                               const double* CB, const double* W, double& vr_out, double& vi_out) {
-  double rc_re[kMaxCplxDens], rc_im[kMaxCplxDens];
+  // values: [0, n_cden) the reciprocals 1/D_c, then the product nodes
+  double vre[kMaxCplxDens + kMaxProdNodes], vim[kMaxCplxDens + kMaxProdNodes];
   for (int c = 0; c < H.n_cden; ++c) {
     const double b = CB[c * kBlock + sl];
     const double Dr = XR_ZERO ? b : fma(T.cden_a[c], Xr, b);    // D = a X + b
     const double r = rcp(fma(Dr, Dr, AXI2[c * A.n_f + f]));
-    rc_re[c] = Dr * r;
-    rc_im[c] = -AXI[c * A.n_f + f] * r;
+    vre[c] = Dr * r;
+    vim[c] = -AXI[c * A.n_f + f] * r;
+  }
+  for (int k = 0; k < H.n_pnode; ++k) {
+    const int src = T.pnode[2 * k], c = T.pnode[2 * k + 1];
+    const double ar = vre[src], ai = vim[src], br = vre[c], bi = vim[c];
+    vre[H.n_cden + k] = fma(ar, br, -ai * bi);
+    vim[H.n_cden + k] = fma(ar, bi, ai * br);
   }
   double vr = H.g2_const ? W[sl] : 0.0, vi = 0.0;
   for (int hg = H.g2_const; hg < H.n_g2; ++hg) {
     const double w = W[hg * kBlock + sl];
-    const int q0 = T.g2[hg], q1 = T.g2[hg + 1];
-    int c = T.g2cd[2 * q0];
-    double Rr = rc_re[c], Ri = rc_im[c];
-    for (int pw = T.g2cd[2 * q0 + 1]; pw > 1; --pw) {
-      const double nr = fma(Rr, rc_re[c], -Ri * rc_im[c]);
-      Ri = fma(Rr, rc_im[c], Ri * rc_re[c]);
-      Rr = nr;
-    }
-    for (int q = q0 + 1; q < q1; ++q) {
-      c = T.g2cd[2 * q];
-      const double ar = rc_re[c], ai = rc_im[c];
-      for (int pw = T.g2cd[2 * q + 1]; pw > 0; --pw) {
-        const double nr = fma(Rr, ar, -Ri * ai);
-        Ri = fma(Rr, ai, Ri * ar);
-        Rr = nr;
-      }
-    }
-    vr = fma(w, Rr, vr);
-    vi = fma(w, Ri, vi);
+    const int v = T.g2node[hg];
+    vr = fma(w, vre[v], vr);
+    vi = fma(w, vim[v], vi);
   }
   vr_out = vr;
   vi_out = vi;

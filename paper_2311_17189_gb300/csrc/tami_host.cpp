@@ -328,7 +328,38 @@ int flatten(tami_diagram* d) {
   for (auto& kv : g1map) g1s.push_back({g2_id[kv.first.first], kv.first.second, kv.second});
   std::stable_sort(g1s.begin(), g1s.end(), [](const G1& x, const G1& y) { return x.g2 < y.g2; });
 
-  if ((int)combos.size() > kMaxCombos || (int)fvs.size() > kMaxFermiValues ||
+  // ---- phase-2 products: a trie over each frequency-dependent group's factors (the denominators
+  // used by more groups first, each repeated by its power), so that groups sharing a leading
+  // sub-product compute it once.  Values: index c < n_cden is 1/D_c itself; index n_cden + k is
+  // product node k = value[src_k] * value[c_k]; each group reads the value at the end of its path.
+  const int n_cd = (int)cdens.size();
+  std::vector<int> cuse(n_cd, 0);
+  for (auto& g : g2s) for (auto& pr : g) ++cuse[pr.first];
+  std::vector<std::pair<int, int>> pnodes;   // (src value index, c)
+  std::vector<int> g2node(g2s.size(), -1);
+  {
+    std::map<std::pair<int, int>, int> child;
+    for (size_t g = 0; g < g2s.size(); ++g) {
+      if (g2s[g].empty()) continue;
+      auto fs = g2s[g];
+      std::stable_sort(fs.begin(), fs.end(), [&](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+        return cuse[a.first] != cuse[b.first] ? cuse[a.first] > cuse[b.first] : a.first < b.first; });
+      std::vector<int> seq;
+      for (auto& pr : fs) for (int k = 0; k < pr.second; ++k) seq.push_back(pr.first);
+      int cur = seq[0];
+      for (size_t i = 1; i < seq.size(); ++i) {
+        const auto key = std::make_pair(cur, seq[i]);
+        const auto it = child.find(key);
+        if (it != child.end()) { cur = it->second; continue; }
+        const int v = n_cd + (int)pnodes.size();
+        pnodes.push_back(key);
+        child[key] = v;
+        cur = v;
+      }
+      g2node[g] = cur;
+    }
+  }
+  if ((int)pnodes.size() > kMaxProdNodes || (int)combos.size() > kMaxCombos || (int)fvs.size() > kMaxFermiValues ||
       (int)rdens.size() > kMaxRealDens || (int)cdens.size() > kMaxCplxDens) {
     set_error("term table exceeds the kernels' per-sample capacities");
     return TAMI_EUNSUPPORTED;
@@ -455,6 +486,7 @@ int flatten(tami_diagram* d) {
   for (auto& g : g2s) ng2cd += (int)g.size();
   h.n_g1rd = ng1rd;
   h.n_g2 = (int)g2s.size(); h.n_g2cd = ng2cd;
+  h.n_pnode = (int)pnodes.size();
   h.g2_const = g2_const;
   h.max_der = max_der;
   Blob B;
@@ -483,6 +515,8 @@ int flatten(tami_diagram* d) {
   h.off_g2 = B.reserve(sizeof(int) * (h.n_g2 + 1));
   h.off_g2cd = B.reserve(sizeof(int) * 2 * ng2cd);
   h.off_g2cd_p = B.reserve(sizeof(double) * ng2cd);
+  h.off_pnode = B.reserve(sizeof(int) * 2 * h.n_pnode);
+  h.off_g2node = B.reserve(sizeof(int) * h.n_g2);
   B.reserve(16);
   h.bytes = (int)B.b.size();
 
@@ -567,6 +601,11 @@ int flatten(tami_diagram* d) {
     }
     B.at<int>(h.off_g2)[h.n_g2] = pos;
   }
+  for (int k = 0; k < h.n_pnode; ++k) {
+    B.at<int>(h.off_pnode)[2 * k] = pnodes[k].first;
+    B.at<int>(h.off_pnode)[2 * k + 1] = pnodes[k].second;
+  }
+  for (int g = 0; g < h.n_g2; ++g) B.at<int>(h.off_g2node)[g] = g2node[g];
   d->blob.swap(B.b);
 
   // ---- info and the flop model of the kernels' explicit arithmetic
@@ -605,11 +644,8 @@ int flatten(tami_diagram* d) {
   }
   I.flops_per_sample = fl;
   double ff = 12.0 * h.n_cden;                          // |D|^2, reciprocal, 1/D (+ Re D off the imaginary axis)
-  for (auto& g : g2s) {
-    int pw = 0;
-    for (auto& pr : g) pw += pr.second;
-    ff += pw ? 6.0 * (pw - 1) + 4.0 : 1.0;              // complex products, fused accumulate
-  }
+  ff += 6.0 * h.n_pnode;                                // complex product per trie node
+  for (auto& g : g2s) ff += g.empty() ? 1.0 : 4.0;      // W R accumulated
   ff += 6.0;                                            // mean and variance sums
   I.flops_per_sample_freq = ff;
   // adjoint: the forward's phase 1 again plus the next derivative of every Fermi value, then per
@@ -625,14 +661,12 @@ int flatten(tami_diagram* d) {
   // Fermi-value adjoint and, for inner edges, a mul for the child's adjoint
   bl += 2.0 * ops.size() + 1.0 * n_inner;
   bl += h.n_rep_ext * 2.0 * 27.0;                       // sin of both components where k_ext enters
+  bl += ng2cd;                                          // p W per group factor
   bl += 3.0 * h.n_fv + 2.0 * nnz + h.n_rep + 10.0 * h.n_rep_ext;   // fvbar -> x -> E -> (mu, k_ext)
   I.bwd_flops_per_sample = bl;
   double bf = 12.0 * h.n_cden + 12.0 * h.n_cden + 2.0;  // reciprocals, Z, dv/dX and b-adjoints, accX
-  for (auto& g : g2s) {
-    int pw = 0;
-    for (auto& pr : g) pw += pr.second;
-    bf += pw ? 6.0 * (pw - 1) + 4.0 + 2.0 + 4.0 * g.size() : 1.0;   // R, Wbar, T, U
-  }
+  bf += 6.0 * h.n_pnode;                                // products (trie nodes)
+  for (auto& g : g2s) bf += g.empty() ? 1.0 : 4.0 + 4.0 * g.size();   // Wbar, U += p W R
   I.bwd_flops_per_sample_freq = bf;
   return TAMI_OK;
 }

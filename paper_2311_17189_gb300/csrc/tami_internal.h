@@ -19,6 +19,7 @@ constexpr int kMaxCombos = 128;
 constexpr int kMaxFermiValues = 256;
 constexpr int kMaxRealDens = 128;
 constexpr int kMaxCplxDens = 64;
+constexpr int kMaxProdNodes = 64;    // phase-2 product nodes beyond the reciprocals themselves
 constexpr int kMaxDer = 5;
 constexpr int kMaxDepth = kMaxVars;   // pole-tree depth = number of summed variables
 
@@ -64,6 +65,7 @@ struct TableHeader {
   int n_g1, n_ops, n_leaves, n_g1rd;
   int max_depth, n_inner;      // pole-tree depth (= m) and inner (non-leaf) edges over all groups
   int n_g2, n_g2cd;
+  int n_pnode;      // phase-2 product nodes
   int g2_const;     // 1 if group 0 of phase 2 has no frequency-dependent factor (R = 1)
   int max_der;
   int bytes;
@@ -91,6 +93,8 @@ struct TableHeader {
   int off_g2;         // int32 [n_g2+1]          complex-den offsets
   int off_g2cd;       // int32 [n_g2cd][2]       complex-den index, power
   int off_g2cd_p;     // double [n_g2cd]          the same powers as doubles
+  int off_pnode;      // int32 [n_pnode][2]      product node k: value[n_cden+k] = value[src] * value[c]
+  int off_g2node;     // int32 [n_g2]             value index of each group's product (-1: R = 1)
 };
 
 }  // namespace tami
