@@ -32,6 +32,27 @@ CFG = W.ORDER4
 FP64_PEAK_TFLOPS = 1.2586   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
 METRIC = "order-4 Sigma evals/s (samples x terms x frequencies, FP64), forward + adjoint"
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel from one ncu
+# capture of this workload at 2^22 samples, per sample; every sample does the same work, so a
+# launch's traffic is this times its samples.  It holds only for the kernel sources it was taken
+# on: the hash of the library sources must match, else the bench reports traffic as null.
+TRAFFIC = {"kernel": "bwd_kernel", "bytes_per_sample": (6.046020e9 + 9.684244e9) / 4194304,
+           "sources_sha256": "77188c6f04a02fd61460ff3379d0cc3692efedd8cbd751443fa2486ea5720a28", "profile": "profiles/bwd_kernel_order4_sigma.md"}
+
+
+def sources_sha256():
+    """sha256 over the library's kernel and table sources (csrc/ and include/), in name order."""
+    import hashlib
+    h = hashlib.sha256()
+    for sub in ("paper_2311_17189_gb300/csrc", "include"):
+        d = os.path.join(ROOT, sub)
+        for name in sorted(os.listdir(d)):
+            if name.endswith((".cu", ".cuh", ".cpp", ".h")):
+                h.update(name.encode())
+                with open(os.path.join(d, name), "rb") as f:
+                    h.update(f.read())
+    return h.hexdigest()
+
 
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -241,6 +262,9 @@ def run_tami(args):
     fl_b = n * (info["bwd_flops_per_sample"] + n_f * info["bwd_flops_per_sample_freq"])
     dom = ("bwd_kernel", fl_b, tb) if tb >= tf else ("fwd_kernel", fl_f, tf)
     achieved = dom[1] / (dom[2] * 1e-3) / 1e12
+    traffic = None
+    if dom[0] == TRAFFIC["kernel"] and sources_sha256() == TRAFFIC["sources_sha256"]:
+        traffic = TRAFFIC["bytes_per_sample"] * n
     h2d = 2 * n_f * 16
     d2h = n_f * 32 + (n_f + 3) * 8
     if rank == 0:
@@ -256,7 +280,8 @@ def run_tami(args):
                        "mu": CFG["mu"], "l2": "flushed before every step (256 MiB write)",
                        "parallelism": f"samples sharded over {world} GPU(s)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                         "traffic_unit": "bytes per launch (ncu capture, scaled per sample)",
                          "kernel": dom[0], "flops_per_launch": dom[1],
                          "fwd_kernel_tflops": fl_f / (tf * 1e-3) / 1e12,
                          "bwd_kernel_tflops": fl_b / (tb * 1e-3) / 1e12,

@@ -184,7 +184,9 @@ __device__ __forceinline__ double rcp(double d) {
 }
 
 // d^k/dx^k g at (g, h = 1 - g): (-beta)^k sum_i (-1)^i A(k,i) g^(i+1) h^(k-i), A = Eulerian
-__device__ __forceinline__ double fermi_poly(int k, double g, double h, double beta) {
+// Out of line: derivative values are few per sample, and one copy keeps the kernels' code small
+// (instruction-fetch stalls are measurable in the adjoint).
+static __device__ __noinline__ double fermi_poly(int k, double g, double h, double beta) {
   if (k == 0) return g;
   double gh = g * h;
   if (k == 1) return -beta * gh;

@@ -626,7 +626,7 @@ int flatten(tami_diagram* d) {
   double fl = 0.0;
   fl += 3.0 * 2 * m;                                    // u -> k: mul + fma per component
   fl += 2.0 * 2.0 * n_lm;                               // line momenta, fma per nonzero label and dimension
-  fl += h.n_rep * (2.0 * 34.0 + 6.0);                   // cos of both components, energy
+  fl += h.n_rep * (2.0 * 30.0 + 6.0);                   // cos of both components (reduction 9, series 21), energy
   fl += 2.0 * nnz;                                      // energy combinations
   for (const Seg& g : segs) {
     fl += 1.0 + 23.0 + (g.sigma < 0 ? 2.0 : 0.0);       // -beta|x|; e^t (10 fma, 3 add/mul); e^t - 1
@@ -660,7 +660,7 @@ int flatten(tami_diagram* d) {
   // pole tree in the adjoint (the forward pass is counted in fl): per edge an fma into the
   // Fermi-value adjoint and, for inner edges, a mul for the child's adjoint
   bl += 2.0 * ops.size() + 1.0 * n_inner;
-  bl += h.n_rep_ext * 2.0 * 27.0;                       // sin of both components where k_ext enters
+  bl += h.n_rep_ext * 2.0 * 21.0;                       // sin of both components where k_ext enters (series)
   bl += ng2cd;                                          // p W per group factor
   bl += 3.0 * h.n_fv + 2.0 * nnz + h.n_rep + 10.0 * h.n_rep_ext;   // fvbar -> x -> E -> (mu, k_ext)
   I.bwd_flops_per_sample = bl;
