@@ -30,6 +30,19 @@ from paper_2311_17189_gb300 import workloads as W  # noqa: E402
 
 CFG = W.ORDER4
 FP64_PEAK_TFLOPS = 1.2586   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+
+
+def _hbm_peak_gbs():
+    """Measured copy bandwidth (read + write) from MEASURED_PEAKS.json, else 6800 GB/s (the
+    fallback measurement on a GB300)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _hbm_peak_gbs()
 METRIC = "order-4 Sigma evals/s (samples x terms x frequencies, FP64), forward + adjoint"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel from one ncu
@@ -300,6 +313,126 @@ def run_tami(args):
     return 0
 
 
+def run_workload(args):
+    """The other configurations of the method, timed on one GPU (parity for each is in tests/):
+    order5 (forward + adjoint at four temperatures), order3_real (forward + adjoint on the real
+    axis), all_orders (every order-2..5 diagram in one persistent graph launch, forward) and
+    energy_x1 (the paper's energy-input example).  Prints one JSON line; not the headline metric."""
+    import torch
+    import paper_2311_17189_gb300 as T
+
+    torch.cuda.set_device(0)
+    dev = "cuda:0"
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    wl = args.workload
+    launches_per_step = 0
+    if wl in ("order5", "order3_real"):
+        c = W.ORDER5 if wl == "order5" else W.ORDER3_REAL
+        if wl == "order5":
+            d = next(x for x in T.enumerate_sigma(c["order"]) if x["code"] == tuple(c["code"]))
+            betas = c["betas"]
+            Xs = [W.matsubara(b, c["n_freq"]) for b in betas]
+        else:
+            d = T.enumerate_sigma(c["order"])[c["diagram_index"]]
+            betas = (c["beta"],)
+            Xs = [W.real_axis(*c["omega"], c["gamma"])]
+        D = T.Diagram(d["alpha"], eps=d["eps"]).upload(0)
+        info = D.info()
+        n = c["n_samples"]
+        lat = W.lattice(c)
+        Xd = [torch.as_tensor(X, dtype=torch.complex128, device=dev) for X in Xs]
+        Gd = [torch.full_like(x, 1.0 + 0.5j) for x in Xd]
+        n_f = len(Xs[0])
+
+        def step(i):
+            for b, X, G in zip(betas, Xd, Gd):
+                D.forward(lat, c["seed"], i * n, n, X, b)
+                D.backward(lat, c["seed"], i * n, n, X, b, G)
+        launches_per_step = 4 * len(betas)
+        evals = float(n) * info["n_terms"] * n_f * len(betas)
+        flops = len(betas) * n * (info["flops_per_sample"] + n_f * info["flops_per_sample_freq"] +
+                                  info["bwd_flops_per_sample"] + n_f * info["bwd_flops_per_sample_freq"])
+        config = {"workload": c["name"], "samples": n, "frequencies": n_f, "terms": info["n_terms"],
+                  "betas": list(betas), "step": "forward + adjoint at every beta"}
+        bytes_step = None
+    elif wl == "all_orders":
+        c = W.ALL_ORDERS
+        lib = []
+        for m in c["orders"]:
+            for d in T.enumerate_sigma(m):
+                lib.append(T.Diagram(d["alpha"], eps=d["eps"], prefactor=(-1.0) ** m * (-1.0) ** d["loops"]))
+        counts = [W.all_orders_samples(k) for k in range(len(lib))]
+        seeds = [c["seed"] + k for k in range(len(lib))]
+        X = W.matsubara(c["beta"], c["n_freq"])
+        n_f = len(X)
+        for D in lib:
+            D.upload(0)
+        B = T.Batch(lib, counts, seeds, n_f)            # chunk size from the autotuner
+        lat = W.lattice(c)
+        Xd = torch.as_tensor(X, dtype=torch.complex128, device=dev)
+
+        def step(i):
+            B.launch(lat, Xd, c["beta"])
+        launches_per_step = 2
+        infos = [D.info() for D in lib]
+        evals = float(sum(k * inf["n_terms"] * n_f for k, inf in zip(counts, infos)))
+        flops = sum(k * (inf["flops_per_sample"] + n_f * inf["flops_per_sample_freq"]) for k, inf in zip(counts, infos))
+        config = {"workload": c["name"], "diagrams": len(lib), "samples": int(sum(counts)), "frequencies": n_f,
+                  "terms": int(sum(inf["n_terms"] for inf in infos)), "beta": c["beta"],
+                  "step": "one graph launch of the persistent kernel (forward)", "plan": B.info()}
+        bytes_step = None
+    elif wl == "energy_x1":
+        c = W.ENERGY_X1
+        D = T.Diagram(c["alpha"]).upload(0)
+        info = D.info()
+        E = torch.as_tensor(W.random_energies(c["n_e"], c["alpha"].shape[0], a=c["a"], seed=c["seed"]), device=dev)
+        X = torch.as_tensor(W.matsubara(c["beta"], c["n_freq"]), dtype=torch.complex128, device=dev)
+        n_f = c["n_freq"]
+
+        def step(i):
+            D.eval_energies(E, X, c["beta"])
+        launches_per_step = 1
+        evals = float(c["n_e"]) * info["n_terms"] * n_f
+        flops = c["n_e"] * (info["flops_per_sample"] + n_f * info["flops_per_sample_freq"])
+        bytes_step = c["n_e"] * (8 * c["alpha"].shape[0] + 16 * n_f)
+        config = {"workload": c["name"], "rows": c["n_e"], "frequencies": n_f, "terms": info["n_terms"],
+                  "beta": c["beta"], "step": "tami_eval_energies, full [n_f][n_e] output"}
+    else:
+        raise SystemExit(f"unknown workload {wl}")
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    ms = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(args.warmup + i)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    t = float(np.mean(ms))
+    tflops = flops / (t * 1e-3) / 1e12
+    line = {"metric": f"{config['workload']} evals/s (samples x terms x frequencies, FP64)",
+            "value": evals / (t * 1e-3), "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "config": config,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tflops / FP64_PEAK_TFLOPS, "flops_per_step": flops},
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk}
+    if bytes_step is not None:
+        gbs = bytes_step / (t * 1e-3) / 1e9
+        line["hbm"] = {"achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": gbs / HBM_PEAK_GBS,
+                       "algorithmic_bytes_per_step": bytes_step}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -309,9 +442,13 @@ def main():
     p.add_argument("--ref-samples", type=int, default=1 << 12)
     p.add_argument("--samples", type=int, default=CFG["n_samples"], help="samples per GPU (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="order4", choices=["order4", "order5", "order3_real", "all_orders", "energy_x1"],
+                   help="order4 is the headline metric; the others time the remaining configurations on one GPU")
     args = p.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "order4":
+        return run_workload(args)
     return run_tami(args)
 
 
