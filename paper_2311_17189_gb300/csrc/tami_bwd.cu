@@ -27,7 +27,7 @@ using namespace dev;
 
 // per-thread capacities of the adjoint (checked before launch)
 constexpr int kBwCombos = 64, kBwFv = 128, kBwRden = 32, kBwCden = 32, kBwG1 = 128, kBwG2 = 64;
-constexpr int kBwFreq = 256, kBwInner = 768, kBwG2cd = 256;
+constexpr int kBwFreq = 256, kBwNodes = 1024, kBwG2cd = 256;
 
 struct BwdParams {
   TableHeader h;
@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
   const double* cden_a = reinterpret_cast<const double*>(smem + H.off_cden_a);
   const int* g1 = reinterpret_cast<const int*>(smem + H.off_g1);
   const int* g1_tgt = reinterpret_cast<const int*>(smem + H.off_g1_tgt);
-  const int2* ops = reinterpret_cast<const int2*>(smem + H.off_ops);
+  const int2* opsb = reinterpret_cast<const int2*>(smem + H.off_opsb);
+  const int* g1_node = reinterpret_cast<const int*>(smem + H.off_g1_node);
   const double* leafA = reinterpret_cast<const double*>(smem + H.off_leafA);
   const int* g1rd = reinterpret_cast<const int*>(smem + H.off_g1rd);
   const int* g2 = reinterpret_cast<const int*>(smem + H.off_g2);
@@ -219,25 +220,20 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
     for (int b = H.n_fseg_bose; b < H.n_fseg; ++b) fermi_segment<false, true>(fseg + 8 * b, fvr, x, beta, fv, fvd);
     double rr[kBwRden];
     for (int i = 0; i < H.n_rden; ++i) rr[i] = rcp(x[rden[2 * i]]);
-    // pole trees, keeping each inner node's value (cv) for the reverse sweep
-    double W1[kBwG1], W2[kBwG2], cv[kBwInner];
-    int nc = 0;
+    // pole trees (adjoint encoding: one slot per node), keeping every node's value for the reverse
+    double W1[kBwG1], W2[kBwG2], val[kBwNodes];
     for (int h = 0; h < H.n_g2; ++h) W2[h] = 0.0;
+    val[0] = 0.0;
     for (int gi = 0; gi < H.n_g1; ++gi) {
-      double ft;
-      {
-        double acc[kMaxDepth + 1];
-        for (int o = g1[4 * gi]; o < g1[4 * gi + 1]; ++o) {
-          const int2 op = ops[o];
-          const int dd = op.x & 63;
-          const bool leaf = op.x & kOpLeaf;
-          if (!leaf) cv[nc++] = acc[dd];
-          const double operand = leaf ? leafA[op.x >> kOpLeafShift] : acc[dd];
-          const double addend = (op.x & kOpFirst) ? 0.0 : acc[dd - 1];
-          acc[dd - 1] = fma(fv[op.y], operand, addend);
-        }
-        ft = acc[0];
+      for (int o = g1[4 * gi]; o < g1[4 * gi + 1]; ++o) {
+        const int2 op = opsb[o];
+        const int dst = op.x & kOpbDstMask, ref = op.x >> kOpbRefShift;
+        const bool leaf = op.x & kOpbLeaf;
+        const double a = leafA[leaf ? ref : 0], b = val[leaf ? 0 : ref];
+        const double addend = (op.x & kOpbFirst) ? 0.0 : val[dst];
+        val[dst] = fma(fv[op.y], leaf ? a : b, addend);
       }
+      double ft = val[g1_node[gi]];
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
         const double r = rr[g1rd[2 * q]];
         for (int pw = g1rd[2 * q + 1]; pw > 0; --pw) ft *= r;
@@ -269,7 +265,6 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
       const int u = cden[2 * c];
       xbar[u] += cden[2 * c + 1] > 0 ? bb[c] : -bb[c];
     }
-    // groups in reverse, so that the inner-node values come off cv in reverse order
     for (int gi = H.n_g1 - 1; gi >= 0; --gi) {
       const double wb = Wb2[g1_tgt[gi]];
       double RR = 1.0;
@@ -280,26 +275,28 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
         // W1 = FT prod rr^p and rr = 1/x:  dW1/dx = -p rr W1
         xbar[rden[2 * i]] -= wb * W1[gi] * (double)pw * rr[i];
       }
-      // pole tree, reverse: for the edge acc[d-1] += F * operand,
-      //   Fbar += operand * accbar[d-1]  and, below inner edges only,  accbar[d] = F * accbar[d-1];
-      // a parent's run of leaves shares accbar[d-1] and needs no child adjoint
-      const int o0 = g1[4 * gi];
-      double bar[kMaxDepth + 1];
-      bar[0] = wb * RR;
+      // pole tree, reverse: for the edge v[dst] += F * operand,
+      //   Fbar += operand * vbar[dst]  and, for inner edges,  vbar[ref] += F * vbar[dst];
+      // a node's run of leaf edges shares vbar[dst].  Post order puts every use of a node after its
+      // own edges, so walking backwards completes vbar of a node before its edges are reached.
+      const int o0 = g1[4 * gi], nb = g1_node[gi], ne = g1_node[gi + 1];
+      double bar[kBwNodes];
+      for (int k = nb + 1; k < ne; ++k) bar[k] = 0.0;
+      bar[nb] = wb * RR;
       for (int o = g1[4 * gi + 1] - 1; o >= o0;) {
-        const int2 op = ops[o];
-        const int dd = op.x & 63;
-        const double pb = bar[dd - 1];
-        if (op.x & kOpLeaf) {
-          const int run = max((op.x >> kOpRunShift) & 255, 1);   // >= 1: the walk always advances
+        const int2 op = opsb[o];
+        const double pb = bar[op.x & kOpbDstMask];
+        if (op.x & kOpbLeaf) {
+          const int run = max((op.x >> kOpbRunShift) & 255, 1);   // >= 1: the walk always advances
           for (int i = 0; i < run; ++i) {
-            const int2 q = ops[o - i];
-            fvbar[q.y] = fma(leafA[q.x >> kOpLeafShift], pb, fvbar[q.y]);
+            const int2 q = opsb[o - i];
+            fvbar[q.y] = fma(leafA[q.x >> kOpbRefShift], pb, fvbar[q.y]);
           }
           o -= run;
         } else {
-          fvbar[op.y] = fma(cv[--nc], pb, fvbar[op.y]);
-          bar[dd] = fv[op.y] * pb;
+          const int ref = op.x >> kOpbRefShift;
+          fvbar[op.y] = fma(val[ref], pb, fvbar[op.y]);
+          bar[ref] = fma(fv[op.y], pb, bar[ref]);
           --o;
         }
       }
@@ -406,7 +403,7 @@ int bwd_check(const tami_diagram* d, int n_f) {
   const TableHeader& h = d->hdr;
   if (h.max_der > 4) { set_error("the adjoint needs derivative orders up to 4"); return TAMI_EUNSUPPORTED; }
   if (h.n_combo > kBwCombos || h.n_fv > kBwFv || h.n_rden > kBwRden || h.n_cden > kBwCden ||
-      h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || h.n_inner > kBwInner || h.n_g2cd > kBwG2cd) {
+      h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || h.n_nodes > kBwNodes || h.n_g2cd > kBwG2cd) {
     set_error("term table exceeds the adjoint kernel's per-sample capacities");
     return TAMI_EUNSUPPORTED;
   }

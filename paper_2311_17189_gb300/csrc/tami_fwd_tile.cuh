@@ -62,18 +62,23 @@ __device__ __forceinline__ TableView table_view(const unsigned char* t, const Ta
 }
 
 // Sum over a group's terms of A_t prod FT factors, by the group's pole-tree program: one fma per
-// tree edge, acc[d-1] = F * (leaf ? A_leaf : acc[d]) + (first child ? 0 : acc[d-1]); the root's
-// sum ends in acc[0].  Every group has at least one edge.
+// edge of the (shared-sub-sum) tree, v[dst] = F * (leaf ? A[ref] : v[ref]) + (first ? 0 : v[dst]),
+// over value slots; the root's sum is written by the group's last op.  Both operand loads use
+// in-range indices, the select picks one.
 __device__ __forceinline__ double pole_tree(const TableView& T, int op0, int op1, const double* fv) {
-  double acc[kMaxDepth + 1];
+  double v[kMaxSlots];
+  v[0] = 0.0;
+  int dst = 0;
   for (int o = op0; o < op1; ++o) {
     const int2 op = T.ops[o];
-    const int d = op.x & 63;
-    const double operand = (op.x & kOpLeaf) ? T.leafA[op.x >> kOpLeafShift] : acc[d];
-    const double addend = (op.x & kOpFirst) ? 0.0 : acc[d - 1];
-    acc[d - 1] = fma(fv[op.y], operand, addend);
+    dst = op.x & kOpDstMask;
+    const int ref = op.x >> kOpRefShift;
+    const bool leaf = op.x & kOpLeaf;
+    const double a = T.leafA[leaf ? ref : 0], b = v[leaf ? 0 : ref];
+    const double addend = (op.x & kOpFirst) ? 0.0 : v[dst];
+    v[dst] = fma(fv[op.y], leaf ? a : b, addend);
   }
-  return acc[0];
+  return v[dst];
 }
 
 // Phase-2 assignment of (frequency, sample) pairs: tpf threads per frequency when n_f <= block,

@@ -403,13 +403,16 @@ int flatten(tami_diagram* d) {
   // level a node branches on is chosen per node: the one with the fewest distinct Fermi values
   // among the node's terms (the usual greedy ordering for small decision trees; ties go to the
   // later residue step), unless the fixed reverse residue order gives fewer edges for the group.
-  // Emitted in post order as a program over a stack of accumulators, one fma per tree edge: for
-  // the edge to child c at depth d,
-  //   acc[d-1] = F_c * (c is a leaf ? A_c : acc[d]) + (c is its parent's first child ? 0 : acc[d-1]).
-  std::vector<std::pair<int, int>> ops;   // (d | first << 6 | leaf << 7 | run << 8 | leaf index << 16, fv)
+  // Identical sub-sums are then shared (a DAG), and the group is emitted in post order as a
+  // program of one fma per edge over value slots:
+  //   v[dst] = F_c * (c is a leaf ? A_c : v[c]) + (c is dst's first child ? 0 : v[dst]).
+  // Two encodings of the same ops: `ops` for the forward with slots reused by liveness (kOp*),
+  // `opsb` for the adjoint with one slot per node, every value kept for the reverse walk (kOpb*).
+  std::vector<std::pair<int, int>> ops, opsb;
   std::vector<double> leafA;
   std::vector<std::pair<int, int>> g1_ops(g1s.size());
-  int n_inner = 0;
+  std::vector<int> g1_node(g1s.size() + 1, 0);
+  int n_inner = 0, max_slots = 0, node_base = 0;
   const int m_depth = nv - 1;
   struct Node { int fv; std::vector<int> kids; double A; };
   auto build_tree = [&](const std::vector<int>& terms, bool greedy) {
@@ -453,33 +456,89 @@ int flatten(tami_diagram* d) {
     std::vector<Node> fixed = build_tree(g1s[g].terms, false);
     if (fixed.size() <= nodes.size()) nodes.swap(fixed);
     const int begin = (int)ops.size();
-    std::function<void(int, int)> emit = [&](int u, int d) {   // children of u sit at depth d + 1
-      const int nk = (int)nodes[u].kids.size();
-      for (int i = 0; i < nk; ++i) {
-        const int c = nodes[u].kids[i];
-        const int first = i == 0 ? 1 : 0;
-        if (d + 1 == m_depth) {       // every child of u is a leaf: the last one carries the run length
-          const int run = i == nk - 1 ? nk : 0;
-          ops.push_back({(d + 1) | (first << 6) | kOpLeaf | (run << kOpRunShift) |
-                         ((int)leafA.size() << kOpLeafShift), nodes[c].fv});
-          leafA.push_back(nodes[c].A);
-        } else {
-          emit(c, d + 1);
-          ops.push_back({(d + 1) | (first << 6), nodes[c].fv});
-          ++n_inner;
+    // Identical sub-sums are computed once: nodes are hash-consed bottom-up on their sorted
+    // (Fermi value, child) lists (a leaf is its coefficient), which turns the tree into a DAG.
+    std::map<long long, int> leaf_uid;                  // coefficient bits -> index into leafA
+    std::map<std::vector<std::pair<int, int>>, int> inner_uid;
+    std::vector<std::vector<std::pair<int, int>>> ukids;   // (fv, child: >= 0 inner uid, < 0 -(leaf index + 1))
+    std::function<int(int)> canon = [&](int u) -> int {
+      if (nodes[u].kids.empty()) {
+        long long bits;
+        std::memcpy(&bits, &nodes[u].A, sizeof bits);
+        auto it = leaf_uid.find(bits);
+        if (it == leaf_uid.end()) {
+          it = leaf_uid.emplace(bits, (int)leafA.size()).first;
+          leafA.push_back(nodes[u].A);
         }
+        return -(it->second + 1);
       }
+      std::vector<std::pair<int, int>> key;
+      for (int c : nodes[u].kids) key.push_back({nodes[c].fv, canon(c)});
+      std::sort(key.begin(), key.end());
+      auto it = inner_uid.find(key);
+      if (it != inner_uid.end()) return it->second;
+      const int id = (int)ukids.size();
+      inner_uid.emplace(key, id);
+      ukids.push_back(key);
+      return id;
     };
-    for (const Node& nd : nodes)
-      if (nd.kids.size() > 255) { set_error("pole tree node with more than 255 children"); return TAMI_EUNSUPPORTED; }
-    emit(0, 0);
-    if (leafA.size() >= (1u << 15)) { set_error("pole tree with too many leaves"); return TAMI_EUNSUPPORTED; }
+    const int root = canon(0);
+    // post order over the unique nodes, children first; node ids for the adjoint: root first
+    struct Op { int dst, ref, fv, first, leaf, run; };
+    std::vector<Op> gops;
+    std::vector<int> gid(ukids.size(), -1);
+    int n_gid = 0;
+    gid[root] = n_gid++;
+    std::vector<char> done(ukids.size(), 0);
+    std::function<void(int)> emit = [&](int id) {
+      for (auto& kr : ukids[id]) if (kr.second >= 0 && !done[kr.second]) emit(kr.second);
+      if (gid[id] < 0) gid[id] = n_gid++;
+      const int nk = (int)ukids[id].size();
+      for (int i = 0; i < nk; ++i) {
+        const auto& kr = ukids[id][i];
+        const bool leaf = kr.second < 0;
+        gops.push_back({id, leaf ? -kr.second - 1 : kr.second, kr.first, i == 0 ? 1 : 0, leaf ? 1 : 0,
+                        leaf && i == nk - 1 ? nk : 0});
+      }
+      done[id] = 1;
+    };
+    emit(root);
+    // forward slots: linear scan, a node's slot from its first edge to its last use
+    std::vector<int> last_use(ukids.size(), -1), slot(ukids.size(), -1), free_slots;
+    for (size_t p = 0; p < gops.size(); ++p) if (!gops[p].leaf) last_use[gops[p].ref] = (int)p;
+    int n_live = 0;
+    const int base = node_base;
+    for (size_t p = 0; p < gops.size(); ++p) {
+      const Op& o = gops[p];
+      if (slot[o.dst] < 0) {
+        if (!free_slots.empty()) { slot[o.dst] = free_slots.back(); free_slots.pop_back(); }
+        else slot[o.dst] = n_live++;
+      }
+      const int fref = o.leaf ? o.ref : slot[o.ref];
+      const int bref = o.leaf ? o.ref : base + gid[o.ref];
+      if (o.run > 255 || n_live > kMaxSlots || base + n_gid > (1 << kOpbDstBits) || fref >= (1 << 23) ||
+          bref >= (1 << (32 - kOpbRefShift - 1))) {
+        set_error("pole tree exceeds the program's encodable sizes");
+        return TAMI_EUNSUPPORTED;
+      }
+      ops.push_back({slot[o.dst] | (o.first ? kOpFirst : 0) | (o.leaf ? kOpLeaf : 0) | (fref << kOpRefShift), o.fv});
+      opsb.push_back({(base + gid[o.dst]) | (o.first ? kOpbFirst : 0) | (o.leaf ? kOpbLeaf : 0) |
+                      (o.run << kOpbRunShift) | (bref << kOpbRefShift), o.fv});
+      if (!o.leaf) ++n_inner;
+      if (!o.leaf && last_use[o.ref] == (int)p) free_slots.push_back(slot[o.ref]);
+    }
+    max_slots = std::max(max_slots, n_live);
+    g1_node[g] = base;
+    node_base += n_gid;
     g1_ops[g] = {begin, (int)ops.size()};
   }
   h.n_ops = (int)ops.size();
   h.n_leaves = (int)leafA.size();
   h.max_depth = m_depth;
   h.n_inner = n_inner;
+  h.n_slots = max_slots;
+  h.n_nodes = node_base;
+  g1_node[g1s.size()] = node_base;
   int ng1rd = 0, ng2cd = 0;
   const int n_mul_ops = (int)ops.size();
   for (auto& g : g1s) ng1rd += (int)g.rd.size();
@@ -510,6 +569,8 @@ int flatten(tami_diagram* d) {
   h.off_g1 = B.reserve(sizeof(int) * 4 * h.n_g1);
   h.off_g1_tgt = B.reserve(sizeof(int) * h.n_g1);
   h.off_ops = B.reserve(sizeof(int) * 2 * h.n_ops);
+  h.off_opsb = B.reserve(sizeof(int) * 2 * h.n_ops);
+  h.off_g1_node = B.reserve(sizeof(int) * (h.n_g1 + 1));
   h.off_leafA = B.reserve(sizeof(double) * h.n_leaves);
   h.off_g1rd = B.reserve(sizeof(int) * 2 * ng1rd);
   h.off_g2 = B.reserve(sizeof(int) * (h.n_g2 + 1));
@@ -570,7 +631,10 @@ int flatten(tami_diagram* d) {
   for (int o = 0; o < h.n_ops; ++o) {
     B.at<int>(h.off_ops)[2 * o] = ops[o].first;
     B.at<int>(h.off_ops)[2 * o + 1] = ops[o].second;
+    B.at<int>(h.off_opsb)[2 * o] = opsb[o].first;
+    B.at<int>(h.off_opsb)[2 * o + 1] = opsb[o].second;
   }
+  for (int g = 0; g <= h.n_g1; ++g) B.at<int>(h.off_g1_node)[g] = g1_node[g];
   for (int i = 0; i < h.n_leaves; ++i) B.at<double>(h.off_leafA)[i] = leafA[i];
   {
     int rdpos = 0;
@@ -658,8 +722,8 @@ int flatten(tami_diagram* d) {
     bl += 1.0;
   }
   // pole tree in the adjoint (the forward pass is counted in fl): per edge an fma into the
-  // Fermi-value adjoint and, for inner edges, a mul for the child's adjoint
-  bl += 2.0 * ops.size() + 1.0 * n_inner;
+  // Fermi-value adjoint and, for inner edges, an fma into the child's adjoint
+  bl += 2.0 * ops.size() + 2.0 * n_inner;
   bl += h.n_rep_ext * 2.0 * 21.0;                       // sin of both components where k_ext enters (series)
   bl += ng2cd;                                          // p W per group factor
   bl += 3.0 * h.n_fv + 2.0 * nnz + h.n_rep + 10.0 * h.n_rep_ext;   // fvbar -> x -> E -> (mu, k_ext)

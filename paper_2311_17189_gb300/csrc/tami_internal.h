@@ -23,11 +23,16 @@ constexpr int kMaxProdNodes = 64;    // phase-2 product nodes beyond the recipro
 constexpr int kMaxDer = 5;
 constexpr int kMaxDepth = kMaxVars;   // pole-tree depth = number of summed variables
 
-// pole-tree program op (see flatten): acc[d-1] = F * (leaf ? A_leaf : acc[d]) + (first ? 0 : acc[d-1]);
-// x = d | first << 6 | leaf << 7 | run << 8 | leaf index << 16, y = Fermi value.  run (8 bits) is
-// set on the last leaf of each parent's run of leaves: the number of leaves in that run.
-enum { kOpFirst = 1 << 6, kOpLeaf = 1 << 7 };
-constexpr int kOpRunShift = 8, kOpLeafShift = 16;
+// Pole-tree programs (see flatten): one op per edge, v[dst] = F * (leaf ? A[ref] : v[ref]) +
+// (first ? 0 : v[dst]); y = Fermi value.
+// Forward encoding (slots reused by liveness): x = dst | first << 6 | leaf << 7 | ref << 8.
+constexpr int kOpDstMask = 63, kOpFirst = 1 << 6, kOpLeaf = 1 << 7, kOpRefShift = 8;
+constexpr int kMaxSlots = 64;
+// Adjoint encoding (one slot per node, ids per diagram): x = dst | first << 11 | leaf << 12 |
+// run << 13 | ref << 21.  run (8 bits) is set on the last leaf edge of a node: its number of
+// leaf edges, which share the node's adjoint.
+constexpr int kOpbDstBits = 11, kOpbDstMask = (1 << kOpbDstBits) - 1, kOpbFirst = 1 << 11, kOpbLeaf = 1 << 12,
+              kOpbRunShift = 13, kOpbRefShift = 21;
 
 void set_error(const std::string& msg);
 
@@ -64,6 +69,7 @@ struct TableHeader {
   int n_rden, n_cden;
   int n_g1, n_ops, n_leaves, n_g1rd;
   int max_depth, n_inner;      // pole-tree depth (= m) and inner (non-leaf) edges over all groups
+  int n_slots, n_nodes;        // forward value slots (most live in one group); DAG nodes over all groups
   int n_g2, n_g2cd;
   int n_pnode;      // phase-2 product nodes
   int g2_const;     // 1 if group 0 of phase 2 has no frequency-dependent factor (R = 1)
@@ -86,8 +92,9 @@ struct TableHeader {
   int off_cden_a;     // double [n_cden]          external-frequency coefficient
   int off_g1;         // int32 [n_g1][4]         op_begin, op_end, rd_begin, rd_end
   int off_g1_tgt;     // int32 [n_g1]             frequency group it feeds (ascending)
-  int off_ops;        // int2 [n_ops]            pole-tree program: x = d | first<<6 | leaf<<7 | run<<8 |
-                      //                         leaf index<<16, y = Fermi value
+  int off_ops;        // int2 [n_ops]            pole-tree program, forward encoding (kOp*)
+  int off_opsb;       // int2 [n_ops]            the same program, adjoint encoding (kOpb*)
+  int off_g1_node;    // int32 [n_g1+1]           first adjoint node id of each group (its root)
   int off_leafA;      // double [n_leaves]        merged coefficients of the leaves
   int off_g1rd;       // int32 [n_g1rd][2]       real-den index, power
   int off_g2;         // int32 [n_g2+1]          complex-den offsets
