@@ -134,12 +134,19 @@ int tami_upload(tami_diagram* d, int device, tami_stream_t stream);
 int tami_sample_energies(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
                          int64_t n, double* E, tami_stream_t stream);
 
+/* Errors common to the evaluating calls (tami_eval_energies, tami_forward, tami_forward_noalloc,
+ * tami_backward, tami_batch_launch): TAMI_EINVAL, with nothing launched, for beta not finite and
+ * positive, n_f outside the call's range, a required pointer NULL, a sample count below 1 (0 rows
+ * is allowed in energy input and launches nothing), or a diagram that is not uploaded or was
+ * uploaded to another device than the current one.  The library stays usable after an error. */
+
 /* Energy-input evaluation (Sec. 2.3, energy_t / frequency_t): for each configuration i and
  * external frequency f, the sum over terms of A * FT(E_i) * R(E_i, X_f).
  *   E    device double [n_e][n_lines] base energies.
  *   X    device double [n_f][2] external frequencies (i nu_n, or omega + i Gamma after analytic
  *        continuation).
- *   out  device double [n_f][n_e][2] (rows are frequencies, Sec. 2.3). */
+ *   out  device double [n_f][n_e][2] (rows are frequencies, Sec. 2.3).
+ * n_e = 0 launches nothing (E and out may then be NULL). */
 int tami_eval_energies(const tami_diagram* d, const double* E, int64_t n_e, const double* X, int n_f,
                        double beta, double* out, tami_stream_t stream);
 

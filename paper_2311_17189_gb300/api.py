@@ -62,6 +62,11 @@ class Diagram:
         L.check(L.lib().tami_diagram_info(self._h, ctypes.byref(i)))
         return {k: getattr(i, k) for k, _ in L.Info._fields_}
 
+    def _dev(self):
+        if self.device is None:
+            raise L.TamiError(L.TAMI_EINVAL, "diagram not uploaded (call upload)")
+        return f"cuda:{self.device}"
+
     def upload(self, device=None):
         torch = _torch()
         dev = torch.cuda.current_device() if device is None else int(device)
@@ -73,7 +78,7 @@ class Diagram:
     # ---------------------------------------------------------------- evaluation
     def sample_energies(self, lattice, seed, offset, n):
         torch = _torch()
-        E = torch.empty((n, self.n_lines), dtype=torch.float64, device=f"cuda:{self.device}")
+        E = torch.empty((n, self.n_lines), dtype=torch.float64, device=self._dev())
         lat = L.Lattice(*[float(v) for v in lattice])
         L.check(L.lib().tami_sample_energies(self._h, ctypes.byref(lat), int(seed), int(offset), int(n),
                                              ctypes.c_void_p(E.data_ptr()), _stream_ptr()))
@@ -97,14 +102,14 @@ class Diagram:
         L.check(L.lib().tami_forward_workspace(self._h, int(n), int(n_f), ctypes.byref(nbytes)))
         need = (nbytes.value + 255) // 256 * 256
         if self._ws is None or self._ws.numel() < need:
-            self._ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
+            self._ws = torch.empty(need, dtype=torch.uint8, device=self._dev())
         return self._ws
 
     def forward(self, lattice, seed, offset, n, X, beta, per_sample=False, out=None):
         """Monte Carlo mean over n momentum samples (Sec. 5.2).  Returns (mean complex [n_f],
         var float64 [n_f, 2], per-sample complex [n_f, n] or None)."""
         torch = _torch()
-        dev = f"cuda:{self.device}"
+        dev = self._dev()
         Xp = _as_c_pairs(X, dev)
         n_f = Xp.shape[0]
         if out is None:
@@ -128,7 +133,7 @@ class Diagram:
         (float64 [3]: mu, kx_ext, ky_ext) and, with per_sample, dX (complex [n_f, n]) and
         grads (float64 [n, 3])."""
         torch = _torch()
-        dev = f"cuda:{self.device}"
+        dev = self._dev()
         Xp = _as_c_pairs(X, dev)
         Gp = _as_c_pairs(gout, dev)
         n_f = Xp.shape[0]

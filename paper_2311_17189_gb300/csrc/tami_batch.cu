@@ -475,6 +475,7 @@ int tami_batch_info(const tami_batch* b, int* n_items, int* grid, int* chunk_til
 int tami_batch_launch(tami_batch* b, const tami_lattice* lat, const double* X, double beta, double* mean, double* var,
                       tami_stream_t stream) {
   if (!b || !lat || !X || !mean) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (!beta_ok(beta)) return TAMI_EINVAL;
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != b->device) { set_error("current device differs from the plan's device"); return TAMI_EINVAL; }

@@ -436,6 +436,7 @@ int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed,
   int rc = bwd_check(d, n_f);
   if (rc) return rc;
   if (!lat || !X || !gout || !workspace || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (!beta_ok(beta)) return TAMI_EINVAL;
   if (((uintptr_t)workspace & 255) != 0) { set_error("workspace must be 256-byte aligned"); return TAMI_EINVAL; }
   size_t smem = 0;
   const int grid = bwd_grid(d, n_f, n_samples, &smem);

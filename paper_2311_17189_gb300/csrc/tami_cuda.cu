@@ -273,8 +273,10 @@ int tami_eval_energies(const tami_diagram* d, const double* E, int64_t n_e, cons
                        double beta, double* out, tami_stream_t stream) {
   int rc = check_common(d, n_f);
   if (rc) return rc;
-  if (!E || !X || !out || n_e < 0) { set_error("bad argument"); return TAMI_EINVAL; }
-  if (n_e == 0) return TAMI_OK;
+  if (n_e < 0) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (!beta_ok(beta)) return TAMI_EINVAL;
+  if (n_e == 0) return TAMI_OK;              // nothing to read or write: E and out may be NULL
+  if (!E || !X || !out) { set_error("bad argument"); return TAMI_EINVAL; }
   FwdParams P = make_params(d, n_f, beta);
   P.n = n_e;
   P.E_in = E;
@@ -298,6 +300,7 @@ int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, 
   int rc = check_common(d, n_f);
   if (rc) return rc;
   if (!lat || !X || !mean || !workspace || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (!beta_ok(beta)) return TAMI_EINVAL;
   if (((uintptr_t)workspace & 255) != 0) { set_error("workspace must be 256-byte aligned"); return TAMI_EINVAL; }
   const int grid = grid_for(d, n_f, n_samples);
   const size_t need = kStatusBytes + sizeof(double) * 4 * (size_t)n_f * (size_t)grid;
@@ -330,6 +333,7 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
   int rc = check_common(d, n_f);
   if (rc) return rc;
   if (!lat || !X || !mean || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (!beta_ok(beta)) return TAMI_EINVAL;
   const int grid = grid_for(d, n_f, n_samples);
   const size_t need = kStatusBytes + sizeof(double) * 4 * (size_t)n_f * (size_t)grid;
   if (need > kNoAllocScratchBytes) {

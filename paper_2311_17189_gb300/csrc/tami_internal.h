@@ -3,6 +3,7 @@
 #pragma once
 
 #include <array>
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -35,6 +36,13 @@ constexpr int kOpbDstBits = 11, kOpbDstMask = (1 << kOpbDstBits) - 1, kOpbFirst 
               kOpbRunShift = 13, kOpbRefShift = 21;
 
 void set_error(const std::string& msg);
+
+// beta must be finite and positive (the kernels evaluate e^{-beta |x|}); sets the error text.
+inline bool beta_ok(double beta) {
+  if (beta > 0.0 && std::isfinite(beta)) return true;
+  set_error("beta must be finite and positive");
+  return false;
+}
 
 // Linear form  sum_l i a[l] nu_l + sum_j e[j] E_j.
 struct Form {
