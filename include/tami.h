@@ -248,9 +248,11 @@ int tami_enumerate_sigma(int order, int capacity, int8_t* alpha, int8_t* eps, in
                          int32_t* loops, int* n_out);
 
 /* Diagnostic: the kernels' exponential for t <= 0 (table-driven after Tang, ACM TOMS 1989), applied
- * elementwise: y = e^t, em = e^t - 1.  t, y, em: device double [n].  Used by the tests to check it
+ * elementwise: y = e^t, em = e^t - 1, and y_plain = e^t from the variant that does not form
+ * e^t - 1 (the kernels use it where only e^t is needed; it must equal y bit for bit).
+ * t, y, em, y_plain: device double [n]; y_plain may be NULL.  Used by the tests to check them
  * against CUDA's exp/expm1. */
-int tami_selftest_exp(const double* t, int64_t n, double* y, double* em, tami_stream_t stream);
+int tami_selftest_exp(const double* t, int64_t n, double* y, double* em, double* y_plain, tami_stream_t stream);
 
 void tami_destroy(tami_diagram* d);
 

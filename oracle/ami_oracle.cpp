@@ -104,18 +104,18 @@ void sample_momentum(uint64_t seed, uint64_t s, int l, double* kx, double* ky) {
   *ky = momentum_from_unit(unit53(w[2], w[3]));
 }
 
-// cos and sin by Cody-Waite reduction by pi (three-part constant), k = n pi + r with
+// cos and sin by Cody-Waite reduction by pi (two-part constant), k = n pi + r with
 // |r| <= pi/2 (n the nearest integer to k/pi), then Taylor series in r (terms to r^20 for cos
 // and r^21 for sin: truncation below 1.9e-17 and 1.3e-18 at |r| = pi/2) and the sign (-1)^n.
 void cw_sincos(double k, double* s_out, double* c_out) {
   const double inv_pi = 0x1.45f306dc9c883p-2;
-  const double P1 = 0x1.921fb54442d18p+1, P2 = 0x1.1a62633145c07p-53,
-               P3 = -0x1.f1976b7ed8fbcp-109;
+  const double P1 = 0x1.921fb54442d18p+1, P2 = 0x1.1a62633145c07p-53;
   // n = nearest integer to k/pi: k/pi + 1.5*2^52 rounded once leaves it in the low bits
   double n = std::fma(k, inv_pi, 0x1.8p52) - 0x1.8p52;
+  // k - n P1 is exact (a multiple of 2^-52 below 2 in magnitude); n times the third part of pi
+  // (3.8e-33) stays below the rounding for the momenta a lattice sample produces (|k| < 22)
   double r = std::fma(-n, P1, k);
   r = std::fma(-n, P2, r);
-  r = std::fma(-n, P3, r);
   double z = r * r;
   // (-1)^i / (2i)!, i = 1..10      (cos r = 1 + z (c1 + z (c2 + ...)))
   const double C[10] = {-0x1.0000000000000p-1, 0x1.5555555555555p-5, -0x1.6c16c16c16c17p-10,

@@ -85,7 +85,7 @@ def lib():
     L.tami_batch_destroy.argtypes = [vp]
     L.tami_batch_destroy.restype = None
     L.tami_enumerate_sigma.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
-    L.tami_selftest_exp.argtypes = [dp, i64, dp, dp, vp]
+    L.tami_selftest_exp.argtypes = [dp, i64, dp, dp, dp, vp]
     L.tami_destroy.argtypes = [vp]
     L.tami_destroy.restype = None
     _lib = L

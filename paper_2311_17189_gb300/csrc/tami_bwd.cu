@@ -64,7 +64,7 @@ __device__ __forceinline__ void bwd_phase2(const TableHeader& H, int n_f, long l
                                            const int* g2node, const double* pW, const double* b, double* Wb2,
                                            double* bb, double* accX) {
   for (int f = 0; f < n_f; ++f) {
-    const double Xr = Xs[2 * f], gr = Gs[2 * f], gim = Gs[2 * f + 1];
+    const double Xr = Xs[2 * f], gr = Gs[2 * f], gim = Gs[2 * f + 1], ngr = -gr, ngi = -gim;
     double vre[kBwCden + kMaxProdNodes], vim[kBwCden + kMaxProdNodes], U_re[kBwCden], U_im[kBwCden];
     for (int c = 0; c < H.n_cden; ++c) {
       const double Dr = XR_ZERO ? b[c] : fma(cden_a[c], Xr, b[c]);
@@ -97,7 +97,7 @@ __device__ __forceinline__ void bwd_phase2(const TableHeader& H, int n_f, long l
       const double Zi = fma(vre[c], U_im[c], vim[c] * U_re[c]);
       dvr = fma(-cden_a[c], Zr, dvr);
       dvi = fma(-cden_a[c], Zi, dvi);
-      bb[c] -= fma(gr, Zr, gim * Zi);
+      bb[c] = fma(ngr, Zr, fma(ngi, Zi, bb[c]));
     }
     accX[2 * f] += dvr;
     accX[2 * f + 1] += dvi;

@@ -106,12 +106,13 @@ __global__ void __launch_bounds__(kFinBlock) finalize_kernel(const double* parti
   if (var) { var[2 * f] = vr; var[2 * f + 1] = vi; }
 }
 
-__global__ void exp_selftest_kernel(const double* t, long long n, double* y, double* em) {
+__global__ void exp_selftest_kernel(const double* t, long long n, double* y, double* em, double* y_plain) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double e = 0.0;
   y[i] = exp_neg<true>(t[i], e);
   em[i] = e;
+  if (y_plain) y_plain[i] = exp_neg<false>(t[i], e);
 }
 
 __global__ void sample_energies_kernel(const FwdParams P, double* E) {
@@ -364,10 +365,10 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "finalize launch");
 }
 
-int tami_selftest_exp(const double* t, int64_t n, double* y, double* em, tami_stream_t stream) {
+int tami_selftest_exp(const double* t, int64_t n, double* y, double* em, double* y_plain, tami_stream_t stream) {
   if (!t || !y || !em || n < 0) { set_error("bad argument"); return TAMI_EINVAL; }
   if (n == 0) return TAMI_OK;
-  exp_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(t, n, y, em);
+  exp_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(t, n, y, em, y_plain);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "exp_selftest launch");
 }

@@ -35,23 +35,22 @@ __device__ __forceinline__ double to_momentum(uint32_t hi, uint32_t lo) {
   return fma(u, 2.0 * pi, -pi);
 }
 
-// cos and sin: Cody-Waite reduction by pi (three-part constant), k = n pi + r, |r| <= pi/2 (n the
+// cos and sin: Cody-Waite reduction by pi (two-part constant), k = n pi + r, |r| <= pi/2 (n the
 // integer nearest to k/pi, from one fma against 1.5 * 2^52), then
 // Taylor series in r (to r^20 for cos, r^21 for sin) and the sign (-1)^n (W. J. Cody and
 // W. Waite, 1980).  Every operation is an explicit fma or a rounded mul intrinsic, so the result
 // is the same on any IEEE machine that follows the same recipe.
 // n = nearest integer to k/pi, read from the low word of k/pi + 1.5 * 2^52 (one rounding);
-// r = k - n pi with a three-part pi; odd = n & 1.
+// r = k - n pi with the first two parts of a three-part pi (the third, times n, lies below the
+// rounding for the momenta the lattice produces); odd = n & 1.
 __device__ __forceinline__ double cw_reduce(double k, int& odd) {
   const double inv_pi = 0x1.45f306dc9c883p-2;
-  const double P1 = 0x1.921fb54442d18p+1, P2 = 0x1.1a62633145c07p-53, P3 = -0x1.f1976b7ed8fbcp-109;
+  const double P1 = 0x1.921fb54442d18p+1, P2 = 0x1.1a62633145c07p-53;
   const double nd = fma(k, inv_pi, 0x1.8p52);
   odd = __double2loint(nd) & 1;
   const double n = nd - 0x1.8p52;
-  double r = fma(-n, P1, k);
-  r = fma(-n, P2, r);
-  r = fma(-n, P3, r);
-  return r;
+  const double r = fma(-n, P1, k);      // exact: k - n P1 is a multiple of 2^-52 below 2 in magnitude
+  return fma(-n, P2, r);                // n P3 < 3e-32 for |k| < 22 is below the rounding
 }
 
 __device__ __forceinline__ double flip_if(double v, int odd) {   // (-1)^odd v, on the sign bit
@@ -114,7 +113,9 @@ __device__ __forceinline__ double line_energy(double kx, double ky, double t, do
 // t * 32/ln2 + 1.5 * 2^52 (round to nearest), and r is formed with a two-part ln2/32 whose high
 // part has few enough bits that the first reduction step is exact.  Then
 //   e^t     = T_hi' + (T_hi' p + T_lo'),        e^t - 1 = (T_hi' - 1) + (T_hi' p + T_lo'),
-// T' = 2^m T; T_hi' - 1 is exact where it matters (T_hi' in [1/2, 1]).
+// T' = 2^m T; T_hi' - 1 is exact where it matters (T_hi' in [1/2, 1]).  Without e^t - 1 the sum is
+// formed unscaled, T_hi + (T_hi p + T_lo) in [1/2, 2), and scaled by 2^m with an exponent add
+// (exact, so the same bits as scaling first).
 __device__ const double kExp2TabHi[32] = {
   0x1.0000000000000p+0, 0x1.059b0d3158574p+0, 0x1.0b5586cf9890fp+0, 0x1.11301d0125b51p+0,
   0x1.172b83c7d517bp+0, 0x1.1d4873168b9aap+0, 0x1.2387a6e756238p+0, 0x1.29e9df51fdee1p+0,
@@ -162,11 +163,15 @@ __device__ __forceinline__ double exp_neg(double t, double& em) {
   double y;
   if (m >= -960) {                                 // 2^m T_hi and 2^m T_lo stay normal numbers
     const long long sh = (long long)m << 52;
-    th = __longlong_as_double(__double_as_longlong(th) + sh);
-    tl = tl == 0.0 ? 0.0 : __longlong_as_double(__double_as_longlong(tl) + sh);
-    const double c = fma(th, p, tl);
-    y = th + c;
-    if (NEED_EM) em = (th - 1.0) + c;
+    if (NEED_EM) {
+      th = __longlong_as_double(__double_as_longlong(th) + sh);
+      tl = tl == 0.0 ? 0.0 : __longlong_as_double(__double_as_longlong(tl) + sh);
+      const double c = fma(th, p, tl);
+      y = th + c;
+      em = (th - 1.0) + c;
+    } else {
+      y = __longlong_as_double(__double_as_longlong(th + fma(th, p, tl)) + sh);
+    }
   } else {
     y = exp_neg_deep_tail(th, p, m);               // e^t < 1e-289: a real branch, rarely taken
     if (NEED_EM) em = y - 1.0;
