@@ -49,8 +49,8 @@ METRIC = "order-4 Sigma evals/s (samples x terms x frequencies, FP64), forward +
 # capture of this workload at 2^22 samples, per sample; every sample does the same work, so a
 # launch's traffic is this times its samples.  It holds only for the kernel sources it was taken
 # on: the hash of the library sources must match, else the bench reports traffic as null.
-TRAFFIC = {"kernel": "bwd_kernel", "bytes_per_sample": (6.046020e9 + 9.684244e9) / 4194304,
-           "sources_sha256": "77188c6f04a02fd61460ff3379d0cc3692efedd8cbd751443fa2486ea5720a28", "profile": "profiles/bwd_kernel_order4_sigma.md"}
+TRAFFIC = {"kernel": "bwd_kernel", "bytes_per_sample": (4.993870e9 + 10.721307e9) / 4194304,
+           "sources_sha256": "03c7face94720a8e707eb3ca44d82a99d9f9e8f9ddf490e905fe453e2b584e4b", "profile": "profiles/bwd_kernel_order4_sigma.md"}
 
 
 def sources_sha256():
