@@ -236,6 +236,15 @@ int tami_batch_launch(tami_batch* b, const tami_lattice* lat, const double* X, d
 
 void tami_batch_destroy(tami_batch* b);
 
+/* Diagnostic for testing the persistent launch's failure detection (no counterpart in the paper):
+ * overwrite entry `item` (0 <= item < the plan's item count) of the plan's device work queue with
+ * (diagram d, tiles [tile0, tile1)) and return the previous entry as {d, tile0, tile1} in prev
+ * (may be NULL).  The kernel checks every entry it pops against the plan (0 <= d < n_d,
+ * 0 <= tile0 < tile1 <= the diagram's tiles); a malformed one is skipped without any access it
+ * describes, the plan's status word is set, and that launch's means and variances are NaN.  The
+ * next launch resets the status.  Synchronous; the plan must be idle. */
+int tami_batch_debug_set_item(tami_batch* b, int item, int d, int64_t tile0, int64_t tile1, int64_t* prev);
+
 /* Hubbard (U n_up n_down) self-energy diagrams of the given order (2..6), one-particle
  * irreducible, without tadpoles, in canonical order, labelled with momentum-conserving alpha
  * (Sec. 2.5: graph representation and labelling).  With capacity 0 only *n_out is set.

@@ -19,7 +19,7 @@ EXPORTS = [
     "tami_last_error", "tami_construct", "tami_label_graph", "tami_construct_from_graph", "tami_diagram_info", "tami_upload", "tami_sample_energies",
     "tami_eval_energies", "tami_forward_workspace", "tami_forward", "tami_forward_noalloc",
     "tami_backward_workspace", "tami_backward", "tami_batch_plan", "tami_batch_info", "tami_batch_launch",
-    "tami_batch_destroy",
+    "tami_batch_destroy", "tami_batch_debug_set_item",
     "tami_enumerate_sigma",
     "tami_selftest_exp", "tami_destroy",
 ]
@@ -83,6 +83,8 @@ def lib():
                                   ctypes.POINTER(ctypes.c_int)]
     L.tami_batch_launch.argtypes = [vp, ctypes.POINTER(Lattice), dp, ctypes.c_double, dp, dp, vp]
     L.tami_batch_destroy.argtypes = [vp]
+    L.tami_batch_debug_set_item.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, i64, ctypes.POINTER(ctypes.c_int64)]
+    L.tami_batch_debug_set_item.restype = ctypes.c_int
     L.tami_batch_destroy.restype = None
     L.tami_enumerate_sigma.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     L.tami_selftest_exp.argtypes = [dp, i64, dp, dp, dp, vp]

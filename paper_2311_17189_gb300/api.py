@@ -183,6 +183,13 @@ class Batch:
         L.check(L.lib().tami_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return {"items": a.value, "grid": b.value, "chunk_tiles": c.value}
 
+    def debug_set_item(self, item, d, tile0, tile1):
+        """Overwrite one entry of the device work queue (tami_batch_debug_set_item); returns the
+        previous entry (d, tile0, tile1)."""
+        prev = (ctypes.c_int64 * 3)()
+        L.check(L.lib().tami_batch_debug_set_item(self._h, int(item), int(d), int(tile0), int(tile1), prev))
+        return tuple(int(v) for v in prev)
+
     def launch(self, lattice, X, beta, out=None):
         """Returns (mean complex [n_d, n_f], var float64 [n_d, n_f, 2])."""
         torch = _torch()

@@ -16,7 +16,7 @@ OUT = os.path.join(PKG, "libtami.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["tami_host.cpp", "tami_graph.cpp", "tami_cuda.cu", "tami_bwd.cu", "tami_batch.cu"]
+SOURCES = ["tami_host.cpp", "tami_graph.cpp", "tami_validate.cpp", "tami_cuda.cu", "tami_bwd.cu", "tami_batch.cu"]
 HEADERS = ["tami_internal.h", "tami_device.cuh", "tami_fwd_tile.cuh"]
 
 

@@ -472,6 +472,21 @@ int tami_batch_info(const tami_batch* b, int* n_items, int* grid, int* chunk_til
   return TAMI_OK;
 }
 
+int tami_batch_debug_set_item(tami_batch* b, int item, int d, int64_t tile0, int64_t tile1, int64_t* prev) {
+  if (!b || !b->mem || item < 0 || item >= b->n_items) { set_error("bad argument"); return TAMI_EINVAL; }
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != b->device) { set_error("current device differs from the plan's device"); return TAMI_EINVAL; }
+  BatchItem* p = reinterpret_cast<BatchItem*>(b->mem + b->L.items) + item;
+  BatchItem old{};
+  cudaError_t e = cudaMemcpy(&old, p, sizeof(old), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy item");
+  if (prev) { prev[0] = old.d; prev[1] = old.tile0; prev[2] = old.tile1; }
+  const BatchItem now{d, 0, tile0, tile1};
+  e = cudaMemcpy(p, &now, sizeof(now), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "cudaMemcpy item");
+}
+
 int tami_batch_launch(tami_batch* b, const tami_lattice* lat, const double* X, double beta, double* mean, double* var,
                       tami_stream_t stream) {
   if (!b || !lat || !X || !mean) { set_error("bad argument"); return TAMI_EINVAL; }

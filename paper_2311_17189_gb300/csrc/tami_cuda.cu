@@ -233,6 +233,13 @@ extern "C" {
 
 int tami_upload(tami_diagram* d, int device, tami_stream_t stream) {
   if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
+  {
+    std::string why;   // never put a table the kernels could read out of range on the device
+    if (!validate_table(d->hdr, d->blob.data(), d->blob.size(), &why)) {
+      set_error("term table failed validation: " + why);
+      return TAMI_EINVAL;
+    }
+  }
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   if (d->d_blob) {

@@ -671,6 +671,13 @@ int flatten(tami_diagram* d) {
   }
   for (int g = 0; g < h.n_g2; ++g) B.at<int>(h.off_g2node)[g] = g2node[g];
   d->blob.swap(B.b);
+  {
+    std::string why;
+    if (!validate_table(h, d->blob.data(), d->blob.size(), &why)) {
+      set_error("flattened table failed validation: " + why);
+      return TAMI_EUNSUPPORTED;
+    }
+  }
 
   // ---- info and the flop model of the kernels' explicit arithmetic
   tami_info& I = d->info;

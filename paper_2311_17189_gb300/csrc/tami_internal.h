@@ -129,4 +129,6 @@ struct tami_diagram {
 
 namespace tami {
 int flatten(tami_diagram* d);  // terms -> hdr + blob + info
+// Checks every index and range of a flattened table (tami_validate.cpp); false with the reason.
+bool validate_table(const TableHeader& h, const unsigned char* blob, size_t size, std::string* why);
 }

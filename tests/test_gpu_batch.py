@@ -104,6 +104,31 @@ def test_batch_rejects_bad_arguments():
         T.Batch(lib, [0] + counts[1:], seeds, 4)
 
 
+def test_poisoned_queue_entry_is_refused_without_a_fault():
+    """Failure detection of the persistent launch, injected on the host: a queue entry naming a
+    diagram or tiles outside the plan is skipped by the kernel (none of the accesses it describes
+    is made), the status word marks the launch and every mean and variance comes back NaN; with
+    the entry restored, the same plan gives the original results bit for bit."""
+    lib, orc, counts, seeds = mixed_batch()
+    X = W.matsubara(BETA, 4)
+    for D in lib:
+        D.upload(0)
+    B = T.Batch(lib, counts, seeds, len(X), chunk_tiles=2)
+    m0, v0 = B.launch(LAT, X, BETA)
+    torch.cuda.synchronize()
+    item = B.info()["items"] // 2
+    tiles0 = (counts[0] + 127) // 128
+    for bad in [(len(lib), 0, 1), (-1, 0, 1), (0, 0, tiles0 + 1), (0, 0, 1 << 40), (0, 1, 1), (0, -3, 1)]:
+        prev = B.debug_set_item(item, *bad)
+        m, v = B.launch(LAT, X, BETA)
+        torch.cuda.synchronize()
+        assert torch.all(torch.isnan(m.real)) and torch.all(torch.isnan(v)), bad
+        assert B.debug_set_item(item, *prev) == bad
+    m1, v1 = B.launch(LAT, X, BETA)
+    torch.cuda.synchronize()
+    assert torch.equal(m1, m0) and torch.equal(v1, v0)
+
+
 def test_all_orders_workload_full_size():
     """Every Hubbard self-energy diagram of orders 2..5 (85 diagrams), diagram d with
     2^(20 + d mod 4) samples and seed 20231128 + d, 32 Matsubara frequencies, beta = 5, in one
