@@ -49,21 +49,24 @@ METRIC = "order-4 Sigma evals/s (samples x terms x frequencies, FP64), forward +
 # capture of this workload at 2^22 samples, per sample; every sample does the same work, so a
 # launch's traffic is this times its samples.  It holds only for the kernel sources it was taken
 # on: the hash of the library sources must match, else the bench reports traffic as null.
-TRAFFIC = {"kernel": "bwd_kernel", "bytes_per_sample": (4.993870e9 + 10.721307e9) / 4194304,
-           "sources_sha256": "03c7face94720a8e707eb3ca44d82a99d9f9e8f9ddf490e905fe453e2b584e4b", "profile": "profiles/bwd_kernel_order4_sigma.md"}
+TRAFFIC = {"kernel": "bwd_kernel", "bytes_per_sample": (4.994559e9 + 10.720098e9) / 4194304,
+           "sources_sha256": "3fad70366ebd38a8706061f6920e1598f893a7585fccdbe19a892585aca1908e", "profile": "profiles/bwd_kernel_order4_sigma.md"}
+
+
+TRAFFIC_SOURCES = ("paper_2311_17189_gb300/csrc/tami_bwd.cu", "paper_2311_17189_gb300/csrc/tami_device.cuh",
+                   "paper_2311_17189_gb300/csrc/tami_internal.h", "paper_2311_17189_gb300/csrc/tami_host.cpp",
+                   "include/tami.h")
 
 
 def sources_sha256():
-    """sha256 over the library's kernel and table sources (csrc/ and include/), in name order."""
+    """sha256 over the sources that fix the dominant kernel's code and its term table (the
+    adjoint kernel, the device helpers, the table layout and the flattener), in this order."""
     import hashlib
     h = hashlib.sha256()
-    for sub in ("paper_2311_17189_gb300/csrc", "include"):
-        d = os.path.join(ROOT, sub)
-        for name in sorted(os.listdir(d)):
-            if name.endswith((".cu", ".cuh", ".cpp", ".h")):
-                h.update(name.encode())
-                with open(os.path.join(d, name), "rb") as f:
-                    h.update(f.read())
+    for rel in TRAFFIC_SOURCES:
+        h.update(rel.encode())
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()
 
 
