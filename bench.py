@@ -49,8 +49,8 @@ METRIC = "order-4 Sigma evals/s (samples x terms x frequencies, FP64), forward +
 # capture of this workload at 2^22 samples, per sample; every sample does the same work, so a
 # launch's traffic is this times its samples.  It holds only for the kernel sources it was taken
 # on: the hash of the library sources must match, else the bench reports traffic as null.
-TRAFFIC = {"kernel": "bwd_kernel", "bytes_per_sample": (4.994559e9 + 10.720098e9) / 4194304,
-           "sources_sha256": "3fad70366ebd38a8706061f6920e1598f893a7585fccdbe19a892585aca1908e", "profile": "profiles/bwd_kernel_order4_sigma.md"}
+TRAFFIC = {"kernel": "bwd_kernel", "bytes_per_sample": (5.373937e9 + 10.441250e9) / 4194304,
+           "sources_sha256": "8939a88e9161f6343026bcea38987e16e23ef59bde9aa6a3de5db8fbab0e900f", "profile": "profiles/bwd_kernel_order4_sigma.md"}
 
 
 TRAFFIC_SOURCES = ("paper_2311_17189_gb300/csrc/tami_bwd.cu", "paper_2311_17189_gb300/csrc/tami_device.cuh",
@@ -212,11 +212,16 @@ def run_tami(args):
     G = torch.view_as_real(torch.as_tensor(g_host, dtype=torch.complex128, device=dev)).contiguous()
     Gc = torch.view_as_complex(G)
 
-    def fwd(i):
-        return D.forward(lat, CFG["seed"], offset + i * n * world, n, Xc, CFG["beta"], out=(mean, var))
+    # the step keeps each sample's line energies and dE/dK factors from the forward for the
+    # adjoint (as torch autograd would); term products are still recomputed in the adjoint
+    saved = D.saved_buffer(n)
+
+    def fwd(i, save=True):
+        return D.forward(lat, CFG["seed"], offset + i * n * world, n, Xc, CFG["beta"], out=(mean, var),
+                         save=saved if save else None)
 
     def bwd(i):
-        return D.backward(lat, CFG["seed"], offset + i * n * world, n, Xc, CFG["beta"], Gc)
+        return D.backward(lat, CFG["seed"], offset + i * n * world, n, Xc, CFG["beta"], Gc, saved=saved)
 
     for i in range(args.warmup):
         fwd(i)
@@ -242,6 +247,15 @@ def run_tami(args):
     wall = time.perf_counter() - wall0
     fwd_ms = [a.elapsed_time(b) for a, b, _ in ev]
     bwd_ms = [b.elapsed_time(c) for _, b, c in ev]
+    # the plain forward (mean and variance only, nothing kept for an adjoint), timed on its own
+    evp = [(mk(), mk()) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        evp[i][0].record(stream)
+        fwd(args.warmup + i, save=False)
+        evp[i][1].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = [a.elapsed_time(b) for a, b in evp]
     # end-to-end through the public API: pinned host inputs in, host results out, every step
     Xh = torch.view_as_real(torch.as_tensor(X, dtype=torch.complex128)).contiguous().pin_memory()
     Gh = torch.view_as_real(torch.as_tensor(g_host, dtype=torch.complex128)).contiguous().pin_memory()
@@ -265,17 +279,18 @@ def run_tami(args):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     clk = clocks.stop()
-    tf, tb = float(np.mean(fwd_ms)), float(np.mean(bwd_ms))
+    tf, tb, tp = float(np.mean(fwd_ms)), float(np.mean(bwd_ms)), float(np.mean(plain_ms))
     ms = tf + tb
     e2e = float(np.mean(e2e_ms))
     if world > 1:
-        t = torch.tensor([ms, e2e, tf], dtype=torch.float64, device=dev)
+        t = torch.tensor([ms, e2e, tf, tb, tp], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e, tf = float(t[0]), float(t[1]), float(t[2])
+        ms, e2e, tf, tb, tp = (float(v) for v in t)
     evals = float(n) * info["n_terms"] * n_f * world
     value = evals / (ms * 1e-3)
-    fl_f = n * (info["flops_per_sample"] + n_f * info["flops_per_sample_freq"])
-    fl_b = n * (info["bwd_flops_per_sample"] + n_f * info["bwd_flops_per_sample_freq"])
+    fl_f = n * (info["fwd_save_flops_per_sample"] + n_f * info["flops_per_sample_freq"])
+    fl_b = n * (info["bwd_saved_flops_per_sample"] + n_f * info["bwd_flops_per_sample_freq"])
+    fl_p = n * (info["flops_per_sample"] + n_f * info["flops_per_sample_freq"])
     dom = ("bwd_kernel", fl_b, tb) if tb >= tf else ("fwd_kernel", fl_f, tf)
     achieved = dom[1] / (dom[2] * 1e-3) / 1e12
     traffic = None
@@ -286,9 +301,10 @@ def run_tami(args):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
-            "step": "forward + adjoint (tami_forward then tami_backward on the same samples)",
-            "plain_fwd": {"value": evals / (tf * 1e-3), "unit": "evals/s", "ms": tf},
-            "adjoint_ms": tb,
+            "step": "forward + adjoint (tami_forward keeping per-sample energies, then tami_backward on the same samples)",
+            "plain_fwd": {"value": evals / (tp * 1e-3), "unit": "evals/s", "ms": tp,
+                          "tflops": fl_p / (tp * 1e-3) / 1e12},
+            "step_fwd_ms": tf, "adjoint_ms": tb,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (Philox momenta, in-kernel)",
             "config": {"workload": CFG["name"], "samples_per_gpu": n, "frequencies": n_f,

@@ -74,13 +74,19 @@ typedef struct {
   int n_groups_fixed;       /* groups of terms with one denominator signature                 */
   int n_groups_freq;        /* groups sharing one frequency-dependent signature               */
   int table_bytes;
-  /* FP64 flops of the kernels' explicit arithmetic (fma = 2): per sample (frequency
-   * independent part, library math calls counted as one flop each) and per (sample, frequency) */
+  /* FP64 flops of the kernels' arithmetic (fma = 2, mul/add = 1; exponential, reciprocal and
+   * trig by their own operation counts): per sample (frequency independent part) and per
+   * (sample, frequency) */
   double flops_per_sample;
   double flops_per_sample_freq;
   /* the same for tami_backward (recomputation + adjoint sweep) */
   double bwd_flops_per_sample;
   double bwd_flops_per_sample_freq;
+  /* rows of tami_forward's `saved` output: computed lines + 2 per line carrying k_ext */
+  int saved_rows;
+  /* per-sample flops of tami_forward when it writes `saved`, and of tami_backward reading it */
+  double fwd_save_flops_per_sample;
+  double bwd_saved_flops_per_sample;
 } tami_info;
 
 const char* tami_last_error(void);
@@ -159,11 +165,17 @@ int tami_forward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, si
  *   mean        device double [n_f][2]  sample mean of the integrand
  *   var         device double [n_f][2]  unbiased sample variances of Re and Im (may be NULL)
  *   per_sample  device double [n_f][n][2] every sample's value, or NULL
+ *   saved       device double [saved_rows][n] (tami_info.saved_rows), or NULL: each sample's line
+ *               energies (one row per computed line) and, for the lines carrying k_ext, the
+ *               factors G_x, G_y of dE/dK = -G; tami_backward reads them instead of recomputing
+ *               momenta, energies and trig (term products are still recomputed).  Row-major,
+ *               sample index fastest.
  *   workspace   device, at least tami_forward_workspace() bytes, 256-byte aligned.
  * The reduction is deterministic for fixed (n, n_f, device). */
 int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
                  int64_t n_samples, const double* X, int n_f, double beta, double* mean, double* var,
-                 double* per_sample, void* workspace, size_t workspace_bytes, tami_stream_t stream);
+                 double* per_sample, double* saved, void* workspace, size_t workspace_bytes,
+                 tami_stream_t stream);
 
 /* Scratch needed by tami_backward for n samples and n_f frequencies. */
 int tami_backward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, size_t* bytes);
@@ -180,13 +192,18 @@ int tami_backward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, s
  *   per_sample_dX    device double [n_f][n][2] or NULL: each sample's dv/dX.
  *   per_sample_grads device double [n][3] or NULL: each sample's
  *               Re sum_f conj(g_f) dv/dtheta (theta = mu, kx, ky; not divided by n).
+ *   saved       device double [saved_rows][n] written by tami_forward over the same diagram,
+ *               lattice, seed, offset and n, or NULL: the line energies and dE/dK factors are
+ *               then read instead of recomputed from the momenta (results identical bit for bit;
+ *               the caller owns the buffer and its consistency with the forward).
  *   gout        device double [n_f][2]; workspace as tami_backward_workspace, 256-byte aligned.
  * Term products are recomputed, not stored.  Limits: n_f <= 256, derivative order <= 4.
  * Deterministic for fixed (n, n_f, device). */
 int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
                   int64_t n_samples, const double* X, int n_f, double beta, const double* gout,
                   double* dsigma_dX, double* grad_X_re, double* grad_params, double* per_sample_dX,
-                  double* per_sample_grads, void* workspace, size_t workspace_bytes, tami_stream_t stream);
+                  double* per_sample_grads, const double* saved, void* workspace, size_t workspace_bytes,
+                  tami_stream_t stream);
 
 /* tami_forward without a workspace argument: the same Monte Carlo evaluation and outputs, with
  * its scratch (a status word and the per-block partial sums) taken from a fixed 4 MiB array

@@ -47,6 +47,8 @@ class Info(ctypes.Structure):
         ("table_bytes", ctypes.c_int),
         ("flops_per_sample", ctypes.c_double), ("flops_per_sample_freq", ctypes.c_double),
         ("bwd_flops_per_sample", ctypes.c_double), ("bwd_flops_per_sample_freq", ctypes.c_double),
+        ("saved_rows", ctypes.c_int),
+        ("fwd_save_flops_per_sample", ctypes.c_double), ("bwd_saved_flops_per_sample", ctypes.c_double),
     ]
 
 
@@ -72,12 +74,12 @@ def lib():
     L.tami_eval_energies.argtypes = [vp, dp, i64, dp, ctypes.c_int, ctypes.c_double, dp, vp]
     L.tami_forward_workspace.argtypes = [vp, i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.tami_forward.argtypes = [vp, ctypes.POINTER(Lattice), u64, u64, i64, dp, ctypes.c_int, ctypes.c_double,
-                               dp, dp, dp, dp, ctypes.c_size_t, vp]
+                               dp, dp, dp, dp, dp, ctypes.c_size_t, vp]
     L.tami_forward_noalloc.argtypes = [vp, ctypes.POINTER(Lattice), u64, u64, i64, dp, ctypes.c_int,
                                        ctypes.c_double, dp, dp, dp, vp]
     L.tami_backward_workspace.argtypes = [vp, i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.tami_backward.argtypes = [vp, ctypes.POINTER(Lattice), u64, u64, i64, dp, ctypes.c_int, ctypes.c_double,
-                                dp, dp, dp, dp, dp, dp, dp, ctypes.c_size_t, vp]
+                                dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_size_t, vp]
     L.tami_batch_plan.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
     L.tami_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int)]

@@ -105,9 +105,16 @@ class Diagram:
             self._ws = torch.empty(need, dtype=torch.uint8, device=self._dev())
         return self._ws
 
-    def forward(self, lattice, seed, offset, n, X, beta, per_sample=False, out=None):
+    def saved_buffer(self, n):
+        """A buffer for forward(save=...) / backward(saved=...): float64 [saved_rows, n]."""
+        torch = _torch()
+        return torch.empty((self.info()["saved_rows"], int(n)), dtype=torch.float64, device=self._dev())
+
+    def forward(self, lattice, seed, offset, n, X, beta, per_sample=False, out=None, save=None):
         """Monte Carlo mean over n momentum samples (Sec. 5.2).  Returns (mean complex [n_f],
-        var float64 [n_f, 2], per-sample complex [n_f, n] or None)."""
+        var float64 [n_f, 2], per-sample complex [n_f, n] or None).  With save (a tensor from
+        saved_buffer(n)) the per-sample line energies and dE/dK factors are written there for a
+        backward() over the same samples."""
         torch = _torch()
         dev = self._dev()
         Xp = _as_c_pairs(X, dev)
@@ -118,20 +125,25 @@ class Diagram:
         else:
             mean, var = out
         ps = torch.empty((n_f, n, 2), dtype=torch.float64, device=dev) if per_sample else None
+        if save is not None and (save.dtype != torch.float64 or not save.is_contiguous() or
+                                 tuple(save.shape) != (self.info()["saved_rows"], int(n))):
+            raise L.TamiError(L.TAMI_EINVAL, "save must be a contiguous float64 [saved_rows, n] tensor")
         ws = self.workspace(n, n_f)
         lat = L.Lattice(*[float(v) for v in lattice])
         L.check(L.lib().tami_forward(self._h, ctypes.byref(lat), int(seed), int(offset), int(n),
                                      ctypes.c_void_p(Xp.data_ptr()), n_f, float(beta),
                                      ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(var.data_ptr()),
                                      ctypes.c_void_p(ps.data_ptr()) if ps is not None else None,
+                                     ctypes.c_void_p(save.data_ptr()) if save is not None else None,
                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr()))
         return (torch.view_as_complex(mean), var, torch.view_as_complex(ps) if ps is not None else None)
 
-    def backward(self, lattice, seed, offset, n, X, beta, gout, per_sample=False):
+    def backward(self, lattice, seed, offset, n, X, beta, gout, per_sample=False, saved=None):
         """Adjoint of forward()'s mean for the upstream gradient gout (complex [n_f]).
         Returns dict: dSigma_dX (complex [n_f]), grad_X_re (float64 [n_f]), grad_params
         (float64 [3]: mu, kx_ext, ky_ext) and, with per_sample, dX (complex [n_f, n]) and
-        grads (float64 [n, 3])."""
+        grads (float64 [n, 3]).  saved: the buffer a forward(save=...) over the same samples
+        filled (then the energies are read, not recomputed; same results)."""
         torch = _torch()
         dev = self._dev()
         Xp = _as_c_pairs(X, dev)
@@ -142,6 +154,9 @@ class Diagram:
         gp = torch.empty((3,), dtype=torch.float64, device=dev)
         ps_dX = torch.empty((n_f, n, 2), dtype=torch.float64, device=dev) if per_sample else None
         ps_g = torch.empty((n, 3), dtype=torch.float64, device=dev) if per_sample else None
+        if saved is not None and (saved.dtype != torch.float64 or not saved.is_contiguous() or
+                                  tuple(saved.shape) != (self.info()["saved_rows"], int(n))):
+            raise L.TamiError(L.TAMI_EINVAL, "saved must be a contiguous float64 [saved_rows, n] tensor")
         nbytes = ctypes.c_size_t()
         L.check(L.lib().tami_backward_workspace(self._h, int(n), n_f, ctypes.byref(nbytes)))
         need = (nbytes.value + 255) // 256 * 256
@@ -152,7 +167,7 @@ class Diagram:
         lat = L.Lattice(*[float(v) for v in lattice])
         L.check(L.lib().tami_backward(self._h, ctypes.byref(lat), int(seed), int(offset), int(n), ptr(Xp), n_f,
                                       float(beta), ptr(Gp), ptr(dX), ptr(gX), ptr(gp), ptr(ps_dX), ptr(ps_g),
-                                      ptr(ws), ws.numel(), _stream_ptr()))
+                                      ptr(saved), ptr(ws), ws.numel(), _stream_ptr()))
         out = {"dSigma_dX": torch.view_as_complex(dX), "grad_X_re": gX, "grad_params": gp}
         if per_sample:
             out["dX"] = torch.view_as_complex(ps_dX)

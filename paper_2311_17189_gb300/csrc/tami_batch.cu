@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchParams P) {
   A.offset = 0;
   A.E_in = nullptr;
   A.per_sample = nullptr;
+  A.saved = nullptr;
   A.n_f = n_f;
   int cur_d = -1;
   uint32_t phase = 0;
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchParams P) {
     A.seed = P.diags[d].seed;
     A.n = P.diags[d].n;
     for (int i = 0; i < kMaxFreqPerThread; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0;
-    for (long long tile = item.tile0; tile < item.tile1; ++tile) fwd_tile<false>(Hs, T, A, tile, Xs, AXI, AXI2, xr_zero, CB, W, M, acc);
+    for (long long tile = item.tile0; tile < item.tile1; ++tile) fwd_tile<false, false>(Hs, T, A, tile, Xs, AXI, AXI2, xr_zero, CB, W, M, acc);
     block_reduce_store(M, n_f, acc, red, P.partial + (size_t)it * n_f * 4);
   }
 }

@@ -41,6 +41,7 @@ struct BwdParams {
   double beta;
   double* ps_dX;         // [n_f][n][2] or null
   double* ps_grad;       // [n][3] or null
+  const double* saved;   // [n_rep + 2 n_rep_ext][n] from tami_forward, or null (recompute)
   double* partial;       // [grid][2 n_f + 3]
   int* status;
 };
@@ -114,6 +115,7 @@ __device__ __forceinline__ void bwd_phase2(const TableHeader& H, int n_f, long l
 #define TAMI_BWD_MIN_BLOCKS 8
 #endif
 
+template <bool SAVED>
 __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const BwdParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const TableHeader& H = P.h;
@@ -174,40 +176,46 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
     const long long s = tile * kBlock + tid;
     if (s >= P.n) continue;
     // ------------------------------------------------------------ forward recomputation
-    double kx[kMaxVars], ky[kMaxVars];
-    const unsigned long long sg = P.offset + (unsigned long long)s;
-    for (int l = 0; l < H.m; ++l) {
-      uint32_t c[4] = {(uint32_t)sg, (uint32_t)(sg >> 32), (uint32_t)l, 0u};
-      philox4x32_10(c, (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-      kx[l] = to_momentum(c[0], c[1]);
-      ky[l] = to_momentum(c[2], c[3]);
-    }
-    kx[H.m] = P.kx;
-    ky[H.m] = P.ky;
-    double E[kMaxLines], Sx[kMaxLines], Cx[kMaxLines], Sy[kMaxLines], Cy[kMaxLines];
-    auto line_momentum = [&](int r, double& ax, double& ay) {
-      ax = 0.0;
-      ay = 0.0;
-      for (int q = lm_ptr[r]; q < lm_ptr[r + 1]; ++q) {
-        const double cf = lm_c[q];
-        const int l = lm_l[q];
-        ax = fma(cf, kx[l], ax);
-        ay = fma(cf, ky[l], ay);
+    // line energies, and for the lines carrying k_ext the factors G of dE/dK = -G: read from the
+    // forward's saved rows, or recomputed from the momenta exactly as the forward forms them
+    double E[kMaxLines], Gx[kMaxLines], Gy[kMaxLines];
+    if (SAVED) {
+      for (int r = 0; r < H.n_rep; ++r) E[repl[r]] = P.saved[(size_t)r * P.n + s];
+      for (int r = 0; r < H.n_rep_ext; ++r) {
+        Gx[r] = P.saved[(size_t)(H.n_rep + 2 * r) * P.n + s];
+        Gy[r] = P.saved[(size_t)(H.n_rep + 2 * r + 1) * P.n + s];
       }
-    };
-    for (int r = 0; r < H.n_rep_ext; ++r) {     // lines carrying k_ext: sin too, for dE/dk_ext
-      const int j = repl[r];
-      double ax, ay, sx, cx, sy, cy;
-      line_momentum(r, ax, ay);
-      cw_sincos(ax, sx, cx);
-      cw_sincos(ay, sy, cy);
-      E[j] = fma(4.0 * P.tp, __dmul_rn(cx, cy), fma(2.0 * P.t, __dadd_rn(cx, cy), P.mu));
-      Sx[j] = sx; Cx[j] = cx; Sy[j] = sy; Cy[j] = cy;
-    }
-    for (int r = H.n_rep_ext; r < H.n_rep; ++r) {
-      double ax, ay;
-      line_momentum(r, ax, ay);
-      E[repl[r]] = line_energy(ax, ay, P.t, P.tp, P.mu);
+    } else {
+      double kx[kMaxVars], ky[kMaxVars];
+      const unsigned long long sg = P.offset + (unsigned long long)s;
+      for (int l = 0; l < H.m; ++l) {
+        uint32_t c[4] = {(uint32_t)sg, (uint32_t)(sg >> 32), (uint32_t)l, 0u};
+        philox4x32_10(c, (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+        kx[l] = to_momentum(c[0], c[1]);
+        ky[l] = to_momentum(c[2], c[3]);
+      }
+      kx[H.m] = P.kx;
+      ky[H.m] = P.ky;
+      auto line_momentum = [&](int r, double& ax, double& ay) {
+        ax = 0.0;
+        ay = 0.0;
+        for (int q = lm_ptr[r]; q < lm_ptr[r + 1]; ++q) {
+          const double cf = lm_c[q];
+          const int l = lm_l[q];
+          ax = fma(cf, kx[l], ax);
+          ay = fma(cf, ky[l], ay);
+        }
+      };
+      for (int r = 0; r < H.n_rep_ext; ++r) {
+        double ax, ay;
+        line_momentum(r, ax, ay);
+        E[repl[r]] = line_energy_grad(ax, ay, P.t, P.tp, P.mu, Gx[r], Gy[r]);
+      }
+      for (int r = H.n_rep_ext; r < H.n_rep; ++r) {
+        double ax, ay;
+        line_momentum(r, ax, ay);
+        E[repl[r]] = line_energy(ax, ay, P.t, P.tp, P.mu);
+      }
     }
     double x[kBwCombos];
     for (int u = 0; u < H.n_combo; ++u) {
@@ -317,12 +325,11 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
     double mub = 0.0, kxb = 0.0, kyb = 0.0;
     for (int r = 0; r < H.n_rep; ++r) mub += Ebar[repl[r]];
     for (int r = 0; r < H.n_rep_ext; ++r) {
-      const int j = repl[r];
-      const double eb = Ebar[j];
+      const double eb = Ebar[repl[r]];
       const double ae = rep_aext[r];
-      // dE/dKx = -(2t + 4t' cos Ky) sin Kx,  dK/dk_ext = alpha_ext
-      kxb = fma(-eb * ae, fma(4.0 * P.tp, Cy[j], 2.0 * P.t) * Sx[j], kxb);
-      kyb = fma(-eb * ae, fma(4.0 * P.tp, Cx[j], 2.0 * P.t) * Sy[j], kyb);
+      // dE/dK = -G = -(2t + 4t' cos K_perp) sin K,  dK/dk_ext = alpha_ext
+      kxb = fma(-eb * ae, Gx[r], kxb);
+      kyb = fma(-eb * ae, Gy[r], kyb);
     }
     gmu += mub;
     gkx += kxb;
@@ -382,9 +389,15 @@ int bwd_grid(const tami_diagram* d, int n_f, long long n, size_t* smem_out) {
   const size_t smem = bwd_smem_bytes(d->hdr, n_f);
   if (smem_out) *smem_out = smem;
   if (smem > dp.smem_optin) return -1;
-  cudaFuncSetAttribute(bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel, kBlock, smem) != cudaSuccess) per_sm = 1;
+  // one grid for both instances (saved rows or recomputation), so that their reductions group the
+  // samples alike and the results agree bit for bit
+  cudaFuncSetAttribute(bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0, per_sm_saved = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel<false>, kBlock, smem) != cudaSuccess) per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_saved, bwd_kernel<true>, kBlock, smem) != cudaSuccess)
+    per_sm_saved = 1;
+  if (per_sm_saved < per_sm) per_sm = per_sm_saved;
   if (per_sm < 1) per_sm = 1;
   long long tiles = (n + kBlock - 1) / kBlock;
   long long grid = (long long)dp.sms * per_sm;
@@ -432,7 +445,8 @@ int tami_backward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, s
 int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
                   int64_t n_samples, const double* X, int n_f, double beta, const double* gout,
                   double* dsigma_dX, double* grad_X_re, double* grad_params, double* per_sample_dX,
-                  double* per_sample_grads, void* workspace, size_t workspace_bytes, tami_stream_t stream) {
+                  double* per_sample_grads, const double* saved, void* workspace, size_t workspace_bytes,
+                  tami_stream_t stream) {
   int rc = bwd_check(d, n_f);
   if (rc) return rc;
   if (!lat || !X || !gout || !workspace || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
@@ -456,8 +470,10 @@ int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed,
   P.seed = seed; P.offset = offset; P.n = n_samples;
   P.X = X; P.G = gout; P.n_f = n_f; P.beta = beta;
   P.ps_dX = per_sample_dX; P.ps_grad = per_sample_grads;
+  P.saved = saved;
   P.partial = partial; P.status = status;
-  bwd_kernel<<<grid, kBlock, smem, st>>>(P);
+  if (saved) bwd_kernel<true><<<grid, kBlock, smem, st>>>(P);
+  else bwd_kernel<false><<<grid, kBlock, smem, st>>>(P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "bwd_kernel launch");
   bwd_finalize_kernel<<<n_f + 1, kFinBlock, 0, st>>>(partial, grid, n_f, n_samples, gout, status,

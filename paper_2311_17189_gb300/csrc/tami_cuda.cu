@@ -41,6 +41,7 @@ struct FwdParams {
   int n_f;
   double beta;
   double* per_sample;           // [n_f][n][2] or null
+  double* saved;                // [n_rep + 2 n_rep_ext][n] for the adjoint, or null (momentum mode)
   double* partial;              // [gridDim][n_f][4] or null
   int* status;                  // device status word or null
 };
@@ -52,7 +53,7 @@ __host__ __device__ __forceinline__ size_t fwd_smem_bytes(const TableHeader& h, 
          sizeof(double) * ((2 + 2 * (size_t)h.n_cden) * n_f + (size_t)(h.n_cden + h.n_g2 + 4) * kBlock);
 }
 
-template <bool ENERGY_IN>
+template <bool ENERGY_IN, bool SAVE>
 __global__ void __launch_bounds__(kBlock) fwd_kernel(const FwdParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const TableHeader& H = P.h;
@@ -74,10 +75,11 @@ __global__ void __launch_bounds__(kBlock) fwd_kernel(const FwdParams P) {
   TileArgs A;
   A.t = P.t; A.tp = P.tp; A.mu = P.mu; A.kx = P.kx; A.ky = P.ky; A.beta = P.beta;
   A.seed = P.seed; A.offset = P.offset; A.n = P.n; A.E_in = P.E_in; A.per_sample = P.per_sample;
+  A.saved = P.saved;
   A.n_f = P.n_f;
   const long long n_tiles = (P.n + kBlock - 1) / kBlock;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x)
-    fwd_tile<ENERGY_IN>(H, T, A, tile, Xs, AXI, AXI2, xr_zero, CB, W, M, acc);
+    fwd_tile<ENERGY_IN, SAVE>(H, T, A, tile, Xs, AXI, AXI2, xr_zero, CB, W, M, acc);
   if (!P.partial) return;
   block_reduce_store(M, P.n_f, acc, red, P.partial + (size_t)blockIdx.x * P.n_f * 4);
 }
@@ -141,15 +143,15 @@ __global__ void sample_energies_kernel(const FwdParams P, double* E) {
 }
 
 // ------------------------------------------------------------------------------- host glue
-template <bool E_IN>
+template <bool E_IN, bool SAVE>
 int launch_fwd(const tami_diagram* d, FwdParams& P, cudaStream_t stream, int max_blocks) {
   const size_t smem = fwd_smem_bytes(d->hdr, P.n_f);
   DeviceProps dp = device_props(d->device);
   if (smem > dp.smem_optin) { set_error("term table and tiles exceed shared memory"); return TAMI_EUNSUPPORTED; }
-  cudaError_t e = cudaFuncSetAttribute(fwd_kernel<E_IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(fwd_kernel<E_IN, SAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<E_IN>, kBlock, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<E_IN, SAVE>, kBlock, smem);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   if (per_sm < 1) per_sm = 1;
   long long tiles = (P.n + kBlock - 1) / kBlock;
@@ -157,7 +159,7 @@ int launch_fwd(const tami_diagram* d, FwdParams& P, cudaStream_t stream, int max
   if (grid > tiles) grid = tiles;
   if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
   if (grid < 1) grid = 1;
-  fwd_kernel<E_IN><<<(unsigned)grid, kBlock, smem, stream>>>(P);
+  fwd_kernel<E_IN, SAVE><<<(unsigned)grid, kBlock, smem, stream>>>(P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fwd_kernel launch");
   return TAMI_OK;
@@ -167,8 +169,9 @@ int grid_for(const tami_diagram* d, int n_f, long long n) {
   DeviceProps dp = device_props(d->device);
   const size_t smem = fwd_smem_bytes(d->hdr, n_f);
   int per_sm = 0;
-  cudaFuncSetAttribute(fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<false>, kBlock, smem) != cudaSuccess) per_sm = 1;
+  cudaFuncSetAttribute(fwd_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<false, false>, kBlock, smem) != cudaSuccess)
+    per_sm = 1;
   if (per_sm < 1) per_sm = 1;
   long long tiles = (n + kBlock - 1) / kBlock;
   long long grid = (long long)dp.sms * per_sm;
@@ -290,7 +293,7 @@ int tami_eval_energies(const tami_diagram* d, const double* E, int64_t n_e, cons
   P.E_in = E;
   P.X = X;
   P.per_sample = out;
-  return launch_fwd<true>(d, P, (cudaStream_t)stream, 0);
+  return launch_fwd<true, false>(d, P, (cudaStream_t)stream, 0);
 }
 
 int tami_forward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, size_t* bytes) {
@@ -304,7 +307,8 @@ int tami_forward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, si
 
 int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
                  int64_t n_samples, const double* X, int n_f, double beta, double* mean, double* var,
-                 double* per_sample, void* workspace, size_t workspace_bytes, tami_stream_t stream) {
+                 double* per_sample, double* saved, void* workspace, size_t workspace_bytes,
+                 tami_stream_t stream) {
   int rc = check_common(d, n_f);
   if (rc) return rc;
   if (!lat || !X || !mean || !workspace || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
@@ -323,9 +327,10 @@ int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, 
   P.seed = seed; P.offset = offset; P.n = n_samples;
   P.X = X;
   P.per_sample = per_sample;
+  P.saved = saved;
   P.partial = partial;
   P.status = status;
-  rc = launch_fwd<false>(d, P, st, grid);
+  rc = saved ? launch_fwd<false, true>(d, P, st, grid) : launch_fwd<false, false>(d, P, st, grid);
   if (rc) return rc;
   finalize_kernel<<<n_f, kFinBlock, 0, st>>>(partial, grid, n_f, n_samples, status, mean, var);
   e = cudaGetLastError();
@@ -365,7 +370,7 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
   P.per_sample = per_sample;
   P.partial = partial;
   P.status = status;
-  rc = launch_fwd<false>(d, P, st, grid);
+  rc = launch_fwd<false, false>(d, P, st, grid);
   if (rc) return rc;
   finalize_kernel<<<n_f, kFinBlock, 0, st>>>(partial, grid, n_f, n_samples, status, mean, var);
   e = cudaGetLastError();

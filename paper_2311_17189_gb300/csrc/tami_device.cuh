@@ -105,6 +105,18 @@ __device__ __forceinline__ double line_energy(double kx, double ky, double t, do
   return fma(4.0 * tp, prod, fma(2.0 * t, sum, mu));
 }
 
+// Energy of a line that carries k_ext, with the factors G = (2t + 4t' cos K_perp) sin K of
+// dE/dK = -G for both components (one sincos per component); E has line_energy's bits.
+__device__ __forceinline__ double line_energy_grad(double kx, double ky, double t, double tp, double mu, double& gx,
+                                                   double& gy) {
+  double sx, cx, sy, cy;
+  cw_sincos(kx, sx, cx);
+  cw_sincos(ky, sy, cy);
+  gx = fma(4.0 * tp, cy, 2.0 * t) * sx;
+  gy = fma(4.0 * tp, cx, 2.0 * t) * sy;
+  return fma(4.0 * tp, __dmul_rn(cx, cy), fma(2.0 * t, __dadd_rn(cx, cy), mu));
+}
+
 // e^t and e^t - 1 for t <= 0, after P. T. P. Tang, "Table-driven implementation of the exponential
 // function in IEEE floating-point arithmetic", ACM TOMS 15 (1989) 144-157:
 // t = k ln2/32 + r with k = 32 m + j (0 <= j < 32), |r| <= ln2/64, and

@@ -113,6 +113,7 @@ struct TileArgs {
   long long n;                      // samples in the stream
   const double* E_in;               // energy input [n][N] or null
   double* per_sample;               // [n_f][n][2] or null
+  double* saved;                    // [n_rep + 2 n_rep_ext][n] energies and dE/dK factors, or null
   int n_f;
 };
 
@@ -187,7 +188,7 @@ __device__ __forceinline__ void phase2_store(const TileArgs& A, int f, long long
 
 // Shared memory per tile: X [n_f][2] (filled by the caller), AXI and AXI2 [n_cden][n_f] (from
 // freq_constants), CB [n_cden][kBlock], W [n_g2][kBlock].
-template <bool ENERGY_IN>
+template <bool ENERGY_IN, bool SAVE>
 __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& T, const TileArgs& A,
                                          long long tile, const double* Xs, const double* AXI, const double* AXI2,
                                          bool xr_zero, double* CB, double* W, const FreqMap& M, double (*acc)[4]) {
@@ -212,16 +213,33 @@ __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& 
         }
         kx[H.m] = A.kx;
         ky[H.m] = A.ky;
-        for (int r = 0; r < H.n_rep; ++r) {
-          double ax = 0.0, ay = 0.0;
+        auto line_momentum = [&](int r, double& ax, double& ay) {
+          ax = 0.0;
+          ay = 0.0;
           for (int q = T.lm_ptr[r]; q < T.lm_ptr[r + 1]; ++q) {
             const double cf = T.lm_c[q];
             const int l = T.lm_l[q];
             ax = fma(cf, kx[l], ax);
             ay = fma(cf, ky[l], ay);
           }
+        };
+        int r = 0;
+        if (SAVE) {   // for the adjoint: the lines carrying k_ext also give their dE/dK factors
+          for (; r < H.n_rep_ext; ++r) {
+            double ax, ay, gx, gy;
+            line_momentum(r, ax, ay);
+            E[T.repl[r]] = line_energy_grad(ax, ay, A.t, A.tp, A.mu, gx, gy);
+            A.saved[(size_t)(H.n_rep + 2 * r) * A.n + s] = gx;
+            A.saved[(size_t)(H.n_rep + 2 * r + 1) * A.n + s] = gy;
+          }
+        }
+        for (; r < H.n_rep; ++r) {
+          double ax, ay;
+          line_momentum(r, ax, ay);
           E[T.repl[r]] = line_energy(ax, ay, A.t, A.tp, A.mu);
         }
+        if (SAVE)
+          for (int q = 0; q < H.n_rep; ++q) A.saved[(size_t)q * A.n + s] = E[T.repl[q]];
       }
       double x[kMaxCombos];
       for (int u = 0; u < H.n_combo; ++u) {

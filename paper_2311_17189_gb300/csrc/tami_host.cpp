@@ -691,6 +691,7 @@ int flatten(tami_diagram* d) {
   I.n_real_dens = h.n_rden; I.n_cplx_dens = h.n_cden;
   I.n_groups_fixed = h.n_g1; I.n_groups_freq = h.n_g2;
   I.table_bytes = h.bytes;
+  I.saved_rows = h.n_rep + 2 * h.n_rep_ext;
   const int m = nv - 1;
   // Counts follow the kernel: fma = 2 flops, mul/add = 1, the reciprocal (estimate + one
   // third-order Newton step) = 3 fma, the table-driven exponential 10 fma + 3 add/mul.
@@ -698,6 +699,8 @@ int flatten(tami_diagram* d) {
   fl += 3.0 * 2 * m;                                    // u -> k: mul + fma per component
   fl += 2.0 * 2.0 * n_lm;                               // line momenta, fma per nonzero label and dimension
   fl += h.n_rep * (2.0 * 30.0 + 6.0);                   // cos of both components (reduction 9, series 21), energy
+  const double energy_flops = fl;                       // what a saved-rows adjoint does not redo
+  const double ext_grad_flops = h.n_rep_ext * 2.0 * (21.0 + 3.0);   // sin and G = (2t + 4t' cos) sin per component
   fl += 2.0 * nnz;                                      // energy combinations
   for (const Seg& g : segs) {
     fl += 1.0 + 23.0 + (g.sigma < 0 ? 2.0 : 0.0);       // -beta|x|; e^t (10 fma, 3 add/mul); e^t - 1
@@ -735,6 +738,8 @@ int flatten(tami_diagram* d) {
   bl += ng2cd;                                          // p W per group factor
   bl += 3.0 * h.n_fv + 2.0 * nnz + h.n_rep + 10.0 * h.n_rep_ext;   // fvbar -> x -> E -> (mu, k_ext)
   I.bwd_flops_per_sample = bl;
+  I.fwd_save_flops_per_sample = I.flops_per_sample + ext_grad_flops;
+  I.bwd_saved_flops_per_sample = bl - energy_flops - ext_grad_flops;
   double bf = 12.0 * h.n_cden + 12.0 * h.n_cden + 2.0;  // reciprocals, Z, dv/dX and b-adjoints, accX
   bf += 6.0 * h.n_pnode;                                // products (trie nodes)
   for (auto& g : g2s) bf += g.empty() ? 1.0 : 4.0 + 4.0 * g.size();   // Wbar, U += p W R

@@ -205,3 +205,26 @@ def test_order5_large_full_size_sampled(beta):
             _, der, denv = S.eval_momenta_deriv(lat, c["seed"], int(i), 1, X, beta, which, envelope=True)
             ref = np.real(np.conj(g) * der[:, 0]).sum()
             assert abs(gs[k] - ref) <= RTOL * (np.abs(g) * denv[:, 0]).sum(), (i, which, gs[k], ref)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_saved_energies_give_the_same_bits(case):
+    """tami_forward with `saved` (line energies and dE/dK factors per sample) and tami_backward
+    reading them give exactly the results of the recomputing path: the forward's outputs, the
+    per-sample adjoints and the reduced gradients, bit for bit."""
+    D, S, lat, beta, X = setup_case(case)
+    n, seed, off = 3 * 128 + 37, 21, 5
+    g = upstream(len(X))
+    sv = D.saved_buffer(n)
+    m0, v0, p0 = D.forward(lat, seed, off, n, X, beta, per_sample=True)
+    m1, v1, p1 = D.forward(lat, seed, off, n, X, beta, per_sample=True, save=sv)
+    assert torch.equal(m0, m1) and torch.equal(v0, v1) and torch.equal(p0, p1)
+    # the leading rows are line energies: each equals one line's tami_sample_energies column bit for bit
+    Eb = D.sample_energies(lat, seed, off, n).cpu().numpy().T.copy().view(np.uint64)
+    n_energy_rows = len({col.tobytes() for col in Eb})
+    for row in sv.cpu().numpy()[:n_energy_rows].copy().view(np.uint64):
+        assert any(np.array_equal(row, col) for col in Eb)
+    b0 = D.backward(lat, seed, off, n, X, beta, g, per_sample=True)
+    b1 = D.backward(lat, seed, off, n, X, beta, g, per_sample=True, saved=sv)
+    for k in ("dSigma_dX", "grad_X_re", "grad_params", "dX", "grads"):
+        assert torch.equal(b0[k], b1[k]), k
