@@ -141,9 +141,15 @@ def cpu_baseline(diagram, X, target_s=10.0):
             break
         n *= 4
     info = S.info()
+    n1 = max(n // cores, 64)                        # one thread: a proportionally smaller sample
+    t0 = time.perf_counter()
+    oracle_step(S, 0, n1, X, 1)
+    dt1 = time.perf_counter() - t0
     return {"value": n * info["terms"] * len(X) / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
             "sample": f"first {n} of the {CFG['n_samples']} samples (same seed), {len(X)} frequencies, "
-                      f"forward + 4 dual-number derivative passes, {dt:.2f} s wall"}
+                      f"forward + 4 dual-number derivative passes, {dt:.2f} s wall",
+            "single_thread": {"value": n1 * info["terms"] * len(X) / dt1, "unit": "evals/s", "cores": 1,
+                              "sample": f"first {n1} samples, {dt1:.2f} s wall"}}
 
 
 def order4_diagram(lib):

@@ -3,7 +3,7 @@
     import paper_2311_17189_gb300 as tami
     d = tami.Diagram(alpha, eps=eps)            # AMI construction by residues (host, C++)
     d.upload()                                   # term table to the current CUDA device
-    mean, var = d.forward(lattice, seed, 0, n, X, beta)   # Monte Carlo over momenta (CUDA)
+    mean, var, _ = d.forward(lattice, seed, 0, n, X, beta)   # Monte Carlo over momenta (CUDA)
 
 Only marshalling lives in Python; the construction is libtami's C++ and every evaluation
 step is a libtami CUDA kernel.  `workloads` holds the seeded synthetic inputs.
