@@ -41,7 +41,7 @@ enum {
   TAMI_ENOMEM = 2,       /* host or device allocation failed                               */
   TAMI_ECUDA = 3,        /* a CUDA runtime call failed                                     */
   TAMI_ETIMEOUT = 4,     /* a bounded device wait gave up                                  */
-  TAMI_EUNSUPPORTED = 5  /* valid input outside what this build handles (see message)     */
+  TAMI_EUNSUPPORTED = 5  /* valid input outside what the library handles (see message)   */
 };
 
 enum { TAMI_MAX_LINES = 16, TAMI_MAX_VARS = 8 };

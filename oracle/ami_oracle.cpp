@@ -22,7 +22,7 @@
 //   * a brute-force Wick enumerator of Hubbard self-energy diagrams with a momentum
 //     labeller [Sec. 2.5 describes graph input and labelling].
 //
-// Readings of the paper that the text leaves open (each also listed in the design doc):
+// Readings of the paper that the text leaves open:
 //   R1  pole of G_j in nu_p: the root of alpha_p^j z + rest = 0, i.e.
 //       z = -alpha_p^j (E_j + sum_{l!=p} i alpha_l^j nu_l) for alpha_p^j = +-1 (Eq. Poles
 //       prints the inner energy with the dispersion's sign).
