@@ -4,7 +4,9 @@ Arrays on the device are torch tensors (complex128 / float64, CUDA); the calls r
 torch's current CUDA stream.  Host-only calls (construction, info, enumeration) take and
 return numpy arrays.
 """
+import contextlib
 import ctypes
+import os
 
 import numpy as np
 
@@ -14,6 +16,13 @@ from . import _lib as L
 def _torch():
     import torch
     return torch
+
+
+def _nvtx(name):
+    """An NVTX range around a library call when TAMI_NVTX=1 (for timeline profilers); else nothing."""
+    if os.environ.get("TAMI_NVTX") == "1":
+        return _torch().cuda.nvtx.range(name)
+    return contextlib.nullcontext()
 
 
 def _stream_ptr():
@@ -91,9 +100,10 @@ class Diagram:
         Xp = _as_c_pairs(X, E.device)
         n_e, n_f = E.shape[0], Xp.shape[0]
         out = torch.empty((n_f, n_e, 2), dtype=torch.float64, device=E.device)
-        L.check(L.lib().tami_eval_energies(self._h, ctypes.c_void_p(E.data_ptr()), n_e,
-                                           ctypes.c_void_p(Xp.data_ptr()), n_f, float(beta),
-                                           ctypes.c_void_p(out.data_ptr()), _stream_ptr()))
+        with _nvtx("tami_eval_energies"):
+            L.check(L.lib().tami_eval_energies(self._h, ctypes.c_void_p(E.data_ptr()), n_e,
+                                               ctypes.c_void_p(Xp.data_ptr()), n_f, float(beta),
+                                               ctypes.c_void_p(out.data_ptr()), _stream_ptr()))
         return torch.view_as_complex(out)
 
     def workspace(self, n, n_f):
@@ -130,12 +140,13 @@ class Diagram:
             raise L.TamiError(L.TAMI_EINVAL, "save must be a contiguous float64 [saved_rows, n] tensor")
         ws = self.workspace(n, n_f)
         lat = L.Lattice(*[float(v) for v in lattice])
-        L.check(L.lib().tami_forward(self._h, ctypes.byref(lat), int(seed), int(offset), int(n),
-                                     ctypes.c_void_p(Xp.data_ptr()), n_f, float(beta),
-                                     ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(var.data_ptr()),
-                                     ctypes.c_void_p(ps.data_ptr()) if ps is not None else None,
-                                     ctypes.c_void_p(save.data_ptr()) if save is not None else None,
-                                     ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr()))
+        with _nvtx("tami_forward"):
+            L.check(L.lib().tami_forward(self._h, ctypes.byref(lat), int(seed), int(offset), int(n),
+                                         ctypes.c_void_p(Xp.data_ptr()), n_f, float(beta),
+                                         ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(var.data_ptr()),
+                                         ctypes.c_void_p(ps.data_ptr()) if ps is not None else None,
+                                         ctypes.c_void_p(save.data_ptr()) if save is not None else None,
+                                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr()))
         return (torch.view_as_complex(mean), var, torch.view_as_complex(ps) if ps is not None else None)
 
     def backward(self, lattice, seed, offset, n, X, beta, gout, per_sample=False, saved=None):
@@ -165,9 +176,10 @@ class Diagram:
         ws = self._bws
         ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
         lat = L.Lattice(*[float(v) for v in lattice])
-        L.check(L.lib().tami_backward(self._h, ctypes.byref(lat), int(seed), int(offset), int(n), ptr(Xp), n_f,
-                                      float(beta), ptr(Gp), ptr(dX), ptr(gX), ptr(gp), ptr(ps_dX), ptr(ps_g),
-                                      ptr(saved), ptr(ws), ws.numel(), _stream_ptr()))
+        with _nvtx("tami_backward"):
+            L.check(L.lib().tami_backward(self._h, ctypes.byref(lat), int(seed), int(offset), int(n), ptr(Xp), n_f,
+                                          float(beta), ptr(Gp), ptr(dX), ptr(gX), ptr(gp), ptr(ps_dX), ptr(ps_g),
+                                          ptr(saved), ptr(ws), ws.numel(), _stream_ptr()))
         out = {"dSigma_dX": torch.view_as_complex(dX), "grad_X_re": gX, "grad_params": gp}
         if per_sample:
             out["dX"] = torch.view_as_complex(ps_dX)
@@ -216,9 +228,10 @@ class Batch:
         else:
             mean, var = out
         lat = L.Lattice(*[float(v) for v in lattice])
-        L.check(L.lib().tami_batch_launch(self._h, ctypes.byref(lat), ctypes.c_void_p(Xp.data_ptr()), float(beta),
-                                          ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(var.data_ptr()),
-                                          _stream_ptr()))
+        with _nvtx("tami_batch_launch"):
+            L.check(L.lib().tami_batch_launch(self._h, ctypes.byref(lat), ctypes.c_void_p(Xp.data_ptr()), float(beta),
+                                              ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(var.data_ptr()),
+                                              _stream_ptr()))
         return torch.view_as_complex(mean), var
 
     def __del__(self):

@@ -81,3 +81,18 @@ def test_largest_frequency_counts(order2):
         _, der, denv = S.eval_momenta_deriv(lat, c["seed"], 7, n, Xb, beta, which, threads=8, envelope=True)
         ref = np.real(np.conj(g)[:, None] * der).sum(axis=0)
         assert np.all(np.abs(got[:, k] - ref) <= RTOL * (np.abs(g)[:, None] * denv).sum(axis=0)), which
+
+
+def test_nvtx_ranges_change_nothing(order2, monkeypatch):
+    """TAMI_NVTX=1 wraps the library calls in NVTX ranges for timeline profilers; the results are
+    the same bits."""
+    D, c = order2
+    lat, beta = W.lattice(c), c["beta"]
+    X = W.matsubara(beta, 3)
+    ref, _, _ = D.forward(lat, c["seed"], 0, 777, X, beta)
+    monkeypatch.setenv("TAMI_NVTX", "1")
+    got, _, _ = D.forward(lat, c["seed"], 0, 777, X, beta)
+    g = D.backward(lat, c["seed"], 0, 777, X, beta, np.ones(3) + 0j)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+    assert torch.all(torch.isfinite(g["grad_params"]))
