@@ -87,6 +87,8 @@ typedef struct {
   /* per-sample flops of tami_forward when it writes `saved`, and of tami_backward reading it */
   double fwd_save_flops_per_sample;
   double bwd_saved_flops_per_sample;
+  /* per (sample, frequency) flops of tami_forward_backward (per sample: bwd_flops_per_sample) */
+  double fused_flops_per_sample_freq;
 } tami_info;
 
 const char* tami_last_error(void);
@@ -204,6 +206,24 @@ int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed,
                   double* dsigma_dX, double* grad_X_re, double* grad_params, double* per_sample_dX,
                   double* per_sample_grads, const double* saved, void* workspace, size_t workspace_bytes,
                   tami_stream_t stream);
+
+/* Scratch needed by tami_forward_backward (per-block partial sums of the adjoint and the forward). */
+int tami_forward_backward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, size_t* bytes);
+
+/* Forward and adjoint in one pass over the samples, for an upstream gradient known beforehand
+ * (no counterpart in the paper, which has no adjoint): the adjoint kernel already recomputes
+ * every energy, Fermi value, term product and denominator product of the forward, so it also
+ * forms each sample's value and the forward's sums.  Outputs as tami_forward (mean, var,
+ * per_sample) and tami_backward (dsigma_dX, grad_X_re, grad_params, per_sample_dX,
+ * per_sample_grads), each optional as there except mean.  dsigma_dX does not depend on gout
+ * (e.g. Sigma and dSigma/domega for the quasiparticle weight in one pass).  Per-sample outputs
+ * equal the separate calls' bit for bit; the reduced ones agree up to the grouping of the sums.
+ * Same limits as tami_backward. */
+int tami_forward_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
+                          int64_t n_samples, const double* X, int n_f, double beta, const double* gout, double* mean,
+                          double* var, double* per_sample, double* dsigma_dX, double* grad_X_re, double* grad_params,
+                          double* per_sample_dX, double* per_sample_grads, void* workspace, size_t workspace_bytes,
+                          tami_stream_t stream);
 
 /* tami_forward without a workspace argument: the same Monte Carlo evaluation and outputs, with
  * its scratch (a status word and the per-block partial sums) taken from a fixed 4 MiB array

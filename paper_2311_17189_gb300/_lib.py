@@ -18,7 +18,8 @@ TAMI_OK, TAMI_EINVAL, TAMI_ENOMEM, TAMI_ECUDA, TAMI_ETIMEOUT, TAMI_EUNSUPPORTED 
 EXPORTS = [
     "tami_last_error", "tami_construct", "tami_label_graph", "tami_construct_from_graph", "tami_diagram_info", "tami_upload", "tami_sample_energies",
     "tami_eval_energies", "tami_forward_workspace", "tami_forward", "tami_forward_noalloc",
-    "tami_backward_workspace", "tami_backward", "tami_batch_plan", "tami_batch_info", "tami_batch_launch",
+    "tami_backward_workspace", "tami_backward", "tami_forward_backward_workspace", "tami_forward_backward",
+    "tami_batch_plan", "tami_batch_info", "tami_batch_launch",
     "tami_batch_destroy", "tami_batch_debug_set_item",
     "tami_enumerate_sigma",
     "tami_selftest_exp", "tami_destroy",
@@ -49,6 +50,7 @@ class Info(ctypes.Structure):
         ("bwd_flops_per_sample", ctypes.c_double), ("bwd_flops_per_sample_freq", ctypes.c_double),
         ("saved_rows", ctypes.c_int),
         ("fwd_save_flops_per_sample", ctypes.c_double), ("bwd_saved_flops_per_sample", ctypes.c_double),
+        ("fused_flops_per_sample_freq", ctypes.c_double),
     ]
 
 
@@ -80,6 +82,9 @@ def lib():
     L.tami_backward_workspace.argtypes = [vp, i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.tami_backward.argtypes = [vp, ctypes.POINTER(Lattice), u64, u64, i64, dp, ctypes.c_int, ctypes.c_double,
                                 dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_size_t, vp]
+    L.tami_forward_backward_workspace.argtypes = [vp, i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.tami_forward_backward.argtypes = [vp, ctypes.POINTER(Lattice), u64, u64, i64, dp, ctypes.c_int, ctypes.c_double,
+                                        dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_size_t, vp]
     L.tami_batch_plan.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
     L.tami_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int)]

@@ -186,6 +186,42 @@ class Diagram:
             out["grads"] = ps_g
         return out
 
+    def forward_backward(self, lattice, seed, offset, n, X, beta, gout, per_sample=False):
+        """forward() and backward() in one pass (tami_forward_backward), for an upstream gradient
+        known beforehand.  Returns the union of their results: mean, var, dSigma_dX, grad_X_re,
+        grad_params and, with per_sample, values (complex [n_f, n]), dX and grads."""
+        torch = _torch()
+        dev = self._dev()
+        Xp = _as_c_pairs(X, dev)
+        Gp = _as_c_pairs(gout, dev)
+        n_f = Xp.shape[0]
+        f64 = dict(dtype=torch.float64, device=dev)
+        mean, var, dX = torch.empty((n_f, 2), **f64), torch.empty((n_f, 2), **f64), torch.empty((n_f, 2), **f64)
+        gX, gp = torch.empty((n_f,), **f64), torch.empty((3,), **f64)
+        ps = torch.empty((n_f, n, 2), **f64) if per_sample else None
+        ps_dX = torch.empty((n_f, n, 2), **f64) if per_sample else None
+        ps_g = torch.empty((n, 3), **f64) if per_sample else None
+        nbytes = ctypes.c_size_t()
+        L.check(L.lib().tami_forward_backward_workspace(self._h, int(n), n_f, ctypes.byref(nbytes)))
+        need = (nbytes.value + 255) // 256 * 256
+        if getattr(self, "_fws", None) is None or self._fws.numel() < need:
+            self._fws = torch.empty(need, dtype=torch.uint8, device=dev)
+        ws = self._fws
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        lat = L.Lattice(*[float(v) for v in lattice])
+        with _nvtx("tami_forward_backward"):
+            L.check(L.lib().tami_forward_backward(self._h, ctypes.byref(lat), int(seed), int(offset), int(n), ptr(Xp),
+                                                  n_f, float(beta), ptr(Gp), ptr(mean), ptr(var), ptr(ps), ptr(dX),
+                                                  ptr(gX), ptr(gp), ptr(ps_dX), ptr(ps_g), ptr(ws), ws.numel(),
+                                                  _stream_ptr()))
+        out = {"mean": torch.view_as_complex(mean), "var": var, "dSigma_dX": torch.view_as_complex(dX),
+               "grad_X_re": gX, "grad_params": gp}
+        if per_sample:
+            out["values"] = torch.view_as_complex(ps)
+            out["dX"] = torch.view_as_complex(ps_dX)
+            out["grads"] = ps_g
+        return out
+
 
 class Batch:
     """Many diagrams in one persistent, graph-captured launch (tami_batch_*).  Each diagram d gets

@@ -42,14 +42,19 @@ struct BwdParams {
   double* ps_dX;         // [n_f][n][2] or null
   double* ps_grad;       // [n][3] or null
   const double* saved;   // [n_rep + 2 n_rep_ext][n] from tami_forward, or null (recompute)
+  double* ps_v;          // fused pass: [n_f][n][2] each sample's value, or null
   double* partial;       // [grid][2 n_f + 3]
   int* status;
 };
 
-// Shared memory: table | X, G [n_f][2] | AXI, AXI2 [n_cden][n_f] | red [4 warps][2 n_f + 3]
-__host__ __device__ __forceinline__ size_t bwd_smem_bytes(const TableHeader& h, int n_f) {
+// Values each block reduces: dv/dX [n_f][2], the three parameter gradients and, in the fused pass,
+// the forward's sums [n_f][4] (Re, Im, Re^2, Im^2).
+__host__ __device__ __forceinline__ int bwd_nval(int n_f, bool fwd) { return 2 * n_f + 3 + (fwd ? 4 * n_f : 0); }
+
+// Shared memory: table | X, G [n_f][2] | AXI, AXI2 [n_cden][n_f] | red [4 warps][nval]
+__host__ __device__ __forceinline__ size_t bwd_smem_bytes(const TableHeader& h, int n_f, bool fwd) {
   return (size_t)align16(h.bytes) +
-         sizeof(double) * ((4 + 2 * (size_t)h.n_cden) * n_f + 4 * (2 * (size_t)n_f + 3));
+         sizeof(double) * ((4 + 2 * (size_t)h.n_cden) * n_f + 4 * (size_t)bwd_nval(n_f, fwd));
 }
 
 // Phase 2 of the adjoint for one sample over all frequencies: the reciprocals, the group products
@@ -58,12 +63,12 @@ __host__ __device__ __forceinline__ size_t bwd_smem_bytes(const TableHeader& h, 
 // the denominator-energy adjoints bb_d -= Re(conj g Z_d).  As in the forward, no data-dependent
 // selects around FP64 work (predicated-off FP64 instructions still cost FP64-pipe time): the R = 1
 // group is group 0 and the imaginary-axis case is a template parameter.
-template <bool XR_ZERO>
+template <bool XR_ZERO, bool FWD>
 __device__ __forceinline__ void bwd_phase2(const TableHeader& H, int n_f, long long s, const BwdParams& P,
                                            const double* Xs, const double* Gs, const double* AXI, const double* AXI2,
                                            const double* cden_a, const int* g2, const int* g2cd, const int* pnode,
-                                           const int* g2node, const double* pW, const double* b, double* Wb2,
-                                           double* bb, double* accX) {
+                                           const int* g2node, const double* pW, const double* b, const double* W2,
+                                           double* Wb2, double* bb, double* accX, double* accV) {
   for (int f = 0; f < n_f; ++f) {
     const double Xr = Xs[2 * f], gr = Gs[2 * f], gim = Gs[2 * f + 1], ngr = -gr, ngi = -gim;
     double vre[kBwCden + kMaxProdNodes], vim[kBwCden + kMaxProdNodes], U_re[kBwCden], U_im[kBwCden];
@@ -82,9 +87,15 @@ __device__ __forceinline__ void bwd_phase2(const TableHeader& H, int n_f, long l
       vim[H.n_cden + k] = fma(ar, bi, ai * br);
     }
     if (H.g2_const) Wb2[0] += gr;                 // R = 1
+    double vr = 0.0, vi = 0.0;                    // fused pass: the sample's value sum_h W_h R_h
+    if (FWD) vr = H.g2_const ? W2[0] : 0.0;
     for (int h = H.g2_const; h < H.n_g2; ++h) {
       const int v = g2node[h];
       const double Rr = vre[v], Ri = vim[v];
+      if (FWD) {
+        vr = fma(W2[h], Rr, vr);
+        vi = fma(W2[h], Ri, vi);
+      }
       Wb2[h] = fma(gr, Rr, fma(gim, Ri, Wb2[h]));
       for (int q = g2[h]; q < g2[h + 1]; ++q) {
         const int cc = g2cd[2 * q];
@@ -106,6 +117,13 @@ __device__ __forceinline__ void bwd_phase2(const TableHeader& H, int n_f, long l
       double2* o = reinterpret_cast<double2*>(P.ps_dX) + (size_t)f * P.n + s;
       *o = make_double2(dvr, dvi);
     }
+    if (FWD) {
+      accV[4 * f] += vr;
+      accV[4 * f + 1] += vi;
+      accV[4 * f + 2] = fma(vr, vr, accV[4 * f + 2]);
+      accV[4 * f + 3] = fma(vi, vi, accV[4 * f + 3]);
+      if (P.ps_v) reinterpret_cast<double2*>(P.ps_v)[(size_t)f * P.n + s] = make_double2(vr, vi);
+    }
   }
 }
 
@@ -115,7 +133,9 @@ __device__ __forceinline__ void bwd_phase2(const TableHeader& H, int n_f, long l
 #define TAMI_BWD_MIN_BLOCKS 8
 #endif
 
-template <bool SAVED>
+// SAVED: read the forward's saved rows instead of recomputing the energies.  FWD: the fused pass,
+// which also forms each sample's value and the forward's sums (mean, variance) in phase 2.
+template <bool SAVED, bool FWD>
 __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const BwdParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const TableHeader& H = P.h;
@@ -126,7 +146,7 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
   double* Gs = Xs + 2 * n_f;
   double* AXI = Gs + 2 * n_f;
   double* AXI2 = AXI + H.n_cden * n_f;
-  double* red = AXI2 + H.n_cden * n_f;       // [4 warps][2 n_f + 3]
+  double* red = AXI2 + H.n_cden * n_f;       // [4 warps][nval]
   for (int i = tid; i < 2 * n_f; i += kBlock) { Xs[i] = P.X[i]; Gs[i] = P.G[i]; }
 
   const int* repl = reinterpret_cast<const int*>(smem + H.off_repl);
@@ -154,8 +174,10 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
   const int* pnode = reinterpret_cast<const int*>(smem + H.off_pnode);
   const int* g2node = reinterpret_cast<const int*>(smem + H.off_g2node);
 
-  double accX[2 * kBwFreq];
+  double accX[2 * kBwFreq], accV[FWD ? 4 * kBwFreq : 1];
   for (int i = 0; i < 2 * n_f; ++i) accX[i] = 0.0;
+  if (FWD)
+    for (int i = 0; i < 4 * n_f; ++i) accV[i] = 0.0;
   double gmu = 0.0, gkx = 0.0, gky = 0.0;
   __syncthreads();
   bool xr_zero;
@@ -262,9 +284,11 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
     }
     for (int c = 0; c < H.n_cden; ++c) bb[c] = 0.0;
     if (xr_zero)
-      bwd_phase2<true>(H, n_f, s, P, Xs, Gs, AXI, AXI2, cden_a, g2, g2cd, pnode, g2node, pW, b, Wb2, bb, accX);
+      bwd_phase2<true, FWD>(H, n_f, s, P, Xs, Gs, AXI, AXI2, cden_a, g2, g2cd, pnode, g2node, pW, b, W2, Wb2, bb,
+                            accX, accV);
     else
-      bwd_phase2<false>(H, n_f, s, P, Xs, Gs, AXI, AXI2, cden_a, g2, g2cd, pnode, g2node, pW, b, Wb2, bb, accX);
+      bwd_phase2<false, FWD>(H, n_f, s, P, Xs, Gs, AXI, AXI2, cden_a, g2, g2cd, pnode, g2node, pW, b, W2, Wb2, bb,
+                             accX, accV);
     // ------------------------------------------------------------ reverse sweep
     double xbar[kBwCombos], fvbar[kBwFv];
     for (int u = 0; u < H.n_combo; ++u) xbar[u] = 0.0;
@@ -341,10 +365,11 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
     }
   }
   // -------------------------------------------------------------- block reduction
-  const int nval = 2 * n_f + 3;
+  const int nval = bwd_nval(n_f, FWD);
   const int warp = tid >> 5, lane = tid & 31;
   for (int i = 0; i < nval; ++i) {
     double v = i < 2 * n_f ? accX[i] : (i == 2 * n_f ? gmu : (i == 2 * n_f + 1 ? gkx : gky));
+    if (FWD && i >= 2 * n_f + 3) v = accV[i - 2 * n_f - 3];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if (lane == 0) red[warp * nval + i] = v;
   }
@@ -384,26 +409,74 @@ __global__ void __launch_bounds__(kFinBlock) bwd_finalize_kernel(const double* p
   }
 }
 
-int bwd_grid(const tami_diagram* d, int n_f, long long n, size_t* smem_out) {
+int bwd_grid(const tami_diagram* d, int n_f, long long n, size_t* smem_out, bool fwd) {
   DeviceProps dp = device_props(d->device);
-  const size_t smem = bwd_smem_bytes(d->hdr, n_f);
+  const size_t smem = bwd_smem_bytes(d->hdr, n_f, fwd);
   if (smem_out) *smem_out = smem;
   if (smem > dp.smem_optin) return -1;
-  // one grid for both instances (saved rows or recomputation), so that their reductions group the
-  // samples alike and the results agree bit for bit
-  cudaFuncSetAttribute(bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0, per_sm_saved = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel<false>, kBlock, smem) != cudaSuccess) per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_saved, bwd_kernel<true>, kBlock, smem) != cudaSuccess)
-    per_sm_saved = 1;
-  if (per_sm_saved < per_sm) per_sm = per_sm_saved;
+  int per_sm = 0;
+  if (fwd) {
+    cudaFuncSetAttribute(bwd_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel<false, true>, kBlock, smem) != cudaSuccess)
+      per_sm = 1;
+  } else {
+    // one grid for both adjoint instances (saved rows or recomputation), so that their reductions
+    // group the samples alike and the results agree bit for bit
+    cudaFuncSetAttribute(bwd_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(bwd_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm_saved = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd_kernel<false, false>, kBlock, smem) != cudaSuccess)
+      per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_saved, bwd_kernel<true, false>, kBlock, smem) !=
+        cudaSuccess)
+      per_sm_saved = 1;
+    if (per_sm_saved < per_sm) per_sm = per_sm_saved;
+  }
   if (per_sm < 1) per_sm = 1;
   long long tiles = (n + kBlock - 1) / kBlock;
   long long grid = (long long)dp.sms * per_sm;
   if (grid > tiles) grid = tiles;
   if (grid < 1) grid = 1;
   return (int)grid;
+}
+
+// The fused pass's final reduction: block f < n_f sums dv/dX_f and the forward's four sums of f,
+// block n_f the three parameter gradients; fixed tree order.
+__global__ void __launch_bounds__(kFinBlock) fused_finalize_kernel(const double* partial, int n_blocks, int n_f,
+                                                                  long long n, const double* G, const int* status,
+                                                                  double* mean, double* var, double* dX,
+                                                                  double* grad_omega, double* grad_params) {
+  __shared__ double sh[6][kFinBlock];
+  const int i = blockIdx.x;
+  const int nval = bwd_nval(n_f, true);
+  double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < n_blocks; b += kFinBlock) {
+    const double* p = partial + (size_t)b * nval;
+    if (i < n_f) {
+      s[0] += p[2 * i];
+      s[1] += p[2 * i + 1];
+      for (int k = 0; k < 4; ++k) s[2 + k] += p[2 * n_f + 3 + 4 * i + k];
+    } else {
+      for (int k = 0; k < 3; ++k) s[k] += p[2 * n_f + k];
+    }
+  }
+  fixed_tree_sum<6>(s, sh);
+  if (threadIdx.x != 0) return;
+  const bool bad = status && *status != 0;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll), nn = (double)n;
+  if (i < n_f) {
+    const double re = bad ? nan : s[0] / nn, im = bad ? nan : s[1] / nn;
+    if (dX) { dX[2 * i] = re; dX[2 * i + 1] = im; }
+    if (grad_omega) grad_omega[i] = bad ? nan : fma(G[2 * i], re, G[2 * i + 1] * im);
+    const double mr = s[2] / nn, mi = s[3] / nn;
+    const double vr = n > 1 ? (s[4] - s[2] * mr) / (nn - 1.0) : 0.0;
+    const double vi = n > 1 ? (s[5] - s[3] * mi) / (nn - 1.0) : 0.0;
+    mean[2 * i] = bad ? nan : mr;
+    mean[2 * i + 1] = bad ? nan : mi;
+    if (var) { var[2 * i] = bad ? nan : vr; var[2 * i + 1] = bad ? nan : vi; }
+  } else if (grad_params) {
+    for (int k = 0; k < 3; ++k) grad_params[k] = bad ? nan : s[k] / nn;
+  }
 }
 
 int bwd_check(const tami_diagram* d, int n_f) {
@@ -436,9 +509,19 @@ int tami_backward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, s
   int rc = bwd_check(d, n_f);
   if (rc) return rc;
   if (!bytes || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
-  const int grid = bwd_grid(d, n_f, n_samples, nullptr);
+  const int grid = bwd_grid(d, n_f, n_samples, nullptr, false);
   if (grid < 0) { set_error("term table and frequencies exceed shared memory"); return TAMI_EUNSUPPORTED; }
-  *bytes = kBwStatusBytes + sizeof(double) * (size_t)(2 * n_f + 3) * (size_t)grid;
+  *bytes = kBwStatusBytes + sizeof(double) * (size_t)bwd_nval(n_f, false) * (size_t)grid;
+  return TAMI_OK;
+}
+
+int tami_forward_backward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, size_t* bytes) {
+  int rc = bwd_check(d, n_f);
+  if (rc) return rc;
+  if (!bytes || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
+  const int grid = bwd_grid(d, n_f, n_samples, nullptr, true);
+  if (grid < 0) { set_error("term table and frequencies exceed shared memory"); return TAMI_EUNSUPPORTED; }
+  *bytes = kBwStatusBytes + sizeof(double) * (size_t)bwd_nval(n_f, true) * (size_t)grid;
   return TAMI_OK;
 }
 
@@ -453,9 +536,9 @@ int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed,
   if (!beta_ok(beta)) return TAMI_EINVAL;
   if (((uintptr_t)workspace & 255) != 0) { set_error("workspace must be 256-byte aligned"); return TAMI_EINVAL; }
   size_t smem = 0;
-  const int grid = bwd_grid(d, n_f, n_samples, &smem);
+  const int grid = bwd_grid(d, n_f, n_samples, &smem, false);
   if (grid < 0) { set_error("term table and frequencies exceed shared memory"); return TAMI_EUNSUPPORTED; }
-  const size_t need = kBwStatusBytes + sizeof(double) * (size_t)(2 * n_f + 3) * (size_t)grid;
+  const size_t need = kBwStatusBytes + sizeof(double) * (size_t)bwd_nval(n_f, false) * (size_t)grid;
   if (workspace_bytes < need) { set_error("workspace too small"); return TAMI_EINVAL; }
   cudaStream_t st = (cudaStream_t)stream;
   int* status = static_cast<int*>(workspace);
@@ -472,14 +555,52 @@ int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed,
   P.ps_dX = per_sample_dX; P.ps_grad = per_sample_grads;
   P.saved = saved;
   P.partial = partial; P.status = status;
-  if (saved) bwd_kernel<true><<<grid, kBlock, smem, st>>>(P);
-  else bwd_kernel<false><<<grid, kBlock, smem, st>>>(P);
+  if (saved) bwd_kernel<true, false><<<grid, kBlock, smem, st>>>(P);
+  else bwd_kernel<false, false><<<grid, kBlock, smem, st>>>(P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "bwd_kernel launch");
   bwd_finalize_kernel<<<n_f + 1, kFinBlock, 0, st>>>(partial, grid, n_f, n_samples, gout, status,
                                                               dsigma_dX, grad_X_re, grad_params);
   e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "bwd finalize launch");
+}
+
+int tami_forward_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
+                          int64_t n_samples, const double* X, int n_f, double beta, const double* gout, double* mean,
+                          double* var, double* per_sample, double* dsigma_dX, double* grad_X_re, double* grad_params,
+                          double* per_sample_dX, double* per_sample_grads, void* workspace, size_t workspace_bytes,
+                          tami_stream_t stream) {
+  int rc = bwd_check(d, n_f);
+  if (rc) return rc;
+  if (!lat || !X || !gout || !mean || !workspace || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (!beta_ok(beta)) return TAMI_EINVAL;
+  if (((uintptr_t)workspace & 255) != 0) { set_error("workspace must be 256-byte aligned"); return TAMI_EINVAL; }
+  size_t smem = 0;
+  const int grid = bwd_grid(d, n_f, n_samples, &smem, true);
+  if (grid < 0) { set_error("term table and frequencies exceed shared memory"); return TAMI_EUNSUPPORTED; }
+  const size_t need = kBwStatusBytes + sizeof(double) * (size_t)bwd_nval(n_f, true) * (size_t)grid;
+  if (workspace_bytes < need) { set_error("workspace too small"); return TAMI_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  int* status = static_cast<int*>(workspace);
+  double* partial = reinterpret_cast<double*>(static_cast<char*>(workspace) + kBwStatusBytes);
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  BwdParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.h = d->hdr;
+  P.table = static_cast<const unsigned char*>(d->d_blob);
+  P.t = lat->t; P.tp = lat->tp; P.mu = lat->mu; P.kx = lat->kx_ext; P.ky = lat->ky_ext;
+  P.seed = seed; P.offset = offset; P.n = n_samples;
+  P.X = X; P.G = gout; P.n_f = n_f; P.beta = beta;
+  P.ps_dX = per_sample_dX; P.ps_grad = per_sample_grads; P.ps_v = per_sample;
+  P.partial = partial; P.status = status;
+  bwd_kernel<false, true><<<grid, kBlock, smem, st>>>(P);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+  fused_finalize_kernel<<<n_f + 1, kFinBlock, 0, st>>>(partial, grid, n_f, n_samples, gout, status, mean, var,
+                                                       dsigma_dX, grad_X_re, grad_params);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "fused finalize launch");
 }
 
 }  // extern "C"

@@ -744,6 +744,9 @@ int flatten(tami_diagram* d) {
   bf += 6.0 * h.n_pnode;                                // products (trie nodes)
   for (auto& g : g2s) bf += g.empty() ? 1.0 : 4.0 + 4.0 * g.size();   // Wbar, U += p W R
   I.bwd_flops_per_sample_freq = bf;
+  double fused = bf + 6.0;                              // the forward's sums
+  for (auto& g : g2s) fused += g.empty() ? 1.0 : 4.0;   // W R accumulated
+  I.fused_flops_per_sample_freq = fused;
   return TAMI_OK;
 }
 

@@ -228,3 +228,27 @@ def test_saved_energies_give_the_same_bits(case):
     b1 = D.backward(lat, seed, off, n, X, beta, g, per_sample=True, saved=sv)
     for k in ("dSigma_dX", "grad_X_re", "grad_params", "dX", "grads"):
         assert torch.equal(b0[k], b1[k]), k
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_fused_forward_backward(case):
+    """tami_forward_backward (forward and adjoint in one pass): each sample's value, dv/dX and
+    contracted gradients equal the separate tami_forward / tami_backward outputs bit for bit; the
+    reduced mean, variance, dSigma/dX and gradients agree with them to the rounding of the sums
+    (the two launches group the partial sums differently)."""
+    D, S, lat, beta, X = setup_case(case)
+    n, seed, off = 3 * 128 + 37, 21, 5
+    g = upstream(len(X))
+    m, v, p = D.forward(lat, seed, off, n, X, beta, per_sample=True)
+    b = D.backward(lat, seed, off, n, X, beta, g, per_sample=True)
+    fb = D.forward_backward(lat, seed, off, n, X, beta, g, per_sample=True)
+    torch.cuda.synchronize()
+    assert torch.equal(fb["values"], p)
+    assert torch.equal(fb["dX"], b["dX"]) and torch.equal(fb["grads"], b["grads"])
+    scale = p.abs().mean(dim=1)
+    assert torch.all((fb["mean"] - m).abs() <= 1e-13 * scale)
+    assert torch.allclose(fb["var"], v, rtol=1e-12, atol=0)
+    dscale = b["dX"].abs().mean(dim=1)
+    assert torch.all((fb["dSigma_dX"] - b["dSigma_dX"]).abs() <= 1e-13 * dscale)
+    gscale = b["grads"].abs().mean(dim=0)
+    assert torch.all((fb["grad_params"] - b["grad_params"]).abs() <= 1e-13 * gscale)
