@@ -386,18 +386,14 @@ def run_workload(args):
         Gd = [torch.full_like(x, 1.0 + 0.5j) for x in Xd]
         n_f = len(Xs[0])
 
-        saved = D.saved_buffer(n)
-
         def step(i):
             for b, X, G in zip(betas, Xd, Gd):
-                D.forward(lat, c["seed"], i * n, n, X, b, save=saved)
-                D.backward(lat, c["seed"], i * n, n, X, b, G, saved=saved)
-        launches_per_step = 4 * len(betas)
+                D.forward_backward(lat, c["seed"], i * n, n, X, b, G)
+        launches_per_step = 2 * len(betas)
         evals = float(n) * info["n_terms"] * n_f * len(betas)
-        flops = len(betas) * n * (info["fwd_save_flops_per_sample"] + n_f * info["flops_per_sample_freq"] +
-                                  info["bwd_saved_flops_per_sample"] + n_f * info["bwd_flops_per_sample_freq"])
+        flops = len(betas) * n * (info["bwd_flops_per_sample"] + n_f * info["fused_flops_per_sample_freq"])
         config = {"workload": c["name"], "samples": n, "frequencies": n_f, "terms": info["n_terms"],
-                  "betas": list(betas), "step": "forward (keeping per-sample energies) + adjoint at every beta"}
+                  "betas": list(betas), "step": "forward + adjoint in one pass (tami_forward_backward) at every beta"}
         bytes_step = None
     elif wl == "all_orders":
         c = W.ALL_ORDERS
