@@ -8,12 +8,14 @@
 // The paper defines the forward evaluation (Sec. 2.3, Sec. 5.2); it has no adjoint.
 //
 // One thread per sample, every phase sample-major: the forward quantities of phase 1 are
-// recomputed (energies, combinations, Fermi values and their next derivative, group weights),
-// phase 2 runs over all frequencies and collects dv/dX, the adjoints of the group weights and
-// of the frequency-dependent denominator energies, and a reverse sweep pushes those back
-// through the term products (recomputed with prefix/suffix products, never stored), the
-// Fermi/Bose derivatives (d/dx P_k = P_{k+1}), the energy combinations and the dispersion
-// (dE/dmu = 1, dE/dk_ext = -alpha_ext * grad eps).  Reductions are in a fixed order.
+// recomputed (combinations, Fermi values and their next derivative, the pole DAG keeping every
+// node's value, group weights) from line energies that are either recomputed from the momenta or
+// read from rows the forward saved; phase 2 runs over all frequencies and collects dv/dX, the
+// adjoints of the group weights and of the frequency-dependent denominator energies; a reverse
+// sweep pushes those back through the pole DAG, the Fermi/Bose derivatives (d/dx P_k = P_{k+1}),
+// the energy combinations and the dispersion (dE/dmu = 1, dE/dk_ext = -alpha_ext * G).  Term
+// products are recomputed, never stored.  The fused instance (tami_forward_backward) also forms
+// each sample's value and the forward's sums in phase 2.  Reductions are in a fixed order.
 #include <algorithm>
 #include <cstring>
 
