@@ -252,3 +252,35 @@ def test_fused_forward_backward(case):
     assert torch.all((fb["dSigma_dX"] - b["dSigma_dX"]).abs() <= 1e-13 * dscale)
     gscale = b["grads"].abs().mean(dim=0)
     assert torch.all((fb["grad_params"] - b["grad_params"]).abs() <= 1e-13 * gscale)
+
+
+def test_order4_fused_full_size_sampled():
+    """The benchmark's launch at its full size: the fused forward + adjoint over 2^24 samples of
+    the order-4 workload with the bench's upstream gradient.  Per-sample values and contracted
+    gradients at 300 random samples against the oracle computed one by one; the means against
+    the means of the per-sample outputs."""
+    c = W.ORDER4
+    d = next(x for x in O.enumerate_sigma(4) if x["code"] == c["code"])
+    D, S = both(d["alpha"], d["eps"])
+    X, lat, beta, n = W.matsubara(c["beta"], c["n_freq"]), W.lattice(c), c["beta"], c["n_samples"]
+    g = np.ones(len(X)) + 0.5j
+    out = D.forward_backward(lat, c["seed"], 0, n, X, beta, g, per_sample=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    idx = np.sort(rng.choice(n, 300, replace=False))
+    ti = torch.as_tensor(idx, device="cuda")
+    vals = out["values"][:, ti].cpu().numpy()
+    grads = out["grads"][ti].cpu().numpy()
+    for k, i in enumerate(idx):
+        r = S.eval_momenta(lat, c["seed"], int(i), 1, X, beta, per_sample=True)
+        assert np.all(np.abs(vals[:, k] - r["values"][:, 0]) <= RTOL * r["envelope"][:, 0]), i
+        for j, which in enumerate(("mu", "kx", "ky")):
+            _, der, denv = S.eval_momenta_deriv(lat, c["seed"], int(i), 1, X, beta, which, envelope=True)
+            ref = np.real(np.conj(g) * der[:, 0]).sum()
+            assert abs(grads[k, j] - ref) <= RTOL * (np.abs(g) * denv[:, 0]).sum(), (i, which)
+    scale = out["values"].abs().mean(dim=1)
+    assert torch.all((out["mean"] - out["values"].mean(dim=1)).abs() <= 1e-12 * scale)
+    gscale = out["grads"].abs().mean(dim=0)
+    assert torch.all((out["grad_params"] - out["grads"].mean(dim=0)).abs() <= 1e-12 * gscale)
+    dscale = out["dX"].abs().mean(dim=1)
+    assert torch.all((out["dSigma_dX"] - out["dX"].mean(dim=1)).abs() <= 1e-12 * dscale)
