@@ -35,6 +35,9 @@ def lib():
         L.orc_fermi_deriv.restype = ctypes.c_double
         L.orc_construct.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, i32p, ctypes.c_double]
         L.orc_construct.restype = ctypes.c_void_p
+        L.orc_construct_ext.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, i32p,
+                                        ctypes.c_double]
+        L.orc_construct_ext.restype = ctypes.c_void_p
         L.orc_destroy.argtypes = [ctypes.c_void_p]
         L.orc_info.argtypes = [ctypes.c_void_p, i64p]
         L.orc_term.argtypes = [ctypes.c_void_p, ctypes.c_int64, dp, i32p, i32p, i32p, i32p, i32p, i32p,
@@ -49,11 +52,12 @@ def lib():
         L.orc_eval_momenta_deriv.argtypes = [ctypes.c_void_p, i32p, dp, ctypes.c_uint64, ctypes.c_uint64,
                                              ctypes.c_int64, dp, dp, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_int, dp, dp, dp, dp, dp, ctypes.c_int]
-        L.orc_eval_energies_deriv.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_int64, dp, dp,
-                                              ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                              ctypes.c_double, dp, dp]
-        L.orc_brute_force.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, dp, ctypes.c_double,
-                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
+        L.orc_eval_energies_deriv.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_int64, dp, dp, dp, dp,
+                                              ctypes.c_int, ctypes.c_double, dp, dp]
+        L.orc_eval_momenta.restype = ctypes.c_int
+        L.orc_eval_momenta_deriv.restype = ctypes.c_int
+        L.orc_brute_force.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, dp, dp, dp,
+                                      ctypes.c_double, ctypes.c_int, dp]
         L.orc_enumerate_sigma.argtypes = [ctypes.c_int]
         L.orc_diagram.argtypes = [ctypes.c_int, i32p, i32p, i32p, dp, i32p]
         _lib = L
@@ -78,6 +82,11 @@ def _err():
     return lib().orc_last_error().decode()
 
 
+def _chk(rc):
+    if rc != 0:
+        raise ValueError("oracle: " + _err())
+
+
 def philox4x32_10(ctr, key):
     c = np.asarray(ctr, dtype=np.uint32)
     k = np.asarray(key, dtype=np.uint32)
@@ -98,19 +107,28 @@ def fermi_deriv(sigma, k, beta, x):
     return lib().orc_fermi_deriv(int(sigma), int(k), float(beta), float(x))
 
 
-class Solution:
-    """AMI solution built by the oracle (flat terms)."""
+def _rows(X, n_ext):
+    """External frequencies as contiguous (re, im) arrays [n_f, n_ext]: X is [n_f] (n_ext = 1) or
+    [n_f, n_ext]."""
+    X = np.asarray(X, dtype=np.complex128).reshape(-1, n_ext)
+    return _f64(X.real), _f64(X.imag), X.shape[0]
 
-    def __init__(self, alpha, eps=None, var_is_boson=None, order=None, prefactor=1.0):
+
+class Solution:
+    """AMI solution built by the oracle (flat terms).  The last n_ext columns of alpha are the
+    external variables (Sec. 2.3); the others are summed."""
+
+    def __init__(self, alpha, eps=None, var_is_boson=None, order=None, prefactor=1.0, n_ext=1):
         alpha = _i32(alpha)
         self.alpha = alpha
         self.N, self.nv = alpha.shape
+        self.n_ext = int(n_ext)
         self.eps = _i32(eps)
         self.boson = _i32(var_is_boson)
         self.order = _i32(order)
-        h = lib().orc_construct(self.N, self.nv, _ptr(alpha, ctypes.c_int), _ptr(self.eps, ctypes.c_int),
-                                _ptr(self.boson, ctypes.c_int), _ptr(self.order, ctypes.c_int),
-                                float(prefactor))
+        h = lib().orc_construct_ext(self.N, self.nv, self.n_ext, _ptr(alpha, ctypes.c_int),
+                                    _ptr(self.eps, ctypes.c_int), _ptr(self.boson, ctypes.c_int),
+                                    _ptr(self.order, ctypes.c_int), float(prefactor))
         if not h:
             raise ValueError("oracle construct failed: " + _err())
         self._h = h
@@ -133,24 +151,27 @@ class Solution:
         fs = np.zeros(cap, dtype=np.int32)
         fk = np.zeros(cap, dtype=np.int32)
         ge = np.zeros(cap * self.N, dtype=np.int32)
-        ga = np.zeros(cap, dtype=np.int32)
+        ga = np.zeros(cap * self.n_ext, dtype=np.int32)
         rc = lib().orc_term(self._h, int(t), ctypes.byref(A), ctypes.byref(nF), _ptr(fc, ctypes.c_int),
                             _ptr(fs, ctypes.c_int), _ptr(fk, ctypes.c_int), ctypes.byref(nG),
                             _ptr(ge, ctypes.c_int), _ptr(ga, ctypes.c_int), cap)
         if rc != 0:
             raise ValueError(_err())
         F = [(tuple(fc[i * self.N:(i + 1) * self.N]), int(fs[i]), int(fk[i])) for i in range(nF.value)]
-        G = [(tuple(ge[i * self.N:(i + 1) * self.N]), int(ga[i])) for i in range(nG.value)]
+        if self.n_ext == 1:
+            G = [(tuple(ge[i * self.N:(i + 1) * self.N]), int(ga[i])) for i in range(nG.value)]
+        else:
+            G = [(tuple(ge[i * self.N:(i + 1) * self.N]), tuple(ga[i * self.n_ext:(i + 1) * self.n_ext]))
+                 for i in range(nG.value)]
         return A.value, F, G
 
     def eval_energies(self, E, X, beta, threads=1):
-        """E: [n_e, N] base energies; X: [n_f] complex.  Returns (values [n_f, n_e] complex,
-        sum|term| [n_f, n_e], envelope [n_f, n_e])."""
+        """E: [n_e, N] base energies; X: [n_f] complex (n_ext = 1) or [n_f, n_ext] (one row of
+        external frequencies per f).  Returns (values [n_f, n_e] complex, sum|term| [n_f, n_e],
+        envelope [n_f, n_e])."""
         E = _f64(E)
         n_e = E.shape[0]
-        X = np.asarray(X, dtype=np.complex128).ravel()
-        xr, xi = _f64(X.real), _f64(X.imag)
-        nf = X.size
+        xr, xi, nf = _rows(X, self.n_ext)
         vr = np.empty((nf, n_e)); vi = np.empty((nf, n_e))
         ab = np.empty((nf, n_e)); en = np.empty((nf, n_e))
         d = ctypes.c_double
@@ -171,9 +192,9 @@ class Solution:
         vr = vi = en = None
         if per_sample:
             vr = np.empty((nf, n)); vi = np.empty((nf, n)); en = np.empty((nf, n))
-        lib().orc_eval_momenta(self._h, _ptr(a, ctypes.c_int), _ptr(lat, d), int(seed), int(offset), int(n),
+        _chk(lib().orc_eval_momenta(self._h, _ptr(a, ctypes.c_int), _ptr(lat, d), int(seed), int(offset), int(n),
                                _ptr(xr, d), _ptr(xi, d), nf, float(beta), _ptr(vr, d), _ptr(vi, d),
-                               _ptr(en, d), _ptr(mean, d), _ptr(var, d), int(threads))
+                               _ptr(en, d), _ptr(mean, d), _ptr(var, d), int(threads)))
         out = {"mean": mean[0::2] + 1j * mean[1::2], "var": var.reshape(nf, 2)}
         if per_sample:
             out["values"] = vr + 1j * vi
@@ -194,24 +215,25 @@ class Solution:
         d = ctypes.c_double
         vr = np.empty((nf, n)); vi = np.empty((nf, n)); dr = np.empty((nf, n)); di = np.empty((nf, n))
         de = np.empty((nf, n))
-        lib().orc_eval_momenta_deriv(self._h, _ptr(a, ctypes.c_int), _ptr(lat, d), int(seed), int(offset),
-                                     int(n), _ptr(xr, d), _ptr(xi, d), nf, float(beta), w, _ptr(vr, d),
-                                     _ptr(vi, d), _ptr(dr, d), _ptr(di, d), _ptr(de, d), int(threads))
+        _chk(lib().orc_eval_momenta_deriv(self._h, _ptr(a, ctypes.c_int), _ptr(lat, d), int(seed), int(offset),
+                                          int(n), _ptr(xr, d), _ptr(xi, d), nf, float(beta), w, _ptr(vr, d),
+                                          _ptr(vi, d), _ptr(dr, d), _ptr(di, d), _ptr(de, d), int(threads)))
         if envelope:
             return vr + 1j * vi, dr + 1j * di, de
         return vr + 1j * vi, dr + 1j * di
 
     def eval_energies_deriv(self, E, dE, X, dX, beta):
+        """Dual-number derivative [n_f, n_e] along dE (base energies, [n_e, N]) and dX (the
+        external frequencies' direction, scalar or [n_ext], the same for every row of X)."""
         E = _f64(E); dE = _f64(dE)
         n_e = E.shape[0]
-        X = np.asarray(X, dtype=np.complex128).ravel()
-        xr, xi = _f64(X.real), _f64(X.imag)
-        nf = X.size
+        xr, xi, nf = _rows(X, self.n_ext)
+        dXv = np.broadcast_to(np.asarray(dX, dtype=np.complex128).ravel(), (self.n_ext,))
+        dxr, dxi = _f64(dXv.real), _f64(dXv.imag)
         d = ctypes.c_double
         dr = np.empty((nf, n_e)); di = np.empty((nf, n_e))
         lib().orc_eval_energies_deriv(self._h, _ptr(E, d), _ptr(dE, d), n_e, _ptr(xr, d), _ptr(xi, d),
-                                      float(np.real(dX)), float(np.imag(dX)), nf, float(beta),
-                                      _ptr(dr, d), _ptr(di, d))
+                                      _ptr(dxr, d), _ptr(dxi, d), nf, float(beta), _ptr(dr, d), _ptr(di, d))
         return dr + 1j * di
 
 
@@ -227,15 +249,18 @@ def sample_energies(alpha, lattice, seed, offset, n):
     return E, k
 
 
-def brute_force(alpha, E, X, beta, nmax, eps=None, var_is_boson=None):
+def brute_force(alpha, E, X, beta, nmax, eps=None, var_is_boson=None, n_ext=1):
+    """Truncated Matsubara sum of prod_j G_j over the first nv - n_ext variables; X: the n_ext
+    external frequencies (scalar for n_ext = 1)."""
     a = _i32(alpha)
     N, nv = a.shape
     E = _f64(E)
+    xr, xi, _ = _rows(X, n_ext)
     out = np.empty(2)
     d = ctypes.c_double
-    lib().orc_brute_force(N, nv, _ptr(a, ctypes.c_int), _ptr(_i32(eps), ctypes.c_int),
-                          _ptr(_i32(var_is_boson), ctypes.c_int), _ptr(E, d), float(np.real(X)),
-                          float(np.imag(X)), float(beta), int(nmax), _ptr(out, d))
+    _chk(lib().orc_brute_force(N, nv, int(n_ext), _ptr(a, ctypes.c_int), _ptr(_i32(eps), ctypes.c_int),
+                               _ptr(_i32(var_is_boson), ctypes.c_int), _ptr(E, d), _ptr(xr, d), _ptr(xi, d),
+                               float(beta), int(nmax), _ptr(out, d)))
     return out[0] + 1j * out[1]
 
 

@@ -14,7 +14,8 @@
 //     resulting term is A * prod(Fermi/Bose factors) * prod(Green's functions)
 //     [Sec. 2.2, "I = A FT R"], kept flat (the FACTORIZE=false form);
 //   * evaluation [Sec. 2.3]: terms evaluated one by one for a batch of energies and
-//     external frequencies, summed with Neumaier compensation;
+//     rows of external frequencies (n_ext >= 1 external variables, the last columns of the
+//     labels, as in the frequency_t rows of Sec. 2.3), summed with Neumaier compensation;
 //   * momentum sampling [Sec. 5.2]: K = k A^T line momenta and a per-line dispersion;
 //   * forward-mode dual-number derivatives of the same evaluation (d/d omega, d/d mu,
 //     d/d k_ext) -- an independent check of an adjoint;
@@ -163,7 +164,7 @@ double deps_dkx(double kx, double ky, double t, double tp) {
 // ---------------------------------------------------------------------------------------
 struct GFac {              // 1 / (sum_l i a_l nu_l + sum_j e_j E_j)  (Eq. Green_Function)
   std::vector<int> e;      // energy coefficients over the N base energies
-  std::vector<int> a;      // frequency coefficients, external variable last
+  std::vector<int> a;      // frequency coefficients, the external variables last
   bool operator==(const GFac& o) const { return e == o.e && a == o.a; }
 };
 struct FFac {              // d^k/dx^k g_sigma(x) at x = c.E
@@ -178,7 +179,8 @@ struct Term {
 };
 
 struct Solution {
-  int N = 0, nv = 0;       // lines (base energies), variables (m internal + 1 external)
+  int N = 0, nv = 0;       // lines (base energies), variables (m internal + n_ext external)
+  int n_ext = 1;           // external frequencies, the last n_ext variables (Sec. 2.3)
   std::vector<Term> terms;
   double prefactor = 1.0;
 };
@@ -313,11 +315,13 @@ int sum_variable(const std::vector<Term>& in, int p, bool p_is_boson,
   return 0;
 }
 
-int construct(int N, int nv, const int* alpha, const int* eps, const int* boson,
+int construct(int N, int nv, int n_ext, const int* alpha, const int* eps, const int* boson,
               const int* order, double prefactor, Solution& S) {
-  if (N < 1 || nv < 2) return fail("bad sizes");
+  if (N < 1 || n_ext < 1 || nv < n_ext + 1) return fail("bad sizes");
+  const int m = nv - n_ext;
   S.N = N;
   S.nv = nv;
+  S.n_ext = n_ext;
   S.prefactor = prefactor;
   std::vector<int> vb(nv, 0);
   if (boson) for (int l = 0; l < nv; ++l) vb[l] = boson[l] ? 1 : 0;
@@ -332,9 +336,9 @@ int construct(int N, int nv, const int* alpha, const int* eps, const int* boson,
     t0.G.push_back(g);
   }
   std::vector<Term> cur{t0}, nxt;
-  for (int s = 0; s < nv - 1; ++s) {
+  for (int s = 0; s < m; ++s) {
     int p = order ? order[s] : s;
-    if (p < 0 || p >= nv - 1) return fail("bad integration order");
+    if (p < 0 || p >= m) return fail("bad integration order");
     if (sum_variable(cur, p, vb[p] != 0, vb, nxt) != 0) return -1;
     cur.swap(nxt);
   }
@@ -400,10 +404,17 @@ double combo(const std::vector<int>& c, const double* E) {
   return x;
 }
 
-cplx den_value(const GFac& g, const double* E, cplx X, int nv) {
-  double eE = combo(g.e, E);
-  double a = g.a[nv - 1];
-  return cplx(std::fma(a, X.real(), eE), a * X.imag());
+// D = sum_q a_{m+q} X_q + e.E for the external frequencies X_0..X_{n_ext-1} of one frequency row
+// (the internal ones are summed away; X = i nu_ext or its continuation omega + i Gamma).
+cplx den_value(const GFac& g, const double* E, const cplx* X, int nv, int n_ext) {
+  const int m = nv - n_ext;
+  double re = combo(g.e, E), im = 0.0;
+  for (int q = 0; q < n_ext; ++q) {
+    double a = g.a[m + q];
+    re = std::fma(a, X[q].real(), re);
+    im += a * X[q].imag();
+  }
+  return cplx(re, im);
 }
 
 struct Neumaier {
@@ -419,7 +430,7 @@ struct Neumaier {
 
 // One sample, one frequency: value, sum |term| and the rounding envelope
 // sum_t |A| prod env(F) prod |G|.
-void eval_one(const Solution& S, const double* E, cplx X, double beta, cplx* val, double* abs_sum,
+void eval_one(const Solution& S, const double* E, const cplx* X, double beta, cplx* val, double* abs_sum,
               double* envelope) {
   Neumaier re, im;
   double as = 0.0, en = 0.0;
@@ -432,7 +443,7 @@ void eval_one(const Solution& S, const double* E, cplx X, double beta, cplx* val
       ft_env *= e;
     }
     cplx r = 1.0;
-    for (const GFac& g : T.G) r *= 1.0 / den_value(g, E, X, S.nv);
+    for (const GFac& g : T.G) r *= 1.0 / den_value(g, E, X, S.nv, S.n_ext);
     cplx term = S.prefactor * ft * r;
     re.add(term.real());
     im.add(term.imag());
@@ -450,8 +461,10 @@ struct Dual {
 };
 Dual dmul(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
 
-void eval_one_dual(const Solution& S, const double* E, const double* dE, cplx X, cplx dX,
+// X, dX: the n_ext external frequencies of the row and their directions.
+void eval_one_dual(const Solution& S, const double* E, const double* dE, const cplx* X, const cplx* dX,
                    double beta, cplx* val, cplx* der, double* der_env) {
+  const int m = S.nv - S.n_ext;
   Neumaier vr, vi, dr, di;
   double env = 0.0;
   for (const Term& T : S.terms) {
@@ -470,15 +483,20 @@ void eval_one_dual(const Solution& S, const double* E, const double* dE, cplx X,
       ev = ev * e0;
     }
     for (const GFac& g : T.G) {
-      cplx D = den_value(g, E, X, S.nv);
+      cplx D = den_value(g, E, X, S.nv, S.n_ext);
       double dEe = 0.0, adEe = 0.0;
       for (size_t j = 0; j < g.e.size(); ++j) { dEe += g.e[j] * dE[j]; adEe += std::fabs(g.e[j] * dE[j]); }
-      double a = (double)g.a[S.nv - 1];
-      cplx dD = dEe + a * dX;
+      cplx dD = dEe;
+      double adX = 0.0;
+      for (int q = 0; q < S.n_ext; ++q) {
+        double a = (double)g.a[m + q];
+        dD += a * dX[q];
+        adX += std::fabs(a) * std::abs(dX[q]);
+      }
       cplx r = 1.0 / D;
       t = dmul(t, Dual{r, -dD * r * r});
       double ar = std::abs(r);
-      ed = ed * ar + ev * (adEe + std::fabs(a) * std::abs(dX)) * ar * ar;
+      ed = ed * ar + ev * (adEe + adX) * ar * ar;
       ev = ev * ar;
     }
     vr.add(t.v.real()); vi.add(t.v.imag());
@@ -520,13 +538,14 @@ void sample_energies(int N, int nv, const int* alpha, const Lattice& L, uint64_t
 }
 
 // ---------------------------------------------------------------------------------------
-// Brute-force truncated Matsubara sum of the starting integrand (Eq. goal):
+// Brute-force truncated Matsubara sum of the starting integrand (Eq. goal) over the m = nv - n_ext
+// internal variables, the n_ext external frequencies held fixed:
 // beta^-m sum over |n_l| window of prod_j 1/(X_j + E_j).  Fermionic nu = (2n+1) pi / beta for
 // n in [-nmax, nmax-1]; bosonic nu = 2 n pi / beta for n in [-nmax, nmax].
 // ---------------------------------------------------------------------------------------
-cplx brute_force(int N, int nv, const int* alpha, const int* eps, const int* boson, const double* E,
-                 cplx X, double beta, int nmax) {
-  int m = nv - 1;
+cplx brute_force(int N, int nv, int n_ext, const int* alpha, const int* eps, const int* boson, const double* E,
+                 const cplx* X, double beta, int nmax) {
+  int m = nv - n_ext;
   std::vector<double> lineE(N, 0.0);
   for (int j = 0; j < N; ++j) {
     if (eps) { for (int k = 0; k < N; ++k) lineE[j] += eps[j * N + k] * E[k]; }
@@ -551,7 +570,8 @@ cplx brute_force(int N, int nv, const int* alpha, const int* eps, const int* bos
         bool b = boson && boson[l];
         w += c * (b ? 2.0 * n[l] * pi / beta : (2.0 * n[l] + 1.0) * pi / beta);
       }
-      cplx xj = cplx(0.0, w) + (double)alpha[j * nv + m] * X;
+      cplx xj = cplx(0.0, w);
+      for (int q = 0; q < n_ext; ++q) xj += (double)alpha[j * nv + m + q] * X[q];
       prod /= (xj + lineE[j]);
     }
     re.add(prod.real());
@@ -764,21 +784,27 @@ double orc_fermi_deriv(int sigma, int k, double beta, double x) {
   return fermi_deriv(sigma, k, beta, x, nullptr);
 }
 
-void* orc_construct(int n_lines, int n_vars, const int* alpha, const int* eps, const int* var_is_boson,
-                    const int* order, double prefactor) {
+// n_ext external variables, the last n_ext columns of alpha; the first n_vars - n_ext are summed.
+void* orc_construct_ext(int n_lines, int n_vars, int n_ext, const int* alpha, const int* eps,
+                        const int* var_is_boson, const int* order, double prefactor) {
   Solution* S = new Solution;
-  if (construct(n_lines, n_vars, alpha, eps, var_is_boson, order, prefactor, *S) != 0) {
+  if (construct(n_lines, n_vars, n_ext, alpha, eps, var_is_boson, order, prefactor, *S) != 0) {
     delete S;
     return nullptr;
   }
   return S;
 }
 
+void* orc_construct(int n_lines, int n_vars, const int* alpha, const int* eps, const int* var_is_boson,
+                    const int* order, double prefactor) {
+  return orc_construct_ext(n_lines, n_vars, 1, alpha, eps, var_is_boson, order, prefactor);
+}
+
 void orc_destroy(void* s) { delete (Solution*)s; }
 
 // info[0] terms, [1] total Fermi factors, [2] total G factors (with powers),
 // [3] max derivative order, [4] max G factors in a term, [5] distinct (c up to sign, sigma)
-// Fermi arguments, [6] distinct (e, a_ext) denominators
+// Fermi arguments, [6] distinct (e, external coefficients) denominators
 void orc_info(const void* sp, int64_t* info) {
   const Solution& S = *(const Solution*)sp;
   int64_t nf = 0, ng = 0, kmax = 0, gmax = 0;
@@ -796,7 +822,7 @@ void orc_info(const void* sp, int64_t* info) {
     }
     for (const GFac& g : T.G) {
       std::vector<int> key = g.e;
-      key.push_back(g.a[S.nv - 1]);
+      for (int q = S.nv - S.n_ext; q < S.nv; ++q) key.push_back(g.a[q]);
       dens.insert(key);
     }
   }
@@ -805,7 +831,7 @@ void orc_info(const void* sp, int64_t* info) {
 }
 
 // Term t: A, and the factor lists.  fc: [nF][N] energy coefficients, fs: sigma, fk: order,
-// ge: [nG][N], ga: [nG] external-frequency coefficient.  Sizes are returned in nF, nG.
+// ge: [nG][N], ga: [nG][n_ext] external-frequency coefficients.  Sizes are returned in nF, nG.
 int orc_term(const void* sp, int64_t t, double* A, int* nF, int* fc, int* fs, int* fk, int* nG,
              int* ge, int* ga, int cap) {
   const Solution& S = *(const Solution*)sp;
@@ -821,23 +847,25 @@ int orc_term(const void* sp, int64_t t, double* A, int* nF, int* fc, int* fs, in
   }
   for (size_t i = 0; i < T.G.size(); ++i) {
     for (int j = 0; j < S.N; ++j) ge[i * S.N + j] = T.G[i].e[j];
-    ga[i] = T.G[i].a[S.nv - 1];
+    for (int q = 0; q < S.n_ext; ++q) ga[i * S.n_ext + q] = T.G[i].a[S.nv - S.n_ext + q];
   }
   return 0;
 }
 
-// Energy input: E [n_e][N] (base energies), X [n_f] complex; out [n_f][n_e] complex,
-// abs_sum and envelope [n_f][n_e] (either may be NULL).
+// Energy input: E [n_e][N] (base energies), X [n_f][n_ext] complex (one row of external
+// frequencies per f); out [n_f][n_e] complex, abs_sum and envelope [n_f][n_e] (either may be NULL).
 int orc_eval_energies(const void* sp, const double* E, int64_t n_e, const double* X_re, const double* X_im,
                       int n_f, double beta, double* out_re, double* out_im, double* abs_sum,
                       double* envelope, int n_threads) {
   const Solution& S = *(const Solution*)sp;
   auto work = [&](int64_t lo, int64_t hi) {
+    std::vector<cplx> Xf(S.n_ext);
     for (int64_t i = lo; i < hi; ++i)
       for (int f = 0; f < n_f; ++f) {
         cplx v;
         double a, e;
-        eval_one(S, E + i * S.N, cplx(X_re[f], X_im[f]), beta, &v, &a, &e);
+        for (int q = 0; q < S.n_ext; ++q) Xf[q] = cplx(X_re[f * S.n_ext + q], X_im[f * S.n_ext + q]);
+        eval_one(S, E + i * S.N, Xf.data(), beta, &v, &a, &e);
         int64_t o = (int64_t)f * n_e + i;
         out_re[o] = v.real(); out_im[o] = v.imag();
         if (abs_sum) abs_sum[o] = a;
@@ -876,6 +904,7 @@ int orc_eval_momenta(const void* sp, const int* alpha, const double* lat, uint64
                      double* per_re, double* per_im, double* envelope, double* mean, double* var,
                      int n_threads) {
   const Solution& S = *(const Solution*)sp;
+  if (S.n_ext != 1) return fail("momentum sampling takes one external momentum (n_ext = 1)");
   Lattice L{lat[0], lat[1], lat[2], lat[3], lat[4]};
   std::vector<double> vr((size_t)n * n_f), vi((size_t)n * n_f);
   auto work = [&](int64_t lo, int64_t hi) {
@@ -885,7 +914,8 @@ int orc_eval_momenta(const void* sp, const int* alpha, const double* lat, uint64
       for (int f = 0; f < n_f; ++f) {
         cplx v;
         double e;
-        eval_one(S, E.data(), cplx(X_re[f], X_im[f]), beta, &v, nullptr, &e);
+        const cplx Xf(X_re[f], X_im[f]);
+        eval_one(S, E.data(), &Xf, beta, &v, nullptr, &e);
         size_t o = (size_t)f * n + i;
         vr[o] = v.real(); vi[o] = v.imag();
         if (envelope) envelope[o] = e;
@@ -924,6 +954,7 @@ int orc_eval_momenta_deriv(const void* sp, const int* alpha, const double* lat, 
                            double beta, int which, double* val_re, double* val_im, double* der_re,
                            double* der_im, double* der_env, int n_threads) {
   const Solution& S = *(const Solution*)sp;
+  if (S.n_ext != 1) return fail("momentum sampling takes one external momentum (n_ext = 1)");
   Lattice L{lat[0], lat[1], lat[2], lat[3], lat[4]};
   int nv = S.nv;
   auto work = [&](int64_t lo, int64_t hi) {
@@ -941,7 +972,8 @@ int orc_eval_momenta_deriv(const void* sp, const int* alpha, const double* lat, 
       for (int f = 0; f < n_f; ++f) {
         cplx v, d;
         double de;
-        eval_one_dual(S, E.data(), dE.data(), cplx(X_re[f], X_im[f]), dX, beta, &v, &d, &de);
+        const cplx Xf(X_re[f], X_im[f]);
+        eval_one_dual(S, E.data(), dE.data(), &Xf, &dX, beta, &v, &d, &de);
         size_t o = (size_t)f * n + i;
         if (val_re) { val_re[o] = v.real(); val_im[o] = v.imag(); }
         der_re[o] = d.real(); der_im[o] = d.imag();
@@ -959,25 +991,33 @@ int orc_eval_momenta_deriv(const void* sp, const int* alpha, const double* lat, 
 }
 
 // Dual-number derivative with energy input: dE [n_e][N] direction for the base energies,
-// dX the frequency direction.
+// X [n_f][n_ext] the frequency rows, dX [n_ext] the direction of the external frequencies
+// (the same for every row).
 int orc_eval_energies_deriv(const void* sp, const double* E, const double* dE, int64_t n_e,
-                            const double* X_re, const double* X_im, double dX_re, double dX_im, int n_f,
-                            double beta, double* der_re, double* der_im) {
+                            const double* X_re, const double* X_im, const double* dX_re, const double* dX_im,
+                            int n_f, double beta, double* der_re, double* der_im) {
   const Solution& S = *(const Solution*)sp;
+  std::vector<cplx> Xf(S.n_ext), dX(S.n_ext);
+  for (int q = 0; q < S.n_ext; ++q) dX[q] = cplx(dX_re[q], dX_im[q]);
   for (int64_t i = 0; i < n_e; ++i)
     for (int f = 0; f < n_f; ++f) {
       cplx v, d;
-      eval_one_dual(S, E + i * S.N, dE + i * S.N, cplx(X_re[f], X_im[f]), cplx(dX_re, dX_im), beta, &v, &d,
-                    nullptr);
+      for (int q = 0; q < S.n_ext; ++q) Xf[q] = cplx(X_re[f * S.n_ext + q], X_im[f * S.n_ext + q]);
+      eval_one_dual(S, E + i * S.N, dE + i * S.N, Xf.data(), dX.data(), beta, &v, &d, nullptr);
       der_re[(size_t)f * n_e + i] = d.real();
       der_im[(size_t)f * n_e + i] = d.imag();
     }
   return 0;
 }
 
-int orc_brute_force(int n_lines, int n_vars, const int* alpha, const int* eps, const int* var_is_boson,
-                    const double* E, double X_re, double X_im, double beta, int nmax, double* out) {
-  cplx v = brute_force(n_lines, n_vars, alpha, eps, var_is_boson, E, cplx(X_re, X_im), beta, nmax);
+// X [n_ext]: the external frequencies (the last n_ext variables); the others are summed.
+int orc_brute_force(int n_lines, int n_vars, int n_ext, const int* alpha, const int* eps,
+                    const int* var_is_boson, const double* E, const double* X_re, const double* X_im,
+                    double beta, int nmax, double* out) {
+  if (n_ext < 1 || n_vars < n_ext + 1) return fail("bad sizes");
+  std::vector<cplx> X(n_ext);
+  for (int q = 0; q < n_ext; ++q) X[q] = cplx(X_re[q], X_im[q]);
+  cplx v = brute_force(n_lines, n_vars, n_ext, alpha, eps, var_is_boson, E, X.data(), beta, nmax);
   out[0] = v.real();
   out[1] = v.imag();
   return 0;
