@@ -357,8 +357,9 @@ def run_tami(args):
 def run_workload(args):
     """The other configurations of the method, timed on one GPU (parity for each is in tests/):
     order5 (forward + adjoint at four temperatures), order3_real (forward + adjoint on the real
-    axis), all_orders (every order-2..5 diagram in one persistent graph launch, forward) and
-    energy_x1 (the paper's energy-input example).  Prints one JSON line; not the headline metric."""
+    axis), all_orders (every order-2..5 diagram in one persistent graph launch, forward),
+    energy_x1 (the paper's energy-input example) and two_freq_x1 (two external frequencies per
+    frequency row, energy input).  Prints one JSON line; not the headline metric."""
     import torch
     import paper_2311_17189_gb300 as T
 
@@ -433,10 +434,30 @@ def run_workload(args):
             D.eval_energies(E, X, c["beta"])
         launches_per_step = 1
         evals = float(c["n_e"]) * info["n_terms"] * n_f
-        flops = c["n_e"] * (info["flops_per_sample"] + n_f * info["flops_per_sample_freq"])
+        flops = c["n_e"] * (info["energy_in_flops_per_sample"] + n_f * info["flops_per_sample_freq"])
         bytes_step = c["n_e"] * (8 * c["alpha"].shape[0] + 16 * n_f)
         config = {"workload": c["name"], "rows": c["n_e"], "frequencies": n_f, "terms": info["n_terms"],
                   "beta": c["beta"], "step": "tami_eval_energies, full [n_f][n_e] output"}
+    elif wl == "two_freq_x1":
+        c = W.TWO_FREQ_X1
+        d = next(x for x in T.enumerate_sigma(c["order"]) if x["code"] == tuple(c["code"]))
+        alpha = W.hold_external(d["alpha"], c["held"])
+        D = T.Diagram(alpha, eps=d["eps"], n_ext=2).upload(0)
+        info = D.info()
+        N = alpha.shape[0]
+        E = torch.as_tensor(W.random_energies(c["n_e"], N, a=c["a"], seed=c["seed"]), device=dev)
+        X = torch.as_tensor(W.matsubara_grid(c["beta"], c["n_grid"], c["n_grid"]), dtype=torch.complex128, device=dev)
+        n_f = X.shape[0]
+
+        def step(i):
+            D.eval_energies(E, X, c["beta"])
+        launches_per_step = 1
+        evals = float(c["n_e"]) * info["n_terms"] * n_f
+        flops = c["n_e"] * (info["energy_in_flops_per_sample"] + n_f * info["flops_per_sample_freq"])
+        bytes_step = c["n_e"] * (8 * N + 16 * n_f) + n_f * 32
+        config = {"workload": c["name"], "rows": c["n_e"], "frequency_rows": n_f, "externals": 2,
+                  "terms": info["n_terms"], "beta": c["beta"],
+                  "step": "tami_eval_energies, full [n_f][n_e] output"}
     else:
         raise SystemExit(f"unknown workload {wl}")
     for i in range(args.warmup):
@@ -481,7 +502,7 @@ def main():
     p.add_argument("--ref-samples", type=int, default=1 << 12)
     p.add_argument("--samples", type=int, default=CFG["n_samples"], help="samples per GPU (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="order4", choices=["order4", "order5", "order3_real", "all_orders", "energy_x1"],
+    p.add_argument("--workload", default="order4", choices=["order4", "order5", "order3_real", "all_orders", "energy_x1", "two_freq_x1"],
                    help="order4 is the headline metric; the others time the remaining configurations on one GPU")
     args = p.parse_args()
     if args.impl == "reference":

@@ -17,8 +17,12 @@
  *     outputs are valid once the stream is synchronised.
  *   - A diagram is library-owned: created by tami_construct, freed by tami_destroy.  Its device
  *     term table is created by tami_upload and freed by tami_destroy.
- *   - Variables: n_vars = m + 1 frequency/momentum labels, the m internal (summed) ones first and
- *     the external one last (Sec. 2.3, "external frequency(s) are the last elements").
+ *   - Variables: n_vars = m + n_ext frequency/momentum labels, the m internal (summed) ones first
+ *     and the n_ext external ones last (Sec. 2.3: a frequency_t row holds m + n_nu entries, "the
+ *     external frequency(s) are the last elements").  tami_construct has n_ext = 1; the momentum
+ *     calls (tami_sample_energies, tami_forward*, tami_backward, tami_batch_plan) need n_ext = 1,
+ *     since the momentum integrand of Sec. 5.2 appends one external momentum, and refuse others
+ *     with TAMI_EUNSUPPORTED; energy input (tami_eval_energies) takes any n_ext.
  *   - Lines: n_lines = N Green's functions G_j = 1/(X_j + E_j) (Eq. Green_Function) with
  *     X_j = sum_l i alpha_jl nu_l and E_j = sum_k eps_jk E_k (base energies E_k).
  */
@@ -44,7 +48,7 @@ enum {
   TAMI_EUNSUPPORTED = 5  /* valid input outside what the library handles (see message)   */
 };
 
-enum { TAMI_MAX_LINES = 16, TAMI_MAX_VARS = 8 };
+enum { TAMI_MAX_LINES = 16, TAMI_MAX_VARS = 8, TAMI_MAX_EXT = 4 };
 
 typedef struct tami_diagram tami_diagram;
 
@@ -89,6 +93,10 @@ typedef struct {
   double bwd_saved_flops_per_sample;
   /* per (sample, frequency) flops of tami_forward_backward (per sample: bwd_flops_per_sample) */
   double fused_flops_per_sample_freq;
+  int n_ext;                /* external variables (the last n_ext of the n_vars labels)       */
+  /* per-row flops of tami_eval_energies (flops_per_sample without the momentum sampling and the
+   * dispersion; per (row, frequency): flops_per_sample_freq) */
+  double energy_in_flops_per_sample;
 } tami_info;
 
 const char* tami_last_error(void);
@@ -108,6 +116,16 @@ const char* tami_last_error(void);
 int tami_construct(int n_lines, int n_vars, const int8_t* alpha, const int8_t* eps,
                    const uint8_t* var_is_boson, const int32_t* order, double prefactor,
                    tami_diagram** out);
+
+/* tami_construct with n_ext external frequencies (Sec. 2.3: n_nu external frequencies, the last
+ * n_nu of the m + n_nu labels): the first m = n_vars - n_ext variables are summed, the last n_ext
+ * stay free; a denominator then carries sum_q a_q X_q.  var_is_boson covers the externals too (a
+ * Fermi/Bose factor whose pole carries an odd number of fermionic frequencies, external ones
+ * included, turns f into -n_B and back).  order: host int32 [m] or NULL.
+ * Errors: those of tami_construct; TAMI_EINVAL unless 1 <= n_ext <= TAMI_MAX_EXT and n_ext < n_vars. */
+int tami_construct_ext(int n_lines, int n_vars, int n_ext, const int8_t* alpha, const int8_t* eps,
+                       const uint8_t* var_is_boson, const int32_t* order, double prefactor,
+                       tami_diagram** out);
 
 /* Momentum labels of a self-energy graph (Sec. 2.5: label_graph and graph_to_R0 on the 4-column
  * "source target B/F spin" format).
@@ -149,10 +167,11 @@ int tami_sample_energies(const tami_diagram* d, const tami_lattice* lat, uint64_
  * uploaded to another device than the current one.  The library stays usable after an error. */
 
 /* Energy-input evaluation (Sec. 2.3, energy_t / frequency_t): for each configuration i and
- * external frequency f, the sum over terms of A * FT(E_i) * R(E_i, X_f).
+ * external frequency row f, the sum over terms of A * FT(E_i) * R(E_i, X_f).
  *   E    device double [n_e][n_lines] base energies.
- *   X    device double [n_f][2] external frequencies (i nu_n, or omega + i Gamma after analytic
- *        continuation).
+ *   X    device double [n_f][n_ext][2]: row f holds the diagram's n_ext external frequencies
+ *        (i nu_n, or omega + i Gamma after analytic continuation), in label order; n_ext = 1 is
+ *        [n_f][2].
  *   out  device double [n_f][n_e][2] (rows are frequencies, Sec. 2.3).
  * n_e = 0 launches nothing (E and out may then be NULL). */
 int tami_eval_energies(const tami_diagram* d, const double* E, int64_t n_e, const double* X, int n_f,

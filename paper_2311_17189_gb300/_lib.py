@@ -16,7 +16,7 @@ TAMI_OK, TAMI_EINVAL, TAMI_ENOMEM, TAMI_ECUDA, TAMI_ETIMEOUT, TAMI_EUNSUPPORTED 
 
 # functions declared in include/tami.h (checked by tests/test_lib_host.py)
 EXPORTS = [
-    "tami_last_error", "tami_construct", "tami_label_graph", "tami_construct_from_graph", "tami_diagram_info", "tami_upload", "tami_sample_energies",
+    "tami_last_error", "tami_construct", "tami_construct_ext", "tami_label_graph", "tami_construct_from_graph", "tami_diagram_info", "tami_upload", "tami_sample_energies",
     "tami_eval_energies", "tami_forward_workspace", "tami_forward", "tami_forward_noalloc",
     "tami_backward_workspace", "tami_backward", "tami_forward_backward_workspace", "tami_forward_backward",
     "tami_batch_plan", "tami_batch_info", "tami_batch_launch",
@@ -51,6 +51,8 @@ class Info(ctypes.Structure):
         ("saved_rows", ctypes.c_int),
         ("fwd_save_flops_per_sample", ctypes.c_double), ("bwd_saved_flops_per_sample", ctypes.c_double),
         ("fused_flops_per_sample_freq", ctypes.c_double),
+        ("n_ext", ctypes.c_int),
+        ("energy_in_flops_per_sample", ctypes.c_double),
     ]
 
 
@@ -67,6 +69,8 @@ def lib():
     vp, i64, u64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
     L.tami_last_error.restype = ctypes.c_char_p
     L.tami_construct.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, ctypes.c_double, ctypes.POINTER(vp)]
+    L.tami_construct_ext.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, ctypes.c_double,
+                                     ctypes.POINTER(vp)]
     L.tami_label_graph.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.tami_construct_from_graph.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(vp)]

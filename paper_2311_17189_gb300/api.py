@@ -30,29 +30,34 @@ def _stream_ptr():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _as_c_pairs(X, device):
-    """complex [n_f] -> contiguous float64 [n_f, 2] on `device`."""
+def _as_c_pairs(X, device, n_ext=1):
+    """complex [n_f] (or [n_f, n_ext]: one row of external frequencies per f) -> contiguous
+    float64 [n_f, 2] ([n_f, n_ext, 2]) on `device`."""
     torch = _torch()
     X = torch.as_tensor(X)
     if not torch.is_complex(X):
         X = X.to(torch.complex128)
-    X = X.to(device=device, dtype=torch.complex128).reshape(-1)
+    X = X.to(device=device, dtype=torch.complex128).reshape(-1) if n_ext == 1 else \
+        X.to(device=device, dtype=torch.complex128).reshape(-1, n_ext)
     return torch.view_as_real(X).contiguous()
 
 
 class Diagram:
-    """An AMI solution (flat terms A * FT * R, Sec. 2.2) and its device term table."""
+    """An AMI solution (flat terms A * FT * R, Sec. 2.2) and its device term table.  The last
+    n_ext columns of alpha are external variables (Sec. 2.3); the others are summed.  Momentum
+    sampling (forward, backward, batches) takes n_ext = 1; eval_energies any n_ext."""
 
-    def __init__(self, alpha, eps=None, var_is_boson=None, order=None, prefactor=1.0):
+    def __init__(self, alpha, eps=None, var_is_boson=None, order=None, prefactor=1.0, n_ext=1):
         a = np.ascontiguousarray(np.asarray(alpha, dtype=np.int8))
         self.alpha = a
         self.n_lines, self.n_vars = a.shape
+        self.n_ext = int(n_ext)
         e = None if eps is None else np.ascontiguousarray(np.asarray(eps, dtype=np.int8))
         b = None if var_is_boson is None else np.ascontiguousarray(np.asarray(var_is_boson, dtype=np.uint8))
         o = None if order is None else np.ascontiguousarray(np.asarray(order, dtype=np.int32))
         h = ctypes.c_void_p()
-        L.check(L.lib().tami_construct(self.n_lines, self.n_vars, L._np_ptr(a), L._np_ptr(e), L._np_ptr(b),
-                                       L._np_ptr(o), float(prefactor), ctypes.byref(h)))
+        L.check(L.lib().tami_construct_ext(self.n_lines, self.n_vars, self.n_ext, L._np_ptr(a), L._np_ptr(e),
+                                           L._np_ptr(b), L._np_ptr(o), float(prefactor), ctypes.byref(h)))
         self._h = h
         self.device = None
         self._ws = None
@@ -94,10 +99,11 @@ class Diagram:
         return E
 
     def eval_energies(self, E, X, beta):
-        """E: float64 [n_e, n_lines] CUDA tensor; X: complex [n_f].  Returns complex128 [n_f, n_e]."""
+        """E: float64 [n_e, n_lines] CUDA tensor; X: complex [n_f] (n_ext = 1) or [n_f, n_ext] (row f:
+        the external frequencies in label order).  Returns complex128 [n_f, n_e]."""
         torch = _torch()
         E = E.to(dtype=torch.float64).contiguous()
-        Xp = _as_c_pairs(X, E.device)
+        Xp = _as_c_pairs(X, E.device, self.n_ext)
         n_e, n_f = E.shape[0], Xp.shape[0]
         out = torch.empty((n_f, n_e, 2), dtype=torch.float64, device=E.device)
         with _nvtx("tami_eval_energies"):

@@ -412,6 +412,11 @@ int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* sampl
   b->n_f = n_f;
   for (int d = 0; d < n_d; ++d) {
     if (!ds[d] || samples[d] < 1) { delete b; set_error("NULL diagram or empty sample count"); return TAMI_EINVAL; }
+    if (ds[d]->n_ext != 1) {
+      delete b;
+      set_error("momentum sampling takes one external frequency and momentum (n_ext = 1)");
+      return TAMI_EUNSUPPORTED;
+    }
     b->ds.push_back(ds[d]);
     b->n.push_back(samples[d]);
     b->seeds.push_back(seeds[d]);

@@ -489,6 +489,7 @@ int bwd_check(const tami_diagram* d, int n_f) {
   cudaGetDevice(&cur);
   if (cur != d->device) { set_error("current device differs from the upload device"); return TAMI_EINVAL; }
   const TableHeader& h = d->hdr;
+  if (h.n_ext != 1) { set_error("momentum sampling takes one external frequency and momentum (n_ext = 1)"); return TAMI_EUNSUPPORTED; }
   if (h.max_der > 4) { set_error("the adjoint needs derivative orders up to 4"); return TAMI_EUNSUPPORTED; }
   if (h.n_combo > kBwCombos || h.n_fv > kBwFv || h.n_rden > kBwRden || h.n_cden > kBwCden ||
       h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || h.n_nodes > kBwNodes || h.n_g2cd > kBwG2cd) {

@@ -37,7 +37,7 @@ struct FwdParams {
   unsigned long long seed, offset;
   long long n;
   const double* E_in;           // energy input [n][N] or null
-  const double* X;              // [n_f][2]
+  const double* X;              // [n_f][n_ext][2]
   int n_f;
   double beta;
   double* per_sample;           // [n_f][n][2] or null
@@ -47,10 +47,11 @@ struct FwdParams {
 };
 
 
-// Shared memory: table | X [n_f][2] | AXI, AXI2 [n_cden][n_f] | CB [n_cden][S] | W [n_g2][S] | red [4][S]
+// Shared memory: table | Xs [n_xk][n_f][2] | AXI, AXI2 [n_cden][n_f] | CB [n_cden][S] | W [n_g2][S] |
+// red [4][S]
 __host__ __device__ __forceinline__ size_t fwd_smem_bytes(const TableHeader& h, int n_f) {
   return (size_t)align16(h.bytes) +
-         sizeof(double) * ((2 + 2 * (size_t)h.n_cden) * n_f + (size_t)(h.n_cden + h.n_g2 + 4) * kBlock);
+         sizeof(double) * ((2 * (size_t)h.n_xk + 2 * (size_t)h.n_cden) * n_f + (size_t)(h.n_cden + h.n_g2 + 4) * kBlock);
 }
 
 template <bool ENERGY_IN, bool SAVE>
@@ -60,13 +61,13 @@ __global__ void __launch_bounds__(kBlock) fwd_kernel(const FwdParams P) {
   const int tid = threadIdx.x;
   if (!stage_table(smem, P.table, H.bytes, P.status)) return;
   double* Xs = reinterpret_cast<double*>(smem + align16(H.bytes));
-  double* AXI = Xs + 2 * P.n_f;
+  double* AXI = Xs + 2 * H.n_xk * P.n_f;
   double* AXI2 = AXI + H.n_cden * P.n_f;
   double* CB = AXI2 + H.n_cden * P.n_f;
   double* W = CB + H.n_cden * kBlock;
   double* red = W + H.n_g2 * kBlock;
-  for (int i = tid; i < 2 * P.n_f; i += kBlock) Xs[i] = P.X[i];
   const TableView T = table_view(smem, H);
+  stage_freqs(H, T, P.X, P.n_f, Xs);
   const FreqMap M = freq_map(P.n_f, tid);
   double acc[kMaxFreqPerThread][4];
   for (int i = 0; i < kMaxFreqPerThread; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0;
@@ -180,6 +181,16 @@ int grid_for(const tami_diagram* d, int n_f, long long n) {
   return (int)grid;
 }
 
+// Momentum sampling (Sec. 5.2) appends one external momentum to the sampled ones: the calls
+// that sample momenta take diagrams with one external variable only.
+int check_momentum(const tami_diagram* d) {
+  if (d && d->n_ext != 1) {
+    set_error("momentum sampling takes one external frequency and momentum (n_ext = 1)");
+    return TAMI_EUNSUPPORTED;
+  }
+  return TAMI_OK;
+}
+
 int check_common(const tami_diagram* d, int n_f) {
   if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
   if (!d->d_blob) { set_error("diagram not uploaded (call tami_upload)"); return TAMI_EINVAL; }
@@ -268,6 +279,7 @@ int tami_upload(tami_diagram* d, int device, tami_stream_t stream) {
 int tami_sample_energies(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
                          int64_t n, double* E, tami_stream_t stream) {
   int rc = check_common(d, 1);
+  if (!rc) rc = check_momentum(d);
   if (rc) return rc;
   if (!lat || !E || n < 0) { set_error("bad argument"); return TAMI_EINVAL; }
   if (n == 0) return TAMI_OK;
@@ -310,6 +322,7 @@ int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, 
                  double* per_sample, double* saved, void* workspace, size_t workspace_bytes,
                  tami_stream_t stream) {
   int rc = check_common(d, n_f);
+  if (!rc) rc = check_momentum(d);
   if (rc) return rc;
   if (!lat || !X || !mean || !workspace || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
   if (!beta_ok(beta)) return TAMI_EINVAL;
@@ -344,6 +357,7 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
                          int64_t n_samples, const double* X, int n_f, double beta, double* mean, double* var,
                          double* per_sample, tami_stream_t stream) {
   int rc = check_common(d, n_f);
+  if (!rc) rc = check_momentum(d);
   if (rc) return rc;
   if (!lat || !X || !mean || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
   if (!beta_ok(beta)) return TAMI_EINVAL;

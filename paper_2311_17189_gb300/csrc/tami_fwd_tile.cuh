@@ -24,6 +24,8 @@ struct TableView {
   const int* rden;
   const int* cden;
   const double* cden_a;
+  const int* cden_xk;
+  const double* xvec;
   const int* g1;
   const int* g1_tgt;
   const int2* ops;
@@ -49,6 +51,8 @@ __device__ __forceinline__ TableView table_view(const unsigned char* t, const Ta
   v.rden = reinterpret_cast<const int*>(t + H.off_rden);
   v.cden = reinterpret_cast<const int*>(t + H.off_cden);
   v.cden_a = reinterpret_cast<const double*>(t + H.off_cden_a);
+  v.cden_xk = reinterpret_cast<const int*>(t + H.off_cden_xk);
+  v.xvec = reinterpret_cast<const double*>(t + H.off_xvec);
   v.g1 = reinterpret_cast<const int*>(t + H.off_g1);
   v.g1_tgt = reinterpret_cast<const int*>(t + H.off_g1_tgt);
   v.ops = reinterpret_cast<const int2*>(t + H.off_ops);
@@ -117,19 +121,43 @@ struct TileArgs {
   int n_f;
 };
 
-// Per-(denominator, frequency) constants of phase 2: AXI = a_c Im X_f and AXI2 = AXI^2, in shared
-// memory [n_cden][n_f] each.  Returns whether every Re X_f is zero (then Re D = b exactly).
+// The external frequencies as the denominators see them: Y_kf = sum_q v_kq X_fq for every
+// external-coefficient vector v_k of the table and frequency row f (X: [n_f][n_ext][2]), into
+// Xs [n_xk][n_f][2].  A complex denominator c is then D = g_c Y_{k_c f} + b.  With one external
+// (v_0 = (1)) this is a copy.  No barrier.
+__device__ __forceinline__ void stage_freqs(const TableHeader& H, const TableView& T, const double* X, int n_f,
+                                            double* Xs) {
+  if (H.n_ext == 1) {
+    for (int i = threadIdx.x; i < 2 * n_f; i += kBlock) Xs[i] = X[i];
+    return;
+  }
+  for (int i = threadIdx.x; i < H.n_xk * n_f; i += kBlock) {
+    const int k = i / n_f, f = i % n_f;
+    const double* v = T.xvec + k * H.n_ext;
+    const double* x = X + 2 * (size_t)f * H.n_ext;
+    double re = v[0] * x[0], im = v[0] * x[1];
+    for (int q = 1; q < H.n_ext; ++q) {
+      re = fma(v[q], x[2 * q], re);
+      im = fma(v[q], x[2 * q + 1], im);
+    }
+    Xs[2 * i] = re;
+    Xs[2 * i + 1] = im;
+  }
+}
+
+// Per-(denominator, frequency) constants of phase 2: AXI = g_c Im Y_{k_c f} and AXI2 = AXI^2, in
+// shared memory [n_cden][n_f] each.  Returns whether every Re Y is zero (then Re D = b exactly).
 // Ends with a barrier.
 __device__ __forceinline__ bool freq_constants(const TableHeader& H, const TableView& T, const double* Xs, int n_f,
                                                double* AXI, double* AXI2) {
   int nonzero = 0;
   for (int i = threadIdx.x; i < H.n_cden * n_f; i += kBlock) {
     const int c = i / n_f, f = i % n_f;
-    const double a = T.cden_a[c] * Xs[2 * f + 1];
+    const double a = T.cden_a[c] * Xs[2 * (T.cden_xk[c] * n_f + f) + 1];
     AXI[i] = a;
     AXI2[i] = a * a;
   }
-  for (int f = threadIdx.x; f < n_f; f += kBlock) nonzero |= Xs[2 * f] != 0.0;
+  for (int i = threadIdx.x; i < H.n_xk * n_f; i += kBlock) nonzero |= Xs[2 * i] != 0.0;
   return !__syncthreads_or(nonzero);
 }
 
@@ -141,13 +169,14 @@ __device__ __forceinline__ bool freq_constants(const TableHeader& H, const Table
 // first (g2_const).
 template <bool XR_ZERO>
 __device__ __forceinline__ void phase2_sample(const TableHeader& H, const TableView& T, const TileArgs& A, int sl,
-                                              int f, double Xr, const double* AXI, const double* AXI2,
+                                              int f, const double* Xs, const double* AXI, const double* AXI2,
                                               const double* CB, const double* W, double& vr_out, double& vi_out) {
   // values: [0, n_cden) the reciprocals 1/D_c, then the product nodes
   double vre[kMaxCplxDens + kMaxProdNodes], vim[kMaxCplxDens + kMaxProdNodes];
   for (int c = 0; c < H.n_cden; ++c) {
     const double b = CB[c * kBlock + sl];
-    const double Dr = XR_ZERO ? b : fma(T.cden_a[c], Xr, b);    // D = a X + b
+    // D = g_c Y_{k_c f} + b
+    const double Dr = XR_ZERO ? b : fma(T.cden_a[c], Xs[2 * (T.cden_xk[c] * A.n_f + f)], b);
     const double r = rcp(fma(Dr, Dr, AXI2[c * A.n_f + f]));
     vre[c] = Dr * r;
     vim[c] = -AXI[c * A.n_f + f] * r;
@@ -186,7 +215,7 @@ __device__ __forceinline__ void phase2_store(const TileArgs& A, int f, long long
   acc[3] = fma(vi, vi, acc[3]);
 }
 
-// Shared memory per tile: X [n_f][2] (filled by the caller), AXI and AXI2 [n_cden][n_f] (from
+// Shared memory per tile: Xs [n_xk][n_f][2] (from stage_freqs), AXI and AXI2 [n_cden][n_f] (from
 // freq_constants), CB [n_cden][kBlock], W [n_g2][kBlock].
 template <bool ENERGY_IN, bool SAVE>
 __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& T, const TileArgs& A,
@@ -287,18 +316,17 @@ __device__ __forceinline__ void phase2_loop(const TableHeader& H, const TableVie
                                             const double* W, const FreqMap& M, double (*acc)[4]) {
   for (int fi = 0; fi < M.nf; ++fi) {
     const int f = M.f0 + fi * M.fstep;
-    const double Xr = Xs[2 * f];
     int sl = M.s0;
     for (; sl + M.sstep < kBlock && s0 + sl + M.sstep < A.n; sl += 2 * M.sstep) {
       double ar, ai, br, bi;
-      phase2_sample<XR_ZERO>(H, T, A, sl, f, Xr, AXI, AXI2, CB, W, ar, ai);
-      phase2_sample<XR_ZERO>(H, T, A, sl + M.sstep, f, Xr, AXI, AXI2, CB, W, br, bi);
+      phase2_sample<XR_ZERO>(H, T, A, sl, f, Xs, AXI, AXI2, CB, W, ar, ai);
+      phase2_sample<XR_ZERO>(H, T, A, sl + M.sstep, f, Xs, AXI, AXI2, CB, W, br, bi);
       phase2_store(A, f, s0 + sl, ar, ai, acc[fi]);
       phase2_store(A, f, s0 + sl + M.sstep, br, bi, acc[fi]);
     }
     for (; sl < kBlock && s0 + sl < A.n; sl += M.sstep) {
       double ar, ai;
-      phase2_sample<XR_ZERO>(H, T, A, sl, f, Xr, AXI, AXI2, CB, W, ar, ai);
+      phase2_sample<XR_ZERO>(H, T, A, sl, f, Xs, AXI, AXI2, CB, W, ar, ai);
       phase2_store(A, f, s0 + sl, ar, ai, acc[fi]);
     }
   }

@@ -191,7 +191,7 @@ struct Blob {
 }  // namespace
 
 int flatten(tami_diagram* d) {
-  const int N = d->N, nv = d->nv;
+  const int N = d->N, nv = d->nv, n_ext = d->n_ext, m = nv - n_ext;
   // ---- energy combinations (sign-canonical), Fermi values, denominators
   std::map<Vec, int> combo_id;
   std::vector<Vec> combos;
@@ -209,8 +209,15 @@ int flatten(tami_diagram* d) {
   struct FvKey { int u, sigma, sign, k; bool operator<(const FvKey& o) const {
       return std::tie(u, sigma, sign, k) < std::tie(o.u, o.sigma, o.sign, o.k); } };
   std::map<FvKey, int> fv_tmp;   // provisional ids, renumbered by base below
-  struct CdKey { int u, sign, a; bool operator<(const CdKey& o) const {
-      return std::tie(u, sign, a) < std::tie(o.u, o.sign, o.a); } };
+  // A complex denominator D = sum_q a_q X_q + s * (combination u).E; its external coefficients
+  // are g * v_k with v_k one of the table's vectors: for one external v_0 = (1) and g = a_0, for
+  // several g = 1 and v_k = a.
+  struct CdKey { int u, sign, a, xk; bool operator<(const CdKey& o) const {
+      return std::tie(u, sign, a, xk) < std::tie(o.u, o.sign, o.a, o.xk); } };
+  using ExtVec = std::array<int8_t, kMaxExt>;
+  std::map<ExtVec, int> xvec_id;
+  std::vector<ExtVec> xvecs;
+  if (n_ext == 1) { ExtVec one{}; one[0] = 1; xvec_id[one] = 0; xvecs.push_back(one); }
   std::map<int, int> rden_id;
   std::vector<int> rdens;
   std::map<CdKey, int> cden_id;
@@ -225,7 +232,7 @@ int flatten(tami_diagram* d) {
   int64_t nF = 0, nG = 0;
   int max_der = 0, max_g = 0;
   std::set<std::pair<Vec, int>> upoles;
-  std::set<std::pair<Vec, int>> udens;
+  std::set<std::pair<Vec, ExtVec>> udens;
   for (const SymTerm& T : d->terms) {
     FlatTerm t;
     t.A = T.A * d->prefactor;
@@ -245,23 +252,36 @@ int flatten(tami_diagram* d) {
       int q = gq.second;
       gcount += q;
       nG += q;
-      int a = g.a[nv - 1];
+      ExtVec av{};
+      int a_first = 0;
+      for (int q2 = 0; q2 < n_ext; ++q2) {
+        av[q2] = g.a[m + q2];
+        if (!a_first) a_first = av[q2];
+      }
       Vec e = g.e;
-      udens.insert({e, a});
-      int dsign = a ? (a > 0 ? 1 : -1) : first_sign(e);
+      udens.insert({e, av});
+      // canonical sign: first external coefficient > 0, else first energy coefficient > 0
+      int dsign = a_first ? (a_first > 0 ? 1 : -1) : first_sign(e);
       if (dsign < 0 && (q & 1)) t.A = -t.A;     // 1/(-D)^q = (-1)^q / D^q
       e = scaled(e, dsign);
-      a *= dsign;
+      for (int q2 = 0; q2 < n_ext; ++q2) av[q2] = (int8_t)(dsign * av[q2]);
       int s;
       int u = combo(e, &s);
-      if (a == 0) {
+      if (a_first == 0) {
         auto it = rden_id.find(u);
         int id;
         if (it == rden_id.end()) { id = (int)rdens.size(); rden_id[u] = id; rdens.push_back(u); }
         else id = it->second;
         t.rd.push_back({id, q});
       } else {
-        CdKey key{u, s, a};
+        int a = 1, xk = 0;
+        if (n_ext == 1) a = av[0];
+        else {
+          auto xi = xvec_id.find(av);
+          if (xi == xvec_id.end()) { xk = (int)xvecs.size(); xvec_id[av] = xk; xvecs.push_back(av); }
+          else xk = xi->second;
+        }
+        CdKey key{u, s, a, xk};
         auto it = cden_id.find(key);
         int id;
         if (it == cden_id.end()) { id = (int)cdens.size(); cden_id[key] = id; cdens.push_back(key); }
@@ -380,12 +400,16 @@ int flatten(tami_diagram* d) {
   std::sort(repl.begin(), repl.end());
   // lines carrying k_ext first: only their energies depend on k_ext (the adjoint needs sin there)
   const int n_rep_ext = (int)(std::stable_partition(repl.begin(), repl.end(), [&](int j) {
-                                return d->alpha[j * nv + nv - 1] != 0; }) - repl.begin());
+                                for (int l = m; l < nv; ++l) if (d->alpha[j * nv + l]) return true;
+                                return false; }) - repl.begin());
 
   // ---- blob
   TableHeader& h = d->hdr;
   h = TableHeader{};
-  h.N = N; h.nv = nv; h.m = nv - 1;
+  h.N = N; h.nv = nv; h.m = m;
+  h.n_ext = n_ext;
+  if (xvecs.empty()) { ExtVec e0{}; e0[0] = 1; xvecs.push_back(e0); }   // no complex denominator
+  h.n_xk = (int)xvecs.size();
   h.n_rep = (int)repl.size();
   h.n_rep_ext = n_rep_ext;
   h.n_combo = (int)combos.size();
@@ -413,7 +437,7 @@ int flatten(tami_diagram* d) {
   std::vector<std::pair<int, int>> g1_ops(g1s.size());
   std::vector<int> g1_node(g1s.size() + 1, 0);
   int n_inner = 0, max_slots = 0, node_base = 0;
-  const int m_depth = nv - 1;
+  const int m_depth = m;
   struct Node { int fv; std::vector<int> kids; double A; };
   auto build_tree = [&](const std::vector<int>& terms, bool greedy) {
     std::vector<Node> nodes(1, Node{-1, {}, 0.0});
@@ -566,6 +590,8 @@ int flatten(tami_diagram* d) {
   h.off_rden = B.reserve(sizeof(int) * 2 * h.n_rden);
   h.off_cden = B.reserve(sizeof(int) * 2 * h.n_cden);
   h.off_cden_a = B.reserve(sizeof(double) * h.n_cden);
+  h.off_cden_xk = B.reserve(sizeof(int) * h.n_cden);
+  h.off_xvec = B.reserve(sizeof(double) * h.n_xk * n_ext);
   h.off_g1 = B.reserve(sizeof(int) * 4 * h.n_g1);
   h.off_g1_tgt = B.reserve(sizeof(int) * h.n_g1);
   h.off_ops = B.reserve(sizeof(int) * 2 * h.n_ops);
@@ -594,7 +620,7 @@ int flatten(tami_diagram* d) {
           B.at<double>(h.off_lm_c)[q] = (double)d->alpha[j * nv + l];
           ++q;
         }
-      B.at<double>(h.off_rep_aext)[r] = (double)d->alpha[j * nv + nv - 1];
+      B.at<double>(h.off_rep_aext)[r] = (double)d->alpha[j * nv + m];
     }
     B.at<int>(h.off_lm_ptr)[h.n_rep] = q;
   }
@@ -627,7 +653,10 @@ int flatten(tami_diagram* d) {
     int* r = B.at<int>(h.off_cden) + 2 * i;
     r[0] = cdens[i].u; r[1] = cdens[i].sign;
     B.at<double>(h.off_cden_a)[i] = (double)cdens[i].a;
+    B.at<int>(h.off_cden_xk)[i] = cdens[i].xk;
   }
+  for (int k = 0; k < h.n_xk; ++k)
+    for (int q = 0; q < n_ext; ++q) B.at<double>(h.off_xvec)[k * n_ext + q] = (double)xvecs[k][q];
   for (int o = 0; o < h.n_ops; ++o) {
     B.at<int>(h.off_ops)[2 * o] = ops[o].first;
     B.at<int>(h.off_ops)[2 * o + 1] = ops[o].second;
@@ -692,7 +721,7 @@ int flatten(tami_diagram* d) {
   I.n_groups_fixed = h.n_g1; I.n_groups_freq = h.n_g2;
   I.table_bytes = h.bytes;
   I.saved_rows = h.n_rep + 2 * h.n_rep_ext;
-  const int m = nv - 1;
+  I.n_ext = n_ext;
   // Counts follow the kernel: fma = 2 flops, mul/add = 1, the reciprocal (estimate + one
   // third-order Newton step) = 3 fma, the table-driven exponential 10 fma + 3 add/mul.
   double fl = 0.0;
@@ -717,6 +746,7 @@ int flatten(tami_diagram* d) {
     fl += 1.0;
   }
   I.flops_per_sample = fl;
+  I.energy_in_flops_per_sample = fl - energy_flops;
   double ff = 12.0 * h.n_cden;                          // |D|^2, reciprocal, 1/D (+ Re D off the imaginary axis)
   ff += 6.0 * h.n_pnode;                                // complex product per trie node
   for (auto& g : g2s) ff += g.empty() ? 1.0 : 4.0;      // W R accumulated
@@ -898,21 +928,27 @@ extern "C" {
 
 const char* tami_last_error(void) { return g_last_error.c_str(); }
 
-int tami_construct(int n_lines, int n_vars, const int8_t* alpha, const int8_t* eps,
-                   const uint8_t* var_is_boson, const int32_t* order, double prefactor,
-                   tami_diagram** out) {
+int tami_construct_ext(int n_lines, int n_vars, int n_ext, const int8_t* alpha, const int8_t* eps,
+                       const uint8_t* var_is_boson, const int32_t* order, double prefactor,
+                       tami_diagram** out) {
   if (!out || !alpha) { set_error("NULL argument"); return TAMI_EINVAL; }
   *out = nullptr;
   if (n_lines < 1 || n_lines > kMaxLines || n_vars < 2 || n_vars > kMaxVars) {
     set_error("n_lines must be in [1,16] and n_vars in [2,8]");
     return TAMI_EINVAL;
   }
+  if (n_ext < 1 || n_ext > kMaxExt || n_ext > n_vars - 1) {
+    set_error("n_ext must be in [1,4] and leave at least one summed variable");
+    return TAMI_EINVAL;
+  }
+  const int m = n_vars - n_ext;
   for (int i = 0; i < n_lines * n_vars; ++i)
     if (alpha[i] < -1 || alpha[i] > 1) { set_error("alpha entries must be -1, 0 or 1"); return TAMI_EINVAL; }
   tami_diagram* d = new (std::nothrow) tami_diagram;
   if (!d) { set_error("out of host memory"); return TAMI_ENOMEM; }
   d->N = n_lines;
   d->nv = n_vars;
+  d->n_ext = n_ext;
   d->prefactor = prefactor;
   d->alpha.assign(alpha, alpha + n_lines * n_vars);
   d->boson.assign(n_vars, 0);
@@ -926,10 +962,10 @@ int tami_construct(int n_lines, int n_vars, const int8_t* alpha, const int8_t* e
     add_factor(t0.G, g, 1);
   }
   std::vector<SymTerm> cur{t0}, nxt;
-  std::vector<char> done(n_vars - 1, 0);
-  for (int s = 0; s < n_vars - 1; ++s) {
+  std::vector<char> done(m, 0);
+  for (int s = 0; s < m; ++s) {
     int p = order ? order[s] : s;
-    if (p < 0 || p >= n_vars - 1 || done[p]) { delete d; set_error("order must be a permutation of 0..m-1"); return TAMI_EINVAL; }
+    if (p < 0 || p >= m || done[p]) { delete d; set_error("order must be a permutation of 0..m-1"); return TAMI_EINVAL; }
     done[p] = 1;
     int rc = sum_over(cur, p, n_vars, d->boson, nxt);
     if (rc != TAMI_OK) { delete d; return rc; }
@@ -940,6 +976,12 @@ int tami_construct(int n_lines, int n_vars, const int8_t* alpha, const int8_t* e
   if (rc != TAMI_OK) { delete d; return rc; }
   *out = d;
   return TAMI_OK;
+}
+
+int tami_construct(int n_lines, int n_vars, const int8_t* alpha, const int8_t* eps,
+                   const uint8_t* var_is_boson, const int32_t* order, double prefactor,
+                   tami_diagram** out) {
+  return tami_construct_ext(n_lines, n_vars, 1, alpha, eps, var_is_boson, order, prefactor, out);
 }
 
 int tami_diagram_info(const tami_diagram* d, tami_info* info) {

@@ -14,6 +14,7 @@ namespace tami {
 
 constexpr int kMaxLines = TAMI_MAX_LINES;
 constexpr int kMaxVars = TAMI_MAX_VARS;
+constexpr int kMaxExt = TAMI_MAX_EXT;
 
 // Per-thread capacities of the evaluation kernels (checked at flatten time).
 constexpr int kMaxCombos = 128;
@@ -82,6 +83,8 @@ struct TableHeader {
   int n_pnode;      // phase-2 product nodes
   int g2_const;     // 1 if group 0 of phase 2 has no frequency-dependent factor (R = 1)
   int max_der;
+  int n_ext;        // external frequencies per frequency row (the last n_ext variables)
+  int n_xk;         // distinct external-coefficient vectors v_k of the complex denominators
   int bytes;
   // offsets
   int off_alpha;      // double [N][nv]
@@ -97,7 +100,9 @@ struct TableHeader {
   int off_fv;         // int32 [n_fv][2]         sign, k
   int off_rden;       // int32 [n_rden][2]       combo, sign
   int off_cden;       // int32 [n_cden][2]       combo, sign
-  int off_cden_a;     // double [n_cden]          external-frequency coefficient
+  int off_cden_a;     // double [n_cden]          g_c: the external coefficients are g_c * v_{k_c}
+  int off_cden_xk;    // int32 [n_cden]           k_c (n_ext = 1: 0, with v_0 = (1) and g_c = a_ext)
+  int off_xvec;       // double [n_xk][n_ext]     v_k; the kernels form Y_kf = sum_q v_kq X_fq per row f
   int off_g1;         // int32 [n_g1][4]         op_begin, op_end, rd_begin, rd_end
   int off_g1_tgt;     // int32 [n_g1]             frequency group it feeds (ascending)
   int off_ops;        // int2 [n_ops]            pole-tree program, forward encoding (kOp*)
@@ -116,6 +121,7 @@ struct TableHeader {
 
 struct tami_diagram {
   int N = 0, nv = 0;
+  int n_ext = 1;                      // external variables (the last n_ext of the nv)
   std::vector<int8_t> alpha;          // [N][nv]
   std::vector<uint8_t> boson;         // [nv]
   double prefactor = 1.0;

@@ -40,7 +40,10 @@ bool validate_table(const TableHeader& h, const unsigned char* blob, size_t size
   Reader R{blob, size};
   auto bad = [&](const std::string& w) { R.fail(w); };
   if ((size_t)h.bytes != size) bad("header size differs from the blob");
-  if (!in(h.N, 1, kMaxLines + 1) || !in(h.nv, 2, kMaxVars + 2) || h.m != h.nv - 1) bad("line or variable count");
+  if (!in(h.N, 1, kMaxLines + 1) || !in(h.nv, 2, kMaxVars + 1) || !in(h.n_ext, 1, kMaxExt + 1) ||
+      h.m != h.nv - h.n_ext || h.m < 1)
+    bad("line or variable count");
+  if (!in(h.n_xk, 1, kMaxCplxDens + 2) || (h.n_ext == 1 && h.n_xk != 1)) bad("external-coefficient vectors");
   if (h.n_rep_ext < 0 || h.n_rep_ext > h.n_rep || h.n_rep > h.N) bad("representative lines");
   if (h.n_combo > kMaxCombos || h.n_fv > kMaxFermiValues || h.n_rden > kMaxRealDens || h.n_cden > kMaxCplxDens ||
       h.n_pnode > kMaxProdNodes || h.n_slots > kMaxSlots || h.max_der > kMaxDer || h.max_der < 0)
@@ -56,6 +59,8 @@ bool validate_table(const TableHeader& h, const unsigned char* blob, size_t size
   const int* fvr = R.at<int>(h.off_fv, 2 * (size_t)h.n_fv, "fv");
   const int* rden = R.at<int>(h.off_rden, 2 * (size_t)h.n_rden, "rden");
   const int* cden = R.at<int>(h.off_cden, 2 * (size_t)h.n_cden, "cden");
+  const int* cden_xk = R.at<int>(h.off_cden_xk, h.n_cden, "cden_xk");
+  const double* xvec = R.at<double>(h.off_xvec, (size_t)h.n_xk * h.n_ext, "xvec");
   const int* g1 = R.at<int>(h.off_g1, 4 * (size_t)h.n_g1, "g1");
   const int* g1_tgt = R.at<int>(h.off_g1_tgt, h.n_g1, "g1_tgt");
   const int* ops = R.at<int>(h.off_ops, 2 * (size_t)h.n_ops, "ops");
@@ -97,7 +102,9 @@ bool validate_table(const TableHeader& h, const unsigned char* blob, size_t size
   if (v != h.n_fv) bad("segments do not cover the Fermi values");
   for (int i = 0; i < h.n_rden; ++i) if (!in(rden[2 * i], 0, h.n_combo)) bad("real denominator combination");
   for (int i = 0; i < h.n_cden; ++i)
-    if (!in(cden[2 * i], 0, h.n_combo) || (cden[2 * i + 1] != 1 && cden[2 * i + 1] != -1)) bad("complex denominator");
+    if (!in(cden[2 * i], 0, h.n_combo) || (cden[2 * i + 1] != 1 && cden[2 * i + 1] != -1) || !in(cden_xk[i], 0, h.n_xk))
+      bad("complex denominator");
+  if (h.n_ext == 1 && xvec[0] != 1.0) bad("external-coefficient vector of a one-external table");
   // phase-1 groups and both pole-DAG programs
   if (g1_node[0] != 0 || g1_node[h.n_g1] != h.n_nodes || h.n_nodes > (1 << kOpbDstBits)) bad("DAG node ranges");
   int op_end = 0, rd_end = 0;

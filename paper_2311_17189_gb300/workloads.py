@@ -79,6 +79,33 @@ ENERGY_X1 = dict(
     a=8.0, beta=1.0, n_freq=100, n_e=1_000_000, seed=SEED,
 )
 
+# Several external frequencies (Sec. 2.3: frequency_t rows with m + n_nu entries, n_nu > 1): the
+# order-4 diagram of ORDER4 with its last loop frequency held external beside the external one
+# (two fermionic externals nu', nu; three sums left), on energy input like the paper's example:
+# 10^6 rows of energies uniform on (-8, 8), 100 frequency rows (nu'_{n'}, nu_n) on the 10 x 10
+# grid n', n = 0..9, beta = 1.
+TWO_FREQ_X1 = dict(
+    name="order4_two_external_x1",
+    order=4, code=(0, 1, 1, 4, 2, 3, 3, 2, 0), held=3,
+    a=8.0, beta=1.0, n_grid=10, n_e=1_000_000, seed=SEED,
+)
+
+
+def hold_external(alpha, held):
+    """Labels with internal variable `held` moved to the external block: columns reordered so the
+    other internal variables come first, then `held`, then the original external (n_ext = 2)."""
+    alpha = np.asarray(alpha)
+    m = alpha.shape[1] - 1
+    cols = [l for l in range(m) if l != held] + [held, m]
+    return np.ascontiguousarray(alpha[:, cols])
+
+
+def matsubara_grid(beta, n1, n2):
+    """Rows (i nu'_{n'}, i nu_n), n' = 0..n1-1 (slow), n = 0..n2-1 (fast), both fermionic."""
+    a, b = np.meshgrid(matsubara(beta, n1), matsubara(beta, n2), indexing="ij")
+    return np.stack([a.ravel(), b.ravel()], axis=1)
+
+
 # Every order-2..5 diagram in one launch: diagram d gets 2^(20 + d mod 4) samples, 32 freqs.
 ALL_ORDERS = dict(
     name="sigma_orders_2_to_5",

@@ -73,6 +73,44 @@ def test_construction_counts_multipole_and_bosonic_cases():
                (b["terms"], b["max_der"], b["unique_poles"], b["unique_dens"])
 
 
+EXT_CASES = [
+    # (alpha, eps, boson, n_ext): several external frequencies (Sec. 2.3, n_nu > 1)
+    ([[1, 1, 0], [1, 0, 1]], None, None, 2),
+    ([[1, 0, 0], [1, 1, -1]], None, None, 2),
+    ([[1, 1, 0, 0], [1, 0, 1, 0], [1, 0, 0, 1]], None, [0, 1, 0, 0], 3),
+    ([[1, 0, 0, 0], [1, 0, 0, 0], [0, 1, 0, 0], [-1, 1, 1, 1]],
+     [[1, 0, 0, 0], [1, 0, 0, 0], [0, 0, 1, 0], [0, 0, 0, 1]], [0, 0, 1, 0], 2),
+]
+
+
+def test_construction_counts_with_several_externals():
+    """Library and oracle construct independently; with n_ext external variables they agree on
+    the terms, derivative orders and the distinct poles and (energy, external-coefficient)
+    denominators, also for the enumerated order-3 and order-4 diagrams with their last internal
+    variable held external."""
+    cases = list(EXT_CASES)
+    for order in (3, 4):
+        for d in T.enumerate_sigma(order)[:4]:
+            b = [0] * (order + 1)
+            b[order - 1] = 1
+            cases.append((d["alpha"], d["eps"], b, 2))
+    for alpha, eps, boson, n_ext in cases:
+        a = T.Diagram(alpha, eps=eps, var_is_boson=boson, n_ext=n_ext).info()
+        b = O.Solution(alpha, eps=eps, var_is_boson=boson, n_ext=n_ext).info()
+        assert a["n_ext"] == n_ext
+        assert (a["n_terms"], a["n_fermi_factors"], a["n_g_factors"], a["max_der"], a["unique_poles"],
+                a["unique_dens"]) == (b["terms"], b["fermi_factors"], b["g_factors"], b["max_der"],
+                                      b["unique_poles"], b["unique_dens"])
+
+
+def test_rejects_bad_external_counts():
+    for n_ext in (0, 3, 5):
+        with pytest.raises(L.TamiError) as e:
+            T.Diagram([[1, 1, 0], [1, 0, 1]], n_ext=n_ext)   # n_vars = 3: at most 2 externals
+        assert e.value.code == L.TAMI_EINVAL
+    assert T.Diagram([[1, 0, 1], [0, 1, 0], [1, 1, 0]], var_is_boson=[1, 0, 0]).info()["n_ext"] == 1
+
+
 def test_order2_table_shape():
     """The order-2 Hubbard self-energy gives exactly 4 terms with 2 Fermi factors and one
     Green's function each (the two two-leaf sums of Fig. treeflow, multiplied out)."""
