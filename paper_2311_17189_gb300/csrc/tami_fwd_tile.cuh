@@ -85,27 +85,53 @@ __device__ __forceinline__ double pole_tree(const TableView& T, int op0, int op1
   return v[dst];
 }
 
-// Phase-2 assignment of (frequency, sample) pairs: tpf threads per frequency when n_f <= block,
-// else several frequencies per thread over all samples of the tile.
+// Phase-2 assignment of the tile's (frequency, sample) pairs to threads.  A thread walks nf
+// segments: segment i is frequency f0 + i * fstep over samples [sb, se) with stride sstep, where
+// (sb, se) is (sb0, se0) for the first segment and (sb1, se1) for the others.
+//   n_f divides kBlock: tpf = kBlock / n_f threads per frequency, samples strided by tpf;
+//   n_f < kBlock otherwise ("balanced"): thread t takes the n_f consecutive pairs
+//     [t n_f, (t+1) n_f) in frequency-major order, i.e. the end of one frequency's samples and the
+//     start of the next one's (at most two segments), so every thread does n_f pairs and no warp
+//     issues FP64 work for a handful of lanes;
+//   n_f > kBlock: frequencies f = t, t + kBlock, ... over all samples.
 struct FreqMap {
-  int tpf, f0, fstep, nf, s0, sstep;
+  int tpf, f0, fstep, nf, sstep, sb0, se0, sb1, se1;
+  int p0;          // balanced: the first of the thread's n_f pairs
+  bool balanced;
 };
 
 __device__ __forceinline__ FreqMap freq_map(int n_f, int tid) {
   FreqMap m;
-  if (n_f <= kBlock) {
+  m.balanced = false;
+  m.sb1 = 0;
+  m.se1 = kBlock;
+  if (n_f <= kBlock && kBlock % n_f == 0) {
     m.tpf = kBlock / n_f;
     m.f0 = tid / m.tpf;
     m.fstep = 1;
     m.nf = m.f0 < n_f ? 1 : 0;
-    m.s0 = tid % m.tpf;
+    m.sb0 = tid % m.tpf;
+    m.se0 = kBlock;
     m.sstep = m.tpf;
+  } else if (n_f < kBlock) {
+    const int p0 = tid * n_f;             // first pair, frequency-major: p = f * kBlock + s
+    m.p0 = p0;
+    m.balanced = true;
+    m.tpf = 0;
+    m.f0 = p0 / kBlock;
+    m.fstep = 1;
+    m.sb0 = p0 % kBlock;
+    m.se0 = min(kBlock, m.sb0 + n_f);
+    m.se1 = m.sb0 + n_f - kBlock;         // samples of frequency f0 + 1, if positive
+    m.nf = m.se1 > 0 ? 2 : 1;
+    m.sstep = 1;
   } else {
     m.tpf = 1;
     m.f0 = tid;
     m.fstep = kBlock;
     m.nf = (n_f - tid + kBlock - 1) / kBlock;
-    m.s0 = 0;
+    m.sb0 = 0;
+    m.se0 = kBlock;
     m.sstep = 1;
   }
   return m;
@@ -310,21 +336,68 @@ __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& 
 
 // Two samples per iteration give the FP64 pipe two independent dependency chains; the sums are
 // still taken sample by sample, in the same order.
+// Swap the running sums of the thread's two frequencies (selects, no FP64 work).
+__device__ __forceinline__ void swap_sums(bool sw, double* a, double* b) {
+  for (int k = 0; k < 4; ++k) {
+    const double x = a[k], y = b[k];
+    a[k] = sw ? y : x;
+    b[k] = sw ? x : y;
+  }
+}
+
 template <bool XR_ZERO>
 __device__ __forceinline__ void phase2_loop(const TableHeader& H, const TableView& T, const TileArgs& A, long long s0,
                                             const double* Xs, const double* AXI, const double* AXI2, const double* CB,
                                             const double* W, const FreqMap& M, double (*acc)[4]) {
+  if (M.balanced) {
+    // One flat loop over the thread's n_f pairs p = p0 .. p0 + n_f - 1 (frequency p / kBlock, slot
+    // p % kBlock), the same trip count in every lane.  The sums go to cur, which holds the
+    // current frequency's sums: when p reaches the next frequency (slot 0) cur and oth swap.
+    // Slots past the end of the sample stream (last tile) are evaluated on whatever the tile
+    // buffers hold and dropped.
+    double cur[4], oth[4];
+    for (int k = 0; k < 4; ++k) { cur[k] = acc[0][k]; oth[k] = acc[1][k]; }
+    bool crossed = false;
+    int j = 0;
+    for (; j + 1 < A.n_f; j += 2) {
+      const int pa = M.p0 + j, pb = pa + 1;
+      const int fa = pa / kBlock, sla = pa % kBlock, fb = pb / kBlock, slb = pb % kBlock;
+      double ar, ai, br, bi;
+      phase2_sample<XR_ZERO>(H, T, A, sla, fa, Xs, AXI, AXI2, CB, W, ar, ai);
+      phase2_sample<XR_ZERO>(H, T, A, slb, fb, Xs, AXI, AXI2, CB, W, br, bi);
+      const bool sa = sla == 0 && j > 0, sb = slb == 0;
+      swap_sums(sa, cur, oth);
+      crossed |= sa;
+      if (s0 + sla < A.n) phase2_store(A, fa, s0 + sla, ar, ai, cur);
+      swap_sums(sb, cur, oth);
+      crossed |= sb;
+      if (s0 + slb < A.n) phase2_store(A, fb, s0 + slb, br, bi, cur);
+    }
+    if (j < A.n_f) {
+      const int pa = M.p0 + j, fa = pa / kBlock, sla = pa % kBlock;
+      double ar, ai;
+      phase2_sample<XR_ZERO>(H, T, A, sla, fa, Xs, AXI, AXI2, CB, W, ar, ai);
+      const bool sa = sla == 0 && j > 0;
+      swap_sums(sa, cur, oth);
+      crossed |= sa;
+      if (s0 + sla < A.n) phase2_store(A, fa, s0 + sla, ar, ai, cur);
+    }
+    swap_sums(crossed, cur, oth);     // back to acc[0] = frequency f0, acc[1] = f0 + 1
+    for (int k = 0; k < 4; ++k) { acc[0][k] = cur[k]; acc[1][k] = oth[k]; }
+    return;
+  }
   for (int fi = 0; fi < M.nf; ++fi) {
     const int f = M.f0 + fi * M.fstep;
-    int sl = M.s0;
-    for (; sl + M.sstep < kBlock && s0 + sl + M.sstep < A.n; sl += 2 * M.sstep) {
+    int sl = fi ? M.sb1 : M.sb0;
+    const int se = fi ? M.se1 : M.se0;
+    for (; sl + M.sstep < se && s0 + sl + M.sstep < A.n; sl += 2 * M.sstep) {
       double ar, ai, br, bi;
       phase2_sample<XR_ZERO>(H, T, A, sl, f, Xs, AXI, AXI2, CB, W, ar, ai);
       phase2_sample<XR_ZERO>(H, T, A, sl + M.sstep, f, Xs, AXI, AXI2, CB, W, br, bi);
       phase2_store(A, f, s0 + sl, ar, ai, acc[fi]);
       phase2_store(A, f, s0 + sl + M.sstep, br, bi, acc[fi]);
     }
-    for (; sl < kBlock && s0 + sl < A.n; sl += M.sstep) {
+    for (; sl < se && s0 + sl < A.n; sl += M.sstep) {
       double ar, ai;
       phase2_sample<XR_ZERO>(H, T, A, sl, f, Xs, AXI, AXI2, CB, W, ar, ai);
       phase2_store(A, f, s0 + sl, ar, ai, acc[fi]);
@@ -337,7 +410,27 @@ __device__ __forceinline__ void phase2_loop(const TableHeader& H, const TableVie
 __device__ __forceinline__ void block_reduce_store(const FreqMap& M, int n_f, double (*acc)[4], double* red,
                                                    double* out) {
   const int tid = threadIdx.x;
-  if (n_f <= kBlock) {
+  if (M.balanced) {
+    // Frequency f is covered by threads tlo..thi (their pair ranges meet [f kBlock, (f+1) kBlock)).
+    // Its sum, in this order: the second segment of tlo when tlo starts on frequency f - 1, then
+    // the first segments of the threads that start on f, in thread order.
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    const int tlo = tid < n_f ? (tid * kBlock) / n_f : 0;
+    const int thi = tid < n_f ? (tid * kBlock + kBlock - 1) / n_f : -1;
+    for (int k = 0; k < 4; ++k) red[k * kBlock + tid] = M.nf > 1 ? acc[1][k] : 0.0;
+    __syncthreads();
+    if (tid < n_f && (tlo * n_f) / kBlock != tid)
+      for (int k = 0; k < 4; ++k) s[k] = red[k * kBlock + tlo];
+    __syncthreads();
+    for (int k = 0; k < 4; ++k) red[k * kBlock + tid] = acc[0][k];
+    __syncthreads();
+    if (tid < n_f) {
+      for (int t = tlo; t <= thi; ++t)
+        if ((t * n_f) / kBlock == tid)
+          for (int k = 0; k < 4; ++k) s[k] += red[k * kBlock + t];
+      for (int k = 0; k < 4; ++k) out[tid * 4 + k] = s[k];
+    }
+  } else if (n_f <= kBlock) {
     for (int k = 0; k < 4; ++k) red[k * kBlock + tid] = acc[0][k];
     __syncthreads();
     if (tid < n_f) {

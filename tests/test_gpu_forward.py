@@ -183,9 +183,11 @@ def test_order4_small_sample_counts(n):
     check_mean(mean, var, ref["values"], ref)
 
 
-@pytest.mark.parametrize("n_f", [1, 3, 129, 300])
+@pytest.mark.parametrize("n_f", [1, 3, 100, 127, 129, 300])
 def test_frequency_counts(n_f):
-    """Frequency counts below, at and above the block size (the per-thread frequency split)."""
+    """Frequency counts below, at and above the block size: the per-thread frequency split, the
+    balanced split of counts that do not divide the block (3, 100, 127) and several frequencies
+    per thread (129, 300)."""
     d = diagram(3, 1)
     D, S = lib_and_oracle(d["alpha"], d["eps"])
     X = W.real_axis(-4, 4, n_f, 0.05) if n_f > 3 else W.matsubara(10.0, n_f)
