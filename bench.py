@@ -49,8 +49,8 @@ METRIC = "order-4 Sigma evals/s (samples x terms x frequencies, FP64), forward +
 # capture of this workload at 2^22 samples, per sample; every sample does the same work, so a
 # launch's traffic is this times its samples.  It holds only for the kernel sources it was taken
 # on: the hash of the library sources must match, else the bench reports traffic as null.
-TRAFFIC = {"kernel": "bwd_kernel<0,1> (fused forward + adjoint)", "bytes_per_sample": (7.281564e9 + 13.051014e9) / 4194304,
-           "sources_sha256": "2d13a0b4e8b524f1f47fcbfbdd18168bea2c6968d73165702ad9cf9b31ba25ef", "profile": "profiles/fused_kernel_order4_sigma.md"}
+TRAFFIC = {"kernel": "bwd_kernel<0,1> (fused forward + adjoint)", "bytes_per_sample": (7.289495e9 + 13.059005e9) / 4194304,
+           "sources_sha256": "c4b5424d9daff69f4a9db8b319da5ca063708b3c22de81a432072b8472b11c29", "profile": "profiles/fused_kernel_order4_sigma.md"}
 
 
 TRAFFIC_SOURCES = ("paper_2311_17189_gb300/csrc/tami_bwd.cu", "paper_2311_17189_gb300/csrc/tami_device.cuh",
@@ -423,7 +423,9 @@ def run_workload(args):
                   "step": "one graph launch of the persistent kernel (forward)", "plan": B.info()}
         bytes_step = None
     elif wl == "energy_x1":
-        c = W.ENERGY_X1
+        c = dict(W.ENERGY_X1)
+        if args.rows:
+            c["n_e"] = args.rows
         D = T.Diagram(c["alpha"]).upload(0)
         info = D.info()
         E = torch.as_tensor(W.random_energies(c["n_e"], c["alpha"].shape[0], a=c["a"], seed=c["seed"]), device=dev)
@@ -439,7 +441,9 @@ def run_workload(args):
         config = {"workload": c["name"], "rows": c["n_e"], "frequencies": n_f, "terms": info["n_terms"],
                   "beta": c["beta"], "step": "tami_eval_energies, full [n_f][n_e] output"}
     elif wl == "two_freq_x1":
-        c = W.TWO_FREQ_X1
+        c = dict(W.TWO_FREQ_X1)
+        if args.rows:
+            c["n_e"] = args.rows
         d = next(x for x in T.enumerate_sigma(c["order"]) if x["code"] == tuple(c["code"]))
         alpha = W.hold_external(d["alpha"], c["held"])
         D = T.Diagram(alpha, eps=d["eps"], n_ext=2).upload(0)
@@ -502,6 +506,7 @@ def main():
     p.add_argument("--ref-samples", type=int, default=1 << 12)
     p.add_argument("--samples", type=int, default=CFG["n_samples"], help="samples per GPU (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--rows", type=int, default=0, help="energy rows of energy_x1 / two_freq_x1 (profiling runs)")
     p.add_argument("--workload", default="order4", choices=["order4", "order5", "order3_real", "all_orders", "energy_x1", "two_freq_x1"],
                    help="order4 is the headline metric; the others time the remaining configurations on one GPU")
     args = p.parse_args()
