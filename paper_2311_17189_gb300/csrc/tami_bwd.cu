@@ -64,7 +64,8 @@ __host__ __device__ __forceinline__ size_t bwd_smem_bytes(const TableHeader& h, 
 // (pW = p W_h per group factor, formed once per sample), Z_d = r_d U_d, dv/dX = -sum_d a_d Z_d and
 // the denominator-energy adjoints bb_d -= Re(conj g Z_d).  As in the forward, no data-dependent
 // selects around FP64 work (predicated-off FP64 instructions still cost FP64-pipe time): the R = 1
-// group is group 0 and the imaginary-axis case is a template parameter.
+// group is group 0 (its weight adjoint, sum_f Re g_f, is the same for every sample: the caller
+// sets it from a per-block sum) and the imaginary-axis case is a template parameter.
 template <bool XR_ZERO, bool FWD>
 __device__ __forceinline__ void bwd_phase2(const TableHeader& H, int n_f, long long s, const BwdParams& P,
                                            const double* Xs, const double* Gs, const double* AXI, const double* AXI2,
@@ -88,7 +89,6 @@ __device__ __forceinline__ void bwd_phase2(const TableHeader& H, int n_f, long l
       vre[H.n_cden + k] = fma(ar, br, -ai * bi);
       vim[H.n_cden + k] = fma(ar, bi, ai * br);
     }
-    if (H.g2_const) Wb2[0] += gr;                 // R = 1
     double vr = 0.0, vi = 0.0;                    // fused pass: the sample's value sum_h W_h R_h
     if (FWD) vr = H.g2_const ? W2[0] : 0.0;
     for (int h = H.g2_const; h < H.n_g2; ++h) {
@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
   if (FWD)
     for (int i = 0; i < 4 * n_f; ++i) accV[i] = 0.0;
   double gmu = 0.0, gkx = 0.0, gky = 0.0;
+  __shared__ double s_gsum;                  // sum_f Re g_f in frequency order: the R = 1 group's Wb
   __syncthreads();
   bool xr_zero;
   {
@@ -191,6 +192,11 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
       AXI2[i] = a * a;
     }
     for (int f = tid; f < n_f; f += kBlock) nonzero |= Xs[2 * f] != 0.0;
+    if (tid == 0) {
+      double g = 0.0;
+      for (int f = 0; f < n_f; ++f) g += Gs[2 * f];
+      s_gsum = g;
+    }
     xr_zero = !__syncthreads_or(nonzero);
   }
 
@@ -291,6 +297,7 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
     else
       bwd_phase2<false, FWD>(H, n_f, s, P, Xs, Gs, AXI, AXI2, cden_a, g2, g2cd, pnode, g2node, pW, b, W2, Wb2, bb,
                              accX, accV);
+    if (H.g2_const) Wb2[0] = s_gsum;             // R = 1: sum_f Re(conj g_f * 1), as the loop would add it
     // ------------------------------------------------------------ reverse sweep
     double xbar[kBwCombos], fvbar[kBwFv];
     for (int u = 0; u < H.n_combo; ++u) xbar[u] = 0.0;
