@@ -27,12 +27,13 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
   }
 }
 
-// [0,1) from 53 bits of two words, then k = 2 pi u - pi with one rounding
+// [0,1) from 53 bits of two words, u = m 2^-53, then k = 2 pi u - pi with one rounding.  m is
+// exact in a double and the powers of two scale exactly, so fma(m, 2 pi 2^-53, -pi) is that
+// rounding of the same real number: one FP64 multiply fewer.
 __device__ __forceinline__ double to_momentum(uint32_t hi, uint32_t lo) {
   unsigned long long m = ((unsigned long long)hi << 21) | (unsigned long long)(lo >> 11);
-  double u = __dmul_rn(__ull2double_rn(m), 0x1.0p-53);
   const double pi = 0x1.921fb54442d18p+1;
-  return fma(u, 2.0 * pi, -pi);
+  return fma(__ull2double_rn(m), 2.0 * pi * 0x1.0p-53, -pi);
 }
 
 // cos and sin: Cody-Waite reduction by pi (two-part constant), k = n pi + r, |r| <= pi/2 (n the
@@ -177,7 +178,9 @@ __device__ __forceinline__ double exp_neg(double t, double& em) {
     const long long sh = (long long)m << 52;
     if (NEED_EM) {
       th = __longlong_as_double(__double_as_longlong(th) + sh);
-      tl = tl == 0.0 ? 0.0 : __longlong_as_double(__double_as_longlong(tl) + sh);
+      // only the j = 0 entry of the low table is 0 (kept 0 rather than exponent-shifted); an
+      // integer test, not an FP64 compare
+      tl = j == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(tl) + sh);
       const double c = fma(th, p, tl);
       y = th + c;
       em = (th - 1.0) + c;
@@ -229,7 +232,7 @@ __device__ __forceinline__ void fermi_segment(const int* seg, const int* fvr, co
   const double y = exp_neg<BOSE>(-beta * fabs(xv), em);
   const double rD = rcp(BOSE ? -em : 1.0 + y);
   const double t2 = (BOSE ? -y : y) * rD;
-  const bool neg = xv <= 0.0;
+  const bool neg = __double_as_longlong(xv) <= 0;   // xv <= 0 (+0, -0 and negatives), on the ALU
   const double g = neg ? rD : t2, h = neg ? t2 : rD;   // g_sigma(x) and g_sigma(-x)
   double d1 = 0.0;
   if (DUAL) d1 = -beta * (g * h);

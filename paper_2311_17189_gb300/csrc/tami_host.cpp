@@ -725,7 +725,7 @@ int flatten(tami_diagram* d) {
   // Counts follow the kernel: fma = 2 flops, mul/add = 1, the reciprocal (estimate + one
   // third-order Newton step) = 3 fma, the table-driven exponential 10 fma + 3 add/mul.
   double fl = 0.0;
-  fl += 3.0 * 2 * m;                                    // u -> k: mul + fma per component
+  fl += 2.0 * 2 * m;                                    // u -> k: one fma per component
   fl += 2.0 * 2.0 * n_lm;                               // line momenta, fma per nonzero label and dimension
   fl += h.n_rep * (2.0 * 30.0 + 6.0);                   // cos of both components (reduction 9, series 21), energy
   const double energy_flops = fl;                       // what a saved-rows adjoint does not redo
