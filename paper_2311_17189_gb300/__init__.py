@@ -9,7 +9,7 @@ Only marshalling lives in Python; the construction is libtami's C++ and every ev
 step is a libtami CUDA kernel.  `workloads` holds the seeded synthetic inputs.
 """
 from . import _lib, mc
-from .api import Batch, Diagram, enumerate_sigma
+from .api import Batch, Diagram, enumerate_sigma, set_jit
 from . import graph
 
-__all__ = ["Batch", "Diagram", "enumerate_sigma", "graph", "_lib", "mc"]
+__all__ = ["Batch", "Diagram", "enumerate_sigma", "graph", "_lib", "mc", "set_jit"]

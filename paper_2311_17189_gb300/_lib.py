@@ -13,12 +13,14 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libtami.so")
 
 TAMI_OK, TAMI_EINVAL, TAMI_ENOMEM, TAMI_ECUDA, TAMI_ETIMEOUT, TAMI_EUNSUPPORTED = range(6)
+TAMI_JIT_NEVER, TAMI_JIT_AUTO, TAMI_JIT_ALWAYS = range(3)
 
 # functions declared in include/tami.h (checked by tests/test_lib_host.py)
 EXPORTS = [
     "tami_last_error", "tami_construct", "tami_construct_ext", "tami_label_graph", "tami_construct_from_graph", "tami_diagram_info", "tami_upload", "tami_sample_energies",
     "tami_eval_energies", "tami_forward_workspace", "tami_forward", "tami_forward_noalloc",
     "tami_backward_workspace", "tami_backward", "tami_forward_backward_workspace", "tami_forward_backward",
+    "tami_set_jit", "tami_jit_prepare", "tami_jit_status", "tami_jit_source",
     "tami_batch_plan", "tami_batch_info", "tami_batch_launch",
     "tami_batch_destroy", "tami_batch_debug_set_item",
     "tami_enumerate_sigma",
@@ -89,6 +91,11 @@ def lib():
     L.tami_forward_backward_workspace.argtypes = [vp, i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.tami_forward_backward.argtypes = [vp, ctypes.POINTER(Lattice), u64, u64, i64, dp, ctypes.c_int, ctypes.c_double,
                                         dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_size_t, vp]
+    L.tami_set_jit.argtypes = [ctypes.c_int]
+    L.tami_jit_prepare.argtypes = [vp]
+    L.tami_jit_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_double)]
+    L.tami_jit_source.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.tami_batch_plan.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
     L.tami_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int)]

@@ -42,6 +42,16 @@ def _as_c_pairs(X, device, n_ext=1):
     return torch.view_as_real(X).contiguous()
 
 
+JIT_MODES = {"never": L.TAMI_JIT_NEVER, "auto": L.TAMI_JIT_AUTO, "always": L.TAMI_JIT_ALWAYS}
+
+
+def set_jit(mode):
+    """Which kernel forward_backward runs (tami_set_jit): 'never' the generic kernel, 'auto' (the
+    default) the diagram's specialised kernel for launches of >= 2^21 samples, 'always' the
+    specialised kernel for every launch.  Process-wide."""
+    L.check(L.lib().tami_set_jit(JIT_MODES[mode]))
+
+
 class Diagram:
     """An AMI solution (flat terms A * FT * R, Sec. 2.2) and its device term table.  The last
     n_ext columns of alpha are external variables (Sec. 2.3); the others are summed.  Momentum
@@ -80,6 +90,26 @@ class Diagram:
         if self.device is None:
             raise L.TamiError(L.TAMI_EINVAL, "diagram not uploaded (call upload)")
         return f"cuda:{self.device}"
+
+    def jit_prepare(self):
+        """Build the specialised fused kernel of this uploaded diagram now (tami_jit_prepare)."""
+        torch = _torch()
+        with torch.cuda.device(self.device):
+            L.check(L.lib().tami_jit_prepare(self._h))
+
+    def jit_status(self):
+        """dict(ready, last_used, compile_ms) of the specialised fused kernel (tami_jit_status)."""
+        r, u, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        L.check(L.lib().tami_jit_status(self._h, ctypes.byref(r), ctypes.byref(u), ctypes.byref(ms)))
+        return {"ready": bool(r.value), "last_used": bool(u.value), "compile_ms": ms.value}
+
+    def jit_source(self):
+        """The CUDA C++ source of the specialised fused kernel (tami_jit_source)."""
+        n = ctypes.c_size_t()
+        L.check(L.lib().tami_jit_source(self._h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        L.check(L.lib().tami_jit_source(self._h, buf, n.value, ctypes.byref(n)))
+        return buf.value.decode()
 
     def upload(self, device=None):
         torch = _torch()

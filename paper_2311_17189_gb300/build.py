@@ -1,8 +1,9 @@
 """Build libtami.so in-tree for sm_103a (GB300).
 
-Two translation units compiled in parallel -- the host construction (g++) and the kernels
-(nvcc, -gencode arch=compute_103a,code=sm_103a) -- then linked with nvcc into
-paper_2311_17189_gb300/libtami.so.  No cmake.
+The host sources (g++) and the kernels (nvcc, -gencode arch=compute_103a,code=sm_103a) are
+compiled in parallel, then linked with nvcc into paper_2311_17189_gb300/libtami.so.  The text of
+csrc/tami_devmath.cuh is also embedded as a string (_build/tami_devmath_src.inc) for the kernels
+that tami_jit.cpp generates and compiles with NVRTC at run time.  No cmake.
 """
 import os
 import subprocess
@@ -16,8 +17,9 @@ OUT = os.path.join(PKG, "libtami.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["tami_host.cpp", "tami_graph.cpp", "tami_validate.cpp", "tami_cuda.cu", "tami_bwd.cu", "tami_batch.cu"]
-HEADERS = ["tami_internal.h", "tami_device.cuh", "tami_fwd_tile.cuh"]
+SOURCES = ["tami_host.cpp", "tami_graph.cpp", "tami_validate.cpp", "tami_jit.cpp", "tami_cuda.cu", "tami_bwd.cu",
+           "tami_batch.cu"]
+HEADERS = ["tami_internal.h", "tami_device.cuh", "tami_devmath.cuh", "tami_fwd_tile.cuh"]
 
 
 def _stale(out, deps):
@@ -27,8 +29,22 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _embed_devmath():
+    """Write csrc/tami_devmath.cuh as a C++ raw string literal (kDevmathSource), if it changed."""
+    with open(os.path.join(CSRC, "tami_devmath.cuh")) as f:
+        text = f.read()
+    assert ")TAMIDEV\"" not in text
+    inc = ("// generated by build.py from csrc/tami_devmath.cuh\n"
+           "static const char kDevmathSource[] = R\"TAMIDEV(" + text + ")TAMIDEV\";\n")
+    path = os.path.join(BUILD, "tami_devmath_src.inc")
+    if not os.path.exists(path) or open(path).read() != inc:
+        with open(path, "w") as f:
+            f.write(inc)
+
+
 def build(force=False, verbose=False):
     os.makedirs(BUILD, exist_ok=True)
+    _embed_devmath()
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "tami.h")]
     objs, procs = [], []
     for src in SOURCES:
@@ -43,7 +59,7 @@ def build(force=False, verbose=False):
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
         else:
-            cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-I", INCLUDE,
+            cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-I", INCLUDE, "-I", BUILD,
                    "-I", "/usr/local/cuda/include", "-c", path, "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     for cmd, p in procs:
@@ -54,7 +70,7 @@ def build(force=False, verbose=False):
         if verbose and out:
             sys.stderr.write(out.decode())
     if force or procs or _stale(OUT, objs):
-        cmd = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", OUT + ".tmp", *objs]
+        cmd = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", OUT + ".tmp", *objs, "-ldl"]
         subprocess.run(cmd, check=True)
         os.replace(OUT + ".tmp", OUT)
     return OUT

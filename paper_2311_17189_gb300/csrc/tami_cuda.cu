@@ -401,6 +401,7 @@ int tami_selftest_exp(const double* t, int64_t n, double* y, double* em, double*
 
 void tami_destroy(tami_diagram* d) {
   if (!d) return;
+  jit_release(d);
   if (d->d_blob) {
     int prev = -1;
     cudaGetDevice(&prev);

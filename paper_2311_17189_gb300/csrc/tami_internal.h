@@ -131,10 +131,19 @@ struct tami_diagram {
   std::vector<unsigned char> blob;    // host copy of the table
   void* d_blob = nullptr;             // device copy
   int device = -1;
+  void* jit = nullptr;                // specialised fused kernel of this table (tami_jit.cpp), or null
 };
 
 namespace tami {
 int flatten(tami_diagram* d);  // terms -> hdr + blob + info
+// Specialised fused kernel (tami_jit.cpp).  jit_select: 1 = launch it for this call (compiled and
+// cached), 0 = the generic kernel, negative = -status (the "always" mode when it cannot be built).
+int jit_select(tami_diagram* d, int64_t n, int n_f);
+int jit_launch_fused(tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset, int64_t n,
+                     const double* X, int n_f, double beta, const double* gout, double* per_sample, double* ps_dX,
+                     double* ps_grad, double* partial, int max_grid, struct CUstream_st* st, int* grid_out);
+void jit_mark_generic(tami_diagram* d);
+void jit_release(tami_diagram* d);
 // Checks every index and range of a flattened table (tami_validate.cpp); false with the reason.
 bool validate_table(const TableHeader& h, const unsigned char* blob, size_t size, std::string* why);
 }

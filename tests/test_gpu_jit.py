@@ -1,0 +1,158 @@
+"""GPU parity of the specialised fused forward + adjoint kernels (generated per table and compiled
+with NVRTC, tami_jit.cpp) against the CPU oracle, and their agreement with the generic kernel.
+
+Per-sample bounds as in test_gpu_forward.py / test_gpu_adjoint.py: 1e-11 of the oracle's rounding
+envelope for values, of its derivative envelope for dSigma/dX and the contracted gradients.
+Reduced outputs (mean, variance, dSigma/dX, gradients) of the two kernels agree to the rounding of
+their sums.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+import paper_2311_17189_gb300 as T
+from paper_2311_17189_gb300 import _lib as L
+from paper_2311_17189_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+@pytest.fixture(autouse=True)
+def _restore_mode():
+    yield
+    T.set_jit("auto")
+
+
+def upstream(n_f, seed=3):
+    r = np.random.default_rng(seed)
+    return r.normal(size=n_f) + 1j * r.normal(size=n_f)
+
+
+def order4_bench():
+    c = W.ORDER4
+    return next(x for x in O.enumerate_sigma(4) if x["code"] == c["code"])
+
+
+CASES = [
+    # name, diagram, lattice, beta, X
+    ("order2_bosonic_transfer", dict(alpha=W.ORDER2["alpha"], eps=None, boson=W.ORDER2["var_is_boson"]),
+     W.lattice(W.ORDER2), 5.0, W.matsubara(5.0, 3)),
+    ("order3_real_axis", (3, 0), (1.0, 0.0, 0.0, np.pi / 2, np.pi / 2), 10.0, W.real_axis(-4.0, 4.0, 7, 0.05)),
+    ("order4_bench", "bench", W.lattice(W.ORDER4), 8.0, W.matsubara(8.0, 16)),
+    ("order5_real_axis", (5, 7), (1.0, -0.2, 0.1, np.pi / 2, np.pi / 3), 5.0, W.real_axis(-2.0, 2.0, 3, 0.1)),
+    ("quadruple_pole", dict(alpha=[[1, 0], [1, 0], [1, 0], [1, 0], [1, 1]],
+                            eps=[[1, 0, 0, 0, 0]] * 4 + [[0, 0, 0, 0, 1]], boson=[0, 1]),
+     (1.0, -0.3, 0.2, np.pi / 3, np.pi / 5), 2.0, W.real_axis(-3.0, 3.0, 5, 0.1)),
+]
+
+
+def setup(case):
+    name, spec, lat, beta, X = case
+    if spec == "bench":
+        d = order4_bench()
+        alpha, eps, boson, pref = d["alpha"], d["eps"], None, 1.0
+    elif isinstance(spec, dict):
+        alpha, eps, boson, pref = np.array(spec["alpha"]), spec["eps"], spec["boson"], 1.0
+    else:
+        d = O.enumerate_sigma(spec[0])[spec[1]]
+        alpha, eps, boson, pref = d["alpha"], d["eps"], None, (-1.0) ** spec[0] * (-1.0) ** d["loops"]
+    D = T.Diagram(alpha, eps=eps, var_is_boson=boson, prefactor=pref).upload(0)
+    S = O.Solution(alpha, eps=eps, var_is_boson=boson, prefactor=pref)
+    return D, S, lat, beta, X
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_specialised_kernel_against_oracle(case):
+    """Every sample's value, dSigma/dX and contracted gradients from the specialised kernel against
+    the oracle (values, forward-mode dual numbers), over several tiles and a ragged tail."""
+    D, S, lat, beta, X = setup(case)
+    T.set_jit("always")
+    n, seed, off = 3 * 128 + 37, 21, 5
+    g = upstream(len(X))
+    out = D.forward_backward(lat, seed, off, n, X, beta, g, per_sample=True)
+    torch.cuda.synchronize()
+    st = D.jit_status()
+    assert st["ready"] and st["last_used"] and st["compile_ms"] > 0
+    ref = S.eval_momenta(lat, seed, off, n, X, beta, per_sample=True, threads=8)
+    v = out["values"].cpu().numpy()
+    assert np.all(np.abs(v - ref["values"]) <= RTOL * ref["envelope"]), np.max(np.abs(v - ref["values"]) / ref["envelope"])
+    _, dref, denv = S.eval_momenta_deriv(lat, seed, off, n, X, beta, "omega", threads=8, envelope=True)
+    dX = out["dX"].cpu().numpy()
+    assert np.all(np.abs(dX - dref) <= RTOL * denv), np.max(np.abs(dX - dref) / denv)
+    grads = out["grads"].cpu().numpy()
+    for k, which in enumerate(("mu", "kx", "ky")):
+        _, der, env = S.eval_momenta_deriv(lat, seed, off, n, X, beta, which, threads=8, envelope=True)
+        gref = np.real(np.conj(g)[:, None] * der).sum(axis=0)
+        bound = RTOL * (np.abs(g)[:, None] * env).sum(axis=0)
+        assert np.all(np.abs(grads[:, k] - gref) <= bound), (which, np.max(np.abs(grads[:, k] - gref) / bound))
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_specialised_kernel_agrees_with_generic(case):
+    """The specialised and the generic kernel on the same samples: reduced outputs agree to the
+    rounding of the sums, and a second specialised run gives the same bits."""
+    D, S, lat, beta, X = setup(case)
+    n, seed, off = 5000, 7, 1 << 33
+    g = upstream(len(X), seed=9)
+    T.set_jit("never")
+    gen = D.forward_backward(lat, seed, off, n, X, beta, g, per_sample=True)
+    torch.cuda.synchronize()
+    assert not D.jit_status()["last_used"]
+    T.set_jit("always")
+    jit = D.forward_backward(lat, seed, off, n, X, beta, g, per_sample=True)
+    again = D.forward_backward(lat, seed, off, n, X, beta, g, per_sample=True)
+    torch.cuda.synchronize()
+    assert D.jit_status()["last_used"]
+    for k in ("mean", "var", "dSigma_dX", "grad_params", "values", "dX", "grads"):
+        assert torch.equal(jit[k], again[k]), k
+    scale = gen["values"].abs().mean(dim=1)
+    assert torch.all((jit["mean"] - gen["mean"]).abs() <= 1e-12 * scale)
+    assert torch.allclose(jit["var"], gen["var"], rtol=1e-10, atol=0)
+    dscale = gen["dX"].abs().mean(dim=1)
+    assert torch.all((jit["dSigma_dX"] - gen["dSigma_dX"]).abs() <= 1e-12 * dscale)
+    gscale = gen["grads"].abs().mean(dim=0)
+    assert torch.all((jit["grad_params"] - gen["grad_params"]).abs() <= 1e-12 * gscale)
+
+
+def test_auto_mode_takes_the_specialised_kernel_for_large_launches():
+    """auto (the default): the generic kernel below 2^21 samples, the specialised one from there on
+    (compiled on that first call and kept with the diagram)."""
+    d = order4_bench()
+    D = T.Diagram(d["alpha"], eps=d["eps"]).upload(0)
+    c = W.ORDER4
+    X, g = W.matsubara(c["beta"], c["n_freq"]), np.ones(c["n_freq"]) + 0.5j
+    T.set_jit("auto")
+    D.forward_backward(W.lattice(c), c["seed"], 0, 4096, X, c["beta"], g)
+    torch.cuda.synchronize()
+    st = D.jit_status()
+    assert not st["ready"] and not st["last_used"]
+    out = D.forward_backward(W.lattice(c), c["seed"], 0, 1 << 21, X, c["beta"], g)
+    torch.cuda.synchronize()
+    st = D.jit_status()
+    assert st["ready"] and st["last_used"]
+    assert np.all(np.isfinite(out["mean"].cpu().numpy()))
+    T.set_jit("never")
+    D.forward_backward(W.lattice(c), c["seed"], 0, 1 << 21, X, c["beta"], g)
+    torch.cuda.synchronize()
+    assert not D.jit_status()["last_used"]
+
+
+def test_always_mode_refuses_what_the_generator_cannot_build():
+    """A two-external diagram has no momentum-mode fused pass at all: refused before any kernel
+    choice (TAMI_EUNSUPPORTED), and tami_jit_prepare refuses it too."""
+    D = T.Diagram([[1, 1, 0], [1, 0, 1]], n_ext=2).upload(0)
+    T.set_jit("always")
+    with pytest.raises(L.TamiError) as e:
+        D.jit_prepare()
+    assert e.value.code == L.TAMI_EUNSUPPORTED
