@@ -267,13 +267,15 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
                          int64_t n_samples, const double* X, int n_f, double beta, double* mean,
                          double* var, double* per_sample, tami_stream_t stream);
 
-/* Specialised kernels (no counterpart in the paper: how this library runs the fused pass).
- * tami_forward_backward can run a kernel written out for the diagram's own table -- every table
- * index a constant, every per-sample array a set of registers -- instead of the generic kernel,
- * which reads the table from shared memory and keeps per-sample arrays in local memory.  It is
- * generated as CUDA C++ on the first call that takes it, compiled for sm_103a with NVRTC (loaded
- * at run time: libnvrtc.so.13, or $TAMI_NVRTC) and cached with the diagram until tami_destroy.
- * Values agree with the generic kernel to rounding.
+/* Specialised kernels (no counterpart in the paper: how this library runs its Monte Carlo calls).
+ * tami_forward, tami_backward and tami_forward_backward can each run a kernel written out for the
+ * diagram's own table -- every table index a constant, every per-sample array a set of registers
+ * -- instead of the generic kernel, which reads the table from shared memory and keeps per-sample
+ * arrays in local memory.  Each is generated as CUDA C++ on the first call that takes it, compiled
+ * for sm_103a with NVRTC (loaded at run time: libnvrtc.so.13, or $TAMI_NVRTC) and cached with the
+ * diagram until tami_destroy.  Values agree with the generic kernels to rounding; workspaces and
+ * outputs are those of the generic calls.  tami_forward_noalloc, energy input and batches always
+ * run the generic kernels.
  *   mode TAMI_JIT_NEVER   the generic kernel always;
  *        TAMI_JIT_AUTO    (default; $TAMI_JIT = never | auto | always sets the initial mode) the
  *                         specialised kernel for launches of at least 2^21 samples when the table
@@ -285,17 +287,19 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
 enum { TAMI_JIT_NEVER = 0, TAMI_JIT_AUTO = 1, TAMI_JIT_ALWAYS = 2 };
 int tami_set_jit(int mode);
 
-/* Build the specialised kernel of an uploaded diagram now (for its upload device).  TAMI_EUNSUPPORTED
- * when the table is outside the generator's limits or NVRTC is missing or fails. */
+/* Build the three specialised kernels of an uploaded diagram now (for its upload device).
+ * TAMI_EUNSUPPORTED when the table is outside the generator's limits or NVRTC is missing or fails. */
 int tami_jit_prepare(tami_diagram* d);
 
-/* ready: the kernel is built; last_used: the diagram's last tami_forward_backward ran it (1) or the
- * generic kernel (0); compile_ms: host time of its generation and compilation. */
+/* ready: bit mask of the built kernels (1 fused, 2 forward, 4 adjoint); last_used: the diagram's last
+ * evaluating Monte Carlo call ran a specialised kernel (1) or a generic one (0); compile_ms: host time
+ * of their generation and compilation. */
 int tami_jit_status(const tami_diagram* d, int* ready, int* last_used, double* compile_ms);
 
-/* The generated CUDA C++ source (host memory, NUL-terminated, truncated to cap bytes); *len is the
- * full size including the NUL.  For inspection and tests. */
-int tami_jit_source(const tami_diagram* d, char* buf, size_t cap, size_t* len);
+/* The generated CUDA C++ source of one kind (0 fused, 1 forward, 2 adjoint), in host memory,
+ * NUL-terminated, truncated to cap bytes; *len is the full size including the NUL.  For inspection
+ * and tests. */
+int tami_jit_source(const tami_diagram* d, int kind, char* buf, size_t cap, size_t* len);
 
 /* Many diagrams in one persistent launch (the paper evaluates one diagram per call; this batches
  * them).  Each diagram d gets samples[d] Philox samples with key seeds[d] (counter offset 0), the

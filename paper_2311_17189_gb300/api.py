@@ -92,23 +92,28 @@ class Diagram:
         return f"cuda:{self.device}"
 
     def jit_prepare(self):
-        """Build the specialised fused kernel of this uploaded diagram now (tami_jit_prepare)."""
+        """Build the specialised kernels of this uploaded diagram now (tami_jit_prepare)."""
         torch = _torch()
         with torch.cuda.device(self.device):
             L.check(L.lib().tami_jit_prepare(self._h))
 
+    JIT_KINDS = {"fused": 0, "forward": 1, "adjoint": 2}
+
     def jit_status(self):
-        """dict(ready, last_used, compile_ms) of the specialised fused kernel (tami_jit_status)."""
+        """Specialised kernels (tami_jit_status): ready = set of built kinds ('fused', 'forward',
+        'adjoint'), last_used = whether the last Monte Carlo call ran one, compile_ms."""
         r, u, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         L.check(L.lib().tami_jit_status(self._h, ctypes.byref(r), ctypes.byref(u), ctypes.byref(ms)))
-        return {"ready": bool(r.value), "last_used": bool(u.value), "compile_ms": ms.value}
+        ready = {k for k, b in self.JIT_KINDS.items() if r.value & (1 << b)}
+        return {"ready": ready, "last_used": bool(u.value), "compile_ms": ms.value}
 
-    def jit_source(self):
-        """The CUDA C++ source of the specialised fused kernel (tami_jit_source)."""
+    def jit_source(self, kind="fused"):
+        """The CUDA C++ source of one specialised kernel (tami_jit_source)."""
+        k = self.JIT_KINDS[kind]
         n = ctypes.c_size_t()
-        L.check(L.lib().tami_jit_source(self._h, None, 0, ctypes.byref(n)))
+        L.check(L.lib().tami_jit_source(self._h, k, None, 0, ctypes.byref(n)))
         buf = ctypes.create_string_buffer(n.value)
-        L.check(L.lib().tami_jit_source(self._h, buf, n.value, ctypes.byref(n)))
+        L.check(L.lib().tami_jit_source(self._h, k, buf, n.value, ctypes.byref(n)))
         return buf.value.decode()
 
     def upload(self, device=None):

@@ -550,26 +550,37 @@ int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed,
   if (grid < 0) { set_error("term table and frequencies exceed shared memory"); return TAMI_EUNSUPPORTED; }
   const size_t need = kBwStatusBytes + sizeof(double) * (size_t)bwd_nval(n_f, false) * (size_t)grid;
   if (workspace_bytes < need) { set_error("workspace too small"); return TAMI_EINVAL; }
+  tami_diagram* dm = const_cast<tami_diagram*>(d);
+  const int sel = jit_select(dm, kJitKindBwd, n_samples, n_f);
+  if (sel < 0) return -sel;
   cudaStream_t st = (cudaStream_t)stream;
   int* status = static_cast<int*>(workspace);
   double* partial = reinterpret_cast<double*>(static_cast<char*>(workspace) + kBwStatusBytes);
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-  BwdParams P;
-  std::memset(&P, 0, sizeof(P));
-  P.h = d->hdr;
-  P.table = static_cast<const unsigned char*>(d->d_blob);
-  P.t = lat->t; P.tp = lat->tp; P.mu = lat->mu; P.kx = lat->kx_ext; P.ky = lat->ky_ext;
-  P.seed = seed; P.offset = offset; P.n = n_samples;
-  P.X = X; P.G = gout; P.n_f = n_f; P.beta = beta;
-  P.ps_dX = per_sample_dX; P.ps_grad = per_sample_grads;
-  P.saved = saved;
-  P.partial = partial; P.status = status;
-  if (saved) bwd_kernel<true, false><<<grid, kBlock, smem, st>>>(P);
-  else bwd_kernel<false, false><<<grid, kBlock, smem, st>>>(P);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "bwd_kernel launch");
-  bwd_finalize_kernel<<<n_f + 1, kFinBlock, 0, st>>>(partial, grid, n_f, n_samples, gout, status,
+  int used_grid = grid;
+  if (sel == 1) {
+    rc = jit_launch(dm, kJitKindBwd, lat, seed, offset, n_samples, X, n_f, beta, gout, nullptr, per_sample_dX,
+                    per_sample_grads, const_cast<double*>(saved), partial, grid, st, &used_grid);
+    if (rc) return rc;
+  } else {
+    jit_mark_generic(dm);
+    BwdParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.h = d->hdr;
+    P.table = static_cast<const unsigned char*>(d->d_blob);
+    P.t = lat->t; P.tp = lat->tp; P.mu = lat->mu; P.kx = lat->kx_ext; P.ky = lat->ky_ext;
+    P.seed = seed; P.offset = offset; P.n = n_samples;
+    P.X = X; P.G = gout; P.n_f = n_f; P.beta = beta;
+    P.ps_dX = per_sample_dX; P.ps_grad = per_sample_grads;
+    P.saved = saved;
+    P.partial = partial; P.status = status;
+    if (saved) bwd_kernel<true, false><<<grid, kBlock, smem, st>>>(P);
+    else bwd_kernel<false, false><<<grid, kBlock, smem, st>>>(P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "bwd_kernel launch");
+  }
+  bwd_finalize_kernel<<<n_f + 1, kFinBlock, 0, st>>>(partial, used_grid, n_f, n_samples, gout, status,
                                                               dsigma_dX, grad_X_re, grad_params);
   e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "bwd finalize launch");
@@ -592,7 +603,7 @@ int tami_forward_backward(const tami_diagram* d, const tami_lattice* lat, uint64
   if (workspace_bytes < need) { set_error("workspace too small"); return TAMI_EINVAL; }
   // the diagram's specialised kernel (compiled once and cached with it) or the generic one
   tami_diagram* dm = const_cast<tami_diagram*>(d);
-  const int sel = jit_select(dm, n_samples, n_f);
+  const int sel = jit_select(dm, kJitKindFused, n_samples, n_f);
   if (sel < 0) return -sel;
   cudaStream_t st = (cudaStream_t)stream;
   int* status = static_cast<int*>(workspace);
@@ -601,8 +612,8 @@ int tami_forward_backward(const tami_diagram* d, const tami_lattice* lat, uint64
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   int used_grid = grid;
   if (sel == 1) {
-    rc = jit_launch_fused(dm, lat, seed, offset, n_samples, X, n_f, beta, gout, per_sample, per_sample_dX,
-                          per_sample_grads, partial, grid, st, &used_grid);
+    rc = jit_launch(dm, kJitKindFused, lat, seed, offset, n_samples, X, n_f, beta, gout, per_sample, per_sample_dX,
+                    per_sample_grads, nullptr, partial, grid, st, &used_grid);
     if (rc) return rc;
   } else {
     jit_mark_generic(dm);

@@ -330,22 +330,33 @@ int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, 
   const int grid = grid_for(d, n_f, n_samples);
   const size_t need = kStatusBytes + sizeof(double) * 4 * (size_t)n_f * (size_t)grid;
   if (workspace_bytes < need) { set_error("workspace too small"); return TAMI_EINVAL; }
+  tami_diagram* dm = const_cast<tami_diagram*>(d);
+  const int sel = jit_select(dm, kJitKindFwd, n_samples, n_f);
+  if (sel < 0) return -sel;
   cudaStream_t st = (cudaStream_t)stream;
   int* status = static_cast<int*>(workspace);
   double* partial = reinterpret_cast<double*>(static_cast<char*>(workspace) + kStatusBytes);
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-  FwdParams P = make_params(d, n_f, beta);
-  P.t = lat->t; P.tp = lat->tp; P.mu = lat->mu; P.kx = lat->kx_ext; P.ky = lat->ky_ext;
-  P.seed = seed; P.offset = offset; P.n = n_samples;
-  P.X = X;
-  P.per_sample = per_sample;
-  P.saved = saved;
-  P.partial = partial;
-  P.status = status;
-  rc = saved ? launch_fwd<false, true>(d, P, st, grid) : launch_fwd<false, false>(d, P, st, grid);
-  if (rc) return rc;
-  finalize_kernel<<<n_f, kFinBlock, 0, st>>>(partial, grid, n_f, n_samples, status, mean, var);
+  int used_grid = grid;
+  if (sel == 1) {
+    rc = jit_launch(dm, kJitKindFwd, lat, seed, offset, n_samples, X, n_f, beta, nullptr, per_sample, nullptr,
+                    nullptr, saved, partial, grid, st, &used_grid);
+    if (rc) return rc;
+  } else {
+    jit_mark_generic(dm);
+    FwdParams P = make_params(d, n_f, beta);
+    P.t = lat->t; P.tp = lat->tp; P.mu = lat->mu; P.kx = lat->kx_ext; P.ky = lat->ky_ext;
+    P.seed = seed; P.offset = offset; P.n = n_samples;
+    P.X = X;
+    P.per_sample = per_sample;
+    P.saved = saved;
+    P.partial = partial;
+    P.status = status;
+    rc = saved ? launch_fwd<false, true>(d, P, st, grid) : launch_fwd<false, false>(d, P, st, grid);
+    if (rc) return rc;
+  }
+  finalize_kernel<<<n_f, kFinBlock, 0, st>>>(partial, used_grid, n_f, n_samples, status, mean, var);
   e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "finalize launch");
 }

@@ -722,17 +722,37 @@ int flatten(tami_diagram* d) {
   I.table_bytes = h.bytes;
   I.saved_rows = h.n_rep + 2 * h.n_rep_ext;
   I.n_ext = n_ext;
-  // Counts follow the kernel: fma = 2 flops, mul/add = 1, the reciprocal (estimate + one
-  // third-order Newton step) = 3 fma, the table-driven exponential 10 fma + 3 add/mul.
+  // Algorithmic flops of the evaluation, per sample and per (sample, frequency): fma = 2, mul or
+  // add = 1, a multiplication by +-1 or an addition to an exact 0 is free (the tables' integer
+  // coefficients are mostly +-1; a kernel that multiplies by them anyway does no useful work
+  // there), the reciprocal (estimate + one third-order Newton step) 6, the table-driven exponential
+  // 10 fma + 3 (e^t - 1: 2 more), cos 30 (reduction 9, series 21), sin 21.  Per frequency the count
+  // is that of the imaginary axis; off it the kernels add one more add per complex denominator.
+  auto unit = [](double c) { return c == 1.0 || c == -1.0; };
+  auto lin = [&](const std::vector<double>& cs) {     // sum_i c_i y_i as an fma chain from 0
+    double f = 0.0;
+    for (size_t i = 0; i < cs.size(); ++i) f += i == 0 ? (unit(cs[i]) ? 0.0 : 1.0) : (unit(cs[i]) ? 1.0 : 2.0);
+    return f;
+  };
   double fl = 0.0;
   fl += 2.0 * 2 * m;                                    // u -> k: one fma per component
-  fl += 2.0 * 2.0 * n_lm;                               // line momenta, fma per nonzero label and dimension
-  fl += h.n_rep * (2.0 * 30.0 + 6.0);                   // cos of both components (reduction 9, series 21), energy
+  for (int j : repl) {                                  // line momenta, both components
+    std::vector<double> cs;
+    for (int l = 0; l < nv; ++l) if (d->alpha[j * nv + l]) cs.push_back((double)d->alpha[j * nv + l]);
+    fl += 2.0 * lin(cs);
+  }
+  fl += h.n_rep * (2.0 * 30.0 + 6.0);                   // cos of both components, energy
   const double energy_flops = fl;                       // what a saved-rows adjoint does not redo
   const double ext_grad_flops = h.n_rep_ext * 2.0 * (21.0 + 3.0);   // sin and G = (2t + 4t' cos) sin per component
-  fl += 2.0 * nnz;                                      // energy combinations
+  double combo_fl = 0.0;                                // energy combinations
+  for (const Vec& c : combos) {
+    std::vector<double> cs;
+    for (int j = 0; j < N; ++j) if (c[j]) cs.push_back((double)c[j]);
+    combo_fl += lin(cs);
+  }
+  fl += combo_fl;
   for (const Seg& g : segs) {
-    fl += 1.0 + 23.0 + (g.sigma < 0 ? 2.0 : 0.0);       // -beta|x|; e^t (10 fma, 3 add/mul); e^t - 1
+    fl += 1.0 + 23.0 + (g.sigma < 0 ? 2.0 : 0.0);       // -beta|x|; e^t; e^t - 1
     fl += 8.0;                                          // D, reciprocal, +-y / D
     for (int v = g.v0; v < g.v1; ++v) {
       const int k = fvs[v].k;
@@ -740,42 +760,55 @@ int flatten(tami_diagram* d) {
     }
   }
   fl += 6.0 * h.n_rden;                                 // real reciprocals
-  fl += 2.0 * n_mul_ops;                                // pole-tree program: one fma per edge
+  double dag_fwd = 0.0, dag_bwd = 0.0;                  // pole DAG: one fma per edge, forward and adjoint
+  for (const auto& op : opsb) {
+    const bool first = op.first & kOpbFirst, leaf = op.first & kOpbLeaf;
+    const bool one = leaf && unit(leafA[op.first >> kOpbRefShift]);
+    dag_fwd += first ? (one ? 0.0 : 1.0) : (one ? 1.0 : 2.0);
+    dag_bwd += leaf ? (one ? 1.0 : 2.0) : 4.0;          // Fbar += A bar (leaf) | Fbar += v bar, bar_c += F bar
+  }
+  fl += dag_fwd;
   for (auto& g : g1s) {
     for (auto& pr : g.rd) fl += pr.second;              // frequency-independent denominators
     fl += 1.0;
   }
   I.flops_per_sample = fl;
   I.energy_in_flops_per_sample = fl - energy_flops;
-  double ff = 12.0 * h.n_cden;                          // |D|^2, reciprocal, 1/D (+ Re D off the imaginary axis)
+  double ff = 10.0 * h.n_cden;                          // |D|^2, reciprocal, 1/D
   ff += 6.0 * h.n_pnode;                                // complex product per trie node
-  for (auto& g : g2s) ff += g.empty() ? 1.0 : 4.0;      // W R accumulated
+  for (auto& g : g2s) ff += g.empty() ? 0.0 : 4.0;      // W R accumulated (the R = 1 group is a copy)
   ff += 6.0;                                            // mean and variance sums
   I.flops_per_sample_freq = ff;
   // adjoint: the forward's phase 1 again plus the next derivative of every Fermi value, then per
   // frequency the phase-2 products with the adjoint contractions, then the reverse sweep
   double bl = fl;
-  for (const FvKey& k : fvs) bl += k.k + 1 == 1 ? 2.0 : k.k + 1 == 2 ? 5.0 : 9.0 + 3.0 * k.k;
-  bl += 2.0 * h.n_cden;                                 // cden adjoints into combinations
+  for (const Seg& g : segs) {                           // next derivative of every Fermi value
+    if (g.vk1 > g.v0) bl += 2.0;                        // -beta g h, shared by the segment's k = 0 values
+    for (int v = g.vk1; v < g.v1; ++v) bl += fvs[v].k + 1 == 2 ? 5.0 : 9.0 + 3.0 * fvs[v].k;
+  }
+  bl += h.n_cden;                                       // cden adjoints into combinations
   for (auto& g : g1s) {
-    for (auto& pr : g.rd) bl += pr.second + 4.0;        // RR and the real-denominator adjoint
+    for (auto& pr : g.rd) bl += pr.second + (pr.second == 1 ? 3.0 : 4.0);   // RR and the real-denominator adjoint
     bl += 1.0;
   }
-  // pole tree in the adjoint (the forward pass is counted in fl): per edge an fma into the
-  // Fermi-value adjoint and, for inner edges, an fma into the child's adjoint
-  bl += 2.0 * ops.size() + 2.0 * n_inner;
+  bl += dag_bwd;
   bl += h.n_rep_ext * 2.0 * 21.0;                       // sin of both components where k_ext enters (series)
-  bl += ng2cd;                                          // p W per group factor
-  bl += 3.0 * h.n_fv + 2.0 * nnz + h.n_rep + 10.0 * h.n_rep_ext;   // fvbar -> x -> E -> (mu, k_ext)
+  for (auto& g : g2s) for (auto& pr : g) bl += pr.second == 1 ? 0.0 : 1.0;   // p W per group factor
+  bl += 2.0 * h.n_fv + h.n_fseg;                        // fvbar P_{k+1} summed per segment into x
+  bl += combo_fl;                                       // x -> E (the same coefficients)
+  bl += h.n_rep;                                        // E -> mu
+  for (int r = 0; r < h.n_rep_ext; ++r)                 // E -> k_ext: (-Ebar a_ext) G per component
+    bl += 4.0 + (unit((double)d->alpha[repl[r] * nv + m]) ? 0.0 : 1.0);
   I.bwd_flops_per_sample = bl;
   I.fwd_save_flops_per_sample = I.flops_per_sample + ext_grad_flops;
   I.bwd_saved_flops_per_sample = bl - energy_flops - ext_grad_flops;
-  double bf = 12.0 * h.n_cden + 12.0 * h.n_cden + 2.0;  // reciprocals, Z, dv/dX and b-adjoints, accX
+  double bf = 10.0 * h.n_cden + 2.0;                    // reciprocals, dv/dX accumulated
+  for (const CdKey& c : cdens) bf += 6.0 + (unit((double)c.a) ? 2.0 : 4.0) + 4.0;   // Z, dv/dX, b-adjoint
   bf += 6.0 * h.n_pnode;                                // products (trie nodes)
-  for (auto& g : g2s) bf += g.empty() ? 1.0 : 4.0 + 4.0 * g.size();   // Wbar, U += p W R
+  for (auto& g : g2s) bf += g.empty() ? 0.0 : 4.0 + 4.0 * g.size();   // Wbar, U += p W R
   I.bwd_flops_per_sample_freq = bf;
   double fused = bf + 6.0;                              // the forward's sums
-  for (auto& g : g2s) fused += g.empty() ? 1.0 : 4.0;   // W R accumulated
+  for (auto& g : g2s) fused += g.empty() ? 0.0 : 4.0;   // W R accumulated
   I.fused_flops_per_sample_freq = fused;
   return TAMI_OK;
 }

@@ -136,12 +136,15 @@ struct tami_diagram {
 
 namespace tami {
 int flatten(tami_diagram* d);  // terms -> hdr + blob + info
-// Specialised fused kernel (tami_jit.cpp).  jit_select: 1 = launch it for this call (compiled and
-// cached), 0 = the generic kernel, negative = -status (the "always" mode when it cannot be built).
-int jit_select(tami_diagram* d, int64_t n, int n_f);
-int jit_launch_fused(tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset, int64_t n,
-                     const double* X, int n_f, double beta, const double* gout, double* per_sample, double* ps_dX,
-                     double* ps_grad, double* partial, int max_grid, struct CUstream_st* st, int* grid_out);
+// Specialised kernels (tami_jit.cpp), one per kind of evaluating call.  jit_select: 1 = launch the
+// specialised kernel for this call (compiled and cached), 0 = the generic kernel, negative =
+// -status (the "always" mode when it cannot be built).  jit_launch writes the generic kernel's
+// per-block partial layout for that call into `partial` (at most max_grid rows).
+enum { kJitKindFused = 0, kJitKindFwd = 1, kJitKindBwd = 2 };
+int jit_select(tami_diagram* d, int kind, int64_t n, int n_f);
+int jit_launch(tami_diagram* d, int kind, const tami_lattice* lat, uint64_t seed, uint64_t offset, int64_t n,
+               const double* X, int n_f, double beta, const double* gout, double* per_sample, double* ps_dX,
+               double* ps_grad, double* saved, double* partial, int max_grid, struct CUstream_st* st, int* grid_out);
 void jit_mark_generic(tami_diagram* d);
 void jit_release(tami_diagram* d);
 // Checks every index and range of a flattened table (tami_validate.cpp); false with the reason.

@@ -128,8 +128,16 @@ struct Out {
   }
 };
 
-void emit_phase2(Out& o, const Table& t, bool xr_zero) {
+// The three kinds of specialised kernel: the fused forward + adjoint (tami_forward_backward), the
+// forward (tami_forward: mean and variance sums, optional per-sample values and saved rows) and the
+// adjoint (tami_backward: recomputing the energies or reading the saved rows).  Each reduces into the
+// per-block layout of its generic counterpart, whose final reduction kernel finishes it.
+enum { kKindFused = kJitKindFused, kKindFwd = kJitKindFwd, kKindBwd = kJitKindBwd, kKinds = 3 };
+const char* const kKernelName[kKinds] = {"tami_jit_fused", "tami_jit_fwd", "tami_jit_bwd"};
+
+void emit_phase2(Out& o, const Table& t, int kind, bool xr_zero) {
   const TableHeader& h = t.h;
+  const bool fwd = kind != kKindBwd, adj = kind != kKindFwd;
   const int nc = h.n_cden, np = h.n_pnode;
   const int* pnode = t.I(h.off_pnode);
   const int* g2 = t.I(h.off_g2);
@@ -137,42 +145,48 @@ void emit_phase2(Out& o, const Table& t, bool xr_zero) {
   const int* g2node = t.I(h.off_g2node);
   const double* cden_a = t.D(h.off_cden_a);
   o("      for (int f = 0; f < n_f; ++f) {");
-  o("        const double Xr = Xs[2 * f], gr = Gs[2 * f], gim = Gs[2 * f + 1], ngr = -gr, ngi = -gim;");
-  o("        (void)Xr; (void)ngr; (void)ngi;");
+  o("        const double Xr = Xs[2 * f]; (void)Xr;");
+  if (adj) o("        const double gr = Gs[2 * f], gim = Gs[2 * f + 1], ngr = -gr, ngi = -gim; (void)ngr; (void)ngi;");
   for (int c = 0; c < nc; ++c) {
     if (xr_zero) o("        const double Dr%d = b%d;", c, c);
     else o("        const double Dr%d = fma(%s, Xr, b%d);", c, lit(cden_a[c]).c_str(), c);
     o("        const double r%d = rcp(fma(Dr%d, Dr%d, AXI2[%d * n_f + f]));", c, c, c, c);
     o("        const double vre%d = Dr%d * r%d, vim%d = -AXI[%d * n_f + f] * r%d;", c, c, c, c, c, c);
-    o("        double U_re%d = 0.0, U_im%d = 0.0;", c, c);
+    if (adj) o("        double U_re%d = 0.0, U_im%d = 0.0;", c, c);
   }
   for (int k = 0; k < np; ++k) {
     const int src = pnode[2 * k], cc = pnode[2 * k + 1], v = nc + k;
     o("        const double vre%d = fma(vre%d, vre%d, -vim%d * vim%d), vim%d = fma(vre%d, vim%d, vim%d * vre%d);", v, src,
       cc, src, cc, v, src, cc, src, cc);
   }
-  o("        double vr = %s, vi = 0.0;", h.g2_const ? "W2_0" : "0.0");
+  if (fwd) o("        double vr = %s, vi = 0.0;", h.g2_const ? "W2_0" : "0.0");
   for (int g = h.g2_const; g < h.n_g2; ++g) {
     const int v = g2node[g];
-    o("        vr = fma(W2_%d, vre%d, vr); vi = fma(W2_%d, vim%d, vi);", g, v, g, v);
-    o("        Wb2_%d = fma(gr, vre%d, fma(gim, vim%d, Wb2_%d));", g, v, v, g);
-    for (int q = g2[g]; q < g2[g + 1]; ++q) {
-      const int cc = g2cd[2 * q];
-      o("        U_re%d = fma(pW%d, vre%d, U_re%d); U_im%d = fma(pW%d, vim%d, U_im%d);", cc, q, v, cc, cc, q, v, cc);
+    if (fwd) o("        vr = fma(W2_%d, vre%d, vr); vi = fma(W2_%d, vim%d, vi);", g, v, g, v);
+    if (adj) {
+      o("        Wb2_%d = fma(gr, vre%d, fma(gim, vim%d, Wb2_%d));", g, v, v, g);
+      for (int q = g2[g]; q < g2[g + 1]; ++q) {
+        const int cc = g2cd[2 * q];
+        o("        U_re%d = fma(pW%d, vre%d, U_re%d); U_im%d = fma(pW%d, vim%d, U_im%d);", cc, q, v, cc, cc, q, v, cc);
+      }
     }
   }
-  o("        double dvr = 0.0, dvi = 0.0;");
-  for (int c = 0; c < nc; ++c) {
-    o("        { const double Zr = fma(vre%d, U_re%d, -vim%d * U_im%d), Zi = fma(vre%d, U_im%d, vim%d * U_re%d);", c, c, c,
-      c, c, c, c, c);
-    o("          dvr = fma(%s, Zr, dvr); dvi = fma(%s, Zi, dvi); bb%d = fma(ngr, Zr, fma(ngi, Zi, bb%d)); }",
-      lit(-cden_a[c]).c_str(), lit(-cden_a[c]).c_str(), c, c);
+  if (adj) {
+    o("        double dvr = 0.0, dvi = 0.0;");
+    for (int c = 0; c < nc; ++c) {
+      o("        { const double Zr = fma(vre%d, U_re%d, -vim%d * U_im%d), Zi = fma(vre%d, U_im%d, vim%d * U_re%d);", c, c,
+        c, c, c, c, c, c);
+      o("          dvr = fma(%s, Zr, dvr); dvi = fma(%s, Zi, dvi); bb%d = fma(ngr, Zr, fma(ngi, Zi, bb%d)); }",
+        lit(-cden_a[c]).c_str(), lit(-cden_a[c]).c_str(), c, c);
+    }
+    o("        accX[2 * f] += dvr; accX[2 * f + 1] += dvi;");
+    o("        if (ps_dX) reinterpret_cast<double2*>(ps_dX)[(size_t)f * n + s] = make_double2(dvr, dvi);");
   }
-  o("        accX[2 * f] += dvr; accX[2 * f + 1] += dvi;");
-  o("        if (ps_dX) reinterpret_cast<double2*>(ps_dX)[(size_t)f * n + s] = make_double2(dvr, dvi);");
-  o("        accV[4 * f] += vr; accV[4 * f + 1] += vi;");
-  o("        accV[4 * f + 2] = fma(vr, vr, accV[4 * f + 2]); accV[4 * f + 3] = fma(vi, vi, accV[4 * f + 3]);");
-  o("        if (ps_v) reinterpret_cast<double2*>(ps_v)[(size_t)f * n + s] = make_double2(vr, vi);");
+  if (fwd) {
+    o("        accV[4 * f] += vr; accV[4 * f + 1] += vi;");
+    o("        accV[4 * f + 2] = fma(vr, vr, accV[4 * f + 2]); accV[4 * f + 3] = fma(vi, vi, accV[4 * f + 3]);");
+    o("        if (ps_v) reinterpret_cast<double2*>(ps_v)[(size_t)f * n + s] = make_double2(vr, vi);");
+  }
   o("      }");
 }
 
@@ -184,9 +198,10 @@ bool jit_supported(const TableHeader& h, std::string* why) {
   return true;
 }
 
-// CUDA C++ source of the specialised kernel `tami_jit_fused` for one table.
-std::string jit_fused_source(const TableHeader& h, const unsigned char* blob) {
+// CUDA C++ source of the specialised kernel of one kind for one table.
+std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind) {
   const Table t{h, blob};
+  const bool fwd = kind != kKindBwd, adj = kind != kKindFwd;
   const int* repl = t.I(h.off_repl);
   const int* lm_ptr = t.I(h.off_lm_ptr);
   const int* lm_l = t.I(h.off_lm_l);
@@ -208,9 +223,11 @@ std::string jit_fused_source(const TableHeader& h, const unsigned char* blob) {
   const int* g1rd = t.I(h.off_g1rd);
   const int* g2 = t.I(h.off_g2);
   const double* g2cd_p = t.D(h.off_g2cd_p);
+  const char* nval = kind == kKindFused ? "6 * n_f + 3" : kind == kKindBwd ? "2 * n_f + 3" : "4 * n_f";
 
   Out o;
-  o("// generated by libtami for one flattened term table: fused forward + adjoint, one sample per thread");
+  o("// generated by libtami for one flattened term table, one sample per thread: %s",
+    kind == kKindFused ? "forward + adjoint" : kind == kKindFwd ? "forward" : "adjoint");
   o("#include \"tami_devmath.cuh\"");
   o("using namespace tami::dev;");
   if (h.n_cden > 0) {
@@ -218,21 +235,26 @@ std::string jit_fused_source(const TableHeader& h, const unsigned char* blob) {
     for (int c = 0; c < h.n_cden; ++c) a += (c ? ", " : "") + lit(cden_a[c]);
     o("__device__ const double kJitCdenA[%d] = {%s};", h.n_cden, a.c_str());
   }
-  o("extern \"C\" __global__ void __launch_bounds__(%d, 8) tami_jit_fused(double lt, double ltp, double lmu, double lkx,",
-    kJitBlock);
-  o("    double lky, unsigned long long seed, unsigned long long offset, long long n, const double* X, const double* G,");
-  o("    int n_f, double beta, double* ps_dX, double* ps_grad, double* ps_v, double* partial) {");
+  o("extern \"C\" __global__ void __launch_bounds__(%d, 8) %s(double lt, double ltp, double lmu, double lkx, double lky,",
+    kJitBlock, kKernelName[kind]);
+  o("    unsigned long long seed, unsigned long long offset, long long n, const double* X, const double* G, int n_f,");
+  o("    double beta, double* ps_dX, double* ps_grad, double* ps_v, double* saved, double* partial) {");
   o("  extern __shared__ __align__(16) double smem[];");
   o("  const int tid = threadIdx.x;");
   o("  double* Xs = smem; double* Gs = Xs + 2 * n_f; double* AXI = Gs + 2 * n_f; double* AXI2 = AXI + %d * n_f;", h.n_cden);
   o("  double* red = AXI2 + %d * n_f;", h.n_cden);
-  o("  (void)AXI; (void)AXI2;");
-  o("  for (int i = tid; i < 2 * n_f; i += %d) { Xs[i] = X[i]; Gs[i] = G[i]; }", kJitBlock);
-  o("  double accX[%d], accV[%d];", 2 * kJitMaxFreq, 4 * kJitMaxFreq);
-  o("  for (int i = 0; i < 2 * n_f; ++i) accX[i] = 0.0;");
-  o("  for (int i = 0; i < 4 * n_f; ++i) accV[i] = 0.0;");
-  o("  double gmu = 0.0, gkx = 0.0, gky = 0.0;");
-  o("  __shared__ double s_gsum;");
+  o("  (void)AXI; (void)AXI2; (void)G; (void)ps_dX; (void)ps_grad; (void)ps_v; (void)saved;");
+  o("  for (int i = tid; i < 2 * n_f; i += %d) { Xs[i] = X[i]; Gs[i] = %s; }", kJitBlock, adj ? "G[i]" : "0.0");
+  if (adj) {
+    o("  double accX[%d];", 2 * kJitMaxFreq);
+    o("  for (int i = 0; i < 2 * n_f; ++i) accX[i] = 0.0;");
+    o("  double gmu = 0.0, gkx = 0.0, gky = 0.0;");
+    o("  __shared__ double s_gsum;");
+  }
+  if (fwd) {
+    o("  double accV[%d];", 4 * kJitMaxFreq);
+    o("  for (int i = 0; i < 4 * n_f; ++i) accV[i] = 0.0;");
+  }
   o("  __syncthreads();");
   o("  bool xr_zero;");
   o("  {");
@@ -244,14 +266,26 @@ std::string jit_fused_source(const TableHeader& h, const unsigned char* blob) {
     o("    }");
   }
   o("    for (int f = tid; f < n_f; f += %d) nonzero |= Xs[2 * f] != 0.0;", kJitBlock);
-  o("    if (tid == 0) { double g = 0.0; for (int f = 0; f < n_f; ++f) g += Gs[2 * f]; s_gsum = g; }");
+  if (adj) o("    if (tid == 0) { double g = 0.0; for (int f = 0; f < n_f; ++f) g += Gs[2 * f]; s_gsum = g; }");
   o("    xr_zero = !__syncthreads_or(nonzero);");
   o("  }");
   o("  const long long n_tiles = (n + %d) / %d;", kJitBlock - 1, kJitBlock);
   o("  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {");
   o("    const long long s = tile * %d + tid;", kJitBlock);
   o("    if (s >= n) continue;");
-  // ---- momenta, line energies
+  // ---- line energies: from the momenta, or (adjoint) from the forward's saved rows
+  for (int r = 0; r < h.n_rep; ++r) o("    double E%d;", repl[r]);
+  if (adj) for (int r = 0; r < h.n_rep_ext; ++r) o("    double Gx%d, Gy%d;", r, r);
+  if (kind == kKindBwd) {
+    o("    if (saved) {");
+    for (int r = 0; r < h.n_rep; ++r) o("      E%d = saved[(size_t)%d * n + s];", repl[r], r);
+    for (int r = 0; r < h.n_rep_ext; ++r)
+      o("      Gx%d = saved[(size_t)%d * n + s]; Gy%d = saved[(size_t)%d * n + s];", r, h.n_rep + 2 * r, r,
+        h.n_rep + 2 * r + 1);
+    o("    } else {");
+  } else {
+    o("    {");
+  }
   o("    const unsigned long long sg = offset + (unsigned long long)s;");
   for (int l = 0; l < h.m; ++l) {
     o("    double kx%d, ky%d;", l, l);
@@ -259,27 +293,36 @@ std::string jit_fused_source(const TableHeader& h, const unsigned char* blob) {
     o("      philox4x32_10(c, (unsigned int)seed, (unsigned int)(seed >> 32));");
     o("      kx%d = to_momentum(c[0], c[1]); ky%d = to_momentum(c[2], c[3]); }", l, l);
   }
-  o("    const double kx%d = lkx, ky%d = lky;", h.m, h.m);
-  o("    (void)kx%d; (void)ky%d;", h.m, h.m);
+  o("    const double kx%d = lkx, ky%d = lky; (void)kx%d; (void)ky%d;", h.m, h.m, h.m, h.m);
   for (int r = 0; r < h.n_rep; ++r) {
     const int j = repl[r];
     o("    double ax%d = 0.0, ay%d = 0.0;", r, r);
     for (int q = lm_ptr[r]; q < lm_ptr[r + 1]; ++q)
       o("    ax%d = fma(%s, kx%d, ax%d); ay%d = fma(%s, ky%d, ay%d);", r, lit(lm_c[q]).c_str(), lm_l[q], r, r,
         lit(lm_c[q]).c_str(), lm_l[q], r);
-    if (r < h.n_rep_ext)
-      o("    double Gx%d, Gy%d; const double E%d = line_energy_grad(ax%d, ay%d, lt, ltp, lmu, Gx%d, Gy%d);", r, r, j, r,
-        r, r, r);
-    else
-      o("    const double E%d = line_energy(ax%d, ay%d, lt, ltp, lmu);", j, r, r);
+    if (r < h.n_rep_ext && adj) {
+      o("    E%d = line_energy_grad(ax%d, ay%d, lt, ltp, lmu, Gx%d, Gy%d);", j, r, r, r, r);
+    } else if (r < h.n_rep_ext) {   // forward: the dE/dK factors only when the rows are saved (same E bits)
+      o("    if (saved) { double gx, gy; E%d = line_energy_grad(ax%d, ay%d, lt, ltp, lmu, gx, gy);", j, r, r);
+      o("      saved[(size_t)%d * n + s] = gx; saved[(size_t)%d * n + s] = gy; }", h.n_rep + 2 * r, h.n_rep + 2 * r + 1);
+      o("    else E%d = line_energy(ax%d, ay%d, lt, ltp, lmu);", j, r, r);
+    } else {
+      o("    E%d = line_energy(ax%d, ay%d, lt, ltp, lmu);", j, r, r);
+    }
   }
+  if (kind == kKindFwd) {
+    o("    if (saved) {");
+    for (int r = 0; r < h.n_rep; ++r) o("      saved[(size_t)%d * n + s] = E%d;", r, repl[r]);
+    o("    }");
+  }
+  o("    }");
   // ---- energy combinations
   for (int u = 0; u < h.n_combo; ++u) {
     o("    double x%d = 0.0;", u);
     for (int q = combo_ptr[u]; q < combo_ptr[u + 1]; ++q)
       o("    x%d = fma(%s, E%d, x%d);", u, lit(combo_c[q]).c_str(), combo_j[q], u);
   }
-  // ---- Fermi/Bose values and their next derivatives, segment by segment
+  // ---- Fermi/Bose values (and, for the adjoint, their next derivatives), segment by segment
   for (int b = 0; b < h.n_fseg; ++b) {
     const int* sgm = fseg + 8 * b;
     const bool bose = b < h.n_fseg_bose;
@@ -289,14 +332,18 @@ std::string jit_fused_source(const TableHeader& h, const unsigned char* blob) {
     o("      const double rD = rcp(%s);", bose ? "-em" : "1.0 + y");
     o("      const double t2 = (%s) * rD;", bose ? "-y" : "y");
     o("      const bool neg = __double_as_longlong(xv) <= 0;");
-    o("      sg%d_g = neg ? rD : t2; sg%d_h = neg ? t2 : rD; sg%d_d1 = -beta * (sg%d_g * sg%d_h); }", b, b, b, b, b);
-    for (int v = sgm[2]; v < sgm[3]; ++v)
-      o("    const double fv%d = sg%d_%c, fvd%d = sg%d_d1;", v, b, fvr[2 * v] > 0 ? 'g' : 'h', v, b);
+    o("      sg%d_g = neg ? rD : t2; sg%d_h = neg ? t2 : rD; sg%d_d1 = %s; }", b, b, b,
+      adj ? ("-beta * (sg" + std::to_string(b) + "_g * sg" + std::to_string(b) + "_h)").c_str() : "0.0");
+    for (int v = sgm[2]; v < sgm[3]; ++v) {
+      o("    const double fv%d = sg%d_%c;", v, b, fvr[2 * v] > 0 ? 'g' : 'h');
+      if (adj) o("    const double fvd%d = sg%d_d1;", v, b);
+    }
     for (int v = sgm[3]; v < sgm[4]; ++v) {
       const bool pos = fvr[2 * v] > 0;
       const int k = fvr[2 * v + 1];
-      o("    const double fv%d = fermi_poly(%d, sg%d_%c, sg%d_%c, beta), fvd%d = fermi_poly(%d, sg%d_%c, sg%d_%c, beta);", v,
-        k, b, pos ? 'g' : 'h', b, pos ? 'h' : 'g', v, k + 1, b, pos ? 'g' : 'h', b, pos ? 'h' : 'g');
+      const char g = pos ? 'g' : 'h', hh = pos ? 'h' : 'g';
+      o("    const double fv%d = fermi_poly(%d, sg%d_%c, sg%d_%c, beta);", v, k, b, g, b, hh);
+      if (adj) o("    const double fvd%d = fermi_poly(%d, sg%d_%c, sg%d_%c, beta);", v, k + 1, b, g, b, hh);
     }
   }
   for (int i = 0; i < h.n_rden; ++i) o("    const double rr%d = rcp(x%d);", i, rden[2 * i]);
@@ -319,78 +366,90 @@ std::string jit_fused_source(const TableHeader& h, const unsigned char* blob) {
     o("    W2_%d += W1_%d;", g1_tgt[gi], gi);
   }
   for (int c = 0; c < h.n_cden; ++c) o("    const double b%d = %sx%d;", c, cden[2 * c + 1] > 0 ? "" : "-", cden[2 * c]);
-  for (int g = 0; g < h.n_g2; ++g) {
-    o("    double Wb2_%d = 0.0;", g);
-    for (int q = g2[g]; q < g2[g + 1]; ++q) o("    const double pW%d = %s * W2_%d;", q, lit(g2cd_p[q]).c_str(), g);
+  if (adj) {
+    for (int g = 0; g < h.n_g2; ++g) {
+      o("    double Wb2_%d = 0.0;", g);
+      for (int q = g2[g]; q < g2[g + 1]; ++q) o("    const double pW%d = %s * W2_%d;", q, lit(g2cd_p[q]).c_str(), g);
+    }
+    for (int c = 0; c < h.n_cden; ++c) o("    double bb%d = 0.0;", c);
   }
-  for (int c = 0; c < h.n_cden; ++c) o("    double bb%d = 0.0;", c);
   // ---- phase 2 over frequencies
   o("    if (xr_zero) {");
-  emit_phase2(o, t, true);
+  emit_phase2(o, t, kind, true);
   o("    } else {");
-  emit_phase2(o, t, false);
+  emit_phase2(o, t, kind, false);
   o("    }");
-  if (h.g2_const) o("    Wb2_0 = s_gsum;");
-  // ---- reverse sweep
-  for (int u = 0; u < h.n_combo; ++u) o("    double xbar%d = 0.0;", u);
-  for (int v = 0; v < h.n_fv; ++v) o("    double fvbar%d = 0.0;", v);
-  for (int c = 0; c < h.n_cden; ++c) o("    xbar%d += %sbb%d;", cden[2 * c], cden[2 * c + 1] > 0 ? "" : "-", c);
-  for (int gi = h.n_g1 - 1; gi >= 0; --gi) {
-    o("    {");
-    o("      const double wb = Wb2_%d; double RR = 1.0;", g1_tgt[gi]);
-    for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
-      const int i = g1rd[2 * q], pw = g1rd[2 * q + 1];
-      for (int k = 0; k < pw; ++k) o("      RR *= rr%d;", i);
-      o("      xbar%d -= wb * W1_%d * %s * rr%d;", rden[2 * i], gi, lit((double)pw).c_str(), i);
-    }
-    const int nb = g1_node[gi], ne = g1_node[gi + 1];
-    for (int k = nb + 1; k < ne; ++k) o("      double bar%d = 0.0;", k);
-    o("      double bar%d = wb * RR;", nb);
-    for (int op = g1[4 * gi + 1] - 1; op >= g1[4 * gi];) {
-      const int x = opsb[2 * op], y = opsb[2 * op + 1];
-      const int dst = x & kDstMask;
-      if (x & kOpbLeaf) {
-        int run = (x >> kOpbRunShift) & 255;
-        if (run < 1) run = 1;
-        for (int i = 0; i < run; ++i) {
-          const int qx = opsb[2 * (op - i)], qy = opsb[2 * (op - i) + 1];
-          o("      fvbar%d = fma(%s, bar%d, fvbar%d);", qy, lit(leafA[qx >> kOpbRefShift]).c_str(), dst, qy);
-        }
-        op -= run;
-      } else {
-        const int ref = x >> kOpbRefShift;
-        o("      fvbar%d = fma(val%d, bar%d, fvbar%d); bar%d = fma(fv%d, bar%d, bar%d);", y, ref, dst, y, ref, y, dst, ref);
-        --op;
+  if (adj) {
+    if (h.g2_const) o("    Wb2_0 = s_gsum;");
+    // ---- reverse sweep
+    for (int u = 0; u < h.n_combo; ++u) o("    double xbar%d = 0.0;", u);
+    for (int v = 0; v < h.n_fv; ++v) o("    double fvbar%d = 0.0;", v);
+    for (int c = 0; c < h.n_cden; ++c) o("    xbar%d += %sbb%d;", cden[2 * c], cden[2 * c + 1] > 0 ? "" : "-", c);
+    for (int gi = h.n_g1 - 1; gi >= 0; --gi) {
+      o("    {");
+      o("      const double wb = Wb2_%d; double RR = 1.0;", g1_tgt[gi]);
+      for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
+        const int i = g1rd[2 * q], pw = g1rd[2 * q + 1];
+        for (int k = 0; k < pw; ++k) o("      RR *= rr%d;", i);
+        o("      xbar%d -= wb * W1_%d * %s * rr%d;", rden[2 * i], gi, lit((double)pw).c_str(), i);
       }
+      const int nb = g1_node[gi], ne = g1_node[gi + 1];
+      for (int k = nb + 1; k < ne; ++k) o("      double bar%d = 0.0;", k);
+      o("      double bar%d = wb * RR;", nb);
+      for (int op = g1[4 * gi + 1] - 1; op >= g1[4 * gi];) {
+        const int x = opsb[2 * op], y = opsb[2 * op + 1];
+        const int dst = x & kDstMask;
+        if (x & kOpbLeaf) {
+          int run = (x >> kOpbRunShift) & 255;
+          if (run < 1) run = 1;
+          for (int i = 0; i < run; ++i) {
+            const int qx = opsb[2 * (op - i)], qy = opsb[2 * (op - i) + 1];
+            o("      fvbar%d = fma(%s, bar%d, fvbar%d);", qy, lit(leafA[qx >> kOpbRefShift]).c_str(), dst, qy);
+          }
+          op -= run;
+        } else {
+          const int ref = x >> kOpbRefShift;
+          o("      fvbar%d = fma(val%d, bar%d, fvbar%d); bar%d = fma(fv%d, bar%d, bar%d);", y, ref, dst, y, ref, y, dst,
+            ref);
+          --op;
+        }
+      }
+      o("    }");
     }
-    o("    }");
+    for (int b = 0; b < h.n_fseg; ++b) {
+      const int* sgm = fseg + 8 * b;
+      o("    {");
+      o("      double acc = 0.0;");
+      for (int v = sgm[2]; v < sgm[4]; ++v)
+        o("      { const double dd = fvbar%d * fvd%d; acc += %sdd; }", v, v, fvr[2 * v] > 0 ? "" : "-");
+      o("      xbar%d += acc;", sgm[0]);
+      o("    }");
+    }
+    for (int r = 0; r < h.n_rep; ++r) o("    double Ebar%d = 0.0;", repl[r]);
+    for (int u = 0; u < h.n_combo; ++u)
+      for (int q = combo_ptr[u]; q < combo_ptr[u + 1]; ++q)
+        o("    Ebar%d = fma(xbar%d, %s, Ebar%d);", combo_j[q], u, lit(combo_c[q]).c_str(), combo_j[q]);
+    o("    double mub = 0.0, kxb = 0.0, kyb = 0.0;");
+    for (int r = 0; r < h.n_rep; ++r) o("    mub += Ebar%d;", repl[r]);
+    for (int r = 0; r < h.n_rep_ext; ++r)
+      o("    { const double eb = Ebar%d, ae = %s; kxb = fma(-eb * ae, Gx%d, kxb); kyb = fma(-eb * ae, Gy%d, kyb); }",
+        repl[r], lit(rep_aext[r]).c_str(), r, r);
+    o("    gmu += mub; gkx += kxb; gky += kyb;");
+    o("    if (ps_grad) { ps_grad[3 * s] = mub; ps_grad[3 * s + 1] = kxb; ps_grad[3 * s + 2] = kyb; }");
   }
-  for (int b = 0; b < h.n_fseg; ++b) {
-    const int* sgm = fseg + 8 * b;
-    o("    {");
-    o("      double acc = 0.0;");
-    for (int v = sgm[2]; v < sgm[4]; ++v)
-      o("      { const double dd = fvbar%d * fvd%d; acc += %sdd; }", v, v, fvr[2 * v] > 0 ? "" : "-");
-    o("      xbar%d += acc;", sgm[0]);
-    o("    }");
-  }
-  for (int r = 0; r < h.n_rep; ++r) o("    double Ebar%d = 0.0;", repl[r]);
-  for (int u = 0; u < h.n_combo; ++u)
-    for (int q = combo_ptr[u]; q < combo_ptr[u + 1]; ++q)
-      o("    Ebar%d = fma(xbar%d, %s, Ebar%d);", combo_j[q], u, lit(combo_c[q]).c_str(), combo_j[q]);
-  o("    double mub = 0.0, kxb = 0.0, kyb = 0.0;");
-  for (int r = 0; r < h.n_rep; ++r) o("    mub += Ebar%d;", repl[r]);
-  for (int r = 0; r < h.n_rep_ext; ++r)
-    o("    { const double eb = Ebar%d, ae = %s; kxb = fma(-eb * ae, Gx%d, kxb); kyb = fma(-eb * ae, Gy%d, kyb); }",
-      repl[r], lit(rep_aext[r]).c_str(), r, r);
-  o("    gmu += mub; gkx += kxb; gky += kyb;");
-  o("    if (ps_grad) { ps_grad[3 * s] = mub; ps_grad[3 * s + 1] = kxb; ps_grad[3 * s + 2] = kyb; }");
   o("  }");
-  // ---- block reduction: the generic kernel's layout [grid][nval], nval = 6 n_f + 3
-  o("  const int nval = 6 * n_f + 3, warp = tid >> 5, lane = tid & 31;");
+  // ---- block reduction into the generic kernel's per-block layout
+  o("  const int nval = %s, warp = tid >> 5, lane = tid & 31;", nval);
   o("  for (int i = 0; i < nval; ++i) {");
-  o("    double v = i < 2 * n_f ? accX[i] : (i == 2 * n_f ? gmu : (i == 2 * n_f + 1 ? gkx : gky));");
-  o("    if (i >= 2 * n_f + 3) v = accV[i - 2 * n_f - 3];");
+  if (kind == kKindFused) {
+    o("    double v = i < 2 * n_f ? accX[i] : (i == 2 * n_f ? gmu : (i == 2 * n_f + 1 ? gkx : gky));");
+    o("    if (i >= 2 * n_f + 3) v = accV[i - 2 * n_f - 3];");
+  } else if (kind == kKindBwd) {
+    o("    const double v0 = i < 2 * n_f ? accX[i] : (i == 2 * n_f ? gmu : (i == 2 * n_f + 1 ? gkx : gky));");
+    o("    double v = v0;");
+  } else {
+    o("    double v = accV[i];");
+  }
   o("    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);");
   o("    if (lane == 0) red[warp * nval + i] = v;");
   o("  }");
@@ -405,14 +464,18 @@ std::string jit_fused_source(const TableHeader& h, const unsigned char* blob) {
 }
 
 // --------------------------------------------------------------------------- compile, cache, launch
-struct JitState {
-  std::mutex mu;
-  int device = -1;
+struct JitKernel {
   cudaLibrary_t lib = nullptr;
   cudaKernel_t fn = nullptr;
   double compile_ms = 0.0;
   bool failed = false;
   std::string error;
+};
+
+struct JitState {
+  std::mutex mu;
+  int device = -1;
+  JitKernel k[kKinds];
   int last_used = 0;
 };
 
@@ -425,36 +488,42 @@ JitState* jit_state(tami_diagram* d) {
 void jit_release(tami_diagram* d) {
   if (!d || !d->jit) return;
   JitState* s = static_cast<JitState*>(d->jit);
-  if (s->lib) cudaLibraryUnload(s->lib);
+  for (JitKernel& k : s->k)
+    if (k.lib) cudaLibraryUnload(k.lib);
   delete s;
   d->jit = nullptr;
 }
 
-// Compile (once per diagram and device) the specialised kernel of d's table.
-int jit_prepare(tami_diagram* d) {
+// Compile (once per diagram, kind and device) the specialised kernel of d's table.
+int jit_prepare(tami_diagram* d, int kind) {
   std::string why;
   if (!jit_supported(d->hdr, &why)) { set_error("specialised kernel: " + why); return TAMI_EUNSUPPORTED; }
   JitState* s = jit_state(d);
   std::lock_guard<std::mutex> lk(s->mu);
-  if (s->fn && s->device == d->device) return TAMI_OK;
-  if (s->failed && s->device == d->device) { set_error(s->error); return TAMI_EUNSUPPORTED; }
-  if (s->lib) { cudaLibraryUnload(s->lib); s->lib = nullptr; s->fn = nullptr; }
-  s->device = d->device;
-  s->failed = false;
+  if (s->device != d->device) {          // a new upload device: build again for it
+    for (JitKernel& k : s->k) {
+      if (k.lib) cudaLibraryUnload(k.lib);
+      k = JitKernel{};
+    }
+    s->device = d->device;
+  }
+  JitKernel& K = s->k[kind];
+  if (K.fn) return TAMI_OK;
+  if (K.failed) { set_error(K.error); return TAMI_EUNSUPPORTED; }
   auto fail = [&](const std::string& m) {
-    s->failed = true;
-    s->error = "specialised kernel: " + m;
-    set_error(s->error);
+    K.failed = true;
+    K.error = "specialised kernel: " + m;
+    set_error(K.error);
     return TAMI_EUNSUPPORTED;
   };
   Nvrtc& nv = nvrtc();
   if (!nv.ok) return fail(nv.why);
   const auto t0 = std::chrono::steady_clock::now();
-  const std::string src = jit_fused_source(d->hdr, d->blob.data());
+  const std::string src = jit_source(d->hdr, d->blob.data(), kind);
   const char* hdr_src[1] = {kDevmathSource};
   const char* hdr_name[1] = {"tami_devmath.cuh"};
   void* prog = nullptr;
-  int rc = nv.create(&prog, src.c_str(), "tami_jit_fused.cu", 1, hdr_src, hdr_name);
+  int rc = nv.create(&prog, src.c_str(), "tami_jit.cu", 1, hdr_src, hdr_name);
   if (rc) return fail(std::string("nvrtcCreateProgram: ") + nv.err(rc));
   const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-w"};
   rc = nv.compile(prog, 3, opts);
@@ -471,33 +540,34 @@ int jit_prepare(tami_diagram* d) {
   std::vector<char> cubin(nb);
   nv.cubin(prog, cubin.data());
   nv.destroy(&prog);
-  cudaError_t e = cudaLibraryLoadData(&s->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  cudaError_t e = cudaLibraryLoadData(&K.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
   if (e != cudaSuccess) return fail(std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e));
-  e = cudaLibraryGetKernel(&s->fn, s->lib, "tami_jit_fused");
+  e = cudaLibraryGetKernel(&K.fn, K.lib, kKernelName[kind]);
   if (e != cudaSuccess) return fail(std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e));
-  s->compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  K.compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return TAMI_OK;
 }
 
-// Whether tami_forward_backward takes the specialised kernel for n samples (and compiles it if so).
-// Returns 1 = use it, 0 = generic kernel, or a negative status (the error, in the "always" mode).
-int jit_select(tami_diagram* d, int64_t n, int n_f) {
+// Whether an evaluating call of this kind takes the specialised kernel for n samples (compiling it if
+// so): 1 = use it, 0 = the generic kernel, or -status (the "always" mode when it cannot be built).
+int jit_select(tami_diagram* d, int kind, int64_t n, int n_f) {
   const int mode = jit_mode();
   if (mode == TAMI_JIT_NEVER) return 0;
   if (mode == TAMI_JIT_AUTO && (n < (int64_t(1) << 21) || !jit_supported(d->hdr, nullptr) || n_f > kJitMaxFreq))
     return 0;
   if (n_f > kJitMaxFreq) { set_error("specialised kernel: n_f above 256"); return -TAMI_EUNSUPPORTED; }
-  const int rc = jit_prepare(d);
+  const int rc = jit_prepare(d, kind);
   if (rc == TAMI_OK) return 1;
   return mode == TAMI_JIT_ALWAYS ? -rc : 0;
 }
 
-int jit_launch_fused(tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset, int64_t n,
-                     const double* X, int n_f, double beta, const double* gout, double* per_sample, double* ps_dX,
-                     double* ps_grad, double* partial, int max_grid, struct CUstream_st* st, int* grid_out) {
+int jit_launch(tami_diagram* d, int kind, const tami_lattice* lat, uint64_t seed, uint64_t offset, int64_t n,
+               const double* X, int n_f, double beta, const double* gout, double* per_sample, double* ps_dX,
+               double* ps_grad, double* saved, double* partial, int max_grid, struct CUstream_st* st, int* grid_out) {
   JitState* s = jit_state(d);
-  const size_t smem = sizeof(double) * ((size_t)(4 + 2 * d->hdr.n_cden) * n_f + 4 * (size_t)(6 * n_f + 3));
-  const void* fn = reinterpret_cast<const void*>(s->fn);
+  const int nval = kind == kKindFused ? 6 * n_f + 3 : kind == kKindBwd ? 2 * n_f + 3 : 4 * n_f;
+  const size_t smem = sizeof(double) * ((size_t)(4 + 2 * d->hdr.n_cden) * n_f + 4 * (size_t)nval);
+  const void* fn = reinterpret_cast<const void*>(s->k[kind].fn);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) { set_error(std::string("specialised kernel attribute: ") + cudaGetErrorString(e)); return TAMI_ECUDA; }
   int per_sm = 0, sms = 0;
@@ -514,8 +584,8 @@ int jit_launch_fused(tami_diagram* d, const tami_lattice* lat, uint64_t seed, ui
   int nf = n_f;
   double b = beta;
   const double *Xp = X, *Gp = gout;
-  double *pdx = ps_dX, *pg = ps_grad, *pv = per_sample, *pp = partial;
-  void* args[] = {&lt, &ltp, &lmu, &lkx, &lky, &sd, &off, &nn, &Xp, &Gp, &nf, &b, &pdx, &pg, &pv, &pp};
+  double *pdx = ps_dX, *pg = ps_grad, *pv = per_sample, *sv = saved, *pp = partial;
+  void* args[] = {&lt, &ltp, &lmu, &lkx, &lky, &sd, &off, &nn, &Xp, &Gp, &nf, &b, &pdx, &pg, &pv, &sv, &pp};
   e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kJitBlock), args, smem, st);
   if (e != cudaSuccess) { set_error(std::string("specialised kernel launch: ") + cudaGetErrorString(e)); return TAMI_ECUDA; }
   s->last_used = 1;
@@ -543,23 +613,33 @@ int tami_set_jit(int mode) {
 int tami_jit_prepare(tami_diagram* d) {
   if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
   if (!d->d_blob) { set_error("diagram not uploaded (call tami_upload)"); return TAMI_EINVAL; }
-  return jit_prepare(d);
+  for (int k = 0; k < kKinds; ++k) {
+    const int rc = jit_prepare(d, k);
+    if (rc) return rc;
+  }
+  return TAMI_OK;
 }
 
 int tami_jit_status(const tami_diagram* d, int* ready, int* last_used, double* compile_ms) {
   if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
   const JitState* s = static_cast<const JitState*>(d->jit);
-  if (ready) *ready = s && s->fn ? 1 : 0;
+  int mask = 0;
+  double ms = 0.0;
+  if (s)
+    for (int k = 0; k < kKinds; ++k)
+      if (s->k[k].fn) { mask |= 1 << k; ms += s->k[k].compile_ms; }
+  if (ready) *ready = mask;
   if (last_used) *last_used = s ? s->last_used : 0;
-  if (compile_ms) *compile_ms = s ? s->compile_ms : 0.0;
+  if (compile_ms) *compile_ms = ms;
   return TAMI_OK;
 }
 
-int tami_jit_source(const tami_diagram* d, char* buf, size_t cap, size_t* len) {
+int tami_jit_source(const tami_diagram* d, int kind, char* buf, size_t cap, size_t* len) {
   if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
+  if (kind < 0 || kind >= kKinds) { set_error("kind must be 0 (fused), 1 (forward) or 2 (adjoint)"); return TAMI_EINVAL; }
   std::string why;
   if (!jit_supported(d->hdr, &why)) { set_error("specialised kernel: " + why); return TAMI_EUNSUPPORTED; }
-  const std::string src = jit_fused_source(d->hdr, d->blob.data());
+  const std::string src = jit_source(d->hdr, d->blob.data(), kind);
   if (len) *len = src.size() + 1;
   if (buf && cap > 0) {
     const size_t k = std::min(cap - 1, src.size());

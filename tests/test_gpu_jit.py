@@ -156,3 +156,62 @@ def test_always_mode_refuses_what_the_generator_cannot_build():
     with pytest.raises(L.TamiError) as e:
         D.jit_prepare()
     assert e.value.code == L.TAMI_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_specialised_forward_and_adjoint_against_oracle(case):
+    """The two-call path on the specialised kernels: the forward (keeping the saved rows) against the
+    oracle's values, its saved rows equal to the generic forward's bit for bit, and the adjoint --
+    reading those rows and recomputing -- against the oracle's dual numbers."""
+    D, S, lat, beta, X = setup(case)
+    n, seed, off = 3 * 128 + 37, 13, 2
+    g = upstream(len(X), seed=4)
+    T.set_jit("never")
+    sv_gen = D.saved_buffer(n)
+    D.forward(lat, seed, off, n, X, beta, save=sv_gen)
+    T.set_jit("always")
+    sv = D.saved_buffer(n)
+    mean, var, ps = D.forward(lat, seed, off, n, X, beta, per_sample=True, save=sv)
+    torch.cuda.synchronize()
+    assert D.jit_status()["last_used"] and "forward" in D.jit_status()["ready"]
+    assert torch.equal(sv, sv_gen)
+    ref = S.eval_momenta(lat, seed, off, n, X, beta, per_sample=True, threads=8)
+    v = ps.cpu().numpy()
+    assert np.all(np.abs(v - ref["values"]) <= RTOL * ref["envelope"])
+    scale = np.mean(ref["envelope"], axis=1) + np.mean(np.abs(ref["values"]), axis=1)
+    assert np.all(np.abs(mean.cpu().numpy() - ref["mean"]) <= RTOL * scale)
+    _, dref, denv = S.eval_momenta_deriv(lat, seed, off, n, X, beta, "omega", threads=8, envelope=True)
+    for saved in (sv, None):
+        b = D.backward(lat, seed, off, n, X, beta, g, per_sample=True, saved=saved)
+        torch.cuda.synchronize()
+        assert D.jit_status()["last_used"] and "adjoint" in D.jit_status()["ready"]
+        dX = b["dX"].cpu().numpy()
+        assert np.all(np.abs(dX - dref) <= RTOL * denv), np.max(np.abs(dX - dref) / denv)
+        grads = b["grads"].cpu().numpy()
+        for k, which in enumerate(("mu", "kx", "ky")):
+            _, der, env = S.eval_momenta_deriv(lat, seed, off, n, X, beta, which, threads=8, envelope=True)
+            gref = np.real(np.conj(g)[:, None] * der).sum(axis=0)
+            assert np.all(np.abs(grads[:, k] - gref) <= RTOL * (np.abs(g)[:, None] * env).sum(axis=0)), which
+
+
+def test_specialised_forward_and_adjoint_agree_with_generic():
+    """Bench table, 1e5 samples: reduced forward and adjoint outputs of the specialised kernels
+    against the generic kernels'."""
+    D, S, lat, beta, X = setup(CASES[2])
+    n, seed, off = 100_000, 3, 0
+    g = np.ones(len(X)) + 0.5j
+    out = {}
+    for mode in ("never", "always"):
+        T.set_jit(mode)
+        sv = D.saved_buffer(n)
+        m, v, ps = D.forward(lat, seed, off, n, X, beta, per_sample=True, save=sv)
+        b = D.backward(lat, seed, off, n, X, beta, g, per_sample=True, saved=sv)
+        torch.cuda.synchronize()
+        assert D.jit_status()["last_used"] == (mode == "always")
+        out[mode] = (m, v, ps, b)
+    (m0, v0, p0, b0), (m1, v1, p1, b1) = out["never"], out["always"]
+    scale = p0.abs().mean(dim=1)
+    assert torch.all((m1 - m0).abs() <= 1e-12 * scale)
+    assert torch.allclose(v1, v0, rtol=1e-10, atol=0)
+    assert torch.all((b1["dSigma_dX"] - b0["dSigma_dX"]).abs() <= 1e-12 * b0["dX"].abs().mean(dim=1))
+    assert torch.all((b1["grad_params"] - b0["grad_params"]).abs() <= 1e-12 * b0["grads"].abs().mean(dim=0))

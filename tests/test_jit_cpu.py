@@ -58,13 +58,26 @@ def tables():
     ]
 
 
+KERNEL = {"fused": "tami_jit_fused", "forward": "tami_jit_fwd", "adjoint": "tami_jit_bwd"}
+
+
+@pytest.mark.parametrize("kind", ["fused", "forward", "adjoint"])
 @pytest.mark.parametrize("name,D", tables(), ids=[t[0] for t in tables()])
-def test_generated_kernel_compiles_for_sm103a(name, D):
-    src = D.jit_source()
-    assert "tami_jit_fused" in src and "__launch_bounds__" in src
+def test_generated_kernel_compiles_for_sm103a(name, D, kind):
+    src = D.jit_source(kind)
+    assert KERNEL[kind] in src and "__launch_bounds__" in src
     rc, log, cubin = compile_cubin(src)
     assert rc == 0, log[:3000]
     assert cubin > 0
+
+
+def test_kinds_differ_only_where_they_should():
+    """The forward kernel carries no adjoint sweep, the adjoint no forward sums."""
+    D = tables()[0][1]
+    fwd, adj, fused = D.jit_source("forward"), D.jit_source("adjoint"), D.jit_source("fused")
+    assert "fvbar" not in fwd and "accX" not in fwd and "accV" in fwd
+    assert "accV" not in adj and "fvbar" in adj and "saved[" in adj
+    assert "fvbar" in fused and "accV" in fused
 
 
 FREQ_FREE = [[1, 0], [1, 0]]   # sum_nu G1 G2 with no external frequency: R = 1, one real denominator
@@ -94,3 +107,5 @@ def test_jit_mode_argument_checked():
     assert L.lib().tami_set_jit(3) == L.TAMI_EINVAL
     assert L.lib().tami_set_jit(-1) == L.TAMI_EINVAL
     T.set_jit("auto")
+    with pytest.raises(L.TamiError):
+        L.check(L.lib().tami_jit_source(tables()[0][1]._h, 3, None, 0, None))
