@@ -47,10 +47,12 @@ METRIC = "order-4 Sigma evals/s (samples x terms x frequencies, FP64), forward +
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel from one ncu
 # capture of this workload at 2^22 samples, per sample; every sample does the same work, so a
-# launch's traffic is this times its samples.  It holds only for the kernel sources it was taken
-# on: the hash of the library sources must match, else the bench reports traffic as null.
-TRAFFIC = {"kernel": "bwd_kernel<0,1> (fused forward + adjoint)", "bytes_per_sample": (7.296589e9 + 13.079258e9) / 4194304,
-           "sources_sha256": "075c4984a71c6ab9e9e492f53c652f1de145f87c115ad75e9b64a49d14a62e76", "profile": "profiles/fused_kernel_order4_sigma.md"}
+# launch's traffic is this times its samples.  It holds only for the kernel it was taken on: the
+# kernel the step ran must be that one and the hash of the library sources must match, else the
+# bench reports traffic as null.
+TRAFFIC = {"kernel": "tami_jit_fused (the diagram's specialised fused forward + adjoint)",
+           "bytes_per_sample": (2.108873e9 + 5.040155e9) / 4194304,
+           "sources_sha256": "cc8349bdc4865ff6f5bb76f7af33ba7a0fe7eb8e788aa993d2ed2bf7f3dc612f", "profile": "profiles/jit_kernels_order4_sigma.md"}
 
 
 TRAFFIC_SOURCES = ("paper_2311_17189_gb300/csrc/tami_bwd.cu", "paper_2311_17189_gb300/csrc/tami_device.cuh",
