@@ -442,7 +442,7 @@ def run_workload(args):
             D.eval_energies(E, X, c["beta"])
         launches_per_step = 1
         evals = float(c["n_e"]) * info["n_terms"] * n_f
-        flops = c["n_e"] * (info["energy_in_flops_per_sample"] + n_f * info["flops_per_sample_freq"])
+        flops = c["n_e"] * (info["energy_in_flops_per_sample"] + n_f * info["energy_in_flops_per_sample_freq"])
         bytes_step = c["n_e"] * (8 * c["alpha"].shape[0] + 16 * n_f)
         config = {"workload": c["name"], "rows": c["n_e"], "frequencies": n_f, "terms": info["n_terms"],
                   "beta": c["beta"], "step": "tami_eval_energies, full [n_f][n_e] output"}
@@ -463,7 +463,7 @@ def run_workload(args):
             D.eval_energies(E, X, c["beta"])
         launches_per_step = 1
         evals = float(c["n_e"]) * info["n_terms"] * n_f
-        flops = c["n_e"] * (info["energy_in_flops_per_sample"] + n_f * info["flops_per_sample_freq"])
+        flops = c["n_e"] * (info["energy_in_flops_per_sample"] + n_f * info["energy_in_flops_per_sample_freq"])
         bytes_step = c["n_e"] * (8 * N + 16 * n_f) + n_f * 32
         config = {"workload": c["name"], "rows": c["n_e"], "frequency_rows": n_f, "externals": 2,
                   "terms": info["n_terms"], "beta": c["beta"],

@@ -95,8 +95,10 @@ typedef struct {
   double fused_flops_per_sample_freq;
   int n_ext;                /* external variables (the last n_ext of the n_vars labels)       */
   /* per-row flops of tami_eval_energies (flops_per_sample without the momentum sampling and the
-   * dispersion; per (row, frequency): flops_per_sample_freq) */
+   * dispersion) and per (row, frequency) (flops_per_sample_freq without the Monte Carlo sums,
+   * which energy input does not return) */
   double energy_in_flops_per_sample;
+  double energy_in_flops_per_sample_freq;
 } tami_info;
 
 const char* tami_last_error(void);
@@ -267,19 +269,21 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
                          int64_t n_samples, const double* X, int n_f, double beta, double* mean,
                          double* var, double* per_sample, tami_stream_t stream);
 
-/* Specialised kernels (no counterpart in the paper: how this library runs its Monte Carlo calls).
- * tami_forward, tami_backward and tami_forward_backward can each run a kernel written out for the
- * diagram's own table -- every table index a constant, every per-sample array a set of registers
+/* Specialised kernels (no counterpart in the paper: how this library runs its evaluating calls).
+ * tami_forward, tami_backward, tami_forward_backward and tami_eval_energies can each run a kernel
+ * written out for the diagram's own table -- every table index a constant, every per-sample array a set of registers
  * -- instead of the generic kernel, which reads the table from shared memory and keeps per-sample
  * arrays in local memory.  Each is generated as CUDA C++ on the first call that takes it, compiled
  * for sm_103a with NVRTC (loaded at run time: libnvrtc.so.13, or $TAMI_NVRTC) and cached with the
  * diagram until tami_destroy.  Values agree with the generic kernels to rounding; workspaces and
- * outputs are those of the generic calls.  tami_forward_noalloc, energy input and batches always
- * run the generic kernels.
+ * outputs are those of the generic calls.  tami_forward_noalloc and batches always run the generic
+ * kernels.
  *   mode TAMI_JIT_NEVER   the generic kernel always;
  *        TAMI_JIT_AUTO    (default; $TAMI_JIT = never | auto | always sets the initial mode) the
- *                         specialised kernel for launches of at least 2^21 samples when the table
- *                         is within the generator's limits and NVRTC is there, else the generic one;
+ *                         specialised kernel for Monte Carlo launches of at least 2^21 samples and
+ *                         energy input of at least 2^25 (row, frequency) values, when the table and
+ *                         frequencies are within the generator's limits (Monte Carlo: n_f <= 256)
+ *                         and NVRTC is there, else the generic one;
  *        TAMI_JIT_ALWAYS  the specialised kernel for every launch; a call whose kernel cannot be
  *                         built fails with TAMI_EUNSUPPORTED (message from NVRTC), nothing launched.
  * The mode is process-wide.  Compilation takes about a second and happens on the host inside the
@@ -287,16 +291,17 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
 enum { TAMI_JIT_NEVER = 0, TAMI_JIT_AUTO = 1, TAMI_JIT_ALWAYS = 2 };
 int tami_set_jit(int mode);
 
-/* Build the three specialised kernels of an uploaded diagram now (for its upload device).
+/* Build the specialised kernels that apply to an uploaded diagram now (for its upload device;
+ * several external frequencies: the energy-input one only).
  * TAMI_EUNSUPPORTED when the table is outside the generator's limits or NVRTC is missing or fails. */
 int tami_jit_prepare(tami_diagram* d);
 
-/* ready: bit mask of the built kernels (1 fused, 2 forward, 4 adjoint); last_used: the diagram's last
- * evaluating Monte Carlo call ran a specialised kernel (1) or a generic one (0); compile_ms: host time
- * of their generation and compilation. */
+/* ready: bit mask of the built kernels (1 fused, 2 forward, 4 adjoint, 8 energy input); last_used:
+ * the diagram's last evaluating call ran a specialised kernel (1) or a generic one (0); compile_ms:
+ * host time of their generation and compilation. */
 int tami_jit_status(const tami_diagram* d, int* ready, int* last_used, double* compile_ms);
 
-/* The generated CUDA C++ source of one kind (0 fused, 1 forward, 2 adjoint), in host memory,
+/* The generated CUDA C++ source of one kind (0 fused, 1 forward, 2 adjoint, 3 energy input), in host memory,
  * NUL-terminated, truncated to cap bytes; *len is the full size including the NUL.  For inspection
  * and tests. */
 int tami_jit_source(const tami_diagram* d, int kind, char* buf, size_t cap, size_t* len);

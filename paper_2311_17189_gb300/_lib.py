@@ -55,6 +55,7 @@ class Info(ctypes.Structure):
         ("fused_flops_per_sample_freq", ctypes.c_double),
         ("n_ext", ctypes.c_int),
         ("energy_in_flops_per_sample", ctypes.c_double),
+        ("energy_in_flops_per_sample_freq", ctypes.c_double),
     ]
 
 

@@ -97,11 +97,11 @@ class Diagram:
         with torch.cuda.device(self.device):
             L.check(L.lib().tami_jit_prepare(self._h))
 
-    JIT_KINDS = {"fused": 0, "forward": 1, "adjoint": 2}
+    JIT_KINDS = {"fused": 0, "forward": 1, "adjoint": 2, "energy": 3}
 
     def jit_status(self):
         """Specialised kernels (tami_jit_status): ready = set of built kinds ('fused', 'forward',
-        'adjoint'), last_used = whether the last Monte Carlo call ran one, compile_ms."""
+        'adjoint', 'energy'), last_used = whether the last evaluating call ran one, compile_ms."""
         r, u, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         L.check(L.lib().tami_jit_status(self._h, ctypes.byref(r), ctypes.byref(u), ctypes.byref(ms)))
         ready = {k for k, b in self.JIT_KINDS.items() if r.value & (1 << b)}

@@ -300,6 +300,16 @@ int tami_eval_energies(const tami_diagram* d, const double* E, int64_t n_e, cons
   if (!beta_ok(beta)) return TAMI_EINVAL;
   if (n_e == 0) return TAMI_OK;              // nothing to read or write: E and out may be NULL
   if (!E || !X || !out) { set_error("bad argument"); return TAMI_EINVAL; }
+  tami_diagram* dm = const_cast<tami_diagram*>(d);
+  const int sel = jit_select(dm, kJitKindEnergy, n_e, n_f);
+  if (sel < 0) return -sel;
+  if (sel == 1) {
+    int grid = 0;
+    tami_lattice none{};
+    return jit_launch(dm, kJitKindEnergy, &none, 0, 0, n_e, X, n_f, beta, nullptr, out, nullptr, nullptr,
+                      const_cast<double*>(E), nullptr, 1 << 30, (cudaStream_t)stream, &grid);
+  }
+  jit_mark_generic(dm);
   FwdParams P = make_params(d, n_f, beta);
   P.n = n_e;
   P.E_in = E;

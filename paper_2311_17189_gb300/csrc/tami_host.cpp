@@ -777,6 +777,7 @@ int flatten(tami_diagram* d) {
   double ff = 10.0 * h.n_cden;                          // |D|^2, reciprocal, 1/D
   ff += 6.0 * h.n_pnode;                                // complex product per trie node
   for (auto& g : g2s) ff += g.empty() ? 0.0 : 4.0;      // W R accumulated (the R = 1 group is a copy)
+  I.energy_in_flops_per_sample_freq = ff;              // energy input returns the values only
   ff += 6.0;                                            // mean and variance sums
   I.flops_per_sample_freq = ff;
   // adjoint: the forward's phase 1 again plus the next derivative of every Fermi value, then per

@@ -140,7 +140,7 @@ int flatten(tami_diagram* d);  // terms -> hdr + blob + info
 // specialised kernel for this call (compiled and cached), 0 = the generic kernel, negative =
 // -status (the "always" mode when it cannot be built).  jit_launch writes the generic kernel's
 // per-block partial layout for that call into `partial` (at most max_grid rows).
-enum { kJitKindFused = 0, kJitKindFwd = 1, kJitKindBwd = 2 };
+enum { kJitKindFused = 0, kJitKindFwd = 1, kJitKindBwd = 2, kJitKindEnergy = 3 };
 int jit_select(tami_diagram* d, int kind, int64_t n, int n_f);
 int jit_launch(tami_diagram* d, int kind, const tami_lattice* lat, uint64_t seed, uint64_t offset, int64_t n,
                const double* X, int n_f, double beta, const double* gout, double* per_sample, double* ps_dX,

@@ -132,23 +132,29 @@ struct Out {
 // forward (tami_forward: mean and variance sums, optional per-sample values and saved rows) and the
 // adjoint (tami_backward: recomputing the energies or reading the saved rows).  Each reduces into the
 // per-block layout of its generic counterpart, whose final reduction kernel finishes it.
-enum { kKindFused = kJitKindFused, kKindFwd = kJitKindFwd, kKindBwd = kJitKindBwd, kKinds = 3 };
-const char* const kKernelName[kKinds] = {"tami_jit_fused", "tami_jit_fwd", "tami_jit_bwd"};
+// The energy-input kind (tami_eval_energies) reads each row's base energies instead of sampling
+// momenta, takes any number of external frequencies and writes every (frequency, row) value.
+enum { kKindFused = kJitKindFused, kKindFwd = kJitKindFwd, kKindBwd = kJitKindBwd, kKindEnergy = kJitKindEnergy,
+       kKinds = 4 };
+const char* const kKernelName[kKinds] = {"tami_jit_fused", "tami_jit_fwd", "tami_jit_bwd", "tami_jit_energy"};
 
 void emit_phase2(Out& o, const Table& t, int kind, bool xr_zero) {
   const TableHeader& h = t.h;
-  const bool fwd = kind != kKindBwd, adj = kind != kKindFwd;
+  const bool energy = kind == kKindEnergy;
+  const bool fwd = kind != kKindBwd, adj = kind == kKindFused || kind == kKindBwd;
   const int nc = h.n_cden, np = h.n_pnode;
   const int* pnode = t.I(h.off_pnode);
   const int* g2 = t.I(h.off_g2);
   const int* g2cd = t.I(h.off_g2cd);
   const int* g2node = t.I(h.off_g2node);
   const double* cden_a = t.D(h.off_cden_a);
+  const int* cden_xk = t.I(h.off_cden_xk);
   o("      for (int f = 0; f < n_f; ++f) {");
   o("        const double Xr = Xs[2 * f]; (void)Xr;");
   if (adj) o("        const double gr = Gs[2 * f], gim = Gs[2 * f + 1], ngr = -gr, ngi = -gim; (void)ngr; (void)ngi;");
   for (int c = 0; c < nc; ++c) {
     if (xr_zero) o("        const double Dr%d = b%d;", c, c);
+    else if (energy) o("        const double Dr%d = fma(%s, Xs[2 * (%d * n_f + f)], b%d);", c, lit(cden_a[c]).c_str(), cden_xk[c], c);
     else o("        const double Dr%d = fma(%s, Xr, b%d);", c, lit(cden_a[c]).c_str(), c);
     o("        const double r%d = rcp(fma(Dr%d, Dr%d, AXI2[%d * n_f + f]));", c, c, c, c);
     o("        const double vre%d = Dr%d * r%d, vim%d = -AXI[%d * n_f + f] * r%d;", c, c, c, c, c, c);
@@ -182,7 +188,9 @@ void emit_phase2(Out& o, const Table& t, int kind, bool xr_zero) {
     o("        accX[2 * f] += dvr; accX[2 * f + 1] += dvi;");
     o("        if (ps_dX) reinterpret_cast<double2*>(ps_dX)[(size_t)f * n + s] = make_double2(dvr, dvi);");
   }
-  if (fwd) {
+  if (energy) {
+    o("        reinterpret_cast<double2*>(ps_v)[(size_t)f * n + s] = make_double2(vr, vi);");
+  } else if (fwd) {
     o("        accV[4 * f] += vr; accV[4 * f + 1] += vi;");
     o("        accV[4 * f + 2] = fma(vr, vr, accV[4 * f + 2]); accV[4 * f + 3] = fma(vi, vi, accV[4 * f + 3]);");
     o("        if (ps_v) reinterpret_cast<double2*>(ps_v)[(size_t)f * n + s] = make_double2(vr, vi);");
@@ -192,8 +200,8 @@ void emit_phase2(Out& o, const Table& t, int kind, bool xr_zero) {
 
 }  // namespace
 
-bool jit_supported(const TableHeader& h, std::string* why) {
-  if (h.n_ext != 1) { if (why) *why = "one external frequency only"; return false; }
+bool jit_supported(const TableHeader& h, int kind, std::string* why) {
+  if (h.n_ext != 1 && kind != kKindEnergy) { if (why) *why = "momentum sampling takes one external frequency"; return false; }
   if (h.n_ops > kJitMaxOps) { if (why) *why = "pole DAG above the generator's size limit"; return false; }
   return true;
 }
@@ -201,7 +209,8 @@ bool jit_supported(const TableHeader& h, std::string* why) {
 // CUDA C++ source of the specialised kernel of one kind for one table.
 std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind) {
   const Table t{h, blob};
-  const bool fwd = kind != kKindBwd, adj = kind != kKindFwd;
+  const bool energy = kind == kKindEnergy;
+  const bool fwd = kind != kKindBwd, adj = kind == kKindFused || kind == kKindBwd;
   const int* repl = t.I(h.off_repl);
   const int* lm_ptr = t.I(h.off_lm_ptr);
   const int* lm_l = t.I(h.off_lm_l);
@@ -223,17 +232,28 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   const int* g1rd = t.I(h.off_g1rd);
   const int* g2 = t.I(h.off_g2);
   const double* g2cd_p = t.D(h.off_g2cd_p);
+  const int* cden_xk = t.I(h.off_cden_xk);
+  const double* xvec = t.D(h.off_xvec);
   const char* nval = kind == kKindFused ? "6 * n_f + 3" : kind == kKindBwd ? "2 * n_f + 3" : "4 * n_f";
 
   Out o;
   o("// generated by libtami for one flattened term table, one sample per thread: %s",
-    kind == kKindFused ? "forward + adjoint" : kind == kKindFwd ? "forward" : "adjoint");
+    kind == kKindFused ? "forward + adjoint" : kind == kKindFwd ? "forward" : kind == kKindBwd ? "adjoint" : "energy input");
   o("#include \"tami_devmath.cuh\"");
   o("using namespace tami::dev;");
   if (h.n_cden > 0) {
-    std::string a;
-    for (int c = 0; c < h.n_cden; ++c) a += (c ? ", " : "") + lit(cden_a[c]);
+    std::string a, k;
+    for (int c = 0; c < h.n_cden; ++c) {
+      a += (c ? ", " : "") + lit(cden_a[c]);
+      k += (c ? ", " : "") + std::to_string(cden_xk[c]);
+    }
     o("__device__ const double kJitCdenA[%d] = {%s};", h.n_cden, a.c_str());
+    o("__device__ const int kJitCdenXk[%d] = {%s};", h.n_cden, k.c_str());
+  }
+  if (energy && h.n_ext > 1) {
+    std::string v;
+    for (int i = 0; i < h.n_xk * h.n_ext; ++i) v += (i ? ", " : "") + lit(xvec[i]);
+    o("__device__ const double kJitXvec[%d] = {%s};", h.n_xk * h.n_ext, v.c_str());
   }
   o("extern \"C\" __global__ void __launch_bounds__(%d, 8) %s(double lt, double ltp, double lmu, double lkx, double lky,",
     kJitBlock, kKernelName[kind]);
@@ -241,17 +261,35 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   o("    double beta, double* ps_dX, double* ps_grad, double* ps_v, double* saved, double* partial) {");
   o("  extern __shared__ __align__(16) double smem[];");
   o("  const int tid = threadIdx.x;");
-  o("  double* Xs = smem; double* Gs = Xs + 2 * n_f; double* AXI = Gs + 2 * n_f; double* AXI2 = AXI + %d * n_f;", h.n_cden);
-  o("  double* red = AXI2 + %d * n_f;", h.n_cden);
-  o("  (void)AXI; (void)AXI2; (void)G; (void)ps_dX; (void)ps_grad; (void)ps_v; (void)saved;");
-  o("  for (int i = tid; i < 2 * n_f; i += %d) { Xs[i] = X[i]; Gs[i] = %s; }", kJitBlock, adj ? "G[i]" : "0.0");
+  if (energy) {
+    // Xs [n_xk][n_f][2]: the frequencies as the denominators see them, Y_kf = sum_q v_kq X_fq
+    o("  double* Xs = smem; double* AXI = Xs + %d * n_f; double* AXI2 = AXI + %d * n_f;", 2 * h.n_xk, h.n_cden);
+    o("  (void)AXI; (void)AXI2; (void)G; (void)ps_dX; (void)ps_grad; (void)partial; (void)seed; (void)offset;");
+    o("  (void)lt; (void)ltp; (void)lmu; (void)lkx; (void)lky;");
+    if (h.n_ext == 1) {
+      o("  for (int i = tid; i < 2 * n_f; i += %d) Xs[i] = X[i];", kJitBlock);
+    } else {
+      o("  for (int i = tid; i < %d * n_f; i += %d) {", h.n_xk, kJitBlock);
+      o("    const int k = i / n_f, f = i %% n_f;");
+      o("    const double* v = kJitXvec + k * %d; const double* x = X + 2 * (size_t)f * %d;", h.n_ext, h.n_ext);
+      o("    double re = v[0] * x[0], im = v[0] * x[1];");
+      o("    for (int q = 1; q < %d; ++q) { re = fma(v[q], x[2 * q], re); im = fma(v[q], x[2 * q + 1], im); }", h.n_ext);
+      o("    Xs[2 * i] = re; Xs[2 * i + 1] = im;");
+      o("  }");
+    }
+  } else {
+    o("  double* Xs = smem; double* Gs = Xs + 2 * n_f; double* AXI = Gs + 2 * n_f; double* AXI2 = AXI + %d * n_f;", h.n_cden);
+    o("  double* red = AXI2 + %d * n_f;", h.n_cden);
+    o("  (void)AXI; (void)AXI2; (void)G; (void)ps_dX; (void)ps_grad; (void)ps_v; (void)saved;");
+    o("  for (int i = tid; i < 2 * n_f; i += %d) { Xs[i] = X[i]; Gs[i] = %s; }", kJitBlock, adj ? "G[i]" : "0.0");
+  }
   if (adj) {
     o("  double accX[%d];", 2 * kJitMaxFreq);
     o("  for (int i = 0; i < 2 * n_f; ++i) accX[i] = 0.0;");
     o("  double gmu = 0.0, gkx = 0.0, gky = 0.0;");
     o("  __shared__ double s_gsum;");
   }
-  if (fwd) {
+  if (fwd && !energy) {
     o("  double accV[%d];", 4 * kJitMaxFreq);
     o("  for (int i = 0; i < 4 * n_f; ++i) accV[i] = 0.0;");
   }
@@ -261,11 +299,12 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   o("    int nonzero = 0;");
   if (h.n_cden > 0) {
     o("    for (int i = tid; i < %d * n_f; i += %d) {", h.n_cden, kJitBlock);
-    o("      const double a = kJitCdenA[i / n_f] * Xs[2 * (i %% n_f) + 1];");
+    if (energy) o("      const double a = kJitCdenA[i / n_f] * Xs[2 * (kJitCdenXk[i / n_f] * n_f + i %% n_f) + 1];");
+    else o("      const double a = kJitCdenA[i / n_f] * Xs[2 * (i %% n_f) + 1];");
     o("      AXI[i] = a; AXI2[i] = a * a;");
     o("    }");
   }
-  o("    for (int f = tid; f < n_f; f += %d) nonzero |= Xs[2 * f] != 0.0;", kJitBlock);
+  o("    for (int i = tid; i < %d * n_f; i += %d) nonzero |= Xs[2 * i] != 0.0;", energy ? h.n_xk : 1, kJitBlock);
   if (adj) o("    if (tid == 0) { double g = 0.0; for (int f = 0; f < n_f; ++f) g += Gs[2 * f]; s_gsum = g; }");
   o("    xr_zero = !__syncthreads_or(nonzero);");
   o("  }");
@@ -276,7 +315,10 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   // ---- line energies: from the momenta, or (adjoint) from the forward's saved rows
   for (int r = 0; r < h.n_rep; ++r) o("    double E%d;", repl[r]);
   if (adj) for (int r = 0; r < h.n_rep_ext; ++r) o("    double Gx%d, Gy%d;", r, r);
-  if (kind == kKindBwd) {
+  if (energy) {
+    o("    {");
+    for (int r = 0; r < h.n_rep; ++r) o("      E%d = saved[(size_t)s * %d + %d];", repl[r], h.N, repl[r]);
+  } else if (kind == kKindBwd) {
     o("    if (saved) {");
     for (int r = 0; r < h.n_rep; ++r) o("      E%d = saved[(size_t)%d * n + s];", repl[r], r);
     for (int r = 0; r < h.n_rep_ext; ++r)
@@ -286,6 +328,7 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   } else {
     o("    {");
   }
+  if (!energy) {
   o("    const unsigned long long sg = offset + (unsigned long long)s;");
   for (int l = 0; l < h.m; ++l) {
     o("    double kx%d, ky%d;", l, l);
@@ -315,6 +358,7 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     for (int r = 0; r < h.n_rep; ++r) o("      saved[(size_t)%d * n + s] = E%d;", r, repl[r]);
     o("    }");
   }
+  }  // !energy
   o("    }");
   // ---- energy combinations
   for (int u = 0; u < h.n_combo; ++u) {
@@ -438,6 +482,10 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     o("    if (ps_grad) { ps_grad[3 * s] = mub; ps_grad[3 * s + 1] = kxb; ps_grad[3 * s + 2] = kyb; }");
   }
   o("  }");
+  if (energy) {   // every value is an output; nothing is reduced
+    o("}");
+    return o.s;
+  }
   // ---- block reduction into the generic kernel's per-block layout
   o("  const int nval = %s, warp = tid >> 5, lane = tid & 31;", nval);
   o("  for (int i = 0; i < nval; ++i) {");
@@ -497,7 +545,7 @@ void jit_release(tami_diagram* d) {
 // Compile (once per diagram, kind and device) the specialised kernel of d's table.
 int jit_prepare(tami_diagram* d, int kind) {
   std::string why;
-  if (!jit_supported(d->hdr, &why)) { set_error("specialised kernel: " + why); return TAMI_EUNSUPPORTED; }
+  if (!jit_supported(d->hdr, kind, &why)) { set_error("specialised kernel: " + why); return TAMI_EUNSUPPORTED; }
   JitState* s = jit_state(d);
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->device != d->device) {          // a new upload device: build again for it
@@ -550,12 +598,22 @@ int jit_prepare(tami_diagram* d, int kind) {
 
 // Whether an evaluating call of this kind takes the specialised kernel for n samples (compiling it if
 // so): 1 = use it, 0 = the generic kernel, or -status (the "always" mode when it cannot be built).
+size_t jit_smem(const TableHeader& h, int kind, int n_f) {
+  if (kind == kKindEnergy) return sizeof(double) * (size_t)(2 * h.n_xk + 2 * h.n_cden) * n_f;
+  const int nval = kind == kKindFused ? 6 * n_f + 3 : kind == kKindBwd ? 2 * n_f + 3 : 4 * n_f;
+  return sizeof(double) * ((size_t)(4 + 2 * h.n_cden) * n_f + 4 * (size_t)nval);
+}
+
 int jit_select(tami_diagram* d, int kind, int64_t n, int n_f) {
   const int mode = jit_mode();
   if (mode == TAMI_JIT_NEVER) return 0;
-  if (mode == TAMI_JIT_AUTO && (n < (int64_t(1) << 21) || !jit_supported(d->hdr, nullptr) || n_f > kJitMaxFreq))
-    return 0;
-  if (n_f > kJitMaxFreq) { set_error("specialised kernel: n_f above 256"); return -TAMI_EUNSUPPORTED; }
+  // large enough to repay a compilation: 2^21 Monte Carlo samples, or 2^25 (row, frequency) values
+  const bool big = kind == kKindEnergy ? (double)n * n_f >= 33554432.0 : n >= (int64_t(1) << 21);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d->device);
+  const bool fits = (kind == kKindEnergy || n_f <= kJitMaxFreq) && jit_smem(d->hdr, kind, n_f) <= (size_t)optin;
+  if (mode == TAMI_JIT_AUTO && (!big || !fits || !jit_supported(d->hdr, kind, nullptr))) return 0;
+  if (!fits) { set_error("specialised kernel: frequencies beyond its per-thread sums or shared memory"); return -TAMI_EUNSUPPORTED; }
   const int rc = jit_prepare(d, kind);
   if (rc == TAMI_OK) return 1;
   return mode == TAMI_JIT_ALWAYS ? -rc : 0;
@@ -565,8 +623,7 @@ int jit_launch(tami_diagram* d, int kind, const tami_lattice* lat, uint64_t seed
                const double* X, int n_f, double beta, const double* gout, double* per_sample, double* ps_dX,
                double* ps_grad, double* saved, double* partial, int max_grid, struct CUstream_st* st, int* grid_out) {
   JitState* s = jit_state(d);
-  const int nval = kind == kKindFused ? 6 * n_f + 3 : kind == kKindBwd ? 2 * n_f + 3 : 4 * n_f;
-  const size_t smem = sizeof(double) * ((size_t)(4 + 2 * d->hdr.n_cden) * n_f + 4 * (size_t)nval);
+  const size_t smem = jit_smem(d->hdr, kind, n_f);
   const void* fn = reinterpret_cast<const void*>(s->k[kind].fn);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) { set_error(std::string("specialised kernel attribute: ") + cudaGetErrorString(e)); return TAMI_ECUDA; }
@@ -613,10 +670,14 @@ int tami_set_jit(int mode) {
 int tami_jit_prepare(tami_diagram* d) {
   if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
   if (!d->d_blob) { set_error("diagram not uploaded (call tami_upload)"); return TAMI_EINVAL; }
+  int built = 0;
   for (int k = 0; k < kKinds; ++k) {
+    if (!jit_supported(d->hdr, k, nullptr)) continue;
     const int rc = jit_prepare(d, k);
     if (rc) return rc;
+    ++built;
   }
+  if (!built) { set_error("specialised kernel: no kind applies to this table"); return TAMI_EUNSUPPORTED; }
   return TAMI_OK;
 }
 
@@ -636,9 +697,12 @@ int tami_jit_status(const tami_diagram* d, int* ready, int* last_used, double* c
 
 int tami_jit_source(const tami_diagram* d, int kind, char* buf, size_t cap, size_t* len) {
   if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
-  if (kind < 0 || kind >= kKinds) { set_error("kind must be 0 (fused), 1 (forward) or 2 (adjoint)"); return TAMI_EINVAL; }
+  if (kind < 0 || kind >= kKinds) {
+    set_error("kind must be 0 (fused), 1 (forward), 2 (adjoint) or 3 (energy input)");
+    return TAMI_EINVAL;
+  }
   std::string why;
-  if (!jit_supported(d->hdr, &why)) { set_error("specialised kernel: " + why); return TAMI_EUNSUPPORTED; }
+  if (!jit_supported(d->hdr, kind, &why)) { set_error("specialised kernel: " + why); return TAMI_EUNSUPPORTED; }
   const std::string src = jit_source(d->hdr, d->blob.data(), kind);
   if (len) *len = src.size() + 1;
   if (buf && cap > 0) {

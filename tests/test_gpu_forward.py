@@ -111,9 +111,10 @@ def test_eval_energies_enumerated_diagrams(order):
 
 def test_energy_input_paper_example_full_size():
     """The paper's evaluation example at its own size (Sec. 5.1): 10^6 energy rows U(-8, 8), 100
-    fermionic frequencies, beta = 1, the full [n_f][n_e] output.  Rows at 2000 random indices
-    against the oracle; a launch over a slice of the rows equals that slice of the full output
-    bit for bit (each row is evaluated by itself)."""
+    fermionic frequencies, beta = 1, the full [n_f][n_e] output (at this size the diagram's
+    specialised kernel).  Rows at 2000 random indices against the oracle; a launch over a slice of
+    the rows equals that slice of the full output bit for bit on either kernel (each row is
+    evaluated by itself), and the generic kernel agrees with it to rounding."""
     c = W.ENERGY_X1
     D, S = lib_and_oracle(c["alpha"])
     E = W.random_energies(c["n_e"], c["alpha"].shape[0], a=c["a"], seed=c["seed"])
@@ -122,14 +123,25 @@ def test_energy_input_paper_example_full_size():
     out = D.eval_energies(Ed, X, c["beta"])
     torch.cuda.synchronize()
     assert tuple(out.shape) == (c["n_freq"], c["n_e"])
+    assert D.jit_status()["last_used"]
     rng = np.random.default_rng(2)
     idx = np.sort(rng.choice(c["n_e"], 2000, replace=False))
     got = out[:, torch.as_tensor(idx, device="cuda")].cpu().numpy()
     ref, _, env = S.eval_energies(E[idx], X, c["beta"])
     check_per_sample(got, ref, env, "energy-input example")
     lo, hi = 123_457, 123_457 + 5 * 128 + 3
-    part = D.eval_energies(Ed[lo:hi].contiguous(), X, c["beta"])
-    assert torch.equal(part, out[:, lo:hi])
+    try:
+        T.set_jit("always")
+        part = D.eval_energies(Ed[lo:hi].contiguous(), X, c["beta"])
+        assert torch.equal(part, out[:, lo:hi])
+        T.set_jit("never")
+        gen = D.eval_energies(Ed, X, c["beta"])
+        part = D.eval_energies(Ed[lo:hi].contiguous(), X, c["beta"])
+        assert torch.equal(part, gen[:, lo:hi])
+        ref, _, env = S.eval_energies(E[idx], X, c["beta"])
+        assert np.all(np.abs(gen[:, torch.as_tensor(idx, device="cuda")].cpu().numpy() - got) <= RTOL * env)
+    finally:
+        T.set_jit("auto")
 
 
 # ---------------------------------------------------------------------------- momentum mode

@@ -148,13 +148,16 @@ def test_auto_mode_takes_the_specialised_kernel_for_large_launches():
     assert not D.jit_status()["last_used"]
 
 
-def test_always_mode_refuses_what_the_generator_cannot_build():
-    """A two-external diagram has no momentum-mode fused pass at all: refused before any kernel
-    choice (TAMI_EUNSUPPORTED), and tami_jit_prepare refuses it too."""
+def test_two_externals_build_the_energy_kernel_only():
+    """A two-external diagram has no Monte Carlo calls (they need one external momentum):
+    tami_jit_prepare builds its energy-input kernel only, and the fused call is refused
+    (TAMI_EUNSUPPORTED) in every mode."""
     D = T.Diagram([[1, 1, 0], [1, 0, 1]], n_ext=2).upload(0)
     T.set_jit("always")
+    D.jit_prepare()
+    assert D.jit_status()["ready"] == {"energy"}
     with pytest.raises(L.TamiError) as e:
-        D.jit_prepare()
+        D.forward_backward((1.0, 0.0, 0.0, 0.5, 0.5), 1, 0, 256, np.array([1j * np.pi]), 1.0, np.ones(1) + 0j)
     assert e.value.code == L.TAMI_EUNSUPPORTED
 
 
@@ -215,3 +218,53 @@ def test_specialised_forward_and_adjoint_agree_with_generic():
     assert torch.allclose(v1, v0, rtol=1e-10, atol=0)
     assert torch.all((b1["dSigma_dX"] - b0["dSigma_dX"]).abs() <= 1e-12 * b0["dX"].abs().mean(dim=1))
     assert torch.all((b1["grad_params"] - b0["grad_params"]).abs() <= 1e-12 * b0["grads"].abs().mean(dim=0))
+
+
+ENERGY_CASES = [
+    # name, alpha, eps, boson, n_ext
+    ("paper_order2", [[1, 0, 0], [0, 1, 0], [-1, 1, 1]], None, None, 1),
+    ("order4_bench", "bench", None, None, 1),
+    ("two_fermionic_ext", [[1, 1, 0], [1, 0, 1]], None, None, 2),
+    ("three_externals", [[1, 1, 0, 0], [1, 0, 1, 0], [1, 0, 0, 1]], None, [0, 1, 0, 0], 3),
+    ("order4_held_external", "held", None, None, 2),
+]
+
+
+@pytest.mark.parametrize("real_axis", [False, True], ids=["matsubara", "real_axis"])
+@pytest.mark.parametrize("case", ENERGY_CASES, ids=[c[0] for c in ENERGY_CASES])
+def test_specialised_energy_input_against_oracle(case, real_axis):
+    """The energy-input kind: every (frequency row, energy row) value against the oracle, with one,
+    two and three external frequencies, on the imaginary axis and with the first external
+    continued to omega + i Gamma; and against the generic kernel."""
+    name, alpha, eps, boson, n_ext = case
+    if alpha == "bench":
+        d = order4_bench()
+        alpha, eps = d["alpha"], d["eps"]
+    elif alpha == "held":
+        d = order4_bench()
+        alpha, eps = W.hold_external(d["alpha"], 3), d["eps"]
+    alpha = np.asarray(alpha)
+    D = T.Diagram(alpha, eps=eps, var_is_boson=boson, n_ext=n_ext).upload(0)
+    S = O.Solution(alpha, eps=eps, var_is_boson=boson, n_ext=n_ext)
+    beta = 2.0
+    bext = [0] * n_ext if boson is None else list(boson[-n_ext:])
+    X = np.empty((6, n_ext), dtype=np.complex128)
+    for q, b in enumerate(bext):
+        nn = np.arange(6) * (q + 1) - 2 * q + (1 if b else 0)
+        X[:, q] = 1j * (2 * nn + (0 if b else 1)) * np.pi / beta
+    if real_axis:
+        X[:, 0] = np.linspace(-2.0, 2.0, 6) + 0.05j
+    if n_ext == 1:
+        X = X[:, 0]
+    E = W.random_energies(3 * 128 + 37, alpha.shape[0], a=4.0, seed=17)
+    Ed = torch.tensor(E, device="cuda")
+    T.set_jit("always")
+    out = D.eval_energies(Ed, X, beta)
+    torch.cuda.synchronize()
+    assert D.jit_status()["last_used"] and "energy" in D.jit_status()["ready"]
+    ref, _, env = S.eval_energies(E, X, beta)
+    got = out.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= RTOL * env), np.max(np.abs(got - ref) / env)
+    T.set_jit("never")
+    gen = D.eval_energies(Ed, X, beta).cpu().numpy()
+    assert np.all(np.abs(got - gen) <= RTOL * env)

@@ -58,10 +58,10 @@ def tables():
     ]
 
 
-KERNEL = {"fused": "tami_jit_fused", "forward": "tami_jit_fwd", "adjoint": "tami_jit_bwd"}
+KERNEL = {"fused": "tami_jit_fused", "forward": "tami_jit_fwd", "adjoint": "tami_jit_bwd", "energy": "tami_jit_energy"}
 
 
-@pytest.mark.parametrize("kind", ["fused", "forward", "adjoint"])
+@pytest.mark.parametrize("kind", ["fused", "forward", "adjoint", "energy"])
 @pytest.mark.parametrize("name,D", tables(), ids=[t[0] for t in tables()])
 def test_generated_kernel_compiles_for_sm103a(name, D, kind):
     src = D.jit_source(kind)
@@ -96,11 +96,20 @@ def test_generator_covers_frequency_free_groups_and_real_denominators():
     assert rc == 0, log[:3000]
 
 
-def test_generator_refuses_several_externals():
-    D = T.Diagram([[1, 1, 0], [1, 0, 1]], n_ext=2)
-    with pytest.raises(L.TamiError) as e:
-        D.jit_source()
-    assert e.value.code == L.TAMI_EUNSUPPORTED
+def test_several_externals_energy_input_only():
+    """Momentum sampling takes one external; the energy-input kind takes several (its frequency
+    rows are combined per external-coefficient vector) and its source compiles."""
+    for alpha, boson, n_ext in (([[1, 1, 0], [1, 0, 1]], None, 2),
+                                ([[1, 1, 0, 0], [1, 0, 1, 0], [1, 0, 0, 1]], [0, 1, 0, 0], 3)):
+        D = T.Diagram(alpha, var_is_boson=boson, n_ext=n_ext)
+        for kind in ("fused", "forward", "adjoint"):
+            with pytest.raises(L.TamiError) as e:
+                D.jit_source(kind)
+            assert e.value.code == L.TAMI_EUNSUPPORTED
+        src = D.jit_source("energy")
+        assert "kJitXvec" in src
+        rc, log, _ = compile_cubin(src)
+        assert rc == 0, log[:3000]
 
 
 def test_jit_mode_argument_checked():
@@ -108,4 +117,4 @@ def test_jit_mode_argument_checked():
     assert L.lib().tami_set_jit(-1) == L.TAMI_EINVAL
     T.set_jit("auto")
     with pytest.raises(L.TamiError):
-        L.check(L.lib().tami_jit_source(tables()[0][1]._h, 3, None, 0, None))
+        L.check(L.lib().tami_jit_source(tables()[0][1]._h, 4, None, 0, None))
