@@ -274,8 +274,8 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
  * written out for the diagram's own table -- every table index a constant, every per-sample array a set of registers
  * -- instead of the generic kernel, which reads the table from shared memory and keeps per-sample
  * arrays in local memory.  Each is generated as CUDA C++ on the first call that takes it, compiled
- * for sm_103a with NVRTC (loaded at run time: libnvrtc.so.13, or $TAMI_NVRTC) and cached with the
- * diagram until tami_destroy.  Values agree with the generic kernels to rounding; workspaces and
+ * for sm_103a with NVRTC (loaded at run time: libnvrtc.so.13, or the path in $TAMI_NVRTC; "none"
+ * disables it) and cached with the diagram until tami_destroy.  Values agree with the generic kernels to rounding; workspaces and
  * outputs are those of the generic calls.  tami_forward_noalloc and batches always run the generic
  * kernels.
  *   mode TAMI_JIT_NEVER   the generic kernel always;

@@ -82,7 +82,10 @@ Nvrtc& nvrtc() {
   if (n.tried) return n;
   n.tried = true;
   std::vector<std::string> names;
-  if (const char* e = std::getenv("TAMI_NVRTC")) names.push_back(e);
+  if (const char* e = std::getenv("TAMI_NVRTC")) {
+    if (!std::strcmp(e, "none")) { n.why = "NVRTC disabled ($TAMI_NVRTC=none)"; return n; }
+    names.push_back(e);
+  }
   names.insert(names.end(), {"libnvrtc.so.13", "/usr/local/cuda/lib64/libnvrtc.so.13", "libnvrtc.so"});
   void* h = nullptr;
   for (const std::string& s : names)

@@ -268,3 +268,53 @@ def test_specialised_energy_input_against_oracle(case, real_axis):
     T.set_jit("never")
     gen = D.eval_energies(Ed, X, beta).cpu().numpy()
     assert np.all(np.abs(got - gen) <= RTOL * env)
+
+
+FALLBACK_SCRIPT = r"""
+import json, sys
+import numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import paper_2311_17189_gb300 as T
+from paper_2311_17189_gb300 import _lib as L, workloads as W
+torch.cuda.set_device(0)
+d = next(x for x in T.enumerate_sigma(4) if x["code"] == tuple(W.ORDER4["code"]))
+D = T.Diagram(d["alpha"], eps=d["eps"]).upload(0)
+c = W.ORDER4
+X, g = W.matsubara(c["beta"], 4), np.ones(4) + 0.5j
+out = {}
+T.set_jit("auto")
+r = D.forward_backward(W.lattice(c), c["seed"], 0, 1 << 21, X, c["beta"], g)
+torch.cuda.synchronize()
+out["auto_finite"] = bool(np.all(np.isfinite(r["mean"].cpu().numpy())))
+out["auto_used"] = D.jit_status()["last_used"]
+T.set_jit("always")
+try:
+    D.forward_backward(W.lattice(c), c["seed"], 0, 1024, X, c["beta"], g)
+    out["always"] = "ran"
+except L.TamiError as e:
+    out["always"] = [e.code, str(e)]
+T.set_jit("never")
+r2 = D.forward_backward(W.lattice(c), c["seed"], 0, 1 << 21, X, c["beta"], g)
+torch.cuda.synchronize()
+out["same_as_generic"] = bool(torch.equal(r["mean"], r2["mean"]))
+print(json.dumps(out))
+"""
+
+
+def test_without_nvrtc_auto_falls_back_and_always_refuses(tmp_path):
+    """Failure of the run-time compiler, made on the host ($TAMI_NVRTC=none, in a child process):
+    `auto` runs the generic kernel (the same bits as `never`), `always` refuses the call with
+    TAMI_EUNSUPPORTED and says why, and nothing faults."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "fallback.py"
+    script.write_text(FALLBACK_SCRIPT)
+    env = dict(os.environ, TAMI_NVRTC="none")
+    r = subprocess.run([sys.executable, str(script), root], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    assert out["auto_finite"] and not out["auto_used"] and out["same_as_generic"]
+    assert out["always"][0] == L.TAMI_EUNSUPPORTED and "NVRTC disabled" in out["always"][1]
