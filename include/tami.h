@@ -314,14 +314,26 @@ int tami_jit_source(const tami_diagram* d, int kind, char* buf, size_t cap, size
  * captures [queue reset, persistent kernel, reduction] into a CUDA graph on the current device.
  * chunk_tiles = 0 lets an autotuner pick the chunk size by timing graph replays with typical
  * inputs; the choice is cached per (GPU, batch signature) in memory and in a text file
- * ($TAMI_TUNE_CACHE, default $HOME/.cache/libtami_autotune.txt).  The diagrams must outlive the plan
- * only until tami_batch_plan returns (their tables are copied).  Allocates device memory. */
+ * ($TAMI_TUNE_CACHE, default $HOME/.cache/libtami_autotune.txt).
+ * Specialised diagrams (see tami_set_jit): in mode "always" every diagram, in "auto" each diagram
+ * with at least 2^20 samples whose kernel builds, runs its own generated forward kernel instead of
+ * being cut into items: the plan compiles those kernels (on parallel host threads, cached with the
+ * diagrams) and the graph launches each over its diagram's whole sample stream after the
+ * persistent kernel; the same reduction finishes them.  "always" refuses the plan
+ * (TAMI_EUNSUPPORTED) when a diagram's kernel cannot be built.  The diagrams must outlive the plan
+ * only until tami_batch_plan returns (their tables are copied, the plan holds its own reference
+ * to their compiled kernels).  Allocates device memory. */
 typedef struct tami_batch tami_batch;
 int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* samples, const uint64_t* seeds, int n_f,
                     int chunk_tiles, tami_batch** out);
 
-/* Work items, grid size and chunk size (tiles of 128 samples per item) of a plan. */
+/* Work items, grid size and chunk size (tiles of 128 samples per item) of a plan's persistent
+ * kernel (n_items = grid = 0 when every diagram is specialised). */
 int tami_batch_info(const tami_batch* b, int* n_items, int* grid, int* chunk_tiles);
+
+/* Which diagrams of a plan run their specialised kernel: flags [n_d] (may be NULL) gets 1 for
+ * those, 0 for the persistent kernel's; n_specialised (may be NULL) their count. */
+int tami_batch_specialised(const tami_batch* b, int* flags, int* n_specialised);
 
 /* Replay the plan: X device double [n_f][2]; mean and var device double [n_d][n_f][2] (var may be
  * NULL), as tami_forward's mean and variances for each diagram.  Launches asynchronously on

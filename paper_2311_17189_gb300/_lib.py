@@ -22,7 +22,7 @@ EXPORTS = [
     "tami_backward_workspace", "tami_backward", "tami_forward_backward_workspace", "tami_forward_backward",
     "tami_set_jit", "tami_jit_prepare", "tami_jit_status", "tami_jit_source",
     "tami_batch_plan", "tami_batch_info", "tami_batch_launch",
-    "tami_batch_destroy", "tami_batch_debug_set_item",
+    "tami_batch_destroy", "tami_batch_debug_set_item", "tami_batch_specialised",
     "tami_enumerate_sigma",
     "tami_selftest_exp", "tami_destroy",
 ]
@@ -101,6 +101,7 @@ def lib():
     L.tami_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int)]
     L.tami_batch_launch.argtypes = [vp, ctypes.POINTER(Lattice), dp, ctypes.c_double, dp, dp, vp]
+    L.tami_batch_specialised.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.tami_batch_destroy.argtypes = [vp]
     L.tami_batch_debug_set_item.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, i64, ctypes.POINTER(ctypes.c_int64)]
     L.tami_batch_debug_set_item.restype = ctypes.c_int

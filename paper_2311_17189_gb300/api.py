@@ -266,7 +266,9 @@ class Diagram:
 
 class Batch:
     """Many diagrams in one persistent, graph-captured launch (tami_batch_*).  Each diagram d gets
-    samples[d] Philox samples with key seeds[d]; the lattice and frequencies are shared."""
+    samples[d] Philox samples with key seeds[d]; the lattice and frequencies are shared.  Diagrams
+    the specialised-kernel mode selects (set_jit) run their own generated forward kernel inside
+    the same graph instead of the persistent kernel's work queue."""
 
     def __init__(self, diagrams, samples, seeds, n_f, chunk_tiles=0):
         torch = _torch()
@@ -285,7 +287,11 @@ class Batch:
     def info(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         L.check(L.lib().tami_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-        return {"items": a.value, "grid": b.value, "chunk_tiles": c.value}
+        flags = (ctypes.c_int * self.n_d)()
+        n_spec = ctypes.c_int()
+        L.check(L.lib().tami_batch_specialised(self._h, flags, ctypes.byref(n_spec)))
+        return {"items": a.value, "grid": b.value, "chunk_tiles": c.value, "specialised": n_spec.value,
+                "specialised_diagrams": [d for d in range(self.n_d) if flags[d]]}
 
     def debug_set_item(self, item, d, tile0, tile1):
         """Overwrite one entry of the device work queue (tami_batch_debug_set_item); returns the

@@ -11,6 +11,11 @@
 // kernel sums each diagram's items in tile order, so results do not depend on which block ran
 // which item.  The chunk size and the grid come from a small autotuner (timed graph replays),
 // cached per GPU and batch signature in memory and in a text file.
+// Specialised diagrams: a diagram whose own generated forward kernel is taken (mode "always", or
+// "auto" at >= 2^20 samples) is not cut into items; the graph launches that kernel over the
+// diagram's whole sample stream after the persistent kernel, reading the launch's parameters
+// from the batch's device buffer, and its per-block partial sums join the diagram's list for the
+// same reduction (summed in block order).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -169,7 +174,11 @@ struct tami_batch {
   std::vector<int64_t> n;
   std::vector<uint64_t> seeds;
   int chunk = 0, grid = 0, n_items = 0;
-  int table_cap = 0, max_cden = 0, max_g2 = 0;
+  int table_cap = 0, max_cden = 0, max_g2 = 0;   // over the diagrams the persistent kernel runs
+  std::vector<int> spec;                           // 1: the diagram runs its specialised kernel
+  std::vector<tami::JitHandle> jit;                // those kernels, kept loaded by the batch
+  std::vector<int> jit_grid;
+  int n_spec = 0;
   size_t smem = 0;
   Layout L{};
   unsigned char* mem = nullptr;
@@ -191,8 +200,9 @@ void release_graph(tami_batch* b) {
   b->mem = nullptr;
 }
 
-// Build items, device buffers and the graph for one (chunk, grid) choice.
-int build(tami_batch* b, int chunk, int grid_cap) {
+// Build items, device buffers and the graph for one (chunk, grid) choice; with_spec = false
+// leaves the specialised diagrams out (tuning replays time the persistent kernel alone).
+int build(tami_batch* b, int chunk, int grid_cap, bool with_spec) {
   release_graph(b);
   const int n_d = b->n_d, n_f = b->n_f;
   std::vector<BatchDiag> diags(n_d);
@@ -210,13 +220,18 @@ int build(tami_batch* b, int chunk, int grid_cap) {
   }
   std::vector<BatchItem> items;
   for (int d = 0; d < n_d; ++d)
-    for (long long t = 0; t < diags[d].tiles; t += chunk)
+    for (long long t = 0; !b->spec[d] && t < diags[d].tiles; t += chunk)
       items.push_back({d, 0, t, std::min<long long>(t + chunk, diags[d].tiles)});
   std::stable_sort(items.begin(), items.end(), [&](const BatchItem& x, const BatchItem& y) {
     return (x.tile1 - x.tile0) * cost_per_tile[x.d] > (y.tile1 - y.tile0) * cost_per_tile[y.d];
   });
   const int n_items = (int)items.size();
-  std::vector<int> item_ptr(n_d + 1, 0), item_list(n_items);
+  // partial rows: the items', then each specialised launch's blocks
+  std::vector<long long> spec_row(n_d, -1);
+  long long n_rows = n_items;
+  for (int d = 0; d < n_d; ++d)
+    if (with_spec && b->spec[d]) { spec_row[d] = n_rows; n_rows += b->jit_grid[d]; }
+  std::vector<int> item_ptr(n_d + 1, 0), item_list((size_t)n_rows);
   {
     std::vector<std::vector<std::pair<long long, int>>> per(n_d);
     for (int i = 0; i < n_items; ++i) per[items[i].d].push_back({items[i].tile0, i});
@@ -225,6 +240,8 @@ int build(tami_batch* b, int chunk, int grid_cap) {
       std::sort(per[d].begin(), per[d].end());
       item_ptr[d] = q;
       for (auto& pr : per[d]) item_list[q++] = pr.second;
+      if (spec_row[d] >= 0)
+        for (int r = 0; r < b->jit_grid[d]; ++r) item_list[q++] = (int)(spec_row[d] + r);
     }
     item_ptr[n_d] = q;
   }
@@ -234,12 +251,12 @@ int build(tami_batch* b, int chunk, int grid_cap) {
   L.diags = take(sizeof(BatchDiag) * n_d);
   L.items = take(sizeof(BatchItem) * n_items);
   L.item_ptr = take(sizeof(int) * (n_d + 1));
-  L.item_list = take(sizeof(int) * n_items);
+  L.item_list = take(sizeof(int) * n_rows);
   L.blobs = take(blob_bytes);
   L.params = take(sizeof(double) * 8);
   L.X = take(sizeof(double) * 2 * n_f);
   L.ctr = take(256);
-  L.partial = take(sizeof(double) * 4 * (size_t)n_f * n_items);
+  L.partial = take(sizeof(double) * 4 * (size_t)n_f * n_rows);
   L.mean = take(sizeof(double) * 2 * (size_t)n_f * n_d);
   L.var = take(sizeof(double) * 2 * (size_t)n_f * n_d);
   L.total = off;
@@ -249,7 +266,7 @@ int build(tami_batch* b, int chunk, int grid_cap) {
   std::memcpy(host.data() + L.diags, diags.data(), sizeof(BatchDiag) * n_d);
   std::memcpy(host.data() + L.items, items.data(), sizeof(BatchItem) * n_items);
   std::memcpy(host.data() + L.item_ptr, item_ptr.data(), sizeof(int) * (n_d + 1));
-  std::memcpy(host.data() + L.item_list, item_list.data(), sizeof(int) * n_items);
+  std::memcpy(host.data() + L.item_list, item_list.data(), sizeof(int) * n_rows);
   for (int d = 0; d < n_d; ++d)
     std::memcpy(host.data() + L.blobs + diags[d].blob_off, b->ds[d]->blob.data(), b->ds[d]->blob.size());
   e = cudaMemcpy(b->mem, host.data(), host.size(), cudaMemcpyHostToDevice);
@@ -267,7 +284,7 @@ int build(tami_batch* b, int chunk, int grid_cap) {
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   int grid = std::max(1, dp.sms * std::max(per_sm, 1));
   if (grid_cap > 0) grid = std::min(grid, grid_cap);
-  grid = std::min(grid, n_items);
+  grid = std::min(grid, n_items);   // 0: every diagram is specialised
   b->grid = grid;
   b->chunk = chunk;
   b->n_items = n_items;
@@ -291,12 +308,19 @@ int build(tami_batch* b, int chunk, int grid_cap) {
   e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
   cudaMemsetAsync(b->mem + L.ctr, 0, 2 * sizeof(int), b->cap);
-  batch_kernel<<<grid, kBlock, b->smem, b->cap>>>(P);
+  if (n_items > 0) batch_kernel<<<grid, kBlock, b->smem, b->cap>>>(P);
+  int rc = TAMI_OK;
+  for (int d = 0; d < n_d && rc == TAMI_OK; ++d)
+    if (spec_row[d] >= 0)
+      rc = jit_launch_at(b->jit[d], b->jit_grid[d], nullptr, P.params, b->seeds[d], 0, b->n[d], P.X, n_f, 0.0,
+                         nullptr, nullptr, nullptr, nullptr, nullptr, P.partial + (size_t)spec_row[d] * n_f * 4,
+                         b->cap);
   const int nt = n_d * n_f;
   batch_reduce_kernel<<<(nt + 127) / 128, 128, 0, b->cap>>>(
       P.partial, reinterpret_cast<const int*>(b->mem + L.item_ptr), reinterpret_cast<const int*>(b->mem + L.item_list),
       P.diags, n_d, n_f, P.status, reinterpret_cast<double*>(b->mem + L.mean), reinterpret_cast<double*>(b->mem + L.var));
   e = cudaStreamEndCapture(b->cap, &b->graph);
+  if (rc) return rc;
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
   e = cudaGraphInstantiate(&b->exec, b->graph, 0);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
@@ -320,12 +344,14 @@ std::string tune_key(const tami_batch* b) {
   unsigned long long hsh = 1469598103934665603ull;
   auto mix = [&](unsigned long long v) { hsh = (hsh ^ v) * 1099511628211ull; };
   for (int d = 0; d < b->n_d; ++d) {
+    if (b->spec[d]) continue;   // not run by the tuned kernel
     mix((unsigned long long)b->ds[d]->info.n_terms);
     mix((unsigned long long)b->n[d]);
     mix((unsigned long long)b->ds[d]->blob.size());
   }
   char buf[512];
-  std::snprintf(buf, sizeof(buf), "%s|sm%d|nd%d|nf%d|%016llx", p.name, p.multiProcessorCount, b->n_d, b->n_f, hsh);
+  std::snprintf(buf, sizeof(buf), "%s|sm%d|nd%d|nf%d|%016llx", p.name, p.multiProcessorCount, b->n_d - b->n_spec,
+                b->n_f, hsh);
   std::string k(buf);
   for (char& c : k) if (c == ' ' || c == '\t') c = '_';
   return k;
@@ -420,6 +446,26 @@ int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* sampl
     b->ds.push_back(ds[d]);
     b->n.push_back(samples[d]);
     b->seeds.push_back(seeds[d]);
+  }
+  // specialised diagrams (compiled now); the kernel cache is state of the diagram object, not of
+  // the table the batch copies
+  b->spec.assign(n_d, 0);
+  b->jit.resize(n_d);
+  b->jit_grid.assign(n_d, 0);
+  {
+    std::vector<tami_diagram*> mut(n_d);
+    for (int d = 0; d < n_d; ++d) mut[d] = const_cast<tami_diagram*>(ds[d]);
+    int rc = jit_select_batch(mut.data(), n_d, samples, n_f, b->spec.data());
+    for (int d = 0; d < n_d && rc == TAMI_OK; ++d) {
+      if (!b->spec[d]) continue;
+      rc = jit_handle(mut[d], kJitKindFwd, n_f, &b->jit[d]);
+      if (!rc) rc = jit_grid(b->jit[d], samples[d], 1 << 30, &b->jit_grid[d]);
+      ++b->n_spec;
+    }
+    if (rc) { delete b; return rc; }
+  }
+  for (int d = 0; d < n_d; ++d) {
+    if (b->spec[d]) continue;
     b->table_cap = std::max(b->table_cap, (int)up256(ds[d]->blob.size()));
     b->max_cden = std::max(b->max_cden, ds[d]->hdr.n_cden);
     b->max_g2 = std::max(b->max_g2, ds[d]->hdr.n_g2);
@@ -428,16 +474,19 @@ int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* sampl
   if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaStreamCreate"); }
   int rc = TAMI_OK;
   if (chunk_tiles > 0) {
-    rc = build(b, chunk_tiles, 0);
+    rc = build(b, chunk_tiles, 0, true);
+  } else if (b->n_spec == n_d) {
+    rc = build(b, 1, 0, true);   // no items: nothing to tune
   } else {
     const std::string key = tune_key(b);
     int c = 0, g = 0;
     if (tune_lookup(key, &c, &g)) {
-      rc = build(b, c, g);
+      rc = build(b, c, g, true);
     } else {
       // candidates: chunk sizes giving about 2..32 items per resident block, full grid
       long long tiles = 0;
-      for (int d = 0; d < n_d; ++d) tiles += (b->n[d] + kBlock - 1) / kBlock;
+      for (int d = 0; d < n_d; ++d)
+        if (!b->spec[d]) tiles += (b->n[d] + kBlock - 1) / kBlock;
       DeviceProps dp = device_props(dev);
       const long long slots = (long long)dp.sms * 8;
       std::vector<int> cands;
@@ -448,13 +497,13 @@ int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* sampl
       double best = 1e300;
       int best_c = cands[0];
       for (int ch : cands) {
-        rc = build(b, ch, 0);
+        rc = build(b, ch, 0, false);
         if (rc) break;
         double ms = time_replays(b, 2);
         if (ms < best) { best = ms; best_c = ch; }
       }
       if (!rc) {
-        rc = build(b, best_c, 0);
+        rc = build(b, best_c, 0, true);
         b->tuned_ms = best;
         if (!rc) tune_store(key, b->chunk, b->grid);
       }
@@ -475,6 +524,14 @@ int tami_batch_info(const tami_batch* b, int* n_items, int* grid, int* chunk_til
   if (n_items) *n_items = b->n_items;
   if (grid) *grid = b->grid;
   if (chunk_tiles) *chunk_tiles = b->chunk;
+  return TAMI_OK;
+}
+
+int tami_batch_specialised(const tami_batch* b, int* flags, int* n_specialised) {
+  if (!b) { set_error("NULL batch"); return TAMI_EINVAL; }
+  if (flags)
+    for (int d = 0; d < b->n_d; ++d) flags[d] = b->spec[d];
+  if (n_specialised) *n_specialised = b->n_spec;
   return TAMI_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <array>
 #include <cmath>
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -145,6 +146,26 @@ int jit_select(tami_diagram* d, int kind, int64_t n, int n_f);
 int jit_launch(tami_diagram* d, int kind, const tami_lattice* lat, uint64_t seed, uint64_t offset, int64_t n,
                const double* X, int n_f, double beta, const double* gout, double* per_sample, double* ps_dX,
                double* ps_grad, double* saved, double* partial, int max_grid, struct CUstream_st* st, int* grid_out);
+// A compiled specialised kernel held apart from its diagram (a batch keeps its diagrams' kernels
+// loaded after the diagrams are gone).  jit_handle compiles if needed; jit_grid sets the shared
+// memory attribute and returns the launch's grid (resident blocks, capped by the tiles and
+// max_grid); jit_launch_at only launches (legal inside a stream capture).  With params non-NULL the
+// kernel reads (t, t', mu, kx, ky, beta) from that device array instead of lat and beta.
+struct JitHandle {
+  std::shared_ptr<void> lib;
+  void* fn = nullptr;
+  size_t smem = 0;
+};
+int jit_handle(tami_diagram* d, int kind, int n_f, JitHandle* h);
+int jit_grid(const JitHandle& h, int64_t n, int max_grid, int* grid);
+int jit_launch_at(const JitHandle& h, int grid, const tami_lattice* lat, const double* params, uint64_t seed,
+                  uint64_t offset, int64_t n, const double* X, int n_f, double beta, const double* gout,
+                  double* per_sample, double* ps_dX, double* ps_grad, double* saved, double* partial,
+                  struct CUstream_st* st);
+// Which diagrams of a batch take their specialised forward kernel (use[d] = 1; compiled here on
+// parallel host threads): none in mode "never"; in "auto" those with >= 2^20 samples whose kernel
+// builds; in "always" every diagram, else the status of the first that cannot be built.
+int jit_select_batch(tami_diagram* const* ds, int n_d, const int64_t* n, int n_f, int* use);
 void jit_mark_generic(tami_diagram* d);
 void jit_release(tami_diagram* d);
 // Checks every index and range of a flattened table (tami_validate.cpp); false with the reason.

@@ -24,7 +24,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
+#include <memory>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -261,9 +264,11 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   o("extern \"C\" __global__ void __launch_bounds__(%d, 8) %s(double lt, double ltp, double lmu, double lkx, double lky,",
     kJitBlock, kKernelName[kind]);
   o("    unsigned long long seed, unsigned long long offset, long long n, const double* X, const double* G, int n_f,");
-  o("    double beta, double* ps_dX, double* ps_grad, double* ps_v, double* saved, double* partial) {");
+  o("    double beta, double* ps_dX, double* ps_grad, double* ps_v, double* saved, double* partial, const double* P) {");
   o("  extern __shared__ __align__(16) double smem[];");
   o("  const int tid = threadIdx.x;");
+  // a launch captured once in a graph reads (t, t', mu, kx, ky, beta) from device memory
+  o("  if (P) { lt = P[0]; ltp = P[1]; lmu = P[2]; lkx = P[3]; lky = P[4]; beta = P[5]; }");
   if (energy) {
     // Xs [n_xk][n_f][2]: the frequencies as the denominators see them, Y_kf = sum_q v_kq X_fq
     o("  double* Xs = smem; double* AXI = Xs + %d * n_f; double* AXI2 = AXI + %d * n_f;", 2 * h.n_xk, h.n_cden);
@@ -516,7 +521,7 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
 
 // --------------------------------------------------------------------------- compile, cache, launch
 struct JitKernel {
-  cudaLibrary_t lib = nullptr;
+  std::shared_ptr<void> lib;    // the loaded cubin; unloaded when its last holder lets go
   cudaKernel_t fn = nullptr;
   double compile_ms = 0.0;
   bool failed = false;
@@ -538,10 +543,7 @@ JitState* jit_state(tami_diagram* d) {
 
 void jit_release(tami_diagram* d) {
   if (!d || !d->jit) return;
-  JitState* s = static_cast<JitState*>(d->jit);
-  for (JitKernel& k : s->k)
-    if (k.lib) cudaLibraryUnload(k.lib);
-  delete s;
+  delete static_cast<JitState*>(d->jit);
   d->jit = nullptr;
 }
 
@@ -552,10 +554,7 @@ int jit_prepare(tami_diagram* d, int kind) {
   JitState* s = jit_state(d);
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->device != d->device) {          // a new upload device: build again for it
-    for (JitKernel& k : s->k) {
-      if (k.lib) cudaLibraryUnload(k.lib);
-      k = JitKernel{};
-    }
+    for (JitKernel& k : s->k) k = JitKernel{};
     s->device = d->device;
   }
   JitKernel& K = s->k[kind];
@@ -591,9 +590,11 @@ int jit_prepare(tami_diagram* d, int kind) {
   std::vector<char> cubin(nb);
   nv.cubin(prog, cubin.data());
   nv.destroy(&prog);
-  cudaError_t e = cudaLibraryLoadData(&K.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  cudaLibrary_t lib = nullptr;
+  cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
   if (e != cudaSuccess) return fail(std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e));
-  e = cudaLibraryGetKernel(&K.fn, K.lib, kKernelName[kind]);
+  K.lib = std::shared_ptr<void>(lib, [](void* l) { cudaLibraryUnload(static_cast<cudaLibrary_t>(l)); });
+  e = cudaLibraryGetKernel(&K.fn, lib, kKernelName[kind]);
   if (e != cudaSuccess) return fail(std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e));
   K.compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return TAMI_OK;
@@ -622,34 +623,107 @@ int jit_select(tami_diagram* d, int kind, int64_t n, int n_f) {
   return mode == TAMI_JIT_ALWAYS ? -rc : 0;
 }
 
-int jit_launch(tami_diagram* d, int kind, const tami_lattice* lat, uint64_t seed, uint64_t offset, int64_t n,
-               const double* X, int n_f, double beta, const double* gout, double* per_sample, double* ps_dX,
-               double* ps_grad, double* saved, double* partial, int max_grid, struct CUstream_st* st, int* grid_out) {
+int jit_handle(tami_diagram* d, int kind, int n_f, JitHandle* h) {
+  const int rc = jit_prepare(d, kind);
+  if (rc) return rc;
   JitState* s = jit_state(d);
-  const size_t smem = jit_smem(d->hdr, kind, n_f);
-  const void* fn = reinterpret_cast<const void*>(s->k[kind].fn);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  std::lock_guard<std::mutex> lk(s->mu);
+  h->lib = s->k[kind].lib;
+  h->fn = reinterpret_cast<void*>(s->k[kind].fn);
+  h->smem = jit_smem(d->hdr, kind, n_f);
+  return TAMI_OK;
+}
+
+int jit_grid(const JitHandle& h, int64_t n, int max_grid, int* grid_out) {
+  cudaError_t e = cudaFuncSetAttribute(h.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h.smem);
   if (e != cudaSuccess) { set_error(std::string("specialised kernel attribute: ") + cudaGetErrorString(e)); return TAMI_ECUDA; }
-  int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kJitBlock, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device);
+  int per_sm = 0, sms = 0, dev = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h.fn, kJitBlock, h.smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   long long grid = (long long)sms * per_sm;
   const long long tiles = (n + kJitBlock - 1) / kJitBlock;
   if (grid > tiles) grid = tiles;
   if (grid > max_grid) grid = max_grid;   // the caller's workspace holds max_grid partial rows
   if (grid < 1) grid = 1;
-  double lt = lat->t, ltp = lat->tp, lmu = lat->mu, lkx = lat->kx_ext, lky = lat->ky_ext;
+  *grid_out = (int)grid;
+  return TAMI_OK;
+}
+
+int jit_launch_at(const JitHandle& h, int grid, const tami_lattice* lat, const double* params, uint64_t seed,
+                  uint64_t offset, int64_t n, const double* X, int n_f, double beta, const double* gout,
+                  double* per_sample, double* ps_dX, double* ps_grad, double* saved, double* partial,
+                  struct CUstream_st* st) {
+  double lt = lat ? lat->t : 0.0, ltp = lat ? lat->tp : 0.0, lmu = lat ? lat->mu : 0.0;
+  double lkx = lat ? lat->kx_ext : 0.0, lky = lat ? lat->ky_ext : 0.0;
   unsigned long long sd = seed, off = offset;
   long long nn = n;
   int nf = n_f;
   double b = beta;
-  const double *Xp = X, *Gp = gout;
+  const double *Xp = X, *Gp = gout, *Pp = params;
   double *pdx = ps_dX, *pg = ps_grad, *pv = per_sample, *sv = saved, *pp = partial;
-  void* args[] = {&lt, &ltp, &lmu, &lkx, &lky, &sd, &off, &nn, &Xp, &Gp, &nf, &b, &pdx, &pg, &pv, &sv, &pp};
-  e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kJitBlock), args, smem, st);
+  void* args[] = {&lt, &ltp, &lmu, &lkx, &lky, &sd, &off, &nn, &Xp, &Gp, &nf, &b, &pdx, &pg, &pv, &sv, &pp, &Pp};
+  const cudaError_t e = cudaLaunchKernel(h.fn, dim3((unsigned)grid), dim3(kJitBlock), args, h.smem, st);
   if (e != cudaSuccess) { set_error(std::string("specialised kernel launch: ") + cudaGetErrorString(e)); return TAMI_ECUDA; }
-  s->last_used = 1;
-  *grid_out = (int)grid;
+  return TAMI_OK;
+}
+
+int jit_launch(tami_diagram* d, int kind, const tami_lattice* lat, uint64_t seed, uint64_t offset, int64_t n,
+               const double* X, int n_f, double beta, const double* gout, double* per_sample, double* ps_dX,
+               double* ps_grad, double* saved, double* partial, int max_grid, struct CUstream_st* st, int* grid_out) {
+  JitHandle h;
+  int rc = jit_handle(d, kind, n_f, &h);
+  if (!rc) rc = jit_grid(h, n, max_grid, grid_out);
+  if (!rc) rc = jit_launch_at(h, *grid_out, lat, nullptr, seed, offset, n, X, n_f, beta, gout, per_sample, ps_dX,
+                              ps_grad, saved, partial, st);
+  if (rc) return rc;
+  jit_state(d)->last_used = 1;
+  return TAMI_OK;
+}
+
+int jit_select_batch(tami_diagram* const* ds, int n_d, const int64_t* n, int n_f, int* use) {
+  for (int d = 0; d < n_d; ++d) use[d] = 0;
+  const int mode = jit_mode();
+  if (mode == TAMI_JIT_NEVER) return TAMI_OK;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  std::vector<int> todo;
+  for (int d = 0; d < n_d; ++d) {
+    std::string why;
+    const bool fits = n_f <= kJitMaxFreq && jit_smem(ds[d]->hdr, kKindFwd, n_f) <= (size_t)optin;
+    const bool ok = fits && jit_supported(ds[d]->hdr, kKindFwd, &why);
+    if (mode == TAMI_JIT_AUTO && (n[d] < (int64_t(1) << 20) || !ok)) continue;
+    if (!ok) {
+      set_error("specialised kernel: " + (fits ? why : std::string("frequencies beyond its per-thread sums or shared memory")));
+      return TAMI_EUNSUPPORTED;
+    }
+    todo.push_back(d);
+  }
+  // compile on up to one host thread per core (NVRTC programs are independent)
+  std::vector<int> rc(todo.size(), TAMI_OK);
+  std::vector<std::string> err(todo.size());
+  std::atomic<size_t> next{0};
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    for (size_t i; (i = next.fetch_add(1)) < todo.size();) {
+      rc[i] = jit_prepare(ds[todo[i]], kKindFwd);
+      if (rc[i]) err[i] = tami_last_error();
+    }
+  };
+  const size_t n_thr = std::min<size_t>(std::max(1u, std::thread::hardware_concurrency()), todo.size());
+  std::vector<std::thread> pool;
+  for (size_t t = 1; t < n_thr; ++t) pool.emplace_back(work);
+  work();
+  for (std::thread& t : pool) t.join();
+  for (size_t i = 0; i < todo.size(); ++i) {
+    if (rc[i] == TAMI_OK) {
+      use[todo[i]] = 1;
+    } else if (mode == TAMI_JIT_ALWAYS) {
+      set_error(err[i]);
+      return rc[i];
+    }
+  }
   return TAMI_OK;
 }
 

@@ -1,6 +1,10 @@
 """GPU tests of the persistent multi-diagram launch (tami_batch_*): every diagram's mean and
 variance against the CPU oracle, against separate tami_forward launches on the same samples,
-determinism of a plan, the autotuner and its cache, and the full all-orders workload."""
+determinism of a plan, the autotuner and its cache, and the full all-orders workload; plans whose
+diagrams run their specialised forward kernels (all of them, or the large ones beside the
+persistent kernel), the parameters such a captured plan reads at each launch, and the kernels a
+plan keeps after its diagrams are gone."""
+import gc
 import os
 
 import numpy as np
@@ -42,14 +46,14 @@ LAT = (1.0, -0.2, 0.1, np.pi / 2, np.pi / 3)
 BETA = 5.0
 
 
-@pytest.mark.parametrize("chunk", [1, 3])
-def test_batch_against_oracle(chunk):
-    lib, orc, counts, seeds = mixed_batch()
-    X = W.matsubara(BETA, 5)
-    B = T.Batch(lib, counts, seeds, len(X), chunk_tiles=chunk)
-    assert B.info()["chunk_tiles"] == chunk
-    mean, var = B.launch(LAT, X, BETA)
-    torch.cuda.synchronize()
+@pytest.fixture
+def jit():
+    """set_jit for one test, restored to the default afterwards."""
+    yield T.set_jit
+    T.set_jit("auto")
+
+
+def check_against_oracle(mean, var, orc, counts, seeds, X):
     mean, var = mean.cpu().numpy(), var.cpu().numpy()
     for d, (S, n, sd) in enumerate(zip(orc, counts, seeds)):
         ref = S.eval_momenta(LAT, sd, 0, n, X, BETA, per_sample=True, threads=8)
@@ -60,6 +64,125 @@ def test_batch_against_oracle(chunk):
             tol = 2.0 / max(n - 1, 1) * np.sum(np.abs(part(dev)) * RTOL * ref["envelope"], axis=1) \
                 + 1e-10 * ref["var"][:, k]
             assert np.all(np.abs(var[d][:, k] - ref["var"][:, k]) <= tol), d
+
+
+@pytest.mark.parametrize("chunk", [1, 3])
+def test_batch_against_oracle(chunk):
+    lib, orc, counts, seeds = mixed_batch()
+    X = W.matsubara(BETA, 5)
+    B = T.Batch(lib, counts, seeds, len(X), chunk_tiles=chunk)
+    assert B.info()["chunk_tiles"] == chunk and B.info()["specialised"] == 0
+    mean, var = B.launch(LAT, X, BETA)
+    torch.cuda.synchronize()
+    check_against_oracle(mean, var, orc, counts, seeds, X)
+
+
+def test_specialised_batch_against_oracle(jit):
+    """Mode "always": every diagram runs its own generated forward kernel in the plan's graph (no
+    work items); means and variances meet the oracle bar as the persistent kernel's do."""
+    jit("always")
+    lib, orc, counts, seeds = mixed_batch()
+    X = W.matsubara(BETA, 5)
+    B = T.Batch(lib, counts, seeds, len(X))
+    info = B.info()
+    assert info["specialised"] == len(lib) and info["items"] == 0 and info["grid"] == 0
+    mean, var = B.launch(LAT, X, BETA)
+    torch.cuda.synchronize()
+    check_against_oracle(mean, var, orc, counts, seeds, X)
+
+
+def single_calls(lib, counts, seeds, lat, X, beta):
+    """Each diagram's tami_forward over its batch samples (the current mode picks the kernel):
+    means, variances and the mean per-sample magnitude."""
+    out = []
+    for d, D in enumerate(lib):
+        D.upload(0)
+        m, v, ps = D.forward(lat, seeds[d], 0, counts[d], X, beta, per_sample=True)
+        out.append((m, v, ps.abs().mean(dim=1)))
+    return out
+
+
+def same_code_close(mean, var, ref, rel=1e-12):
+    """Batch results against single calls running the same kernel code: they differ only in how
+    the partial sums are grouped."""
+    for d, (m, v, scale) in enumerate(ref):
+        assert torch.all((mean[d] - m).abs() <= rel * scale), d
+        assert torch.allclose(var[d], v, rtol=1e-10, atol=0), d
+
+
+def test_specialised_batch_reads_each_launchs_parameters(jit):
+    """The specialised kernels are captured once; a later launch with another lattice, beta and
+    frequencies (same count) must use them, as single calls with those inputs do."""
+    lib, orc, counts, seeds = mixed_batch()
+    X1, X2 = W.matsubara(BETA, 6), W.real_axis(-1.5, 2.5, 6, 0.2)
+    lat2, beta2 = (0.8, 0.25, -0.3, 0.4, -1.1), 3.0
+    jit("always")
+    B = T.Batch(lib, counts, seeds, 6)
+    assert B.info()["specialised"] == len(lib)
+    r1 = single_calls(lib, counts, seeds, LAT, X1, BETA)
+    r2 = single_calls(lib, counts, seeds, lat2, X2, beta2)
+    for _ in range(2):
+        m1, v1 = B.launch(LAT, X1, BETA)
+        m2, v2 = B.launch(lat2, X2, beta2)
+        torch.cuda.synchronize()
+        same_code_close(m1, v1, r1)
+        same_code_close(m2, v2, r2)
+        assert not torch.allclose(m1, m2)
+
+
+def test_auto_mixes_specialised_and_persistent_diagrams(jit):
+    """Mode "auto": the diagram with 2^20 samples takes its specialised kernel, the others stay
+    work items of the persistent kernel in the same graph.  Results repeat bit for bit; the
+    persistent kernel's diagrams give the bits of a plan without specialised kernels, the
+    specialised one agrees with its single specialised call."""
+    lib, orc, counts, seeds = mixed_batch()
+    counts = [1 << 20] + counts[1:]
+    X = W.matsubara(BETA, 8)
+    jit("auto")
+    B = T.Batch(lib, counts, seeds, len(X), chunk_tiles=2)
+    info = B.info()
+    assert info["specialised_diagrams"] == [0] and info["items"] >= 1
+    m1, v1 = B.launch(LAT, X, BETA)
+    m2, v2 = B.launch(LAT, X, BETA)
+    jit("never")
+    G = T.Batch(lib, counts, seeds, len(X), chunk_tiles=2)
+    assert G.info()["specialised"] == 0
+    g, gv = G.launch(LAT, X, BETA)
+    torch.cuda.synchronize()
+    assert torch.equal(m1, m2) and torch.equal(v1, v2)
+    assert torch.equal(m1[1:], g[1:]) and torch.equal(v1[1:], gv[1:])
+    jit("always")
+    ref = single_calls(lib[:1], counts[:1], seeds[:1], LAT, X, BETA)
+    assert lib[0].jit_status()["last_used"]
+    same_code_close(m1[:1], v1[:1], ref)
+
+
+def test_plan_keeps_its_kernels_after_the_diagrams_are_destroyed(jit):
+    jit("always")
+    lib, orc, counts, seeds = mixed_batch()
+    X = W.matsubara(BETA, 3)
+    B = T.Batch(lib, counts, seeds, len(X))
+    m1, v1 = B.launch(LAT, X, BETA)
+    torch.cuda.synchronize()
+    B.diagrams = []
+    del lib
+    gc.collect()
+    m2, v2 = B.launch(LAT, X, BETA)
+    torch.cuda.synchronize()
+    assert torch.equal(m1, m2) and torch.equal(v1, v2)
+
+
+def test_specialised_limits_in_batches(jit):
+    """More frequencies than the specialised kernels' per-thread sums hold (256): "always" refuses
+    the plan, "auto" keeps every diagram on the persistent kernel."""
+    lib, orc, counts, seeds = mixed_batch()
+    jit("always")
+    with pytest.raises(L.TamiError) as e:
+        T.Batch(lib[:1], [1 << 20], seeds[:1], 300, chunk_tiles=4)
+    assert e.value.code == L.TAMI_EUNSUPPORTED
+    jit("auto")
+    B = T.Batch(lib[:1], [1 << 20], seeds[:1], 300, chunk_tiles=4)
+    assert B.info()["specialised"] == 0 and B.info()["items"] >= 1
 
 
 def test_batch_matches_single_launches_and_is_deterministic():
@@ -129,12 +252,17 @@ def test_poisoned_queue_entry_is_refused_without_a_fault():
     assert torch.equal(m1, m0) and torch.equal(v1, v0)
 
 
-def test_all_orders_workload_full_size():
+@pytest.mark.parametrize("mode", ["never", "auto"])
+def test_all_orders_workload_full_size(mode, jit):
     """Every Hubbard self-energy diagram of orders 2..5 (85 diagrams), diagram d with
     2^(20 + d mod 4) samples and seed 20231128 + d, 32 Matsubara frequencies, beta = 5, in one
-    persistent launch; each diagram's mean against a separate tami_forward launch over the same
-    samples on the generic kernel, whose tile code the persistent kernel shares (the two then
-    differ only in how partial sums are grouped)."""
+    graph launch: the persistent kernel over every diagram ("never"), or every diagram's
+    specialised forward kernel ("auto": all have >= 2^20 samples).  Each diagram's mean against a
+    separate tami_forward launch over the same samples running the same code (the generic kernel,
+    whose tile code the persistent kernel shares, or the diagram's specialised kernel), so the two
+    differ only in how partial sums are grouped.  The two kernel families differ by more than that
+    (their multiply-adds are contracted differently, and the terms cancel), so each meets the
+    oracle bar in its own small-size tests instead."""
     c = W.ALL_ORDERS
     diags, lib = [], []
     for m in c["orders"]:
@@ -146,17 +274,17 @@ def test_all_orders_workload_full_size():
     seeds = [c["seed"] + d for d in range(n_d)]
     X = W.matsubara(c["beta"], c["n_freq"])
     lat = W.lattice(c)
+    jit(mode)
     B = T.Batch(lib, counts, seeds, len(X), chunk_tiles=16)
+    assert B.info()["specialised"] == (n_d if mode == "auto" else 0)
     mean, var = B.launch(lat, X, c["beta"])
     torch.cuda.synchronize()
     assert torch.isfinite(torch.view_as_real(mean)).all()
-    T.set_jit("never")
-    try:
-        for d, D in enumerate(lib):
-            D.upload(0)
-            m, v, _ = D.forward(lat, seeds[d], 0, counts[d], X, c["beta"])
-            rms = torch.sqrt(v.sum(dim=1) + m.abs() ** 2)
-            assert torch.all((mean[d] - m).abs() <= 1e-12 * rms), d
-            assert torch.allclose(var[d], v, rtol=1e-9, atol=0)
-    finally:
-        T.set_jit("auto")
+    jit("always" if mode == "auto" else "never")
+    for d, D in enumerate(lib):
+        D.upload(0)
+        m, v, _ = D.forward(lat, seeds[d], 0, counts[d], X, c["beta"])
+        assert D.jit_status()["last_used"] == (mode == "auto")
+        rms = torch.sqrt(v.sum(dim=1) + m.abs() ** 2)
+        assert torch.all((mean[d] - m).abs() <= 1e-12 * rms), d
+        assert torch.allclose(var[d], v, rtol=1e-9, atol=0)

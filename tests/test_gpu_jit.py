@@ -297,14 +297,27 @@ T.set_jit("never")
 r2 = D.forward_backward(W.lattice(c), c["seed"], 0, 1 << 21, X, c["beta"], g)
 torch.cuda.synchronize()
 out["same_as_generic"] = bool(torch.equal(r["mean"], r2["mean"]))
+T.set_jit("auto")
+B = T.Batch([D], [1 << 20], [c["seed"]], len(X), chunk_tiles=4)
+out["batch_auto_specialised"] = B.info()["specialised"]
+m, _ = B.launch(W.lattice(c), X, c["beta"])
+torch.cuda.synchronize()
+out["batch_auto_finite"] = bool(torch.isfinite(torch.view_as_real(m)).all())
+T.set_jit("always")
+try:
+    T.Batch([D], [1 << 20], [c["seed"]], len(X), chunk_tiles=4)
+    out["batch_always"] = "planned"
+except L.TamiError as e:
+    out["batch_always"] = [e.code, str(e)]
 print(json.dumps(out))
 """
 
 
 def test_without_nvrtc_auto_falls_back_and_always_refuses(tmp_path):
     """Failure of the run-time compiler, made on the host ($TAMI_NVRTC=none, in a child process):
-    `auto` runs the generic kernel (the same bits as `never`), `always` refuses the call with
-    TAMI_EUNSUPPORTED and says why, and nothing faults."""
+    `auto` runs the generic kernel (the same bits as `never`) and plans batches on the persistent
+    kernel alone, `always` refuses the call and the plan with TAMI_EUNSUPPORTED and says why, and
+    nothing faults."""
     import json
     import os
     import subprocess
@@ -318,3 +331,5 @@ def test_without_nvrtc_auto_falls_back_and_always_refuses(tmp_path):
     out = json.loads(r.stdout.strip().splitlines()[-1])
     assert out["auto_finite"] and not out["auto_used"] and out["same_as_generic"]
     assert out["always"][0] == L.TAMI_EUNSUPPORTED and "NVRTC disabled" in out["always"][1]
+    assert out["batch_auto_specialised"] == 0 and out["batch_auto_finite"]
+    assert out["batch_always"][0] == L.TAMI_EUNSUPPORTED and "NVRTC disabled" in out["batch_always"][1]
