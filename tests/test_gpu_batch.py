@@ -267,8 +267,11 @@ def test_all_orders_workload_full_size(mode, jit):
     diags, lib = [], []
     for m in c["orders"]:
         for d in T.enumerate_sigma(m):
+            diags.append((m, d))
             lib.append(T.Diagram(d["alpha"], eps=d["eps"], prefactor=(-1.0) ** m * (-1.0) ** d["loops"]))
     n_d = len(lib)
+    largest = int(np.argmax([D.info()["n_terms"] for D in lib]))
+    sampled = sorted({0, 1, 14, largest})      # orders 2, 3, 4 and the largest order-5 table
     assert n_d == 85
     counts = [W.all_orders_samples(d) for d in range(n_d)]
     seeds = [c["seed"] + d for d in range(n_d)]
@@ -281,10 +284,22 @@ def test_all_orders_workload_full_size(mode, jit):
     torch.cuda.synchronize()
     assert torch.isfinite(torch.view_as_real(mean)).all()
     jit("always" if mode == "auto" else "never")
+    rng = np.random.default_rng(11)
     for d, D in enumerate(lib):
         D.upload(0)
-        m, v, _ = D.forward(lat, seeds[d], 0, counts[d], X, c["beta"])
+        m, v, ps = D.forward(lat, seeds[d], 0, counts[d], X, c["beta"], per_sample=d in sampled)
         assert D.jit_status()["last_used"] == (mode == "auto")
         rms = torch.sqrt(v.sum(dim=1) + m.abs() ** 2)
         assert torch.all((mean[d] - m).abs() <= 1e-12 * rms), d
         assert torch.allclose(var[d], v, rtol=1e-9, atol=0)
+        if d in sampled:
+            # per-sample values of the same kernel at 40 random samples against the oracle
+            order, dd = diags[d]
+            od = next(x for x in O.enumerate_sigma(order) if x["code"] == dd["code"])
+            S = O.Solution(od["alpha"], eps=od["eps"], prefactor=(-1.0) ** order * (-1.0) ** od["loops"])
+            idx = np.sort(rng.choice(counts[d], 40, replace=False))
+            vals = ps[:, torch.as_tensor(idx, device=ps.device)].cpu().numpy()
+            for k, i in enumerate(idx):
+                r = S.eval_momenta(lat, seeds[d], int(i), 1, X, c["beta"], per_sample=True)
+                assert np.all(np.abs(vals[:, k] - r["values"][:, 0]) <= RTOL * r["envelope"][:, 0]), (d, i)
+            del ps
