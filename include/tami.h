@@ -276,8 +276,13 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
  * arrays in local memory.  Each is generated as CUDA C++ on the first call that takes it, compiled
  * for sm_103a with NVRTC (loaded at run time: libnvrtc.so.13, or the path in $TAMI_NVRTC; "none"
  * disables it) and cached with the diagram until tami_destroy.  Values agree with the generic kernels to rounding; workspaces and
- * outputs are those of the generic calls.  tami_forward_noalloc and batches always run the generic
- * kernels.
+ * outputs are those of the generic calls.  tami_forward_noalloc always runs the generic kernel;
+ * batches take the specialised forward kernels of their large diagrams (tami_batch_plan).
+ * Compiled kernels are also kept on disk, one file per compilation, in $TAMI_JIT_CACHE (default
+ * $HOME/.cache/libtami_jit; "none": no disk cache): an entry records the NVRTC version, options,
+ * device arithmetic and source it was built from and a checksum, is loaded only when all of them
+ * match the compilation at hand (and NVRTC loads), and is written through a temporary file and a
+ * rename.  A missing, damaged or unwritable cache only costs a compilation.
  *   mode TAMI_JIT_NEVER   the generic kernel always;
  *        TAMI_JIT_AUTO    (default; $TAMI_JIT = never | auto | always sets the initial mode) the
  *                         specialised kernel for Monte Carlo launches of at least 2^21 samples and
@@ -300,6 +305,10 @@ int tami_jit_prepare(tami_diagram* d);
  * the diagram's last evaluating call ran a specialised kernel (1) or a generic one (0); compile_ms:
  * host time of their generation and compilation. */
 int tami_jit_status(const tami_diagram* d, int* ready, int* last_used, double* compile_ms);
+
+/* from_cache: bit mask (as tami_jit_status's ready) of the built kernels that were loaded from the
+ * disk cache instead of compiled. */
+int tami_jit_cached(const tami_diagram* d, int* from_cache);
 
 /* The generated CUDA C++ source of one kind (0 fused, 1 forward, 2 adjoint, 3 energy input), in host memory,
  * NUL-terminated, truncated to cap bytes; *len is the full size including the NUL.  For inspection

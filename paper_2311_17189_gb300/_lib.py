@@ -20,7 +20,7 @@ EXPORTS = [
     "tami_last_error", "tami_construct", "tami_construct_ext", "tami_label_graph", "tami_construct_from_graph", "tami_diagram_info", "tami_upload", "tami_sample_energies",
     "tami_eval_energies", "tami_forward_workspace", "tami_forward", "tami_forward_noalloc",
     "tami_backward_workspace", "tami_backward", "tami_forward_backward_workspace", "tami_forward_backward",
-    "tami_set_jit", "tami_jit_prepare", "tami_jit_status", "tami_jit_source",
+    "tami_set_jit", "tami_jit_prepare", "tami_jit_status", "tami_jit_source", "tami_jit_cached",
     "tami_batch_plan", "tami_batch_info", "tami_batch_launch",
     "tami_batch_destroy", "tami_batch_debug_set_item", "tami_batch_specialised",
     "tami_enumerate_sigma",
@@ -97,6 +97,7 @@ def lib():
     L.tami_jit_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_double)]
     L.tami_jit_source.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    L.tami_jit_cached.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.tami_batch_plan.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
     L.tami_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int)]

@@ -100,12 +100,15 @@ class Diagram:
     JIT_KINDS = {"fused": 0, "forward": 1, "adjoint": 2, "energy": 3}
 
     def jit_status(self):
-        """Specialised kernels (tami_jit_status): ready = set of built kinds ('fused', 'forward',
-        'adjoint', 'energy'), last_used = whether the last evaluating call ran one, compile_ms."""
-        r, u, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        """Specialised kernels (tami_jit_status, tami_jit_cached): ready = set of built kinds
+        ('fused', 'forward', 'adjoint', 'energy'), last_used = whether the last evaluating call ran
+        one, compile_ms, cached = the built kinds loaded from the disk cache."""
+        r, u, ms, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
         L.check(L.lib().tami_jit_status(self._h, ctypes.byref(r), ctypes.byref(u), ctypes.byref(ms)))
+        L.check(L.lib().tami_jit_cached(self._h, ctypes.byref(c)))
         ready = {k for k, b in self.JIT_KINDS.items() if r.value & (1 << b)}
-        return {"ready": ready, "last_used": bool(u.value), "compile_ms": ms.value}
+        cached = {k for k, b in self.JIT_KINDS.items() if c.value & (1 << b)}
+        return {"ready": ready, "last_used": bool(u.value), "compile_ms": ms.value, "cached": cached}
 
     def jit_source(self, kind="fused"):
         """The CUDA C++ source of one specialised kernel (tami_jit_source)."""

@@ -162,6 +162,14 @@ int jit_launch_at(const JitHandle& h, int grid, const tami_lattice* lat, const d
                   uint64_t offset, int64_t n, const double* X, int n_f, double beta, const double* gout,
                   double* per_sample, double* ps_dX, double* ps_grad, double* saved, double* partial,
                   struct CUstream_st* st);
+// Disk cache of compiled specialised kernels.  An entry holds the identity of its compilation
+// (compiler version, options, device arithmetic, kernel source), the cubin and a checksum of both;
+// jit_cache_read accepts an entry only when the file is whole, its identity equals `ident` byte for
+// byte and the checksum matches, so a damaged or foreign entry never reaches the driver.
+// jit_cache_write writes a temporary file and renames it over `path`.
+uint64_t jit_fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ull);
+bool jit_cache_read(const std::string& path, const std::string& ident, std::vector<char>* cubin);
+bool jit_cache_write(const std::string& path, const std::string& ident, const std::vector<char>& cubin);
 // Which diagrams of a batch take their specialised forward kernel (use[d] = 1; compiled here on
 // parallel host threads): none in mode "never"; in "auto" those with >= 2^20 samples whose kernel
 // builds; in "always" every diagram, else the status of the first that cannot be built.

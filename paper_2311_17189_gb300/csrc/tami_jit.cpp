@@ -15,6 +15,8 @@
 // "always" mode, the call fails with TAMI_EUNSUPPORTED).
 #include <cuda_runtime.h>
 #include <dlfcn.h>
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <chrono>
@@ -24,6 +26,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <atomic>
 #include <memory>
 #include <mutex>
@@ -71,6 +74,8 @@ struct Nvrtc {
   typedef int (*GetData)(void*, char*);
   typedef int (*Destroy)(void**);
   typedef const char* (*ErrStr)(int);
+  typedef int (*Version)(int*, int*);
+  std::string version;           // "nvrtc <major>.<minor>", part of every disk-cache entry's identity
   Create create = nullptr;
   Compile compile = nullptr;
   GetSize log_size = nullptr, cubin_size = nullptr;
@@ -102,10 +107,33 @@ Nvrtc& nvrtc() {
   n.cubin = (Nvrtc::GetData)dlsym(h, "nvrtcGetCUBIN");
   n.destroy = (Nvrtc::Destroy)dlsym(h, "nvrtcDestroyProgram");
   n.err = (Nvrtc::ErrStr)dlsym(h, "nvrtcGetErrorString");
-  n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy && n.err;
+  Nvrtc::Version ver = (Nvrtc::Version)dlsym(h, "nvrtcVersion");
+  int major = 0, minor = 0;
+  n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy && n.err && ver &&
+         ver(&major, &minor) == 0;
+  n.version = "nvrtc " + std::to_string(major) + "." + std::to_string(minor);
   if (!n.ok) n.why = "NVRTC lacks an expected entry point";
   return n;
 }
+
+// --------------------------------------------------------------------------- disk cache of cubins
+// $TAMI_JIT_CACHE names the directory (default $HOME/.cache/libtami_jit; "none": no cache).  The
+// cache is consulted only when NVRTC loads, since the compiler's version is part of every entry's
+// identity.
+std::string jit_cache_dir() {
+  const char* p = std::getenv("TAMI_JIT_CACHE");
+  if (p && !std::strcmp(p, "none")) return "";
+  if (p && *p) return p;
+  const char* h = std::getenv("HOME");
+  return std::string(h ? h : ".") + "/.cache/libtami_jit";
+}
+
+void make_dirs(const std::string& dir) {   // mkdir -p; failures show up when the file is written
+  for (size_t i = 1; i <= dir.size(); ++i)
+    if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+}
+
+const char kCacheMagic[8] = {'T', 'A', 'M', 'I', 'J', 'I', 'T', '1'};
 
 // --------------------------------------------------------------------------- the generator
 struct Table {
@@ -519,11 +547,70 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   return o.s;
 }
 
+// --------------------------------------------------------------------------- disk cache entries
+uint64_t jit_fnv1a(const void* p, size_t n, uint64_t h) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+  return h;
+}
+
+// Entry layout: magic (8 bytes), identity length (u64), identity, cubin length (u64), cubin,
+// FNV-1a 64 of identity then cubin (u64).
+bool jit_cache_read(const std::string& path, const std::string& ident, std::vector<char>* cubin) {
+  FILE* f = std::fopen(path.c_str(), "rb");
+  if (!f) return false;
+  std::vector<char> buf;
+  char chunk[65536];
+  size_t got;
+  while ((got = std::fread(chunk, 1, sizeof chunk, f)) > 0 && buf.size() <= (size_t(64) << 20))
+    buf.insert(buf.end(), chunk, chunk + got);
+  std::fclose(f);
+  size_t at = 0;
+  auto take_u64 = [&](uint64_t* v) {
+    if (buf.size() - at < 8) return false;
+    std::memcpy(v, buf.data() + at, 8);
+    at += 8;
+    return true;
+  };
+  uint64_t n_ident = 0, n_cubin = 0, sum = 0;
+  if (buf.size() < 8 || std::memcmp(buf.data(), kCacheMagic, 8)) return false;
+  at = 8;
+  if (!take_u64(&n_ident) || n_ident != ident.size() || buf.size() - at < n_ident) return false;
+  if (std::memcmp(buf.data() + at, ident.data(), n_ident)) return false;
+  at += n_ident;
+  if (!take_u64(&n_cubin) || n_cubin == 0 || buf.size() - at < n_cubin) return false;
+  const char* cb = buf.data() + at;
+  at += n_cubin;
+  if (!take_u64(&sum) || at != buf.size()) return false;
+  if (sum != jit_fnv1a(cb, n_cubin, jit_fnv1a(ident.data(), ident.size()))) return false;
+  cubin->assign(cb, cb + n_cubin);
+  return true;
+}
+
+bool jit_cache_write(const std::string& path, const std::string& ident, const std::vector<char>& cubin) {
+  const size_t slash = path.find_last_of('/');
+  if (slash != std::string::npos && slash > 0) make_dirs(path.substr(0, slash));
+  const std::string tmp = path + ".tmp" + std::to_string((long long)getpid()) + "_" +
+                          std::to_string(std::hash<std::thread::id>{}(std::this_thread::get_id()));
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return false;
+  const uint64_t n_ident = ident.size(), n_cubin = cubin.size();
+  const uint64_t sum = jit_fnv1a(cubin.data(), cubin.size(), jit_fnv1a(ident.data(), ident.size()));
+  bool ok = std::fwrite(kCacheMagic, 1, 8, f) == 8 && std::fwrite(&n_ident, 8, 1, f) == 1 &&
+            std::fwrite(ident.data(), 1, ident.size(), f) == ident.size() && std::fwrite(&n_cubin, 8, 1, f) == 1 &&
+            std::fwrite(cubin.data(), 1, cubin.size(), f) == cubin.size() && std::fwrite(&sum, 8, 1, f) == 1;
+  ok = (std::fclose(f) == 0) && ok;
+  if (ok) ok = std::rename(tmp.c_str(), path.c_str()) == 0;
+  if (!ok) std::remove(tmp.c_str());
+  return ok;
+}
+
 // --------------------------------------------------------------------------- compile, cache, launch
 struct JitKernel {
   std::shared_ptr<void> lib;    // the loaded cubin; unloaded when its last holder lets go
   cudaKernel_t fn = nullptr;
   double compile_ms = 0.0;
+  bool from_cache = false;      // the cubin came from the disk cache
   bool failed = false;
   std::string error;
 };
@@ -572,30 +659,66 @@ int jit_prepare(tami_diagram* d, int kind) {
   const std::string src = jit_source(d->hdr, d->blob.data(), kind);
   const char* hdr_src[1] = {kDevmathSource};
   const char* hdr_name[1] = {"tami_devmath.cuh"};
-  void* prog = nullptr;
-  int rc = nv.create(&prog, src.c_str(), "tami_jit.cu", 1, hdr_src, hdr_name);
-  if (rc) return fail(std::string("nvrtcCreateProgram: ") + nv.err(rc));
   const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-w"};
-  rc = nv.compile(prog, 3, opts);
-  if (rc) {
-    size_t n = 0;
-    nv.log_size(prog, &n);
-    std::string log(n, '\0');
-    if (n) nv.log(prog, &log[0]);
-    nv.destroy(&prog);
-    return fail(std::string("NVRTC compile failed: ") + nv.err(rc) + "\n" + log.substr(0, 2000));
+  const int n_opts = (int)(sizeof opts / sizeof opts[0]);
+  // identity of the compilation: compiler, options, the included header and the source
+  std::string ident = nv.version + "\n";
+  for (const char* o : opts) ident += std::string(o) + " ";
+  ident += "\n";
+  ident += kDevmathSource;
+  ident += "\n";
+  ident += src;
+  std::string path;
+  const std::string dir = jit_cache_dir();
+  if (!dir.empty()) {
+    char name[32];
+    std::snprintf(name, sizeof name, "%016llx.tjc",
+                  (unsigned long long)jit_fnv1a(ident.data(), ident.size(), 1469598103934665603ull));
+    path = dir + "/" + name;
   }
-  size_t nb = 0;
-  nv.cubin_size(prog, &nb);
-  std::vector<char> cubin(nb);
-  nv.cubin(prog, cubin.data());
-  nv.destroy(&prog);
-  cudaLibrary_t lib = nullptr;
-  cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-  if (e != cudaSuccess) return fail(std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e));
-  K.lib = std::shared_ptr<void>(lib, [](void* l) { cudaLibraryUnload(static_cast<cudaLibrary_t>(l)); });
-  e = cudaLibraryGetKernel(&K.fn, lib, kKernelName[kind]);
-  if (e != cudaSuccess) return fail(std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e));
+  auto compile = [&](std::vector<char>* cubin) -> std::string {   // "" on success, else the error
+    void* prog = nullptr;
+    int rc = nv.create(&prog, src.c_str(), "tami_jit.cu", 1, hdr_src, hdr_name);
+    if (rc) return std::string("nvrtcCreateProgram: ") + nv.err(rc);
+    rc = nv.compile(prog, n_opts, opts);
+    if (rc) {
+      size_t n = 0;
+      nv.log_size(prog, &n);
+      std::string log(n, '\0');
+      if (n) nv.log(prog, &log[0]);
+      nv.destroy(&prog);
+      return std::string("NVRTC compile failed: ") + nv.err(rc) + "\n" + log.substr(0, 2000);
+    }
+    size_t nb = 0;
+    nv.cubin_size(prog, &nb);
+    cubin->resize(nb);
+    nv.cubin(prog, cubin->data());
+    nv.destroy(&prog);
+    return "";
+  };
+  auto load = [&](const std::vector<char>& cubin, std::string* err) {
+    cudaLibrary_t lib = nullptr;
+    cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) { *err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e); return false; }
+    K.lib = std::shared_ptr<void>(lib, [](void* l) { cudaLibraryUnload(static_cast<cudaLibrary_t>(l)); });
+    e = cudaLibraryGetKernel(&K.fn, lib, kKernelName[kind]);
+    if (e != cudaSuccess) {
+      K.lib.reset();
+      K.fn = nullptr;
+      *err = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e);
+      return false;
+    }
+    return true;
+  };
+  std::vector<char> cubin;
+  std::string err;
+  K.from_cache = !path.empty() && jit_cache_read(path, ident, &cubin) && load(cubin, &err);
+  if (!K.from_cache) {
+    err = compile(&cubin);
+    if (!err.empty()) return fail(err);
+    if (!load(cubin, &err)) return fail(err);
+    if (!path.empty()) jit_cache_write(path, ident, cubin);   // best effort: a failed write only costs a compile
+  }
   K.compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return TAMI_OK;
 }
@@ -755,6 +878,17 @@ int tami_jit_prepare(tami_diagram* d) {
     ++built;
   }
   if (!built) { set_error("specialised kernel: no kind applies to this table"); return TAMI_EUNSUPPORTED; }
+  return TAMI_OK;
+}
+
+int tami_jit_cached(const tami_diagram* d, int* from_cache) {
+  if (!d || !from_cache) { set_error("NULL argument"); return TAMI_EINVAL; }
+  const JitState* s = static_cast<const JitState*>(d->jit);
+  int mask = 0;
+  if (s)
+    for (int k = 0; k < kKinds; ++k)
+      if (s->k[k].fn && s->k[k].from_cache) mask |= 1 << k;
+  *from_cache = mask;
   return TAMI_OK;
 }
 

@@ -333,3 +333,63 @@ def test_without_nvrtc_auto_falls_back_and_always_refuses(tmp_path):
     assert out["always"][0] == L.TAMI_EUNSUPPORTED and "NVRTC disabled" in out["always"][1]
     assert out["batch_auto_specialised"] == 0 and out["batch_auto_finite"]
     assert out["batch_always"][0] == L.TAMI_EUNSUPPORTED and "NVRTC disabled" in out["batch_always"][1]
+
+
+CACHE_SCRIPT = r"""
+import json, sys
+import numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import paper_2311_17189_gb300 as T
+from paper_2311_17189_gb300 import workloads as W
+torch.cuda.set_device(0)
+d = next(x for x in T.enumerate_sigma(4) if x["code"] == tuple(W.ORDER4["code"]))
+D = T.Diagram(d["alpha"], eps=d["eps"]).upload(0)
+c = W.ORDER4
+X, g = W.matsubara(c["beta"], 4), np.ones(4) + 0.5j
+D.jit_prepare()
+st = D.jit_status()
+T.set_jit("always")
+r = D.forward_backward(W.lattice(c), c["seed"], 0, 4096, X, c["beta"], g)
+torch.cuda.synchronize()
+bits = [float(v).hex() for v in torch.view_as_real(r["mean"]).cpu().numpy().ravel()]
+bits += [float(v).hex() for v in r["grad_params"].cpu().numpy().ravel()]
+print(json.dumps({"ready": sorted(st["ready"]), "cached": sorted(st["cached"]), "bits": bits}))
+"""
+
+
+def test_disk_cache_of_compiled_kernels(tmp_path):
+    """Compiled kernels persist across processes: a first process compiles and writes one entry
+    per kind (no temporary file left), a second loads every kind from the cache and gives the same
+    bits; a truncated entry is compiled again and rewritten; $TAMI_JIT_CACHE=none writes nothing."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "cache.py"
+    script.write_text(CACHE_SCRIPT)
+    cache, home = tmp_path / "cache", tmp_path / "home"
+    home.mkdir()
+
+    def run(cache_env):
+        env = dict(os.environ, TAMI_JIT_CACHE=cache_env, HOME=str(home))
+        r = subprocess.run([sys.executable, str(script), root], env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+    first = run(str(cache))
+    assert first["ready"] == ["adjoint", "energy", "forward", "fused"] and first["cached"] == []
+    entries = sorted(cache.iterdir())
+    assert len(entries) == 4 and all(p.suffix == ".tjc" for p in entries)
+    second = run(str(cache))
+    assert second["cached"] == second["ready"] == first["ready"]
+    assert second["bits"] == first["bits"]
+    size = entries[0].stat().st_size
+    with open(entries[0], "r+b") as f:
+        f.truncate(size // 2)
+    third = run(str(cache))
+    assert len(third["cached"]) == 3 and third["bits"] == first["bits"]
+    assert entries[0].stat().st_size == size and len(list(cache.iterdir())) == 4
+    off = run("none")
+    assert off["cached"] == [] and off["bits"] == first["bits"]
+    assert not any(home.rglob("*.tjc"))
