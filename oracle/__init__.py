@@ -6,9 +6,11 @@ Sec. 5.2), written in C++ (ami_oracle.cpp) and loaded here with ctypes.  Only te
 __graft_entry__.smoke() and bench.py's CPU-baseline leg may import this package; the library
 in paper_2311_17189_gb300/ never does, and the two share no code.
 
-Parity status of each function (what pins it) is stated in tests/test_oracle_*.py; the
-enumerator's diagram counts are cross-checked only against the library's own enumerator
-(parity unpinned beyond that).
+Parity status of each function (what pins it) is stated in tests/test_oracle_*.py.  The
+enumerator's diagram set is cross-checked against the library's own enumerator and pinned by the
+half-filled Hubbard atom (tests/test_oracle_atomic.py): its exact self-energy U/2 + U^2/(4 i omega)
+fixes every order's sum, which the enumerated diagrams reach as the line energies go to zero (down
+to a single diagram at orders 2-4; at order 5 only diagrams above a few per cent of the largest).
 """
 import ctypes
 import os
