@@ -395,22 +395,25 @@ def test_disk_cache_of_compiled_kernels(tmp_path):
     assert not any(home.rglob("*.tjc"))
 
 
-def test_specialised_kernels_on_every_enumerated_diagram():
+@pytest.mark.parametrize("mode", ["always", "never"])
+def test_every_enumerated_diagram(mode):
     """Every Hubbard self-energy diagram of orders 2-5 (85 tables, up to 744 flat terms) through
-    its specialised fused forward + adjoint kernel: each sample's value, dSigma/dX and contracted
-    gradients against the oracle, over a tile and a ragged tail; half of the diagrams on the
-    imaginary axis and half on the real axis (the generator's two phase-2 variants).  Also each
-    diagram's specialised energy-input kernel against the oracle's energy-input evaluation.  The
-    kernels are compiled on parallel host threads first."""
+    the fused forward + adjoint kernel and through the two-call path (forward keeping rows, adjoint
+    reading them): each sample's value, dSigma/dX and contracted gradients against the oracle, over
+    a tile and a ragged tail; half of the diagrams on the imaginary axis
+    and half on the real axis (the two phase-2 variants).  Also each diagram's energy-input
+    kernel against the oracle's energy-input evaluation.  "always": the diagrams' specialised
+    kernels (compiled on parallel host threads first); "never": the generic kernels."""
     import os
     from concurrent.futures import ThreadPoolExecutor
     diags = [(m, d) for m in (2, 3, 4, 5) for d in O.enumerate_sigma(m)]
     assert len(diags) == 85
     pref = [(-1.0) ** m * (-1.0) ** d["loops"] for m, d in diags]
     lib = [T.Diagram(d["alpha"], eps=d["eps"], prefactor=p).upload(0) for (m, d), p in zip(diags, pref)]
-    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
-        list(ex.map(lambda D: D.jit_prepare(), lib))
-    T.set_jit("always")
+    if mode == "always":
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+            list(ex.map(lambda D: D.jit_prepare(), lib))
+    T.set_jit(mode)
     lat, beta, n, off = (1.0, -0.2, 0.1, np.pi / 2, np.pi / 3), 5.0, 128 + 22, 7
     rng = np.random.default_rng(29)
     for i, ((m, d), p, D) in enumerate(zip(diags, pref, lib)):
@@ -419,20 +422,25 @@ def test_specialised_kernels_on_every_enumerated_diagram():
         g = upstream(len(X), seed=i)
         seed = 100 + i
         out = D.forward_backward(lat, seed, off, n, X, beta, g, per_sample=True)
+        sv = D.saved_buffer(n)        # the two-call path: forward keeping rows, adjoint reading them
+        _, _, ps = D.forward(lat, seed, off, n, X, beta, per_sample=True, save=sv)
+        two = D.backward(lat, seed, off, n, X, beta, g, per_sample=True, saved=sv)
         E = rng.uniform(-3.0, 3.0, size=(40, np.asarray(d["eps"]).shape[1]))
         ev = D.eval_energies(torch.as_tensor(E, device="cuda"), X, beta)
         torch.cuda.synchronize()
-        assert D.jit_status()["last_used"], i
+        assert D.jit_status()["last_used"] == (mode == "always"), i
         tag = (m, d["code"])
         ref = S.eval_momenta(lat, seed, off, n, X, beta, per_sample=True, threads=8)
-        v = out["values"].cpu().numpy()
-        assert np.all(np.abs(v - ref["values"]) <= RTOL * ref["envelope"]), tag
+        for v in (out["values"].cpu().numpy(), ps.cpu().numpy()):
+            assert np.all(np.abs(v - ref["values"]) <= RTOL * ref["envelope"]), tag
         _, dref, denv = S.eval_momenta_deriv(lat, seed, off, n, X, beta, "omega", threads=8, envelope=True)
-        assert np.all(np.abs(out["dX"].cpu().numpy() - dref) <= RTOL * denv), tag
-        grads = out["grads"].cpu().numpy()
+        for r in (out, two):
+            assert np.all(np.abs(r["dX"].cpu().numpy() - dref) <= RTOL * denv), tag
         for k, which in enumerate(("mu", "kx", "ky")):
             _, der, env = S.eval_momenta_deriv(lat, seed, off, n, X, beta, which, threads=8, envelope=True)
             gref = np.real(np.conj(g)[:, None] * der).sum(axis=0)
-            assert np.all(np.abs(grads[:, k] - gref) <= RTOL * (np.abs(g)[:, None] * env).sum(axis=0)), (tag, which)
+            for r in (out, two):
+                grads = r["grads"].cpu().numpy()
+                assert np.all(np.abs(grads[:, k] - gref) <= RTOL * (np.abs(g)[:, None] * env).sum(axis=0)), (tag, which)
         eref, _, eenv = S.eval_energies(E, X, beta)
         assert np.all(np.abs(ev.cpu().numpy() - eref) <= RTOL * eenv), tag
