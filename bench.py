@@ -48,28 +48,22 @@ METRIC = "order-4 Sigma evals/s (samples x terms x frequencies, FP64), forward +
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel from one ncu
 # capture of this workload at 2^22 samples, per sample; every sample does the same work, so a
 # launch's traffic is this times its samples.  It holds only for the kernel it was taken on: the
-# kernel the step ran must be that one and the hash of the library sources must match, else the
-# bench reports traffic as null.
+# step must have run that kernel, and the kernel's identity -- the generated source of the
+# diagram's fused kind with the device arithmetic it includes, the identity under which the library
+# caches the compilation (whose options are fixed in the library) -- must hash to the captured
+# one, else the bench reports traffic as null.
 TRAFFIC = {"kernel": "tami_jit_fused (the diagram's specialised fused forward + adjoint)",
-           "bytes_per_sample": (2.100367e9 + 5.037143e9) / 4194304,
-           "sources_sha256": "7fa44f3ab5d93c75fea8744dba69d96ca998a3b858d6fee983d714e2556a59f0", "profile": "profiles/jit_kernels_order4_sigma.md"}
+           "bytes_per_sample": (2.050213e9 + 4.957428e9) / 4194304,
+           "kernel_sha256": "8cd8a503e30c6cbad8692492c582e79e26235bb4b0b1640d1f4fe99118ab162a", "profile": "profiles/jit_kernels_order4_sigma.md"}
 
 
-TRAFFIC_SOURCES = ("paper_2311_17189_gb300/csrc/tami_bwd.cu", "paper_2311_17189_gb300/csrc/tami_device.cuh",
-                   "paper_2311_17189_gb300/csrc/tami_internal.h", "paper_2311_17189_gb300/csrc/tami_host.cpp",
-                   "paper_2311_17189_gb300/csrc/tami_devmath.cuh", "paper_2311_17189_gb300/csrc/tami_jit.cpp")
-
-
-def sources_sha256():
-    """sha256 over the sources that fix the dominant kernel's code and its term table (the
-    adjoint kernel, the device helpers, the table layout, the flattener, the device arithmetic and
-    the generator of the specialised kernel), in this order."""
+def kernel_sha256(D):
+    """sha256 over the fused kernel source generated for diagram D and the device-arithmetic
+    header that source includes."""
     import hashlib
-    h = hashlib.sha256()
-    for rel in TRAFFIC_SOURCES:
-        h.update(rel.encode())
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+    h = hashlib.sha256(D.jit_source("fused").encode())
+    with open(os.path.join(ROOT, "paper_2311_17189_gb300", "csrc", "tami_devmath.cuh"), "rb") as f:
+        h.update(f.read())
     return h.hexdigest()
 
 
@@ -319,7 +313,7 @@ def run_tami(args):
     dom = (fused_kernel, fl_x, ms)
     achieved = dom[1] / (dom[2] * 1e-3) / 1e12
     traffic = None
-    if dom[0] == TRAFFIC["kernel"] and sources_sha256() == TRAFFIC["sources_sha256"]:
+    if dom[0] == TRAFFIC["kernel"] and kernel_sha256(D) == TRAFFIC["kernel_sha256"]:
         traffic = TRAFFIC["bytes_per_sample"] * n
     h2d = 2 * n_f * 16
     d2h = n_f * 32 + (n_f + 3) * 8

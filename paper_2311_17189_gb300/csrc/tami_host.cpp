@@ -8,6 +8,7 @@
 #include <map>
 #include <set>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "tami_internal.h"
@@ -728,46 +729,86 @@ int flatten(tami_diagram* d) {
   // there), the reciprocal (estimate + one third-order Newton step) 6, the table-driven exponential
   // 10 fma + 3 (e^t - 1: 2 more), cos 30 (reduction 9, series 21), sin 21.  Per frequency the count
   // is that of the imaginary axis; off it the kernels add one more add per complex denominator.
+  // Forward sums of the form sum_i c_i y_i (line momenta, energy combinations, pole-DAG nodes) are
+  // fma chains from 0, and chains that begin with the same steps share those partial sums: each
+  // distinct prefix is counted once, as a compiled kernel evaluates it once.  The reverse passes
+  // share nothing (every adjoint differs) and count every step.
   auto unit = [](double c) { return c == 1.0 || c == -1.0; };
+  auto step_cost = [&](bool first, double c) { return first ? (unit(c) ? 0.0 : 1.0) : (unit(c) ? 1.0 : 2.0); };
   auto lin = [&](const std::vector<double>& cs) {     // sum_i c_i y_i as an fma chain from 0
     double f = 0.0;
-    for (size_t i = 0; i < cs.size(); ++i) f += i == 0 ? (unit(cs[i]) ? 0.0 : 1.0) : (unit(cs[i]) ? 1.0 : 2.0);
+    for (size_t i = 0; i < cs.size(); ++i) f += step_cost(i == 0, cs[i]);
     return f;
   };
+  struct Prefixes {     // (prefix, variable, operand kind, operand) -> prefix id; cost of the new ones
+    std::map<std::tuple<int, int, int, long long>, int> id;
+    double flops = 0.0;
+    int step(int parent, int var, int kind, long long operand, double cost) {
+      const auto r = id.emplace(std::make_tuple(parent, var, kind, operand), (int)id.size() + 1);
+      if (r.second) flops += cost;
+      return r.first->second;
+    }
+  };
+  auto bits = [](double v) { long long b; std::memcpy(&b, &v, sizeof b); return b; };
   double fl = 0.0;
   fl += 2.0 * 2 * m;                                    // u -> k: one fma per component
-  for (int j : repl) {                                  // line momenta, both components
-    std::vector<double> cs;
-    for (int l = 0; l < nv; ++l) if (d->alpha[j * nv + l]) cs.push_back((double)d->alpha[j * nv + l]);
-    fl += 2.0 * lin(cs);
+  {
+    Prefixes mom;                                       // line momenta, both components
+    for (int j : repl) {
+      int p = 0;
+      bool first = true;
+      for (int l = 0; l < nv; ++l) {
+        const double a = (double)d->alpha[j * nv + l];
+        if (a == 0.0) continue;
+        p = mom.step(p, l, 0, bits(a), step_cost(first, a));
+        first = false;
+      }
+    }
+    fl += 2.0 * mom.flops;
   }
   fl += h.n_rep * (2.0 * 30.0 + 6.0);                   // cos of both components, energy
   const double energy_flops = fl;                       // what a saved-rows adjoint does not redo
   const double ext_grad_flops = h.n_rep_ext * 2.0 * (21.0 + 3.0);   // sin and G = (2t + 4t' cos) sin per component
-  double combo_fl = 0.0;                                // energy combinations
+  double combo_fl = 0.0;                                // energy combinations (every step: the reverse pass)
+  Prefixes cmb;                                         // (distinct prefixes: the forward)
   for (const Vec& c : combos) {
     std::vector<double> cs;
-    for (int j = 0; j < N; ++j) if (c[j]) cs.push_back((double)c[j]);
+    int p = 0;
+    for (int j = 0; j < N; ++j)
+      if (c[j]) {
+        const double cj = (double)c[j];
+        p = cmb.step(p, j, 0, bits(cj), step_cost(cs.empty(), cj));
+        cs.push_back(cj);
+      }
     combo_fl += lin(cs);
   }
-  fl += combo_fl;
+  fl += cmb.flops;
   for (const Seg& g : segs) {
     fl += 1.0 + 23.0 + (g.sigma < 0 ? 2.0 : 0.0);       // -beta|x|; e^t; e^t - 1
-    fl += 8.0;                                          // D, reciprocal, +-y / D
+    fl += g.sigma < 0 ? 7.0 : 8.0;                      // D (1 + y, or -(e^t - 1): free), reciprocal, +-y / D
     for (int v = g.v0; v < g.v1; ++v) {
       const int k = fvs[v].k;
       fl += k == 0 ? 0.0 : k == 1 ? 2.0 : k == 2 ? 5.0 : k == 3 ? 9.0 : 16.0 + 4.0 * k;
     }
   }
   fl += 6.0 * h.n_rden;                                 // real reciprocals
-  double dag_fwd = 0.0, dag_bwd = 0.0;                  // pole DAG: one fma per edge, forward and adjoint
-  for (const auto& op : opsb) {
-    const bool first = op.first & kOpbFirst, leaf = op.first & kOpbLeaf;
-    const bool one = leaf && unit(leafA[op.first >> kOpbRefShift]);
-    dag_fwd += first ? (one ? 0.0 : 1.0) : (one ? 1.0 : 2.0);
-    dag_bwd += leaf ? (one ? 1.0 : 2.0) : 4.0;          // Fbar += A bar (leaf) | Fbar += v bar, bar_c += F bar
+  double dag_bwd = 0.0;                                 // pole DAG: one fma per edge (adjoint: every edge)
+  {
+    Prefixes dag;                                       // forward: distinct prefixes of the nodes' chains
+    int max_node = 0;
+    for (const auto& op : opsb) max_node = std::max(max_node, op.first & kOpbDstMask);
+    std::vector<int> cur(max_node + 1, 0);              // a node's prefix so far; its value once complete
+    for (const auto& op : opsb) {
+      const int x = op.first, dst = x & kOpbDstMask, ref = x >> kOpbRefShift;
+      const bool first = x & kOpbFirst, leaf = x & kOpbLeaf;
+      const bool one = leaf && unit(leafA[ref]);
+      const int parent = first ? 0 : cur[dst];
+      cur[dst] = leaf ? dag.step(parent, op.second, 0, bits(leafA[ref]), step_cost(first, leafA[ref]))
+                      : dag.step(parent, op.second, 1, cur[ref], step_cost(first, 2.0));
+      dag_bwd += leaf ? (one ? 1.0 : 2.0) : 4.0;        // Fbar += A bar (leaf) | Fbar += v bar, bar_c += F bar
+    }
+    fl += dag.flops;
   }
-  fl += dag_fwd;
   for (auto& g : g1s) {
     for (auto& pr : g.rd) fl += pr.second;              // frequency-independent denominators
     fl += 1.0;

@@ -1,0 +1,112 @@
+"""The algorithmic flop model (tami_info.flops_per_sample and flops_per_sample_freq, which the
+bench's roofline divides by time) counted a second way: from the forward kernel source the library
+generates for the same table, statement by statement, under the model's conventions -- fma = 2,
+mul or add = 1, a multiplication by +-1 or an addition to an exact 0 free, the reciprocal 6, the
+exponential 23 (+2 for e^t - 1), a line energy 66 (two cosines of 30, then 6), the Fermi
+derivative polynomials as listed below -- and with every sum written as an fma chain from 0
+(line momenta, energy combinations, pole-DAG nodes) counted once per distinct prefix, since
+chains that begin with the same steps share those partial sums.  No GPU needed: the source is
+generated on the host."""
+import re
+
+import pytest
+
+import paper_2311_17189_gb300 as T
+from paper_2311_17189_gb300 import workloads as W
+
+UNIT = ("0x1p+0", "-0x1p+0")
+POLY = {0: 0, 1: 2, 2: 5, 3: 9}
+
+
+def step(first, coef):
+    unit = coef in UNIT
+    return (0 if unit else 1) if first else (1 if unit else 2)
+
+
+def chains(body, pattern):
+    """Flops of the fma chains `dst = fma(coef, var, dst)` (first step onto 0.0), each distinct
+    prefix once; pattern groups: dst, coef, var."""
+    seen, cur, fl = {}, {}, 0
+    for m in re.finditer(pattern, body):
+        dst, coef, var = m.group(1), m.group(2).strip(), m.group(3)
+        first = dst not in cur
+        pref = cur.get(dst, ()) + ((var, coef),)
+        if pref not in seen:
+            seen[pref] = True
+            fl += step(first, coef)
+        cur[dst] = pref
+    return fl
+
+
+def dag(body):
+    """Pole-DAG nodes: val<d> = fma(fv<y>, OPERAND, 0.0 | val<d>), an operand being a leaf
+    coefficient or another node's (complete) value."""
+    seen, cur, fl = set(), {}, 0
+    for m in re.finditer(r'val(\d+) = fma\(fv(\d+), ([^,]+), ([^)]+)\);', body):
+        d, y, opnd, add = m.group(1), m.group(2), m.group(3).strip(), m.group(4).strip()
+        first = add == "0.0"
+        node = re.fullmatch(r'val(\d+)', opnd)
+        operand = ("node", cur[node.group(1)]) if node else ("leaf", opnd)
+        pref = (() if first else cur[d]) + ((y, operand),)
+        if pref not in seen:
+            seen.add(pref)
+            fl += step(first, "x" if node else opnd)
+        cur[d] = pref
+    return fl
+
+
+def per_sample(src):
+    body = src[src.index("for (long long tile"):src.index("if (xr_zero) {")]
+    fl = 2 * body.count("to_momentum(")
+    fl += 2 * chains(body, r'ax(\d+) = fma\(([^,]+), kx(\d+), ax\d+\);')     # both components
+    fl += 66 * len(re.findall(r'\bline_energy\(', body))                  # (the saved-rows branch aside)
+    fl += chains(body, r'\bx(\d+) = fma\(([^,]+), E(\d+), x\d+\);')
+    fl += (1 + 25 + 6 + 1) * body.count("exp_neg<true>")                     # -beta|x|, e^t and e^t - 1, 1/D, y/D
+    fl += (1 + 23 + 7 + 1) * body.count("exp_neg<false>")                    # ... D = 1 + y
+    fl += sum(POLY.get(int(k), 16 + 4 * int(k)) for k in re.findall(r'fermi_poly\((\d+),', body))
+    fl += 6 * len(re.findall(r'rr\d+ = rcp\(', body))
+    fl += dag(body)
+    fl += len(re.findall(r'W1_\d+ \*= rr\d+;', body)) + len(re.findall(r'W2_\d+ \+= W1_\d+;', body))
+    return fl
+
+
+def per_frequency(src):
+    a = src.index("if (xr_zero) {")
+    loop = src[a:src.index("} else {", a)]
+    fl = 10 * len(re.findall(r'= rcp\(fma\(Dr\d+, Dr\d+,', loop))          # |D|^2, reciprocal, 1/D
+    fl += 6 * len(re.findall(r'const double vre\d+ = fma\(', loop))         # complex product per trie node
+    fl += 2 * len(re.findall(r'= fma\(W2_\d+,', loop))                      # W R accumulated
+    fl += 2 + 4                                                             # mean and variance sums
+    return fl
+
+
+def tables():
+    out = [("order2_bosonic", T.Diagram(W.ORDER2["alpha"], var_is_boson=W.ORDER2["var_is_boson"])),
+           ("quadruple_pole", T.Diagram([[1, 0], [1, 0], [1, 0], [1, 0], [1, 1]],
+                                        eps=[[1, 0, 0, 0, 0]] * 4 + [[0, 0, 0, 0, 1]], var_is_boson=[0, 1]))]
+    for m in (2, 3, 4, 5):
+        for i, d in enumerate(T.enumerate_sigma(m)):
+            out.append((f"order{m}_{i}", T.Diagram(d["alpha"], eps=d["eps"])))
+    return out
+
+
+def test_model_counts_what_the_generated_forward_computes():
+    checked = 0
+    for name, D in tables():
+        src = D.jit_source("forward")
+        info = D.info()
+        assert per_sample(src) == info["flops_per_sample"], name
+        assert per_frequency(src) == info["flops_per_sample_freq"], name
+        checked += 1
+    assert checked == 87
+
+
+def test_shared_prefixes_are_counted_once():
+    """The bench's order-4 table: its pole-DAG nodes share chain prefixes (the forward count is
+    below one fma per edge), and the counter above sees the same saving the model does."""
+    d = next(x for x in T.enumerate_sigma(4) if x["code"] == tuple(W.ORDER4["code"]))
+    src = T.Diagram(d["alpha"], eps=d["eps"]).jit_source("forward")
+    body = src[src.index("for (long long tile"):src.index("if (xr_zero) {")]
+    every = sum(step(m.group(4).strip() == "0.0", m.group(3).strip() if not m.group(3).strip().startswith("val") else "x")
+                for m in re.finditer(r'val(\d+) = fma\(fv(\d+), ([^,]+), ([^)]+)\);', body))
+    assert dag(body) < every
