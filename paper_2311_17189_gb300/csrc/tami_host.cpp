@@ -191,6 +191,32 @@ struct Blob {
 
 }  // namespace
 
+DagPrefixes dag_prefixes(const int* opsb, int n_ops, const double* leafA) {
+  DagPrefixes r;
+  int max_node = 0;
+  for (int i = 0; i < n_ops; ++i) max_node = std::max(max_node, opsb[2 * i] & kOpbDstMask);
+  r.node_value.assign(max_node + 1, -1);
+  r.op_prefix.resize(n_ops);
+  r.op_new.resize(n_ops);
+  std::map<std::tuple<int, int, int, long long>, int> id;   // a leaf keyed by its coefficient's bits
+  std::vector<int> cur(max_node + 1, -1);
+  for (int i = 0; i < n_ops; ++i) {
+    const int x = opsb[2 * i], y = opsb[2 * i + 1];
+    const int dst = x & kOpbDstMask, ref = x >> kOpbRefShift;
+    const bool leaf = x & kOpbLeaf;
+    const int parent = (x & kOpbFirst) ? -1 : cur[dst];
+    const DagPrefix q{parent, y, leaf ? 0 : 1, leaf ? ref : r.node_value[ref]};
+    long long key = q.operand;
+    if (leaf) std::memcpy(&key, &leafA[ref], sizeof key);
+    const auto ins = id.emplace(std::make_tuple(q.parent, q.fv, q.node, key), (int)r.p.size());
+    if (ins.second) r.p.push_back(q);
+    r.op_prefix[i] = ins.first->second;
+    r.op_new[i] = ins.second;
+    cur[dst] = r.node_value[dst] = ins.first->second;
+  }
+  return r;
+}
+
 int flatten(tami_diagram* d) {
   const int N = d->N, nv = d->nv, n_ext = d->n_ext, m = nv - n_ext;
   // ---- energy combinations (sign-canonical), Fermi values, denominators
@@ -792,22 +818,37 @@ int flatten(tami_diagram* d) {
     }
   }
   fl += 6.0 * h.n_rden;                                 // real reciprocals
-  double dag_bwd = 0.0;                                 // pole DAG: one fma per edge (adjoint: every edge)
+  double dag_bwd = 0.0;                                 // pole DAG, forward and adjoint
   {
-    Prefixes dag;                                       // forward: distinct prefixes of the nodes' chains
-    int max_node = 0;
-    for (const auto& op : opsb) max_node = std::max(max_node, op.first & kOpbDstMask);
-    std::vector<int> cur(max_node + 1, 0);              // a node's prefix so far; its value once complete
-    for (const auto& op : opsb) {
-      const int x = op.first, dst = x & kOpbDstMask, ref = x >> kOpbRefShift;
-      const bool first = x & kOpbFirst, leaf = x & kOpbLeaf;
-      const bool one = leaf && unit(leafA[ref]);
-      const int parent = first ? 0 : cur[dst];
-      cur[dst] = leaf ? dag.step(parent, op.second, 0, bits(leafA[ref]), step_cost(first, leafA[ref]))
-                      : dag.step(parent, op.second, 1, cur[ref], step_cost(first, 2.0));
-      dag_bwd += leaf ? (one ? 1.0 : 2.0) : 4.0;        // Fbar += A bar (leaf) | Fbar += v bar, bar_c += F bar
+    std::vector<int> flat(2 * opsb.size());
+    for (size_t i = 0; i < opsb.size(); ++i) { flat[2 * i] = opsb[i].first; flat[2 * i + 1] = opsb[i].second; }
+    const DagPrefixes dp = dag_prefixes(flat.data(), (int)opsb.size(), leafA.data());
+    for (const DagPrefix& q : dp.p) fl += step_cost(q.parent < 0, q.node ? 2.0 : leafA[q.operand]);
+    // adjoint, as the specialised kernels walk it: every group root seeded with its weight's adjoint
+    // (one mul per group, counted with the groups below; a second seed of the same root is an fma),
+    // then the prefixes in reverse creation order: F_y's adjoint += operand x adjoint, a node
+    // operand's value gets F_y x adjoint, and the adjoint passes to the parent prefix (a copy where
+    // that is the parent's first contribution, else an add)
+    std::vector<char> has(dp.p.size(), 0);
+    for (int g = 0; g < (int)g1_node.size() - 1 && g < h.n_g1; ++g) {
+      const int rp = dp.node_value[g1_node[g]];
+      if (has[rp]) dag_bwd += 1.0;
+      has[rp] = 1;
     }
-    fl += dag.flops;
+    for (int k = (int)dp.p.size() - 1; k >= 0; --k) {
+      if (!has[k]) continue;
+      const DagPrefix& q = dp.p[k];
+      if (q.node) {
+        dag_bwd += 2.0 + (has[q.operand] ? 2.0 : 1.0);
+        has[q.operand] = 1;
+      } else {
+        dag_bwd += unit(leafA[q.operand]) ? 1.0 : 2.0;
+      }
+      if (q.parent >= 0) {
+        if (has[q.parent]) dag_bwd += 1.0;
+        has[q.parent] = 1;
+      }
+    }
   }
   for (auto& g : g1s) {
     for (auto& pr : g.rd) fl += pr.second;              // frequency-independent denominators

@@ -176,6 +176,25 @@ bool jit_cache_write(const std::string& path, const std::string& ident, const st
 int jit_select_batch(tami_diagram* const* ds, int n_d, const int64_t* n, int n_f, int* use);
 void jit_mark_generic(tami_diagram* d);
 void jit_release(tami_diagram* d);
+// Distinct prefixes of the pole DAG's fma chains (tami_host.cpp).  A node's value is a chain
+// val = fma(F_y, operand, val) from 0 over its ops in program order; chains of different nodes that
+// begin with the same steps share those partial sums.  Every prefix is created by the first op
+// that reaches it, so prefixes come in program order and a node's value is complete before any
+// prefix references it.  Input: the adjoint encoding's ops (pairs {x, y}, kOpb* fields) and the
+// leaf coefficients (leaves with equal coefficients are the same operand).
+struct DagPrefix {
+  int parent;    // prefix this one extends, -1 for a chain's first step
+  int fv;        // Fermi value F_y
+  int node;      // 0: operand is leaf coefficient `operand`; 1: the value (prefix) `operand`
+  int operand;
+};
+struct DagPrefixes {
+  std::vector<DagPrefix> p;        // creation order
+  std::vector<int> op_prefix;      // op -> the prefix it lands on
+  std::vector<char> op_new;        // op creates that prefix
+  std::vector<int> node_value;     // node id -> prefix holding its value
+};
+DagPrefixes dag_prefixes(const int* opsb, int n_ops, const double* leafA);
 // Checks every index and range of a flattened table (tami_validate.cpp); false with the reason.
 bool validate_table(const TableHeader& h, const unsigned char* blob, size_t size, std::string* why);
 }

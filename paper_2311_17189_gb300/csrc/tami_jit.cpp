@@ -427,20 +427,20 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     }
   }
   for (int i = 0; i < h.n_rden; ++i) o("    const double rr%d = rcp(x%d);", i, rden[2 * i]);
-  // ---- pole DAG (one variable per node), group weights
+  // ---- pole DAG: one variable per distinct prefix of the nodes' fma chains (shared partial sums
+  // once), group weights
   for (int g = 0; g < h.n_g2; ++g) o("    double W2_%d = 0.0;", g);
-  std::vector<char> declared(h.n_nodes > 0 ? h.n_nodes : 1, 0);
+  const DagPrefixes dp = dag_prefixes(opsb, h.n_ops, leafA);
   for (int gi = 0; gi < h.n_g1; ++gi) {
     for (int op = g1[4 * gi]; op < g1[4 * gi + 1]; ++op) {
-      const int x = opsb[2 * op], y = opsb[2 * op + 1];
-      const int dst = x & kDstMask, ref = x >> kOpbRefShift;
-      const bool leaf = x & kOpbLeaf, first = x & kOpbFirst;
-      if (!declared[dst]) { o("    double val%d;", dst); declared[dst] = 1; }
-      const std::string opnd = leaf ? lit(leafA[ref]) : "val" + std::to_string(ref);
-      const std::string add = first ? "0.0" : "val" + std::to_string(dst);
-      o("    val%d = fma(fv%d, %s, %s);", dst, y, opnd.c_str(), add.c_str());
+      if (!dp.op_new[op]) continue;
+      const int k = dp.op_prefix[op];
+      const DagPrefix& q = dp.p[k];
+      const std::string opnd = q.node ? "pv" + std::to_string(q.operand) : lit(leafA[q.operand]);
+      const std::string add = q.parent < 0 ? "0.0" : "pv" + std::to_string(q.parent);
+      o("    const double pv%d = fma(fv%d, %s, %s);", k, q.fv, opnd.c_str(), add.c_str());
     }
-    o("    double W1_%d = val%d;", gi, g1_node[gi]);
+    o("    double W1_%d = pv%d;", gi, dp.node_value[g1_node[gi]]);
     for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q)
       for (int pw = g1rd[2 * q + 1]; pw > 0; --pw) o("    W1_%d *= rr%d;", gi, g1rd[2 * q]);
     o("    W2_%d += W1_%d;", g1_tgt[gi], gi);
@@ -465,7 +465,12 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     for (int u = 0; u < h.n_combo; ++u) o("    double xbar%d = 0.0;", u);
     for (int v = 0; v < h.n_fv; ++v) o("    double fvbar%d = 0.0;", v);
     for (int c = 0; c < h.n_cden; ++c) o("    xbar%d += %sbb%d;", cden[2 * c], cden[2 * c + 1] > 0 ? "" : "-", c);
+    // pole DAG backwards: the group roots seeded with their weights' adjoints, then the prefixes in
+    // reverse creation order (every contribution to a prefix's adjoint comes from a later prefix)
+    std::vector<char> has(dp.p.size(), 0);
     for (int gi = h.n_g1 - 1; gi >= 0; --gi) {
+      const int rp = dp.node_value[g1_node[gi]];
+      if (!has[rp]) o("    double bp%d;", rp);
       o("    {");
       o("      const double wb = Wb2_%d; double RR = 1.0;", g1_tgt[gi]);
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
@@ -473,28 +478,27 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
         for (int k = 0; k < pw; ++k) o("      RR *= rr%d;", i);
         o("      xbar%d -= wb * W1_%d * %s * rr%d;", rden[2 * i], gi, lit((double)pw).c_str(), i);
       }
-      const int nb = g1_node[gi], ne = g1_node[gi + 1];
-      for (int k = nb + 1; k < ne; ++k) o("      double bar%d = 0.0;", k);
-      o("      double bar%d = wb * RR;", nb);
-      for (int op = g1[4 * gi + 1] - 1; op >= g1[4 * gi];) {
-        const int x = opsb[2 * op], y = opsb[2 * op + 1];
-        const int dst = x & kDstMask;
-        if (x & kOpbLeaf) {
-          int run = (x >> kOpbRunShift) & 255;
-          if (run < 1) run = 1;
-          for (int i = 0; i < run; ++i) {
-            const int qx = opsb[2 * (op - i)], qy = opsb[2 * (op - i) + 1];
-            o("      fvbar%d = fma(%s, bar%d, fvbar%d);", qy, lit(leafA[qx >> kOpbRefShift]).c_str(), dst, qy);
-          }
-          op -= run;
-        } else {
-          const int ref = x >> kOpbRefShift;
-          o("      fvbar%d = fma(val%d, bar%d, fvbar%d); bar%d = fma(fv%d, bar%d, bar%d);", y, ref, dst, y, ref, y, dst,
-            ref);
-          --op;
-        }
-      }
+      if (has[rp]) o("      bp%d = fma(wb, RR, bp%d);", rp, rp);
+      else o("      bp%d = wb * RR;", rp);
+      has[rp] = 1;
       o("    }");
+    }
+    for (int k = (int)dp.p.size() - 1; k >= 0; --k) {
+      if (!has[k]) continue;
+      const DagPrefix& q = dp.p[k];
+      if (q.node) {
+        o("    fvbar%d = fma(pv%d, bp%d, fvbar%d);", q.fv, q.operand, k, q.fv);
+        if (has[q.operand]) o("    bp%d = fma(fv%d, bp%d, bp%d);", q.operand, q.fv, k, q.operand);
+        else o("    double bp%d = fv%d * bp%d;", q.operand, q.fv, k);
+        has[q.operand] = 1;
+      } else {
+        o("    fvbar%d = fma(%s, bp%d, fvbar%d);", q.fv, lit(leafA[q.operand]).c_str(), k, q.fv);
+      }
+      if (q.parent >= 0) {
+        if (has[q.parent]) o("    bp%d += bp%d;", q.parent, k);
+        else o("    double bp%d = bp%d;", q.parent, k);
+        has[q.parent] = 1;
+      }
     }
     for (int b = 0; b < h.n_fseg; ++b) {
       const int* sgm = fseg + 8 * b;
