@@ -423,6 +423,7 @@ extern "C" {
 
 int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* samples, const uint64_t* seeds, int n_f,
                     int chunk_tiles, tami_batch** out) {
+  return guarded([&]() -> int {
   if (!ds || !samples || !seeds || !out || n_d < 1 || n_f < 1 || n_f > kMaxFreqPerThread * kBlock) {
     set_error("bad argument (n_d >= 1, 1 <= n_f <= 2048, non-NULL arrays)");
     return TAMI_EINVAL;
@@ -517,6 +518,7 @@ int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* sampl
   }
   *out = b;
   return TAMI_OK;
+  });
 }
 
 int tami_batch_info(const tami_batch* b, int* n_items, int* grid, int* chunk_tiles) {

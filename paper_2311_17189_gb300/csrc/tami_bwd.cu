@@ -540,6 +540,7 @@ int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed,
                   double* dsigma_dX, double* grad_X_re, double* grad_params, double* per_sample_dX,
                   double* per_sample_grads, const double* saved, void* workspace, size_t workspace_bytes,
                   tami_stream_t stream) {
+  return guarded([&]() -> int {
   int rc = bwd_check(d, n_f);
   if (rc) return rc;
   if (!lat || !X || !gout || !workspace || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
@@ -584,6 +585,7 @@ int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed,
                                                               dsigma_dX, grad_X_re, grad_params);
   e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "bwd finalize launch");
+  });
 }
 
 int tami_forward_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
@@ -591,6 +593,7 @@ int tami_forward_backward(const tami_diagram* d, const tami_lattice* lat, uint64
                           double* var, double* per_sample, double* dsigma_dX, double* grad_X_re, double* grad_params,
                           double* per_sample_dX, double* per_sample_grads, void* workspace, size_t workspace_bytes,
                           tami_stream_t stream) {
+  return guarded([&]() -> int {
   int rc = bwd_check(d, n_f);
   if (rc) return rc;
   if (!lat || !X || !gout || !mean || !workspace || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
@@ -634,6 +637,7 @@ int tami_forward_backward(const tami_diagram* d, const tami_lattice* lat, uint64
                                                        dsigma_dX, grad_X_re, grad_params);
   e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "fused finalize launch");
+  });
 }
 
 }  // extern "C"

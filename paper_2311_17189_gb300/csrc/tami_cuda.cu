@@ -246,6 +246,7 @@ using namespace tami;
 extern "C" {
 
 int tami_upload(tami_diagram* d, int device, tami_stream_t stream) {
+  return guarded([&]() -> int {
   if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
   {
     std::string why;   // never put a table the kernels could read out of range on the device
@@ -274,10 +275,12 @@ int tami_upload(tami_diagram* d, int device, tami_stream_t stream) {
   d->d_blob = p;
   d->device = device;
   return TAMI_OK;
+  });
 }
 
 int tami_sample_energies(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
                          int64_t n, double* E, tami_stream_t stream) {
+  return guarded([&]() -> int {
   int rc = check_common(d, 1);
   if (!rc) rc = check_momentum(d);
   if (rc) return rc;
@@ -290,10 +293,12 @@ int tami_sample_energies(const tami_diagram* d, const tami_lattice* lat, uint64_
   sample_energies_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(P, E);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "sample_energies launch");
+  });
 }
 
 int tami_eval_energies(const tami_diagram* d, const double* E, int64_t n_e, const double* X, int n_f,
                        double beta, double* out, tami_stream_t stream) {
+  return guarded([&]() -> int {
   int rc = check_common(d, n_f);
   if (rc) return rc;
   if (n_e < 0) { set_error("bad argument"); return TAMI_EINVAL; }
@@ -316,6 +321,7 @@ int tami_eval_energies(const tami_diagram* d, const double* E, int64_t n_e, cons
   P.X = X;
   P.per_sample = out;
   return launch_fwd<true, false>(d, P, (cudaStream_t)stream, 0);
+  });
 }
 
 int tami_forward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, size_t* bytes) {
@@ -331,6 +337,7 @@ int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, 
                  int64_t n_samples, const double* X, int n_f, double beta, double* mean, double* var,
                  double* per_sample, double* saved, void* workspace, size_t workspace_bytes,
                  tami_stream_t stream) {
+  return guarded([&]() -> int {
   int rc = check_common(d, n_f);
   if (!rc) rc = check_momentum(d);
   if (rc) return rc;
@@ -369,6 +376,7 @@ int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, 
   finalize_kernel<<<n_f, kFinBlock, 0, st>>>(partial, used_grid, n_f, n_samples, status, mean, var);
   e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "finalize launch");
+  });
 }
 
 // Same evaluation as tami_forward, with its scratch taken from a fixed array inside the

@@ -154,6 +154,7 @@ extern "C" {
 
 int tami_label_graph(const int32_t* edges, int n_edges, int capacity_lines, int8_t* alpha, int8_t* eps,
                      int32_t* row_line, int* n_lines, int* n_vars, int* loops) {
+  return guarded([&]() -> int {
   GraphLabels G;
   int rc = label_graph_impl(edges, n_edges, G);
   if (rc) return rc;
@@ -165,13 +166,16 @@ int tami_label_graph(const int32_t* edges, int n_edges, int capacity_lines, int8
   if (eps) std::copy(G.eps.begin(), G.eps.end(), eps);
   if (row_line) std::copy(G.row_line.begin(), G.row_line.end(), row_line);
   return TAMI_OK;
+  });
 }
 
 int tami_construct_from_graph(const int32_t* edges, int n_edges, double prefactor, tami_diagram** out) {
+  return guarded([&]() -> int {
   GraphLabels G;
   int rc = label_graph_impl(edges, n_edges, G);
   if (rc) return rc;
   return tami_construct(G.N, G.nv, G.alpha.data(), G.eps.data(), nullptr, nullptr, prefactor, out);
+  });
 }
 
 }  // extern "C"

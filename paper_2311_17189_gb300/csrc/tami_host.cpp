@@ -1047,6 +1047,7 @@ const char* tami_last_error(void) { return g_last_error.c_str(); }
 int tami_construct_ext(int n_lines, int n_vars, int n_ext, const int8_t* alpha, const int8_t* eps,
                        const uint8_t* var_is_boson, const int32_t* order, double prefactor,
                        tami_diagram** out) {
+  return guarded([&]() -> int {
   if (!out || !alpha) { set_error("NULL argument"); return TAMI_EINVAL; }
   *out = nullptr;
   if (n_lines < 1 || n_lines > kMaxLines || n_vars < 2 || n_vars > kMaxVars) {
@@ -1092,12 +1093,15 @@ int tami_construct_ext(int n_lines, int n_vars, int n_ext, const int8_t* alpha, 
   if (rc != TAMI_OK) { delete d; return rc; }
   *out = d;
   return TAMI_OK;
+  });
 }
 
 int tami_construct(int n_lines, int n_vars, const int8_t* alpha, const int8_t* eps,
                    const uint8_t* var_is_boson, const int32_t* order, double prefactor,
                    tami_diagram** out) {
+  return guarded([&]() -> int {
   return tami_construct_ext(n_lines, n_vars, 1, alpha, eps, var_is_boson, order, prefactor, out);
+  });
 }
 
 int tami_diagram_info(const tami_diagram* d, tami_info* info) {
@@ -1108,6 +1112,7 @@ int tami_diagram_info(const tami_diagram* d, tami_info* info) {
 
 int tami_enumerate_sigma(int order, int capacity, int8_t* alpha, int8_t* eps, int32_t* code,
                          int32_t* loops, int* n_out) {
+  return guarded([&]() -> int {
   if (order < 2 || order > 6 || capacity < 0) { set_error("order must be in [2,6]"); return TAMI_EINVAL; }
   const int m = order, N = 2 * m - 1, nv = m + 1;
   std::set<std::vector<int>> codes;
@@ -1139,6 +1144,7 @@ int tami_enumerate_sigma(int order, int capacity, int8_t* alpha, int8_t* eps, in
   }
   if (n_out) *n_out = n;
   return TAMI_OK;
+  });
 }
 
 }  // extern "C"

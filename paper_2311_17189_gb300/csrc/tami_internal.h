@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstdint>
 #include <memory>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -176,6 +178,23 @@ bool jit_cache_write(const std::string& path, const std::string& ident, const st
 int jit_select_batch(tami_diagram* const* ds, int n_d, const int64_t* n, int n_f, int* use);
 void jit_mark_generic(tami_diagram* d);
 void jit_release(tami_diagram* d);
+// Runs an entry point's body and turns a C++ exception (host memory exhausted, a thread that could
+// not be started) into a status with a message: nothing throws across the C ABI.
+template <class F>
+int guarded(F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    set_error("out of host memory");
+    return TAMI_ENOMEM;
+  } catch (const std::exception& e) {
+    set_error(std::string("host error: ") + e.what());
+    return TAMI_EINVAL;
+  } catch (...) {
+    set_error("host error");
+    return TAMI_EINVAL;
+  }
+}
 // Distinct prefixes of the pole DAG's fma chains (tami_host.cpp).  A node's value is a chain
 // val = fma(F_y, operand, val) from 0 over its ops in program order; chains of different nodes that
 // begin with the same steps share those partial sums.  Every prefix is created by the first op

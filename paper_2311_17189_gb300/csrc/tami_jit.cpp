@@ -840,7 +840,13 @@ int jit_select_batch(tami_diagram* const* ds, int n_d, const int64_t* n, int n_f
   };
   const size_t n_thr = std::min<size_t>(std::max(1u, std::thread::hardware_concurrency()), todo.size());
   std::vector<std::thread> pool;
-  for (size_t t = 1; t < n_thr; ++t) pool.emplace_back(work);
+  for (size_t t = 1; t < n_thr; ++t) {
+    try {
+      pool.emplace_back(work);
+    } catch (...) {            // no more threads to be had: the ones running (and this one) finish the list
+      break;
+    }
+  }
   work();
   for (std::thread& t : pool) t.join();
   for (size_t i = 0; i < todo.size(); ++i) {
@@ -872,6 +878,7 @@ int tami_set_jit(int mode) {
 }
 
 int tami_jit_prepare(tami_diagram* d) {
+  return guarded([&]() -> int {
   if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
   if (!d->d_blob) { set_error("diagram not uploaded (call tami_upload)"); return TAMI_EINVAL; }
   int built = 0;
@@ -883,6 +890,7 @@ int tami_jit_prepare(tami_diagram* d) {
   }
   if (!built) { set_error("specialised kernel: no kind applies to this table"); return TAMI_EUNSUPPORTED; }
   return TAMI_OK;
+  });
 }
 
 int tami_jit_cached(const tami_diagram* d, int* from_cache) {
@@ -911,6 +919,7 @@ int tami_jit_status(const tami_diagram* d, int* ready, int* last_used, double* c
 }
 
 int tami_jit_source(const tami_diagram* d, int kind, char* buf, size_t cap, size_t* len) {
+  return guarded([&]() -> int {
   if (!d) { set_error("NULL diagram"); return TAMI_EINVAL; }
   if (kind < 0 || kind >= kKinds) {
     set_error("kind must be 0 (fused), 1 (forward), 2 (adjoint) or 3 (energy input)");
@@ -926,6 +935,7 @@ int tami_jit_source(const tami_diagram* d, int kind, char* buf, size_t cap, size
     buf[k] = '\0';
   }
   return TAMI_OK;
+  });
 }
 
 }  // extern "C"
