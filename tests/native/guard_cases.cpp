@@ -1,6 +1,6 @@
 // The C ABI's exception guard (tami_internal.h, guarded): a body that throws std::bad_alloc returns
 // TAMI_ENOMEM, any other exception TAMI_EINVAL, each with a message for tami_last_error; a body that
-// returns passes its status through.  Built and run by tests/test_abi_guard_cpu.py; needs no GPU.
+// returns passes its status through.  Built and run by tests/test_host_harness_cpu.py; needs no GPU.
 #include <cstdio>
 #include <cstring>
 #include <new>
