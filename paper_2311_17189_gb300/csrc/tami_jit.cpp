@@ -242,6 +242,10 @@ bool jit_supported(const TableHeader& h, int kind, std::string* why) {
 
 // CUDA C++ source of the specialised kernel of one kind for one table.
 std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind) {
+  // Large tables (over 256 pole-DAG ops) are written out into more code than the instruction
+  // caches hold; their Fermi segments call one out-of-line copy of the exponential, reciprocal and
+  // selects (smaller code; the largest order-5 table: 2.6 % faster, the order-4 table unchanged).
+  const bool seg_calls = h.n_ops > 256;
   const Table t{h, blob};
   const bool energy = kind == kKindEnergy;
   const bool fwd = kind != kKindBwd, adj = kind == kKindFused || kind == kKindBwd;
@@ -288,6 +292,19 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     std::string v;
     for (int i = 0; i < h.n_xk * h.n_ext; ++i) v += (i ? ", " : "") + lit(xvec[i]);
     o("__device__ const double kJitXvec[%d] = {%s};", h.n_xk * h.n_ext, v.c_str());
+  }
+  if (seg_calls) {
+    // one out-of-line copy of a Fermi segment's exponential, reciprocal and selects (smaller code)
+    for (int bose = 0; bose < 2; ++bose) {
+      o("static __device__ __noinline__ double2 tami_seg_%s(double xv, double beta) {", bose ? "bose" : "fermi");
+      o("  double em = 0.0;");
+      o("  const double y = exp_neg<%s>(-beta * fabs(xv), em); (void)em;", bose ? "true" : "false");
+      o("  const double rD = rcp(%s);", bose ? "-em" : "1.0 + y");
+      o("  const double t2 = (%s) * rD;", bose ? "-y" : "y");
+      o("  const bool neg = __double_as_longlong(xv) <= 0;");
+      o("  return make_double2(neg ? rD : t2, neg ? t2 : rD);");
+      o("}");
+    }
   }
   o("extern \"C\" __global__ void __launch_bounds__(%d, 8) %s(double lt, double ltp, double lmu, double lkx, double lky,",
     kJitBlock, kKernelName[kind]);
@@ -407,6 +424,11 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     const int* sgm = fseg + 8 * b;
     const bool bose = b < h.n_fseg_bose;
     o("    double sg%d_g, sg%d_h, sg%d_d1;", b, b, b);
+    if (seg_calls) {
+      o("    { const double2 gh = tami_seg_%s(x%d, beta);", bose ? "bose" : "fermi", sgm[0]);
+      o("      sg%d_g = gh.x; sg%d_h = gh.y; sg%d_d1 = %s; }", b, b, b,
+        adj ? ("-beta * (sg" + std::to_string(b) + "_g * sg" + std::to_string(b) + "_h)").c_str() : "0.0");
+    } else {
     o("    { const double xv = x%d; double em = 0.0;", sgm[0]);
     o("      const double y = exp_neg<%s>(-beta * fabs(xv), em); (void)em;", bose ? "true" : "false");
     o("      const double rD = rcp(%s);", bose ? "-em" : "1.0 + y");
@@ -414,6 +436,7 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     o("      const bool neg = __double_as_longlong(xv) <= 0;");
     o("      sg%d_g = neg ? rD : t2; sg%d_h = neg ? t2 : rD; sg%d_d1 = %s; }", b, b, b,
       adj ? ("-beta * (sg" + std::to_string(b) + "_g * sg" + std::to_string(b) + "_h)").c_str() : "0.0");
+    }
     for (int v = sgm[2]; v < sgm[3]; ++v) {
       o("    const double fv%d = sg%d_%c;", v, b, fvr[2 * v] > 0 ? 'g' : 'h');
       if (adj) o("    const double fvd%d = sg%d_d1;", v, b);

@@ -56,8 +56,10 @@ def per_sample(src):
     fl += 2 * chains(body, r'ax(\d+) = fma\(([^,]+), kx(\d+), ax\d+\);')     # both components
     fl += 66 * len(re.findall(r'\bline_energy\(', body))                  # (the saved-rows branch aside)
     fl += chains(body, r'\bx(\d+) = fma\(([^,]+), E(\d+), x\d+\);')
-    fl += (1 + 25 + 6 + 1) * body.count("exp_neg<true>")                     # -beta|x|, e^t and e^t - 1, 1/D, y/D
-    fl += (1 + 23 + 7 + 1) * body.count("exp_neg<false>")                    # ... D = 1 + y
+    bose = body.count("exp_neg<true>") + body.count("tami_seg_bose(")       # inline, or the out-of-line copy
+    fermi = body.count("exp_neg<false>") + body.count("tami_seg_fermi(")     # that large tables call
+    fl += (1 + 25 + 6 + 1) * bose                                           # -beta|x|, e^t and e^t - 1, 1/D, y/D
+    fl += (1 + 23 + 7 + 1) * fermi                                          # ... D = 1 + y
     fl += sum(POLY.get(int(k), 16 + 4 * int(k)) for k in re.findall(r'fermi_poly\((\d+),', body))
     fl += 6 * len(re.findall(r'rr\d+ = rcp\(', body))
     fl += dag(body)
