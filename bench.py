@@ -57,6 +57,51 @@ TRAFFIC = {"kernel": "tami_jit_fused (the diagram's specialised fused forward + 
            "kernel_sha256": "37cb13584745c7be589842b78220c8444a565c161da7e913b09d03b40d2ba439", "profile": "profiles/jit_kernels_order4_sigma.md"}
 
 
+def fp64_rate_measured(stream, target_s=0.25):
+    """FP64 fma rate of this GPU from libtami's probe (tami_selftest_fp64_rate: 64 independent
+    fma recurrences per thread per trip, 8 blocks of 256 threads per SM), timed with CUDA events
+    on `stream`: the best of three launches after one warm-up, in TFLOP/s."""
+    import ctypes
+    import torch
+    from paper_2311_17189_gb300 import _lib as L
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = 8 * sms
+    out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    fl = ctypes.c_double()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    trips = 256
+
+    def launch(tr):
+        L.check(L.lib().tami_selftest_fp64_rate(blocks, tr, ctypes.c_void_p(out.data_ptr()), ctypes.byref(fl), sp))
+
+    launch(trips)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launch(trips)
+    e1.record(stream)
+    e1.synchronize()
+    trips = max(1, int(trips * target_s / max(e0.elapsed_time(e1) * 1e-3, 1e-6)))
+    best = None
+    for _ in range(3):
+        e0.record(stream)
+        launch(trips)
+        e1.record(stream)
+        e1.synchronize()
+        rate = fl.value / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        best = rate if best is None else max(best, rate)
+    return {"tflops": best, "launch_s": e0.elapsed_time(e1) * 1e-3, "blocks": blocks,
+            "probe": "tami_selftest_fp64_rate: 64 independent fma recurrences per thread per trip, best of 3"}
+
+
+def roofline_peak(measured):
+    """The FP64 denominator: the measured fma rate where it is below the derived unit-count peak
+    (the pipe cannot be faster than it shows here), else the derived peak."""
+    if measured and measured["tflops"] < FP64_PEAK_TFLOPS:
+        return measured["tflops"], "measured on this GPU in this run (tami_selftest_fp64_rate, FP64 fma)"
+    return FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (nominal 1.25 TFLOP/s)"
+
+
 def kernel_sha256(D):
     """sha256 over the fused kernel source generated for diagram D and the device-arithmetic
     header that source includes."""
@@ -296,6 +341,7 @@ def run_tami(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
+    fp64 = fp64_rate_measured(stream)
     clk = clocks.stop()
     tf, tb, tp = float(np.mean(fwd_ms)), float(np.mean(bwd_ms)), float(np.mean(plain_ms))
     ms = float(np.mean(fused_ms))
@@ -312,6 +358,7 @@ def run_tami(args):
     fl_x = n * (info["bwd_flops_per_sample"] + n_f * info["fused_flops_per_sample_freq"])
     dom = (fused_kernel, fl_x, ms)
     achieved = dom[1] / (dom[2] * 1e-3) / 1e12
+    peak, peak_src = roofline_peak(fp64)
     traffic = None
     if dom[0] == TRAFFIC["kernel"] and kernel_sha256(D) == TRAFFIC["kernel_sha256"]:
         traffic = TRAFFIC["bytes_per_sample"] * n
@@ -334,12 +381,12 @@ def run_tami(args):
                        "terms": info["n_terms"], "beta": CFG["beta"], "t": CFG["t"], "tp": CFG["tp"],
                        "mu": CFG["mu"], "l2": "flushed before every step (256 MiB write)",
                        "parallelism": f"samples sharded over {world} GPU(s)"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
                          "traffic_unit": "bytes per launch (ncu capture, scaled per sample)",
-                         "kernel": dom[0], "flops_per_launch": dom[1],
-
-                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (nominal 1.25 TFLOP/s)"},
+                         "kernel": dom[0], "flops_per_launch": dom[1], "peak_source": peak_src,
+                         "peak_derived": FP64_PEAK_TFLOPS, "frac_of_derived": achieved / FP64_PEAK_TFLOPS,
+                         "peak_measured": fp64},
             "e2e": {"value": evals / (e2e * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": 2 * args.steps,
@@ -482,15 +529,18 @@ def run_workload(args):
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
+    fp64 = fp64_rate_measured(stream)
     clk = clocks.stop()
     t = float(np.mean(ms))
     tflops = flops / (t * 1e-3) / 1e12
+    peak, peak_src = roofline_peak(fp64)
     line = {"metric": f"{config['workload']} evals/s (samples x terms x frequencies, FP64)",
             "value": evals / (t * 1e-3), "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "dtype": "f64",
             "data": "synthetic", "config": config,
-            "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": tflops / FP64_PEAK_TFLOPS, "flops_per_step": flops},
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "flops_per_step": flops, "peak_source": peak_src,
+                         "frac_of_derived": tflops / FP64_PEAK_TFLOPS, "peak_measured": fp64},
             "gpu_launches": launches_per_step * args.steps, "clocks": clk}
     if bytes_step is not None:
         gbs = bytes_step / (t * 1e-3) / 1e9

@@ -99,6 +99,9 @@ typedef struct {
    * which energy input does not return) */
   double energy_in_flops_per_sample;
   double energy_in_flops_per_sample_freq;
+  /* pole DAG of the factorised FT (Sec. 2.1): edges (one fma each) and nodes; phase-2 factors:
+   * the complex-denominator powers over the frequency-dependent groups */
+  int n_dag_ops, n_dag_nodes, n_phase2_factors;
 } tami_info;
 
 const char* tami_last_error(void);
@@ -378,6 +381,20 @@ int tami_enumerate_sigma(int order, int capacity, int8_t* alpha, int8_t* eps, in
  * t, y, em, y_plain: device double [n]; y_plain may be NULL.  Used by the tests to check them
  * against CUDA's exp/expm1. */
 int tami_selftest_exp(const double* t, int64_t n, double* y, double* em, double* y_plain, tami_stream_t stream);
+
+/* Diagnostic: the kernels' cos and sin (Cody-Waite reduction by pi and Taylor series, the
+ * dispersion of Sec. 5.2's lattice samples; the paper leaves eps(k) to the user) applied
+ * elementwise: s = sin k, c = cos k.  k, s, c: device double [n].  c holds NaN where the
+ * cosine-only path that the energies use differs from the sin/cos path in any bit.  Used by the
+ * tests to bound them against the C library's sin and cos. */
+int tami_selftest_sincos(const double* k, int64_t n, double* s, double* c, tami_stream_t stream);
+
+/* Diagnostic: a probe of the FP64 fma issue rate (not a term of the paper; it measures the
+ * ceiling that the evaluation kernels are held against).  Launches `blocks` blocks of 256
+ * threads, each running 64 independent fma recurrences per trip for `trips` trips; `out`
+ * (device double [blocks * 256]) receives the recurrences' sums, and `flops` (host, may be
+ * NULL) the flops of the launch (2 per fma).  The caller times the launch on `stream`. */
+int tami_selftest_fp64_rate(int blocks, int64_t trips, double* out, double* flops, tami_stream_t stream);
 
 void tami_destroy(tami_diagram* d);
 

@@ -45,17 +45,17 @@ def lib():
         L.orc_term.argtypes = [ctypes.c_void_p, ctypes.c_int64, dp, i32p, i32p, i32p, i32p, i32p, i32p,
                                i32p, ctypes.c_int]
         L.orc_eval_energies.argtypes = [ctypes.c_void_p, dp, ctypes.c_int64, dp, dp, ctypes.c_int,
-                                        ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
+                                        ctypes.c_double, dp, dp, dp, dp, dp, ctypes.c_int]
         L.orc_sample_energies.argtypes = [ctypes.c_int, ctypes.c_int, i32p, dp, ctypes.c_uint64,
                                           ctypes.c_uint64, ctypes.c_int64, dp, dp]
         L.orc_eval_momenta.argtypes = [ctypes.c_void_p, i32p, dp, ctypes.c_uint64, ctypes.c_uint64,
                                        ctypes.c_int64, dp, dp, ctypes.c_int, ctypes.c_double, dp, dp, dp,
-                                       dp, dp, ctypes.c_int]
+                                       dp, dp, dp, ctypes.c_int]
         L.orc_eval_momenta_deriv.argtypes = [ctypes.c_void_p, i32p, dp, ctypes.c_uint64, ctypes.c_uint64,
                                              ctypes.c_int64, dp, dp, ctypes.c_int, ctypes.c_double,
-                                             ctypes.c_int, dp, dp, dp, dp, dp, ctypes.c_int]
+                                             ctypes.c_int, dp, dp, dp, dp, dp, dp, dp, ctypes.c_int]
         L.orc_eval_energies_deriv.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_int64, dp, dp, dp, dp,
-                                              ctypes.c_int, ctypes.c_double, dp, dp]
+                                              ctypes.c_int, ctypes.c_double, dp, dp, dp]
         L.orc_eval_momenta.restype = ctypes.c_int
         L.orc_eval_momenta_deriv.restype = ctypes.c_int
         L.orc_brute_force.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, dp, dp, dp,
@@ -167,23 +167,29 @@ class Solution:
                  for i in range(nG.value)]
         return A.value, F, G
 
-    def eval_energies(self, E, X, beta, threads=1):
+    def eval_energies(self, E, X, beta, threads=1, sens=False):
         """E: [n_e, N] base energies; X: [n_f] complex (n_ext = 1) or [n_f, n_ext] (one row of
         external frequencies per f).  Returns (values [n_f, n_e] complex, sum|term| [n_f, n_e],
-        envelope [n_f, n_e])."""
+        envelope [n_f, n_e]) and, with sens=True, the energy sensitivity
+        sum_t sum_j |d term_t / d E_j| [n_f, n_e] as a fourth item."""
         E = _f64(E)
         n_e = E.shape[0]
         xr, xi, nf = _rows(X, self.n_ext)
         vr = np.empty((nf, n_e)); vi = np.empty((nf, n_e))
         ab = np.empty((nf, n_e)); en = np.empty((nf, n_e))
+        sn = np.empty((nf, n_e)) if sens else None
         d = ctypes.c_double
         lib().orc_eval_energies(self._h, _ptr(E, d), n_e, _ptr(xr, d), _ptr(xi, d), nf, float(beta),
-                                _ptr(vr, d), _ptr(vi, d), _ptr(ab, d), _ptr(en, d), int(threads))
+                                _ptr(vr, d), _ptr(vi, d), _ptr(ab, d), _ptr(en, d), _ptr(sn, d), int(threads))
+        if sens:
+            return vr + 1j * vi, ab, en, sn
         return vr + 1j * vi, ab, en
 
     def eval_momenta(self, lattice, seed, offset, n, X, beta, per_sample=True, threads=1, alpha=None):
         """Momentum-sampled evaluation.  lattice = (t, t', mu, kx_ext, ky_ext).  Returns dict with
-        mean [n_f] complex, var [n_f, 2], and (if per_sample) values/envelope [n_f, n]."""
+        mean [n_f] complex, var [n_f, 2], and (if per_sample) values, envelope (the rounding
+        envelope) and sens (sum_t sum_j |d term_t / d E_j|, the first-order change per unit change
+        of every base energy) [n_f, n]."""
         a = self.alpha if alpha is None else _i32(alpha)
         lat = _f64(lattice)
         X = np.asarray(X, dtype=np.complex128).ravel()
@@ -191,23 +197,26 @@ class Solution:
         nf = X.size
         d = ctypes.c_double
         mean = np.empty(2 * nf); var = np.empty(2 * nf)
-        vr = vi = en = None
+        vr = vi = en = sn = None
         if per_sample:
-            vr = np.empty((nf, n)); vi = np.empty((nf, n)); en = np.empty((nf, n))
+            vr = np.empty((nf, n)); vi = np.empty((nf, n)); en = np.empty((nf, n)); sn = np.empty((nf, n))
         _chk(lib().orc_eval_momenta(self._h, _ptr(a, ctypes.c_int), _ptr(lat, d), int(seed), int(offset), int(n),
                                _ptr(xr, d), _ptr(xi, d), nf, float(beta), _ptr(vr, d), _ptr(vi, d),
-                               _ptr(en, d), _ptr(mean, d), _ptr(var, d), int(threads)))
+                               _ptr(en, d), _ptr(sn, d), _ptr(mean, d), _ptr(var, d), int(threads)))
         out = {"mean": mean[0::2] + 1j * mean[1::2], "var": var.reshape(nf, 2)}
         if per_sample:
             out["values"] = vr + 1j * vi
             out["envelope"] = en
+            out["sens"] = sn
         return out
 
     def eval_momenta_deriv(self, lattice, seed, offset, n, X, beta, which, threads=1, alpha=None,
-                           envelope=False):
+                           envelope=False, sens=False):
         """Per-sample dual-number derivative [n_f, n] along which in
-        {'omega', 'mu', 'kx', 'ky'}; returns (values, derivatives) or, with envelope=True,
-        (values, derivatives, derivative rounding envelope)."""
+        {'omega', 'mu', 'kx', 'ky'}; returns (values, derivatives), with envelope=True
+        (values, derivatives, derivative rounding envelope), and with sens=True also the energy
+        sensitivities of the derivative and of the value (sum_t sum_j |d (d term_t) / d E_j| and
+        sum_t sum_j |d term_t / d E_j|), in that order."""
         w = {"omega": 0, "mu": 1, "kx": 2, "ky": 3}[which]
         a = self.alpha if alpha is None else _i32(alpha)
         lat = _f64(lattice)
@@ -217,16 +226,23 @@ class Solution:
         d = ctypes.c_double
         vr = np.empty((nf, n)); vi = np.empty((nf, n)); dr = np.empty((nf, n)); di = np.empty((nf, n))
         de = np.empty((nf, n))
+        sv = ds = None
+        if sens:
+            sv = np.empty((nf, n)); ds = np.empty((nf, n))
         _chk(lib().orc_eval_momenta_deriv(self._h, _ptr(a, ctypes.c_int), _ptr(lat, d), int(seed), int(offset),
                                           int(n), _ptr(xr, d), _ptr(xi, d), nf, float(beta), w, _ptr(vr, d),
-                                          _ptr(vi, d), _ptr(dr, d), _ptr(di, d), _ptr(de, d), int(threads)))
+                                          _ptr(vi, d), _ptr(dr, d), _ptr(di, d), _ptr(de, d), _ptr(sv, d),
+                                          _ptr(ds, d), int(threads)))
+        if sens:
+            return vr + 1j * vi, dr + 1j * di, de, ds, sv
         if envelope:
             return vr + 1j * vi, dr + 1j * di, de
         return vr + 1j * vi, dr + 1j * di
 
-    def eval_energies_deriv(self, E, dE, X, dX, beta):
+    def eval_energies_deriv(self, E, dE, X, dX, beta, sens=False):
         """Dual-number derivative [n_f, n_e] along dE (base energies, [n_e, N]) and dX (the
-        external frequencies' direction, scalar or [n_ext], the same for every row of X)."""
+        external frequencies' direction, scalar or [n_ext], the same for every row of X); with
+        sens=True also the derivative's energy sensitivity sum_t sum_j |d (d term_t) / d E_j|."""
         E = _f64(E); dE = _f64(dE)
         n_e = E.shape[0]
         xr, xi, nf = _rows(X, self.n_ext)
@@ -234,8 +250,12 @@ class Solution:
         dxr, dxi = _f64(dXv.real), _f64(dXv.imag)
         d = ctypes.c_double
         dr = np.empty((nf, n_e)); di = np.empty((nf, n_e))
+        ds = np.empty((nf, n_e)) if sens else None
         lib().orc_eval_energies_deriv(self._h, _ptr(E, d), _ptr(dE, d), n_e, _ptr(xr, d), _ptr(xi, d),
-                                      _ptr(dxr, d), _ptr(dxi, d), nf, float(beta), _ptr(dr, d), _ptr(di, d))
+                                      _ptr(dxr, d), _ptr(dxi, d), nf, float(beta), _ptr(dr, d), _ptr(di, d),
+                                      _ptr(ds, d))
+        if sens:
+            return dr + 1j * di, ds
         return dr + 1j * di
 
 

@@ -38,11 +38,13 @@
 //       into powers before each residue step; the multipole residue is expanded with the
 //       Leibniz rule over the distinct factors, and no terms are merged afterwards.
 //
-// Bitwise-reproducible inputs.  Line momenta, energies and energy combinations are built
-// with explicit fma() in a fixed order, and cos/sin use Cody-Waite reduction by pi plus Taylor
-// series (W. J. Cody and W. Waite, Software Manual for the Elementary Functions, 1980), so
-// that an independent device implementation following the same published recipe sees the
-// very same energies.  Compile with -ffp-contract=off.
+// Inputs.  Philox momenta and the u -> k map are integer and one-rounding operations, line
+// momenta are sums of the labelled momenta in variable order, and the dispersion is the plain
+// definition with the C library's cos and sin (the paper leaves the dispersion eps(k) to the
+// user, Sec. 5.2).  An independent device implementation therefore sees the same momenta bit
+// for bit and energies that differ by the two sides' trig and rounding errors; the per-sample
+// sensitivity sum_t sum_j |d term_t / d E_j| returned with each evaluation bounds what such an
+// energy difference can change.  Compile with -ffp-contract=off.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -105,58 +107,17 @@ void sample_momentum(uint64_t seed, uint64_t s, int l, double* kx, double* ky) {
   *ky = momentum_from_unit(unit53(w[2], w[3]));
 }
 
-// cos and sin by Cody-Waite reduction by pi (two-part constant), k = n pi + r with
-// |r| <= pi/2 (n the nearest integer to k/pi), then Taylor series in r (terms to r^20 for cos
-// and r^21 for sin: truncation below 1.9e-17 and 1.3e-18 at |r| = pi/2) and the sign (-1)^n.
-void cw_sincos(double k, double* s_out, double* c_out) {
-  const double inv_pi = 0x1.45f306dc9c883p-2;
-  const double P1 = 0x1.921fb54442d18p+1, P2 = 0x1.1a62633145c07p-53;
-  // n = nearest integer to k/pi: k/pi + 1.5*2^52 rounded once leaves it in the low bits
-  double n = std::fma(k, inv_pi, 0x1.8p52) - 0x1.8p52;
-  // k - n P1 is exact (a multiple of 2^-52 below 2 in magnitude); n times the third part of pi
-  // (3.8e-33) stays below the rounding for the momenta a lattice sample produces (|k| < 22)
-  double r = std::fma(-n, P1, k);
-  r = std::fma(-n, P2, r);
-  double z = r * r;
-  // (-1)^i / (2i)!, i = 1..10      (cos r = 1 + z (c1 + z (c2 + ...)))
-  const double C[10] = {-0x1.0000000000000p-1, 0x1.5555555555555p-5, -0x1.6c16c16c16c17p-10,
-                        0x1.a01a01a01a01ap-16, -0x1.27e4fb7789f5cp-22, 0x1.1eed8eff8d898p-29,
-                        -0x1.93974a8c07c9dp-37, 0x1.ae7f3e733b81fp-45, -0x1.6827863b97d97p-53,
-                        0x1.e542ba4020225p-62};
-  // (-1)^i / (2i+1)!, i = 1..10    (sin r = r + r z (s1 + z (s2 + ...)))
-  const double S[10] = {-0x1.5555555555555p-3, 0x1.1111111111111p-7, -0x1.a01a01a01a01ap-13,
-                        0x1.71de3a556c734p-19, -0x1.ae64567f544e4p-26, 0x1.6124613a86d09p-33,
-                        -0x1.ae7f3e733b81fp-41, 0x1.952c77030ad4ap-49, -0x1.2f49b46814157p-57,
-                        0x1.71b8ef6dcf572p-66};
-  double pc = C[9];
-  for (int i = 8; i >= 0; --i) pc = std::fma(pc, z, C[i]);
-  double cr = std::fma(z, pc, 1.0);
-  double ps = S[9];
-  for (int i = 8; i >= 0; --i) ps = std::fma(ps, z, S[i]);
-  double sr = std::fma(r * z, ps, r);
-  bool odd = ((long)n & 1) != 0;
-  *c_out = odd ? -cr : cr;
-  *s_out = odd ? -sr : sr;
-}
-
 // Hubbard dispersion on the square lattice, eps(k) = -2t(cos kx + cos ky) - 4t' cos kx cos ky;
 // the line energy of the integrand is E = mu - eps(k)  (the paper's epsilon^j is minus the
 // dispersion, Eq. Green_Function; the chemical potential enters with it).
 double line_energy(double kx, double ky, double t, double tp, double mu) {
-  double sx, cx, sy, cy;
-  cw_sincos(kx, &sx, &cx);
-  cw_sincos(ky, &sy, &cy);
-  double sum = cx + cy;
-  double prod = cx * cy;
-  return std::fma(4.0 * tp, prod, std::fma(2.0 * t, sum, mu));
+  double cx = std::cos(kx), cy = std::cos(ky);
+  return mu + 2.0 * t * (cx + cy) + 4.0 * tp * cx * cy;
 }
 
 // d eps / d kx at (kx, ky): 2t sin kx + 4t' sin kx cos ky.
 double deps_dkx(double kx, double ky, double t, double tp) {
-  double sx, cx, sy, cy;
-  cw_sincos(kx, &sx, &cx);
-  cw_sincos(ky, &sy, &cy);
-  return 2.0 * t * sx + 4.0 * tp * sx * cy;
+  return 2.0 * t * std::sin(kx) + 4.0 * tp * std::sin(kx) * std::cos(ky);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -428,31 +389,58 @@ struct Neumaier {
   double value() const { return s + c; }
 };
 
-// One sample, one frequency: value, sum |term| and the rounding envelope
-// sum_t |A| prod env(F) prod |G|.
+// sum_j |c_j|: how far c.E can move when every base energy moves by at most one unit
+double l1(const std::vector<int>& c) {
+  double a = 0.0;
+  for (int v : c) a += std::fabs((double)v);
+  return a;
+}
+
+// One sample, one frequency: value, sum |term|, the rounding envelope
+// sum_t |A| prod env(F) prod |G|, and the sensitivity to the base energies
+// sum_t sum_j |d term_t / d E_j|, bounded factor by factor with the product rule on magnitudes:
+// a factor v(x) of argument x = c.E contributes |v'(x)| sum_j |c_j| times the other factors'
+// magnitudes (v' = g^(k+1) for a Fermi/Bose factor, -1/D^2 for a Green's function).
 void eval_one(const Solution& S, const double* E, const cplx* X, double beta, cplx* val, double* abs_sum,
-              double* envelope) {
+              double* envelope, double* sens = nullptr) {
   Neumaier re, im;
-  double as = 0.0, en = 0.0;
+  double as = 0.0, en = 0.0, se = 0.0;
   for (const Term& T : S.terms) {
     double ft = T.A, ft_env = std::fabs(T.A);
+    double mag = std::fabs(S.prefactor * T.A), sm = 0.0;   // running |product| and its sensitivity
     for (const FFac& f : T.F) {
       double e;
-      double v = fermi_deriv(f.sigma, f.k, beta, combo(f.c, E), &e);
+      double x = combo(f.c, E);
+      double v = fermi_deriv(f.sigma, f.k, beta, x, &e);
       ft *= v;
       ft_env *= e;
+      if (sens) {
+        double dv = std::fabs(fermi_deriv(f.sigma, f.k + 1, beta, x, nullptr)) * l1(f.c);
+        sm = sm * std::fabs(v) + mag * dv;
+        mag *= std::fabs(v);
+      }
     }
     cplx r = 1.0;
-    for (const GFac& g : T.G) r *= 1.0 / den_value(g, E, X, S.nv, S.n_ext);
+    for (const GFac& g : T.G) {
+      cplx rg = 1.0 / den_value(g, E, X, S.nv, S.n_ext);
+      r *= rg;
+      if (sens) {
+        double a = std::abs(rg);
+        sm = sm * a + mag * a * a * l1(g.e);
+        mag *= a;
+      }
+    }
     cplx term = S.prefactor * ft * r;
     re.add(term.real());
     im.add(term.imag());
     as += std::abs(term);
     en += std::fabs(S.prefactor) * ft_env * std::abs(r);
+    se += sm;
   }
   *val = cplx(re.value(), im.value());
   if (abs_sum) *abs_sum = as;
   if (envelope) *envelope = en;
+  if (sens) *sens = se;
 }
 
 // Forward-mode dual numbers: value and derivative along one seeded direction.
@@ -462,25 +450,42 @@ struct Dual {
 Dual dmul(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
 
 // X, dX: the n_ext external frequencies of the row and their directions.
+// der_env: the rounding envelope of the derivative (the product rule applied to magnitudes).
+// sens: sum_t sum_j |d term_t / d E_j| (as in eval_one); dsens: sum_t sum_j |d (d term_t) / d E_j|,
+// the sensitivity of the derivative to the base energies, from the second-order product rule on
+// magnitudes: with a = |v|, b = |v' dx|, s = |v'| sum|c|, q = |v'' dx| sum|c| per factor,
+// (V, D, S, Q) <- (V a, D a + V b, S a + V s, Q a + D s + S b + V q).
 void eval_one_dual(const Solution& S, const double* E, const double* dE, const cplx* X, const cplx* dX,
-                   double beta, cplx* val, cplx* der, double* der_env) {
+                   double beta, cplx* val, cplx* der, double* der_env, double* sens = nullptr,
+                   double* dsens = nullptr) {
   const int m = S.nv - S.n_ext;
   Neumaier vr, vi, dr, di;
-  double env = 0.0;
+  double env = 0.0, se = 0.0, dse = 0.0;
   for (const Term& T : S.terms) {
     Dual t{cplx(S.prefactor * T.A), 0.0};
     // rounding envelope of the derivative: the same product rule on magnitudes
     double ev = std::fabs(S.prefactor * T.A), ed = 0.0;
+    double MV = ev, MD = 0.0, MS = 0.0, MQ = 0.0;
     for (const FFac& f : T.F) {
       double x = combo(f.c, E);
       double dx = 0.0, adx = 0.0;
       for (size_t j = 0; j < f.c.size(); ++j) { dx += f.c[j] * dE[j]; adx += std::fabs(f.c[j] * dE[j]); }
       double e0, e1;
       double p = fermi_deriv(f.sigma, f.k, beta, x, &e0);
-      double dp = fermi_deriv(f.sigma, f.k + 1, beta, x, &e1) * dx;
+      double p1 = fermi_deriv(f.sigma, f.k + 1, beta, x, &e1);
+      double dp = p1 * dx;
       t = dmul(t, Dual{cplx(p), cplx(dp)});
       ed = ed * e0 + ev * e1 * adx;
       ev = ev * e0;
+      if (sens || dsens) {
+        double p2 = fermi_deriv(f.sigma, f.k + 2, beta, x, nullptr);
+        double a = std::fabs(p), b = std::fabs(p1) * adx, s1 = std::fabs(p1) * l1(f.c);
+        double q = std::fabs(p2) * adx * l1(f.c);
+        MQ = MQ * a + MD * s1 + MS * b + MV * q;
+        MS = MS * a + MV * s1;
+        MD = MD * a + MV * b;
+        MV = MV * a;
+      }
     }
     for (const GFac& g : T.G) {
       cplx D = den_value(g, E, X, S.nv, S.n_ext);
@@ -498,14 +503,26 @@ void eval_one_dual(const Solution& S, const double* E, const double* dE, const c
       double ar = std::abs(r);
       ed = ed * ar + ev * (adEe + adX) * ar * ar;
       ev = ev * ar;
+      if (sens || dsens) {
+        double a = ar, b = (adEe + adX) * ar * ar, s1 = ar * ar * l1(g.e);
+        double q = 2.0 * ar * ar * ar * (adEe + adX) * l1(g.e);
+        MQ = MQ * a + MD * s1 + MS * b + MV * q;
+        MS = MS * a + MV * s1;
+        MD = MD * a + MV * b;
+        MV = MV * a;
+      }
     }
     vr.add(t.v.real()); vi.add(t.v.imag());
     dr.add(t.d.real()); di.add(t.d.imag());
     env += ed;
+    se += MS;
+    dse += MQ;
   }
   *val = cplx(vr.value(), vi.value());
   *der = cplx(dr.value(), di.value());
   if (der_env) *der_env = env;
+  if (sens) *sens = se;
+  if (dsens) *dsens = dse;
 }
 
 // Lattice parameters (t, t', mu, k_ext) and the per-line momenta of one sample.
@@ -776,8 +793,9 @@ const char* orc_last_error() { return g_err.c_str(); }
 
 void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox(ctr, key, out); }
 
+// sin and cos as the oracle's dispersion uses them (the C library's).
 void orc_sincos(const double* k, int64_t n, double* s, double* c) {
-  for (int64_t i = 0; i < n; ++i) cw_sincos(k[i], &s[i], &c[i]);
+  for (int64_t i = 0; i < n; ++i) { s[i] = std::sin(k[i]); c[i] = std::cos(k[i]); }
 }
 
 double orc_fermi_deriv(int sigma, int k, double beta, double x) {
@@ -856,20 +874,21 @@ int orc_term(const void* sp, int64_t t, double* A, int* nF, int* fc, int* fs, in
 // frequencies per f); out [n_f][n_e] complex, abs_sum and envelope [n_f][n_e] (either may be NULL).
 int orc_eval_energies(const void* sp, const double* E, int64_t n_e, const double* X_re, const double* X_im,
                       int n_f, double beta, double* out_re, double* out_im, double* abs_sum,
-                      double* envelope, int n_threads) {
+                      double* envelope, double* sens, int n_threads) {
   const Solution& S = *(const Solution*)sp;
   auto work = [&](int64_t lo, int64_t hi) {
     std::vector<cplx> Xf(S.n_ext);
     for (int64_t i = lo; i < hi; ++i)
       for (int f = 0; f < n_f; ++f) {
         cplx v;
-        double a, e;
+        double a, e, sn;
         for (int q = 0; q < S.n_ext; ++q) Xf[q] = cplx(X_re[f * S.n_ext + q], X_im[f * S.n_ext + q]);
-        eval_one(S, E + i * S.N, Xf.data(), beta, &v, &a, &e);
+        eval_one(S, E + i * S.N, Xf.data(), beta, &v, &a, &e, sens ? &sn : nullptr);
         int64_t o = (int64_t)f * n_e + i;
         out_re[o] = v.real(); out_im[o] = v.imag();
         if (abs_sum) abs_sum[o] = a;
         if (envelope) envelope[o] = e;
+        if (sens) sens[o] = sn;
       }
   };
   if (n_threads <= 1) { work(0, n_e); return 0; }
@@ -896,13 +915,15 @@ int orc_sample_energies(int n_lines, int n_vars, const int* alpha, const double*
   return 0;
 }
 
-// Momentum mode: per-sample values [n_f][n] (optional), envelope [n_f][n] (optional), and the
-// Monte Carlo mean [n_f] (complex) and unbiased variances of Re and Im [n_f][2].
+// Momentum mode: per-sample values [n_f][n] (optional), rounding envelope and energy sensitivity
+// sum_t sum_j |d term_t / d E_j| [n_f][n] (each optional), and the Monte Carlo mean [n_f]
+// (complex) and unbiased variances of Re and Im [n_f][2] (Sec. 2.3, "summing the rows": the
+// mean over samples; the variance divides by n - 1).
 // alpha is the labelling used for the momenta (rows of the construction's alpha).
 int orc_eval_momenta(const void* sp, const int* alpha, const double* lat, uint64_t seed, uint64_t offset,
                      int64_t n, const double* X_re, const double* X_im, int n_f, double beta,
-                     double* per_re, double* per_im, double* envelope, double* mean, double* var,
-                     int n_threads) {
+                     double* per_re, double* per_im, double* envelope, double* sens, double* mean,
+                     double* var, int n_threads) {
   const Solution& S = *(const Solution*)sp;
   if (S.n_ext != 1) return fail("momentum sampling takes one external momentum (n_ext = 1)");
   Lattice L{lat[0], lat[1], lat[2], lat[3], lat[4]};
@@ -913,12 +934,13 @@ int orc_eval_momenta(const void* sp, const int* alpha, const double* lat, uint64
       sample_energies(S.N, S.nv, alpha, L, seed, offset + i, E.data(), Kx.data(), Ky.data());
       for (int f = 0; f < n_f; ++f) {
         cplx v;
-        double e;
+        double e, sn;
         const cplx Xf(X_re[f], X_im[f]);
-        eval_one(S, E.data(), &Xf, beta, &v, nullptr, &e);
+        eval_one(S, E.data(), &Xf, beta, &v, nullptr, &e, sens ? &sn : nullptr);
         size_t o = (size_t)f * n + i;
         vr[o] = v.real(); vi[o] = v.imag();
         if (envelope) envelope[o] = e;
+        if (sens) sens[o] = sn;
       }
     }
   };
@@ -945,14 +967,15 @@ int orc_eval_momenta(const void* sp, const int* alpha, const double* lat, uint64
 }
 
 // Dual-number derivative of the per-sample value along one direction (der_env, optional: the
-// rounding envelope of the derivative, the product rule applied to magnitudes):
+// rounding envelope of the derivative, the product rule applied to magnitudes; sens and dsens,
+// optional: the energy sensitivities of the value and of the derivative, as in eval_one_dual):
 // which = 0: d/d omega (X -> X + h, the same shift for every frequency; the derivative of
 // Sigma_f is with respect to its own omega_f), 1: d/d mu, 2: d/d kx_ext, 3: d/d ky_ext.
 // der [n_f][n] complex (re, im arrays).
 int orc_eval_momenta_deriv(const void* sp, const int* alpha, const double* lat, uint64_t seed,
                            uint64_t offset, int64_t n, const double* X_re, const double* X_im, int n_f,
                            double beta, int which, double* val_re, double* val_im, double* der_re,
-                           double* der_im, double* der_env, int n_threads) {
+                           double* der_im, double* der_env, double* sens, double* dsens, int n_threads) {
   const Solution& S = *(const Solution*)sp;
   if (S.n_ext != 1) return fail("momentum sampling takes one external momentum (n_ext = 1)");
   Lattice L{lat[0], lat[1], lat[2], lat[3], lat[4]};
@@ -971,13 +994,16 @@ int orc_eval_momenta_deriv(const void* sp, const int* alpha, const double* lat, 
       cplx dX = which == 0 ? cplx(1.0, 0.0) : cplx(0.0, 0.0);
       for (int f = 0; f < n_f; ++f) {
         cplx v, d;
-        double de;
+        double de, sn, dsn;
         const cplx Xf(X_re[f], X_im[f]);
-        eval_one_dual(S, E.data(), dE.data(), &Xf, &dX, beta, &v, &d, &de);
+        eval_one_dual(S, E.data(), dE.data(), &Xf, &dX, beta, &v, &d, &de, sens ? &sn : nullptr,
+                      dsens ? &dsn : nullptr);
         size_t o = (size_t)f * n + i;
         if (val_re) { val_re[o] = v.real(); val_im[o] = v.imag(); }
         der_re[o] = d.real(); der_im[o] = d.imag();
         if (der_env) der_env[o] = de;
+        if (sens) sens[o] = sn;
+        if (dsens) dsens[o] = dsn;
       }
     }
   };
@@ -992,10 +1018,10 @@ int orc_eval_momenta_deriv(const void* sp, const int* alpha, const double* lat, 
 
 // Dual-number derivative with energy input: dE [n_e][N] direction for the base energies,
 // X [n_f][n_ext] the frequency rows, dX [n_ext] the direction of the external frequencies
-// (the same for every row).
+// (the same for every row).  dsens [n_f][n_e] (optional): the derivative's energy sensitivity.
 int orc_eval_energies_deriv(const void* sp, const double* E, const double* dE, int64_t n_e,
                             const double* X_re, const double* X_im, const double* dX_re, const double* dX_im,
-                            int n_f, double beta, double* der_re, double* der_im) {
+                            int n_f, double beta, double* der_re, double* der_im, double* dsens) {
   const Solution& S = *(const Solution*)sp;
   std::vector<cplx> Xf(S.n_ext), dX(S.n_ext);
   for (int q = 0; q < S.n_ext; ++q) dX[q] = cplx(dX_re[q], dX_im[q]);
@@ -1003,9 +1029,12 @@ int orc_eval_energies_deriv(const void* sp, const double* E, const double* dE, i
     for (int f = 0; f < n_f; ++f) {
       cplx v, d;
       for (int q = 0; q < S.n_ext; ++q) Xf[q] = cplx(X_re[f * S.n_ext + q], X_im[f * S.n_ext + q]);
-      eval_one_dual(S, E + i * S.N, dE + i * S.N, Xf.data(), dX.data(), beta, &v, &d, nullptr);
+      double dsn;
+      eval_one_dual(S, E + i * S.N, dE + i * S.N, Xf.data(), dX.data(), beta, &v, &d, nullptr, nullptr,
+                    dsens ? &dsn : nullptr);
       der_re[(size_t)f * n_e + i] = d.real();
       der_im[(size_t)f * n_e + i] = d.imag();
+      if (dsens) dsens[(size_t)f * n_e + i] = dsn;
     }
   return 0;
 }

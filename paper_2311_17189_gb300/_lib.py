@@ -24,7 +24,7 @@ EXPORTS = [
     "tami_batch_plan", "tami_batch_info", "tami_batch_launch",
     "tami_batch_destroy", "tami_batch_debug_set_item", "tami_batch_specialised",
     "tami_enumerate_sigma",
-    "tami_selftest_exp", "tami_destroy",
+    "tami_selftest_exp", "tami_selftest_sincos", "tami_selftest_fp64_rate", "tami_destroy",
 ]
 
 
@@ -56,6 +56,7 @@ class Info(ctypes.Structure):
         ("n_ext", ctypes.c_int),
         ("energy_in_flops_per_sample", ctypes.c_double),
         ("energy_in_flops_per_sample_freq", ctypes.c_double),
+        ("n_dag_ops", ctypes.c_int), ("n_dag_nodes", ctypes.c_int), ("n_phase2_factors", ctypes.c_int),
     ]
 
 
@@ -109,6 +110,8 @@ def lib():
     L.tami_batch_destroy.restype = None
     L.tami_enumerate_sigma.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     L.tami_selftest_exp.argtypes = [dp, i64, dp, dp, dp, vp]
+    L.tami_selftest_sincos.argtypes = [dp, i64, dp, dp, vp]
+    L.tami_selftest_fp64_rate.argtypes = [ctypes.c_int, i64, dp, ctypes.POINTER(ctypes.c_double), vp]
     L.tami_destroy.argtypes = [vp]
     L.tami_destroy.restype = None
     _lib = L

@@ -265,11 +265,11 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
     for (int gi = 0; gi < H.n_g1; ++gi) {
       for (int o = g1[4 * gi]; o < g1[4 * gi + 1]; ++o) {
         const int2 op = opsb[o];
-        const int dst = op.x & kOpbDstMask, ref = op.x >> kOpbRefShift;
+        const int dst = op.x & kOpbDstMask, ref = op.y >> kOpbRefShift;
         const bool leaf = op.x & kOpbLeaf;
         const double a = leafA[leaf ? ref : 0], b = val[leaf ? 0 : ref];
         const double addend = (op.x & kOpbFirst) ? 0.0 : val[dst];
-        val[dst] = fma(fv[op.y], leaf ? a : b, addend);
+        val[dst] = fma(fv[op.y & kOpbFvMask], leaf ? a : b, addend);
       }
       double ft = val[g1_node[gi]];
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
@@ -331,13 +331,14 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
           const int run = max((op.x >> kOpbRunShift) & 255, 1);   // >= 1: the walk always advances
           for (int i = 0; i < run; ++i) {
             const int2 q = opsb[o - i];
-            fvbar[q.y] = fma(leafA[q.x >> kOpbRefShift], pb, fvbar[q.y]);
+            const int qf = q.y & kOpbFvMask;
+            fvbar[qf] = fma(leafA[q.y >> kOpbRefShift], pb, fvbar[qf]);
           }
           o -= run;
         } else {
-          const int ref = op.x >> kOpbRefShift;
-          fvbar[op.y] = fma(val[ref], pb, fvbar[op.y]);
-          bar[ref] = fma(fv[op.y], pb, bar[ref]);
+          const int ref = op.y >> kOpbRefShift, f = op.y & kOpbFvMask;
+          fvbar[f] = fma(val[ref], pb, fvbar[f]);
+          bar[ref] = fma(fv[f], pb, bar[ref]);
           --o;
         }
       }
@@ -500,7 +501,14 @@ int bwd_check(const tami_diagram* d, int n_f) {
   if (h.max_der > 4) { set_error("the adjoint needs derivative orders up to 4"); return TAMI_EUNSUPPORTED; }
   if (h.n_combo > kBwCombos || h.n_fv > kBwFv || h.n_rden > kBwRden || h.n_cden > kBwCden ||
       h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || h.n_nodes > kBwNodes || h.n_g2cd > kBwG2cd) {
-    set_error("term table exceeds the adjoint kernel's per-sample capacities");
+    set_error("term table exceeds the generic adjoint kernel's per-sample capacities: " + std::to_string(h.n_combo) +
+              " combinations (" + std::to_string(kBwCombos) + "), " + std::to_string(h.n_fv) + " Fermi values (" +
+              std::to_string(kBwFv) + "), " + std::to_string(h.n_rden) + " real denominators (" +
+              std::to_string(kBwRden) + "), " + std::to_string(h.n_cden) + " complex denominators (" +
+              std::to_string(kBwCden) + "), " + std::to_string(h.n_g1) + " groups (" + std::to_string(kBwG1) +
+              "), " + std::to_string(h.n_g2) + " frequency groups (" + std::to_string(kBwG2) + "), " +
+              std::to_string(h.n_nodes) + " DAG nodes (" + std::to_string(kBwNodes) + "), " +
+              std::to_string(h.n_g2cd) + " phase-2 factors (" + std::to_string(kBwG2cd) + ")");
     return TAMI_EUNSUPPORTED;
   }
   return TAMI_OK;

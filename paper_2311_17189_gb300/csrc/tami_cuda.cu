@@ -118,6 +118,38 @@ __global__ void exp_selftest_kernel(const double* t, long long n, double* y, dou
   if (y_plain) y_plain[i] = exp_neg<false>(t[i], e);
 }
 
+__global__ void sincos_selftest_kernel(const double* k, long long n, double* s, double* c) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double sv, cv;
+  cw_sincos(k[i], sv, cv);
+  s[i] = sv;
+  c[i] = cv;
+  // the cosine-only path of the dispersion gives the same bits
+  if (__double_as_longlong(cw_cos(k[i])) != __double_as_longlong(cv)) c[i] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// FP64 issue-rate probe: kChains independent fma recurrences per thread, a <- a m + c with
+// |m| < 1 (bounded, never subnormal), kUnroll steps per trip, the sums written out so that
+// nothing is dropped.  2 kChains kUnroll trips flops per thread.
+constexpr int kRateChains = 8, kRateUnroll = 8;
+__global__ void __launch_bounds__(256) fp64_rate_kernel(long long trips, double m, double c, double* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double a[kRateChains];
+#pragma unroll
+  for (int k = 0; k < kRateChains; ++k) a[k] = 1e-3 * (double)((t + k) & 1023);
+  for (long long it = 0; it < trips; ++it) {
+#pragma unroll
+    for (int u = 0; u < kRateUnroll; ++u)
+#pragma unroll
+      for (int k = 0; k < kRateChains; ++k) a[k] = fma(a[k], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kRateChains; ++k) s += a[k];
+  out[t] = s;
+}
+
 __global__ void sample_energies_kernel(const FwdParams P, double* E) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.n) return;
@@ -426,6 +458,24 @@ int tami_selftest_exp(const double* t, int64_t n, double* y, double* em, double*
   exp_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(t, n, y, em, y_plain);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "exp_selftest launch");
+}
+
+int tami_selftest_sincos(const double* k, int64_t n, double* s, double* c, tami_stream_t stream) {
+  if (!k || !s || !c || n < 0) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (n == 0) return TAMI_OK;
+  sincos_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(k, n, s, c);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "sincos_selftest launch");
+}
+
+int tami_selftest_fp64_rate(int blocks, int64_t trips, double* out, double* flops, tami_stream_t stream) {
+  if (blocks < 1 || trips < 1 || !out) { set_error("bad argument"); return TAMI_EINVAL; }
+  // m, c passed at run time so that the recurrence cannot be folded
+  fp64_rate_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>((long long)trips, 0.9999999, 1e-3, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "fp64_rate launch");
+  if (flops) *flops = 2.0 * kRateChains * kRateUnroll * (double)trips * 256.0 * (double)blocks;
+  return TAMI_OK;
 }
 
 void tami_destroy(tami_diagram* d) {

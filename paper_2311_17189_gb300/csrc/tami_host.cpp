@@ -202,10 +202,10 @@ DagPrefixes dag_prefixes(const int* opsb, int n_ops, const double* leafA) {
   std::vector<int> cur(max_node + 1, -1);
   for (int i = 0; i < n_ops; ++i) {
     const int x = opsb[2 * i], y = opsb[2 * i + 1];
-    const int dst = x & kOpbDstMask, ref = x >> kOpbRefShift;
+    const int dst = x & kOpbDstMask, ref = y >> kOpbRefShift;
     const bool leaf = x & kOpbLeaf;
     const int parent = (x & kOpbFirst) ? -1 : cur[dst];
-    const DagPrefix q{parent, y, leaf ? 0 : 1, leaf ? ref : r.node_value[ref]};
+    const DagPrefix q{parent, y & kOpbFvMask, leaf ? 0 : 1, leaf ? ref : r.node_value[ref]};
     long long key = q.operand;
     if (leaf) std::memcpy(&key, &leafA[ref], sizeof key);
     const auto ins = id.emplace(std::make_tuple(q.parent, q.fv, q.node, key), (int)r.p.size());
@@ -408,7 +408,12 @@ int flatten(tami_diagram* d) {
   }
   if ((int)pnodes.size() > kMaxProdNodes || (int)combos.size() > kMaxCombos || (int)fvs.size() > kMaxFermiValues ||
       (int)rdens.size() > kMaxRealDens || (int)cdens.size() > kMaxCplxDens) {
-    set_error("term table exceeds the kernels' per-sample capacities");
+    set_error("term table exceeds the kernels' per-sample capacities: " + std::to_string(combos.size()) +
+              " energy combinations (at most " + std::to_string(kMaxCombos) + "), " + std::to_string(fvs.size()) +
+              " Fermi values (" + std::to_string(kMaxFermiValues) + "), " + std::to_string(rdens.size()) +
+              " real denominators (" + std::to_string(kMaxRealDens) + "), " + std::to_string(cdens.size()) +
+              " complex denominators (" + std::to_string(kMaxCplxDens) + "), " + std::to_string(pnodes.size()) +
+              " product nodes (" + std::to_string(kMaxProdNodes) + ")");
     return TAMI_EUNSUPPORTED;
   }
   // ---- momentum labels: representative lines
@@ -568,13 +573,16 @@ int flatten(tami_diagram* d) {
       const int fref = o.leaf ? o.ref : slot[o.ref];
       const int bref = o.leaf ? o.ref : base + gid[o.ref];
       if (o.run > 255 || n_live > kMaxSlots || base + n_gid > (1 << kOpbDstBits) || fref >= (1 << 23) ||
-          bref >= (1 << (32 - kOpbRefShift - 1))) {
-        set_error("pole tree exceeds the program's encodable sizes");
+          bref > kOpbMaxRef || o.fv > kOpbFvMask) {
+        set_error("pole tree exceeds the program's encodable sizes: leaf run " + std::to_string(o.run) +
+                  " (at most 255), live slots " + std::to_string(n_live) + " (" + std::to_string(kMaxSlots) +
+                  "), nodes " + std::to_string(base + n_gid) + " (" + std::to_string(1 << kOpbDstBits) +
+                  "), adjoint operand " + std::to_string(bref) + " (" + std::to_string(kOpbMaxRef) + ")");
         return TAMI_EUNSUPPORTED;
       }
       ops.push_back({slot[o.dst] | (o.first ? kOpFirst : 0) | (o.leaf ? kOpLeaf : 0) | (fref << kOpRefShift), o.fv});
       opsb.push_back({(base + gid[o.dst]) | (o.first ? kOpbFirst : 0) | (o.leaf ? kOpbLeaf : 0) |
-                      (o.run << kOpbRunShift) | (bref << kOpbRefShift), o.fv});
+                      (o.run << kOpbRunShift), o.fv | (bref << kOpbRefShift)});
       if (!o.leaf) ++n_inner;
       if (!o.leaf && last_use[o.ref] == (int)p) free_slots.push_back(slot[o.ref]);
     }
@@ -860,6 +868,9 @@ int flatten(tami_diagram* d) {
   ff += 6.0 * h.n_pnode;                                // complex product per trie node
   for (auto& g : g2s) ff += g.empty() ? 0.0 : 4.0;      // W R accumulated (the R = 1 group is a copy)
   I.energy_in_flops_per_sample_freq = ff;              // energy input returns the values only
+  I.n_dag_ops = h.n_ops;
+  I.n_dag_nodes = h.n_nodes;
+  I.n_phase2_factors = h.n_g2cd;
   ff += 6.0;                                            // mean and variance sums
   I.flops_per_sample_freq = ff;
   // adjoint: the forward's phase 1 again plus the next derivative of every Fermi value, then per

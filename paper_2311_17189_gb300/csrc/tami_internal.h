@@ -24,7 +24,7 @@ constexpr int kMaxCombos = 128;
 constexpr int kMaxFermiValues = 256;
 constexpr int kMaxRealDens = 128;
 constexpr int kMaxCplxDens = 64;
-constexpr int kMaxProdNodes = 64;    // phase-2 product nodes beyond the reciprocals themselves
+constexpr int kMaxProdNodes = 128;   // phase-2 product nodes beyond the reciprocals themselves
 constexpr int kMaxDer = 5;
 constexpr int kMaxDepth = kMaxVars;   // pole-tree depth = number of summed variables
 
@@ -33,11 +33,11 @@ constexpr int kMaxDepth = kMaxVars;   // pole-tree depth = number of summed vari
 // Forward encoding (slots reused by liveness): x = dst | first << 6 | leaf << 7 | ref << 8.
 constexpr int kOpDstMask = 63, kOpFirst = 1 << 6, kOpLeaf = 1 << 7, kOpRefShift = 8;
 constexpr int kMaxSlots = 64;
-// Adjoint encoding (one slot per node, ids per diagram): x = dst | first << 11 | leaf << 12 |
-// run << 13 | ref << 21.  run (8 bits) is set on the last leaf edge of a node: its number of
-// leaf edges, which share the node's adjoint.
-constexpr int kOpbDstBits = 11, kOpbDstMask = (1 << kOpbDstBits) - 1, kOpbFirst = 1 << 11, kOpbLeaf = 1 << 12,
-              kOpbRunShift = 13, kOpbRefShift = 21;
+// Adjoint encoding (one slot per node, ids per diagram): x = dst | first << 20 | leaf << 21 |
+// run << 22, y = fv | ref << 12.  run (8 bits) is set on the last leaf edge of a node: its number
+// of leaf edges, which share the node's adjoint.
+constexpr int kOpbDstBits = 20, kOpbDstMask = (1 << kOpbDstBits) - 1, kOpbFirst = 1 << 20, kOpbLeaf = 1 << 21,
+              kOpbRunShift = 22, kOpbFvMask = (1 << 12) - 1, kOpbRefShift = 12, kOpbMaxRef = (1 << 19) - 1;
 
 void set_error(const std::string& msg);
 

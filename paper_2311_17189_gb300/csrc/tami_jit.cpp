@@ -43,7 +43,7 @@ namespace tami {
 namespace {
 
 constexpr int kJitBlock = 128;          // threads per block, as the generic kernel (one sample each)
-constexpr int kJitMaxOps = 2048;        // pole-DAG edges the generator writes out
+constexpr int kJitMaxOps = 1 << 15;     // pole-DAG edges the generator writes out
 constexpr int kJitMaxFreq = 256;        // frequencies (the generic adjoint's limit)
 
 // adjoint encoding of the pole-DAG ops (see tami_internal.h)

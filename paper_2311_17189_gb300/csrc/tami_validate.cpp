@@ -132,9 +132,9 @@ bool validate_table(const TableHeader& h, const unsigned char* blob, size_t size
       wf[dst] = 1;
       last_dst = dst;
       const int xb = opsb[2 * o], yb = opsb[2 * o + 1];
-      const int bd = xb & kOpbDstMask, br = xb >> kOpbRefShift, run = (xb >> kOpbRunShift) & 255;
+      const int bd = xb & kOpbDstMask, br = yb >> kOpbRefShift, run = (xb >> kOpbRunShift) & 255;
       const bool bl = xb & kOpbLeaf, bf = xb & kOpbFirst;
-      if (yb != y || bl != leaf || bf != first || !in(bd, g1_node[gi], g1_node[gi + 1])) { bad("adjoint op"); break; }
+      if ((yb & kOpbFvMask) != y || yb < 0 || xb < 0 || bl != leaf || bf != first || !in(bd, g1_node[gi], g1_node[gi + 1])) { bad("adjoint op"); break; }
       if (bl ? !in(br, 0, h.n_leaves) : !(in(br, g1_node[gi], g1_node[gi + 1]) && wb[br])) { bad("adjoint op reads an unset node"); break; }
       if (!bf && !wb[bd]) { bad("adjoint op accumulates into an unset node"); break; }
       if (run > 0) {   // the run's leaf edges are the run - 1 ops before this one, all into bd

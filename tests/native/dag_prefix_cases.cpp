@@ -11,15 +11,14 @@
 
 using namespace tami;
 
-static int op(int dst, bool first, bool leaf, int ref) {
-  return dst | (first ? kOpbFirst : 0) | (leaf ? kOpbLeaf : 0) | (ref << kOpbRefShift);
-}
+static int op(int dst, bool first, bool leaf) { return dst | (first ? kOpbFirst : 0) | (leaf ? kOpbLeaf : 0); }
+static int fv(int f, int ref) { return f | (ref << kOpbRefShift); }
 
 int main() {
   const double leafA[3] = {2.0, 3.0, 2.0};
-  const std::vector<int> ops = {op(0, true, true, 0), 1,  op(0, false, true, 1), 2,
-                                op(1, true, true, 2), 1,  op(1, false, true, 1), 2,  op(1, false, true, 0), 3,
-                                op(2, true, false, 0), 4, op(2, false, false, 1), 5};
+  const std::vector<int> ops = {op(0, true, true), fv(1, 0),  op(0, false, true), fv(2, 1),
+                                op(1, true, true), fv(1, 2),  op(1, false, true), fv(2, 1),  op(1, false, true), fv(3, 0),
+                                op(2, true, false), fv(4, 0), op(2, false, false), fv(5, 1)};
   const DagPrefixes dp = dag_prefixes(ops.data(), (int)ops.size() / 2, leafA);
   int fails = 0;
   auto expect = [&](bool ok, const char* what) { std::printf("%s %s\n", ok ? "ok" : "FAIL", what); fails += !ok; };

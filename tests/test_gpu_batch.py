@@ -17,6 +17,8 @@ import paper_2311_17189_gb300 as T
 from paper_2311_17189_gb300 import _lib as L
 from paper_2311_17189_gb300 import workloads as W
 
+import bounds as Bd
+
 pytestmark = pytest.mark.gpu
 
 RTOL = 1e-11
@@ -57,11 +59,11 @@ def check_against_oracle(mean, var, orc, counts, seeds, X):
     mean, var = mean.cpu().numpy(), var.cpu().numpy()
     for d, (S, n, sd) in enumerate(zip(orc, counts, seeds)):
         ref = S.eval_momenta(LAT, sd, 0, n, X, BETA, per_sample=True, threads=8)
-        scale = np.mean(ref["envelope"], axis=1) + np.mean(np.abs(ref["values"]), axis=1)
+        scale = Bd.mean_scale(ref, LAT)
         assert np.all(np.abs(mean[d] - ref["mean"]) <= RTOL * scale), d
         dev = ref["values"] - ref["mean"][:, None]
         for part, k in ((np.real, 0), (np.imag, 1)):
-            tol = 2.0 / max(n - 1, 1) * np.sum(np.abs(part(dev)) * RTOL * ref["envelope"], axis=1) \
+            tol = 2.0 / max(n - 1, 1) * np.sum(np.abs(part(dev)) * Bd.value_bound(ref, LAT), axis=1) \
                 + 1e-10 * ref["var"][:, k]
             assert np.all(np.abs(var[d][:, k] - ref["var"][:, k]) <= tol), d
 
@@ -301,5 +303,5 @@ def test_all_orders_workload_full_size(mode, jit):
             vals = ps[:, torch.as_tensor(idx, device=ps.device)].cpu().numpy()
             for k, i in enumerate(idx):
                 r = S.eval_momenta(lat, seeds[d], int(i), 1, X, c["beta"], per_sample=True)
-                assert np.all(np.abs(vals[:, k] - r["values"][:, 0]) <= RTOL * r["envelope"][:, 0]), (d, i)
+                assert np.all(np.abs(vals[:, k] - r["values"][:, 0]) <= Bd.value_bound(r, lat)[:, 0]), (d, i)
             del ps

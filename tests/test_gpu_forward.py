@@ -1,15 +1,15 @@
 """GPU parity of the forward path (CUDA kernels through the C ABI) against the CPU oracle.
 
-Tolerances.  Both sides build identical energies (same Philox stream, same Cody-Waite/Taylor
-cos, same fma order), identical energy combinations and identical denominators up to sign;
-they differ only in the rounding of exp/expm1, the reciprocals and the order of products and
-sums.  Each of those is a relative error of a few ulp on a factor, so the per-sample error is
-bounded by a small multiple of 2^-53 times the rounding envelope
-sum_t |A_t| prod env(FT factors) prod |G| that the oracle returns; the tests allow 1e-11 of it
-(the relative 1e-11 of the target, scaled to the terms that cancel).  Monte Carlo means are
-compared to 1e-11 of (mean envelope + mean |value|): the first bounds the mean of the
-per-sample errors, the second the summation (sample-to-sample cancellation makes |mean| itself
-the wrong scale).
+Tolerances.  With energy input both sides read the same energies; they differ only in the
+rounding of exp/expm1, the reciprocals and the order of products and sums.  Each of those is a
+relative error of a few ulp on a factor, so the per-sample error is bounded by a small multiple
+of 2^-53 times the rounding envelope sum_t |A_t| prod env(FT factors) prod |G| that the oracle
+returns; the tests allow 1e-11 of it (the relative 1e-11 of the target, scaled to the terms that
+cancel).  In momentum mode the two sides' energies also differ by their cos/sin (the oracle uses
+the C library's, the kernels their own), by at most dE; the bound adds twice dE times the
+oracle's energy sensitivity (tests/bounds.py).  Monte Carlo means are compared to 1e-11 of
+(mean bound / 1e-11 + mean |value|): the first bounds the mean of the per-sample errors, the
+second the summation (sample-to-sample cancellation makes |mean| itself the wrong scale).
 """
 import numpy as np
 import pytest
@@ -19,6 +19,8 @@ torch = pytest.importorskip("torch")
 import oracle as O
 import paper_2311_17189_gb300 as T
 from paper_2311_17189_gb300 import workloads as W
+
+import bounds as B
 
 pytestmark = pytest.mark.gpu
 
@@ -45,10 +47,12 @@ def diagram(order, index=None, code=None):
     return ds[index]
 
 
-def check_per_sample(gpu, ref, env, what):
+def check_per_sample(gpu, ref, env, what, pert=0.0):
+    """|gpu - ref| <= RTOL env + pert per sample (pert: the input part of the bound in momentum
+    mode); returns the share of samples that also meet a plain relative RTOL."""
     gpu = np.asarray(gpu)
     err = np.abs(gpu - ref)
-    bound = RTOL * env
+    bound = RTOL * env + pert
     bad = err > bound
     assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} samples off; worst err/env " \
                           f"{np.max(err / np.maximum(env, 1e-300)):.3e}"
@@ -57,15 +61,20 @@ def check_per_sample(gpu, ref, env, what):
 
 # ---------------------------------------------------------------------------- sampling
 @pytest.mark.parametrize("order,offset", [(2, 0), (4, 0), (4, (1 << 33) + 12345), (5, 77)])
-def test_sampled_energies_bitwise(order, offset):
-    """Philox momenta, line momenta and dispersion: bit-for-bit the oracle's energies."""
+def test_sampled_energies_within_trig_bound(order, offset):
+    """Philox momenta, line momenta and dispersion: every energy within dE of the oracle's (the
+    two sides' cos/sin and rounding, tests/bounds.py).  A wrong counter, key, label or sign moves
+    energies by O(1), far outside dE."""
     d = diagram(order, 0)
     D = T.Diagram(d["alpha"], eps=d["eps"]).upload(0)
     lat = (1.0, -0.3, -0.5, np.pi / 2, np.pi / 2)
     n = 5000
     Eg = D.sample_energies(lat, W.SEED, offset, n).cpu().numpy()
     Eo, _ = O.sample_energies(d["alpha"], lat, W.SEED, offset, n)
-    assert np.array_equal(Eg.view(np.uint64), Eo.view(np.uint64))
+    err = np.abs(Eg - Eo)
+    assert np.max(err) <= B.energy_error(lat), (np.max(err), B.energy_error(lat))
+    print(f"order {order}: max |E_gpu - E_oracle| = {np.max(err):.2e} (bound {B.energy_error(lat):.2e}), "
+          f"{np.mean(err == 0):.3f} equal")
 
 
 # ---------------------------------------------------------------------------- energy input
@@ -152,17 +161,17 @@ def run_both(D, S, lat, seed, offset, n, X, beta, threads=8):
     return mean.cpu().numpy(), var.cpu().numpy(), ps.cpu().numpy(), ref
 
 
-def check_mean(mean, var, ps_ref, ref):
-    # the mean of per-sample errors is bounded by the mean of the per-sample envelopes; the
+def check_mean(mean, var, ps_ref, ref, lat):
+    # the mean of per-sample errors is bounded by the mean of the per-sample bounds; the
     # summation itself adds rounding relative to mean |value|
-    scale = np.mean(ref["envelope"], axis=1) + np.mean(np.abs(ps_ref), axis=1)
+    scale = B.mean_scale(ref, lat)
     assert np.all(np.abs(mean - ref["mean"]) <= RTOL * scale)
     # var = sum (x - mean)^2 / (n-1): per-sample errors dx <= RTOL env move it by at most
     # 2/(n-1) sum |x - mean| dx, plus the rounding of the sums
     n = ps_ref.shape[1]
     dev = ps_ref - ref["mean"][:, None]
     for part, k in ((np.real, 0), (np.imag, 1)):
-        tol = 2.0 / max(n - 1, 1) * np.sum(np.abs(part(dev)) * RTOL * ref["envelope"], axis=1) \
+        tol = 2.0 / max(n - 1, 1) * np.sum(np.abs(part(dev)) * B.value_bound(ref, lat), axis=1) \
             + 1e-10 * ref["var"][:, k]
         assert np.all(np.abs(var[:, k] - ref["var"][:, k]) <= tol)
 
@@ -173,13 +182,14 @@ def test_order2_hubbard_full_workload():
     c = W.ORDER2
     D, S = lib_and_oracle(c["alpha"], boson=c["var_is_boson"])
     X = W.matsubara(c["beta"], c["n_freq"])
-    mean, var, ps, ref = run_both(D, S, W.lattice(c), c["seed"], 0, c["n_samples"], X, c["beta"])
-    frac = check_per_sample(ps, ref["values"], ref["envelope"], "order 2")
+    lat = W.lattice(c)
+    mean, var, ps, ref = run_both(D, S, lat, c["seed"], 0, c["n_samples"], X, c["beta"])
+    frac = check_per_sample(ps, ref["values"], ref["envelope"], "order 2", B.value_pert(ref, lat))
     # share of samples that also meet a plain relative 1e-11; the rest sit where the flat
     # term-by-term form cancels (e.g. f(-E1) - f(-E3) with both close to 1), for both sides
     print(f"order-2 full workload: {frac:.4f} of samples within plain relative 1e-11")
     assert frac > 0.9
-    check_mean(mean, var, ref["values"], ref)
+    check_mean(mean, var, ref["values"], ref, lat)
 
 
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 3 * 128 + 37, 4096 + 5])
@@ -190,9 +200,10 @@ def test_order4_small_sample_counts(n):
     d = diagram(4, code=c["code"])
     D, S = lib_and_oracle(d["alpha"], d["eps"])
     X = W.matsubara(c["beta"], c["n_freq"])
-    mean, var, ps, ref = run_both(D, S, W.lattice(c), c["seed"], 3, n, X, c["beta"])
-    check_per_sample(ps, ref["values"], ref["envelope"], f"order 4 n={n}")
-    check_mean(mean, var, ref["values"], ref)
+    lat = W.lattice(c)
+    mean, var, ps, ref = run_both(D, S, lat, c["seed"], 3, n, X, c["beta"])
+    check_per_sample(ps, ref["values"], ref["envelope"], f"order 4 n={n}", B.value_pert(ref, lat))
+    check_mean(mean, var, ref["values"], ref, lat)
 
 
 @pytest.mark.parametrize("n_f", [1, 3, 100, 127, 129, 300])
@@ -203,9 +214,10 @@ def test_frequency_counts(n_f):
     d = diagram(3, 1)
     D, S = lib_and_oracle(d["alpha"], d["eps"])
     X = W.real_axis(-4, 4, n_f, 0.05) if n_f > 3 else W.matsubara(10.0, n_f)
-    mean, var, ps, ref = run_both(D, S, (1.0, 0.0, 0.0, np.pi / 2, np.pi / 2), 5, 0, 700, X, 10.0)
-    check_per_sample(ps, ref["values"], ref["envelope"], f"n_f={n_f}")
-    check_mean(mean, var, ref["values"], ref)
+    lat = (1.0, 0.0, 0.0, np.pi / 2, np.pi / 2)
+    mean, var, ps, ref = run_both(D, S, lat, 5, 0, 700, X, 10.0)
+    check_per_sample(ps, ref["values"], ref["envelope"], f"n_f={n_f}", B.value_pert(ref, lat))
+    check_mean(mean, var, ref["values"], ref, lat)
 
 
 @pytest.mark.parametrize("order", [3, 5])
@@ -217,9 +229,10 @@ def test_all_diagrams_momentum_mode(order):
         pref = (-1.0) ** order * (-1.0) ** d["loops"]
         D, S = lib_and_oracle(d["alpha"], d["eps"], prefactor=pref)
         X = W.matsubara(5.0, 2)
-        mean, var, ps, ref = run_both(D, S, (1.0, -0.2, 0.1, np.pi / 2, np.pi / 3), 9, 1000, 400, X, 5.0)
-        check_per_sample(ps, ref["values"], ref["envelope"], f"order {order} {d['code']}")
-        check_mean(mean, var, ref["values"], ref)
+        lat = (1.0, -0.2, 0.1, np.pi / 2, np.pi / 3)
+        mean, var, ps, ref = run_both(D, S, lat, 9, 1000, 400, X, 5.0)
+        check_per_sample(ps, ref["values"], ref["envelope"], f"order {order} {d['code']}", B.value_pert(ref, lat))
+        check_mean(mean, var, ref["values"], ref, lat)
 
 
 def test_order4_full_size_sampled():
@@ -236,9 +249,12 @@ def test_order4_full_size_sampled():
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(n, 2000, replace=False))
     got = ps[:, torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    fr = []
     for k, i in enumerate(idx):
         r = S.eval_momenta(W.lattice(c), c["seed"], int(i), 1, X, c["beta"], per_sample=True)
-        check_per_sample(got[:, k:k + 1], r["values"], r["envelope"], f"sample {i}")
+        fr.append(check_per_sample(got[:, k:k + 1], r["values"], r["envelope"], f"sample {i}",
+                                   B.value_pert(r, W.lattice(c))))
+    print(f"order-4 bench workload: {np.mean(fr):.4f} of sampled values within plain relative 1e-11")
     ps_mean = ps.mean(dim=1).cpu().numpy()
     scale = ps.abs().mean(dim=1).cpu().numpy()
     assert np.all(np.abs(mean.cpu().numpy() - ps_mean) <= 1e-12 * scale)

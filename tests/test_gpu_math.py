@@ -1,6 +1,8 @@
-"""The kernels' own elementary functions against CUDA's: the table-driven exponential for t <= 0
-(e^t and e^t - 1, after Tang, ACM TOMS 1989) against torch.exp / torch.expm1 on the device
-(CUDA's exp/expm1), and against mpmath at a few points."""
+"""The kernels' own elementary functions: the table-driven exponential for t <= 0 (e^t and
+e^t - 1, after Tang, ACM TOMS 1989) against torch.exp / torch.expm1 on the device (CUDA's
+exp/expm1) and against mpmath at a few points; the Cody-Waite cos/sin of the dispersion against
+the C library's (the oracle's), which fixes TRIG_ERR of the momentum-mode parity bounds; and the
+FP64 fma-rate probe's flop count against its own outputs."""
 import ctypes
 
 import numpy as np
@@ -8,7 +10,10 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle as O
 from paper_2311_17189_gb300 import _lib as L
+
+import bounds as B
 
 pytestmark = pytest.mark.gpu
 
@@ -66,3 +71,48 @@ def test_exp_neg_against_high_precision():
         ey = mp.exp(mp.mpf(float(ti)))
         assert abs(y[i] - float(ey)) <= 3e-16 * float(ey)
         assert abs(em[i] - float(ey - 1)) <= 3e-16 * abs(float(ey - 1))
+
+
+def test_sincos_against_c_library():
+    """Kernel cos/sin within TRIG_ERR (3e-16, absolute) of the C library's, which the oracle's
+    dispersion uses (itself pinned to one ulp of 50-digit values), over the range of line momenta
+    a lattice sample produces (|k| up to about 7 pi) and beyond; exact at 0; the cosine-only path
+    of the energies gives the sin/cos path's bits.  The bound is absolute: one polynomial on
+    [-pi/2, pi/2], whose Horner sum 1 + z p(z) cancels near the zeros of cos (the dispersion
+    needs only absolute accuracy)."""
+    rng = np.random.default_rng(3)
+    k = np.concatenate([np.linspace(-7 * np.pi, 7 * np.pi, 400001), rng.uniform(-22.0, 22.0, 200000),
+                        np.array([0.0, -0.0, np.pi / 2, -np.pi / 2, np.pi, 1e-300, -1e-8])])
+    kt = torch.tensor(k, device="cuda")
+    st = torch.empty_like(kt)
+    ct = torch.empty_like(kt)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L.check(L.lib().tami_selftest_sincos(ctypes.c_void_p(kt.data_ptr()), kt.numel(), ctypes.c_void_p(st.data_ptr()),
+                                         ctypes.c_void_p(ct.data_ptr()), s))
+    torch.cuda.synchronize()
+    sg, cg = st.cpu().numpy(), ct.cpu().numpy()
+    assert np.all(np.isfinite(cg)), "cosine-only path differs from the sin/cos path"
+    so, co = O.sincos(k)
+    es, ec = np.max(np.abs(sg - so)), np.max(np.abs(cg - co))
+    print(f"kernel sin/cos against the C library: max abs diff {es:.2e} / {ec:.2e}")
+    assert es <= B.TRIG_ERR and ec <= B.TRIG_ERR
+    assert sg[-7] == 0.0 and cg[-7] == 1.0
+
+
+def test_fp64_rate_probe_does_its_work():
+    """The FP64 rate probe's recurrences a <- 0.9999999 a + 1e-3 from known starts: every thread's
+    sum equals the closed form to rounding, so the timed launch does all the flops it reports."""
+    blocks, trips = 4, 1000
+    out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    fl = ctypes.c_double()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L.check(L.lib().tami_selftest_fp64_rate(blocks, trips, ctypes.c_void_p(out.data_ptr()), ctypes.byref(fl), s))
+    torch.cuda.synchronize()
+    assert fl.value == 2.0 * 64 * trips * 256 * blocks
+    m, c, steps = 0.9999999, 1e-3, 8 * trips
+    t = np.arange(blocks * 256)
+    ref = np.zeros(blocks * 256)
+    for k in range(8):
+        a0 = 1e-3 * ((t + k) & 1023)
+        ref += a0 * m ** steps + c * (1 - m ** steps) / (1 - m)
+    assert np.allclose(out.cpu().numpy(), ref, rtol=1e-9, atol=0)

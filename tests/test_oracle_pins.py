@@ -46,18 +46,23 @@ def test_philox_known_answers():
 
 
 # ---------------------------------------------------------------------------- trig
-def test_sincos_accuracy_and_exact_points():
-    """Cody-Waite reduction by pi + Taylor series: cos/sin within 3e-16 absolute of libm over the
-    momentum range (one polynomial on [-pi/2, pi/2]: near the zeros of cos the Horner sum
-    1 + z p(z) cancels, so the bound is absolute, about 1.1 ulp of 1; the dispersion needs only
-    absolute accuracy)."""
-    k = np.concatenate([np.linspace(-7 * np.pi, 7 * np.pi, 400001), np.array([0.0, -0.0, np.pi / 2, np.pi])])
+def test_sincos_against_high_precision():
+    """The oracle's dispersion takes sin and cos from the C library (the paper leaves eps(k) to
+    the user, Sec. 5.2): within one ulp of 50-digit values over the range of line momenta, exact
+    at 0, and sin^2 + cos^2 = 1 as an identity that needs no reference."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    rng = np.random.default_rng(17)
+    k = np.concatenate([rng.uniform(-7 * np.pi, 7 * np.pi, 4000), np.linspace(-22, 22, 1001),
+                        np.array([np.pi / 2, np.pi, 1e-9, -3e-5])])
     s, c = O.sincos(k)
-    assert np.max(np.abs(s - np.sin(k))) <= 3e-16
-    assert np.max(np.abs(c - np.cos(k))) <= 3e-16
+    for i in range(k.size):
+        x = mpmath.mpf(float(k[i]))
+        for got, ref in ((s[i], mpmath.sin(x)), (c[i], mpmath.cos(x))):
+            r = float(ref)
+            assert abs(got - r) <= np.spacing(abs(r)) + 1e-300, (k[i], got, r)
     s0, c0 = O.sincos([0.0])
     assert s0[0] == 0.0 and c0[0] == 1.0
-    # Pythagoras as an independent identity
     assert np.max(np.abs(s * s + c * c - 1.0)) < 5e-16
 
 
@@ -403,3 +408,94 @@ def test_enumerated_order2_matches_second_order_sigma_mean():
     se = np.sqrt((r1["var"][0] + r2["var"][0]) / n)
     diff = r1["mean"][0] - r2["mean"][0]
     assert abs(diff.real) < 5 * se[0] and abs(diff.imag) < 5 * se[1]
+
+
+# ---------------------------------------------------------------------------- sensitivities
+SENS_CASES = [
+    ("paper_order2", [[1, 0, 0], [0, 1, 0], [-1, 1, 1]], None, None, 2.0),
+    ("bosonic_q_order2", [[1, 0, 1], [0, 1, 0], [1, 1, 0]], None, [1, 0, 0], 5.0),
+    ("quadruple_pole", [[1, 0], [1, 0], [1, 0], [1, 0], [1, 1]], [[1, 0, 0, 0, 0]] * 4 + [[0, 0, 0, 0, 1]],
+     [0, 1], 1.2),
+]
+
+
+@pytest.mark.parametrize("case", SENS_CASES, ids=[c[0] for c in SENS_CASES])
+def test_energy_sensitivity_bounds_gradient_and_finite_changes(case):
+    """The oracle's energy sensitivity sum_t sum_j |d term_t / d E_j| is an upper bound of what a
+    change of the base energies can do to the value, the quantity the GPU parity tests use to
+    allow for the two sides' different cos/sin: (i) it is at least sum_j |d Sigma / d E_j|, from
+    dual numbers along each coordinate; (ii) moving every energy by at most h (random signs)
+    changes the value by at most h sens (first order; h small); (iii) it is exact where the
+    solution is one factor of one energy: the double pole sum_nu 1/(i nu + E)^2 / beta leaves a
+    single term A f'(E), whose sensitivity is |A f''(E)| = |d Sigma / d E|."""
+    _, alpha, eps, boson, beta = case
+    S = O.Solution(alpha, eps=eps, var_is_boson=boson)
+    rng = np.random.default_rng(5)
+    N = np.asarray(alpha).shape[0]
+    E = rng.uniform(-2, 2, (6, N))
+    X = np.array([1j * np.pi / beta, 0.7 + 0.1j])
+    v, _, env, sens = S.eval_energies(E, X, beta, sens=True)
+    grad = np.zeros_like(sens)
+    for j in range(N):
+        dE = np.zeros_like(E)
+        dE[:, j] = 1.0
+        grad += np.abs(S.eval_energies_deriv(E, dE, X, 0.0, beta))
+    assert np.all(grad <= sens * (1 + 1e-12)), np.max(grad / sens)
+    h = 1e-7
+    for _ in range(4):
+        dE = h * rng.choice([-1.0, 1.0], size=E.shape)
+        vp, _, _ = S.eval_energies(E + dE, X, beta)
+        assert np.all(np.abs(vp - v) <= h * sens * (1 + 1e-4) + 1e-13 * env)
+    # double pole: one term A f'(E) of one energy, where the bound is attained
+    P = O.Solution([[1, 0], [1, 0]], eps=[[1, 0], [1, 0]])
+    assert P.info()["terms"] == 1
+    E1 = np.array([[0.3, 0.0], [-1.7, 0.0], [0.05, 0.0]])
+    X1 = np.array([0.0j])
+    _, _, _, s1 = P.eval_energies(E1, X1, beta, sens=True)
+    dE = np.zeros_like(E1)
+    dE[:, 0] = 1.0
+    g1 = np.abs(P.eval_energies_deriv(E1, dE, X1, 0.0, beta))
+    assert np.allclose(s1, g1, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("case", SENS_CASES, ids=[c[0] for c in SENS_CASES])
+def test_derivative_sensitivity_bounds_second_differences(case):
+    """The derivative's energy sensitivity sum_t sum_j |d (d term_t) / d E_j| bounds
+    sum_j |d D / d E_j| for D = d Sigma / d mu (every base energy moves with mu) and for
+    D = d Sigma / d omega, with d D / d E_j from central differences of the dual derivative."""
+    _, alpha, eps, boson, beta = case
+    S = O.Solution(alpha, eps=eps, var_is_boson=boson)
+    rng = np.random.default_rng(9)
+    N = np.asarray(alpha).shape[0]
+    E = rng.uniform(-2, 2, (5, N))
+    X = np.array([1j * np.pi / beta, 0.4 + 0.2j])
+    h = 1e-6
+    for dE_dir, dX in ((np.ones_like(E), 0.0), (np.zeros_like(E), 1.0)):
+        _, dsens = S.eval_energies_deriv(E, dE_dir, X, dX, beta, sens=True)
+        tot = np.zeros_like(dsens)
+        for j in range(N):
+            e = np.zeros_like(E)
+            e[:, j] = h
+            tot += np.abs(S.eval_energies_deriv(E + e, dE_dir, X, dX, beta)
+                          - S.eval_energies_deriv(E - e, dE_dir, X, dX, beta)) / (2 * h)
+        assert np.all(tot <= dsens * (1 + 1e-5) + 1e-9), np.max(tot / dsens)
+
+
+def test_monte_carlo_mean_and_variance_are_numpy_moments():
+    """The oracle's Monte Carlo reduction (Sec. 2.3, "summing the rows"; variance unbiased, n - 1)
+    against numpy's mean and var(ddof=1) of the oracle's own per-sample values, for Re and Im,
+    at a sample count where dividing by n instead of n - 1 would differ by 2 %."""
+    d = O.enumerate_sigma(3)[1]
+    S = O.Solution(d["alpha"], eps=d["eps"])
+    lat = (1.0, -0.3, -0.5, np.pi / 2, np.pi / 2)
+    X = 1j * np.pi / 8.0 * np.array([1, 3, 5])
+    for n in (2, 50, 3001):
+        r = S.eval_momenta(lat, 42, 7, n, X, 8.0, per_sample=True)
+        v = r["values"]
+        scale = np.mean(np.abs(v), axis=1)
+        assert np.all(np.abs(r["mean"] - v.mean(axis=1)) <= 1e-14 * scale)
+        for part, k in ((np.real, 0), (np.imag, 1)):
+            ref = np.var(part(v), axis=1, ddof=1)
+            assert np.all(np.abs(r["var"][:, k] - ref) <= 1e-12 * ref), (n, k)
+    r1 = S.eval_momenta(lat, 42, 7, 1, X, 8.0, per_sample=True)
+    assert np.array_equal(r1["mean"], r1["values"][:, 0]) and np.all(r1["var"] == 0.0)
