@@ -403,7 +403,7 @@ def run_tami(args):
 
 def run_workload(args):
     """The other configurations of the method, timed on one GPU (parity for each is in tests/):
-    order5 (forward + adjoint at four temperatures), order3_real (forward + adjoint on the real
+    order5 and order6 (forward + adjoint at four temperatures), order3_real (forward + adjoint on the real
     axis), all_orders (every order-2..5 diagram in one graph launch, forward),
     energy_x1 (the paper's energy-input example) and two_freq_x1 (two external frequencies per
     frequency row, energy input).  Prints one JSON line; not the headline metric."""
@@ -416,9 +416,9 @@ def run_workload(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     wl = args.workload
     launches_per_step = 0
-    if wl in ("order5", "order3_real"):
-        c = W.ORDER5 if wl == "order5" else W.ORDER3_REAL
-        if wl == "order5":
+    if wl in ("order5", "order6", "order3_real"):
+        c = {"order5": W.ORDER5, "order6": W.ORDER6, "order3_real": W.ORDER3_REAL}[wl]
+        if wl in ("order5", "order6"):
             d = next(x for x in T.enumerate_sigma(c["order"]) if x["code"] == tuple(c["code"]))
             betas = c["betas"]
             Xs = [W.matsubara(b, c["n_freq"]) for b in betas]
@@ -560,7 +560,8 @@ def main():
     p.add_argument("--samples", type=int, default=CFG["n_samples"], help="samples per GPU (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--rows", type=int, default=0, help="energy rows of energy_x1 / two_freq_x1 (profiling runs)")
-    p.add_argument("--workload", default="order4", choices=["order4", "order5", "order3_real", "all_orders", "energy_x1", "two_freq_x1"],
+    p.add_argument("--workload", default="order4",
+                   choices=["order4", "order5", "order6", "order3_real", "all_orders", "energy_x1", "two_freq_x1"],
                    help="order4 is the headline metric; the others time the remaining configurations on one GPU")
     p.add_argument("--jit", default="auto", choices=["auto", "never", "always"],
                    help="specialised kernels: auto (large calls), never (generic kernels) or always (profiling runs)")

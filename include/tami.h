@@ -267,6 +267,10 @@ int tami_forward_backward(const tami_diagram* d, const tami_lattice* lat, uint64
  *   - Every call shares the one array and it keeps the last call's contents; the call clears the
  *     status word itself.  Calls whose work overlaps on the GPU (other streams, other host
  *     threads) race on the array: serialise them.
+ *   - The looked-up address is kept for the life of the process: a device reset
+ *     (cudaDeviceReset) while libtami is loaded is not supported with this call.
+ *   - It always runs the generic kernel (never a specialised one, whose grid it does not size
+ *     for); a table the generic kernel cannot stage returns TAMI_EUNSUPPORTED.
  * Arguments, layouts and errors are otherwise those of tami_forward. */
 int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
                          int64_t n_samples, const double* X, int n_f, double beta, double* mean,
@@ -374,6 +378,28 @@ int tami_batch_debug_set_item(tami_batch* b, int item, int d, int64_t tile0, int
  * Any output pointer may be NULL. */
 int tami_enumerate_sigma(int order, int capacity, int8_t* alpha, int8_t* eps, int32_t* code,
                          int32_t* loops, int* n_out);
+
+/* Staging of the term table by the generic forward kernels (tami_eval_energies, tami_forward,
+ * tami_forward_noalloc and the persistent kernel of a batch plan; the paper's tables are data
+ * read by every evaluation, Sec. 2.3).  Each block copies the table into shared memory with bulk
+ * (TMA) copies.  TAMI_STAGING_AUTO (the default) keeps the whole forward pole-DAG program of the
+ * factorised FT (Sec. 2.1) resident when it fits beside the tiles and otherwise streams it
+ * through two shared-memory buffers of chunk_ops ops each, a bulk copy per chunk, double
+ * buffered; TAMI_STAGING_STREAMED always streams (same results bit for bit).  chunk_ops: even,
+ * in [16, 4096]; 0 keeps the current value (default 512).  Process-wide; a batch plan takes the
+ * setting at planning time.  TAMI_EINVAL for other values. */
+#define TAMI_STAGING_AUTO 0
+#define TAMI_STAGING_STREAMED 1
+int tami_set_table_staging(int mode, int chunk_ops);
+
+/* Test hook (not a term of the paper): bound the first stage of every mbarrier wait of the generic
+ * kernels' table staging to `first_stage_spins` polls (0 .. 2^24; -1 restores the default 2^24).
+ * A wait that runs out sets the call's status word (TAMI_ETIMEOUT in the device status; the
+ * reduced outputs of that launch become NaN) and then waits again, bounded by 2^24 polls, for the
+ * copy to land, so a completed copy is still used safely.  With 0 every staging wait "runs out"
+ * on a valid copy, which lets a test drive that path without any fault.  Plans (tami_batch_plan)
+ * take the value at planning time; the other calls at each launch.  Process-wide. */
+int tami_debug_set_wait_limit(int64_t first_stage_spins);
 
 /* Diagnostic: the kernels' exponential for t <= 0 (table-driven after Tang, ACM TOMS 1989), applied
  * elementwise: y = e^t, em = e^t - 1, and y_plain = e^t from the variant that does not form

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_PKG, "libtami.so")
 
 TAMI_OK, TAMI_EINVAL, TAMI_ENOMEM, TAMI_ECUDA, TAMI_ETIMEOUT, TAMI_EUNSUPPORTED = range(6)
 TAMI_JIT_NEVER, TAMI_JIT_AUTO, TAMI_JIT_ALWAYS = range(3)
+TAMI_STAGING_AUTO, TAMI_STAGING_STREAMED = range(2)
 
 # functions declared in include/tami.h (checked by tests/test_lib_host.py)
 EXPORTS = [
@@ -24,6 +25,7 @@ EXPORTS = [
     "tami_batch_plan", "tami_batch_info", "tami_batch_launch",
     "tami_batch_destroy", "tami_batch_debug_set_item", "tami_batch_specialised",
     "tami_enumerate_sigma",
+    "tami_set_table_staging", "tami_debug_set_wait_limit",
     "tami_selftest_exp", "tami_selftest_sincos", "tami_selftest_fp64_rate", "tami_destroy",
 ]
 
@@ -109,6 +111,8 @@ def lib():
     L.tami_batch_debug_set_item.restype = ctypes.c_int
     L.tami_batch_destroy.restype = None
     L.tami_enumerate_sigma.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
+    L.tami_set_table_staging.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.tami_debug_set_wait_limit.argtypes = [i64]
     L.tami_selftest_exp.argtypes = [dp, i64, dp, dp, dp, vp]
     L.tami_selftest_sincos.argtypes = [dp, i64, dp, dp, vp]
     L.tami_selftest_fp64_rate.argtypes = [ctypes.c_int, i64, dp, ctypes.POINTER(ctypes.c_double), vp]

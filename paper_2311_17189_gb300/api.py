@@ -52,6 +52,23 @@ def set_jit(mode):
     L.check(L.lib().tami_set_jit(JIT_MODES[mode]))
 
 
+STAGING_MODES = {"auto": L.TAMI_STAGING_AUTO, "streamed": L.TAMI_STAGING_STREAMED}
+
+
+def set_table_staging(mode, chunk_ops=0):
+    """How the generic forward kernels stage a table (tami_set_table_staging): 'auto' keeps the
+    pole-DAG program resident in shared memory when it fits beside the tiles and streams it in
+    chunks otherwise, 'streamed' always streams it (same bits); chunk_ops even in [16, 4096], 0
+    keeps the current chunk size.  Process-wide."""
+    L.check(L.lib().tami_set_table_staging(STAGING_MODES[mode], int(chunk_ops)))
+
+
+def debug_set_wait_limit(first_stage_spins):
+    """Test hook (tami_debug_set_wait_limit): bound the first stage of the generic kernels'
+    mbarrier waits; -1 restores the default."""
+    L.check(L.lib().tami_debug_set_wait_limit(int(first_stage_spins)))
+
+
 class Diagram:
     """An AMI solution (flat terms A * FT * R, Sec. 2.2) and its device term table.  The last
     n_ext columns of alpha are external variables (Sec. 2.3); the others are summed.  Momentum

@@ -60,26 +60,33 @@ struct BatchParams {
   const double* params;   // t, t', mu, kx, ky, beta
   const double* X;
   int n_f;
-  int table_cap, max_cden, max_g2;   // largest table (bytes), denominators and groups
+  int table_cap, max_cden, max_g2;   // largest staged table part (bytes), denominators and groups
+  int ring_chunk;         // streamed programs: ops per ring buffer; 0 when every program is resident
+  long long wait_limit;   // bound of the first stage of every mbarrier wait
   int* counter;
   int* status;
   double* partial;        // [n_items][n_f][4]
 };
 
-size_t batch_smem_bytes(int table_cap, int n_f, int max_cden, int max_g2) {
-  return (size_t)table_cap +
+// Shared memory: staged table part (table_cap: [0, off_opsb) of the largest table, or [0, off_ops)
+// with streamed programs) | ring [2][ring_chunk] ops | Xs | AXI, AXI2 | CB | W | red
+size_t batch_smem_bytes(int table_cap, int ring_chunk, int n_f, int max_cden, int max_g2) {
+  return (size_t)table_cap + 2 * 8 * (size_t)ring_chunk +
          sizeof(double) * ((2 + 2 * (size_t)max_cden) * n_f + (size_t)(max_cden + max_g2 + 4) * kBlock);
 }
 
+template <bool STREAM>
 __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TableHeader Hs;
   __shared__ __align__(8) unsigned long long bar;
+  __shared__ __align__(8) unsigned long long ring_bar[2];
   __shared__ int s_item;
   const int tid = threadIdx.x;
   const int n_f = P.n_f;
   unsigned char* tab = smem;
-  double* Xs = reinterpret_cast<double*>(smem + P.table_cap);
+  const int ring_chunk = STREAM ? P.ring_chunk : 0;
+  double* Xs = reinterpret_cast<double*>(smem + P.table_cap + 2 * 8 * (size_t)ring_chunk);
   double* AXI = Xs + 2 * n_f;
   double* AXI2 = AXI + P.max_cden * n_f;
   double* CB = AXI2 + P.max_cden * n_f;
@@ -87,6 +94,18 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchParams P) {
   double* red = W + P.max_g2 * kBlock;
   for (int i = tid; i < 2 * n_f; i += kBlock) Xs[i] = P.X[i];
   mbar_init(&bar);
+  OpRing R;
+  if (STREAM) {
+    mbar_init(&ring_bar[0]);
+    mbar_init(&ring_bar[1]);
+    R.buf = reinterpret_cast<int2*>(smem + P.table_cap);
+    R.bar = ring_bar;
+    R.status = P.status;
+    R.limit = P.wait_limit;
+    R.chunk = ring_chunk;
+    R.waits[0] = R.waits[1] = 0;
+    R.failed = false;
+  }
   const FreqMap M = freq_map(n_f, tid);
   TileArgs A;
   A.t = P.params[0]; A.tp = P.params[1]; A.mu = P.params[2]; A.kx = P.params[3]; A.ky = P.params[4];
@@ -116,17 +135,24 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchParams P) {
     if (d != cur_d) {
       if (tid == 0) Hs = P.diags[d].h;
       __syncthreads();
-      const bool ok = bulk_stage(tab, P.blobs + P.diags[d].blob_off, Hs.bytes, &bar, phase, P.status);
+      const bool ok = bulk_stage(tab, P.blobs + P.diags[d].blob_off, STREAM ? Hs.off_ops : Hs.off_opsb, &bar, phase,
+                                 P.status, P.wait_limit);
       if (__syncthreads_or(!ok)) return;
       phase ^= 1u;
       cur_d = d;
+      if (STREAM) {
+        R.src = P.blobs + P.diags[d].blob_off + Hs.off_ops;
+        R.n_ops = Hs.n_ops;
+        R.n_chunks = (Hs.n_ops + ring_chunk - 1) / ring_chunk;
+      }
       xr_zero = freq_constants(Hs, table_view(tab, Hs), Xs, n_f, AXI, AXI2);
     }
     const TableView T = table_view(tab, Hs);
     A.seed = P.diags[d].seed;
     A.n = P.diags[d].n;
     for (int i = 0; i < kMaxFreqPerThread; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0;
-    for (long long tile = item.tile0; tile < item.tile1; ++tile) fwd_tile<false, false>(Hs, T, A, tile, Xs, AXI, AXI2, xr_zero, CB, W, M, acc);
+    for (long long tile = item.tile0; tile < item.tile1; ++tile)
+      fwd_tile<false, false, STREAM>(Hs, T, A, tile, Xs, AXI, AXI2, xr_zero, CB, W, M, acc, R);
     block_reduce_store(M, n_f, acc, red, P.partial + (size_t)it * n_f * 4);
   }
 }
@@ -175,6 +201,7 @@ struct tami_batch {
   std::vector<uint64_t> seeds;
   int chunk = 0, grid = 0, n_items = 0;
   int table_cap = 0, max_cden = 0, max_g2 = 0;   // over the diagrams the persistent kernel runs
+  int ring_chunk = 0;                              // streamed programs: ops per ring buffer
   std::vector<int> spec;                           // 1: the diagram runs its specialised kernel
   std::vector<tami::JitHandle> jit;                // those kernels, kept loaded by the batch
   std::vector<int> jit_grid;
@@ -275,12 +302,16 @@ int build(tami_batch* b, int chunk, int grid_cap, bool with_spec) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
   // grid: resident blocks, capped
   DeviceProps dp = device_props(b->device);
-  b->smem = batch_smem_bytes(b->table_cap, n_f, b->max_cden, b->max_g2);
-  if (b->smem > dp.smem_optin) { set_error("largest table and tiles exceed shared memory"); return TAMI_EUNSUPPORTED; }
-  e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  b->smem = batch_smem_bytes(b->table_cap, b->ring_chunk, n_f, b->max_cden, b->max_g2);
+  if (b->smem > dp.smem_optin) {
+    set_error("largest table and tiles exceed shared memory even with the pole-DAG programs streamed");
+    return TAMI_EUNSUPPORTED;
+  }
+  const void* kfn = b->ring_chunk ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>;
+  e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBlock, b->smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kBlock, b->smem);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   int grid = std::max(1, dp.sms * std::max(per_sm, 1));
   if (grid_cap > 0) grid = std::min(grid, grid_cap);
@@ -300,6 +331,8 @@ int build(tami_batch* b, int chunk, int grid_cap, bool with_spec) {
   P.X = reinterpret_cast<const double*>(b->mem + L.X);
   P.n_f = n_f;
   P.table_cap = b->table_cap;
+  P.ring_chunk = b->ring_chunk;
+  P.wait_limit = wait_limit();
   P.max_cden = b->max_cden;
   P.max_g2 = b->max_g2;
   P.counter = reinterpret_cast<int*>(b->mem + L.ctr);
@@ -308,7 +341,10 @@ int build(tami_batch* b, int chunk, int grid_cap, bool with_spec) {
   e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
   cudaMemsetAsync(b->mem + L.ctr, 0, 2 * sizeof(int), b->cap);
-  if (n_items > 0) batch_kernel<<<grid, kBlock, b->smem, b->cap>>>(P);
+  if (n_items > 0) {
+    if (b->ring_chunk) batch_kernel<true><<<grid, kBlock, b->smem, b->cap>>>(P);
+    else batch_kernel<false><<<grid, kBlock, b->smem, b->cap>>>(P);
+  }
   int rc = TAMI_OK;
   for (int d = 0; d < n_d && rc == TAMI_OK; ++d)
     if (spec_row[d] >= 0)
@@ -465,11 +501,26 @@ int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* sampl
     }
     if (rc) { delete b; return rc; }
   }
+  // staging: every forward program resident beside the tiles when the largest fits (and streaming
+  // is not forced), else the programs streamed through the ring
+  int cap_res = 0, cap_prog = 0;
   for (int d = 0; d < n_d; ++d) {
     if (b->spec[d]) continue;
-    b->table_cap = std::max(b->table_cap, (int)up256(ds[d]->blob.size()));
+    cap_res = std::max(cap_res, ds[d]->hdr.off_opsb);
+    cap_prog = std::max(cap_prog, ds[d]->hdr.off_ops);
     b->max_cden = std::max(b->max_cden, ds[d]->hdr.n_cden);
     b->max_g2 = std::max(b->max_g2, ds[d]->hdr.n_g2);
+  }
+  {
+    const size_t optin = device_props(b->device).smem_optin;
+    if (staging_mode() != TAMI_STAGING_STREAMED &&
+        batch_smem_bytes(cap_res, 0, n_f, b->max_cden, b->max_g2) <= optin) {
+      b->table_cap = cap_res;
+      b->ring_chunk = 0;
+    } else {
+      b->table_cap = cap_prog;
+      b->ring_chunk = ring_chunk_ops();
+    }
   }
   e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaStreamCreate"); }

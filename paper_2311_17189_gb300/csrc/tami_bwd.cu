@@ -47,15 +47,22 @@ struct BwdParams {
   double* ps_v;          // fused pass: [n_f][n][2] each sample's value, or null
   double* partial;       // [grid][2 n_f + 3]
   int* status;
+  long long wait_limit;   // bound of the first stage of the staging wait
 };
 
 // Values each block reduces: dv/dX [n_f][2], the three parameter gradients and, in the fused pass,
 // the forward's sums [n_f][4] (Re, Im, Re^2, Im^2).
 __host__ __device__ __forceinline__ int bwd_nval(int n_f, bool fwd) { return 2 * n_f + 3 + (fwd ? 4 * n_f : 0); }
 
-// Shared memory: table | X, G [n_f][2] | AXI, AXI2 [n_cden][n_f] | red [4 warps][nval]
+// Shared memory: table | X, G [n_f][2] | AXI, AXI2 [n_cden][n_f] | red [4 warps][nval].  The table
+// part is [0, off_ops) followed by the adjoint program [off_opsb, bytes) (the forward program is
+// not staged).
+__host__ __device__ __forceinline__ size_t bwd_table_smem(const TableHeader& h) {
+  return (size_t)h.off_ops + (size_t)(h.bytes - h.off_opsb);
+}
+
 __host__ __device__ __forceinline__ size_t bwd_smem_bytes(const TableHeader& h, int n_f, bool fwd) {
-  return (size_t)align16(h.bytes) +
+  return bwd_table_smem(h) +
          sizeof(double) * ((4 + 2 * (size_t)h.n_cden) * n_f + 4 * (size_t)bwd_nval(n_f, fwd));
 }
 
@@ -142,9 +149,10 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
   extern __shared__ __align__(16) unsigned char smem[];
   const TableHeader& H = P.h;
   const int tid = threadIdx.x;
-  if (!stage_table(smem, P.table, H.bytes, P.status)) return;
+  if (!stage_table(smem, P.table, H.off_ops, P.status, P.wait_limit, P.table + H.off_opsb, H.bytes - H.off_opsb))
+    return;
   const int n_f = P.n_f;
-  double* Xs = reinterpret_cast<double*>(smem + align16(H.bytes));
+  double* Xs = reinterpret_cast<double*>(smem + bwd_table_smem(H));
   double* Gs = Xs + 2 * n_f;
   double* AXI = Gs + 2 * n_f;
   double* AXI2 = AXI + H.n_cden * n_f;
@@ -166,7 +174,7 @@ __global__ void __launch_bounds__(kBlock, TAMI_BWD_MIN_BLOCKS) bwd_kernel(const 
   const double* cden_a = reinterpret_cast<const double*>(smem + H.off_cden_a);
   const int* g1 = reinterpret_cast<const int*>(smem + H.off_g1);
   const int* g1_tgt = reinterpret_cast<const int*>(smem + H.off_g1_tgt);
-  const int2* opsb = reinterpret_cast<const int2*>(smem + H.off_opsb);
+  const int2* opsb = reinterpret_cast<const int2*>(smem + H.off_ops);   // staged right after [0, off_ops)
   const int* g1_node = reinterpret_cast<const int*>(smem + H.off_g1_node);
   const double* leafA = reinterpret_cast<const double*>(smem + H.off_leafA);
   const int* g1rd = reinterpret_cast<const int*>(smem + H.off_g1rd);
@@ -419,11 +427,41 @@ __global__ void __launch_bounds__(kFinBlock) bwd_finalize_kernel(const double* p
   }
 }
 
-int bwd_grid(const tami_diagram* d, int n_f, long long n, size_t* smem_out, bool fwd) {
+// Whether the generic adjoint kernel can take the table: its per-thread arrays and shared memory.
+bool bwd_generic_ok(const tami_diagram* d, int n_f, bool fwd) {
+  const TableHeader& h = d->hdr;
+  if (h.n_combo > kBwCombos || h.n_fv > kBwFv || h.n_rden > kBwRden || h.n_cden > kBwCden ||
+      h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || h.n_nodes > kBwNodes || h.n_g2cd > kBwG2cd) {
+    set_error("term table exceeds the generic adjoint kernel's per-sample capacities: " + std::to_string(h.n_combo) +
+              " combinations (" + std::to_string(kBwCombos) + "), " + std::to_string(h.n_fv) + " Fermi values (" +
+              std::to_string(kBwFv) + "), " + std::to_string(h.n_rden) + " real denominators (" +
+              std::to_string(kBwRden) + "), " + std::to_string(h.n_cden) + " complex denominators (" +
+              std::to_string(kBwCden) + "), " + std::to_string(h.n_g1) + " groups (" + std::to_string(kBwG1) +
+              "), " + std::to_string(h.n_g2) + " frequency groups (" + std::to_string(kBwG2) + "), " +
+              std::to_string(h.n_nodes) + " DAG nodes (" + std::to_string(kBwNodes) + "), " +
+              std::to_string(h.n_g2cd) + " phase-2 factors (" + std::to_string(kBwG2cd) + ")");
+    return false;
+  }
+  if (bwd_smem_bytes(h, n_f, fwd) > device_props(d->device).smem_optin) {
+    set_error("term table and frequencies exceed shared memory in the generic adjoint kernel");
+    return false;
+  }
+  return true;
+}
+
+// Grid of an adjoint launch (the workspace holds its partial rows).  A table the generic kernel
+// cannot take (*generic_ok = false) runs only on the specialised kernel, whose launch is clamped to
+// the workspace's rows: 4 blocks per SM.
+int bwd_grid(const tami_diagram* d, int n_f, long long n, size_t* smem_out, bool fwd, bool* generic_ok = nullptr) {
   DeviceProps dp = device_props(d->device);
   const size_t smem = bwd_smem_bytes(d->hdr, n_f, fwd);
   if (smem_out) *smem_out = smem;
-  if (smem > dp.smem_optin) return -1;
+  const bool ok = bwd_generic_ok(d, n_f, fwd);
+  if (generic_ok) *generic_ok = ok;
+  if (!ok) {
+    const long long tiles = (n + kBlock - 1) / kBlock;
+    return (int)std::max(1LL, std::min(tiles, 4LL * dp.sms));
+  }
   int per_sm = 0;
   if (fwd) {
     cudaFuncSetAttribute(bwd_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -499,18 +537,6 @@ int bwd_check(const tami_diagram* d, int n_f) {
   const TableHeader& h = d->hdr;
   if (h.n_ext != 1) { set_error("momentum sampling takes one external frequency and momentum (n_ext = 1)"); return TAMI_EUNSUPPORTED; }
   if (h.max_der > 4) { set_error("the adjoint needs derivative orders up to 4"); return TAMI_EUNSUPPORTED; }
-  if (h.n_combo > kBwCombos || h.n_fv > kBwFv || h.n_rden > kBwRden || h.n_cden > kBwCden ||
-      h.n_g1 > kBwG1 || h.n_g2 > kBwG2 || h.n_nodes > kBwNodes || h.n_g2cd > kBwG2cd) {
-    set_error("term table exceeds the generic adjoint kernel's per-sample capacities: " + std::to_string(h.n_combo) +
-              " combinations (" + std::to_string(kBwCombos) + "), " + std::to_string(h.n_fv) + " Fermi values (" +
-              std::to_string(kBwFv) + "), " + std::to_string(h.n_rden) + " real denominators (" +
-              std::to_string(kBwRden) + "), " + std::to_string(h.n_cden) + " complex denominators (" +
-              std::to_string(kBwCden) + "), " + std::to_string(h.n_g1) + " groups (" + std::to_string(kBwG1) +
-              "), " + std::to_string(h.n_g2) + " frequency groups (" + std::to_string(kBwG2) + "), " +
-              std::to_string(h.n_nodes) + " DAG nodes (" + std::to_string(kBwNodes) + "), " +
-              std::to_string(h.n_g2cd) + " phase-2 factors (" + std::to_string(kBwG2cd) + ")");
-    return TAMI_EUNSUPPORTED;
-  }
   return TAMI_OK;
 }
 
@@ -528,7 +554,6 @@ int tami_backward_workspace(const tami_diagram* d, int64_t n_samples, int n_f, s
   if (rc) return rc;
   if (!bytes || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
   const int grid = bwd_grid(d, n_f, n_samples, nullptr, false);
-  if (grid < 0) { set_error("term table and frequencies exceed shared memory"); return TAMI_EUNSUPPORTED; }
   *bytes = kBwStatusBytes + sizeof(double) * (size_t)bwd_nval(n_f, false) * (size_t)grid;
   return TAMI_OK;
 }
@@ -538,7 +563,6 @@ int tami_forward_backward_workspace(const tami_diagram* d, int64_t n_samples, in
   if (rc) return rc;
   if (!bytes || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
   const int grid = bwd_grid(d, n_f, n_samples, nullptr, true);
-  if (grid < 0) { set_error("term table and frequencies exceed shared memory"); return TAMI_EUNSUPPORTED; }
   *bytes = kBwStatusBytes + sizeof(double) * (size_t)bwd_nval(n_f, true) * (size_t)grid;
   return TAMI_OK;
 }
@@ -555,13 +579,15 @@ int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed,
   if (!beta_ok(beta)) return TAMI_EINVAL;
   if (((uintptr_t)workspace & 255) != 0) { set_error("workspace must be 256-byte aligned"); return TAMI_EINVAL; }
   size_t smem = 0;
-  const int grid = bwd_grid(d, n_f, n_samples, &smem, false);
-  if (grid < 0) { set_error("term table and frequencies exceed shared memory"); return TAMI_EUNSUPPORTED; }
+  bool generic_ok = true;
+  const int grid = bwd_grid(d, n_f, n_samples, &smem, false, &generic_ok);
+  const std::string generic_why = generic_ok ? std::string() : std::string(tami_last_error());
   const size_t need = kBwStatusBytes + sizeof(double) * (size_t)bwd_nval(n_f, false) * (size_t)grid;
   if (workspace_bytes < need) { set_error("workspace too small"); return TAMI_EINVAL; }
   tami_diagram* dm = const_cast<tami_diagram*>(d);
-  const int sel = jit_select(dm, kJitKindBwd, n_samples, n_f);
+  const int sel = jit_select(dm, kJitKindBwd, n_samples, n_f, generic_ok);
   if (sel < 0) return -sel;
+  if (sel == 0 && !generic_ok) { set_error(generic_why); return TAMI_EUNSUPPORTED; }
   cudaStream_t st = (cudaStream_t)stream;
   int* status = static_cast<int*>(workspace);
   double* partial = reinterpret_cast<double*>(static_cast<char*>(workspace) + kBwStatusBytes);
@@ -584,6 +610,7 @@ int tami_backward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed,
     P.ps_dX = per_sample_dX; P.ps_grad = per_sample_grads;
     P.saved = saved;
     P.partial = partial; P.status = status;
+    P.wait_limit = wait_limit();
     if (saved) bwd_kernel<true, false><<<grid, kBlock, smem, st>>>(P);
     else bwd_kernel<false, false><<<grid, kBlock, smem, st>>>(P);
     e = cudaGetLastError();
@@ -608,14 +635,16 @@ int tami_forward_backward(const tami_diagram* d, const tami_lattice* lat, uint64
   if (!beta_ok(beta)) return TAMI_EINVAL;
   if (((uintptr_t)workspace & 255) != 0) { set_error("workspace must be 256-byte aligned"); return TAMI_EINVAL; }
   size_t smem = 0;
-  const int grid = bwd_grid(d, n_f, n_samples, &smem, true);
-  if (grid < 0) { set_error("term table and frequencies exceed shared memory"); return TAMI_EUNSUPPORTED; }
+  bool generic_ok = true;
+  const int grid = bwd_grid(d, n_f, n_samples, &smem, true, &generic_ok);
+  const std::string generic_why = generic_ok ? std::string() : std::string(tami_last_error());
   const size_t need = kBwStatusBytes + sizeof(double) * (size_t)bwd_nval(n_f, true) * (size_t)grid;
   if (workspace_bytes < need) { set_error("workspace too small"); return TAMI_EINVAL; }
   // the diagram's specialised kernel (compiled once and cached with it) or the generic one
   tami_diagram* dm = const_cast<tami_diagram*>(d);
-  const int sel = jit_select(dm, kJitKindFused, n_samples, n_f);
+  const int sel = jit_select(dm, kJitKindFused, n_samples, n_f, generic_ok);
   if (sel < 0) return -sel;
+  if (sel == 0 && !generic_ok) { set_error(generic_why); return TAMI_EUNSUPPORTED; }
   cudaStream_t st = (cudaStream_t)stream;
   int* status = static_cast<int*>(workspace);
   double* partial = reinterpret_cast<double*>(static_cast<char*>(workspace) + kBwStatusBytes);
@@ -637,6 +666,7 @@ int tami_forward_backward(const tami_diagram* d, const tami_lattice* lat, uint64
     P.X = X; P.G = gout; P.n_f = n_f; P.beta = beta;
     P.ps_dX = per_sample_dX; P.ps_grad = per_sample_grads; P.ps_v = per_sample;
     P.partial = partial; P.status = status;
+    P.wait_limit = wait_limit();
     bwd_kernel<false, true><<<grid, kBlock, smem, st>>>(P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");

@@ -18,6 +18,8 @@
 
 #include <cstdint>
 #include <cstring>
+#include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -44,23 +46,47 @@ struct FwdParams {
   double* saved;                // [n_rep + 2 n_rep_ext][n] for the adjoint, or null (momentum mode)
   double* partial;              // [gridDim][n_f][4] or null
   int* status;                  // device status word or null
+  int ring_chunk;               // streamed program: ops per ring buffer (even); 0 when resident
+  long long wait_limit;         // bound of the first stage of every mbarrier wait
 };
 
 
+// Staged part of the table: [0, off_opsb) (everything the forward reads), or with a streamed
+// program [0, off_ops) and the two ring buffers.
+__host__ __device__ __forceinline__ size_t fwd_table_smem(const TableHeader& h, int ring_chunk) {
+  return ring_chunk ? (size_t)h.off_ops + 2 * 8 * (size_t)ring_chunk : (size_t)h.off_opsb;
+}
+
 // Shared memory: table | Xs [n_xk][n_f][2] | AXI, AXI2 [n_cden][n_f] | CB [n_cden][S] | W [n_g2][S] |
 // red [4][S]
-__host__ __device__ __forceinline__ size_t fwd_smem_bytes(const TableHeader& h, int n_f) {
-  return (size_t)align16(h.bytes) +
+__host__ __device__ __forceinline__ size_t fwd_smem_bytes(const TableHeader& h, int n_f, int ring_chunk) {
+  return fwd_table_smem(h, ring_chunk) +
          sizeof(double) * ((2 * (size_t)h.n_xk + 2 * (size_t)h.n_cden) * n_f + (size_t)(h.n_cden + h.n_g2 + 4) * kBlock);
 }
 
-template <bool ENERGY_IN, bool SAVE>
+template <bool ENERGY_IN, bool SAVE, bool STREAM>
 __global__ void __launch_bounds__(kBlock) fwd_kernel(const FwdParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long ring_bar[2];
   const TableHeader& H = P.h;
   const int tid = threadIdx.x;
-  if (!stage_table(smem, P.table, H.bytes, P.status)) return;
-  double* Xs = reinterpret_cast<double*>(smem + align16(H.bytes));
+  if (!stage_table(smem, P.table, STREAM ? H.off_ops : H.off_opsb, P.status, P.wait_limit)) return;
+  OpRing R;
+  if (STREAM) {
+    mbar_init(&ring_bar[0]);
+    mbar_init(&ring_bar[1]);
+    R.src = P.table + H.off_ops;
+    R.buf = reinterpret_cast<int2*>(smem + H.off_ops);
+    R.bar = ring_bar;
+    R.status = P.status;
+    R.limit = P.wait_limit;
+    R.n_ops = H.n_ops;
+    R.chunk = P.ring_chunk;
+    R.n_chunks = (H.n_ops + P.ring_chunk - 1) / P.ring_chunk;
+    R.waits[0] = R.waits[1] = 0;
+    R.failed = false;
+  }
+  double* Xs = reinterpret_cast<double*>(smem + fwd_table_smem(H, STREAM ? P.ring_chunk : 0));
   double* AXI = Xs + 2 * H.n_xk * P.n_f;
   double* AXI2 = AXI + H.n_cden * P.n_f;
   double* CB = AXI2 + H.n_cden * P.n_f;
@@ -80,7 +106,7 @@ __global__ void __launch_bounds__(kBlock) fwd_kernel(const FwdParams P) {
   A.n_f = P.n_f;
   const long long n_tiles = (P.n + kBlock - 1) / kBlock;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x)
-    fwd_tile<ENERGY_IN, SAVE>(H, T, A, tile, Xs, AXI, AXI2, xr_zero, CB, W, M, acc);
+    fwd_tile<ENERGY_IN, SAVE, STREAM>(H, T, A, tile, Xs, AXI, AXI2, xr_zero, CB, W, M, acc, R);
   if (!P.partial) return;
   block_reduce_store(M, P.n_f, acc, red, P.partial + (size_t)blockIdx.x * P.n_f * 4);
 }
@@ -176,36 +202,72 @@ __global__ void sample_energies_kernel(const FwdParams P, double* E) {
 }
 
 // ------------------------------------------------------------------------------- host glue
+// How the generic forward stages a table: the program resident beside the tiles when it fits
+// (and streaming is not forced), else streamed through the ring; ring_chunk = 0 means resident.
+// Returns false when even the streamed layout exceeds shared memory.
+bool fwd_staging(const tami_diagram* d, int n_f, int* ring_chunk, size_t* smem) {
+  const size_t optin = device_props(d->device).smem_optin;
+  const int mode = staging_mode();
+  if (mode != TAMI_STAGING_STREAMED && fwd_smem_bytes(d->hdr, n_f, 0) <= optin) {
+    *ring_chunk = 0;
+    *smem = fwd_smem_bytes(d->hdr, n_f, 0);
+    return true;
+  }
+  *ring_chunk = ring_chunk_ops();
+  *smem = fwd_smem_bytes(d->hdr, n_f, *ring_chunk);
+  if (*smem > optin) {
+    set_error("term table and tiles exceed shared memory even with the pole-DAG program streamed: " +
+              std::to_string(*smem) + " bytes (at most " + std::to_string(optin) + ")");
+    return false;
+  }
+  return true;
+}
+
+template <bool E_IN, bool SAVE, bool STREAM>
+int fwd_blocks_per_sm(size_t smem) {
+  cudaFuncSetAttribute(fwd_kernel<E_IN, SAVE, STREAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<E_IN, SAVE, STREAM>, kBlock, smem) != cudaSuccess)
+    per_sm = 1;
+  return per_sm < 1 ? 1 : per_sm;
+}
+
 template <bool E_IN, bool SAVE>
 int launch_fwd(const tami_diagram* d, FwdParams& P, cudaStream_t stream, int max_blocks) {
-  const size_t smem = fwd_smem_bytes(d->hdr, P.n_f);
+  size_t smem = 0;
+  int chunk = 0;
+  if (!fwd_staging(d, P.n_f, &chunk, &smem)) return TAMI_EUNSUPPORTED;
+  P.ring_chunk = chunk;
   DeviceProps dp = device_props(d->device);
-  if (smem > dp.smem_optin) { set_error("term table and tiles exceed shared memory"); return TAMI_EUNSUPPORTED; }
-  cudaError_t e = cudaFuncSetAttribute(fwd_kernel<E_IN, SAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<E_IN, SAVE>, kBlock, smem);
-  if (e != cudaSuccess) return cuda_fail(e, "occupancy");
-  if (per_sm < 1) per_sm = 1;
+  const int per_sm = chunk ? fwd_blocks_per_sm<E_IN, SAVE, true>(smem) : fwd_blocks_per_sm<E_IN, SAVE, false>(smem);
   long long tiles = (P.n + kBlock - 1) / kBlock;
   long long grid = (long long)dp.sms * per_sm;
   if (grid > tiles) grid = tiles;
   if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
   if (grid < 1) grid = 1;
-  fwd_kernel<E_IN, SAVE><<<(unsigned)grid, kBlock, smem, stream>>>(P);
-  e = cudaGetLastError();
+  if (chunk) fwd_kernel<E_IN, SAVE, true><<<(unsigned)grid, kBlock, smem, stream>>>(P);
+  else fwd_kernel<E_IN, SAVE, false><<<(unsigned)grid, kBlock, smem, stream>>>(P);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fwd_kernel launch");
   return TAMI_OK;
 }
 
-int grid_for(const tami_diagram* d, int n_f, long long n) {
+// Grid of a momentum-mode forward launch (the workspace holds one partial row per block).  When
+// the generic kernel cannot stage the table (*generic_ok = false) only the specialised kernel can
+// run it, whose launch is clamped to the rows of the workspace: 4 blocks per SM.
+int grid_for(const tami_diagram* d, int n_f, long long n, bool* generic_ok = nullptr) {
   DeviceProps dp = device_props(d->device);
-  const size_t smem = fwd_smem_bytes(d->hdr, n_f);
-  int per_sm = 0;
-  cudaFuncSetAttribute(fwd_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<false, false>, kBlock, smem) != cudaSuccess)
-    per_sm = 1;
-  if (per_sm < 1) per_sm = 1;
+  size_t smem = 0;
+  int chunk = 0;
+  const bool ok = fwd_staging(d, n_f, &chunk, &smem);
+  if (generic_ok) *generic_ok = ok;
+  if (!ok) {
+    const long long tiles = (n + kBlock - 1) / kBlock;
+    return (int)std::max(1LL, std::min(tiles, 4LL * dp.sms));
+  }
+  // the saving instance shares the grid (one workspace size for both)
+  const int per_sm = chunk ? std::min(fwd_blocks_per_sm<false, false, true>(smem), fwd_blocks_per_sm<false, true, true>(smem))
+                           : std::min(fwd_blocks_per_sm<false, false, false>(smem), fwd_blocks_per_sm<false, true, false>(smem));
   long long tiles = (n + kBlock - 1) / kBlock;
   long long grid = (long long)dp.sms * per_sm;
   if (grid > tiles) grid = tiles;
@@ -240,10 +302,15 @@ FwdParams make_params(const tami_diagram* d, int n_f, double beta) {
   P.table = static_cast<const unsigned char*>(d->d_blob);
   P.n_f = n_f;
   P.beta = beta;
+  P.wait_limit = wait_limit();
   return P;
 }
 
 constexpr size_t kStatusBytes = 256;
+
+std::atomic<int> g_staging_mode{TAMI_STAGING_AUTO};
+std::atomic<int> g_ring_chunk{512};
+std::atomic<long long> g_wait_limit{kSpinLimit};
 
 // Scratch of tami_forward_noalloc: a status word (first 256 bytes) followed by the per-block
 // partial sums [grid][n_f][4].  It lives in the library image, so every GPU that loads the
@@ -271,6 +338,10 @@ unsigned char* noalloc_scratch(int dev) {
 }
 
 }  // namespace
+
+int staging_mode() { return g_staging_mode.load(); }
+int ring_chunk_ops() { return g_ring_chunk.load(); }
+long long wait_limit() { return g_wait_limit.load(); }
 }  // namespace tami
 
 using namespace tami;
@@ -338,7 +409,10 @@ int tami_eval_energies(const tami_diagram* d, const double* E, int64_t n_e, cons
   if (n_e == 0) return TAMI_OK;              // nothing to read or write: E and out may be NULL
   if (!E || !X || !out) { set_error("bad argument"); return TAMI_EINVAL; }
   tami_diagram* dm = const_cast<tami_diagram*>(d);
-  const int sel = jit_select(dm, kJitKindEnergy, n_e, n_f);
+  int chunk = 0;
+  size_t smem = 0;
+  const bool generic_ok = fwd_staging(d, n_f, &chunk, &smem);
+  const int sel = jit_select(dm, kJitKindEnergy, n_e, n_f, generic_ok);
   if (sel < 0) return -sel;
   if (sel == 1) {
     int grid = 0;
@@ -376,11 +450,12 @@ int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, 
   if (!lat || !X || !mean || !workspace || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
   if (!beta_ok(beta)) return TAMI_EINVAL;
   if (((uintptr_t)workspace & 255) != 0) { set_error("workspace must be 256-byte aligned"); return TAMI_EINVAL; }
-  const int grid = grid_for(d, n_f, n_samples);
+  bool generic_ok = true;
+  const int grid = grid_for(d, n_f, n_samples, &generic_ok);
   const size_t need = kStatusBytes + sizeof(double) * 4 * (size_t)n_f * (size_t)grid;
   if (workspace_bytes < need) { set_error("workspace too small"); return TAMI_EINVAL; }
   tami_diagram* dm = const_cast<tami_diagram*>(d);
-  const int sel = jit_select(dm, kJitKindFwd, n_samples, n_f);
+  const int sel = jit_select(dm, kJitKindFwd, n_samples, n_f, generic_ok);
   if (sel < 0) return -sel;
   cudaStream_t st = (cudaStream_t)stream;
   int* status = static_cast<int*>(workspace);
@@ -417,12 +492,15 @@ int tami_forward(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, 
 int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_t seed, uint64_t offset,
                          int64_t n_samples, const double* X, int n_f, double beta, double* mean, double* var,
                          double* per_sample, tami_stream_t stream) {
+  return guarded([&]() -> int {
   int rc = check_common(d, n_f);
   if (!rc) rc = check_momentum(d);
   if (rc) return rc;
   if (!lat || !X || !mean || n_samples < 1) { set_error("bad argument"); return TAMI_EINVAL; }
   if (!beta_ok(beta)) return TAMI_EINVAL;
-  const int grid = grid_for(d, n_f, n_samples);
+  bool generic_ok = true;
+  const int grid = grid_for(d, n_f, n_samples, &generic_ok);
+  if (!generic_ok) return TAMI_EUNSUPPORTED;   // this call runs the generic kernel only
   const size_t need = kStatusBytes + sizeof(double) * 4 * (size_t)n_f * (size_t)grid;
   if (need > kNoAllocScratchBytes) {
     set_error("tami_forward_noalloc: needs " + std::to_string(need) + " bytes of scratch for n_f=" +
@@ -445,11 +523,33 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
   P.per_sample = per_sample;
   P.partial = partial;
   P.status = status;
+  jit_mark_generic(const_cast<tami_diagram*>(d));
   rc = launch_fwd<false, false>(d, P, st, grid);
   if (rc) return rc;
   finalize_kernel<<<n_f, kFinBlock, 0, st>>>(partial, grid, n_f, n_samples, status, mean, var);
   e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "finalize launch");
+  });
+}
+
+int tami_set_table_staging(int mode, int chunk_ops) {
+  if ((mode != TAMI_STAGING_AUTO && mode != TAMI_STAGING_STREAMED) ||
+      (chunk_ops != 0 && (chunk_ops < 16 || chunk_ops > 4096 || (chunk_ops & 1)))) {
+    set_error("table staging: mode TAMI_STAGING_AUTO or TAMI_STAGING_STREAMED, chunk_ops 0 or even in [16, 4096]");
+    return TAMI_EINVAL;
+  }
+  g_staging_mode.store(mode);
+  if (chunk_ops) g_ring_chunk.store(chunk_ops);
+  return TAMI_OK;
+}
+
+int tami_debug_set_wait_limit(int64_t first_stage_spins) {
+  if (first_stage_spins < -1 || first_stage_spins > dev::kSpinLimit) {
+    set_error("wait limit: -1 (default) or 0 .. 2^24");
+    return TAMI_EINVAL;
+  }
+  g_wait_limit.store(first_stage_spins < 0 ? dev::kSpinLimit : (long long)first_stage_spins);
+  return TAMI_OK;
 }
 
 int tami_selftest_exp(const double* t, int64_t n, double* y, double* em, double* y_plain, tami_stream_t stream) {

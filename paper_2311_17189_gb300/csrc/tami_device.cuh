@@ -50,19 +50,32 @@ __device__ __forceinline__ void mbar_init(unsigned long long* bar) {
   }
 }
 
-__device__ __forceinline__ bool bulk_stage(unsigned char* dst, const unsigned char* src, int bytes,
-                                           unsigned long long* bar, uint32_t parity, int* status) {
+// Thread 0 only: arm `bar` for `bytes` bytes in total and start the copy of bytes0 bytes from src0
+// to dst0 and, if bytes1 > 0, of bytes1 bytes from src1 to dst1 (all multiples of 16, addresses
+// 16-byte aligned), both completing on `bar`.
+__device__ __forceinline__ void bulk_issue(unsigned char* dst0, const unsigned char* src0, int bytes0,
+                                           unsigned char* dst1, const unsigned char* src1, int bytes1,
+                                           unsigned long long* bar) {
   const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
-  if (threadIdx.x == 0) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    // order this block's earlier generic-proxy reads of dst before the async-proxy writes
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+  // order this block's earlier generic-proxy reads of the destinations before the async-proxy writes
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes0 + bytes1) : "memory");
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"((uint32_t)__cvta_generic_to_shared(dst0)), "l"(src0), "r"(bytes0), "r"(b) : "memory");
+  if (bytes1 > 0)
     asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(d), "l"(src), "r"(bytes), "r"(b) : "memory");
-  }
+                 ::"r"((uint32_t)__cvta_generic_to_shared(dst1)), "l"(src1), "r"(bytes1), "r"(b) : "memory");
+}
+
+// Every thread: wait, bounded, for phase `parity` of `bar`; on timeout the status word is set and
+// the copy is waited for again (bounded), so that it has landed before the block goes on or exits.
+// `limit` bounds the first wait (kSpinLimit unless a test shortens it, tami_debug_set_wait_limit);
+// the second is always bounded by kSpinLimit.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, int* status,
+                                          long long limit = kSpinLimit) {
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
   uint32_t done = 0;
-  for (long long it = 0; it < kSpinLimit && !done; ++it) {
+  for (long long it = 0; it < limit && !done; ++it) {
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
                  : "=r"(done) : "r"(b), "r"(parity) : "memory");
     if (!done && it > 64) __nanosleep(64);
@@ -78,13 +91,23 @@ __device__ __forceinline__ bool bulk_stage(unsigned char* dst, const unsigned ch
   return done != 0;
 }
 
-__device__ __forceinline__ bool stage_table(unsigned char* dst, const unsigned char* src, int bytes, int* status) {
-  // one-shot staging: init the barrier, copy, wait on phase 0
+__device__ __forceinline__ bool bulk_stage(unsigned char* dst, const unsigned char* src, int bytes,
+                                           unsigned long long* bar, uint32_t parity, int* status,
+                                           long long limit = kSpinLimit) {
+  if (threadIdx.x == 0) bulk_issue(dst, src, bytes, nullptr, nullptr, 0, bar);
+  return mbar_wait(bar, parity, status, limit);
+}
+
+// One-shot staging of a table: [src, src + bytes0) to dst and, if bytes1 > 0, [src1, src1 + bytes1)
+// right after it; the decision to go on is the same in every thread of the block.
+__device__ __forceinline__ bool stage_table(unsigned char* dst, const unsigned char* src, int bytes0,
+                                            int* status, long long limit, const unsigned char* src1 = nullptr,
+                                            int bytes1 = 0) {
   __shared__ __align__(8) unsigned long long bar;
   mbar_init(&bar);
   __syncthreads();
-  const bool ok = bulk_stage(dst, src, bytes, &bar, 0u, status);
-  // the decision to go on must be the same in every thread of the block
+  if (threadIdx.x == 0) bulk_issue(dst, src, bytes0, dst + bytes0, src1, bytes1, &bar);
+  const bool ok = mbar_wait(&bar, 0u, status, limit);
   return !__syncthreads_or(!ok);
 }
 

@@ -65,16 +65,76 @@ __device__ __forceinline__ TableView table_view(const unsigned char* t, const Ta
   return v;
 }
 
+// The forward pole-DAG program streamed through shared memory, for tables whose program does not
+// fit beside the tiles: two buffers of `chunk` ops, each filled by one cp.async.bulk completed on
+// its own mbarrier; chunk c goes to buffer c & 1.  Every thread of the block walks the whole
+// program in order once per tile (threads without a sample walk it too), so moving to the next
+// chunk is a block-wide step: a barrier (no thread reads the old buffer any more), the refill of
+// that buffer with chunk c + 2 and the wait for chunk c + 1.  Every chunk that is issued is waited
+// for within the tile.  A wait that runs out sets the status word and leaves the ring failed: it
+// then hands out one in-range op (slot 0, leaf 0, value 0) and issues nothing more, and the
+// launch's outputs are NaN.
+struct OpRing {
+  const unsigned char* src;   // the program in global memory (the blob at off_ops)
+  int2* buf;                  // [2][chunk] in shared memory
+  unsigned long long* bar;    // [2] mbarriers, initialised by the kernel
+  int* status;
+  long long limit;            // bound of a wait's first stage
+  int n_ops, chunk, n_chunks;
+  int cur, lo, hi;            // the chunk in use and its op range
+  int waits[2];               // completed waits per barrier: the next wait's parity is waits & 1
+  bool failed;
+
+  __device__ __forceinline__ void fill(int c) {   // thread 0 only
+    const int o0 = c * chunk, n = min(chunk, n_ops - o0);
+    // whole 16-byte units: an odd last chunk reads one op past the program (the adjoint program
+    // follows it in the blob); the ring buffer holds it (chunk is even)
+    bulk_issue(reinterpret_cast<unsigned char*>(buf + (c & 1) * chunk), src + 8 * (size_t)o0, (8 * n + 15) & ~15,
+               nullptr, nullptr, 0, bar + (c & 1));
+  }
+  __device__ __forceinline__ void wait(int b) {
+    const bool ok = mbar_wait(bar + b, (uint32_t)(waits[b] & 1), status, limit);
+    ++waits[b];
+    failed |= __syncthreads_or(!ok) != 0;
+  }
+  // start of a tile's walk: chunks 0 and 1 in flight, wait for chunk 0
+  __device__ __forceinline__ void begin() {
+    __syncthreads();
+    if (!failed && threadIdx.x == 0) {
+      fill(0);
+      if (n_chunks > 1) fill(1);
+    }
+    cur = 0;
+    lo = 0;
+    hi = min(chunk, n_ops);
+    if (!failed) wait(0);
+  }
+  __device__ __forceinline__ void advance() {
+    __syncthreads();
+    if (!failed && threadIdx.x == 0 && cur + 2 < n_chunks) fill(cur + 2);
+    ++cur;
+    lo = cur * chunk;
+    hi = min(lo + chunk, n_ops);
+    if (!failed) wait(cur & 1);
+  }
+  __device__ __forceinline__ int2 get(int o) {
+    if (o >= hi) advance();
+    if (failed) return make_int2(kOpFirst | kOpLeaf, 0);
+    return buf[(cur & 1) * chunk + (o - lo)];
+  }
+};
+
 // Sum over a group's terms of A_t prod FT factors, by the group's pole-tree program: one fma per
 // edge of the (shared-sub-sum) tree, v[dst] = F * (leaf ? A[ref] : v[ref]) + (first ? 0 : v[dst]),
 // over value slots; the root's sum is written by the group's last op.  Both operand loads use
-// in-range indices, the select picks one.
-__device__ __forceinline__ double pole_tree(const TableView& T, int op0, int op1, const double* fv) {
+// in-range indices, the select picks one.  STREAM: the ops come from the ring.
+template <bool STREAM>
+__device__ __forceinline__ double pole_tree(const TableView& T, OpRing& R, int op0, int op1, const double* fv) {
   double v[kMaxSlots];
   v[0] = 0.0;
   int dst = 0;
   for (int o = op0; o < op1; ++o) {
-    const int2 op = T.ops[o];
+    const int2 op = STREAM ? R.get(o) : T.ops[o];
     dst = op.x & kOpDstMask;
     const int ref = op.x >> kOpRefShift;
     const bool leaf = op.x & kOpLeaf;
@@ -242,20 +302,27 @@ __device__ __forceinline__ void phase2_store(const TileArgs& A, int f, long long
 }
 
 // Shared memory per tile: Xs [n_xk][n_f][2] (from stage_freqs), AXI and AXI2 [n_cden][n_f] (from
-// freq_constants), CB [n_cden][kBlock], W [n_g2][kBlock].
-template <bool ENERGY_IN, bool SAVE>
+// freq_constants), CB [n_cden][kBlock], W [n_g2][kBlock].  STREAM: the pole-DAG program comes
+// through the ring R, which every thread of the block walks (a thread without a sample on zero
+// energies, its values dropped by phase 2).
+template <bool ENERGY_IN, bool SAVE, bool STREAM>
 __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& T, const TileArgs& A,
                                          long long tile, const double* Xs, const double* AXI, const double* AXI2,
-                                         bool xr_zero, double* CB, double* W, const FreqMap& M, double (*acc)[4]) {
+                                         bool xr_zero, double* CB, double* W, const FreqMap& M, double (*acc)[4],
+                                         OpRing& R) {
   const int tid = threadIdx.x;
   const long long s0 = tile * kBlock;
   const double beta = A.beta;
   // ---------------------------------------------------------------- phase 1 (thread = sample)
   {
     const long long s = s0 + tid;
-    if (s < A.n) {
+    const bool active = s < A.n;
+    if (STREAM) R.begin();
+    if (active || STREAM) {
       double E[kMaxLines];
-      if (ENERGY_IN) {
+      if (!active) {
+        for (int r = 0; r < H.n_rep; ++r) E[T.repl[r]] = 0.0;
+      } else if (ENERGY_IN) {
         for (int r = 0; r < H.n_rep; ++r) E[T.repl[r]] = A.E_in[s * H.N + T.repl[r]];
       } else {
         double kx[kMaxVars], ky[kMaxVars];
@@ -313,7 +380,7 @@ __device__ __forceinline__ void fwd_tile(const TableHeader& H, const TableView& 
       for (int gi = 0; gi < H.n_g1; ++gi) {
         const int tg = T.g1_tgt[gi];
         if (tg != cur) { W[cur * kBlock + tid] = wacc; wacc = 0.0; cur = tg; }
-        double ft = pole_tree(T, T.g1[4 * gi], T.g1[4 * gi + 1], fv);
+        double ft = pole_tree<STREAM>(T, R, T.g1[4 * gi], T.g1[4 * gi + 1], fv);
         for (int q = T.g1[4 * gi + 2]; q < T.g1[4 * gi + 3]; ++q) {
           const double r = rr[T.g1rd[2 * q]];
           for (int pw = T.g1rd[2 * q + 1]; pw > 0; --pw) ft *= r;

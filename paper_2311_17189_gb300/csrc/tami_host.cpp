@@ -629,8 +629,6 @@ int flatten(tami_diagram* d) {
   h.off_xvec = B.reserve(sizeof(double) * h.n_xk * n_ext);
   h.off_g1 = B.reserve(sizeof(int) * 4 * h.n_g1);
   h.off_g1_tgt = B.reserve(sizeof(int) * h.n_g1);
-  h.off_ops = B.reserve(sizeof(int) * 2 * h.n_ops);
-  h.off_opsb = B.reserve(sizeof(int) * 2 * h.n_ops);
   h.off_g1_node = B.reserve(sizeof(int) * (h.n_g1 + 1));
   h.off_leafA = B.reserve(sizeof(double) * h.n_leaves);
   h.off_g1rd = B.reserve(sizeof(int) * 2 * ng1rd);
@@ -639,6 +637,10 @@ int flatten(tami_diagram* d) {
   h.off_g2cd_p = B.reserve(sizeof(double) * ng2cd);
   h.off_pnode = B.reserve(sizeof(int) * 2 * h.n_pnode);
   h.off_g2node = B.reserve(sizeof(int) * h.n_g2);
+  // the two pole-DAG programs last: a forward kernel stages [0, off_opsb), an adjoint [0, off_ops)
+  // and [off_opsb, bytes), and a program too large for shared memory is streamed from off_ops
+  h.off_ops = B.reserve(sizeof(int) * 2 * h.n_ops);
+  h.off_opsb = B.reserve(sizeof(int) * 2 * h.n_ops);
   B.reserve(16);
   h.bytes = (int)B.b.size();
 

@@ -70,7 +70,11 @@ struct SymTerm {
 };
 
 // Flattened table.  All offsets are byte offsets into one blob, 16-byte aligned, so the blob
-// can be moved into shared memory with one bulk copy.  Integer records are int32.
+// can be moved into shared memory with bulk copies.  Integer records are int32.  The two
+// pole-DAG programs are the last sections, [off_ops, off_opsb) and [off_opsb, bytes), everything
+// else lies in [0, off_ops): a forward kernel stages [0, off_opsb), an adjoint kernel [0, off_ops)
+// and [off_opsb, bytes), and a forward whose program does not fit beside its tiles stages
+// [0, off_ops) and streams the program in chunks.
 struct TableHeader {
   int N, nv, m;
   int n_rep;        // lines whose energy is computed (first line of each momentum label)
@@ -108,8 +112,6 @@ struct TableHeader {
   int off_xvec;       // double [n_xk][n_ext]     v_k; the kernels form Y_kf = sum_q v_kq X_fq per row f
   int off_g1;         // int32 [n_g1][4]         op_begin, op_end, rd_begin, rd_end
   int off_g1_tgt;     // int32 [n_g1]             frequency group it feeds (ascending)
-  int off_ops;        // int2 [n_ops]            pole-tree program, forward encoding (kOp*)
-  int off_opsb;       // int2 [n_ops]            the same program, adjoint encoding (kOpb*)
   int off_g1_node;    // int32 [n_g1+1]           first adjoint node id of each group (its root)
   int off_leafA;      // double [n_leaves]        merged coefficients of the leaves
   int off_g1rd;       // int32 [n_g1rd][2]       real-den index, power
@@ -118,6 +120,8 @@ struct TableHeader {
   int off_g2cd_p;     // double [n_g2cd]          the same powers as doubles
   int off_pnode;      // int32 [n_pnode][2]      product node k: value[n_cden+k] = value[src] * value[c]
   int off_g2node;     // int32 [n_g2]             value index of each group's product (-1: R = 1)
+  int off_ops;        // int2 [n_ops]            pole-tree program, forward encoding (kOp*)
+  int off_opsb;       // int2 [n_ops]            the same program, adjoint encoding (kOpb*)
 };
 
 }  // namespace tami
@@ -144,7 +148,15 @@ int flatten(tami_diagram* d);  // terms -> hdr + blob + info
 // -status (the "always" mode when it cannot be built).  jit_launch writes the generic kernel's
 // per-block partial layout for that call into `partial` (at most max_grid rows).
 enum { kJitKindFused = 0, kJitKindFwd = 1, kJitKindBwd = 2, kJitKindEnergy = 3 };
-int jit_select(tami_diagram* d, int kind, int64_t n, int n_f);
+// generic_ok = false: the generic kernel cannot take the table (auto mode then specialises at any size)
+int jit_select(tami_diagram* d, int kind, int64_t n, int n_f, bool generic_ok = true);
+// How the generic forward kernels stage a table (tami_set_table_staging): TAMI_STAGING_AUTO keeps
+// the pole-DAG program resident when it fits beside the tiles, TAMI_STAGING_STREAMED always
+// streams it through the ring in chunks of ring_chunk_ops() ops.
+int staging_mode();
+int ring_chunk_ops();
+// Bound of the first stage of every mbarrier wait of the generic kernels (tami_debug_set_wait_limit).
+long long wait_limit();
 int jit_launch(tami_diagram* d, int kind, const tami_lattice* lat, uint64_t seed, uint64_t offset, int64_t n,
                const double* X, int n_f, double beta, const double* gout, double* per_sample, double* ps_dX,
                double* ps_grad, double* saved, double* partial, int max_grid, struct CUstream_st* st, int* grid_out);

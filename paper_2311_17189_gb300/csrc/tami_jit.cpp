@@ -758,11 +758,12 @@ size_t jit_smem(const TableHeader& h, int kind, int n_f) {
   return sizeof(double) * ((size_t)(4 + 2 * h.n_cden) * n_f + 4 * (size_t)nval);
 }
 
-int jit_select(tami_diagram* d, int kind, int64_t n, int n_f) {
+int jit_select(tami_diagram* d, int kind, int64_t n, int n_f, bool generic_ok) {
   const int mode = jit_mode();
   if (mode == TAMI_JIT_NEVER) return 0;
-  // large enough to repay a compilation: 2^21 Monte Carlo samples, or 2^25 (row, frequency) values
-  const bool big = kind == kKindEnergy ? (double)n * n_f >= 33554432.0 : n >= (int64_t(1) << 21);
+  // large enough to repay a compilation: 2^21 Monte Carlo samples, or 2^25 (row, frequency) values;
+  // a table the generic kernel cannot take goes to the specialised one at any size
+  const bool big = !generic_ok || (kind == kKindEnergy ? (double)n * n_f >= 33554432.0 : n >= (int64_t(1) << 21));
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d->device);
   const bool fits = (kind == kKindEnergy || n_f <= kJitMaxFreq) && jit_smem(d->hdr, kind, n_f) <= (size_t)optin;

@@ -2,6 +2,7 @@
 // read is checked against the size of what it indexes, the segment and group ranges against each
 // other, and both pole-DAG programs against their slot liveness (no value read before it is
 // written, every group ending on its root).  A table that fails is never uploaded.
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -37,9 +38,16 @@ bool in(long long v, long long lo, long long hi) { return v >= lo && v < hi; }
 }  // namespace
 
 bool validate_table(const TableHeader& h, const unsigned char* blob, size_t size, std::string* why) {
-  Reader R{blob, size};
+  // every section but the two programs lies in [0, off_ops); the programs are [off_ops, off_opsb)
+  // and [off_opsb, bytes) (the kernels stage these ranges by themselves)
+  const size_t prog = (size_t)h.off_ops;
+  Reader R{blob, prog <= size ? prog : 0};
   auto bad = [&](const std::string& w) { R.fail(w); };
   if ((size_t)h.bytes != size) bad("header size differs from the blob");
+  const size_t prog_bytes = (8 * (size_t)std::max(h.n_ops, 0) + 15) & ~size_t(15);
+  if (h.off_ops < 0 || (h.off_ops & 15) != 0 || (size_t)h.off_opsb != prog + prog_bytes ||
+      (size_t)h.bytes != prog + 2 * prog_bytes + 16)
+    bad("pole-DAG programs are not the last sections");
   if (!in(h.N, 1, kMaxLines + 1) || !in(h.nv, 2, kMaxVars + 1) || !in(h.n_ext, 1, kMaxExt + 1) ||
       h.m != h.nv - h.n_ext || h.m < 1)
     bad("line or variable count");
@@ -63,8 +71,10 @@ bool validate_table(const TableHeader& h, const unsigned char* blob, size_t size
   const double* xvec = R.at<double>(h.off_xvec, (size_t)h.n_xk * h.n_ext, "xvec");
   const int* g1 = R.at<int>(h.off_g1, 4 * (size_t)h.n_g1, "g1");
   const int* g1_tgt = R.at<int>(h.off_g1_tgt, h.n_g1, "g1_tgt");
-  const int* ops = R.at<int>(h.off_ops, 2 * (size_t)h.n_ops, "ops");
-  const int* opsb = R.at<int>(h.off_opsb, 2 * (size_t)h.n_ops, "opsb");
+  Reader RP{blob, size};
+  const int* ops = RP.at<int>(h.off_ops, 2 * (size_t)h.n_ops, "ops");
+  const int* opsb = RP.at<int>(h.off_opsb, 2 * (size_t)h.n_ops, "opsb");
+  if (!RP.ok) bad(RP.why);
   const int* g1_node = R.at<int>(h.off_g1_node, h.n_g1 + 1, "g1_node");
   R.at<double>(h.off_leafA, h.n_leaves, "leafA");
   const int* g1rd = R.at<int>(h.off_g1rd, 2 * (size_t)h.n_g1rd, "g1rd");

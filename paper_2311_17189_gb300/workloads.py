@@ -70,6 +70,17 @@ ORDER5 = dict(
     n_freq=1, n_samples=1 << 26, seed=SEED,
 )
 
+# Order 6 (the paper's scaling study runs to orders 6 and 9, Sec. 6.2): the order-6 diagram with
+# the largest flat table of this enumerator (5136 terms), forward + adjoint over 2^24 samples at
+# the order-5 workload's temperatures, one frequency i pi/beta.
+ORDER6 = dict(
+    name="order6_hubbard_sigma",
+    order=6,
+    code=(0, 1, 1, 6, 2, 4, 3, 5, 0, 3, 5, 2, 4),
+    t=1.0, tp=0.0, mu=0.0, betas=(2.0, 5.0, 10.0, 20.0), U=1.0, kext=(PI / 2, PI / 2),
+    n_freq=1, n_samples=1 << 24, seed=SEED,
+)
+
 # The paper's evaluation example at its own size (Sec. 5.1): the order-2 integrand of Sec. 5
 # (frequency labels (1,0,0), (0,1,0), (-1,1,1), identity energies) on 10^6 rows of energies
 # uniform on (-8, 8) and 100 fermionic Matsubara frequencies, beta = 1.

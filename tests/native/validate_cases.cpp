@@ -48,6 +48,8 @@ int main() {
     {"phase-1 group ranges overlap", [&](TableHeader& h, auto& b) { *I(b, h.off_g1, 0) = 1; }},
     {"slot count above capacity", [&](TableHeader& h, auto&) { h.n_slots = kMaxSlots + 1; }},
     {"section past the blob end", [&](TableHeader& h, auto&) { h.off_g2node = h.bytes; }},
+    {"section inside the pole-DAG programs", [&](TableHeader& h, auto&) { h.off_g2node = h.off_ops; }},
+    {"adjoint program overlapping the forward one", [&](TableHeader& h, auto&) { h.off_opsb = h.off_ops; }},
     {"external-coefficient vector index out of range", [&](TableHeader& h, auto& b) { *I(b, h.off_cden_xk, 0) = h.n_xk; }},
     {"external count inconsistent with the variables", [&](TableHeader& h, auto&) { h.n_ext = 2; }},
   };

@@ -23,4 +23,4 @@ def test_validator_refuses_corrupted_tables(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     print(r.stdout)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert r.stdout.count("refused") == 15
+    assert r.stdout.count("refused") == 17
