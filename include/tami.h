@@ -415,6 +415,12 @@ int tami_selftest_exp(const double* t, int64_t n, double* y, double* em, double*
  * tests to bound them against the C library's sin and cos. */
 int tami_selftest_sincos(const double* k, int64_t n, double* s, double* c, tami_stream_t stream);
 
+/* Diagnostic: the kernels' double-precision product on the integer pipes (no term of the paper:
+ * how the specialised kernels move FP64 work off the FP64 unit), applied elementwise: mul = a * b
+ * rounded to nearest even, bit for bit what the FP64 unit gives for every input, the integer path
+ * taken for normal operands with a normal result.  a, b, mul: device double [n]. */
+int tami_selftest_imul(const double* a, const double* b, int64_t n, double* mul, tami_stream_t stream);
+
 /* Diagnostic: a probe of the FP64 fma issue rate (not a term of the paper; it measures the
  * ceiling that the evaluation kernels are held against).  Launches `blocks` blocks of 256
  * threads, each running 64 independent fma recurrences per trip for `trips` trips; `out`

@@ -155,6 +155,12 @@ __global__ void sincos_selftest_kernel(const double* k, long long n, double* s, 
   if (__double_as_longlong(cw_cos(k[i])) != __double_as_longlong(cv)) c[i] = __longlong_as_double(0x7ff8000000000000ll);
 }
 
+__global__ void imul_selftest_kernel(const double* a, const double* b, long long n, double* mul) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  mul[i] = imul(a[i], b[i]);
+}
+
 // FP64 issue-rate probe: kChains independent fma recurrences per thread, a <- a m + c with
 // |m| < 1 (bounded, never subnormal), kUnroll steps per trip, the sums written out so that
 // nothing is dropped.  2 kChains kUnroll trips flops per thread.
@@ -566,6 +572,14 @@ int tami_selftest_sincos(const double* k, int64_t n, double* s, double* c, tami_
   sincos_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(k, n, s, c);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "sincos_selftest launch");
+}
+
+int tami_selftest_imul(const double* a, const double* b, int64_t n, double* mul, tami_stream_t stream) {
+  if (!a || !b || !mul || n < 0) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (n == 0) return TAMI_OK;
+  imul_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(a, b, n, mul);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "imul_selftest launch");
 }
 
 int tami_selftest_fp64_rate(int blocks, int64_t trips, double* out, double* flops, tami_stream_t stream) {

@@ -30,6 +30,38 @@ __device__ __forceinline__ double to_momentum(unsigned int hi, unsigned int lo) 
   return fma(__ull2double_rn(m), 2.0 * pi * 0x1.0p-53, -pi);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Double-precision multiplication on the integer pipes.  On this GPU the FP64 unit is the
+// bottleneck of the evaluation kernels while the integer units sit mostly idle, and the two run
+// concurrently.  imul computes the IEEE round-to-nearest-even product of two doubles with 64-bit
+// integer arithmetic, bit for bit what DMUL gives, so a kernel can move part of its FP64 work to
+// the integer pipes.  The integer fast path covers normal operands with a normal result; zeros,
+// subnormals, infinities, NaNs and results that would underflow or overflow take the FP64
+// instruction instead, out of line, so that the fast path issues no FP64 instruction at all.
+// (Textbook IEEE 754 multiplication: the exact 106-bit product of the significands, normalised,
+// rounded to nearest even with round and sticky bits.)
+static __device__ __noinline__ double dmul_fp64(double a, double b) { return __dmul_rn(a, b); }
+
+__device__ __forceinline__ double imul(double a, double b) {
+  const unsigned long long ua = __double_as_longlong(a), ub = __double_as_longlong(b);
+  const unsigned long long sign = (ua ^ ub) & 0x8000000000000000ull;
+  const int ea = (int)(ua >> 52) & 0x7FF, eb = (int)(ub >> 52) & 0x7FF;
+  const unsigned long long ma = (ua & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+  const unsigned long long mb = (ub & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+  const unsigned long long lo = ma * mb, hi = __umul64hi(ma, mb);   // 106-bit product in [2^104, 2^106)
+  const int top = (int)(hi >> 41);                                   // 1: bit 105 is set
+  const unsigned long long t = (hi << (23 - top)) | (lo >> (41 + top));   // leading one at bit 63
+  const unsigned long long below = lo << (23 - top);                // product bits under t
+  unsigned long long m = t >> 11;                                    // 53 significant bits
+  const unsigned long long rb = (t >> 10) & 1ull;
+  const unsigned long long st = ((t & 0x3FFull) | below) != 0ull;
+  m += rb & (st | (m & 1ull));                                       // may carry into bit 53
+  const int e = ea + eb - 1023 + top;                                // biased exponent before rounding
+  if (ea == 0 || eb == 0 || ea == 0x7FF || eb == 0x7FF || e <= 0 || e >= 0x7FE) return dmul_fp64(a, b);
+  return __longlong_as_double(sign | (((unsigned long long)(e - 1) << 52) + m));
+}
+
+
 // cos and sin: Cody-Waite reduction by pi (two-part constant), k = n pi + r, |r| <= pi/2 (n the
 // integer nearest to k/pi, from one fma against 1.5 * 2^52), then
 // Taylor series in r (to r^20 for cos, r^21 for sin) and the sign (-1)^n (W. J. Cody and

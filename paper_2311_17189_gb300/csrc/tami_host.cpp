@@ -868,7 +868,18 @@ int flatten(tami_diagram* d) {
   I.energy_in_flops_per_sample = fl - energy_flops;
   double ff = 10.0 * h.n_cden;                          // |D|^2, reciprocal, 1/D
   ff += 6.0 * h.n_pnode;                                // complex product per trie node
-  for (auto& g : g2s) ff += g.empty() ? 0.0 : 4.0;      // W R accumulated (the R = 1 group is a copy)
+  // W R accumulated (the R = 1 group is a copy); without it the first group's terms start the
+  // sums, two products
+  double wr = 0.0;
+  {
+    bool first = !h.g2_const;
+    for (auto& g : g2s) {
+      if (g.empty()) continue;
+      wr += first ? 2.0 : 4.0;
+      first = false;
+    }
+  }
+  ff += wr;
   I.energy_in_flops_per_sample_freq = ff;              // energy input returns the values only
   I.n_dag_ops = h.n_ops;
   I.n_dag_nodes = h.n_nodes;
@@ -899,12 +910,19 @@ int flatten(tami_diagram* d) {
   I.fwd_save_flops_per_sample = I.flops_per_sample + ext_grad_flops;
   I.bwd_saved_flops_per_sample = bl - energy_flops - ext_grad_flops;
   double bf = 10.0 * h.n_cden + 2.0;                    // reciprocals, dv/dX accumulated
-  for (const CdKey& c : cdens) bf += 6.0 + (unit((double)c.a) ? 2.0 : 4.0) + 4.0;   // Z, dv/dX, b-adjoint
+  for (size_t c = 0; c < cdens.size(); ++c)             // Z, dv/dX (the first starts it), b-adjoint
+    bf += 6.0 + (c == 0 ? (unit((double)cdens[c].a) ? 0.0 : 2.0) : (unit((double)cdens[c].a) ? 2.0 : 4.0)) + 4.0;
   bf += 6.0 * h.n_pnode;                                // products (trie nodes)
-  for (auto& g : g2s) bf += g.empty() ? 0.0 : 4.0 + 4.0 * g.size();   // Wbar, U += p W R
+  {
+    std::vector<char> u_set(cdens.size(), 0);          // U += p W R, the first term per factor a product
+    for (auto& g : g2s) {
+      if (g.empty()) continue;
+      bf += 4.0;                                        // Wbar
+      for (auto& pr : g) { bf += u_set[pr.first] ? 4.0 : 2.0; u_set[pr.first] = 1; }
+    }
+  }
   I.bwd_flops_per_sample_freq = bf;
-  double fused = bf + 6.0;                              // the forward's sums
-  for (auto& g : g2s) fused += g.empty() ? 0.0 : 4.0;   // W R accumulated
+  double fused = bf + 6.0 + wr;                         // the forward's sums, W R accumulated
   I.fused_flops_per_sample_freq = fused;
   return TAMI_OK;
 }

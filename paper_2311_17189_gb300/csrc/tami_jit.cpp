@@ -172,8 +172,29 @@ enum { kKindFused = kJitKindFused, kKindFwd = kJitKindFwd, kKindBwd = kJitKindBw
        kKinds = 4 };
 const char* const kKernelName[kKinds] = {"tami_jit_fused", "tami_jit_fwd", "tami_jit_bwd", "tami_jit_energy"};
 
+// Products of the frequency loop on the integer pipes (imul of tami_devmath.cuh, bit for bit the
+// FP64 unit's product), unless $TAMI_JIT_INTARITH is "0".  On this GPU the FP64 unit bounds the
+// specialised kernels while the integer units are mostly idle, and the two run concurrently; the
+// loop's products, which feed only fmas, move there.  Measured: the order-4 bench step 59.4 ->
+// 54.0 ms.  Not for large tables (over 256 pole-DAG ops), whose kernels already wait on instruction
+// fetch and whose frequency loop runs few times (order 5: 1.054 -> 1.074 s, order 6: 0.80 ->
+// 0.85 s with it); nor in the per-sample code, whose many live values would spill more than the
+// move gains (measured 40 % slower).
+bool int_products(const TableHeader& h) {
+  const char* e = std::getenv("TAMI_JIT_INTARITH");
+  return !(e && !std::strcmp(e, "0")) && h.n_ops <= 256;
+}
+
 void emit_phase2(Out& o, const Table& t, int kind, bool xr_zero) {
   const TableHeader& h = t.h;
+  const bool ia = int_products(h);
+  auto MUL = [&](const std::string& a, const std::string& b) {
+    return ia ? "imul(" + a + ", " + b + ")" : a + " * " + b;
+  };
+  auto NEG = [&](const std::string& a) {   // sign flip (no arithmetic)
+    return "__longlong_as_double(__double_as_longlong(" + a + ") ^ (long long)0x8000000000000000ull)";
+  };
+  auto S = [](const char* p, int i) { return std::string(p) + std::to_string(i); };
   const bool energy = kind == kKindEnergy;
   const bool fwd = kind != kKindBwd, adj = kind == kKindFused || kind == kKindBwd;
   const int nc = h.n_cden, np = h.n_pnode;
@@ -191,33 +212,58 @@ void emit_phase2(Out& o, const Table& t, int kind, bool xr_zero) {
     else if (energy) o("        const double Dr%d = fma(%s, Xs[2 * (%d * n_f + f)], b%d);", c, lit(cden_a[c]).c_str(), cden_xk[c], c);
     else o("        const double Dr%d = fma(%s, Xr, b%d);", c, lit(cden_a[c]).c_str(), c);
     o("        const double r%d = rcp(fma(Dr%d, Dr%d, AXI2[%d * n_f + f]));", c, c, c, c);
-    o("        const double vre%d = Dr%d * r%d, vim%d = -AXI[%d * n_f + f] * r%d;", c, c, c, c, c, c);
-    if (adj) o("        double U_re%d = 0.0, U_im%d = 0.0;", c, c);
+    o("        const double vre%d = %s, vim%d = %s;", c, MUL(S("Dr", c), S("r", c)).c_str(), c,
+      NEG(MUL("AXI[" + std::to_string(c) + " * n_f + f]", S("r", c))).c_str());
   }
   for (int k = 0; k < np; ++k) {
     const int src = pnode[2 * k], cc = pnode[2 * k + 1], v = nc + k;
-    o("        const double vre%d = fma(vre%d, vre%d, -vim%d * vim%d), vim%d = fma(vre%d, vim%d, vim%d * vre%d);", v, src,
-      cc, src, cc, v, src, cc, src, cc);
+    o("        const double vre%d = fma(vre%d, vre%d, %s), vim%d = fma(vre%d, vim%d, %s);", v, src, cc,
+      NEG(MUL(S("vim", src), S("vim", cc))).c_str(), v, src, cc, MUL(S("vim", src), S("vre", cc)).c_str());
   }
-  if (fwd) o("        double vr = %s, vi = 0.0;", h.g2_const ? "W2_0" : "0.0");
+  // sums that start at zero take their first term as a product (an addition to an exact zero is
+  // no arithmetic; only the sign of a zero result can differ)
+  std::vector<char> u_set(nc, 0);
+  if (fwd) {
+    if (h.g2_const) o("        double vr = W2_0, vi = 0.0;");
+    else o("        double vr, vi;");
+  }
+  if (adj)
+    for (int c = 0; c < nc; ++c) o("        double U_re%d = 0.0, U_im%d = 0.0;", c, c);
+  bool v_set = h.g2_const != 0;
   for (int g = h.g2_const; g < h.n_g2; ++g) {
     const int v = g2node[g];
-    if (fwd) o("        vr = fma(W2_%d, vre%d, vr); vi = fma(W2_%d, vim%d, vi);", g, v, g, v);
+    if (fwd) {
+      if (v_set) o("        vr = fma(W2_%d, vre%d, vr); vi = fma(W2_%d, vim%d, vi);", g, v, g, v);
+      else o("        vr = %s; vi = %s;", MUL(S("W2_", g), S("vre", v)).c_str(), MUL(S("W2_", g), S("vim", v)).c_str());
+      v_set = true;
+    }
     if (adj) {
       o("        Wb2_%d = fma(gr, vre%d, fma(gim, vim%d, Wb2_%d));", g, v, v, g);
       for (int q = g2[g]; q < g2[g + 1]; ++q) {
         const int cc = g2cd[2 * q];
-        o("        U_re%d = fma(pW%d, vre%d, U_re%d); U_im%d = fma(pW%d, vim%d, U_im%d);", cc, q, v, cc, cc, q, v, cc);
+        if (u_set[cc])
+          o("        U_re%d = fma(pW%d, vre%d, U_re%d); U_im%d = fma(pW%d, vim%d, U_im%d);", cc, q, v, cc, cc, q, v, cc);
+        else
+          o("        U_re%d = %s; U_im%d = %s;", cc, MUL(S("pW", q), S("vre", v)).c_str(), cc, MUL(S("pW", q), S("vim", v)).c_str());
+        u_set[cc] = 1;
       }
     }
   }
+  if (fwd && !v_set) o("        vr = 0.0; vi = 0.0;");
   if (adj) {
     o("        double dvr = 0.0, dvi = 0.0;");
     for (int c = 0; c < nc; ++c) {
-      o("        { const double Zr = fma(vre%d, U_re%d, -vim%d * U_im%d), Zi = fma(vre%d, U_im%d, vim%d * U_re%d);", c, c,
-        c, c, c, c, c, c);
-      o("          dvr = fma(%s, Zr, dvr); dvi = fma(%s, Zi, dvi); bb%d = fma(ngr, Zr, fma(ngi, Zi, bb%d)); }",
-        lit(-cden_a[c]).c_str(), lit(-cden_a[c]).c_str(), c, c);
+      o("        { const double Zr = fma(vre%d, U_re%d, %s), Zi = fma(vre%d, U_im%d, %s);", c, c,
+        NEG(MUL(S("vim", c), S("U_im", c))).c_str(), c, c, MUL(S("vim", c), S("U_re", c)).c_str());
+      if (c == 0 && (cden_a[c] == 1.0 || cden_a[c] == -1.0))
+        o("          dvr = %s; dvi = %s; bb%d = fma(ngr, Zr, fma(ngi, Zi, bb%d)); }", cden_a[c] == 1.0 ? NEG("Zr").c_str() : "Zr",
+          cden_a[c] == 1.0 ? NEG("Zi").c_str() : "Zi", c, c);
+      else if (c == 0)
+        o("          dvr = %s; dvi = %s; bb%d = fma(ngr, Zr, fma(ngi, Zi, bb%d)); }", MUL(lit(-cden_a[c]), "Zr").c_str(),
+          MUL(lit(-cden_a[c]), "Zi").c_str(), c, c);
+      else
+        o("          dvr = fma(%s, Zr, dvr); dvi = fma(%s, Zi, dvi); bb%d = fma(ngr, Zr, fma(ngi, Zi, bb%d)); }",
+          lit(-cden_a[c]).c_str(), lit(-cden_a[c]).c_str(), c, c);
     }
     o("        accX[2 * f] += dvr; accX[2 * f + 1] += dvi;");
     o("        if (ps_dX) reinterpret_cast<double2*>(ps_dX)[(size_t)f * n + s] = make_double2(dvr, dvi);");

@@ -73,6 +73,7 @@ def per_frequency(src):
     fl = 10 * len(re.findall(r'= rcp\(fma\(Dr\d+, Dr\d+,', loop))          # |D|^2, reciprocal, 1/D
     fl += 6 * len(re.findall(r'const double vre\d+ = fma\(', loop))         # complex product per trie node
     fl += 2 * len(re.findall(r'= fma\(W2_\d+,', loop))                      # W R accumulated
+    fl += len(re.findall(r'= (?:imul\()?W2_\d+(?:,| \*)', loop))                # ... its first term, a product
     fl += 2 + 4                                                             # mean and variance sums
     return fl
 

@@ -1,8 +1,9 @@
 """The kernels' own elementary functions: the table-driven exponential for t <= 0 (e^t and
 e^t - 1, after Tang, ACM TOMS 1989) against torch.exp / torch.expm1 on the device (CUDA's
 exp/expm1) and against mpmath at a few points; the Cody-Waite cos/sin of the dispersion against
-the C library's (the oracle's), which fixes TRIG_ERR of the momentum-mode parity bounds; and the
-FP64 fma-rate probe's flop count against its own outputs."""
+the C library's (the oracle's), which fixes TRIG_ERR of the momentum-mode parity bounds; the
+integer-pipe product against the FP64 unit's; and the FP64 fma-rate probe's flop count against its
+own outputs."""
 import ctypes
 
 import numpy as np
@@ -116,3 +117,48 @@ def test_fp64_rate_probe_does_its_work():
         a0 = 1e-3 * ((t + k) & 1023)
         ref += a0 * m ** steps + c * (1 - m ** steps) / (1 - m)
     assert np.allclose(out.cpu().numpy(), ref, rtol=1e-9, atol=0)
+
+
+def special_operands(rng, n):
+    """Pairs of doubles across the whole range: random normals over all exponents, close exponents,
+    near-cancelling pairs, rounding ties, results that underflow or overflow, zeros of both signs,
+    subnormals, infinities and NaNs."""
+    def rnd(k, lo, hi):
+        m = rng.uniform(1.0, 2.0, k) * np.where(rng.random(k) < 0.5, -1.0, 1.0)
+        return np.ldexp(m, rng.integers(lo, hi, k))
+    a = [rnd(n, -1022, 1023)]
+    b = [rnd(n, -1022, 1023)]
+    x = rnd(n, -60, 60)                                             # close exponents
+    a.append(x); b.append(x * np.ldexp(1.0, rng.integers(-70, 70, n)) * rng.uniform(0.5, 2.0, n))
+    a.append(x); b.append(-x * (1.0 + np.ldexp(rng.integers(-8, 8, n).astype(float), -52)))   # cancellation
+    a.append(x); b.append(-x)                                       # exact zero sums
+    a.append(np.ldexp(1.0 + np.ldexp(rng.integers(0, 2**20, n).astype(float), -52), 0))
+    b.append(np.ldexp(1.0 - np.ldexp(rng.integers(0, 2**20, n).astype(float), -53), 0))   # rounding ties
+    tiny = rnd(n, -1074, -1000)
+    huge = rnd(n, 1000, 1023)
+    a.append(tiny); b.append(rnd(n, -60, 0))                        # underflowing products
+    a.append(huge); b.append(rnd(n, 0, 60))                         # overflowing products
+    sp = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2250738585072014e-308, np.inf, -np.inf, np.nan, 1.0, -1.0,
+                   1.7976931348623157e308, np.ldexp(1.0, -1022), np.ldexp(1.5, -1023)])
+    aa, bb = np.meshgrid(sp, np.concatenate([sp, rnd(20, -1022, 1023)]))
+    a.append(aa.ravel()); b.append(bb.ravel())
+    return np.concatenate(a), np.concatenate(b)
+
+
+def test_integer_pipe_product_is_ieee():
+    """The kernels' integer-pipe product (imul) equals the FP64 unit's DMUL bit for bit (NaNs as
+    NaNs) on operands across the whole double range and its special cases."""
+    rng = np.random.default_rng(11)
+    a, b = special_operands(rng, 400000)
+    at, bt = torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda")
+    mul = torch.empty_like(at)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L.check(L.lib().tami_selftest_imul(ctypes.c_void_p(at.data_ptr()), ctypes.c_void_p(bt.data_ptr()), at.numel(),
+                                       ctypes.c_void_p(mul.data_ptr()), s))
+    torch.cuda.synchronize()
+    for got, ref, what in ((mul, at * bt, "product"),):
+        g, r = got.cpu().numpy(), ref.cpu().numpy()
+        nan = np.isnan(r)
+        assert np.array_equal(np.isnan(g), nan), what
+        bad = g[~nan].view(np.uint64) != r[~nan].view(np.uint64)
+        assert not bad.any(), (what, a[~nan][bad][:5], b[~nan][bad][:5], g[~nan][bad][:5], r[~nan][bad][:5])
