@@ -210,6 +210,11 @@ struct tami_batch {
   Layout L{};
   unsigned char* mem = nullptr;
   cudaStream_t cap = nullptr;
+  // the specialised launches go to parallel branches of the graph (forked from and joined back to
+  // cap), so that one launch's blocks fill the SMs another launch's tail leaves idle
+  static constexpr int kBranches = 4;
+  cudaStream_t br[kBranches] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kBranches] = {};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   double tuned_ms = -1.0;
@@ -225,6 +230,19 @@ void release_graph(tami_batch* b) {
   b->exec = nullptr;
   b->graph = nullptr;
   b->mem = nullptr;
+}
+
+void release_streams(tami_batch* b) {
+  for (int i = 0; i < tami_batch::kBranches; ++i) {
+    if (b->br[i]) cudaStreamDestroy(b->br[i]);
+    if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+    b->br[i] = nullptr;
+    b->ev_join[i] = nullptr;
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  b->ev_fork = nullptr;
+  b->cap = nullptr;
 }
 
 // Build items, device buffers and the graph for one (chunk, grid) choice; with_spec = false
@@ -341,16 +359,27 @@ int build(tami_batch* b, int chunk, int grid_cap, bool with_spec) {
   e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
   cudaMemsetAsync(b->mem + L.ctr, 0, 2 * sizeof(int), b->cap);
+  int n_br = 0;
+  for (int d = 0; d < n_d; ++d) if (spec_row[d] >= 0) ++n_br;
+  if (n_br > tami_batch::kBranches) n_br = tami_batch::kBranches;
+  if (n_br > 0) {
+    cudaEventRecord(b->ev_fork, b->cap);
+    for (int i = 0; i < n_br; ++i) cudaStreamWaitEvent(b->br[i], b->ev_fork, 0);
+  }
   if (n_items > 0) {
     if (b->ring_chunk) batch_kernel<true><<<grid, kBlock, b->smem, b->cap>>>(P);
     else batch_kernel<false><<<grid, kBlock, b->smem, b->cap>>>(P);
   }
   int rc = TAMI_OK;
-  for (int d = 0; d < n_d && rc == TAMI_OK; ++d)
+  for (int d = 0, k = 0; d < n_d && rc == TAMI_OK; ++d)
     if (spec_row[d] >= 0)
       rc = jit_launch_at(b->jit[d], b->jit_grid[d], nullptr, P.params, b->seeds[d], 0, b->n[d], P.X, n_f, 0.0,
                          nullptr, nullptr, nullptr, nullptr, nullptr, P.partial + (size_t)spec_row[d] * n_f * 4,
-                         b->cap);
+                         b->br[k++ % n_br]);
+  for (int i = 0; i < n_br; ++i) {
+    cudaEventRecord(b->ev_join[i], b->br[i]);
+    cudaStreamWaitEvent(b->cap, b->ev_join[i], 0);
+  }
   const int nt = n_d * n_f;
   batch_reduce_kernel<<<(nt + 127) / 128, 128, 0, b->cap>>>(
       P.partial, reinterpret_cast<const int*>(b->mem + L.item_ptr), reinterpret_cast<const int*>(b->mem + L.item_list),
@@ -524,6 +553,12 @@ int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* sampl
   }
   e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaStreamCreate"); }
+  for (int i = 0; i < tami_batch::kBranches && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->br[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) { release_streams(b); delete b; return cuda_fail(e, "cudaStreamCreate"); }
   int rc = TAMI_OK;
   if (chunk_tiles > 0) {
     rc = build(b, chunk_tiles, 0, true);
@@ -547,15 +582,27 @@ int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* sampl
         if (std::find(cands.begin(), cands.end(), ch) == cands.end()) cands.push_back(ch);
       }
       double best = 1e300;
-      int best_c = cands[0];
+      int best_c = cands[0], best_g = 0;
       for (int ch : cands) {
         rc = build(b, ch, 0, false);
         if (rc) break;
         double ms = time_replays(b, 2);
         if (ms < best) { best = ms; best_c = ch; }
       }
+      // then the residency at that work-item size: 1, 2, 4 ... blocks per SM up to the resident
+      // maximum the full grid has (fewer resident blocks: more shared memory and L1 per block)
+      if (!rc) rc = build(b, best_c, 0, false);
       if (!rc) {
-        rc = build(b, best_c, 0, true);
+        const int full = b->grid;
+        for (int per = 1; per * dp.sms < full && !rc; per *= 2) {
+          rc = build(b, best_c, per * dp.sms, false);
+          if (rc) break;
+          double ms = time_replays(b, 2);
+          if (ms < best) { best = ms; best_g = per * dp.sms; }
+        }
+      }
+      if (!rc) {
+        rc = build(b, best_c, best_g, true);
         b->tuned_ms = best;
         if (!rc) tune_store(key, b->chunk, b->grid);
       }
@@ -563,7 +610,7 @@ int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* sampl
   }
   if (rc) {
     release_graph(b);
-    cudaStreamDestroy(b->cap);
+    release_streams(b);
     delete b;
     return rc;
   }
@@ -635,7 +682,7 @@ void tami_batch_destroy(tami_batch* b) {
   cudaGetDevice(&prev);
   cudaSetDevice(b->device);
   release_graph(b);
-  if (b->cap) cudaStreamDestroy(b->cap);
+  release_streams(b);
   if (prev >= 0) cudaSetDevice(prev);
   delete b;
 }

@@ -438,8 +438,16 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   o("    const double kx%d = lkx, ky%d = lky; (void)kx%d; (void)ky%d;", h.m, h.m, h.m, h.m);
   for (int r = 0; r < h.n_rep; ++r) {
     const int j = repl[r];
-    o("    double ax%d = 0.0, ay%d = 0.0;", r, r);
-    for (int q = lm_ptr[r]; q < lm_ptr[r + 1]; ++q)
+    // a sum that starts with a +-1 label starts as that momentum (no addition to an exact zero)
+    int q0 = lm_ptr[r];
+    if (q0 < lm_ptr[r + 1] && (lm_c[q0] == 1.0 || lm_c[q0] == -1.0)) {
+      const char* sg = lm_c[q0] > 0 ? "" : "-";
+      o("    double ax%d = %skx%d, ay%d = %sky%d;", r, sg, lm_l[q0], r, sg, lm_l[q0]);
+      ++q0;
+    } else {
+      o("    double ax%d = 0.0, ay%d = 0.0;", r, r);
+    }
+    for (int q = q0; q < lm_ptr[r + 1]; ++q)
       o("    ax%d = fma(%s, kx%d, ax%d); ay%d = fma(%s, ky%d, ay%d);", r, lit(lm_c[q]).c_str(), lm_l[q], r, r,
         lit(lm_c[q]).c_str(), lm_l[q], r);
     if (r < h.n_rep_ext && adj) {
@@ -461,8 +469,14 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   o("    }");
   // ---- energy combinations
   for (int u = 0; u < h.n_combo; ++u) {
-    o("    double x%d = 0.0;", u);
-    for (int q = combo_ptr[u]; q < combo_ptr[u + 1]; ++q)
+    int q0 = combo_ptr[u];
+    if (q0 < combo_ptr[u + 1] && (combo_c[q0] == 1.0 || combo_c[q0] == -1.0)) {
+      o("    double x%d = %sE%d;", u, combo_c[q0] > 0 ? "" : "-", combo_j[q0]);
+      ++q0;
+    } else {
+      o("    double x%d = 0.0;", u);
+    }
+    for (int q = q0; q < combo_ptr[u + 1]; ++q)
       o("    x%d = fma(%s, E%d, x%d);", u, lit(combo_c[q]).c_str(), combo_j[q], u);
   }
   // ---- Fermi/Bose values (and, for the adjoint, their next derivatives), segment by segment
@@ -507,7 +521,10 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       const DagPrefix& q = dp.p[k];
       const std::string opnd = q.node ? "pv" + std::to_string(q.operand) : lit(leafA[q.operand]);
       const std::string add = q.parent < 0 ? "0.0" : "pv" + std::to_string(q.parent);
-      o("    const double pv%d = fma(fv%d, %s, %s);", k, q.fv, opnd.c_str(), add.c_str());
+      if (q.parent < 0 && !q.node && (leafA[q.operand] == 1.0 || leafA[q.operand] == -1.0))
+        o("    const double pv%d = %sfv%d;", k, leafA[q.operand] > 0 ? "" : "-", q.fv);   // +-F, no arithmetic
+      else
+        o("    const double pv%d = fma(fv%d, %s, %s);", k, q.fv, opnd.c_str(), add.c_str());
     }
     o("    double W1_%d = pv%d;", gi, dp.node_value[g1_node[gi]]);
     for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q)

@@ -23,10 +23,16 @@ def step(first, coef):
     return (0 if unit else 1) if first else (1 if unit else 2)
 
 
-def chains(body, pattern):
-    """Flops of the fma chains `dst = fma(coef, var, dst)` (first step onto 0.0), each distinct
-    prefix once; pattern groups: dst, coef, var."""
+def chains(body, pattern, start=None):
+    """Flops of the fma chains `dst = fma(coef, var, dst)` (first step onto 0.0, or the chain
+    started by `start`, a copy of +-var with no arithmetic), each distinct prefix once; pattern
+    groups: dst, coef, var; start groups: dst, sign, var."""
     seen, cur, fl = {}, {}, 0
+    if start:
+        for m in re.finditer(start, body):
+            pref = ((m.group(3), "-0x1p+0" if m.group(2) else "0x1p+0"),)
+            seen[pref] = True
+            cur[m.group(1)] = pref
     for m in re.finditer(pattern, body):
         dst, coef, var = m.group(1), m.group(2).strip(), m.group(3)
         first = dst not in cur
@@ -42,6 +48,9 @@ def dag(body):
     """Pole-DAG prefixes: const double pv<k> = fma(fv<y>, OPERAND, 0.0 | pv<parent>), an operand
     being a leaf coefficient or another prefix (a node's value); each written once."""
     fl, seen = 0, set()
+    for m in re.finditer(r'const double pv(\d+) = (-?)fv(\d+);', body):   # +-F: a unit leaf, no arithmetic
+        assert m.group(1) not in seen
+        seen.add(m.group(1))
     for m in re.finditer(r'const double pv(\d+) = fma\(fv(\d+), ([^,]+), ([^)]+)\);', body):
         k, opnd, add = m.group(1), m.group(3).strip(), m.group(4).strip()
         assert k not in seen
@@ -53,9 +62,10 @@ def dag(body):
 def per_sample(src):
     body = src[src.index("for (long long tile"):src.index("if (xr_zero) {")]
     fl = 2 * body.count("to_momentum(")
-    fl += 2 * chains(body, r'ax(\d+) = fma\(([^,]+), kx(\d+), ax\d+\);')     # both components
+    fl += 2 * chains(body, r'ax(\d+) = fma\(([^,]+), kx(\d+), ax\d+\);',     # both components
+                     r'double ax(\d+) = (-?)kx(\d+),')
     fl += 66 * len(re.findall(r'\bline_energy\(', body))                  # (the saved-rows branch aside)
-    fl += chains(body, r'\bx(\d+) = fma\(([^,]+), E(\d+), x\d+\);')
+    fl += chains(body, r'\bx(\d+) = fma\(([^,]+), E(\d+), x\d+\);', r'double x(\d+) = (-?)E(\d+);')
     bose = body.count("exp_neg<true>") + body.count("tami_seg_bose(")       # inline, or the out-of-line copy
     fermi = body.count("exp_neg<false>") + body.count("tami_seg_fermi(")     # that large tables call
     fl += (1 + 25 + 6 + 1) * bose                                           # -beta|x|, e^t and e^t - 1, 1/D, y/D

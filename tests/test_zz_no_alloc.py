@@ -78,8 +78,14 @@ def test_noalloc_smaller_call_after_larger_one(setup):
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(setup):
+    """A request whose scratch (the same size tami_forward would need, tami_forward_workspace) is
+    above the fixed 4 MiB array is refused with TAMI_EINVAL and nothing launched."""
     c, D = setup
-    X = W.real_axis(-4.0, 4.0, 256, 0.05)
-    rc, _, _ = call_noalloc(D, c, 1 << 20, X)
+    X = W.real_axis(-4.0, 4.0, 2048, 0.05)
+    n = 1 << 20
+    need = ctypes.c_size_t()
+    L.check(L.lib().tami_forward_workspace(D._h, n, len(X), ctypes.byref(need)))
+    assert need.value > 4 << 20
+    rc, _, _ = call_noalloc(D, c, n, X)
     assert rc == L.TAMI_EINVAL
     assert "scratch" in L.lib().tami_last_error().decode()
