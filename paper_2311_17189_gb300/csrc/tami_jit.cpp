@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <regex>
 #include <functional>
 #include <atomic>
 #include <memory>
@@ -180,6 +181,20 @@ const char* const kKernelName[kKinds] = {"tami_jit_fused", "tami_jit_fwd", "tami
 // fetch and whose frequency loop runs few times (order 5: 1.054 -> 1.074 s, order 6: 0.80 ->
 // 0.85 s with it); nor in the per-sample code, whose many live values would spill more than the
 // move gains (measured 40 % slower).
+// The adjoint kinds' frequency loop reads its per-sample inputs (the group weights W, the products
+// p W and the frequency-free parts b of the denominators) from shared memory, [value][thread],
+// through volatile loads that the compiler cannot hoist back into registers: the loop body then
+// fits more of its working values in the 64 registers and spills less (order-4 fused step 53.4 ->
+// 49.5 ms, order-3 real-axis workload 108.8 -> 90.9 ms; the plain forward, with fewer live values,
+// gains nothing; the running sums Wbar and b-adjoint there as well measured 0.3 % slower).  $TAMI_JIT_SMEMVALS=0 keeps
+// them in registers.  Tables whose loop inputs exceed 32 KB per block (static shared memory) keep
+// them in registers.
+bool smem_loop_values(const TableHeader& h, bool adj) {
+  const char* e = std::getenv("TAMI_JIT_SMEMVALS");
+  const size_t bytes = sizeof(double) * kJitBlock * (size_t)(h.n_g2 + h.n_g2cd + h.n_cden);
+  return adj && !(e && !std::strcmp(e, "0")) && bytes <= 32768;
+}
+
 bool int_products(const TableHeader& h) {
   const char* e = std::getenv("TAMI_JIT_INTARITH");
   return !(e && !std::strcmp(e, "0")) && h.n_ops <= 256;
@@ -407,6 +422,8 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   if (adj) o("    if (tid == 0) { double g = 0.0; for (int f = 0; f < n_f; ++f) g += Gs[2 * f]; s_gsum = g; }");
   o("    xr_zero = !__syncthreads_or(nonzero);");
   o("  }");
+  if (smem_loop_values(h, adj))
+    o("  __shared__ volatile double jsv[%d];", kJitBlock * (h.n_g2 + h.n_g2cd + h.n_cden));
   o("  const long long n_tiles = (n + %d) / %d;", kJitBlock - 1, kJitBlock);
   o("  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {");
   o("    const long long s = tile * %d + tid;", kJitBlock);
@@ -539,12 +556,42 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     }
     for (int c = 0; c < h.n_cden; ++c) o("    double bb%d = 0.0;", c);
   }
-  // ---- phase 2 over frequencies
+  // ---- phase 2 over frequencies (the adjoint kinds' loop inputs in shared memory, see
+  // smem_loop_values)
+  const bool sv = smem_loop_values(h, adj);
+  const int n_sv = h.n_g2 + h.n_g2cd + h.n_cden;
+  if (sv) {
+    for (int g = 0; g < h.n_g2; ++g) o("    jsv[%d * %d + tid] = W2_%d;", g, kJitBlock, g);
+    for (int q = 0; q < h.n_g2cd; ++q) o("    jsv[%d * %d + tid] = pW%d;", h.n_g2 + q, kJitBlock, q);
+    for (int c = 0; c < h.n_cden; ++c) o("    jsv[%d * %d + tid] = b%d;", n_sv - h.n_cden + c, kJitBlock, c);
+  }
+  const size_t loop0 = o.s.size();
   o("    if (xr_zero) {");
   emit_phase2(o, t, kind, true);
   o("    } else {");
   emit_phase2(o, t, kind, false);
   o("    }");
+  if (sv) {
+    std::string loop = o.s.substr(loop0);
+    auto rename = [&](const char* pat, int base) {
+      const std::regex re(pat);
+      std::string out;
+      std::sregex_iterator it(loop.begin(), loop.end(), re), end;
+      size_t last = 0;
+      for (; it != end; ++it) {
+        out += loop.substr(last, it->position() - last);
+        out += "jsv[" + std::to_string(base + std::stoi((*it)[1].str())) + " * " + std::to_string(kJitBlock) + " + tid]";
+        last = it->position() + it->length();
+      }
+      out += loop.substr(last);
+      loop.swap(out);
+    };
+    rename("\\bW2_(\\d+)\\b", 0);
+    rename("\\bpW(\\d+)\\b", h.n_g2);
+    rename("\\bb(\\d+)\\b", n_sv - h.n_cden);
+    o.s.resize(loop0);
+    o.s += loop;
+  }
   if (adj) {
     if (h.g2_const) o("    Wb2_0 = s_gsum;");
     // ---- reverse sweep
