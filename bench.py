@@ -53,15 +53,19 @@ METRIC = "order-4 Sigma evals/s (samples x terms x frequencies, FP64), forward +
 # caches the compilation (whose options are fixed in the library) -- must hash to the captured
 # one, else the bench reports traffic as null.
 TRAFFIC = {"kernel": "tami_jit_fused (the diagram's specialised fused forward + adjoint)",
-           "bytes_per_sample": (4.210279e9 + 5.372503e9) / 4194304,
-           "kernel_sha256": "945891538638211536dc4c7c24f35b3acc50fea902fde49a2160774f87c1c4e9",
+           "bytes_per_sample": (4.406293e9 + 5.582651e9) / 4194304,
+           "kernel_sha256": "8617a17629d7009001ae23aca37540d0868f35c09531efbe4cc1a02bcc287622",
            "profile": "profiles/jit_kernels_order4_sigma.md"}
 
 
+FP64_RATE_VARIANTS = 4   # operand patterns of tami_selftest_fp64_rate (TAMI_FP64_RATE_VARIANTS)
+
+
 def fp64_rate_measured(stream, target_s=0.25):
-    """FP64 fma rate of this GPU from libtami's probe (tami_selftest_fp64_rate: 64 independent
-    fma recurrences per thread per trip, 8 blocks of 256 threads per SM), timed with CUDA events
-    on `stream`: the best of three launches after one warm-up, in TFLOP/s."""
+    """FP64 fma rate of this GPU from libtami's probe (tami_selftest_fp64_rate: independent fma
+    recurrences, 8 blocks of 256 threads per SM), timed with CUDA events on `stream`: for each of
+    its operand patterns one warm-up and three launches of about `target_s`; the fastest launch
+    of all, in TFLOP/s (the FP64 unit's rate depends on the operands' register placement)."""
     import ctypes
     import torch
     from paper_2311_17189_gb300 import _lib as L
@@ -72,27 +76,35 @@ def fp64_rate_measured(stream, target_s=0.25):
     sp = ctypes.c_void_p(stream.cuda_stream)
     trips = 256
 
-    def launch(tr):
-        L.check(L.lib().tami_selftest_fp64_rate(blocks, tr, ctypes.c_void_p(out.data_ptr()), ctypes.byref(fl), sp))
+    def launch(v, tr):
+        L.check(L.lib().tami_selftest_fp64_rate(v, blocks, tr, ctypes.c_void_p(out.data_ptr()), ctypes.byref(fl), sp))
 
-    launch(trips)
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    launch(trips)
-    e1.record(stream)
-    e1.synchronize()
-    trips = max(1, int(trips * target_s / max(e0.elapsed_time(e1) * 1e-3, 1e-6)))
-    best = None
-    for _ in range(3):
+    best, best_v, best_s, rates = None, None, None, []
+    for v in range(FP64_RATE_VARIANTS):
+        tr = 256
+        launch(v, tr)
+        torch.cuda.synchronize()
         e0.record(stream)
-        launch(trips)
+        launch(v, tr)
         e1.record(stream)
         e1.synchronize()
-        rate = fl.value / (e0.elapsed_time(e1) * 1e-3) / 1e12
-        best = rate if best is None else max(best, rate)
-    return {"tflops": best, "launch_s": e0.elapsed_time(e1) * 1e-3, "blocks": blocks,
-            "probe": "tami_selftest_fp64_rate: 64 independent fma recurrences per thread per trip, best of 3"}
+        tr = max(1, int(tr * target_s / max(e0.elapsed_time(e1) * 1e-3, 1e-6)))
+        vbest = None
+        for _ in range(3):
+            e0.record(stream)
+            launch(v, tr)
+            e1.record(stream)
+            e1.synchronize()
+            rate = fl.value / (e0.elapsed_time(e1) * 1e-3) / 1e12
+            if vbest is None or rate > vbest:
+                vbest = rate
+            if best is None or rate > best:
+                best, best_v, best_s = rate, v, e0.elapsed_time(e1) * 1e-3
+        rates.append(round(vbest, 4))
+    return {"tflops": best, "launch_s": best_s, "blocks": blocks, "variant": best_v, "variants_tflops": rates,
+            "probe": "tami_selftest_fp64_rate: independent fma recurrences, the fastest of its operand patterns, "
+                     "best of 3 launches each"}
 
 
 def roofline_peak(measured):

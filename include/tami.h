@@ -423,10 +423,21 @@ int tami_selftest_imul(const double* a, const double* b, int64_t n, double* mul,
 
 /* Diagnostic: a probe of the FP64 fma issue rate (not a term of the paper; it measures the
  * ceiling that the evaluation kernels are held against).  Launches `blocks` blocks of 256
- * threads, each running 64 independent fma recurrences per trip for `trips` trips; `out`
- * (device double [blocks * 256]) receives the recurrences' sums, and `flops` (host, may be
- * NULL) the flops of the launch (2 per fma).  The caller times the launch on `stream`. */
-int tami_selftest_fp64_rate(int blocks, int64_t trips, double* out, double* flops, tami_stream_t stream);
+ * threads, each running independent fma recurrences, a_k <- m_k a_k + c_k (or the running sum
+ * a_k <- m_k c_k + a_k), for `trips` trips; `variant` in [0, TAMI_FP64_RATE_VARIANTS) picks the
+ * operand pattern, on which the FP64 unit's rate depends (register-file placement), so a caller
+ * measuring the ceiling takes the fastest:
+ *   0: 8 recurrences x 8 steps per trip, one multiplier and addend for all (m = 0.9999999,
+ *      c = 1e-3);
+ *   1: 4 x 8, recurrence k with its own m_k = m - 1e-9 k, c_k = c + 1e-9 k;
+ *   2: 4 x 16, the running sums a_k <- m_k c_k + a_k;
+ *   3: 3 x 16, as 1.
+ * Recurrence k of thread t starts at 1e-3 ((t + k) mod 1024).  `out` (device double
+ * [blocks * 256]) receives each thread's sum of its recurrences, and `flops` (host, may be NULL)
+ * the flops of the launch (2 per fma).  The caller times the launch on `stream`.  TAMI_EINVAL for a
+ * bad variant, blocks < 1, trips < 1 or a NULL `out`. */
+#define TAMI_FP64_RATE_VARIANTS 4
+int tami_selftest_fp64_rate(int variant, int blocks, int64_t trips, double* out, double* flops, tami_stream_t stream);
 
 void tami_destroy(tami_diagram* d);
 

@@ -116,7 +116,7 @@ def lib():
     L.tami_selftest_exp.argtypes = [dp, i64, dp, dp, dp, vp]
     L.tami_selftest_sincos.argtypes = [dp, i64, dp, dp, vp]
     L.tami_selftest_imul.argtypes = [dp, dp, i64, dp, vp]
-    L.tami_selftest_fp64_rate.argtypes = [ctypes.c_int, i64, dp, ctypes.POINTER(ctypes.c_double), vp]
+    L.tami_selftest_fp64_rate.argtypes = [ctypes.c_int, ctypes.c_int, i64, dp, ctypes.POINTER(ctypes.c_double), vp]
     L.tami_destroy.argtypes = [vp]
     L.tami_destroy.restype = None
     _lib = L

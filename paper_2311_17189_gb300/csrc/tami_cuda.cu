@@ -161,24 +161,33 @@ __global__ void imul_selftest_kernel(const double* a, const double* b, long long
   mul[i] = imul(a[i], b[i]);
 }
 
-// FP64 issue-rate probe: kChains independent fma recurrences per thread, a <- a m + c with
-// |m| < 1 (bounded, never subnormal), kUnroll steps per trip, the sums written out so that
-// nothing is dropped.  2 kChains kUnroll trips flops per thread.
-constexpr int kRateChains = 8, kRateUnroll = 8;
+// FP64 issue-rate probes: C independent fma recurrences per thread, U steps of each per trip, the
+// sums written out so that nothing is dropped; 2 C U trips flops per thread.  How fast the FP64
+// unit runs them depends on how the operands sit in the register file, so there are several
+// operand patterns and a caller takes the fastest:
+//   OWN = false: a_k <- a_k m + c, one multiplier and addend for every chain;
+//   OWN = true, ACC = false: a_k <- a_k m_k + c_k, each chain its own multiplier and addend;
+//   OWN = true, ACC = true: a_k <- m_k c_k + a_k, the chain in the addend (a running sum).
+// m_k = m - 1e-9 k, c_k = c + 1e-9 k, |m_k| < 1: bounded, never subnormal.
+template <int C, int U, bool OWN, bool ACC>
 __global__ void __launch_bounds__(256) fp64_rate_kernel(long long trips, double m, double c, double* out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  double a[kRateChains];
+  double a[C], mm[C], cc[C];
 #pragma unroll
-  for (int k = 0; k < kRateChains; ++k) a[k] = 1e-3 * (double)((t + k) & 1023);
+  for (int k = 0; k < C; ++k) {
+    a[k] = 1e-3 * (double)((t + k) & 1023);
+    mm[k] = OWN ? m - 1e-9 * k : m;
+    cc[k] = OWN ? c + 1e-9 * k : c;
+  }
   for (long long it = 0; it < trips; ++it) {
 #pragma unroll
-    for (int u = 0; u < kRateUnroll; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int k = 0; k < kRateChains; ++k) a[k] = fma(a[k], m, c);
+      for (int k = 0; k < C; ++k) a[k] = ACC ? fma(mm[k], cc[k], a[k]) : fma(a[k], OWN ? mm[k] : m, OWN ? cc[k] : c);
   }
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < kRateChains; ++k) s += a[k];
+  for (int k = 0; k < C; ++k) s += a[k];
   out[t] = s;
 }
 
@@ -582,13 +591,24 @@ int tami_selftest_imul(const double* a, const double* b, int64_t n, double* mul,
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "imul_selftest launch");
 }
 
-int tami_selftest_fp64_rate(int blocks, int64_t trips, double* out, double* flops, tami_stream_t stream) {
-  if (blocks < 1 || trips < 1 || !out) { set_error("bad argument"); return TAMI_EINVAL; }
-  // m, c passed at run time so that the recurrence cannot be folded
-  fp64_rate_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>((long long)trips, 0.9999999, 1e-3, out);
+int tami_selftest_fp64_rate(int variant, int blocks, int64_t trips, double* out, double* flops, tami_stream_t stream) {
+  if (variant < 0 || variant >= TAMI_FP64_RATE_VARIANTS || blocks < 1 || trips < 1 || !out) {
+    set_error("bad argument");
+    return TAMI_EINVAL;
+  }
+  // m, c passed at run time so that the recurrences cannot be folded
+  const cudaStream_t st = (cudaStream_t)stream;
+  const long long tr = (long long)trips;
+  int per_trip = 0;   // fmas per thread per trip
+  switch (variant) {
+    case 0: fp64_rate_kernel<8, 8, false, false><<<(unsigned)blocks, 256, 0, st>>>(tr, 0.9999999, 1e-3, out); per_trip = 64; break;
+    case 1: fp64_rate_kernel<4, 8, true, false><<<(unsigned)blocks, 256, 0, st>>>(tr, 0.9999999, 1e-3, out); per_trip = 32; break;
+    case 2: fp64_rate_kernel<4, 16, true, true><<<(unsigned)blocks, 256, 0, st>>>(tr, 0.9999999, 1e-3, out); per_trip = 64; break;
+    default: fp64_rate_kernel<3, 16, true, false><<<(unsigned)blocks, 256, 0, st>>>(tr, 0.9999999, 1e-3, out); per_trip = 48; break;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fp64_rate launch");
-  if (flops) *flops = 2.0 * kRateChains * kRateUnroll * (double)trips * 256.0 * (double)blocks;
+  if (flops) *flops = 2.0 * per_trip * (double)trips * 256.0 * (double)blocks;
   return TAMI_OK;
 }
 

@@ -168,6 +168,7 @@ int jit_launch(tami_diagram* d, int kind, const tami_lattice* lat, uint64_t seed
 struct JitHandle {
   std::shared_ptr<void> lib;
   void* fn = nullptr;
+  int block = 128;     // threads per block
   size_t smem = 0;
 };
 int jit_handle(tami_diagram* d, int kind, int n_f, JitHandle* h);

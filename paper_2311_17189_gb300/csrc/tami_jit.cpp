@@ -43,7 +43,7 @@ namespace tami {
 
 namespace {
 
-constexpr int kJitBlock = 128;          // threads per block, as the generic kernel (one sample each)
+constexpr int kJitBlock = 128;          // threads per block of the energy-input kind (one row each)
 constexpr int kJitMaxOps = 1 << 15;     // pole-DAG edges the generator writes out
 constexpr int kJitMaxFreq = 256;        // frequencies (the generic adjoint's limit)
 
@@ -187,12 +187,36 @@ const char* const kKernelName[kKinds] = {"tami_jit_fused", "tami_jit_fwd", "tami
 // fits more of its working values in the 64 registers and spills less (order-4 fused step 53.4 ->
 // 49.5 ms, order-3 real-axis workload 108.8 -> 90.9 ms; the plain forward, with fewer live values,
 // gains nothing; the running sums Wbar and b-adjoint there as well measured 0.3 % slower).  $TAMI_JIT_SMEMVALS=0 keeps
-// them in registers.  Tables whose loop inputs exceed 32 KB per block (static shared memory) keep
-// them in registers.
-bool smem_loop_values(const TableHeader& h, bool adj) {
+// them in registers.  The slots sit in dynamic shared memory after the reduction buffer; tables
+// with more than 24 such values per thread keep them in registers (24 x 8 B x 1024 threads of a
+// lockstep SM = 192 KB).
+int loop_value_count(const TableHeader& h) { return h.n_g2 + h.n_g2cd + h.n_cden; }
+bool smem_loop_values(const TableHeader& h, bool adj, int block) {
   const char* e = std::getenv("TAMI_JIT_SMEMVALS");
-  const size_t bytes = sizeof(double) * kJitBlock * (size_t)(h.n_g2 + h.n_g2cd + h.n_cden);
-  return adj && !(e && !std::strcmp(e, "0")) && bytes <= 32768;
+  (void)block;
+  return adj && !(e && !std::strcmp(e, "0")) && loop_value_count(h) <= 24;
+}
+
+// Threads per block of a specialised kernel.  The Monte Carlo kinds run in lockstep blocks: 512
+// threads ($TAMI_JIT_LOCKSTEP: 256, 512 or 1024), two blocks per SM, whose warps meet at a barrier
+// every $TAMI_JIT_SYNC_OPS pole-DAG steps (default 64) in the straight-line per-sample code, so
+// that the warps of an SM fetch the same stretch of code at a time instead of spreading over the
+// whole kernel.  A large table's kernel is far larger than the instruction caches: the order-6
+// table's fused step went from 790 to 677 ms (it had waited mostly on instruction fetch); the
+// order-4 step 49.7 -> 48.2 ms, order 3 on the real axis 91.1 -> 86.4 ms, order 5 1.029 ->
+// 1.020 s, against 128-thread blocks without barriers.  The energy-input kind (no reduction, short
+// code) keeps 128-thread blocks.
+int lockstep_block(const TableHeader& h, int kind) {
+  (void)h;
+  if (kind == kKindEnergy) return kJitBlock;
+  const char* e = std::getenv("TAMI_JIT_LOCKSTEP");
+  const int b = e ? std::atoi(e) : 512;
+  return (b == 256 || b == 1024) ? b : 512;
+}
+int lockstep_sync_ops() {
+  const char* e = std::getenv("TAMI_JIT_SYNC_OPS");
+  const int k = e ? std::atoi(e) : 64;
+  return k >= 4 ? k : 64;
 }
 
 bool int_products(const TableHeader& h) {
@@ -280,15 +304,19 @@ void emit_phase2(Out& o, const Table& t, int kind, bool xr_zero) {
         o("          dvr = fma(%s, Zr, dvr); dvi = fma(%s, Zi, dvi); bb%d = fma(ngr, Zr, fma(ngi, Zi, bb%d)); }",
           lit(-cden_a[c]).c_str(), lit(-cden_a[c]).c_str(), c, c);
     }
+    o("        if (act) {");   // a lane past the end adds and writes nothing
     o("        accX[2 * f] += dvr; accX[2 * f + 1] += dvi;");
     o("        if (ps_dX) reinterpret_cast<double2*>(ps_dX)[(size_t)f * n + s] = make_double2(dvr, dvi);");
+    o("        }");
   }
   if (energy) {
     o("        reinterpret_cast<double2*>(ps_v)[(size_t)f * n + s] = make_double2(vr, vi);");
   } else if (fwd) {
+    o("        if (act) {");
     o("        accV[4 * f] += vr; accV[4 * f + 1] += vi;");
     o("        accV[4 * f + 2] = fma(vr, vr, accV[4 * f + 2]); accV[4 * f + 3] = fma(vi, vi, accV[4 * f + 3]);");
     o("        if (ps_v) reinterpret_cast<double2*>(ps_v)[(size_t)f * n + s] = make_double2(vr, vi);");
+    o("        }");
   }
   o("      }");
 }
@@ -334,8 +362,15 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   const int* cden_xk = t.I(h.off_cden_xk);
   const double* xvec = t.D(h.off_xvec);
   const char* nval = kind == kKindFused ? "6 * n_f + 3" : kind == kKindBwd ? "2 * n_f + 3" : "4 * n_f";
+  const int B = lockstep_block(h, kind);
+  const bool ls = B != kJitBlock;
+  const int sync_ops = lockstep_sync_ops();
 
   Out o;
+  int since_sync = 0;
+  auto step_sync = [&]() {   // lockstep blocks: a barrier every sync_ops pole-DAG steps
+    if (ls && ++since_sync >= sync_ops) { o("    __syncthreads();"); since_sync = 0; }
+  };
   o("// generated by libtami for one flattened term table, one sample per thread: %s",
     kind == kKindFused ? "forward + adjoint" : kind == kKindFwd ? "forward" : kind == kKindBwd ? "adjoint" : "energy input");
   o("#include \"tami_devmath.cuh\"");
@@ -367,8 +402,8 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       o("}");
     }
   }
-  o("extern \"C\" __global__ void __launch_bounds__(%d, 8) %s(double lt, double ltp, double lmu, double lkx, double lky,",
-    kJitBlock, kKernelName[kind]);
+  o("extern \"C\" __global__ void __launch_bounds__(%d, %d) %s(double lt, double ltp, double lmu, double lkx, double lky,",
+    B, 1024 / B, kKernelName[kind]);
   o("    unsigned long long seed, unsigned long long offset, long long n, const double* X, const double* G, int n_f,");
   o("    double beta, double* ps_dX, double* ps_grad, double* ps_v, double* saved, double* partial, const double* P) {");
   o("  extern __shared__ __align__(16) double smem[];");
@@ -381,9 +416,9 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     o("  (void)AXI; (void)AXI2; (void)G; (void)ps_dX; (void)ps_grad; (void)partial; (void)seed; (void)offset;");
     o("  (void)lt; (void)ltp; (void)lmu; (void)lkx; (void)lky;");
     if (h.n_ext == 1) {
-      o("  for (int i = tid; i < 2 * n_f; i += %d) Xs[i] = X[i];", kJitBlock);
+      o("  for (int i = tid; i < 2 * n_f; i += %d) Xs[i] = X[i];", B);
     } else {
-      o("  for (int i = tid; i < %d * n_f; i += %d) {", h.n_xk, kJitBlock);
+      o("  for (int i = tid; i < %d * n_f; i += %d) {", h.n_xk, B);
       o("    const int k = i / n_f, f = i %% n_f;");
       o("    const double* v = kJitXvec + k * %d; const double* x = X + 2 * (size_t)f * %d;", h.n_ext, h.n_ext);
       o("    double re = v[0] * x[0], im = v[0] * x[1];");
@@ -394,8 +429,9 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   } else {
     o("  double* Xs = smem; double* Gs = Xs + 2 * n_f; double* AXI = Gs + 2 * n_f; double* AXI2 = AXI + %d * n_f;", h.n_cden);
     o("  double* red = AXI2 + %d * n_f;", h.n_cden);
+    if (smem_loop_values(h, adj, B)) o("  volatile double* jsv = red + %d;", B);   // after the [warp][32] buffer
     o("  (void)AXI; (void)AXI2; (void)G; (void)ps_dX; (void)ps_grad; (void)ps_v; (void)saved;");
-    o("  for (int i = tid; i < 2 * n_f; i += %d) { Xs[i] = X[i]; Gs[i] = %s; }", kJitBlock, adj ? "G[i]" : "0.0");
+    o("  for (int i = tid; i < 2 * n_f; i += %d) { Xs[i] = X[i]; Gs[i] = %s; }", B, adj ? "G[i]" : "0.0");
   }
   if (adj) {
     o("  double accX[%d];", 2 * kJitMaxFreq);
@@ -412,22 +448,28 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   o("  {");
   o("    int nonzero = 0;");
   if (h.n_cden > 0) {
-    o("    for (int i = tid; i < %d * n_f; i += %d) {", h.n_cden, kJitBlock);
+    o("    for (int i = tid; i < %d * n_f; i += %d) {", h.n_cden, B);
     if (energy) o("      const double a = kJitCdenA[i / n_f] * Xs[2 * (kJitCdenXk[i / n_f] * n_f + i %% n_f) + 1];");
     else o("      const double a = kJitCdenA[i / n_f] * Xs[2 * (i %% n_f) + 1];");
     o("      AXI[i] = a; AXI2[i] = a * a;");
     o("    }");
   }
-  o("    for (int i = tid; i < %d * n_f; i += %d) nonzero |= Xs[2 * i] != 0.0;", energy ? h.n_xk : 1, kJitBlock);
+  o("    for (int i = tid; i < %d * n_f; i += %d) nonzero |= Xs[2 * i] != 0.0;", energy ? h.n_xk : 1, B);
   if (adj) o("    if (tid == 0) { double g = 0.0; for (int f = 0; f < n_f; ++f) g += Gs[2 * f]; s_gsum = g; }");
   o("    xr_zero = !__syncthreads_or(nonzero);");
   o("  }");
-  if (smem_loop_values(h, adj))
-    o("  __shared__ volatile double jsv[%d];", kJitBlock * (h.n_g2 + h.n_g2cd + h.n_cden));
-  o("  const long long n_tiles = (n + %d) / %d;", kJitBlock - 1, kJitBlock);
+  o("  const long long n_tiles = (n + %d) / %d;", B - 1, B);
   o("  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {");
-  o("    const long long s = tile * %d + tid;", kJitBlock);
-  o("    if (s >= n) continue;");
+  if (ls) {
+    // every thread reaches every barrier: a lane past the end runs the last sample again and
+    // neither adds nor writes
+    o("    const long long s0 = tile * %d + tid;", B);
+    o("    const bool act = s0 < n;");
+    o("    const long long s = act ? s0 : n - 1;");
+  } else {
+    o("    const long long s = tile * %d + tid;", B);
+    o("    if (s >= n) continue;");
+  }
   // ---- line energies: from the momenta, or (adjoint) from the forward's saved rows
   for (int r = 0; r < h.n_rep; ++r) o("    double E%d;", repl[r]);
   if (adj) for (int r = 0; r < h.n_rep_ext; ++r) o("    double Gx%d, Gy%d;", r, r);
@@ -471,14 +513,15 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       o("    E%d = line_energy_grad(ax%d, ay%d, lt, ltp, lmu, Gx%d, Gy%d);", j, r, r, r, r);
     } else if (r < h.n_rep_ext) {   // forward: the dE/dK factors only when the rows are saved (same E bits)
       o("    if (saved) { double gx, gy; E%d = line_energy_grad(ax%d, ay%d, lt, ltp, lmu, gx, gy);", j, r, r);
-      o("      saved[(size_t)%d * n + s] = gx; saved[(size_t)%d * n + s] = gy; }", h.n_rep + 2 * r, h.n_rep + 2 * r + 1);
+      o("      if (act) { saved[(size_t)%d * n + s] = gx; saved[(size_t)%d * n + s] = gy; } }", h.n_rep + 2 * r,
+        h.n_rep + 2 * r + 1);
       o("    else E%d = line_energy(ax%d, ay%d, lt, ltp, lmu);", j, r, r);
     } else {
       o("    E%d = line_energy(ax%d, ay%d, lt, ltp, lmu);", j, r, r);
     }
   }
   if (kind == kKindFwd) {
-    o("    if (saved) {");
+    o("    if (saved && act) {");
     for (int r = 0; r < h.n_rep; ++r) o("      saved[(size_t)%d * n + s] = E%d;", r, repl[r]);
     o("    }");
   }
@@ -542,6 +585,7 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
         o("    const double pv%d = %sfv%d;", k, leafA[q.operand] > 0 ? "" : "-", q.fv);   // +-F, no arithmetic
       else
         o("    const double pv%d = fma(fv%d, %s, %s);", k, q.fv, opnd.c_str(), add.c_str());
+      step_sync();
     }
     o("    double W1_%d = pv%d;", gi, dp.node_value[g1_node[gi]]);
     for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q)
@@ -558,12 +602,12 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   }
   // ---- phase 2 over frequencies (the adjoint kinds' loop inputs in shared memory, see
   // smem_loop_values)
-  const bool sv = smem_loop_values(h, adj);
+  const bool sv = smem_loop_values(h, adj, B);
   const int n_sv = h.n_g2 + h.n_g2cd + h.n_cden;
   if (sv) {
-    for (int g = 0; g < h.n_g2; ++g) o("    jsv[%d * %d + tid] = W2_%d;", g, kJitBlock, g);
-    for (int q = 0; q < h.n_g2cd; ++q) o("    jsv[%d * %d + tid] = pW%d;", h.n_g2 + q, kJitBlock, q);
-    for (int c = 0; c < h.n_cden; ++c) o("    jsv[%d * %d + tid] = b%d;", n_sv - h.n_cden + c, kJitBlock, c);
+    for (int g = 0; g < h.n_g2; ++g) o("    jsv[%d * %d + tid] = W2_%d;", g, B, g);
+    for (int q = 0; q < h.n_g2cd; ++q) o("    jsv[%d * %d + tid] = pW%d;", h.n_g2 + q, B, q);
+    for (int c = 0; c < h.n_cden; ++c) o("    jsv[%d * %d + tid] = b%d;", n_sv - h.n_cden + c, B, c);
   }
   const size_t loop0 = o.s.size();
   o("    if (xr_zero) {");
@@ -580,7 +624,7 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       size_t last = 0;
       for (; it != end; ++it) {
         out += loop.substr(last, it->position() - last);
-        out += "jsv[" + std::to_string(base + std::stoi((*it)[1].str())) + " * " + std::to_string(kJitBlock) + " + tid]";
+        out += "jsv[" + std::to_string(base + std::stoi((*it)[1].str())) + " * " + std::to_string(B) + " + tid]";
         last = it->position() + it->length();
       }
       out += loop.substr(last);
@@ -618,6 +662,7 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     }
     for (int k = (int)dp.p.size() - 1; k >= 0; --k) {
       if (!has[k]) continue;
+      step_sync();
       const DagPrefix& q = dp.p[k];
       if (q.node) {
         o("    fvbar%d = fma(pv%d, bp%d, fvbar%d);", q.fv, q.operand, k, q.fv);
@@ -651,8 +696,10 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     for (int r = 0; r < h.n_rep_ext; ++r)
       o("    { const double eb = Ebar%d, ae = %s; kxb = fma(-eb * ae, Gx%d, kxb); kyb = fma(-eb * ae, Gy%d, kyb); }",
         repl[r], lit(rep_aext[r]).c_str(), r, r);
-    o("    gmu += mub; gkx += kxb; gky += kyb;");
-    o("    if (ps_grad) { ps_grad[3 * s] = mub; ps_grad[3 * s + 1] = kxb; ps_grad[3 * s + 2] = kyb; }");
+    o("    if (act) {");
+    o("      gmu += mub; gkx += kxb; gky += kyb;");
+    o("      if (ps_grad) { ps_grad[3 * s] = mub; ps_grad[3 * s + 1] = kxb; ps_grad[3 * s + 2] = kyb; }");
+    o("    }");
   }
   o("  }");
   if (energy) {   // every value is an output; nothing is reduced
@@ -672,13 +719,17 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     o("    double v = accV[i];");
   }
   o("    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);");
-  o("    if (lane == 0) red[warp * nval + i] = v;");
-  o("  }");
-  o("  __syncthreads();");
-  o("  for (int i = tid; i < nval; i += %d) {", kJitBlock);
-  o("    double v = 0.0;");
-  o("    for (int w = 0; w < %d; ++w) v += red[w * nval + i];", kJitBlock / 32);
-  o("    partial[(size_t)blockIdx.x * nval + i] = v;");
+  // 32 values at a time through a [warp][32] buffer
+  o("    if (lane == 0) red[warp * 32 + (i & 31)] = v;");
+  o("    if ((i & 31) == 31 || i == nval - 1) {");
+  o("      __syncthreads();");
+  o("      if (tid <= (i & 31)) {");
+  o("        double u = 0.0;");
+  o("        for (int w = 0; w < %d; ++w) u += red[w * 32 + tid];", B / 32);
+  o("        partial[(size_t)blockIdx.x * nval + (i & ~31) + tid] = u;");
+  o("      }");
+  o("      __syncthreads();");
+  o("    }");
   o("  }");
   o("}");
   return o.s;
@@ -746,6 +797,7 @@ bool jit_cache_write(const std::string& path, const std::string& ident, const st
 struct JitKernel {
   std::shared_ptr<void> lib;    // the loaded cubin; unloaded when its last holder lets go
   cudaKernel_t fn = nullptr;
+  int block = 128;              // threads per block the source was generated for
   double compile_ms = 0.0;
   bool from_cache = false;      // the cubin came from the disk cache
   bool failed = false;
@@ -794,6 +846,7 @@ int jit_prepare(tami_diagram* d, int kind) {
   if (!nv.ok) return fail(nv.why);
   const auto t0 = std::chrono::steady_clock::now();
   const std::string src = jit_source(d->hdr, d->blob.data(), kind);
+  K.block = lockstep_block(d->hdr, kind);
   const char* hdr_src[1] = {kDevmathSource};
   const char* hdr_name[1] = {"tami_devmath.cuh"};
   const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-w"};
@@ -862,10 +915,12 @@ int jit_prepare(tami_diagram* d, int kind) {
 
 // Whether an evaluating call of this kind takes the specialised kernel for n samples (compiling it if
 // so): 1 = use it, 0 = the generic kernel, or -status (the "always" mode when it cannot be built).
-size_t jit_smem(const TableHeader& h, int kind, int n_f) {
+size_t jit_smem(const TableHeader& h, int kind, int n_f, int block) {
   if (kind == kKindEnergy) return sizeof(double) * (size_t)(2 * h.n_xk + 2 * h.n_cden) * n_f;
-  const int nval = kind == kKindFused ? 6 * n_f + 3 : kind == kKindBwd ? 2 * n_f + 3 : 4 * n_f;
-  return sizeof(double) * ((size_t)(4 + 2 * h.n_cden) * n_f + 4 * (size_t)nval);
+  const size_t red = (size_t)block;   // the block reduction's [warp][32] buffer
+  const bool adj = kind == kKindFused || kind == kKindBwd;
+  const size_t jsv = smem_loop_values(h, adj, block) ? (size_t)block * loop_value_count(h) : 0;
+  return sizeof(double) * ((size_t)(4 + 2 * h.n_cden) * n_f + red + jsv);
 }
 
 int jit_select(tami_diagram* d, int kind, int64_t n, int n_f, bool generic_ok) {
@@ -876,7 +931,8 @@ int jit_select(tami_diagram* d, int kind, int64_t n, int n_f, bool generic_ok) {
   const bool big = !generic_ok || (kind == kKindEnergy ? (double)n * n_f >= 33554432.0 : n >= (int64_t(1) << 21));
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d->device);
-  const bool fits = (kind == kKindEnergy || n_f <= kJitMaxFreq) && jit_smem(d->hdr, kind, n_f) <= (size_t)optin;
+  const bool fits = (kind == kKindEnergy || n_f <= kJitMaxFreq) &&
+                    jit_smem(d->hdr, kind, n_f, lockstep_block(d->hdr, kind)) <= (size_t)optin;
   if (mode == TAMI_JIT_AUTO && (!big || !fits || !jit_supported(d->hdr, kind, nullptr))) return 0;
   if (!fits) { set_error("specialised kernel: frequencies beyond its per-thread sums or shared memory"); return -TAMI_EUNSUPPORTED; }
   const int rc = jit_prepare(d, kind);
@@ -891,7 +947,8 @@ int jit_handle(tami_diagram* d, int kind, int n_f, JitHandle* h) {
   std::lock_guard<std::mutex> lk(s->mu);
   h->lib = s->k[kind].lib;
   h->fn = reinterpret_cast<void*>(s->k[kind].fn);
-  h->smem = jit_smem(d->hdr, kind, n_f);
+  h->block = s->k[kind].block;
+  h->smem = jit_smem(d->hdr, kind, n_f, h->block);
   return TAMI_OK;
 }
 
@@ -899,11 +956,11 @@ int jit_grid(const JitHandle& h, int64_t n, int max_grid, int* grid_out) {
   cudaError_t e = cudaFuncSetAttribute(h.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h.smem);
   if (e != cudaSuccess) { set_error(std::string("specialised kernel attribute: ") + cudaGetErrorString(e)); return TAMI_ECUDA; }
   int per_sm = 0, sms = 0, dev = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h.fn, kJitBlock, h.smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h.fn, h.block, h.smem) != cudaSuccess || per_sm < 1) per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   long long grid = (long long)sms * per_sm;
-  const long long tiles = (n + kJitBlock - 1) / kJitBlock;
+  const long long tiles = (n + h.block - 1) / h.block;
   if (grid > tiles) grid = tiles;
   if (grid > max_grid) grid = max_grid;   // the caller's workspace holds max_grid partial rows
   if (grid < 1) grid = 1;
@@ -924,7 +981,7 @@ int jit_launch_at(const JitHandle& h, int grid, const tami_lattice* lat, const d
   const double *Xp = X, *Gp = gout, *Pp = params;
   double *pdx = ps_dX, *pg = ps_grad, *pv = per_sample, *sv = saved, *pp = partial;
   void* args[] = {&lt, &ltp, &lmu, &lkx, &lky, &sd, &off, &nn, &Xp, &Gp, &nf, &b, &pdx, &pg, &pv, &sv, &pp, &Pp};
-  const cudaError_t e = cudaLaunchKernel(h.fn, dim3((unsigned)grid), dim3(kJitBlock), args, h.smem, st);
+  const cudaError_t e = cudaLaunchKernel(h.fn, dim3((unsigned)grid), dim3((unsigned)h.block), args, h.smem, st);
   if (e != cudaSuccess) { set_error(std::string("specialised kernel launch: ") + cudaGetErrorString(e)); return TAMI_ECUDA; }
   return TAMI_OK;
 }
@@ -952,7 +1009,7 @@ int jit_select_batch(tami_diagram* const* ds, int n_d, const int64_t* n, int n_f
   std::vector<int> todo;
   for (int d = 0; d < n_d; ++d) {
     std::string why;
-    const bool fits = n_f <= kJitMaxFreq && jit_smem(ds[d]->hdr, kKindFwd, n_f) <= (size_t)optin;
+    const bool fits = n_f <= kJitMaxFreq && jit_smem(ds[d]->hdr, kKindFwd, n_f, lockstep_block(ds[d]->hdr, kKindFwd)) <= (size_t)optin;
     const bool ok = fits && jit_supported(ds[d]->hdr, kKindFwd, &why);
     if (mode == TAMI_JIT_AUTO && (n[d] < (int64_t(1) << 20) || !ok)) continue;
     if (!ok) {

@@ -100,23 +100,33 @@ def test_sincos_against_c_library():
     assert sg[-7] == 0.0 and cg[-7] == 1.0
 
 
-def test_fp64_rate_probe_does_its_work():
-    """The FP64 rate probe's recurrences a <- 0.9999999 a + 1e-3 from known starts: every thread's
-    sum equals the closed form to rounding, so the timed launch does all the flops it reports."""
+# (recurrences per thread, steps per trip, own multiplier and addend per recurrence, running sum)
+RATE_VARIANTS = [(8, 8, False, False), (4, 8, True, False), (4, 16, True, True), (3, 16, True, False)]
+
+
+@pytest.mark.parametrize("variant", range(len(RATE_VARIANTS)))
+def test_fp64_rate_probe_does_its_work(variant):
+    """Every operand pattern of the FP64 rate probe: the recurrences a_k <- m_k a_k + c_k (or the
+    running sums a_k <- m_k c_k + a_k) from known starts give each thread the closed-form sum to
+    rounding, so the timed launch does all the flops it reports; a variant out of range is refused."""
     blocks, trips = 4, 1000
+    C, U, own, acc = RATE_VARIANTS[variant]
     out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
     fl = ctypes.c_double()
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    L.check(L.lib().tami_selftest_fp64_rate(blocks, trips, ctypes.c_void_p(out.data_ptr()), ctypes.byref(fl), s))
+    L.check(L.lib().tami_selftest_fp64_rate(variant, blocks, trips, ctypes.c_void_p(out.data_ptr()), ctypes.byref(fl), s))
     torch.cuda.synchronize()
-    assert fl.value == 2.0 * 64 * trips * 256 * blocks
-    m, c, steps = 0.9999999, 1e-3, 8 * trips
+    assert fl.value == 2.0 * C * U * trips * 256 * blocks
+    m, c, steps = 0.9999999, 1e-3, U * trips
     t = np.arange(blocks * 256)
     ref = np.zeros(blocks * 256)
-    for k in range(8):
+    for k in range(C):
+        mk, ck = (m - 1e-9 * k, c + 1e-9 * k) if own else (m, c)
         a0 = 1e-3 * ((t + k) & 1023)
-        ref += a0 * m ** steps + c * (1 - m ** steps) / (1 - m)
+        ref += a0 + steps * (mk * ck) if acc else a0 * mk ** steps + ck * (1 - mk ** steps) / (1 - mk)
     assert np.allclose(out.cpu().numpy(), ref, rtol=1e-9, atol=0)
+    assert L.lib().tami_selftest_fp64_rate(len(RATE_VARIANTS), blocks, trips, ctypes.c_void_p(out.data_ptr()),
+                                           ctypes.byref(fl), s) == L.TAMI_EINVAL
 
 
 def special_operands(rng, n):
