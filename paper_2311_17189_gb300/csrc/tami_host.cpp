@@ -895,7 +895,11 @@ int flatten(tami_diagram* d) {
   }
   bl += h.n_cden;                                       // cden adjoints into combinations
   for (auto& g : g1s) {
-    for (auto& pr : g.rd) bl += pr.second + (pr.second == 1 ? 3.0 : 4.0);   // RR and the real-denominator adjoint
+    // the group weight W1 = pv RR, with RR (the product of its real-denominator reciprocals) kept
+    // from the forward: the root's adjoint wb RR, and each real denominator's adjoint
+    // -wb W1 pw rr (wb W1 once per group, the power a product where it is not 1, one fma)
+    if (!g.rd.empty()) bl += 1.0;
+    for (auto& pr : g.rd) bl += pr.second == 1 ? 2.0 : 3.0;
     bl += 1.0;
   }
   bl += dag_bwd;

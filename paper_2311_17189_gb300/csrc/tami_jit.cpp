@@ -213,10 +213,23 @@ int lockstep_block(const TableHeader& h, int kind) {
   const int b = e ? std::atoi(e) : 512;
   return (b == 256 || b == 1024) ? b : 512;
 }
+// Blocks per SM the kernel is compiled for: 1024 threads per SM, 64 registers each.  (128
+// registers at 512 threads per SM halve the large tables' spills and change no step by more than
+// 1 %: the kernels are bound by FP64 issue, not by their local-memory traffic.)
+int blocks_per_sm(int block) { return 1024 / block; }
 int lockstep_sync_ops() {
   const char* e = std::getenv("TAMI_JIT_SYNC_OPS");
   const int k = e ? std::atoi(e) : 64;
   return k >= 4 ? k : 64;
+}
+
+// Each group's product of real-denominator reciprocals RR is formed first and kept for the
+// adjoint, W1 = pv RR, instead of W1 built factor by factor and RR formed again in the reverse
+// sweep (order-6 step 676 -> 663 ms, fewer spills; order 4 unchanged).  $TAMI_JIT_KEEPRR=0 builds
+// W1 factor by factor.
+bool keep_rr() {
+  const char* e = std::getenv("TAMI_JIT_KEEPRR");
+  return !(e && !std::strcmp(e, "0"));
 }
 
 bool int_products(const TableHeader& h) {
@@ -403,7 +416,7 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     }
   }
   o("extern \"C\" __global__ void __launch_bounds__(%d, %d) %s(double lt, double ltp, double lmu, double lkx, double lky,",
-    B, 1024 / B, kKernelName[kind]);
+    B, kind == kKindEnergy ? 8 : blocks_per_sm(B), kKernelName[kind]);
   o("    unsigned long long seed, unsigned long long offset, long long n, const double* X, const double* G, int n_f,");
   o("    double beta, double* ps_dX, double* ps_grad, double* ps_v, double* saved, double* partial, const double* P) {");
   o("  extern __shared__ __align__(16) double smem[];");
@@ -587,9 +600,20 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
         o("    const double pv%d = fma(fv%d, %s, %s);", k, q.fv, opnd.c_str(), add.c_str());
       step_sync();
     }
-    o("    double W1_%d = pv%d;", gi, dp.node_value[g1_node[gi]]);
-    for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q)
-      for (int pw = g1rd[2 * q + 1]; pw > 0; --pw) o("    W1_%d *= rr%d;", gi, g1rd[2 * q]);
+    if (keep_rr() && g1[4 * gi + 2] < g1[4 * gi + 3]) {
+      bool first = true;
+      for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q)
+        for (int pw = g1rd[2 * q + 1]; pw > 0; --pw) {
+          if (first) o("    double RR_%d = rr%d;", gi, g1rd[2 * q]);
+          else o("    RR_%d *= rr%d;", gi, g1rd[2 * q]);
+          first = false;
+        }
+      o("    double W1_%d = pv%d * RR_%d;", gi, dp.node_value[g1_node[gi]], gi);
+    } else {
+      o("    double W1_%d = pv%d;", gi, dp.node_value[g1_node[gi]]);
+      for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q)
+        for (int pw = g1rd[2 * q + 1]; pw > 0; --pw) o("    W1_%d *= rr%d;", gi, g1rd[2 * q]);
+    }
     o("    W2_%d += W1_%d;", g1_tgt[gi], gi);
   }
   for (int c = 0; c < h.n_cden; ++c) o("    const double b%d = %sx%d;", c, cden[2 * c + 1] > 0 ? "" : "-", cden[2 * c]);
@@ -649,10 +673,12 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       const int rp = dp.node_value[g1_node[gi]];
       if (!has[rp]) o("    double bp%d;", rp);
       o("    {");
-      o("      const double wb = Wb2_%d; double RR = 1.0;", g1_tgt[gi]);
+      const bool kept = keep_rr() && g1[4 * gi + 2] < g1[4 * gi + 3];
+      if (kept) o("      const double wb = Wb2_%d; const double RR = RR_%d;", g1_tgt[gi], gi);
+      else o("      const double wb = Wb2_%d; double RR = 1.0;", g1_tgt[gi]);
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
         const int i = g1rd[2 * q], pw = g1rd[2 * q + 1];
-        for (int k = 0; k < pw; ++k) o("      RR *= rr%d;", i);
+        if (!kept) for (int k = 0; k < pw; ++k) o("      RR *= rr%d;", i);
         o("      xbar%d -= wb * W1_%d * %s * rr%d;", rden[2 * i], gi, lit((double)pw).c_str(), i);
       }
       if (has[rp]) o("      bp%d = fma(wb, RR, bp%d);", rp, rp);

@@ -74,6 +74,7 @@ def per_sample(src):
     fl += 6 * len(re.findall(r'rr\d+ = rcp\(', body))
     fl += dag(body)
     fl += len(re.findall(r'W1_\d+ \*= rr\d+;', body)) + len(re.findall(r'W2_\d+ \+= W1_\d+;', body))
+    fl += len(re.findall(r'RR_\d+ \*= rr\d+;', body)) + len(re.findall(r'double W1_\d+ = pv\d+ \* RR_\d+;', body))
     return fl
 
 
