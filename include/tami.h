@@ -421,6 +421,14 @@ int tami_selftest_sincos(const double* k, int64_t n, double* s, double* c, tami_
  * taken for normal operands with a normal result.  a, b, mul: device double [n]. */
 int tami_selftest_imul(const double* a, const double* b, int64_t n, double* mul, tami_stream_t stream);
 
+/* Diagnostic: the call-free variant of that product (imul_ftz), which large tables' specialised
+ * kernels use for their per-sample products, applied elementwise: for normal operands with a
+ * normal result the IEEE product, bit for bit; otherwise flush to zero — a zero or subnormal
+ * operand, or a result below 2^-1022, gives a signed zero, a result above the range a signed
+ * infinity, an infinite operand a signed infinity (a NaN against a zero or subnormal operand), a
+ * NaN operand a NaN.  a, b, mul: device double [n]. */
+int tami_selftest_imul_ftz(const double* a, const double* b, int64_t n, double* mul, tami_stream_t stream);
+
 /* Diagnostic: a probe of the FP64 fma issue rate (not a term of the paper; it measures the
  * ceiling that the evaluation kernels are held against).  Launches `blocks` blocks of 256
  * threads, each running independent fma recurrences, a_k <- m_k a_k + c_k (or the running sum

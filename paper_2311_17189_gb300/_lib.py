@@ -26,7 +26,7 @@ EXPORTS = [
     "tami_batch_destroy", "tami_batch_debug_set_item", "tami_batch_specialised",
     "tami_enumerate_sigma",
     "tami_set_table_staging", "tami_debug_set_wait_limit",
-    "tami_selftest_exp", "tami_selftest_sincos", "tami_selftest_imul", "tami_selftest_fp64_rate", "tami_destroy",
+    "tami_selftest_exp", "tami_selftest_sincos", "tami_selftest_imul", "tami_selftest_imul_ftz", "tami_selftest_fp64_rate", "tami_destroy",
 ]
 
 
@@ -116,6 +116,7 @@ def lib():
     L.tami_selftest_exp.argtypes = [dp, i64, dp, dp, dp, vp]
     L.tami_selftest_sincos.argtypes = [dp, i64, dp, dp, vp]
     L.tami_selftest_imul.argtypes = [dp, dp, i64, dp, vp]
+    L.tami_selftest_imul_ftz.argtypes = [dp, dp, i64, dp, vp]
     L.tami_selftest_fp64_rate.argtypes = [ctypes.c_int, ctypes.c_int, i64, dp, ctypes.POINTER(ctypes.c_double), vp]
     L.tami_destroy.argtypes = [vp]
     L.tami_destroy.restype = None

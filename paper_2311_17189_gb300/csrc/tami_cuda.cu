@@ -161,6 +161,12 @@ __global__ void imul_selftest_kernel(const double* a, const double* b, long long
   mul[i] = imul(a[i], b[i]);
 }
 
+__global__ void imul_ftz_selftest_kernel(const double* a, const double* b, long long n, double* mul) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  mul[i] = imul_ftz(a[i], b[i]);
+}
+
 // FP64 issue-rate probes: C independent fma recurrences per thread, U steps of each per trip, the
 // sums written out so that nothing is dropped; 2 C U trips flops per thread.  How fast the FP64
 // unit runs them depends on how the operands sit in the register file, so there are several
@@ -589,6 +595,14 @@ int tami_selftest_imul(const double* a, const double* b, int64_t n, double* mul,
   imul_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(a, b, n, mul);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "imul_selftest launch");
+}
+
+int tami_selftest_imul_ftz(const double* a, const double* b, int64_t n, double* mul, tami_stream_t stream) {
+  if (!a || !b || !mul || n < 0) { set_error("bad argument"); return TAMI_EINVAL; }
+  if (n == 0) return TAMI_OK;
+  imul_ftz_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(a, b, n, mul);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TAMI_OK : cuda_fail(e, "imul_ftz_selftest launch");
 }
 
 int tami_selftest_fp64_rate(int variant, int blocks, int64_t trips, double* out, double* flops, tami_stream_t stream) {

@@ -42,10 +42,12 @@ __device__ __forceinline__ double to_momentum(unsigned int hi, unsigned int lo) 
 // rounded to nearest even with round and sticky bits.)
 static __device__ __noinline__ double dmul_fp64(double a, double b) { return __dmul_rn(a, b); }
 
-__device__ __forceinline__ double imul(double a, double b) {
-  const unsigned long long ua = __double_as_longlong(a), ub = __double_as_longlong(b);
+// The normal path shared by imul and imul_ftz: the rounded product's bits for normal operands
+// whose result is normal (e in [1, 0x7FE]); e, the biased exponent before rounding, says whether
+// it is.
+__device__ __forceinline__ unsigned long long imul_bits(unsigned long long ua, unsigned long long ub, int ea, int eb,
+                                                        int& e) {
   const unsigned long long sign = (ua ^ ub) & 0x8000000000000000ull;
-  const int ea = (int)(ua >> 52) & 0x7FF, eb = (int)(ub >> 52) & 0x7FF;
   const unsigned long long ma = (ua & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
   const unsigned long long mb = (ub & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
   const unsigned long long lo = ma * mb, hi = __umul64hi(ma, mb);   // 106-bit product in [2^104, 2^106)
@@ -56,9 +58,41 @@ __device__ __forceinline__ double imul(double a, double b) {
   const unsigned long long rb = (t >> 10) & 1ull;
   const unsigned long long st = ((t & 0x3FFull) | below) != 0ull;
   m += rb & (st | (m & 1ull));                                       // may carry into bit 53
-  const int e = ea + eb - 1023 + top;                                // biased exponent before rounding
+  e = ea + eb - 1023 + top;
+  return sign | (((unsigned long long)(e - 1) << 52) + m);
+}
+
+__device__ __forceinline__ double imul(double a, double b) {
+  const unsigned long long ua = __double_as_longlong(a), ub = __double_as_longlong(b);
+  const int ea = (int)(ua >> 52) & 0x7FF, eb = (int)(ub >> 52) & 0x7FF;
+  int e;
+  const unsigned long long r = imul_bits(ua, ub, ea, eb, e);
   if (ea == 0 || eb == 0 || ea == 0x7FF || eb == 0x7FF || e <= 0 || e >= 0x7FE) return dmul_fp64(a, b);
-  return __longlong_as_double(sign | (((unsigned long long)(e - 1) << 52) + m));
+  return __longlong_as_double(r);
+}
+
+// The same product without the FP64 instruction anywhere (no call, no branch: the compiler cannot
+// turn it into a predicated DMUL that would take an FP64 issue slot), for code whose products all
+// move to the integer pipes.  Normal operands with a normal result: the IEEE product, bit for bit.
+// Otherwise flush to zero: a zero or subnormal operand, or a result below the normal range, gives
+// a signed zero; a result above the range a signed infinity; an infinite operand a signed
+// infinity (a NaN against a zero or subnormal one); a NaN operand a quiet NaN (its payload kept).
+__device__ __forceinline__ double imul_ftz(double a, double b) {
+  const unsigned long long ua = __double_as_longlong(a), ub = __double_as_longlong(b);
+  const int ea = (int)(ua >> 52) & 0x7FF, eb = (int)(ub >> 52) & 0x7FF;
+  int e;
+  unsigned long long r = imul_bits(ua, ub, ea, eb, e);
+  const unsigned long long sign = (ua ^ ub) & 0x8000000000000000ull;
+  const bool zero_in = ea == 0 || eb == 0;
+  r = (e <= 0 || zero_in) ? sign : r;
+  r = (e >= 0x7FF && !zero_in) ? (sign | 0x7FF0000000000000ull) : r;
+  const bool a_nan = (ua << 1) > 0xFFE0000000000000ull, b_nan = (ub << 1) > 0xFFE0000000000000ull;
+  const bool inf_in = ea == 0x7FF || eb == 0x7FF;
+  const unsigned long long special = a_nan ? (ua | 0x0008000000000000ull)
+                                   : b_nan ? (ub | 0x0008000000000000ull)
+                                   : zero_in ? 0x7FF8000000000000ull : (sign | 0x7FF0000000000000ull);
+  r = inf_in ? special : r;
+  return __longlong_as_double(r);
 }
 
 

@@ -232,6 +232,21 @@ bool keep_rr() {
   return !(e && !std::strcmp(e, "0"));
 }
 
+// The per-sample products of tables up to 256 pole-DAG ops (group weights, Fermi segments, the
+// reverse sweep's first adjoint terms, the real denominators' adjoints) run on the integer pipes
+// as well, with the call-free imul_ftz (IEEE products for normal values; subnormals flush to
+// zero): order-4 step 48.07 -> 47.22 ms.  Larger tables keep them on the FP64 unit: there the
+// integer product's registers double the spills (order 6: 663 -> 730 ms).  $TAMI_JIT_PSMUL=0 keeps
+// every table's per-sample products on the FP64 unit.
+bool ps_products(const TableHeader& h) {
+  const char* e = std::getenv("TAMI_JIT_PSMUL");
+  return h.n_ops <= 256 && !(e && !std::strcmp(e, "0"));
+}
+// a * b, on the integer pipes where the per-sample products go there
+std::string pmul(bool ps, const std::string& a, const std::string& b) {
+  return ps ? "imul_ftz(" + a + ", " + b + ")" : a + " * " + b;
+}
+
 bool int_products(const TableHeader& h) {
   const char* e = std::getenv("TAMI_JIT_INTARITH");
   return !(e && !std::strcmp(e, "0")) && h.n_ops <= 256;
@@ -240,8 +255,10 @@ bool int_products(const TableHeader& h) {
 void emit_phase2(Out& o, const Table& t, int kind, bool xr_zero) {
   const TableHeader& h = t.h;
   const bool ia = int_products(h);
+  const bool ps = ps_products(h);
+  auto PM = [&](const std::string& a, const std::string& b) { return pmul(ps, a, b); };
   auto MUL = [&](const std::string& a, const std::string& b) {
-    return ia ? "imul(" + a + ", " + b + ")" : a + " * " + b;
+    return ia ? "imul(" + a + ", " + b + ")" : PM(a, b);
   };
   auto NEG = [&](const std::string& a) {   // sign flip (no arithmetic)
     return "__longlong_as_double(__double_as_longlong(" + a + ") ^ (long long)0x8000000000000000ull)";
@@ -348,6 +365,8 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   // caches hold; their Fermi segments call one out-of-line copy of the exponential, reciprocal and
   // selects (smaller code; the largest order-5 table: 2.6 % faster, the order-4 table unchanged).
   const bool seg_calls = h.n_ops > 256;
+  const bool ps = ps_products(h);
+  auto PM = [&](const std::string& a, const std::string& b) { return pmul(ps, a, b); };
   const Table t{h, blob};
   const bool energy = kind == kKindEnergy;
   const bool fwd = kind != kKindBwd, adj = kind == kKindFused || kind == kKindBwd;
@@ -407,9 +426,9 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     for (int bose = 0; bose < 2; ++bose) {
       o("static __device__ __noinline__ double2 tami_seg_%s(double xv, double beta) {", bose ? "bose" : "fermi");
       o("  double em = 0.0;");
-      o("  const double y = exp_neg<%s>(-beta * fabs(xv), em); (void)em;", bose ? "true" : "false");
+      o("  const double y = exp_neg<%s>(%s, em); (void)em;", bose ? "true" : "false", PM("-beta", "fabs(xv)").c_str());
       o("  const double rD = rcp(%s);", bose ? "-em" : "1.0 + y");
-      o("  const double t2 = (%s) * rD;", bose ? "-y" : "y");
+      o("  const double t2 = %s;", PM(bose ? "(-y)" : "(y)", "rD").c_str());
       o("  const bool neg = __double_as_longlong(xv) <= 0;");
       o("  return make_double2(neg ? rD : t2, neg ? t2 : rD);");
       o("}");
@@ -560,15 +579,17 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     if (seg_calls) {
       o("    { const double2 gh = tami_seg_%s(x%d, beta);", bose ? "bose" : "fermi", sgm[0]);
       o("      sg%d_g = gh.x; sg%d_h = gh.y; sg%d_d1 = %s; }", b, b, b,
-        adj ? ("-beta * (sg" + std::to_string(b) + "_g * sg" + std::to_string(b) + "_h)").c_str() : "0.0");
+        adj ? PM("-beta", ps ? PM("sg" + std::to_string(b) + "_g", "sg" + std::to_string(b) + "_h")
+                                 : "(sg" + std::to_string(b) + "_g * sg" + std::to_string(b) + "_h)").c_str() : "0.0");
     } else {
     o("    { const double xv = x%d; double em = 0.0;", sgm[0]);
-    o("      const double y = exp_neg<%s>(-beta * fabs(xv), em); (void)em;", bose ? "true" : "false");
+    o("      const double y = exp_neg<%s>(%s, em); (void)em;", bose ? "true" : "false", PM("-beta", "fabs(xv)").c_str());
     o("      const double rD = rcp(%s);", bose ? "-em" : "1.0 + y");
-    o("      const double t2 = (%s) * rD;", bose ? "-y" : "y");
+    o("      const double t2 = %s;", PM(bose ? "(-y)" : "(y)", "rD").c_str());
     o("      const bool neg = __double_as_longlong(xv) <= 0;");
     o("      sg%d_g = neg ? rD : t2; sg%d_h = neg ? t2 : rD; sg%d_d1 = %s; }", b, b, b,
-      adj ? ("-beta * (sg" + std::to_string(b) + "_g * sg" + std::to_string(b) + "_h)").c_str() : "0.0");
+      adj ? PM("-beta", ps ? PM("sg" + std::to_string(b) + "_g", "sg" + std::to_string(b) + "_h")
+                                 : "(sg" + std::to_string(b) + "_g * sg" + std::to_string(b) + "_h)").c_str() : "0.0");
     }
     for (int v = sgm[2]; v < sgm[3]; ++v) {
       o("    const double fv%d = sg%d_%c;", v, b, fvr[2 * v] > 0 ? 'g' : 'h');
@@ -605,14 +626,18 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q)
         for (int pw = g1rd[2 * q + 1]; pw > 0; --pw) {
           if (first) o("    double RR_%d = rr%d;", gi, g1rd[2 * q]);
+          else if (ps) o("    RR_%d = imul_ftz(RR_%d, rr%d);", gi, gi, g1rd[2 * q]);
           else o("    RR_%d *= rr%d;", gi, g1rd[2 * q]);
           first = false;
         }
-      o("    double W1_%d = pv%d * RR_%d;", gi, dp.node_value[g1_node[gi]], gi);
+      o("    double W1_%d = %s;", gi, PM("pv" + std::to_string(dp.node_value[g1_node[gi]]), "RR_" + std::to_string(gi)).c_str());
     } else {
       o("    double W1_%d = pv%d;", gi, dp.node_value[g1_node[gi]]);
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q)
-        for (int pw = g1rd[2 * q + 1]; pw > 0; --pw) o("    W1_%d *= rr%d;", gi, g1rd[2 * q]);
+        for (int pw = g1rd[2 * q + 1]; pw > 0; --pw) {
+          if (ps) o("    W1_%d = imul_ftz(W1_%d, rr%d);", gi, gi, g1rd[2 * q]);
+          else o("    W1_%d *= rr%d;", gi, g1rd[2 * q]);
+        }
     }
     o("    W2_%d += W1_%d;", g1_tgt[gi], gi);
   }
@@ -620,7 +645,12 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   if (adj) {
     for (int g = 0; g < h.n_g2; ++g) {
       o("    double Wb2_%d = 0.0;", g);
-      for (int q = g2[g]; q < g2[g + 1]; ++q) o("    const double pW%d = %s * W2_%d;", q, lit(g2cd_p[q]).c_str(), g);
+      for (int q = g2[g]; q < g2[g + 1]; ++q) {
+        if (ps && (g2cd_p[q] == 1.0 || g2cd_p[q] == -1.0))
+          o("    const double pW%d = %sW2_%d;", q, g2cd_p[q] > 0 ? "" : "-", g);
+        else
+          o("    const double pW%d = %s;", q, PM(lit(g2cd_p[q]), "W2_" + std::to_string(g)).c_str());
+      }
     }
     for (int c = 0; c < h.n_cden; ++c) o("    double bb%d = 0.0;", c);
   }
@@ -679,10 +709,16 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
         const int i = g1rd[2 * q], pw = g1rd[2 * q + 1];
         if (!kept) for (int k = 0; k < pw; ++k) o("      RR *= rr%d;", i);
-        o("      xbar%d -= wb * W1_%d * %s * rr%d;", rden[2 * i], gi, lit((double)pw).c_str(), i);
+        if (ps) {   // wb W1 once per group, then one fma per factor
+          if (q == g1[4 * gi + 2]) o("      const double tw = %s;", PM("wb", "W1_" + std::to_string(gi)).c_str());
+          o("      xbar%d = fma(-%s, rr%d, xbar%d);", rden[2 * i], pw == 1 ? "tw" : PM("tw", lit((double)pw)).c_str(), i,
+            rden[2 * i]);
+        } else {
+          o("      xbar%d -= wb * W1_%d * %s * rr%d;", rden[2 * i], gi, lit((double)pw).c_str(), i);
+        }
       }
       if (has[rp]) o("      bp%d = fma(wb, RR, bp%d);", rp, rp);
-      else o("      bp%d = wb * RR;", rp);
+      else o("      bp%d = %s;", rp, PM("wb", "RR").c_str());
       has[rp] = 1;
       o("    }");
     }
@@ -693,7 +729,7 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       if (q.node) {
         o("    fvbar%d = fma(pv%d, bp%d, fvbar%d);", q.fv, q.operand, k, q.fv);
         if (has[q.operand]) o("    bp%d = fma(fv%d, bp%d, bp%d);", q.operand, q.fv, k, q.operand);
-        else o("    double bp%d = fv%d * bp%d;", q.operand, q.fv, k);
+        else o("    double bp%d = %s;", q.operand, PM("fv" + std::to_string(q.fv), "bp" + std::to_string(k)).c_str());
         has[q.operand] = 1;
       } else {
         o("    fvbar%d = fma(%s, bp%d, fvbar%d);", q.fv, lit(leafA[q.operand]).c_str(), k, q.fv);

@@ -73,8 +73,11 @@ def per_sample(src):
     fl += sum(POLY.get(int(k), 16 + 4 * int(k)) for k in re.findall(r'fermi_poly\((\d+),', body))
     fl += 6 * len(re.findall(r'rr\d+ = rcp\(', body))
     fl += dag(body)
-    fl += len(re.findall(r'W1_\d+ \*= rr\d+;', body)) + len(re.findall(r'W2_\d+ \+= W1_\d+;', body))
-    fl += len(re.findall(r'RR_\d+ \*= rr\d+;', body)) + len(re.findall(r'double W1_\d+ = pv\d+ \* RR_\d+;', body))
+    # group weights: products on the FP64 unit (x *= y, x * y) or the integer pipes (imul_ftz(x, y))
+    fl += len(re.findall(r'W1_\d+ (?:\*= rr\d+|= imul_ftz\(W1_\d+, rr\d+\));', body))
+    fl += len(re.findall(r'W2_\d+ \+= W1_\d+;', body))
+    fl += len(re.findall(r'RR_\d+ (?:\*= rr\d+|= imul_ftz\(RR_\d+, rr\d+\));', body))
+    fl += len(re.findall(r'double W1_\d+ = (?:pv\d+ \* RR_\d+|imul_ftz\(pv\d+, RR_\d+\));', body))
     return fl
 
 

@@ -172,3 +172,40 @@ def test_integer_pipe_product_is_ieee():
         assert np.array_equal(np.isnan(g), nan), what
         bad = g[~nan].view(np.uint64) != r[~nan].view(np.uint64)
         assert not bad.any(), (what, a[~nan][bad][:5], b[~nan][bad][:5], g[~nan][bad][:5], r[~nan][bad][:5])
+
+
+def test_integer_pipe_product_ftz():
+    """The call-free integer-pipe product (imul_ftz) on the same operands: the IEEE product (from
+    numpy) bit for bit wherever both operands are normal and the product is normal; a signed zero
+    for a zero or subnormal operand or a product below 2^-1022 (at exactly 2^-1022, where the
+    unrounded product may lie just below, either); a signed infinity for an overflowing product
+    or an infinite operand against a normal one; a NaN for a NaN operand or infinity times a zero
+    or subnormal."""
+    rng = np.random.default_rng(12)
+    a, b = special_operands(rng, 400000)
+    at, bt = torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda")
+    mul = torch.empty_like(at)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L.check(L.lib().tami_selftest_imul_ftz(ctypes.c_void_p(at.data_ptr()), ctypes.c_void_p(bt.data_ptr()),
+                                           at.numel(), ctypes.c_void_p(mul.data_ptr()), s))
+    torch.cuda.synchronize()
+    g = mul.cpu().numpy()
+    tiny = np.ldexp(1.0, -1022)
+    with np.errstate(all="ignore"):
+        r = a * b
+    sign = np.signbit(a) ^ np.signbit(b)
+    fin_a, fin_b = np.isfinite(a), np.isfinite(b)
+    sub_a, sub_b = fin_a & (np.abs(a) < tiny), fin_b & (np.abs(b) < tiny)
+    nan_ref = np.isnan(a) | np.isnan(b) | (np.isinf(a) & sub_b) | (np.isinf(b) & sub_a)
+    assert np.array_equal(np.isnan(g), nan_ref)
+    ok = ~nan_ref
+    inf_in = (np.isinf(a) | np.isinf(b)) & ok
+    assert np.all(np.isinf(g[inf_in])) and np.array_equal(np.signbit(g[inf_in]), sign[inf_in])
+    fin = ok & ~inf_in
+    flush = fin & (sub_a | sub_b | (np.abs(r) < tiny))
+    assert np.all(g[flush] == 0.0) and np.array_equal(np.signbit(g[flush]), sign[flush])
+    edge = fin & ~flush & (np.abs(r) == tiny)
+    assert np.all((g[edge] == 0.0) | (g[edge] == r[edge]))
+    rest = fin & ~flush & ~edge
+    bad = g[rest].view(np.uint64) != r[rest].view(np.uint64)
+    assert not bad.any(), (a[rest][bad][:5], b[rest][bad][:5], g[rest][bad][:5], r[rest][bad][:5])
