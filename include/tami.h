@@ -283,7 +283,11 @@ int tami_forward_noalloc(const tami_diagram* d, const tami_lattice* lat, uint64_
  * arrays in local memory.  Each is generated as CUDA C++ on the first call that takes it, compiled
  * for sm_103a with NVRTC (loaded at run time: libnvrtc.so.13, or the path in $TAMI_NVRTC; "none"
  * disables it) and cached with the diagram until tami_destroy.  Values agree with the generic kernels to rounding; workspaces and
- * outputs are those of the generic calls.  tami_forward_noalloc always runs the generic kernel;
+ * outputs are those of the generic calls.  Part of their double products run on the integer
+ * pipes, bit for bit the FP64 unit's for normal values; for tables of at most 256 pole-DAG ops the
+ * per-sample products among them flush results below 2^-1022 (and subnormal operands) to zero.
+ * The Monte Carlo kinds run 512-thread blocks, two per SM, whose warps meet at barriers in the
+ * straight-line per-sample code.  tami_forward_noalloc always runs the generic kernel;
  * batches take the specialised forward kernels of their large diagrams (tami_batch_plan).
  * Compiled kernels are also kept on disk, one file per compilation, in $TAMI_JIT_CACHE (default
  * $HOME/.cache/libtami_jit; "none": no disk cache): an entry records the NVRTC version, options,
