@@ -247,15 +247,21 @@ std::string pmul(bool ps, const std::string& a, const std::string& b) {
   return ps ? "imul_ftz(" + a + ", " + b + ")" : a + " * " + b;
 }
 
+// The frequency loop's products (1/D = D r, the trie's complex products, Z, the sums' first terms)
+// run on the integer pipes with imul, for every table: with 32 frequencies the 85 order-2..5
+// diagrams went from 2.668 to 2.255 s once the large tables (which had kept them on the FP64 unit
+// while their kernels waited on instruction fetch) took them too.  $TAMI_JIT_INTARITH=0 keeps them
+// on the FP64 unit.
 bool int_products(const TableHeader& h) {
+  (void)h;
   const char* e = std::getenv("TAMI_JIT_INTARITH");
-  return !(e && !std::strcmp(e, "0")) && h.n_ops <= 256;
+  return !(e && !std::strcmp(e, "0"));
 }
 
 void emit_phase2(Out& o, const Table& t, int kind, bool xr_zero) {
   const TableHeader& h = t.h;
   const bool ia = int_products(h);
-  const bool ps = ps_products(h);
+  const bool ps = ps_products(h) && kind != kKindEnergy;
   auto PM = [&](const std::string& a, const std::string& b) { return pmul(ps, a, b); };
   auto MUL = [&](const std::string& a, const std::string& b) {
     return ia ? "imul(" + a + ", " + b + ")" : PM(a, b);
@@ -365,7 +371,9 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   // caches hold; their Fermi segments call one out-of-line copy of the exponential, reciprocal and
   // selects (smaller code; the largest order-5 table: 2.6 % faster, the order-4 table unchanged).
   const bool seg_calls = h.n_ops > 256;
-  const bool ps = ps_products(h);
+  // (the energy-input kind keeps its per-row products on the FP64 unit: 1.093 -> 1.125 ms with them
+  // on the integer pipes on the paper's energy-input example)
+  const bool ps = ps_products(h) && kind != kKindEnergy;
   auto PM = [&](const std::string& a, const std::string& b) { return pmul(ps, a, b); };
   const Table t{h, blob};
   const bool energy = kind == kKindEnergy;
