@@ -153,6 +153,38 @@ def test_specialised_kernel_agrees_with_generic(case):
                    (jit["mean"], jit["var"], jit["values"], jit))
 
 
+@pytest.mark.parametrize("n", [1, 2, 511, 512, 513, 1537])
+def test_specialised_kernels_at_tile_edges(n):
+    """The Monte Carlo kernels run 512-sample tiles in lockstep blocks (every lane reaches every
+    barrier; a lane past the end runs the last sample again and adds and writes nothing).  At
+    sample counts around the tile size: the fused pass's and the forward's per-sample outputs equal
+    those of a longer launch over the same samples bit for bit, and the reduced outputs are the
+    means (and the variance) of the per-sample ones."""
+    D, S, lat, beta, X = setup(CASES[2])
+    T.set_jit("always")
+    seed, off = 13, 77
+    g = upstream(len(X), seed=4)
+    big = D.forward_backward(lat, seed, off, 2048, X, beta, g, per_sample=True)
+    out = D.forward_backward(lat, seed, off, n, X, beta, g, per_sample=True)
+    m, v, ps = D.forward(lat, seed, off, n, X, beta, per_sample=True)
+    torch.cuda.synchronize()
+    assert D.jit_status()["last_used"]
+    assert torch.equal(out["values"], big["values"][:, :n]) and torch.equal(ps, big["values"][:, :n])
+    assert torch.equal(out["dX"], big["dX"][:, :n]) and torch.equal(out["grads"], big["grads"][:n])
+    p = ps.cpu().numpy()
+    scale = np.abs(p).mean(axis=1)
+    for mean in (m.cpu().numpy(), out["mean"].cpu().numpy()):
+        assert np.all(np.abs(mean - p.mean(axis=1)) <= 1e-13 * scale)
+    if n > 1:
+        var = np.stack([np.var(p.real, axis=1, ddof=1), np.var(p.imag, axis=1, ddof=1)], axis=1)
+        for vv in (v.cpu().numpy(), out["var"].cpu().numpy()):
+            assert np.allclose(vv, var, rtol=1e-9, atol=1e-300)
+    dX = out["dX"].cpu().numpy()
+    assert np.all(np.abs(out["dSigma_dX"].cpu().numpy() - dX.mean(axis=1)) <= 1e-13 * np.abs(dX).mean(axis=1))
+    gr = out["grads"].cpu().numpy()
+    assert np.all(np.abs(out["grad_params"].cpu().numpy() - gr.mean(axis=0)) <= 1e-13 * np.abs(gr).mean(axis=0))
+
+
 def test_auto_mode_takes_the_specialised_kernel_for_large_launches():
     """auto (the default): the generic kernel below 2^21 samples, the specialised one from there on
     (compiled on that first call and kept with the diagram)."""

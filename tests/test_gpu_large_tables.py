@@ -113,21 +113,29 @@ def test_streamed_batch_gives_resident_bits(modes):
 @functools.lru_cache(maxsize=1)
 def order6_cases():
     """Order-6 diagrams: the largest flat table, the table with the largest generic-forward shared
-    memory, and two others, chosen from the library's own table sizes."""
+    memory, the first table whose terms need second Fermi derivatives (third in the adjoint), and
+    two others, chosen from the library's own table sizes."""
     ds = O.enumerate_sigma(6)
     infos = [T.Diagram(d["alpha"], eps=d["eps"]).info() for d in ds]
     terms = [i["n_terms"] for i in infos]
     smem = [i["table_bytes"] + 8 * 128 * (i["n_cplx_dens"] + i["n_groups_freq"]) for i in infos]
-    picks = [int(np.argmax(terms)), int(np.argmax(smem)), len(ds) // 3, 2 * len(ds) // 3]
+    second = next(k for k, i in enumerate(infos) if i["max_der"] >= 2)
+    picks = [int(np.argmax(terms)), int(np.argmax(smem)), second, len(ds) // 3, 2 * len(ds) // 3]
     return ds, infos, list(dict.fromkeys(picks))
 
 
 def test_order6_enumeration_and_tables():
-    """515 order-6 diagrams (the two enumerators agree), every one constructs, and the largest
-    flat table has 5136 terms."""
-    ds, infos, _ = order6_cases()
+    """515 order-6 diagrams (the two enumerators agree), every one constructs, the largest flat
+    table has 5136 terms, and the deepest Fermi derivative any of them needs is the second (the
+    oracle's construction agrees on it)."""
+    ds, infos, picks = order6_cases()
     assert len(ds) == 515 == len(T.enumerate_sigma(6))
     assert max(i["n_terms"] for i in infos) == 5136
+    assert max(i["max_der"] for i in infos) == 2
+    second = next(k for k, i in enumerate(infos) if i["max_der"] >= 2)
+    assert second in picks
+    d = ds[second]
+    assert O.Solution(d["alpha"], eps=d["eps"]).info()["max_der"] == 2
     for i, d in enumerate(ds[::37]):
         S = O.Solution(d["alpha"], eps=d["eps"])
         assert S.info()["terms"] == infos[37 * i]["n_terms"]
@@ -135,9 +143,10 @@ def test_order6_enumeration_and_tables():
 
 def test_order6_forward_and_adjoint_against_oracle(modes):
     """Order-6 tables per sample against the oracle: the forward (generic kernel, program resident
-    or streamed as it fits) and the fused forward + adjoint (the specialised kernel: these tables
-    exceed the generic adjoint's per-thread capacities, so the default mode specialises them at
-    any size) -- values, dSigma/dX and the contracted gradients."""
+    or streamed as it fits) and the fused forward + adjoint -- values, dSigma/dX and the contracted
+    gradients.  The largest tables exceed the generic adjoint's per-thread capacities, so the
+    default mode specialises them at any size; a table the generic adjoint holds (the one with
+    second Fermi derivatives) is checked through both kernel families."""
     ds, infos, picks = order6_cases()
     X = W.matsubara(5.0, 2)
     g = np.array([1.0 + 0.5j, -0.25 + 1.0j])
@@ -147,22 +156,30 @@ def test_order6_forward_and_adjoint_against_oracle(modes):
         pref = (-1.0) ** 6 * (-1.0) ** d["loops"]
         D, S = pair(d, pref)
         m, v, ps = D.forward(LAT, seed, off, n, X, 5.0, per_sample=True)
-        fb = D.forward_backward(LAT, seed, off, n, X, 5.0, g, per_sample=True)
+        runs = [D.forward_backward(LAT, seed, off, n, X, 5.0, g, per_sample=True)]
         torch.cuda.synchronize()
-        assert D.jit_status()["last_used"], i          # the fused pass ran the specialised kernel
+        if i == int(np.argmax([f["n_terms"] for f in infos])):
+            assert D.jit_status()["last_used"], i      # the fused pass ran the specialised kernel
+        if not D.jit_status()["last_used"]:
+            T.set_jit("always")
+            runs.append(D.forward_backward(LAT, seed, off, n, X, 5.0, g, per_sample=True))
+            torch.cuda.synchronize()
+            assert D.jit_status()["last_used"], i
+            T.set_jit("auto")
         ref = S.eval_momenta(LAT, seed, off, n, X, 5.0, per_sample=True, threads=16)
         vb = B.value_bound(ref, LAT)
-        for got in (ps.cpu().numpy(), fb["values"].cpu().numpy()):
-            err = np.abs(got - ref["values"])
-            assert np.all(err <= vb), (i, np.max(err / vb))
         assert np.all(np.abs(m.cpu().numpy() - ref["mean"]) <= RTOL * B.mean_scale(ref, LAT)), i
         dref, dbd = B.oracle_deriv(S, LAT, seed, off, n, X, 5.0, "omega", threads=16)
-        assert np.all(np.abs(fb["dX"].cpu().numpy() - dref) <= dbd), i
-        grads = fb["grads"].cpu().numpy()
-        for k, which in enumerate(("mu", "kx", "ky")):
-            der, dbd = B.oracle_deriv(S, LAT, seed, off, n, X, 5.0, which, threads=16)
-            gref = np.real(np.conj(g)[:, None] * der).sum(axis=0)
-            assert np.all(np.abs(grads[:, k] - gref) <= (np.abs(g)[:, None] * dbd).sum(axis=0)), (i, which)
+        gders = [B.oracle_deriv(S, LAT, seed, off, n, X, 5.0, w, threads=16) for w in ("mu", "kx", "ky")]
+        for got in [ps] + [fb["values"] for fb in runs]:
+            err = np.abs(got.cpu().numpy() - ref["values"])
+            assert np.all(err <= vb), (i, np.max(err / vb))
+        for fb in runs:
+            assert np.all(np.abs(fb["dX"].cpu().numpy() - dref) <= dbd), i
+            grads = fb["grads"].cpu().numpy()
+            for k, (der, gbd) in enumerate(gders):
+                gref = np.real(np.conj(g)[:, None] * der).sum(axis=0)
+                assert np.all(np.abs(grads[:, k] - gref) <= (np.abs(g)[:, None] * gbd).sum(axis=0)), (i, k)
 
 
 def test_order6_program_streamed_where_it_does_not_fit(modes):
