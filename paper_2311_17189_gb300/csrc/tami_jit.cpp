@@ -199,7 +199,7 @@ bool smem_loop_values(const TableHeader& h, bool adj, int block) {
 
 // Threads per block of a specialised kernel.  The Monte Carlo kinds run in lockstep blocks: 512
 // threads ($TAMI_JIT_LOCKSTEP: 256, 512 or 1024), two blocks per SM, whose warps meet at a barrier
-// every $TAMI_JIT_SYNC_OPS pole-DAG steps (default 64) in the straight-line per-sample code, so
+// every $TAMI_JIT_SYNC_OPS pole-DAG steps (default 32) in the straight-line per-sample code, so
 // that the warps of an SM fetch the same stretch of code at a time instead of spreading over the
 // whole kernel.  A large table's kernel is far larger than the instruction caches: the order-6
 // table's fused step went from 790 to 677 ms (it had waited mostly on instruction fetch); the
@@ -217,10 +217,14 @@ int lockstep_block(const TableHeader& h, int kind) {
 // registers at 512 threads per SM halve the large tables' spills and change no step by more than
 // 1 %: the kernels are bound by FP64 issue, not by their local-memory traffic.)
 int blocks_per_sm(int block) { return 1024 / block; }
+// Barrier spacing: on the order-4 table (about 120 pole-DAG steps per sample) a barrier every 32
+// steps gave 47.3 ms per step, every 16 or 64 47.5-47.6 ms, and none at all (a spacing above the
+// table's steps) 61.7 ms -- without a barrier per tile the warps of a block drift apart over the
+// ~100 tiles each block takes and spread over the code again.
 int lockstep_sync_ops() {
   const char* e = std::getenv("TAMI_JIT_SYNC_OPS");
-  const int k = e ? std::atoi(e) : 64;
-  return k >= 4 ? k : 64;
+  const int k = e ? std::atoi(e) : 32;
+  return k >= 4 ? k : 32;
 }
 
 // Each group's product of real-denominator reciprocals RR is formed first and kept for the
