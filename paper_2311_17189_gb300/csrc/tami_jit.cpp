@@ -215,8 +215,15 @@ int lockstep_block(const TableHeader& h, int kind) {
 }
 // Blocks per SM the kernel is compiled for: 1024 threads per SM, 64 registers each.  (128
 // registers at 512 threads per SM halve the large tables' spills and change no step by more than
-// 1 %: the kernels are bound by FP64 issue, not by their local-memory traffic.)
-int blocks_per_sm(int block) { return 1024 / block; }
+// 1 %: the kernels are bound by FP64 issue, not by their local-memory traffic.)  $TAMI_JIT_REGS
+// (80, 128) compiles for fewer resident threads with that many registers each.
+int blocks_per_sm(int block) {
+  const char* e = std::getenv("TAMI_JIT_REGS");
+  const int regs = e ? std::atoi(e) : 64;
+  if (regs <= 64 || regs > 255) return 1024 / block;
+  const int b = 65536 / (block * regs);
+  return b >= 1 ? b : 1;
+}
 // Barrier spacing: on the order-4 table (about 120 pole-DAG steps per sample) a barrier every 32
 // steps gave 47.3 ms per step, every 16 or 64 47.5-47.6 ms, and none at all (a spacing above the
 // table's steps) 61.7 ms -- without a barrier per tile the warps of a block drift apart over the
