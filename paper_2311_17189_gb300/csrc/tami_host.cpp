@@ -763,7 +763,7 @@ int flatten(tami_diagram* d) {
   // add = 1, a multiplication by +-1 or an addition to an exact 0 is free (the tables' integer
   // coefficients are mostly +-1; a kernel that multiplies by them anyway does no useful work
   // there), the reciprocal (estimate + one third-order Newton step) 6, the table-driven exponential
-  // 10 fma + 3 (e^t - 1: 2 more), cos 30 (reduction 9, series 21), sin 21.  Per frequency the count
+  // 8 fma + 3 (e^t - 1: 2 more), cos 30 (reduction 9, series 21), sin 21.  Per frequency the count
   // is that of the imaginary axis; off it the kernels add one more add per complex denominator.
   // Forward sums of the form sum_i c_i y_i (line momenta, energy combinations, pole-DAG nodes) are
   // fma chains from 0, and chains that begin with the same steps share those partial sums: each
@@ -820,7 +820,7 @@ int flatten(tami_diagram* d) {
   }
   fl += cmb.flops;
   for (const Seg& g : segs) {
-    fl += 1.0 + 23.0 + (g.sigma < 0 ? 2.0 : 0.0);       // -beta|x|; e^t; e^t - 1
+    fl += 1.0 + 19.0 + (g.sigma < 0 ? 2.0 : 0.0);       // -beta|x|; e^t; e^t - 1
     fl += g.sigma < 0 ? 7.0 : 8.0;                      // D (1 + y, or -(e^t - 1): free), reciprocal, +-y / D
     for (int v = g.v0; v < g.v1; ++v) {
       const int k = fvs[v].k;

@@ -2,7 +2,7 @@
 bench's roofline divides by time) counted a second way: from the forward kernel source the library
 generates for the same table, statement by statement, under the model's conventions -- fma = 2,
 mul or add = 1, a multiplication by +-1 or an addition to an exact 0 free, the reciprocal 6, the
-exponential 23 (+2 for e^t - 1), a line energy 66 (two cosines of 30, then 6), the Fermi
+exponential 19 (+2 for e^t - 1), a line energy 66 (two cosines of 30, then 6), the Fermi
 derivative polynomials as listed below -- and with every sum written as an fma chain from 0
 (line momenta, energy combinations, pole-DAG nodes) counted once per distinct prefix, since
 chains that begin with the same steps share those partial sums.  No GPU needed: the source is
@@ -68,8 +68,8 @@ def per_sample(src):
     fl += chains(body, r'\bx(\d+) = fma\(([^,]+), E(\d+), x\d+\);', r'double x(\d+) = (-?)E(\d+);')
     bose = body.count("exp_neg<true>") + body.count("tami_seg_bose(")       # inline, or the out-of-line copy
     fermi = body.count("exp_neg<false>") + body.count("tami_seg_fermi(")     # that large tables call
-    fl += (1 + 25 + 6 + 1) * bose                                           # -beta|x|, e^t and e^t - 1, 1/D, y/D
-    fl += (1 + 23 + 7 + 1) * fermi                                          # ... D = 1 + y
+    fl += (1 + 21 + 6 + 1) * bose                                           # -beta|x|, e^t and e^t - 1, 1/D, y/D
+    fl += (1 + 19 + 7 + 1) * fermi                                          # ... D = 1 + y
     fl += sum(POLY.get(int(k), 16 + 4 * int(k)) for k in re.findall(r'fermi_poly\((\d+),', body))
     fl += 6 * len(re.findall(r'rr\d+ = rcp\(', body))
     fl += dag(body)
