@@ -196,23 +196,49 @@ DagPrefixes dag_prefixes(const int* opsb, int n_ops, const double* leafA) {
   int max_node = 0;
   for (int i = 0; i < n_ops; ++i) max_node = std::max(max_node, opsb[2 * i] & kOpbDstMask);
   r.node_value.assign(max_node + 1, -1);
+  r.node_sign.assign(max_node + 1, 1);
   r.op_prefix.resize(n_ops);
+  r.op_sign.resize(n_ops);
   r.op_new.resize(n_ops);
-  std::map<std::tuple<int, int, int, long long>, int> id;   // a leaf keyed by its coefficient's bits
-  std::vector<int> cur(max_node + 1, -1);
+  // (parent, F, operand kind, operand: a leaf by its signed coefficient's bits, a node operand by
+  // its prefix and sign) -> prefix
+  std::map<std::tuple<int, int, int, long long>, int> id;
+  std::vector<int> cur(max_node + 1, -1), cur_sign(max_node + 1, 1);
   for (int i = 0; i < n_ops; ++i) {
     const int x = opsb[2 * i], y = opsb[2 * i + 1];
     const int dst = x & kOpbDstMask, ref = y >> kOpbRefShift;
     const bool leaf = x & kOpbLeaf;
     const int parent = (x & kOpbFirst) ? -1 : cur[dst];
-    const DagPrefix q{parent, y & kOpbFvMask, leaf ? 0 : 1, leaf ? ref : r.node_value[ref]};
-    long long key = q.operand;
-    if (leaf) std::memcpy(&key, &leafA[ref], sizeof key);
+    // the op's partial sum is fma(F, operand, sp * parent prefix) = sign * fma(F, sign * operand,
+    // parent prefix): sign = sp with a parent; a first step takes the operand's sign out instead
+    const int sp = parent < 0 ? 1 : cur_sign[dst];
+    if (leaf ? leafA[ref] == 0.0 : r.node_value[ref] < 0) {
+      // an operand that is identically zero (a leaf whose terms cancelled exactly, or a node made
+      // only of such) adds nothing: the partial sum stays the parent's (none: zero)
+      r.op_prefix[i] = parent;
+      r.op_sign[i] = (signed char)sp;
+      r.op_new[i] = 0;
+      cur[dst] = r.node_value[dst] = parent;
+      cur_sign[dst] = r.node_sign[dst] = (signed char)sp;
+      continue;
+    }
+    const int so = leaf ? (leafA[ref] < 0 ? -1 : 1) : r.node_sign[ref];
+    const int sign = parent < 0 ? so : sp;
+    const DagPrefix q{parent, y & kOpbFvMask, leaf ? 0 : 1, leaf ? ref : r.node_value[ref], leaf ? sign : sign * so};
+    long long key;
+    if (leaf) {
+      const double c = q.osign * leafA[ref];
+      std::memcpy(&key, &c, sizeof key);
+    } else {
+      key = 2LL * q.operand + (q.osign < 0 ? 1 : 0);
+    }
     const auto ins = id.emplace(std::make_tuple(q.parent, q.fv, q.node, key), (int)r.p.size());
     if (ins.second) r.p.push_back(q);
     r.op_prefix[i] = ins.first->second;
+    r.op_sign[i] = (signed char)sign;
     r.op_new[i] = ins.second;
     cur[dst] = r.node_value[dst] = ins.first->second;
+    cur_sign[dst] = r.node_sign[dst] = (signed char)sign;
   }
   return r;
 }
@@ -829,11 +855,15 @@ int flatten(tami_diagram* d) {
   }
   fl += 6.0 * h.n_rden;                                 // real reciprocals
   double dag_bwd = 0.0;                                 // pole DAG, forward and adjoint
+  // groups whose weight is identically zero (every term cancelled): the specialised kernels skip
+  // them, weight, products and adjoint alike
+  std::vector<char> g1_zero(g1s.size(), 0);
   {
     std::vector<int> flat(2 * opsb.size());
     for (size_t i = 0; i < opsb.size(); ++i) { flat[2 * i] = opsb[i].first; flat[2 * i + 1] = opsb[i].second; }
     const DagPrefixes dp = dag_prefixes(flat.data(), (int)opsb.size(), leafA.data());
-    for (const DagPrefix& q : dp.p) fl += step_cost(q.parent < 0, q.node ? 2.0 : leafA[q.operand]);
+    for (size_t g = 0; g < g1s.size(); ++g) g1_zero[g] = dp.node_value[g1_node[g]] < 0;
+    for (const DagPrefix& q : dp.p) fl += step_cost(q.parent < 0, q.node ? 2.0 : q.osign * leafA[q.operand]);
     // adjoint, as the specialised kernels walk it: every group root seeded with its weight's adjoint
     // (one mul per group, counted with the groups below; a second seed of the same root is an fma),
     // then the prefixes in reverse creation order: F_y's adjoint += operand x adjoint, a node
@@ -842,6 +872,7 @@ int flatten(tami_diagram* d) {
     std::vector<char> has(dp.p.size(), 0);
     for (int g = 0; g < (int)g1_node.size() - 1 && g < h.n_g1; ++g) {
       const int rp = dp.node_value[g1_node[g]];
+      if (rp < 0) continue;
       if (has[rp]) dag_bwd += 1.0;
       has[rp] = 1;
     }
@@ -860,8 +891,9 @@ int flatten(tami_diagram* d) {
       }
     }
   }
-  for (auto& g : g1s) {
-    for (auto& pr : g.rd) fl += pr.second;              // frequency-independent denominators
+  for (size_t g = 0; g < g1s.size(); ++g) {
+    if (g1_zero[g]) continue;
+    for (auto& pr : g1s[g].rd) fl += pr.second;         // frequency-independent denominators
     fl += 1.0;
   }
   I.flops_per_sample = fl;
@@ -894,10 +926,12 @@ int flatten(tami_diagram* d) {
     for (int v = g.vk1; v < g.v1; ++v) bl += fvs[v].k + 1 == 2 ? 5.0 : 9.0 + 3.0 * fvs[v].k;
   }
   bl += h.n_cden;                                       // cden adjoints into combinations
-  for (auto& g : g1s) {
+  for (size_t gi = 0; gi < g1s.size(); ++gi) {
     // the group weight W1 = pv RR, with RR (the product of its real-denominator reciprocals) kept
     // from the forward: the root's adjoint wb RR, and each real denominator's adjoint
     // -wb W1 pw rr (wb W1 once per group, the power a product where it is not 1, one fma)
+    if (g1_zero[gi]) continue;
+    const auto& g = g1s[gi];
     if (!g.rd.empty()) bl += 1.0;
     for (auto& pr : g.rd) bl += pr.second == 1 ? 2.0 : 3.0;
     bl += 1.0;

@@ -210,21 +210,28 @@ int guarded(F&& body) {
 }
 // Distinct prefixes of the pole DAG's fma chains (tami_host.cpp).  A node's value is a chain
 // val = fma(F_y, operand, val) from 0 over its ops in program order; chains of different nodes that
-// begin with the same steps share those partial sums.  Every prefix is created by the first op
-// that reaches it, so prefixes come in program order and a node's value is complete before any
-// prefix references it.  Input: the adjoint encoding's ops (pairs {x, y}, kOpb* fields) and the
-// leaf coefficients (leaves with equal coefficients are the same operand).
+// begin with the same steps share those partial sums, and so do chains that are the same steps with
+// every sign flipped: a prefix stands for a partial sum up to its sign (op_sign, node_sign), since
+// fma(F, -a, -c) = -fma(F, a, c) exactly in round-to-nearest (a chain's first product onto +0.0 may
+// differ in the sign of a zero result only).  A prefix's value is fma(F_fv, osign * operand,
+// parent's value), the sign of a node operand's own prefix folded into osign.  Every prefix is
+// created by the first op that reaches it, so prefixes come in program order and a node's value is
+// complete before any prefix references it.  Input: the adjoint encoding's ops (pairs {x, y}, kOpb*
+// fields) and the leaf coefficients (leaves with equal coefficients are the same operand).
 struct DagPrefix {
   int parent;    // prefix this one extends, -1 for a chain's first step
   int fv;        // Fermi value F_y
-  int node;      // 0: operand is leaf coefficient `operand`; 1: the value (prefix) `operand`
+  int node;      // 0: operand is leaf coefficient osign * leafA[operand]; 1: osign * the value (prefix) `operand`
   int operand;
+  int osign;     // +1 or -1
 };
 struct DagPrefixes {
   std::vector<DagPrefix> p;        // creation order
   std::vector<int> op_prefix;      // op -> the prefix it lands on
+  std::vector<signed char> op_sign;    // op's partial sum = op_sign * that prefix's value
   std::vector<char> op_new;        // op creates that prefix
   std::vector<int> node_value;     // node id -> prefix holding its value
+  std::vector<signed char> node_sign;  // node's value = node_sign * that prefix's value
 };
 DagPrefixes dag_prefixes(const int* opsb, int n_ops, const double* leafA);
 // Checks every index and range of a flattened table (tami_validate.cpp); false with the reason.

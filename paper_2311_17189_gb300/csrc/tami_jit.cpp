@@ -248,9 +248,10 @@ bool keep_rr() {
 // as well, with the call-free imul_ftz (IEEE products for normal values; subnormals flush to
 // zero): order-4 step 48.07 -> 47.22 ms.  Larger tables keep them on the FP64 unit: there the
 // integer product's registers double the spills (order 6: 663 -> 730 ms).  $TAMI_JIT_PSMUL=0 keeps
-// every table's per-sample products on the FP64 unit.
+// every table's per-sample products on the FP64 unit, $TAMI_JIT_PSMUL=all moves them for every table.
 bool ps_products(const TableHeader& h) {
   const char* e = std::getenv("TAMI_JIT_PSMUL");
+  if (e && !std::strcmp(e, "all")) return true;   // every table ($TAMI_JIT_PSMUL=all)
   return h.n_ops <= 256 && !(e && !std::strcmp(e, "0"));
 }
 // a * b, on the integer pipes where the per-sample products go there
@@ -624,22 +625,31 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   }
   for (int i = 0; i < h.n_rden; ++i) o("    const double rr%d = rcp(x%d);", i, rden[2 * i]);
   // ---- pole DAG: one variable per distinct prefix of the nodes' fma chains (shared partial sums
-  // once), group weights
+  // once, a chain and its sign-flipped twin one variable, the twin read through a free operand
+  // negation; operands that are identically zero left out, and with them the groups whose terms all
+  // cancelled), group weights
   for (int g = 0; g < h.n_g2; ++g) o("    double W2_%d = 0.0;", g);
   const DagPrefixes dp = dag_prefixes(opsb, h.n_ops, leafA);
+  // a group root's value: its prefix with the root's sign
+  auto root_pv = [&](int gi) {
+    const int nd = g1_node[gi];
+    return std::string(dp.node_sign[nd] < 0 ? "-pv" : "pv") + std::to_string(dp.node_value[nd]);
+  };
   for (int gi = 0; gi < h.n_g1; ++gi) {
     for (int op = g1[4 * gi]; op < g1[4 * gi + 1]; ++op) {
       if (!dp.op_new[op]) continue;
       const int k = dp.op_prefix[op];
       const DagPrefix& q = dp.p[k];
-      const std::string opnd = q.node ? "pv" + std::to_string(q.operand) : lit(leafA[q.operand]);
+      const double c = q.node ? 0.0 : q.osign * leafA[q.operand];
+      const std::string opnd = q.node ? (q.osign < 0 ? "-pv" : "pv") + std::to_string(q.operand) : lit(c);
       const std::string add = q.parent < 0 ? "0.0" : "pv" + std::to_string(q.parent);
-      if (q.parent < 0 && !q.node && (leafA[q.operand] == 1.0 || leafA[q.operand] == -1.0))
-        o("    const double pv%d = %sfv%d;", k, leafA[q.operand] > 0 ? "" : "-", q.fv);   // +-F, no arithmetic
+      if (q.parent < 0 && !q.node && (c == 1.0 || c == -1.0))
+        o("    const double pv%d = %sfv%d;", k, c > 0 ? "" : "-", q.fv);   // +-F, no arithmetic
       else
         o("    const double pv%d = fma(fv%d, %s, %s);", k, q.fv, opnd.c_str(), add.c_str());
       step_sync();
     }
+    if (dp.node_value[g1_node[gi]] < 0) continue;   // every term of the group cancelled: weight 0
     if (keep_rr() && g1[4 * gi + 2] < g1[4 * gi + 3]) {
       bool first = true;
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q)
@@ -649,9 +659,9 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
           else o("    RR_%d *= rr%d;", gi, g1rd[2 * q]);
           first = false;
         }
-      o("    double W1_%d = %s;", gi, PM("pv" + std::to_string(dp.node_value[g1_node[gi]]), "RR_" + std::to_string(gi)).c_str());
+      o("    double W1_%d = %s;", gi, PM(root_pv(gi), "RR_" + std::to_string(gi)).c_str());
     } else {
-      o("    double W1_%d = pv%d;", gi, dp.node_value[g1_node[gi]]);
+      o("    double W1_%d = %s;", gi, root_pv(gi).c_str());
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q)
         for (int pw = g1rd[2 * q + 1]; pw > 0; --pw) {
           if (ps) o("    W1_%d = imul_ftz(W1_%d, rr%d);", gi, gi, g1rd[2 * q]);
@@ -720,9 +730,12 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
     std::vector<char> has(dp.p.size(), 0);
     for (int gi = h.n_g1 - 1; gi >= 0; --gi) {
       const int rp = dp.node_value[g1_node[gi]];
+      if (rp < 0) continue;   // a zero weight: no adjoint to pass on
       if (!has[rp]) o("    double bp%d;", rp);
       o("    {");
       const bool kept = keep_rr() && g1[4 * gi + 2] < g1[4 * gi + 3];
+      // wb: the adjoint of the root's value; the root's prefix gets it with the root's sign
+      const char* rs = dp.node_sign[g1_node[gi]] < 0 ? "-" : "";
       if (kept) o("      const double wb = Wb2_%d; const double RR = RR_%d;", g1_tgt[gi], gi);
       else o("      const double wb = Wb2_%d; double RR = 1.0;", g1_tgt[gi]);
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
@@ -736,8 +749,8 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
           o("      xbar%d -= wb * W1_%d * %s * rr%d;", rden[2 * i], gi, lit((double)pw).c_str(), i);
         }
       }
-      if (has[rp]) o("      bp%d = fma(wb, RR, bp%d);", rp, rp);
-      else o("      bp%d = %s;", rp, PM("wb", "RR").c_str());
+      if (has[rp]) o("      bp%d = fma(%swb, RR, bp%d);", rp, rs, rp);
+      else o("      bp%d = %s;", rp, PM(std::string(rs) + "wb", "RR").c_str());
       has[rp] = 1;
       o("    }");
     }
@@ -745,13 +758,14 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       if (!has[k]) continue;
       step_sync();
       const DagPrefix& q = dp.p[k];
-      if (q.node) {
-        o("    fvbar%d = fma(pv%d, bp%d, fvbar%d);", q.fv, q.operand, k, q.fv);
-        if (has[q.operand]) o("    bp%d = fma(fv%d, bp%d, bp%d);", q.operand, q.fv, k, q.operand);
-        else o("    double bp%d = %s;", q.operand, PM("fv" + std::to_string(q.fv), "bp" + std::to_string(k)).c_str());
+      if (q.node) {   // the operand enters with its sign osign: so do both of its adjoint terms
+        const char* os = q.osign < 0 ? "-" : "";
+        o("    fvbar%d = fma(%spv%d, bp%d, fvbar%d);", q.fv, os, q.operand, k, q.fv);
+        if (has[q.operand]) o("    bp%d = fma(%sfv%d, bp%d, bp%d);", q.operand, os, q.fv, k, q.operand);
+        else o("    double bp%d = %s;", q.operand, PM(os + ("fv" + std::to_string(q.fv)), "bp" + std::to_string(k)).c_str());
         has[q.operand] = 1;
       } else {
-        o("    fvbar%d = fma(%s, bp%d, fvbar%d);", q.fv, lit(leafA[q.operand]).c_str(), k, q.fv);
+        o("    fvbar%d = fma(%s, bp%d, fvbar%d);", q.fv, lit(q.osign * leafA[q.operand]).c_str(), k, q.fv);
       }
       if (q.parent >= 0) {
         if (has[q.parent]) o("    bp%d += bp%d;", q.parent, k);

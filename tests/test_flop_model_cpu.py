@@ -46,7 +46,8 @@ def chains(body, pattern, start=None):
 
 def dag(body):
     """Pole-DAG prefixes: const double pv<k> = fma(fv<y>, OPERAND, 0.0 | pv<parent>), an operand
-    being a leaf coefficient or another prefix (a node's value); each written once."""
+    being a leaf coefficient or another prefix (a node's value, possibly negated: a free operand
+    sign); each written once."""
     fl, seen = 0, set()
     for m in re.finditer(r'const double pv(\d+) = (-?)fv(\d+);', body):   # +-F: a unit leaf, no arithmetic
         assert m.group(1) not in seen
@@ -55,7 +56,7 @@ def dag(body):
         k, opnd, add = m.group(1), m.group(3).strip(), m.group(4).strip()
         assert k not in seen
         seen.add(k)
-        fl += step(add == "0.0", "x" if opnd.startswith("pv") else opnd)
+        fl += step(add == "0.0", "x" if opnd.lstrip("-").startswith("pv") else opnd)
     return fl
 
 
@@ -77,7 +78,7 @@ def per_sample(src):
     fl += len(re.findall(r'W1_\d+ (?:\*= rr\d+|= imul_ftz\(W1_\d+, rr\d+\));', body))
     fl += len(re.findall(r'W2_\d+ \+= W1_\d+;', body))
     fl += len(re.findall(r'RR_\d+ (?:\*= rr\d+|= imul_ftz\(RR_\d+, rr\d+\));', body))
-    fl += len(re.findall(r'double W1_\d+ = (?:pv\d+ \* RR_\d+|imul_ftz\(pv\d+, RR_\d+\));', body))
+    fl += len(re.findall(r'double W1_\d+ = (?:-?pv\d+ \* RR_\d+|imul_ftz\(-?pv\d+, RR_\d+\));', body))
     return fl
 
 
@@ -120,3 +121,47 @@ def test_shared_prefixes_are_counted_once():
     src = T.Diagram(d["alpha"], eps=d["eps"]).jit_source("forward")
     parents = re.findall(r'const double pv\d+ = fma\(fv\d+, [^,]+, (pv\d+)\);', src)
     assert max(parents.count(p) for p in set(parents)) >= 2
+
+
+def signed_prefix_keys(src):
+    """Each pole-DAG prefix of a generated kernel as a structural key up to its sign: a chain's
+    partial sum and the same steps with every sign flipped are one value (fma(F, -a, -c) =
+    -fma(F, a, c) in round-to-nearest), so the generator writes only one of them."""
+    canon, keys = {}, []
+
+    def operand(tok):
+        tok = tok.strip()
+        if tok.startswith("pv") or tok.startswith("-pv"):
+            s, c = canon[tok.lstrip("-")]
+            return ("node", c), (-s if tok.startswith("-") else s)
+        v = float.fromhex(tok)
+        return ("leaf", abs(v)), (1 if v > 0 else -1)
+
+    for m in re.finditer(r'const double (pv\d+) = (?:(-?)fv(\d+)|fma\(fv(\d+), ([^,]+), ([^)]+)\));', src):
+        if m.group(3) is not None:                     # +-F: a chain's first step on a unit leaf
+            key, sign = ("F", m.group(3)), -1 if m.group(2) else 1
+        else:
+            (ko, so) = operand(m.group(5))
+            add = m.group(6).strip()
+            if add == "0.0":
+                key, sign = ("first", m.group(4), ko), so
+            else:
+                sp, cp = canon[add]
+                key, sign = ("step", cp, m.group(4), ko, so * sp), sp
+        keys.append(key)
+        canon[m.group(1)] = (sign, len(keys) - 1 if key not in keys[:-1] else keys.index(key))
+    return keys
+
+
+def test_no_prefix_is_another_with_its_signs_flipped():
+    """Every prefix the generated kernels write is distinct up to sign and none multiplies a zero
+    coefficient (all 87 tables), and the bench's order-4 table does use flipped prefixes (a negated
+    node operand or root)."""
+    for name, D in tables():
+        src = D.jit_source("forward")
+        keys = signed_prefix_keys(src)
+        assert len(keys) == len(set(keys)), name
+        assert "0x0p+0" not in src, name      # a leaf whose terms cancelled exactly is left out
+    d = next(x for x in T.enumerate_sigma(4) if x["code"] == tuple(W.ORDER4["code"]))
+    src = T.Diagram(d["alpha"], eps=d["eps"]).jit_source("fused")
+    assert re.search(r'fma\(fv\d+, -pv\d+,', src) or re.search(r'W1_\d+ = (?:imul_ftz\()?-pv', src)
