@@ -334,7 +334,8 @@ int tami_jit_source(const tami_diagram* d, int kind, char* buf, size_t cap, size
  * captures [queue reset, persistent kernel, reduction] into a CUDA graph on the current device.
  * chunk_tiles = 0 lets an autotuner pick the chunk size by timing graph replays with typical
  * inputs; the choice is cached per (GPU, batch signature) in memory and in a text file
- * ($TAMI_TUNE_CACHE, default $HOME/.cache/libtami_autotune.txt).
+ * ($TAMI_TUNE_CACHE, default $HOME/.cache/libtami_autotune.txt); $TAMI_TUNE_LOG names a file that
+ * each timed candidate (chunk, grid, items, milliseconds per replay) is appended to.
  * Specialised diagrams (see tami_set_jit): in mode "always" every diagram, in "auto" each diagram
  * with at least 2^20 samples whose kernel builds, runs its own generated forward kernel instead of
  * being cut into items: the plan compiles those kernels (on parallel host threads, cached with the

@@ -464,6 +464,18 @@ void tuning_inputs(tami_batch* b) {
   cudaMemcpy(b->mem + b->L.X, X.data(), sizeof(double) * X.size(), cudaMemcpyHostToDevice);
 }
 
+// Each timed candidate of a tuning run is appended to $TAMI_TUNE_LOG, when it is set, as one line
+// "<plan key> chunk=<tiles per item> grid=<blocks> items=<n> ms=<per replay>", for sweep records.
+void tune_log(const std::string& key, const tami_batch* b, double ms) {
+  const char* p = std::getenv("TAMI_TUNE_LOG");
+  if (!p || !*p) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (FILE* f = std::fopen(p, "a")) {
+    std::fprintf(f, "%s chunk=%d grid=%d items=%d ms=%.4f\n", key.c_str(), b->chunk, b->grid, b->n_items, ms);
+    std::fclose(f);
+  }
+}
+
 double time_replays(tami_batch* b, int reps) {
   tuning_inputs(b);
   cudaEvent_t e0, e1;
@@ -587,6 +599,7 @@ int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* sampl
         rc = build(b, ch, 0, false);
         if (rc) break;
         double ms = time_replays(b, 2);
+        tune_log(key, b, ms);
         if (ms < best) { best = ms; best_c = ch; }
       }
       // then the residency at that work-item size: 1, 2, 4 ... blocks per SM up to the resident
@@ -598,6 +611,7 @@ int tami_batch_plan(const tami_diagram* const* ds, int n_d, const int64_t* sampl
           rc = build(b, best_c, per * dp.sms, false);
           if (rc) break;
           double ms = time_replays(b, 2);
+          tune_log(key, b, ms);
           if (ms < best) { best = ms; best_g = per * dp.sms; }
         }
       }

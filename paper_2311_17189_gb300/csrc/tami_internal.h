@@ -214,7 +214,9 @@ int guarded(F&& body) {
 // every sign flipped: a prefix stands for a partial sum up to its sign (op_sign, node_sign), since
 // fma(F, -a, -c) = -fma(F, a, c) exactly in round-to-nearest (a chain's first product onto +0.0 may
 // differ in the sign of a zero result only).  A prefix's value is fma(F_fv, osign * operand,
-// parent's value), the sign of a node operand's own prefix folded into osign.  Every prefix is
+// parent's value), the sign of a node operand's own prefix folded into osign.  An operand that is
+// identically zero (a leaf coefficient 0: terms that cancelled exactly when merged; a node made only
+// of such) adds nothing and creates no prefix.  Every prefix is
 // created by the first op that reaches it, so prefixes come in program order and a node's value is
 // complete before any prefix references it.  Input: the adjoint encoding's ops (pairs {x, y}, kOpb*
 // fields) and the leaf coefficients (leaves with equal coefficients are the same operand).
@@ -227,10 +229,10 @@ struct DagPrefix {
 };
 struct DagPrefixes {
   std::vector<DagPrefix> p;        // creation order
-  std::vector<int> op_prefix;      // op -> the prefix it lands on
+  std::vector<int> op_prefix;      // op -> the prefix it lands on (-1: the partial sum is still zero)
   std::vector<signed char> op_sign;    // op's partial sum = op_sign * that prefix's value
   std::vector<char> op_new;        // op creates that prefix
-  std::vector<int> node_value;     // node id -> prefix holding its value
+  std::vector<int> node_value;     // node id -> prefix holding its value (-1: identically zero)
   std::vector<signed char> node_sign;  // node's value = node_sign * that prefix's value
 };
 DagPrefixes dag_prefixes(const int* opsb, int n_ops, const double* leafA);

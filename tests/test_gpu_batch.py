@@ -205,6 +205,7 @@ def test_batch_matches_single_launches_and_is_deterministic():
 
 def test_autotune_and_cache(tmp_path, monkeypatch):
     monkeypatch.setenv("TAMI_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    monkeypatch.setenv("TAMI_TUNE_LOG", str(tmp_path / "tune.log"))
     lib, orc, counts, seeds = mixed_batch()
     counts = [c * 40 for c in counts]
     X = W.matsubara(BETA, 8)
@@ -213,9 +214,15 @@ def test_autotune_and_cache(tmp_path, monkeypatch):
     assert i1["chunk_tiles"] >= 1 and i1["items"] >= 1 and i1["grid"] >= 1
     text = (tmp_path / "tune.txt").read_text()
     assert len(text.strip().splitlines()) == 1
+    # the sweep record: every timed candidate, the chosen (chunk, grid) among them
+    log = (tmp_path / "tune.log").read_text().strip().splitlines()
+    cands = [dict(kv.split("=") for kv in line.split()[1:]) for line in log]
+    assert len(cands) >= 2 and all(float(c["ms"]) > 0 for c in cands)
+    assert any(int(c["chunk"]) == i1["chunk_tiles"] and int(c["grid"]) == i1["grid"] for c in cands)
     B2 = T.Batch(lib, counts, seeds, len(X), chunk_tiles=0)          # cache hit: no new line
     assert B2.info()["chunk_tiles"] == i1["chunk_tiles"]
     assert (tmp_path / "tune.txt").read_text() == text
+    assert len((tmp_path / "tune.log").read_text().strip().splitlines()) == len(log)   # nothing timed
     m1, _ = B1.launch(LAT, X, BETA)
     m2, _ = B2.launch(LAT, X, BETA)
     assert torch.equal(m1, m2)
