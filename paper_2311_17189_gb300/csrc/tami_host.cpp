@@ -796,12 +796,10 @@ int flatten(tami_diagram* d) {
   // distinct prefix is counted once, as a compiled kernel evaluates it once.  The reverse passes
   // share nothing (every adjoint differs) and count every step.
   auto unit = [](double c) { return c == 1.0 || c == -1.0; };
+  // the derivative polynomial of order k >= 2 (fermi_poly: g h, h - g, the powers of beta, g and h,
+  // the Eulerian-number sum)
+  auto poly_cost = [](int k) { return k == 2 ? 5.0 : k == 3 ? 9.0 : k == 4 ? 17.0 : 23.0; };
   auto step_cost = [&](bool first, double c) { return first ? (unit(c) ? 0.0 : 1.0) : (unit(c) ? 1.0 : 2.0); };
-  auto lin = [&](const std::vector<double>& cs) {     // sum_i c_i y_i as an fma chain from 0
-    double f = 0.0;
-    for (size_t i = 0; i < cs.size(); ++i) f += step_cost(i == 0, cs[i]);
-    return f;
-  };
   struct Prefixes {     // (prefix, variable, operand kind, operand) -> prefix id; cost of the new ones
     std::map<std::tuple<int, int, int, long long>, int> id;
     double flops = 0.0;
@@ -831,33 +829,43 @@ int flatten(tami_diagram* d) {
   fl += h.n_rep * (2.0 * 30.0 + 6.0);                   // cos of both components, energy
   const double energy_flops = fl;                       // what a saved-rows adjoint does not redo
   const double ext_grad_flops = h.n_rep_ext * 2.0 * (21.0 + 3.0);   // sin and G = (2t + 4t' cos) sin per component
-  double combo_fl = 0.0;                                // energy combinations (every step: the reverse pass)
-  Prefixes cmb;                                         // (distinct prefixes: the forward)
+  Prefixes cmb;                                         // energy combinations (distinct prefixes)
   for (const Vec& c : combos) {
-    std::vector<double> cs;
+    bool first = true;
     int p = 0;
     for (int j = 0; j < N; ++j)
       if (c[j]) {
         const double cj = (double)c[j];
-        p = cmb.step(p, j, 0, bits(cj), step_cost(cs.empty(), cj));
-        cs.push_back(cj);
+        p = cmb.step(p, j, 0, bits(cj), step_cost(first, cj));
+        first = false;
       }
-    combo_fl += lin(cs);
   }
   fl += cmb.flops;
   for (const Seg& g : segs) {
     fl += 1.0 + 19.0 + (g.sigma < 0 ? 2.0 : 0.0);       // -beta|x|; e^t; e^t - 1
     fl += g.sigma < 0 ? 7.0 : 8.0;                      // D (1 + y, or -(e^t - 1): free), reciprocal, +-y / D
+    bool k1 = false;                                    // -beta g h once per segment: every k = 1 value
     for (int v = g.v0; v < g.v1; ++v) {
       const int k = fvs[v].k;
-      fl += k == 0 ? 0.0 : k == 1 ? 2.0 : k == 2 ? 5.0 : k == 3 ? 9.0 : 16.0 + 4.0 * k;
+      k1 |= k == 1;
+      fl += k <= 1 ? 0.0 : poly_cost(k);
     }
+    if (k1) fl += 2.0;
   }
   fl += 6.0 * h.n_rden;                                 // real reciprocals
   double dag_bwd = 0.0;                                 // pole DAG, forward and adjoint
   // groups whose weight is identically zero (every term cancelled): the specialised kernels skip
   // them, weight, products and adjoint alike
   std::vector<char> g1_zero(g1s.size(), 0);
+  // The reverse sweep's sums take their first term as an assignment (a copy, free, or a product),
+  // every later term as an add or an fma, as the specialised kernels write them: `sum_term` counts
+  // one term of a sum whose has-a-value flag is h.
+  auto sum_term = [](char& h, double first_cost, double later_cost) {
+    const double c = h ? later_cost : first_cost;
+    h = 1;
+    return c;
+  };
+  std::vector<char> hfv(fvs.size(), 0);                 // Fermi values whose adjoint has a term
   {
     std::vector<int> flat(2 * opsb.size());
     for (size_t i = 0; i < opsb.size(); ++i) { flat[2 * i] = opsb[i].first; flat[2 * i + 1] = opsb[i].second; }
@@ -867,8 +875,8 @@ int flatten(tami_diagram* d) {
     // adjoint, as the specialised kernels walk it: every group root seeded with its weight's adjoint
     // (one mul per group, counted with the groups below; a second seed of the same root is an fma),
     // then the prefixes in reverse creation order: F_y's adjoint += operand x adjoint, a node
-    // operand's value gets F_y x adjoint, and the adjoint passes to the parent prefix (a copy where
-    // that is the parent's first contribution, else an add)
+    // operand's value gets F_y x adjoint, and the adjoint passes to the parent prefix (each a sum
+    // whose first term is a copy or a product)
     std::vector<char> has(dp.p.size(), 0);
     for (int g = 0; g < (int)g1_node.size() - 1 && g < h.n_g1; ++g) {
       const int rp = dp.node_value[g1_node[g]];
@@ -880,10 +888,10 @@ int flatten(tami_diagram* d) {
       if (!has[k]) continue;
       const DagPrefix& q = dp.p[k];
       if (q.node) {
-        dag_bwd += 2.0 + (has[q.operand] ? 2.0 : 1.0);
-        has[q.operand] = 1;
+        dag_bwd += sum_term(hfv[q.fv], 1.0, 2.0) + sum_term(has[q.operand], 1.0, 2.0);
       } else {
-        dag_bwd += unit(leafA[q.operand]) ? 1.0 : 2.0;
+        const bool u1 = unit(leafA[q.operand]);
+        dag_bwd += sum_term(hfv[q.fv], u1 ? 0.0 : 1.0, u1 ? 1.0 : 2.0);
       }
       if (q.parent >= 0) {
         if (has[q.parent]) dag_bwd += 1.0;
@@ -891,10 +899,13 @@ int flatten(tami_diagram* d) {
       }
     }
   }
-  for (size_t g = 0; g < g1s.size(); ++g) {
-    if (g1_zero[g]) continue;
-    for (auto& pr : g1s[g].rd) fl += pr.second;         // frequency-independent denominators
-    fl += 1.0;
+  {
+    std::set<int> w2_set;                               // W2 takes its first group weight as a copy
+    for (size_t g = 0; g < g1s.size(); ++g) {
+      if (g1_zero[g]) continue;
+      for (auto& pr : g1s[g].rd) fl += pr.second;       // frequency-independent denominators
+      if (!w2_set.insert(g1s[g].g2).second) fl += 1.0;
+    }
   }
   I.flops_per_sample = fl;
   I.energy_in_flops_per_sample = fl - energy_flops;
@@ -922,28 +933,48 @@ int flatten(tami_diagram* d) {
   // frequency the phase-2 products with the adjoint contractions, then the reverse sweep
   double bl = fl;
   for (const Seg& g : segs) {                           // next derivative of every Fermi value
-    if (g.vk1 > g.v0) bl += 2.0;                        // -beta g h, shared by the segment's k = 0 values
-    for (int v = g.vk1; v < g.v1; ++v) bl += fvs[v].k + 1 == 2 ? 5.0 : 9.0 + 3.0 * fvs[v].k;
+    bool k1 = false;                                    // -beta g h, shared by the segment's k = 0 values
+    for (int v = g.vk1; v < g.v1; ++v) k1 |= fvs[v].k == 1;   // (counted above where k = 1 values use it)
+    if (g.vk1 > g.v0 && !k1) bl += 2.0;
+    for (int v = g.vk1; v < g.v1; ++v) bl += poly_cost(fvs[v].k + 1);
   }
-  bl += h.n_cden;                                       // cden adjoints into combinations
+  std::vector<char> hx(combos.size(), 0);              // combinations whose adjoint has a term
+  for (const CdKey& c : cdens) bl += sum_term(hx[c.u], 0.0, 1.0);   // cden adjoints into combinations
   for (size_t gi = 0; gi < g1s.size(); ++gi) {
     // the group weight W1 = pv RR, with RR (the product of its real-denominator reciprocals) kept
     // from the forward: the root's adjoint wb RR, and each real denominator's adjoint
-    // -wb W1 pw rr (wb W1 once per group, the power a product where it is not 1, one fma)
+    // -wb W1 pw rr (wb W1 once per group, the power a product where it is not 1, one fma or, for the
+    // denominator's first term, a product)
     if (g1_zero[gi]) continue;
     const auto& g = g1s[gi];
     if (!g.rd.empty()) bl += 1.0;
-    for (auto& pr : g.rd) bl += pr.second == 1 ? 2.0 : 3.0;
+    for (auto& pr : g.rd) bl += (pr.second == 1 ? 0.0 : 1.0) + sum_term(hx[rdens[pr.first]], 1.0, 2.0);
     bl += 1.0;
   }
   bl += dag_bwd;
   bl += h.n_rep_ext * 2.0 * 21.0;                       // sin of both components where k_ext enters (series)
   for (auto& g : g2s) for (auto& pr : g) bl += pr.second == 1 ? 0.0 : 1.0;   // p W per group factor
-  bl += 2.0 * h.n_fv + h.n_fseg;                        // fvbar P_{k+1} summed per segment into x
-  bl += combo_fl;                                       // x -> E (the same coefficients)
-  bl += h.n_rep;                                        // E -> mu
-  for (int r = 0; r < h.n_rep_ext; ++r)                 // E -> k_ext: (-Ebar a_ext) G per component
-    bl += 4.0 + (unit((double)d->alpha[repl[r] * nv + m]) ? 0.0 : 1.0);
+  for (const Seg& g : segs) {                           // +-fvbar P_{k+1} summed per segment into x
+    char any = 0;
+    double c = 0.0;
+    for (int v = g.v0; v < g.v1; ++v)
+      if (hfv[v]) c += sum_term(any, 1.0, 2.0);
+    if (any) bl += c + sum_term(hx[g.combo], 0.0, 1.0);
+  }
+  {
+    std::vector<char> hE(N, 0);                          // x -> E (the combinations' coefficients)
+    for (size_t u = 0; u < combos.size(); ++u) {
+      if (!hx[u]) continue;
+      for (int j = 0; j < N; ++j)
+        if (combos[u][j]) {
+          const bool u1 = unit((double)combos[u][j]);
+          bl += sum_term(hE[j], u1 ? 0.0 : 1.0, u1 ? 1.0 : 2.0);
+        }
+    }
+  }
+  bl += h.n_rep - 1;                                    // E -> mu
+  for (int r = 0; r < h.n_rep_ext; ++r)                 // E -> k_ext: (-Ebar a_ext) G per component,
+    bl += (r ? 4.0 : 2.0) + (unit((double)d->alpha[repl[r] * nv + m]) ? 0.0 : 1.0);   // the first a product
   I.bwd_flops_per_sample = bl;
   I.fwd_save_flops_per_sample = I.flops_per_sample + ext_grad_flops;
   I.bwd_saved_flops_per_sample = bl - energy_flops - ext_grad_flops;

@@ -248,11 +248,27 @@ bool keep_rr() {
 // as well, with the call-free imul_ftz (IEEE products for normal values; subnormals flush to
 // zero): order-4 step 48.07 -> 47.22 ms.  Larger tables keep them on the FP64 unit: there the
 // integer product's registers double the spills (order 6: 663 -> 730 ms).  $TAMI_JIT_PSMUL=0 keeps
-// every table's per-sample products on the FP64 unit, $TAMI_JIT_PSMUL=all moves them for every table.
-bool ps_products(const TableHeader& h) {
+// every table's per-sample products on the FP64 unit, $TAMI_JIT_PSMUL=all moves them for every table,
+// $TAMI_JIT_PSMUL=fwd every table's forward part (values and weights; the reverse sweep keeps the
+// default).
+bool ps_products(const TableHeader& h, bool reverse = false) {
   const char* e = std::getenv("TAMI_JIT_PSMUL");
   if (e && !std::strcmp(e, "all")) return true;   // every table ($TAMI_JIT_PSMUL=all)
+  if (e && !std::strcmp(e, "fwd") && !reverse) return true;   // every table's forward part
   return h.n_ops <= 256 && !(e && !std::strcmp(e, "0"));
+}
+// The reverse sweep's sums (combination, Fermi-value and energy adjoints, each segment's sum) take
+// their first term as an assignment, a copy or a product, instead of an add or fma onto 0.0 that the
+// compiler must keep; $TAMI_JIT_FIRSTTERM=0 starts them from 0.0 instead.
+bool first_terms() {
+  const char* e = std::getenv("TAMI_JIT_FIRSTTERM");
+  return !(e && !std::strcmp(e, "0"));
+}
+// With the per-sample products on the integer pipes, a pole-DAG chain's first step F * operand is
+// one of them; $TAMI_JIT_PSFIRST=0 keeps it an fma onto 0.0 on the FP64 unit.
+bool ps_first_steps() {
+  const char* e = std::getenv("TAMI_JIT_PSFIRST");
+  return !(e && !std::strcmp(e, "0"));
 }
 // a * b, on the integer pipes where the per-sample products go there
 std::string pmul(bool ps, const std::string& a, const std::string& b) {
@@ -385,7 +401,7 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   const bool seg_calls = h.n_ops > 256;
   // (the energy-input kind keeps its per-row products on the FP64 unit: 1.093 -> 1.125 ms with them
   // on the integer pipes on the paper's energy-input example)
-  const bool ps = ps_products(h) && kind != kKindEnergy;
+  bool ps = ps_products(h) && kind != kKindEnergy;   // the reverse sweep may set it otherwise
   auto PM = [&](const std::string& a, const std::string& b) { return pmul(ps, a, b); };
   const Table t{h, blob};
   const bool energy = kind == kKindEnergy;
@@ -595,21 +611,25 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   for (int b = 0; b < h.n_fseg; ++b) {
     const int* sgm = fseg + 8 * b;
     const bool bose = b < h.n_fseg_bose;
+    // d1 = -beta g h: the k = 0 values' derivatives (adjoint) and every k = 1 value of the segment
+    // (g and h alike: the first derivative is symmetric in them)
+    bool has_k1 = false;
+    for (int v = sgm[3]; v < sgm[4]; ++v) has_k1 |= fvr[2 * v + 1] == 1;
+    const std::string d1 = (adj || has_k1)
+        ? PM("-beta", ps ? PM("sg" + std::to_string(b) + "_g", "sg" + std::to_string(b) + "_h")
+                         : "(sg" + std::to_string(b) + "_g * sg" + std::to_string(b) + "_h)")
+        : std::string("0.0");
     o("    double sg%d_g, sg%d_h, sg%d_d1;", b, b, b);
     if (seg_calls) {
       o("    { const double2 gh = tami_seg_%s(x%d, beta);", bose ? "bose" : "fermi", sgm[0]);
-      o("      sg%d_g = gh.x; sg%d_h = gh.y; sg%d_d1 = %s; }", b, b, b,
-        adj ? PM("-beta", ps ? PM("sg" + std::to_string(b) + "_g", "sg" + std::to_string(b) + "_h")
-                                 : "(sg" + std::to_string(b) + "_g * sg" + std::to_string(b) + "_h)").c_str() : "0.0");
+      o("      sg%d_g = gh.x; sg%d_h = gh.y; sg%d_d1 = %s; }", b, b, b, d1.c_str());
     } else {
     o("    { const double xv = x%d; double em = 0.0;", sgm[0]);
     o("      const double y = exp_neg<%s>(%s, em); (void)em;", bose ? "true" : "false", PM("-beta", "fabs(xv)").c_str());
     o("      const double rD = rcp(%s);", bose ? "-em" : "1.0 + y");
     o("      const double t2 = %s;", PM(bose ? "(-y)" : "(y)", "rD").c_str());
     o("      const bool neg = __double_as_longlong(xv) <= 0;");
-    o("      sg%d_g = neg ? rD : t2; sg%d_h = neg ? t2 : rD; sg%d_d1 = %s; }", b, b, b,
-      adj ? PM("-beta", ps ? PM("sg" + std::to_string(b) + "_g", "sg" + std::to_string(b) + "_h")
-                                 : "(sg" + std::to_string(b) + "_g * sg" + std::to_string(b) + "_h)").c_str() : "0.0");
+    o("      sg%d_g = neg ? rD : t2; sg%d_h = neg ? t2 : rD; sg%d_d1 = %s; }", b, b, b, d1.c_str());
     }
     for (int v = sgm[2]; v < sgm[3]; ++v) {
       o("    const double fv%d = sg%d_%c;", v, b, fvr[2 * v] > 0 ? 'g' : 'h');
@@ -619,7 +639,8 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       const bool pos = fvr[2 * v] > 0;
       const int k = fvr[2 * v + 1];
       const char g = pos ? 'g' : 'h', hh = pos ? 'h' : 'g';
-      o("    const double fv%d = fermi_poly(%d, sg%d_%c, sg%d_%c, beta);", v, k, b, g, b, hh);
+      if (k == 1) o("    const double fv%d = sg%d_d1;", v, b);
+      else o("    const double fv%d = fermi_poly(%d, sg%d_%c, sg%d_%c, beta);", v, k, b, g, b, hh);
       if (adj) o("    const double fvd%d = fermi_poly(%d, sg%d_%c, sg%d_%c, beta);", v, k + 1, b, g, b, hh);
     }
   }
@@ -628,7 +649,11 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   // once, a chain and its sign-flipped twin one variable, the twin read through a free operand
   // negation; operands that are identically zero left out, and with them the groups whose terms all
   // cancelled), group weights
-  for (int g = 0; g < h.n_g2; ++g) o("    double W2_%d = 0.0;", g);
+  // Sums take their first term as an assignment (a copy or a product) instead of an add onto 0.0,
+  // which the compiler must keep (0.0 + x is not x for x = -0.0): W2 here, and the reverse sweep's
+  // adjoints below.  A sum that receives nothing is set to 0.0 where it is read.
+  for (int g = 0; g < h.n_g2; ++g) o("    double W2_%d;", g);
+  std::vector<char> has_w2(h.n_g2, 0);
   const DagPrefixes dp = dag_prefixes(opsb, h.n_ops, leafA);
   // a group root's value: its prefix with the root's sign
   auto root_pv = [&](int gi) {
@@ -645,6 +670,8 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       const std::string add = q.parent < 0 ? "0.0" : "pv" + std::to_string(q.parent);
       if (q.parent < 0 && !q.node && (c == 1.0 || c == -1.0))
         o("    const double pv%d = %sfv%d;", k, c > 0 ? "" : "-", q.fv);   // +-F, no arithmetic
+      else if (q.parent < 0 && ps && ps_first_steps())   // a chain's first step is a product
+        o("    const double pv%d = %s;", k, PM("fv" + std::to_string(q.fv), opnd).c_str());
       else
         o("    const double pv%d = fma(fv%d, %s, %s);", k, q.fv, opnd.c_str(), add.c_str());
       step_sync();
@@ -668,8 +695,11 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
           else o("    W1_%d *= rr%d;", gi, g1rd[2 * q]);
         }
     }
-    o("    W2_%d += W1_%d;", g1_tgt[gi], gi);
+    o(has_w2[g1_tgt[gi]] ? "    W2_%d += W1_%d;" : "    W2_%d = W1_%d;", g1_tgt[gi], gi);
+    has_w2[g1_tgt[gi]] = 1;
   }
+  for (int g = 0; g < h.n_g2; ++g)
+    if (!has_w2[g]) o("    W2_%d = 0.0;", g);
   for (int c = 0; c < h.n_cden; ++c) o("    const double b%d = %sx%d;", c, cden[2 * c + 1] > 0 ? "" : "-", cden[2 * c]);
   if (adj) {
     for (int g = 0; g < h.n_g2; ++g) {
@@ -722,9 +752,16 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
   if (adj) {
     if (h.g2_const) o("    Wb2_0 = s_gsum;");
     // ---- reverse sweep
-    for (int u = 0; u < h.n_combo; ++u) o("    double xbar%d = 0.0;", u);
-    for (int v = 0; v < h.n_fv; ++v) o("    double fvbar%d = 0.0;", v);
-    for (int c = 0; c < h.n_cden; ++c) o("    xbar%d += %sbb%d;", cden[2 * c], cden[2 * c + 1] > 0 ? "" : "-", c);
+    ps = ps_products(h, true) && kind != kKindEnergy;
+    const bool ft = first_terms();
+    for (int u = 0; u < h.n_combo; ++u) o(ft ? "    double xbar%d;" : "    double xbar%d = 0.0;", u);
+    for (int v = 0; v < h.n_fv; ++v) o(ft ? "    double fvbar%d;" : "    double fvbar%d = 0.0;", v);
+    std::vector<char> hx(h.n_combo, ft ? 0 : 1), hf(h.n_fv, ft ? 0 : 1);   // the adjoint has its first term
+    for (int c = 0; c < h.n_cden; ++c) {
+      const int u = cden[2 * c];
+      o(hx[u] ? "    xbar%d += %sbb%d;" : "    xbar%d = %sbb%d;", u, cden[2 * c + 1] > 0 ? "" : "-", c);
+      hx[u] = 1;
+    }
     // pole DAG backwards: the group roots seeded with their weights' adjoints, then the prefixes in
     // reverse creation order (every contribution to a prefix's adjoint comes from a later prefix)
     std::vector<char> has(dp.p.size(), 0);
@@ -741,13 +778,17 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       for (int q = g1[4 * gi + 2]; q < g1[4 * gi + 3]; ++q) {
         const int i = g1rd[2 * q], pw = g1rd[2 * q + 1];
         if (!kept) for (int k = 0; k < pw; ++k) o("      RR *= rr%d;", i);
+        const int u = rden[2 * i];
         if (ps) {   // wb W1 once per group, then one fma per factor
           if (q == g1[4 * gi + 2]) o("      const double tw = %s;", PM("wb", "W1_" + std::to_string(gi)).c_str());
-          o("      xbar%d = fma(-%s, rr%d, xbar%d);", rden[2 * i], pw == 1 ? "tw" : PM("tw", lit((double)pw)).c_str(), i,
-            rden[2 * i]);
+          const std::string tp = pw == 1 ? "tw" : PM("tw", lit((double)pw));
+          if (hx[u]) o("      xbar%d = fma(-%s, rr%d, xbar%d);", u, tp.c_str(), i, u);
+          else o("      xbar%d = %s;", u, PM("-" + tp, "rr" + std::to_string(i)).c_str());
         } else {
-          o("      xbar%d -= wb * W1_%d * %s * rr%d;", rden[2 * i], gi, lit((double)pw).c_str(), i);
+          if (hx[u]) o("      xbar%d -= wb * W1_%d * %s * rr%d;", u, gi, lit((double)pw).c_str(), i);
+          else o("      xbar%d = -(wb * W1_%d * %s * rr%d);", u, gi, lit((double)pw).c_str(), i);
         }
+        hx[u] = 1;
       }
       if (has[rp]) o("      bp%d = fma(%swb, RR, bp%d);", rp, rs, rp);
       else o("      bp%d = %s;", rp, PM(std::string(rs) + "wb", "RR").c_str());
@@ -760,12 +801,18 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       const DagPrefix& q = dp.p[k];
       if (q.node) {   // the operand enters with its sign osign: so do both of its adjoint terms
         const char* os = q.osign < 0 ? "-" : "";
-        o("    fvbar%d = fma(%spv%d, bp%d, fvbar%d);", q.fv, os, q.operand, k, q.fv);
+        if (hf[q.fv]) o("    fvbar%d = fma(%spv%d, bp%d, fvbar%d);", q.fv, os, q.operand, k, q.fv);
+        else o("    fvbar%d = %s;", q.fv, PM(os + ("pv" + std::to_string(q.operand)), "bp" + std::to_string(k)).c_str());
+        hf[q.fv] = 1;
         if (has[q.operand]) o("    bp%d = fma(%sfv%d, bp%d, bp%d);", q.operand, os, q.fv, k, q.operand);
         else o("    double bp%d = %s;", q.operand, PM(os + ("fv" + std::to_string(q.fv)), "bp" + std::to_string(k)).c_str());
         has[q.operand] = 1;
       } else {
-        o("    fvbar%d = fma(%s, bp%d, fvbar%d);", q.fv, lit(q.osign * leafA[q.operand]).c_str(), k, q.fv);
+        const double c = q.osign * leafA[q.operand];
+        if (hf[q.fv]) o("    fvbar%d = fma(%s, bp%d, fvbar%d);", q.fv, lit(c).c_str(), k, q.fv);
+        else if (c == 1.0 || c == -1.0) o("    fvbar%d = %sbp%d;", q.fv, c > 0 ? "" : "-", k);
+        else o("    fvbar%d = %s;", q.fv, PM(lit(c), "bp" + std::to_string(k)).c_str());
+        hf[q.fv] = 1;
       }
       if (q.parent >= 0) {
         if (has[q.parent]) o("    bp%d += bp%d;", q.parent, k);
@@ -773,24 +820,49 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
         has[q.parent] = 1;
       }
     }
+    // each segment's Fermi values pass their adjoints to the combination: x-adjoint += sum over
+    // the values of +-fvbar P_{k+1} (the sign: h = 1 - g enters with -1)
     for (int b = 0; b < h.n_fseg; ++b) {
       const int* sgm = fseg + 8 * b;
+      bool any = false;
+      for (int v = sgm[2]; v < sgm[4]; ++v) any |= hf[v] != 0;
+      if (!any) continue;
       o("    {");
-      o("      double acc = 0.0;");
-      for (int v = sgm[2]; v < sgm[4]; ++v)
-        o("      { const double dd = fvbar%d * fvd%d; acc += %sdd; }", v, v, fvr[2 * v] > 0 ? "" : "-");
-      o("      xbar%d += acc;", sgm[0]);
+      bool first = ft;
+      if (!ft) o("      double acc = 0.0;");
+      for (int v = sgm[2]; v < sgm[4]; ++v) {
+        if (!hf[v]) continue;
+        const char* sg = fvr[2 * v] > 0 ? "" : "-";
+        if (first) o("      double acc = %s;", PM(sg + ("fvbar" + std::to_string(v)), "fvd" + std::to_string(v)).c_str());
+        else o("      acc = fma(%sfvbar%d, fvd%d, acc);", sg, v, v);
+        first = false;
+      }
+      o(hx[sgm[0]] ? "      xbar%d += acc;" : "      xbar%d = acc;", sgm[0]);
+      hx[sgm[0]] = 1;
       o("    }");
     }
-    for (int r = 0; r < h.n_rep; ++r) o("    double Ebar%d = 0.0;", repl[r]);
-    for (int u = 0; u < h.n_combo; ++u)
-      for (int q = combo_ptr[u]; q < combo_ptr[u + 1]; ++q)
-        o("    Ebar%d = fma(xbar%d, %s, Ebar%d);", combo_j[q], u, lit(combo_c[q]).c_str(), combo_j[q]);
-    o("    double mub = 0.0, kxb = 0.0, kyb = 0.0;");
-    for (int r = 0; r < h.n_rep; ++r) o("    mub += Ebar%d;", repl[r]);
+    std::vector<char> hE(h.N, ft ? 0 : 1);
+    for (int r = 0; r < h.n_rep; ++r) o(ft ? "    double Ebar%d;" : "    double Ebar%d = 0.0;", repl[r]);
+    for (int u = 0; u < h.n_combo; ++u) {
+      if (!hx[u]) continue;   // no adjoint reached this combination
+      for (int q = combo_ptr[u]; q < combo_ptr[u + 1]; ++q) {
+        const int j = combo_j[q];
+        const double c = combo_c[q];
+        if (hE[j]) o("    Ebar%d = fma(xbar%d, %s, Ebar%d);", j, u, lit(c).c_str(), j);
+        else if (c == 1.0 || c == -1.0) o("    Ebar%d = %sxbar%d;", j, c > 0 ? "" : "-", u);
+        else o("    Ebar%d = %s;", j, PM("xbar" + std::to_string(u), lit(c)).c_str());
+        hE[j] = 1;
+      }
+    }
+    for (int r = 0; r < h.n_rep; ++r)
+      if (!hE[repl[r]]) o("    Ebar%d = 0.0;", repl[r]);
+    o("    double mub = Ebar%d, kxb = 0.0, kyb = 0.0;", repl[0]);
+    for (int r = 1; r < h.n_rep; ++r) o("    mub += Ebar%d;", repl[r]);
     for (int r = 0; r < h.n_rep_ext; ++r)
-      o("    { const double eb = Ebar%d, ae = %s; kxb = fma(-eb * ae, Gx%d, kxb); kyb = fma(-eb * ae, Gy%d, kyb); }",
-        repl[r], lit(rep_aext[r]).c_str(), r, r);
+      if (r) o("    { const double eb = Ebar%d, ae = %s; kxb = fma(-eb * ae, Gx%d, kxb); kyb = fma(-eb * ae, Gy%d, kyb); }",
+               repl[r], lit(rep_aext[r]).c_str(), r, r);
+      else o("    { const double eb = Ebar%d, ae = %s; kxb = %s; kyb = %s; }", repl[r], lit(rep_aext[r]).c_str(),
+             PM("(-eb * ae)", "Gx" + std::to_string(r)).c_str(), PM("(-eb * ae)", "Gy" + std::to_string(r)).c_str());
     o("    if (act) {");
     o("      gmu += mub; gkx += kxb; gky += kyb;");
     o("      if (ps_grad) { ps_grad[3 * s] = mub; ps_grad[3 * s + 1] = kxb; ps_grad[3 * s + 2] = kyb; }");

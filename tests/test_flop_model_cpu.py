@@ -2,8 +2,9 @@
 bench's roofline divides by time) counted a second way: from the forward kernel source the library
 generates for the same table, statement by statement, under the model's conventions -- fma = 2,
 mul or add = 1, a multiplication by +-1 or an addition to an exact 0 free, the reciprocal 6, the
-exponential 19 (+2 for e^t - 1), a line energy 66 (two cosines of 30, then 6), the Fermi
-derivative polynomials as listed below -- and with every sum written as an fma chain from 0
+exponential 19 (+2 for e^t - 1), a line energy 66 (two cosines of 30, then 6), the first
+derivative -beta g h once per segment that needs it, the higher Fermi derivative polynomials as
+listed below -- and with every sum written as an fma chain from 0
 (line momenta, energy combinations, pole-DAG nodes) counted once per distinct prefix, since
 chains that begin with the same steps share those partial sums.  No GPU needed: the source is
 generated on the host."""
@@ -15,7 +16,7 @@ import paper_2311_17189_gb300 as T
 from paper_2311_17189_gb300 import workloads as W
 
 UNIT = ("0x1p+0", "-0x1p+0")
-POLY = {0: 0, 1: 2, 2: 5, 3: 9}
+POLY = {0: 0, 1: 2, 2: 5, 3: 9, 4: 17, 5: 23}   # fermi_poly(k): g h, h - g, powers, the Eulerian sum
 
 
 def step(first, coef):
@@ -57,6 +58,10 @@ def dag(body):
         assert k not in seen
         seen.add(k)
         fl += step(add == "0.0", "x" if opnd.lstrip("-").startswith("pv") else opnd)
+    for m in re.finditer(r'const double pv(\d+) = imul_ftz\(fv(\d+), ([^)]+)\);', body):   # a first step,
+        assert m.group(1) not in seen                                                     # on the integer pipes
+        seen.add(m.group(1))
+        fl += 1
     return fl
 
 
@@ -71,7 +76,8 @@ def per_sample(src):
     fermi = body.count("exp_neg<false>") + body.count("tami_seg_fermi(")     # that large tables call
     fl += (1 + 21 + 6 + 1) * bose                                           # -beta|x|, e^t and e^t - 1, 1/D, y/D
     fl += (1 + 19 + 7 + 1) * fermi                                          # ... D = 1 + y
-    fl += sum(POLY.get(int(k), 16 + 4 * int(k)) for k in re.findall(r'fermi_poly\((\d+),', body))
+    fl += sum(POLY[int(k)] for k in re.findall(r'fermi_poly\((\d+),', body))
+    fl += 2 * len(re.findall(r'sg\d+_d1 = (?!0\.0;)', body))                 # -beta g h: the k = 1 values
     fl += 6 * len(re.findall(r'rr\d+ = rcp\(', body))
     fl += dag(body)
     # group weights: products on the FP64 unit (x *= y, x * y) or the integer pipes (imul_ftz(x, y))
@@ -137,12 +143,13 @@ def signed_prefix_keys(src):
         v = float.fromhex(tok)
         return ("leaf", abs(v)), (1 if v > 0 else -1)
 
-    for m in re.finditer(r'const double (pv\d+) = (?:(-?)fv(\d+)|fma\(fv(\d+), ([^,]+), ([^)]+)\));', src):
+    pat = r'const double (pv\d+) = (?:(-?)fv(\d+)|(?:fma|imul_ftz)\(fv(\d+), ([^,)]+)(?:, ([^)]+))?\));'
+    for m in re.finditer(pat, src):
         if m.group(3) is not None:                     # +-F: a chain's first step on a unit leaf
             key, sign = ("F", m.group(3)), -1 if m.group(2) else 1
         else:
             (ko, so) = operand(m.group(5))
-            add = m.group(6).strip()
+            add = (m.group(6) or "0.0").strip()        # imul_ftz(F, operand): a first step
             if add == "0.0":
                 key, sign = ("first", m.group(4), ko), so
             else:
@@ -165,3 +172,107 @@ def test_no_prefix_is_another_with_its_signs_flipped():
     d = next(x for x in T.enumerate_sigma(4) if x["code"] == tuple(W.ORDER4["code"]))
     src = T.Diagram(d["alpha"], eps=d["eps"]).jit_source("fused")
     assert re.search(r'fma\(fv\d+, -pv\d+,', src) or re.search(r'W1_\d+ = (?:imul_ftz\()?-pv', src)
+
+
+# ---- the adjoint: bwd_flops_per_sample counted again from the fused kernel's source
+
+UNIT_LIT = re.compile(r'^-?0x1p\+0$')
+
+
+def _expr_cost(e, shared):
+    """Flops of one generated expression under the model's conventions: fma = 2 (an add where a
+    factor is +-1, a product onto 0.0), a product = 1 (free by +-1), negation free.  `shared`
+    holds the group weights' wb * W1 products already counted (the compiler forms each once)."""
+    e = e.strip()
+    while e.startswith("(") and _closing(e, 0) == len(e) - 1:
+        e = e[1:-1].strip()
+    if e.startswith("-") and not e.startswith("-0x"):
+        return _expr_cost(e[1:], shared)
+    m = re.match(r'^(fma|imul_ftz|imul)\((.*)\)$', e)
+    if m and _closing(e, len(m.group(1))) == len(e) - 1:
+        args = _split(m.group(2))
+        sub = sum(_expr_cost(a, shared) for a in args)
+        units = sum(bool(UNIT_LIT.match(a.strip())) for a in args[:2])
+        if m.group(1) == "fma":
+            if args[2].strip() == "0.0":
+                return sub + (0 if units else 1)
+            return sub + (1 if units else 2)
+        return sub + (0 if units else 1)
+    factors = _split(e, "*")
+    if len(factors) > 1:
+        sub = sum(_expr_cost(f, shared) for f in factors)
+        names = [f.strip() for f in factors]
+        n = sum(1 for f in names[1:] if not UNIT_LIT.match(f))
+        if UNIT_LIT.match(names[0]):
+            n -= 0 if len(names) == 1 else (1 if n else 0)
+        if names[:2] and names[0] == "wb" and names[1].startswith("W1_"):   # wb * W1 once per group
+            if names[1] in shared:
+                n -= 1
+            shared.add(names[1])
+        return sub + max(n, 0)
+    return 0
+
+
+def _closing(s, i):
+    depth = 0
+    for j in range(i, len(s)):
+        depth += s[j] == "("
+        depth -= s[j] == ")"
+        if depth == 0 and s[j] == ")":
+            return j
+    return -1
+
+
+def _split(s, sep=","):
+    out, depth, cur = [], 0, ""
+    for ch in s:
+        depth += ch == "("
+        depth -= ch == ")"
+        if ch == sep and depth == 0:
+            out.append(cur)
+            cur = ""
+        else:
+            cur += ch
+    return out + [cur]
+
+
+def reverse_sweep(src):
+    """Flops of the reverse sweep (from the combination adjoints to the parameter adjoints)."""
+    body = src[src.index("for (long long tile"):]
+    a = body.index("double xbar0")
+    rev = body[a:body.index("if (act) {", a)]
+    fl, shared, lits = 0, set(), {}
+    for st in re.split(r"[;{}]", rev):
+        st = st.strip()
+        if not st or st.startswith("__syncthreads"):
+            continue
+        st = re.sub(r"^(const )?double ", "", st)
+        for part in _split(st):                   # declarations may list several names
+            m = re.match(r"^(\w+)\s*(\+=|-=|\*=|=)\s*(.*)$", part.strip())
+            if not m:
+                continue
+            rhs = m.group(3).strip()
+            if re.match(r"^-?0x[0-9a-f.]+p[+-]\d+$", rhs):   # a name for a literal (a_ext)
+                lits[m.group(1)] = rhs
+                continue
+            for k, v in lits.items():
+                rhs = re.sub(r"\b%s\b" % k, v, rhs)
+            fl += _expr_cost(rhs, shared) + (0 if m.group(2) == "=" else 1)
+    return fl
+
+
+def test_adjoint_model_counts_what_the_generated_adjoint_computes():
+    """bwd_flops_per_sample = the fused kernel's per-sample forward part (as the forward count, with
+    the k_ext lines' energies and gradients, cos and sin: 108 each), the loop inputs p W, and the
+    reverse sweep, statement by statement; all 87 tables."""
+    checked = 0
+    for name, D in tables():
+        src = D.jit_source("fused")
+        body = src[src.index("for (long long tile"):src.index("if (xr_zero) {")]
+        fl = per_sample(src) + 108 * len(re.findall(r"\bline_energy_grad\(", body))
+        for m in re.finditer(r"const double pW\d+ = ([^;]+);", body):
+            fl += _expr_cost(m.group(1), set())
+        fl += reverse_sweep(src)
+        assert fl == D.info()["bwd_flops_per_sample"], name
+        checked += 1
+    assert checked == 87
