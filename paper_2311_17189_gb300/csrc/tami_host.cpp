@@ -936,7 +936,9 @@ int flatten(tami_diagram* d) {
     bool k1 = false;                                    // -beta g h, shared by the segment's k = 0 values
     for (int v = g.vk1; v < g.v1; ++v) k1 |= fvs[v].k == 1;   // (counted above where k = 1 values use it)
     if (g.vk1 > g.v0 && !k1) bl += 2.0;
-    for (int v = g.vk1; v < g.v1; ++v) bl += poly_cost(fvs[v].k + 1);
+    if (k1) bl += 3.0;                                  // -beta d1 (h - g): every k = 1 value's derivative
+    for (int v = g.vk1; v < g.v1; ++v)
+      if (fvs[v].k != 1) bl += poly_cost(fvs[v].k + 1);
   }
   std::vector<char> hx(combos.size(), 0);              // combinations whose adjoint has a term
   for (const CdKey& c : cdens) bl += sum_term(hx[c.u], 0.0, 1.0);   // cden adjoints into combinations

@@ -635,13 +635,19 @@ std::string jit_source(const TableHeader& h, const unsigned char* blob, int kind
       o("    const double fv%d = sg%d_%c;", v, b, fvr[2 * v] > 0 ? 'g' : 'h');
       if (adj) o("    const double fvd%d = sg%d_d1;", v, b);
     }
+    // the adjoint's second derivative d2 = -beta d1 (h - g) = beta^2 g h (h - g), once per segment
+    // with k = 1 values (an h value's is -d2)
+    if (adj && has_k1)
+      o("    const double sg%d_d2 = %s;", b,
+        PM(PM("-beta", "sg" + std::to_string(b) + "_d1"), "(sg" + std::to_string(b) + "_h - sg" + std::to_string(b) + "_g)").c_str());
     for (int v = sgm[3]; v < sgm[4]; ++v) {
       const bool pos = fvr[2 * v] > 0;
       const int k = fvr[2 * v + 1];
       const char g = pos ? 'g' : 'h', hh = pos ? 'h' : 'g';
       if (k == 1) o("    const double fv%d = sg%d_d1;", v, b);
       else o("    const double fv%d = fermi_poly(%d, sg%d_%c, sg%d_%c, beta);", v, k, b, g, b, hh);
-      if (adj) o("    const double fvd%d = fermi_poly(%d, sg%d_%c, sg%d_%c, beta);", v, k + 1, b, g, b, hh);
+      if (adj && k == 1) o("    const double fvd%d = %ssg%d_d2;", v, pos ? "" : "-", b);
+      else if (adj) o("    const double fvd%d = fermi_poly(%d, sg%d_%c, sg%d_%c, beta);", v, k + 1, b, g, b, hh);
     }
   }
   for (int i = 0; i < h.n_rden; ++i) o("    const double rr%d = rcp(x%d);", i, rden[2 * i]);

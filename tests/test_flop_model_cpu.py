@@ -181,11 +181,15 @@ UNIT_LIT = re.compile(r'^-?0x1p\+0$')
 
 def _expr_cost(e, shared):
     """Flops of one generated expression under the model's conventions: fma = 2 (an add where a
-    factor is +-1, a product onto 0.0), a product = 1 (free by +-1), negation free.  `shared`
-    holds the group weights' wb * W1 products already counted (the compiler forms each once)."""
+    factor is +-1, a product onto 0.0), a product = 1 (free by +-1), an add or subtract = 1,
+    negation free.  `shared` holds the group weights' wb * W1 products already counted (the
+    compiler forms each once)."""
     e = e.strip()
     while e.startswith("(") and _closing(e, 0) == len(e) - 1:
         e = e[1:-1].strip()
+    terms = [t for t in _split_sum(e) if t.strip()]
+    if len(terms) > 1:
+        return sum(_expr_cost(t, shared) for t in terms) + len(terms) - 1
     if e.startswith("-") and not e.startswith("-0x"):
         return _expr_cost(e[1:], shared)
     m = re.match(r'^(fma|imul_ftz|imul)\((.*)\)$', e)
@@ -211,6 +215,22 @@ def _expr_cost(e, shared):
             shared.add(names[1])
         return sub + max(n, 0)
     return 0
+
+
+def _split_sum(s):
+    """Top-level terms of a sum or difference (a leading sign and the exponent signs of hex
+    literals do not split)."""
+    out, depth, cur = [], 0, ""
+    for i, ch in enumerate(s):
+        depth += ch == "("
+        depth -= ch == ")"
+        if (ch in "+-" and depth == 0 and cur.strip() and not re.search(r"0x[0-9a-f.]+p$", cur)
+                and cur.strip()[-1] not in "*(,+-"):   # a unary sign after an operator does not split
+            out.append(cur)
+            cur = ""
+        else:
+            cur += ch
+    return out + [cur]
 
 
 def _closing(s, i):
@@ -270,6 +290,8 @@ def test_adjoint_model_counts_what_the_generated_adjoint_computes():
         src = D.jit_source("fused")
         body = src[src.index("for (long long tile"):src.index("if (xr_zero) {")]
         fl = per_sample(src) + 108 * len(re.findall(r"\bline_energy_grad\(", body))
+        for m in re.finditer(r"const double sg\d+_d2 = ([^;]+);", body):   # second derivatives
+            fl += _expr_cost(m.group(1), set())
         for m in re.finditer(r"const double pW\d+ = ([^;]+);", body):
             fl += _expr_cost(m.group(1), set())
         fl += reverse_sweep(src)
