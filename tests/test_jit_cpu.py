@@ -71,6 +71,26 @@ def test_generated_kernel_compiles_for_sm103a(name, D, kind):
     assert cubin > 0
 
 
+@pytest.mark.parametrize("env", [{"TAMI_JIT_FIRSTTERM": "0"}, {"TAMI_JIT_PSFIRST": "0"}, {"TAMI_JIT_PSMUL": "fwd"},
+                                 {"TAMI_JIT_PSMUL": "all"}, {"TAMI_JIT_PSMUL": "0"}],
+                         ids=["firstterm0", "psfirst0", "psmul_fwd", "psmul_all", "psmul0"])
+def test_measured_variants_still_compile(env, monkeypatch):
+    """The generator's A/B switches (read when a source is generated) give kernels that compile, on
+    a small and a large table, so the variants measured against the defaults stay buildable; the
+    default source differs from the variant where the switch applies."""
+    small, large = tables()[0][1], tables()[3][1]
+    base = {n: D.jit_source("fused") for n, D in (("small", small), ("large", large))}
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    changed = False
+    for n, D in (("small", small), ("large", large)):
+        src = D.jit_source("fused")
+        changed |= src != base[n]
+        rc, log, cubin = compile_cubin(src)
+        assert rc == 0 and cubin > 0, (n, log[:3000])
+    assert changed
+
+
 def test_kinds_differ_only_where_they_should():
     """The forward kernel carries no adjoint sweep, the adjoint no forward sums."""
     D = tables()[0][1]
