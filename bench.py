@@ -53,8 +53,8 @@ METRIC = "order-4 Sigma evals/s (samples x terms x frequencies, FP64), forward +
 # caches the compilation (whose options are fixed in the library) -- must hash to the captured
 # one, else the bench reports traffic as null.
 TRAFFIC = {"kernel": "tami_jit_fused (the diagram's specialised fused forward + adjoint)",
-           "bytes_per_sample": (4.609480e9 + 5.660774e9) / 4194304,
-           "kernel_sha256": "9287aa97bd9f7e746744b61ed2de460701d0789bddea445e3b2b48e8861fc19f",
+           "bytes_per_sample": (4.650301e9 + 5.725492e9) / 4194304,
+           "kernel_sha256": "cc21cf574bb547fa71c92372ed461d9c6e83bd460e6a6fa46c67ef91d21e9a88",
            "profile": "profiles/jit_kernels_order4_sigma.md"}
 
 
