@@ -15,7 +15,9 @@ A second test runs the whole frequency-free chain from the base energies -- comb
 generated Fermi/Bose segment code with its derivative values, the pole DAG and the weights -- and
 checks the energy adjoints of the reverse sweep, segment sums included, against complex-step
 derivatives with respect to each energy (planted sign errors in the segment sums, the first and
-second derivatives and the energy coefficients are caught).  No GPU needed."""
+second derivatives and the energy coefficients are caught).  A third runs one frequency of the
+generated loop, on and off the imaginary axis, and checks its weight and denominator adjoints and
+dSigma/dX against complex-step derivatives of the loop's own value.  No GPU needed."""
 import cmath
 import math
 import re
@@ -266,3 +268,121 @@ def test_energy_adjoints_equal_complex_step_derivatives(name, D):
         checked += 1
     assert checked > 0
     assert abs(base["mub"] - total) <= 1e-11 * scale, (name, base["mub"], total)
+
+
+# ---- the frequency loop: one frequency of the generated loop body
+
+def _neg_rewrite(s):
+    """The generated sign flip __longlong_as_double(__double_as_longlong(e) ^ sign bit) as -(e)."""
+    head = "__longlong_as_double(__double_as_longlong("
+    tail = ") ^ (long long)0x8000000000000000ull)"
+    while head in s:
+        i = s.index(head)
+        j = _closing_paren(s, i + len(head) - 1)
+        assert s[j:j + len(tail)] == tail, s[j:j + 60]
+        s = s[:i] + "(-(" + s[i + len(head):j] + "))" + s[j + len(tail):]
+    return s
+
+
+def _closing_paren(s, i):
+    depth = 0
+    for j in range(i, len(s)):
+        depth += s[j] == "("
+        depth -= s[j] == ")"
+        if depth == 0:
+            return j
+    raise AssertionError("unbalanced")
+
+
+def loop_bodies(src):
+    """(imaginary-axis body, general body, loop inputs as Python, shared-memory slot names) of the
+    fused kernel's frequency loop."""
+    body = src[src.index("for (long long tile"):]
+    a = body.index("if (xr_zero) {")
+    out = []
+    for start in (a, body.index("} else {", a)):
+        k = body.index("for (int f = 0; f < n_f; ++f) {", start)
+        o = k + len("for (int f = 0; f < n_f; ++f) ")      # the loop's opening brace
+        text = body[o + 1:_closing_brace(body, o)]
+        text = re.sub(r"if \(act\) \{.*?\n\s*\}", "", text, flags=re.S)     # the running sums
+        text = _neg_rewrite(text)
+        text = text.replace("Xs[2 * f]", "Xr_in").replace("Gs[2 * f + 1]", "Gi_in").replace("Gs[2 * f]", "Gr_in")
+        text = re.sub(r"AXI2\[(\d+) \* n_f \+ f\]", r"AXI2_\1", text)
+        text = re.sub(r"AXI\[(\d+) \* n_f \+ f\]", r"AXI_\1", text)
+        text = re.sub(r"jsv\[(\d+) \* \d+ \+ tid\]", r"jsv_\1", text)
+        out.append(_python(text))
+    fwd = body[:a]
+    pw = "\n".join(_python(m.group(0)) for m in re.finditer(r"const double pW\d+ = [^;]+;", fwd))
+    slots = {int(m.group(1)): m.group(2) for m in re.finditer(r"jsv\[(\d+) \* \d+ \+ tid\] = (\w+);", fwd)}
+    return out[0], out[1], pw, slots
+
+
+def _closing_brace(s, i):
+    depth = 0
+    for j in range(i, len(s)):
+        depth += s[j] == "{"
+        depth -= s[j] == "}"
+        if depth == 0:
+            return j
+    raise AssertionError("unbalanced")
+
+
+@pytest.mark.parametrize("name,D", tables(), ids=[t[0] for t in tables()])
+def test_frequency_loop_adjoints_equal_complex_step_derivatives(name, D):
+    """One frequency of the generated loop, on and off the imaginary axis: with L = Re(conj(g) v)
+    for the sample's value v = sum_t W2_t R_t(X) and an upstream gradient g, the loop's weight and
+    denominator adjoints (Wb2, bb) equal complex-step derivatives of L with respect to W2 and to the
+    denominators' real parts b, and its dv/dX equals the complex derivative of v (along the real
+    axis, or i times the derivative along the imaginary one)."""
+    src = D.jit_source("fused")
+    on_axis, off_axis, pw, slots = loop_bodies(src)
+    cden_a = [float.fromhex(v.strip()) for v in
+              re.search(r"kJitCdenA\[\d+\] = \{([^}]*)\}", src).group(1).split(",")]
+    rng = np.random.default_rng(5)
+    text = "\n".join([pw] + list(slots.values()) + [on_axis])
+    w2 = sorted(set(re.findall(r"\bW2_\d+\b", text)))
+    bs = sorted(set(re.findall(r"\bb\d+\b", text)))
+    vals = {k: float(rng.uniform(-1, 1)) for k in w2}
+    vals.update({k: float(rng.uniform(0.5, 2.0)) * (1 if rng.random() < 0.5 else -1) for k in bs})
+    Gr, Gi, Xr0, Xi0 = (float(v) for v in rng.uniform(-1, 1, 4))
+
+    def run_body(body, v, Xr, Xi):
+        ns = dict(v)
+        ns.update(Gr_in=Gr, Gi_in=Gi, Xr_in=Xr)
+        for c, a in enumerate(cden_a):
+            ns["AXI_%d" % c], ns["AXI2_%d" % c] = a * Xi, (a * Xi) ** 2
+        for k in [n for n in list(ns) if n.startswith(("Wb2_", "bb"))]:
+            del ns[k]
+        for t in w2:
+            ns["Wb2_" + t[3:]] = 0.0
+        for c in range(len(cden_a)):
+            ns["bb%d" % c] = 0.0
+        code = pw + "\n" + "\n".join("jsv_%d = %s" % (k, n) for k, n in sorted(slots.items())) + "\n" + body
+        exec(code, dict(FUNCS), ns)
+        return ns
+
+    h = 1e-30
+    for axis, body, Xr in (("on", on_axis, 0.0), ("off", off_axis, Xr0)):
+        base = run_body(body, vals, Xr, Xi0)
+        L = lambda ns: Gr * ns["vr"] + Gi * ns["vi"]
+
+        def step(var, Xr=Xr, Xi=Xi0):
+            v = dict(vals)
+            if var in v:
+                v[var] = v[var] + 1j * h
+            return run_body(body, v, Xr, Xi)
+
+        for t in w2:
+            d = L(step(t)).imag / h
+            assert abs(base["Wb2_" + t[3:]] - d) <= 1e-12 * max(1.0, abs(d)), (name, axis, t)
+        for b in bs:
+            d = L(step(b)).imag / h
+            assert abs(base["bb" + b[1:]] - d) <= 1e-12 * max(1.0, abs(d)), (name, axis, b)
+        if axis == "off":                              # d/dXr of v
+            ns = step(None, Xr=Xr + 1j * h)
+            dr, di = ns["vr"].imag / h, ns["vi"].imag / h
+        else:                                          # dv/dX = -i d/dXi of v
+            ns = step(None, Xi=Xi0 + 1j * h)
+            dr, di = ns["vi"].imag / h, -ns["vr"].imag / h
+        scale = max(1.0, abs(dr), abs(di))
+        assert abs(base["dvr"] - dr) <= 1e-12 * scale and abs(base["dvi"] - di) <= 1e-12 * scale, (name, axis)
