@@ -17,7 +17,8 @@ checks the energy adjoints of the reverse sweep, segment sums included, against 
 derivatives with respect to each energy (planted sign errors in the segment sums, the first and
 second derivatives and the energy coefficients are caught).  A third runs one frequency of the
 generated loop, on and off the imaginary axis, and checks its weight and denominator adjoints and
-dSigma/dX against complex-step derivatives of the loop's own value.  No GPU needed."""
+dSigma/dX against complex-step derivatives of the loop's own value.  A fourth checks the generated
+line momenta and energies against the diagram's momentum labels.  No GPU needed."""
 import cmath
 import math
 import re
@@ -386,3 +387,44 @@ def test_frequency_loop_adjoints_equal_complex_step_derivatives(name, D):
             dr, di = ns["vi"].imag / h, -ns["vr"].imag / h
         scale = max(1.0, abs(dr), abs(di))
         assert abs(base["dvr"] - dr) <= 1e-12 * scale and abs(base["dvi"] - di) <= 1e-12 * scale, (name, axis)
+
+
+# ---- the line momenta and energies of the generated prologue (step a2/a3)
+
+def _line_energy(ax, ay, t, tp, mu):
+    cx, cy = math.cos(ax), math.cos(ay)
+    return mu + 2.0 * t * (cx + cy) + 4.0 * tp * cx * cy
+
+
+@pytest.mark.parametrize("name,D,alpha", [(n, D, a) for n, D, a in
+                                          [(t[0], t[1], None) for t in tables()[:1]] +
+                                          [(f"order{m}_{i}", T.Diagram(d["alpha"], eps=d["eps"]), d["alpha"])
+                                           for m in (2, 3, 4, 5) for i, d in enumerate(T.enumerate_sigma(m))]],
+                         ids=lambda v: v if isinstance(v, str) else "")
+def test_line_energies_follow_the_momentum_labels(name, D, alpha):
+    """Every line energy the generated kernel computes is mu - eps(K_j) of the line's momentum
+    K_j = sum_l alpha_jl k_l + alpha_j,ext k_ext, with the labels read from the diagram (not from
+    the generated code), for random loop and external momenta and lattice parameters."""
+    if alpha is None:
+        alpha = np.array(W.ORDER2["alpha"])
+    src = D.jit_source("fused")
+    body = src[src.index("for (long long tile"):]
+    m = alpha.shape[1] - 1
+    a = body.index("const double kx%d = lkx" % m)
+    prologue = body[a:body.index("\n    }", a)]
+    prologue = re.sub(r"line_energy_grad\(([^,]+), ([^,]+), lt, ltp, lmu, \w+, \w+\)",
+                      r"line_energy(\1, \2, lt, ltp, lmu)", prologue)
+    code = _python(prologue.replace("(void)kx%d; (void)ky%d;" % (m, m), ""))
+    rng = np.random.default_rng(3)
+    ns = {"kx%d" % l: float(rng.uniform(-np.pi, np.pi)) for l in range(m)}
+    ns.update({"ky%d" % l: float(rng.uniform(-np.pi, np.pi)) for l in range(m)})
+    ns.update(lkx=float(rng.uniform(-np.pi, np.pi)), lky=float(rng.uniform(-np.pi, np.pi)),
+              lt=1.0, ltp=float(rng.uniform(-0.5, 0.5)), lmu=float(rng.uniform(-1, 1)))
+    exec(code, {"fma": FUNCS["fma"], "line_energy": _line_energy}, ns)
+    lines = sorted(int(k[1:]) for k in ns if re.fullmatch(r"E\d+", k))
+    assert lines, name
+    for j in lines:
+        kx = sum(int(alpha[j][l]) * ns["kx%d" % l] for l in range(m)) + int(alpha[j][m]) * ns["lkx"]
+        ky = sum(int(alpha[j][l]) * ns["ky%d" % l] for l in range(m)) + int(alpha[j][m]) * ns["lky"]
+        want = _line_energy(kx, ky, ns["lt"], ns["ltp"], ns["lmu"])
+        assert abs(ns["E%d" % j] - want) <= 1e-12, (name, j)
