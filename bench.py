@@ -563,6 +563,47 @@ def run_workload(args):
     return 0
 
 
+def run_construct(args):
+    """Host-side construction (step a11: residues, flattening into the device table, validation;
+    no GPU): wall time per diagram for the paper's order-2 example and the largest enumerated
+    tables at orders 4-6, and for enumerating and constructing every order-6 diagram.  Not the
+    metric; one JSON line."""
+    import resource
+    import paper_2311_17189_gb300 as T
+
+    def per_call_ms(make, reps):
+        make()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            make()
+        return (time.perf_counter() - t0) / reps * 1e3
+
+    rss0 = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss
+    example = np.array([[1, 0, 0], [0, 1, 0], [-1, 1, 1]], dtype=np.int8)   # the paper's order-2 example
+    rows = [{"diagram": "order2_paper_example", "terms": T.Diagram(example).info()["n_terms"],
+             "ms": per_call_ms(lambda: T.Diagram(example), 200)}]
+    for c in (W.ORDER4, W.ORDER5, W.ORDER6):
+        d = next(x for x in T.enumerate_sigma(c["order"]) if x["code"] == tuple(c["code"]))
+        make = lambda: T.Diagram(d["alpha"], eps=d["eps"])
+        rows.append({"diagram": c["name"], "terms": make().info()["n_terms"],
+                     "ms": per_call_ms(make, max(2, args.steps))})
+    rss1 = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss
+    t0 = time.perf_counter()
+    ds = T.enumerate_sigma(6)
+    t1 = time.perf_counter()
+    lib = [T.Diagram(x["alpha"], eps=x["eps"]) for x in ds]       # all held at once
+    t2 = time.perf_counter()
+    terms = sum(D.info()["n_terms"] for D in lib)
+    rss2 = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss
+    print(json.dumps({"metric": "host construction wall time (AMI residues + flattening + validation)",
+                      "unit": "ms", "diagrams": rows,
+                      "order6_all": {"diagrams": len(lib), "terms": terms, "enumerate_ms": (t1 - t0) * 1e3,
+                                     "construct_ms": (t2 - t1) * 1e3, "held_rss_mb": (rss2 - rss1) / 1024.0},
+                      "single_diagrams_peak_rss_growth_mb": (rss1 - rss0) / 1024.0, "cores": 1,
+                      "host": os.uname().machine}))
+    return 0
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -574,13 +615,17 @@ def main():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--rows", type=int, default=0, help="energy rows of energy_x1 / two_freq_x1 (profiling runs)")
     p.add_argument("--workload", default="order4",
-                   choices=["order4", "order5", "order6", "order3_real", "all_orders", "energy_x1", "two_freq_x1"],
-                   help="order4 is the headline metric; the others time the remaining configurations on one GPU")
+                   choices=["order4", "order5", "order6", "order3_real", "all_orders", "energy_x1", "two_freq_x1",
+                            "construct"],
+                   help="order4 is the headline metric; the others time the remaining configurations on one GPU "
+                        "(construct: the host-side construction, no GPU)")
     p.add_argument("--jit", default="auto", choices=["auto", "never", "always"],
                    help="specialised kernels: auto (large calls), never (generic kernels) or always (profiling runs)")
     args = p.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "construct":
+        return run_construct(args)
     import paper_2311_17189_gb300 as T
     T.set_jit(args.jit)
     if args.workload != "order4":

@@ -134,3 +134,17 @@ def test_rejects_malformed_input():
     assert e.value.code == L.TAMI_EINVAL
     with pytest.raises(L.TamiError):
         T.enumerate_sigma(1)
+
+
+def test_bench_construct_workload_runs_on_the_host():
+    """bench.py --workload construct times the host-side construction without a GPU and prints one
+    JSON line: every order-6 diagram constructed, term counts as the library reports them."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "construct", "--steps", "2"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert [d["terms"] for d in line["diagrams"]] == [4, 104, 744, 5136]
+    assert line["order6_all"]["diagrams"] == 515 and all(d["ms"] > 0 for d in line["diagrams"])
