@@ -1193,6 +1193,7 @@ int tami_construct_ext(int n_lines, int n_vars, int n_ext, const int8_t* alpha, 
   d->terms.swap(cur);
   int rc = flatten(d);
   if (rc != TAMI_OK) { delete d; return rc; }
+  std::vector<SymTerm>().swap(d->terms);   // everything later reads the flattened table
   *out = d;
   return TAMI_OK;
   });

@@ -132,7 +132,7 @@ struct tami_diagram {
   std::vector<int8_t> alpha;          // [N][nv]
   std::vector<uint8_t> boson;         // [nv]
   double prefactor = 1.0;
-  std::vector<tami::SymTerm> terms;
+  std::vector<tami::SymTerm> terms;   // the symbolic solution, released once flattened into blob
   tami_info info{};
   tami::TableHeader hdr{};
   std::vector<unsigned char> blob;    // host copy of the table
