@@ -117,9 +117,10 @@ def run(code, ns):
     return ns
 
 
+@pytest.mark.parametrize("kind", ["fused", "adjoint"])
 @pytest.mark.parametrize("name,D", tables(), ids=[t[0] for t in tables()])
-def test_reverse_sweep_equals_complex_step_derivatives(name, D):
-    combos, fwd, rev = sections(D.jit_source("fused"))
+def test_reverse_sweep_equals_complex_step_derivatives(name, D, kind):
+    combos, fwd, rev = sections(D.jit_source(kind))
     fwd_c, rev_c = compile(fwd, "fwd", "exec"), compile(combos + "\n" + fwd + "\n" + rev, "all", "exec")
     from_e = compile(combos + "\n" + fwd, "combos+fwd", "exec")
     rng = np.random.default_rng(7)
@@ -232,13 +233,15 @@ def chain_sections(src):
     return _chain_python(fwd), _python(rev)
 
 
+@pytest.mark.parametrize("kind", ["fused", "adjoint"])
 @pytest.mark.parametrize("name,D", tables(), ids=[t[0] for t in tables()])
-def test_energy_adjoints_equal_complex_step_derivatives(name, D):
+def test_energy_adjoints_equal_complex_step_derivatives(name, D, kind):
     """With the Fermi/Bose values and their derivatives computed by the generated segment code from
     the energies, the energy adjoints of the reverse sweep (the segment sums included) equal
     complex-step derivatives of L = sum_t wb_t W2_t + sum_c bb_c b_c with respect to each base
-    energy, and mu's adjoint their sum; random energies, beta, wb and bb."""
-    src = D.jit_source("fused")
+    energy, and mu's adjoint their sum; random energies, beta, wb and bb.  Both kinds that carry
+    the reverse sweep: the fused pass and the adjoint reading saved energies."""
+    src = D.jit_source(kind)
     fwd, rev = chain_sections(src)
     glb = dict(CHAIN_FUNCS)
     exec(_device_functions(src), glb)
