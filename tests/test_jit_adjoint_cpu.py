@@ -1,4 +1,4 @@
-"""The specialised kernels' reverse sweep checked on the host, for every table: the generated
+"""The specialised kernels checked on the host, for every table: the generated
 statements of the pole DAG, the group weights and their adjoints are run as plain Python on random
 inputs, and the adjoints they produce are compared with complex-step derivatives of the forward
 statements they belong to.
@@ -18,7 +18,9 @@ derivatives with respect to each energy (planted sign errors in the segment sums
 second derivatives and the energy coefficients are caught).  A third runs one frequency of the
 generated loop, on and off the imaginary axis, and checks its weight and denominator adjoints and
 dSigma/dX against complex-step derivatives of the loop's own value.  A fourth checks the generated
-line momenta and energies against the diagram's momentum labels.  No GPU needed."""
+line momenta and energies against the diagram's momentum labels, and a fifth the generated value
+itself against the oracle's (its own construction, term by term) at the same energies.  No GPU
+needed."""
 import cmath
 import math
 import re
@@ -431,3 +433,54 @@ def test_line_energies_follow_the_momentum_labels(name, D, alpha):
         ky = sum(int(alpha[j][l]) * ns["ky%d" % l] for l in range(m)) + int(alpha[j][m]) * ns["lky"]
         want = _line_energy(kx, ky, ns["lt"], ns["ltp"], ns["lmu"])
         assert abs(ns["E%d" % j] - want) <= 1e-12, (name, j)
+
+
+# ---- the generated value against the oracle, on the host
+
+@pytest.mark.parametrize("kind", ["forward", "fused"])
+@pytest.mark.parametrize("name,D,oracle_args", [
+    ("order2_bosonic", T.Diagram(W.ORDER2["alpha"], var_is_boson=W.ORDER2["var_is_boson"]),
+     (W.ORDER2["alpha"], None, W.ORDER2["var_is_boson"]))] +
+    [(f"order{m}_{i}", T.Diagram(d["alpha"], eps=d["eps"]), (d["alpha"], d["eps"], None))
+     for m in (2, 3, 4, 5) for i, d in enumerate(T.enumerate_sigma(m))],
+    ids=lambda v: v if isinstance(v, str) else "")
+def test_generated_value_matches_the_oracle(name, D, oracle_args, kind):
+    """The generated per-sample code from the base energies on -- combinations, the Fermi/Bose
+    segments, the pole DAG, the weights and one frequency of the loop -- run as Python, gives the
+    oracle's value of the same diagram (its own construction, term by term) at the same energies,
+    on and off the imaginary axis, within 1e-12 of the oracle's rounding envelope."""
+    import oracle as O
+    src = D.jit_source(kind)
+    fwd, _ = chain_sections(src) if kind == "fused" else (None, None)
+    if kind == "forward":
+        body = src[src.index("for (long long tile"):]
+        c0 = body.index("    double x0 = ")
+        fwd = _chain_python(body[c0:body.index("if (xr_zero) {")])
+    on_axis, off_axis, pw, slots = loop_bodies(src)
+    cden_a = [float.fromhex(v.strip()) for v in
+              re.search(r"kJitCdenA\[\d+\] = \{([^}]*)\}", src).group(1).split(",")]
+    glb = dict(CHAIN_FUNCS)
+    exec(_device_functions(src), glb)
+    alpha, eps, boson = oracle_args
+    alpha = np.asarray(alpha)
+    sol = O.Solution(alpha, eps=eps, var_is_boson=boson)
+    rng = np.random.default_rng(13)
+    rows = {}
+    E = np.empty(alpha.shape[0])
+    for j, row in enumerate(map(tuple, alpha)):          # lines with equal labels share an energy
+        rows.setdefault(row, float(rng.uniform(-2.0, 2.0)))
+        E[j] = rows[row]
+    beta = 1.3
+    for body, X in ((on_axis, complex(0.0, 3 * np.pi / beta)), (off_axis, complex(0.7, 0.05))):
+        ns = {"E%d" % j: float(E[j]) for j in range(len(E))}
+        ns.update(beta=beta, Xr_in=X.real, Gr_in=0.0, Gi_in=0.0)
+        for c, a in enumerate(cden_a):
+            ns["AXI_%d" % c], ns["AXI2_%d" % c] = a * X.imag, (a * X.imag) ** 2
+        for k in range(64):
+            ns["Wb2_%d" % k] = 0.0
+            ns["bb%d" % k] = 0.0
+        code = fwd + "\n" + "\n".join("jsv_%d = %s" % (k, n) for k, n in sorted(slots.items())) + "\n" + body
+        exec(code, dict(glb), ns)
+        want, _, env = sol.eval_energies(E[None, :], np.array([X]), beta)
+        got = complex(ns["vr"], ns["vi"])
+        assert abs(got - want[0, 0]) <= 1e-12 * env[0, 0] + 1e-300, (name, kind, X, got, want[0, 0])
