@@ -18,8 +18,9 @@ derivatives with respect to each energy (planted sign errors in the segment sums
 second derivatives and the energy coefficients are caught).  A third runs one frequency of the
 generated loop, on and off the imaginary axis, and checks its weight and denominator adjoints and
 dSigma/dX against complex-step derivatives of the loop's own value.  A fourth checks the generated
-line momenta and energies against the diagram's momentum labels, and a fifth the generated value
-itself against the oracle's (its own construction, term by term) at the same energies.  No GPU
+line momenta and energies against the diagram's momentum labels, and the last two the generated
+value itself against the oracle's (its own construction, term by term) at the same energies: the
+Monte Carlo kinds, and the energy-input kind with one or two external frequencies per row.  No GPU
 needed."""
 import cmath
 import math
@@ -51,8 +52,8 @@ def _python(section):
     out = []
     for st in re.split(r"[;{}]", section):
         st = st.strip()
-        if not st or st.startswith("__syncthreads") or st.startswith("jsv["):
-            continue
+        if not st or st.startswith(("__syncthreads", "jsv[", "reinterpret_cast")):
+            continue                                 # barriers, shared-memory and output stores
         st = re.sub(r"^(const )?(double2|double|bool) ", "", st)
         parts = [p.strip() for p in _split_commas(st)]
         for p in parts:
@@ -313,6 +314,7 @@ def loop_bodies(src):
         text = re.sub(r"if \(act\) \{.*?\n\s*\}", "", text, flags=re.S)     # the running sums
         text = _neg_rewrite(text)
         text = text.replace("Xs[2 * f]", "Xr_in").replace("Gs[2 * f + 1]", "Gi_in").replace("Gs[2 * f]", "Gr_in")
+        text = re.sub(r"Xs\[2 \* \((\d+) \* n_f \+ f\)\]", r"Yr_in_\1", text)   # energy input: Re Y_k
         text = re.sub(r"AXI2\[(\d+) \* n_f \+ f\]", r"AXI2_\1", text)
         text = re.sub(r"AXI\[(\d+) \* n_f \+ f\]", r"AXI_\1", text)
         text = re.sub(r"jsv\[(\d+) \* \d+ \+ tid\]", r"jsv_\1", text)
@@ -484,3 +486,67 @@ def test_generated_value_matches_the_oracle(name, D, oracle_args, kind):
         want, _, env = sol.eval_energies(E[None, :], np.array([X]), beta)
         got = complex(ns["vr"], ns["vi"])
         assert abs(got - want[0, 0]) <= 1e-12 * env[0, 0] + 1e-300, (name, kind, X, got, want[0, 0])
+
+
+def _energy_kind_tables():
+    out = [(t[0], t[1], t[2], 1) for t in _value_tables()]
+    for m, i in ((3, 0), (3, 1), (4, 0), (4, 5), (4, 11)):
+        d = T.enumerate_sigma(m)[i]
+        a2 = W.hold_external(d["alpha"], m - 1)
+        out.append((f"order{m}_{i}_two_external", T.Diagram(a2, eps=d["eps"], n_ext=2), (a2, d["eps"], None), 2))
+    return out
+
+
+def _value_tables():
+    return ([("order2_bosonic", T.Diagram(W.ORDER2["alpha"], var_is_boson=W.ORDER2["var_is_boson"]),
+              (W.ORDER2["alpha"], None, W.ORDER2["var_is_boson"]))] +
+            [(f"order{m}_{i}", T.Diagram(d["alpha"], eps=d["eps"]), (d["alpha"], d["eps"], None))
+             for m in (2, 3, 4, 5) for i, d in enumerate(T.enumerate_sigma(m))])
+
+
+@pytest.mark.parametrize("name,D,oracle_args,n_ext", _energy_kind_tables(),
+                         ids=lambda v: v if isinstance(v, str) else "")
+def test_energy_kind_value_matches_the_oracle(name, D, oracle_args, n_ext):
+    """The energy-input kind (energies read, every value written; several external frequencies per
+    row): its generated per-row code, run as Python from the base energies with the frequency row
+    staged as the kernel stages it (Y_k = sum_q v_kq X_q), gives the oracle's value at the same
+    energies and frequency row, on and off the imaginary axis, within 1e-12 of its envelope."""
+    import oracle as O
+    src = D.jit_source("energy")
+    body = src[src.index("for (long long tile"):]
+    c0 = body.index("    double x0 = ")
+    fwd = _chain_python(body[c0:body.index("if (xr_zero) {")])
+    on_axis, off_axis, pw, slots = loop_bodies(src)
+    cden_a = [float.fromhex(v.strip()) for v in
+              re.search(r"kJitCdenA\[\d+\] = \{([^}]*)\}", src).group(1).split(",")]
+    m = re.search(r"kJitCdenXk\[\d+\] = \{([^}]*)\}", src)
+    cden_xk = [int(v) for v in m.group(1).split(",")] if m else [0] * len(cden_a)
+    m = re.search(r"kJitXvec\[\d+\] = \{([^}]*)\}", src)
+    xvec = (np.array([float.fromhex(v.strip()) for v in m.group(1).split(",")]).reshape(-1, n_ext)
+            if m else np.ones((1, 1)))
+    glb = dict(CHAIN_FUNCS)
+    exec(_device_functions(src), glb)
+    alpha, eps, boson = oracle_args
+    alpha = np.asarray(alpha)
+    sol = O.Solution(alpha, eps=eps, var_is_boson=boson, n_ext=n_ext)
+    rng = np.random.default_rng(17)
+    rows = {}
+    E = np.empty(alpha.shape[0])
+    for j, row in enumerate(map(tuple, alpha)):
+        rows.setdefault(row, float(rng.uniform(-2.0, 2.0)))
+        E[j] = rows[row]
+    beta = 1.1
+    on = np.array([1j * np.pi * (2 * q + 1) / beta for q in range(n_ext)])
+    off = np.array([0.6 - 0.3 * q + 0.04j for q in range(n_ext)])
+    for body_code, Xrow in ((on_axis, on), (off_axis, off)):
+        Y = xvec @ Xrow
+        ns = {"E%d" % j: float(E[j]) for j in range(len(E))}
+        ns.update(beta=beta, Xr_in=0.0)
+        for k, y in enumerate(Y):
+            ns["Yr_in_%d" % k] = y.real
+        for c, (a, k) in enumerate(zip(cden_a, cden_xk)):
+            ns["AXI_%d" % c], ns["AXI2_%d" % c] = a * Y[k].imag, (a * Y[k].imag) ** 2
+        exec(fwd + "\n" + body_code, dict(glb), ns)
+        want, _, env = sol.eval_energies(E[None, :], Xrow[None, :], beta)
+        got = complex(ns["vr"], ns["vi"])
+        assert abs(got - want[0, 0]) <= 1e-12 * env[0, 0] + 1e-300, (name, Xrow, got, want[0, 0])
