@@ -33,6 +33,17 @@ import paper_2311_17189_gb300 as T
 from paper_2311_17189_gb300 import workloads as W
 
 
+def _order6():
+    """Order-6 tables: the first, the first with second derivatives (diagram 70) and the one with
+    the most flat terms (the order-6 workload's)."""
+    ds = T.enumerate_sigma(6)
+    big = next(i for i, d in enumerate(ds) if d["code"] == tuple(W.ORDER6["code"]))
+    return [(i, ds[i]) for i in (0, 70, big)]
+
+
+ORDER6 = _order6()
+
+
 def tables():
     out = [("order2_bosonic", T.Diagram(W.ORDER2["alpha"], var_is_boson=W.ORDER2["var_is_boson"])),
            ("quadruple_pole", T.Diagram([[1, 0], [1, 0], [1, 0], [1, 0], [1, 1]],
@@ -40,7 +51,16 @@ def tables():
     for m in (2, 3, 4, 5):
         for i, d in enumerate(T.enumerate_sigma(m)):
             out.append((f"order{m}_{i}", T.Diagram(d["alpha"], eps=d["eps"])))
+    out += [(f"order6_{i}", T.Diagram(d["alpha"], eps=d["eps"])) for i, d in ORDER6]
     return out
+
+
+def _value_tables():
+    return ([("order2_bosonic", T.Diagram(W.ORDER2["alpha"], var_is_boson=W.ORDER2["var_is_boson"]),
+              (W.ORDER2["alpha"], None, W.ORDER2["var_is_boson"]))] +
+            [(f"order{m}_{i}", T.Diagram(d["alpha"], eps=d["eps"]), (d["alpha"], d["eps"], None))
+             for m in (2, 3, 4, 5) for i, d in enumerate(T.enumerate_sigma(m))] +
+            [(f"order6_{i}", T.Diagram(d["alpha"], eps=d["eps"]), (d["alpha"], d["eps"], None)) for i, d in ORDER6])
 
 
 HEX = re.compile(r"-?0x[0-9a-f.]+p[+-]\d+")
@@ -440,12 +460,7 @@ def test_line_energies_follow_the_momentum_labels(name, D, alpha):
 # ---- the generated value against the oracle, on the host
 
 @pytest.mark.parametrize("kind", ["forward", "fused"])
-@pytest.mark.parametrize("name,D,oracle_args", [
-    ("order2_bosonic", T.Diagram(W.ORDER2["alpha"], var_is_boson=W.ORDER2["var_is_boson"]),
-     (W.ORDER2["alpha"], None, W.ORDER2["var_is_boson"]))] +
-    [(f"order{m}_{i}", T.Diagram(d["alpha"], eps=d["eps"]), (d["alpha"], d["eps"], None))
-     for m in (2, 3, 4, 5) for i, d in enumerate(T.enumerate_sigma(m))],
-    ids=lambda v: v if isinstance(v, str) else "")
+@pytest.mark.parametrize("name,D,oracle_args", _value_tables(), ids=lambda v: v if isinstance(v, str) else "")
 def test_generated_value_matches_the_oracle(name, D, oracle_args, kind):
     """The generated per-sample code from the base energies on -- combinations, the Fermi/Bose
     segments, the pole DAG, the weights and one frequency of the loop -- run as Python, gives the
@@ -495,13 +510,6 @@ def _energy_kind_tables():
         a2 = W.hold_external(d["alpha"], m - 1)
         out.append((f"order{m}_{i}_two_external", T.Diagram(a2, eps=d["eps"], n_ext=2), (a2, d["eps"], None), 2))
     return out
-
-
-def _value_tables():
-    return ([("order2_bosonic", T.Diagram(W.ORDER2["alpha"], var_is_boson=W.ORDER2["var_is_boson"]),
-              (W.ORDER2["alpha"], None, W.ORDER2["var_is_boson"]))] +
-            [(f"order{m}_{i}", T.Diagram(d["alpha"], eps=d["eps"]), (d["alpha"], d["eps"], None))
-             for m in (2, 3, 4, 5) for i, d in enumerate(T.enumerate_sigma(m))])
 
 
 @pytest.mark.parametrize("name,D,oracle_args,n_ext", _energy_kind_tables(),
