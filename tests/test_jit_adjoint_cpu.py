@@ -558,3 +558,25 @@ def test_energy_kind_value_matches_the_oracle(name, D, oracle_args, n_ext):
         want, _, env = sol.eval_energies(E[None, :], Xrow[None, :], beta)
         got = complex(ns["vr"], ns["vi"])
         assert abs(got - want[0, 0]) <= 1e-12 * env[0, 0] + 1e-300, (name, Xrow, got, want[0, 0])
+
+
+def test_paper_order2_example_is_evaluated_in_factorised_form():
+    """The paper's order-2 example (Sec. 5, the tree of its factorisation figure): its four flat
+    terms A FT R share one denominator, and the generated pole DAG evaluates their Fermi part as a
+    product of two differences of Fermi/Bose values, [F_a - F_b][F_c - F_d] (three arithmetic DAG
+    steps), not as four products."""
+    sympy = pytest.importorskip("sympy")
+    D = T.Diagram(np.array([[1, 0, 0], [0, 1, 0], [-1, 1, 1]], dtype=np.int8))
+    assert D.info()["n_terms"] == 4
+    src = D.jit_source("forward")
+    body = src[src.index("double W2_0"):src.index("const double b0")]     # the DAG and the weight
+    fv = {v: sympy.Symbol(v) for v in set(re.findall(r"\bfv\d+\b", body))}
+    ns = dict(fv)
+    code = _python(body)
+    exec(code, {"fma": lambda a, b, c: a * b + c, "mul": lambda a, b: a * b}, ns)
+    w = sympy.expand(ns["W2_0"])
+    assert len(w.as_ordered_terms()) == 4                         # the four flat terms
+    factors = [f for f in sympy.factor_list(w)[1]]
+    assert len(factors) == 2 and all(len(sympy.Poly(f, *fv.values()).terms()) == 2 and e == 1
+                                      for f, e in factors)
+    assert len(re.findall(r"const double pv\d+ = (?:fma|imul_ftz)\(", body)) == 3   # (a copy is free)
