@@ -9,8 +9,8 @@ Only marshalling lives in Python; the construction is libtami's C++ and every ev
 step is a libtami CUDA kernel.  `workloads` holds the seeded synthetic inputs.
 """
 from . import _lib, mc
-from .api import Batch, Diagram, debug_set_wait_limit, enumerate_sigma, set_jit, set_table_staging
+from .api import Batch, Diagram, construct_many, debug_set_wait_limit, enumerate_sigma, set_jit, set_table_staging
 from . import graph
 
-__all__ = ["Batch", "Diagram", "debug_set_wait_limit", "enumerate_sigma", "graph", "_lib", "mc", "set_jit",
-           "set_table_staging"]
+__all__ = ["Batch", "Diagram", "construct_many", "debug_set_wait_limit", "enumerate_sigma", "graph", "_lib", "mc",
+           "set_jit", "set_table_staging"]

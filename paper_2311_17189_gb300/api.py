@@ -363,3 +363,19 @@ def enumerate_sigma(order):
                                          ctypes.byref(n)))
     return [{"alpha": a[i], "eps": e[i], "code": tuple(int(v) for v in c[i]), "loops": int(lo[i])}
             for i in range(cnt)]
+
+
+def construct_many(specs, threads=None):
+    """Diagrams for many label sets at once: each spec is a dict of Diagram's arguments (alpha,
+    and optionally eps, var_is_boson, order, prefactor, n_ext).  The constructions run on a pool of
+    host threads (libtami's construction keeps no shared state, and the ctypes call releases the
+    interpreter lock); the result is in the order of `specs`, the first failure is raised."""
+    from concurrent.futures import ThreadPoolExecutor
+    specs = list(specs)
+    if not specs:
+        return []
+    workers = max(1, min(len(specs), int(threads) if threads else (os.cpu_count() or 1)))
+    if workers == 1:
+        return [Diagram(**sp) for sp in specs]
+    with ThreadPoolExecutor(max_workers=workers) as pool:
+        return list(pool.map(lambda sp: Diagram(**sp), specs))

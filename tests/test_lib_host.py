@@ -148,3 +148,19 @@ def test_bench_construct_workload_runs_on_the_host():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert [d["terms"] for d in line["diagrams"]] == [4, 104, 744, 5136]
     assert line["order6_all"]["diagrams"] == 515 and all(d["ms"] > 0 for d in line["diagrams"])
+
+
+def test_construct_many_on_host_threads_equals_one_by_one():
+    """construct_many builds diagrams on a pool of host threads: the same tables (term counts, flop
+    model, generated kernels) in the order of the specs as constructing them one by one; a bad spec
+    raises the library's error."""
+    specs = [dict(alpha=d["alpha"], eps=d["eps"]) for d in T.enumerate_sigma(5)]
+    one = [T.Diagram(**sp) for sp in specs]
+    many = T.construct_many(specs, threads=4)
+    assert len(many) == len(one)
+    for a, b in zip(one, many):
+        assert a.info() == b.info()
+        assert a.jit_source("fused") == b.jit_source("fused")
+    assert T.construct_many([]) == []
+    with pytest.raises(L.TamiError):
+        T.construct_many(specs[:3] + [dict(alpha=np.zeros((17, 3), dtype=np.int8))], threads=2)
