@@ -55,9 +55,13 @@ def tables():
     return out
 
 
+QUAD = ([[1, 0], [1, 0], [1, 0], [1, 0], [1, 1]], [[1, 0, 0, 0, 0]] * 4 + [[0, 0, 0, 0, 1]], [0, 1])
+
+
 def _value_tables():
     return ([("order2_bosonic", T.Diagram(W.ORDER2["alpha"], var_is_boson=W.ORDER2["var_is_boson"]),
-              (W.ORDER2["alpha"], None, W.ORDER2["var_is_boson"]))] +
+              (W.ORDER2["alpha"], None, W.ORDER2["var_is_boson"])),
+             ("quadruple_pole", T.Diagram(QUAD[0], eps=QUAD[1], var_is_boson=QUAD[2]), QUAD)] +
             [(f"order{m}_{i}", T.Diagram(d["alpha"], eps=d["eps"]), (d["alpha"], d["eps"], None))
              for m in (2, 3, 4, 5) for i, d in enumerate(T.enumerate_sigma(m))] +
             [(f"order6_{i}", T.Diagram(d["alpha"], eps=d["eps"]), (d["alpha"], d["eps"], None)) for i, d in ORDER6])
